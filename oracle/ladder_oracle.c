@@ -1,0 +1,294 @@
+/*
+ * Plain FP64 CPU oracle for the particle-particle ladder term.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call, link or
+ * load this file; only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark use it.  It shares no code, header, table or helper with the
+ * CUDA library.
+ *
+ * Every routine is the definition written out with plain loops in double
+ * precision, in the order the paper states it, with no blocking, no symmetry
+ * shortcuts and no reordering beyond parallelising independent outputs.
+ *
+ * Notation (Sec. II): o = N_occ, v = N_vir, n = N_ABS (auxiliary functions).
+ *   B   [n][v][v]      RI factor of the virtual block, B[P][a][c] = m^P_ac
+ *   t1  [o][v]         singles t_i^a
+ *   t2  [o][o][v][v]   doubles t_ij^ab
+ *   tau [o][o][v][v]   tau_ij^ab
+ *   R   [o][o][v][v]   ladder term L_ij^ab
+ * All arrays are row-major (C order).
+ */
+#include <stddef.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define IDX4(i, j, a, b, o, v) ((((size_t)(i) * (o) + (j)) * (v) + (a)) * (v) + (b))
+#define IDX3(P, a, c, v) (((size_t)(P) * (v) + (a)) * (v) + (c))
+
+/* Eq. pp-Ladder-01: tau_ij^ab = t_ij^ab + t_i^a t_j^b. */
+void oracle_tau(int o, int v, const double *t1, const double *t2, double *tau)
+{
+    for (int i = 0; i < o; ++i)
+        for (int j = 0; j < o; ++j)
+            for (int a = 0; a < v; ++a)
+                for (int b = 0; b < v; ++b)
+                    tau[IDX4(i, j, a, b, o, v)] =
+                        t2[IDX4(i, j, a, b, o, v)] + t1[(size_t)i * v + a] * t1[(size_t)j * v + b];
+}
+
+/* One (a,b) column of the integrals under the RI factorisation (Eq. RIM with
+ * Eq. eri): V[c][d] = (ac|bd) = v^{ab}_{cd} = sum_P m^P_ac m^P_bd. */
+static void integrals_ab(int v, int n, const double *B, int a, int b, double *V)
+{
+    memset(V, 0, sizeof(double) * (size_t)v * v);
+    for (int P = 0; P < n; ++P)
+        for (int c = 0; c < v; ++c) {
+            const double bac = B[IDX3(P, a, c, v)];
+            for (int d = 0; d < v; ++d)
+                V[(size_t)c * v + d] += bac * B[IDX3(P, b, d, v)];
+        }
+}
+
+/* Eq. pp-Ladder-0 with the undressed integrals b^{ab}_{cd} = v^{ab}_{cd}:
+ * R_ij^ab = sum_{c,d} (ac|bd) tau_ij^cd, for every i, j, a, b. */
+void oracle_ladder(int o, int v, int n, const double *B, const double *tau, double *R)
+{
+    #pragma omp parallel
+    {
+        double *V = (double *)malloc(sizeof(double) * (size_t)v * v);
+        #pragma omp for schedule(dynamic)
+        for (int ab = 0; ab < v * v; ++ab) {
+            const int a = ab / v, b = ab % v;
+            integrals_ab(v, n, B, a, b, V);
+            for (int i = 0; i < o; ++i)
+                for (int j = 0; j < o; ++j) {
+                    double s = 0.0;
+                    for (int c = 0; c < v; ++c)
+                        for (int d = 0; d < v; ++d)
+                            s += V[(size_t)c * v + d] * tau[IDX4(i, j, c, d, o, v)];
+                    R[IDX4(i, j, a, b, o, v)] = s;
+                }
+        }
+        free(V);
+    }
+}
+
+/* The same result for a list of (a,b) columns only: Rsel[k][i][j] = R_ij^{a_k b_k}.
+ * Used for sampled checks at sizes where the full term takes too long. */
+void oracle_ladder_pairs(int o, int v, int n, const double *B, const double *tau,
+                         int npairs, const int *pa, const int *pb, double *Rsel)
+{
+    #pragma omp parallel
+    {
+        double *V = (double *)malloc(sizeof(double) * (size_t)v * v);
+        #pragma omp for schedule(dynamic)
+        for (int k = 0; k < npairs; ++k) {
+            integrals_ab(v, n, B, pa[k], pb[k], V);
+            for (int i = 0; i < o; ++i)
+                for (int j = 0; j < o; ++j) {
+                    double s = 0.0;
+                    for (int c = 0; c < v; ++c)
+                        for (int d = 0; d < v; ++d)
+                            s += V[(size_t)c * v + d] * tau[IDX4(i, j, c, d, o, v)];
+                    Rsel[((size_t)k * o + i) * o + j] = s;
+                }
+        }
+        free(V);
+    }
+}
+
+/* Brute force: build the whole four-virtual integral array v^{ab}_{cd}
+ * (Eq. eri under Eq. RIM) explicitly, then contract it with tau.  Only for
+ * tiny v (the array has v^4 entries). */
+int oracle_ladder_brute(int o, int v, int n, const double *B, const double *tau, double *R)
+{
+    const size_t v4 = (size_t)v * v * v * v;
+    double *I = (double *)calloc(v4, sizeof(double)); /* I[a][b][c][d] = (ac|bd) */
+    if (!I) return -1;
+    for (int a = 0; a < v; ++a)
+        for (int b = 0; b < v; ++b)
+            for (int c = 0; c < v; ++c)
+                for (int d = 0; d < v; ++d) {
+                    double s = 0.0;
+                    for (int P = 0; P < n; ++P)
+                        s += B[IDX3(P, a, c, v)] * B[IDX3(P, b, d, v)];
+                    I[IDX4(a, b, c, d, v, v)] = s;
+                }
+    for (int i = 0; i < o; ++i)
+        for (int j = 0; j < o; ++j)
+            for (int a = 0; a < v; ++a)
+                for (int b = 0; b < v; ++b) {
+                    double s = 0.0;
+                    for (int c = 0; c < v; ++c)
+                        for (int d = 0; d < v; ++d)
+                            s += I[IDX4(a, b, c, d, v, v)] * tau[IDX4(i, j, c, d, o, v)];
+                    R[IDX4(i, j, a, b, o, v)] = s;
+                }
+    free(I);
+    return 0;
+}
+
+/* Ladder energy E_L = sum_ijab R_ij^ab (2 t_ij^ab - t_ij^ba): the
+ * "twice direct minus exchange" weighting of the closed-shell CCSD energy
+ * expression (Sec. II.A) applied to the ladder term. */
+double oracle_energy(int o, int v, const double *R, const double *t2)
+{
+    double e = 0.0;
+    for (int i = 0; i < o; ++i)
+        for (int j = 0; j < o; ++j)
+            for (int a = 0; a < v; ++a)
+                for (int b = 0; b < v; ++b)
+                    e += R[IDX4(i, j, a, b, o, v)] *
+                         (2.0 * t2[IDX4(i, j, a, b, o, v)] - t2[IDX4(i, j, b, a, o, v)]);
+    return e;
+}
+
+/* Energy weights W_ij^ab = dE_L/dR_ij^ab = 2 t_ij^ab - t_ij^ba. */
+void oracle_energy_weights(int o, int v, const double *t2, double *W)
+{
+    for (int i = 0; i < o; ++i)
+        for (int j = 0; j < o; ++j)
+            for (int a = 0; a < v; ++a)
+                for (int b = 0; b < v; ++b)
+                    W[IDX4(i, j, a, b, o, v)] =
+                        2.0 * t2[IDX4(i, j, a, b, o, v)] - t2[IDX4(i, j, b, a, o, v)];
+}
+
+/* Gradient of E = sum_ijab W_ij^ab R_ij^ab with respect to tau, for fixed W:
+ * dE/dtau_ij^cd = sum_ab W_ij^ab (ac|bd). */
+void oracle_grad_tau(int o, int v, int n, const double *B, const double *W, double *dtau)
+{
+    const size_t total = (size_t)o * o * v * v;
+    memset(dtau, 0, sizeof(double) * total);
+    double *V = (double *)malloc(sizeof(double) * (size_t)v * v);
+    /* Each (a,b) column adds W_ij^ab V[c][d] into every dtau_ij^cd.  The loop
+     * over (a,b) stays serial so that the sum is taken in one fixed order. */
+    for (int a = 0; a < v; ++a)
+        for (int b = 0; b < v; ++b) {
+            integrals_ab(v, n, B, a, b, V);
+            #pragma omp parallel for
+            for (int ij = 0; ij < o * o; ++ij) {
+                const int i = ij / o, j = ij % o;
+                const double w = W[IDX4(i, j, a, b, o, v)];
+                for (int c = 0; c < v; ++c)
+                    for (int d = 0; d < v; ++d)
+                        dtau[IDX4(i, j, c, d, o, v)] += w * V[(size_t)c * v + d];
+            }
+        }
+    free(V);
+}
+
+/* Gradient with respect to the RI factor, for fixed W and tau.  Each factor
+ * m^P_xy enters (ac|bd) once as m^P_ac (a=x, c=y) and once as m^P_bd (b=x,
+ * d=y):
+ *   dE/dB[P][x][y] = sum_{ij,b,d} W_ij^{xb} tau_ij^{yd} B[P][b][d]
+ *                  + sum_{ij,a,c} W_ij^{ax} tau_ij^{cy} B[P][a][c].
+ * Both terms are evaluated as written; no symmetry of W or tau is assumed. */
+void oracle_grad_B(int o, int v, int n, const double *B, const double *tau,
+                   const double *W, double *dB)
+{
+    memset(dB, 0, sizeof(double) * (size_t)n * v * v);
+    #pragma omp parallel
+    {
+        double *G = (double *)malloc(sizeof(double) * (size_t)v * v);
+        #pragma omp for schedule(dynamic)
+        for (int x = 0; x < v; ++x) {
+            /* first term: for each b, G[y][d] = sum_ij W_ij^{xb} tau_ij^{yd} */
+            for (int b = 0; b < v; ++b) {
+                memset(G, 0, sizeof(double) * (size_t)v * v);
+                for (int i = 0; i < o; ++i)
+                    for (int j = 0; j < o; ++j) {
+                        const double w = W[IDX4(i, j, x, b, o, v)];
+                        for (int y = 0; y < v; ++y)
+                            for (int d = 0; d < v; ++d)
+                                G[(size_t)y * v + d] += w * tau[IDX4(i, j, y, d, o, v)];
+                    }
+                for (int P = 0; P < n; ++P)
+                    for (int y = 0; y < v; ++y) {
+                        double s = 0.0;
+                        for (int d = 0; d < v; ++d)
+                            s += G[(size_t)y * v + d] * B[IDX3(P, b, d, v)];
+                        dB[IDX3(P, x, y, v)] += s;
+                    }
+            }
+            /* second term: for each a, G[c][y] = sum_ij W_ij^{ax} tau_ij^{cy} */
+            for (int a = 0; a < v; ++a) {
+                memset(G, 0, sizeof(double) * (size_t)v * v);
+                for (int i = 0; i < o; ++i)
+                    for (int j = 0; j < o; ++j) {
+                        const double w = W[IDX4(i, j, a, x, o, v)];
+                        for (int c = 0; c < v; ++c)
+                            for (int y = 0; y < v; ++y)
+                                G[(size_t)c * v + y] += w * tau[IDX4(i, j, c, y, o, v)];
+                    }
+                for (int P = 0; P < n; ++P)
+                    for (int y = 0; y < v; ++y) {
+                        double s = 0.0;
+                        for (int c = 0; c < v; ++c)
+                            s += G[(size_t)c * v + y] * B[IDX3(P, a, c, v)];
+                        dB[IDX3(P, x, y, v)] += s;
+                    }
+            }
+        }
+        free(G);
+    }
+}
+
+/* Selected entries of dE/dtau: out[k] = sum_ab W_{i_k j_k}^{ab} (a c_k | b d_k). */
+void oracle_grad_tau_entries(int o, int v, int n, const double *B, const double *W,
+                             int m, const int *ei, const int *ej, const int *ec,
+                             const int *ed, double *out)
+{
+    #pragma omp parallel for schedule(dynamic)
+    for (int k = 0; k < m; ++k) {
+        double s = 0.0;
+        for (int a = 0; a < v; ++a)
+            for (int b = 0; b < v; ++b) {
+                double vint = 0.0;
+                for (int P = 0; P < n; ++P)
+                    vint += B[IDX3(P, a, ec[k], v)] * B[IDX3(P, b, ed[k], v)];
+                s += W[IDX4(ei[k], ej[k], a, b, o, v)] * vint;
+            }
+        out[k] = s;
+    }
+}
+
+/* Selected entries of dE/dB, both terms as in oracle_grad_B. */
+void oracle_grad_B_entries(int o, int v, int n, const double *B, const double *tau,
+                           const double *W, int m, const int *eP, const int *ex,
+                           const int *ey, double *out)
+{
+    #pragma omp parallel for schedule(dynamic)
+    for (int k = 0; k < m; ++k) {
+        const int P = eP[k], x = ex[k], y = ey[k];
+        double s = 0.0;
+        for (int i = 0; i < o; ++i)
+            for (int j = 0; j < o; ++j) {
+                for (int b = 0; b < v; ++b) {
+                    const double w = W[IDX4(i, j, x, b, o, v)];
+                    double t = 0.0;
+                    for (int d = 0; d < v; ++d)
+                        t += tau[IDX4(i, j, y, d, o, v)] * B[IDX3(P, b, d, v)];
+                    s += w * t;
+                }
+                for (int a = 0; a < v; ++a) {
+                    const double w = W[IDX4(i, j, a, x, o, v)];
+                    double t = 0.0;
+                    for (int c = 0; c < v; ++c)
+                        t += tau[IDX4(i, j, c, y, o, v)] * B[IDX3(P, a, c, v)];
+                    s += w * t;
+                }
+            }
+        out[k] = s;
+    }
+}
+
+int oracle_threads(void)
+{
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
