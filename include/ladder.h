@@ -1,0 +1,134 @@
+/*
+ * ladder.h -- C ABI of the GB300 particle-particle ladder library.
+ *
+ * The library evaluates the closed-shell pp-ladder term of RI-CCSD
+ * (arxiv 1810.08142, Sec. II.C):
+ *
+ *   R_ij^ab = sum_cd v^{ab}_{cd} tau_ij^cd                    (Eq. pp-Ladder-0)
+ *   tau_ij^ab = t_ij^ab + t_i^a t_j^b                         (Eq. pp-Ladder-01)
+ *   v^{ab}_{cd} = (ac|bd) = sum_P B^P_ac B^P_bd               (Eq. eri with Eq. RIM)
+ *
+ * with the undressed integrals (no t1 dressing of Eq. pp-Ladder-1), and the
+ * ladder energy E_L = sum_ijab R_ij^ab (2 t_ij^ab - t_ij^ba).
+ *
+ * Conventions for every call:
+ *   - Indices: o = number of occupied orbitals (i, j), v = number of virtual
+ *     orbitals (a, b, c, d), naux = number of auxiliary functions (P).
+ *   - Arrays are float64, C order (last index fastest), device pointers unless
+ *     a name ends in _host, caller-owned, 16-byte aligned:
+ *       B    [naux][v][v]    B[P][a][c] = B^P_ac (no a<->c symmetry assumed)
+ *       t1   [o][v]          t_i^a
+ *       t2   [o][o][v][v]    t_ij^ab
+ *       tau  [o][o][v][v]    tau_ij^ab
+ *       R    [o][o][v][v]    R_ij^ab
+ *   - tau (and t2) must have the pair symmetry tau_ij^cd = tau_ji^dc of
+ *     Sec. II.C.  Only the blocks with i <= j are read; R is written in full.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream).  No call synchronises the device or allocates device
+ *     memory after ladder_set_workspace.
+ *   - Argument errors are returned synchronously and nothing is enqueued.
+ *     Errors found on the device (a bounded wait that ran out) are recorded in
+ *     a status word inside the workspace; ladder_last_device_error reads it.
+ *   - A plan is not thread safe: one host thread at a time per plan, and calls
+ *     that share a plan's workspace must not overlap on the device (enqueue
+ *     them on one stream).
+ */
+#ifndef LADDER_H
+#define LADDER_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ladder_plan_s *ladder_plan_t;
+
+typedef enum {
+    LADDER_OK = 0,
+    LADDER_EINVAL = 1,      /* bad size, null or misaligned pointer, bad mode */
+    LADDER_ENOMEM = 2,      /* host allocation failed */
+    LADDER_ECUDA = 3,       /* a CUDA runtime or driver call failed */
+    LADDER_ETIMEOUT = 4,    /* a bounded device wait ran out (device status) */
+    LADDER_ENOTSUP = 5,     /* mode or shape not supported on this device */
+    LADDER_EWORKSPACE = 6   /* workspace missing or too small */
+} ladder_status;
+
+typedef enum {
+    LADDER_FP64 = 0,        /* plain method: FP64 tensor-core (DMMA) path, exact to rounding */
+    LADDER_BF16X3 = 1,      /* split BF16, two slices (hi, lo), three products, FP32 accumulation */
+    LADDER_BF16X6 = 2,      /* split BF16, three slices, six products, FP32 accumulation */
+    LADDER_AUTO = 3         /* let the plan pick (autotuned cache, else BF16X6) */
+} ladder_mode;
+
+/* Create a plan for one shape.  1 <= o <= 256, 1 <= v <= 4096, 1 <= naux <= 65536.
+ * The plan owns no device memory; see ladder_workspace_size. */
+ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out);
+
+/* Mode the plan resolved to (LADDER_AUTO resolves at plan time). */
+ladder_status ladder_plan_mode(ladder_plan_t plan, int *mode);
+
+/* Bytes of device scratch the plan needs (slices of B and tau, packed pair
+ * combinations, reduction partials, the device status word).  The caller
+ * allocates it and hands it over with ladder_set_workspace; the plan keeps
+ * the pointer (not the memory) until ladder_destroy or the next call. */
+ladder_status ladder_workspace_size(ladder_plan_t plan, size_t *bytes);
+ladder_status ladder_set_workspace(ladder_plan_t plan, void *dptr, size_t bytes);
+
+/* Eq. pp-Ladder-01: tau = t2 + t1 (x) t1 on the device, in FP64.  tau may not alias t2. */
+ladder_status ladder_tau(ladder_plan_t plan, const double *t1, const double *t2,
+                         double *tau, void *stream);
+
+/* Eq. pp-Ladder-0: R_ij^ab = sum_cd (ac|bd) tau_ij^cd.  R is overwritten (not
+ * accumulated); R may not alias B or tau.  The (ac|bd) integrals are formed
+ * tile by tile on chip and never written to memory. */
+ladder_status ladder_apply(ladder_plan_t plan, const double *B, const double *tau,
+                           double *R, void *stream);
+
+/* E_L = sum_ijab R_ij^ab (2 t_ij^ab - t_ij^ba), reduced in FP64 in a fixed
+ * order (bitwise reproducible); writes one double at E_dev (device memory). */
+ladder_status ladder_energy(ladder_plan_t plan, const double *R, const double *t2,
+                            double *E_dev, void *stream);
+
+/* Adjoint of ladder_apply for E = sum W_ij^ab R_ij^ab with fixed weights W
+ * (W must be pair symmetric, W_ij^ab = W_ji^ba; for E_L, W = 2 t2 - t2^T):
+ *   dtau_ij^cd = sum_ab W_ij^ab (ac|bd)                          (transposed ladder)
+ *   dB^P_xy    = sum_{ij,b,d} W_ij^{xb} tau_ij^{yd} B^P_bd
+ *              + sum_{ij,a,c} W_ij^{ax} tau_ij^{cy} B^P_ac
+ * Either output may be NULL to skip it.  Outputs are overwritten. */
+ladder_status ladder_backward(ladder_plan_t plan, const double *B, const double *tau,
+                              const double *W, double *dtau, double *dB, void *stream);
+
+/* Host-buffer convenience path: copies B and tau from host memory (pinned
+ * memory recommended), runs ladder_apply and ladder_energy-free apply, and
+ * copies R back to R_host.  Needs device buffers d_B, d_tau, d_R of the
+ * sizes above, supplied by the caller.  Synchronises `stream` before return. */
+ladder_status ladder_apply_host(ladder_plan_t plan, const double *B_host, const double *tau_host,
+                                double *R_host, double *d_B, double *d_tau, double *d_R,
+                                void *stream);
+
+/* Ragged batch: n molecules with their own (o_k, v_k, naux_k), one plan. */
+ladder_status ladder_plan_batched(int n, const int *o, const int *v, const int *naux, int mode,
+                                  ladder_plan_t *out);
+/* B[k], tau[k], R[k] are device pointers for molecule k (host arrays of n pointers). */
+ladder_status ladder_apply_batched(ladder_plan_t plan, const double *const *B,
+                                   const double *const *tau, double *const *R, void *stream);
+
+/* Reads and clears the device status word (synchronises `stream`).
+ * Returns LADDER_OK or LADDER_ETIMEOUT; *where receives the site code of the
+ * first failed wait (0 if none) when where != NULL. */
+ladder_status ladder_last_device_error(ladder_plan_t plan, void *stream, int *where);
+
+/* Algorithmic flop count of one ladder_apply (two flops per multiply-add of
+ * the symmetric/antisymmetric scheme; identical for every mode). */
+double ladder_flops(ladder_plan_t plan);
+
+const char *ladder_status_string(ladder_status s);
+
+void ladder_destroy(ladder_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LADDER_H */

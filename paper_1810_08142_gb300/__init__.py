@@ -1,0 +1,231 @@
+"""GB300 particle-particle ladder library: thin Python binding of libladder.so.
+
+Every function below has the name of the C entry point it wraps (see
+include/ladder.h) and only marshals arguments: torch tensors are passed as raw
+device pointers plus the current CUDA stream.  All arithmetic runs in the CUDA
+kernels of the shared library; there is no CPU fallback, and importing this
+package on a machine without the built library raises.
+
+The term (arxiv 1810.08142, Sec. II.C):
+    R_ij^ab = sum_cd (ac|bd) tau_ij^cd,   tau = t2 + t1 (x) t1,
+    (ac|bd) = sum_P B^P_ac B^P_bd,        E_L = sum R_ij^ab (2 t_ij^ab - t_ij^ba).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libladder.so")
+
+LADDER_FP64, LADDER_BF16X3, LADDER_BF16X6, LADDER_AUTO = 0, 1, 2, 3
+MODES = {"fp64": LADDER_FP64, "bf16x3": LADDER_BF16X3, "bf16x6": LADDER_BF16X6, "auto": LADDER_AUTO}
+STATUS = {0: "LADDER_OK", 1: "LADDER_EINVAL", 2: "LADDER_ENOMEM", 3: "LADDER_ECUDA",
+          4: "LADDER_ETIMEOUT", 5: "LADDER_ENOTSUP", 6: "LADDER_EWORKSPACE"}
+
+# every entry point that include/ladder.h declares
+EXPORTS = ("ladder_plan", "ladder_plan_mode", "ladder_workspace_size", "ladder_set_workspace",
+           "ladder_tau", "ladder_apply", "ladder_energy", "ladder_backward", "ladder_apply_host",
+           "ladder_plan_batched", "ladder_apply_batched", "ladder_last_device_error",
+           "ladder_flops", "ladder_status_string", "ladder_destroy")
+
+
+class LadderError(RuntimeError):
+    def __init__(self, func, status):
+        self.status = status
+        super().__init__("%s failed: %s" % (func, STATUS.get(status, status)))
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libladder.so (built by build.py); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libladder.so is not built (run `python -m paper_1810_08142_gb300.build`)")
+    lib = ctypes.CDLL(path)
+    i, pp, sz = ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t
+    ip = ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "ladder_plan": [i, i, i, i, pp],
+        "ladder_plan_mode": [_P, ip],
+        "ladder_workspace_size": [_P, ctypes.POINTER(sz)],
+        "ladder_set_workspace": [_P, _P, sz],
+        "ladder_tau": [_P, _P, _P, _P, _P],
+        "ladder_apply": [_P, _P, _P, _P, _P],
+        "ladder_energy": [_P, _P, _P, _P, _P],
+        "ladder_backward": [_P, _P, _P, _P, _P, _P, _P],
+        "ladder_apply_host": [_P, _P, _P, _P, _P, _P, _P, _P],
+        "ladder_plan_batched": [i, ip, ip, ip, i, pp],
+        "ladder_apply_batched": [_P, pp, pp, pp, _P],
+        "ladder_last_device_error": [_P, _P, ip],
+        "ladder_flops": [_P],
+        "ladder_status_string": [i],
+        "ladder_destroy": [_P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.ladder_flops.restype = ctypes.c_double
+    lib.ladder_status_string.restype = ctypes.c_char_p
+    lib.ladder_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def _check(name, st):
+    if st != 0:
+        raise LadderError(name, st)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# ---- one-to-one wrappers ---------------------------------------------------
+def ladder_plan(o: int, v: int, naux: int, mode: int) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check("ladder_plan", load_library().ladder_plan(o, v, naux, mode, ctypes.byref(h)))
+    return h
+
+
+def ladder_plan_mode(plan) -> int:
+    m = ctypes.c_int()
+    _check("ladder_plan_mode", load_library().ladder_plan_mode(plan, ctypes.byref(m)))
+    return m.value
+
+
+def ladder_workspace_size(plan) -> int:
+    n = ctypes.c_size_t()
+    _check("ladder_workspace_size", load_library().ladder_workspace_size(plan, ctypes.byref(n)))
+    return n.value
+
+
+def ladder_set_workspace(plan, ws) -> None:
+    _check("ladder_set_workspace",
+           load_library().ladder_set_workspace(plan, _ptr(ws), ws.numel() * ws.element_size()))
+
+
+def ladder_tau(plan, t1, t2, tau, stream=None) -> None:
+    _check("ladder_tau", load_library().ladder_tau(plan, _ptr(t1), _ptr(t2), _ptr(tau), _stream(stream)))
+
+
+def ladder_apply(plan, B, tau, R, stream=None) -> None:
+    _check("ladder_apply", load_library().ladder_apply(plan, _ptr(B), _ptr(tau), _ptr(R), _stream(stream)))
+
+
+def ladder_energy(plan, R, t2, E, stream=None) -> None:
+    _check("ladder_energy", load_library().ladder_energy(plan, _ptr(R), _ptr(t2), _ptr(E), _stream(stream)))
+
+
+def ladder_backward(plan, B, tau, W, dtau, dB, stream=None) -> None:
+    _check("ladder_backward", load_library().ladder_backward(
+        plan, _ptr(B), _ptr(tau), _ptr(W), _ptr(dtau), _ptr(dB), _stream(stream)))
+
+
+def ladder_apply_host(plan, B_host, tau_host, R_host, d_B, d_tau, d_R, stream=None) -> None:
+    _check("ladder_apply_host", load_library().ladder_apply_host(
+        plan, _ptr(B_host), _ptr(tau_host), _ptr(R_host), _ptr(d_B), _ptr(d_tau), _ptr(d_R),
+        _stream(stream)))
+
+
+def ladder_plan_batched(o, v, naux, mode: int) -> ctypes.c_void_p:
+    n = len(o)
+    arr = lambda xs: (ctypes.c_int * n)(*[int(x) for x in xs])
+    h = ctypes.c_void_p()
+    _check("ladder_plan_batched",
+           load_library().ladder_plan_batched(n, arr(o), arr(v), arr(naux), mode, ctypes.byref(h)))
+    return h
+
+
+def ladder_apply_batched(plan, Bs, taus, Rs, stream=None) -> None:
+    n = len(Bs)
+    arr = lambda ts: (ctypes.c_void_p * n)(*[t.data_ptr() for t in ts])
+    _check("ladder_apply_batched", load_library().ladder_apply_batched(
+        plan, arr(Bs), arr(taus), arr(Rs), _stream(stream)))
+
+
+def ladder_last_device_error(plan, stream=None):
+    where = ctypes.c_int()
+    st = load_library().ladder_last_device_error(plan, _stream(stream), ctypes.byref(where))
+    return st, where.value
+
+
+def ladder_status_string(status: int) -> str:
+    return load_library().ladder_status_string(int(status)).decode()
+
+
+def ladder_flops(plan) -> float:
+    return float(load_library().ladder_flops(plan))
+
+
+def ladder_destroy(plan) -> None:
+    load_library().ladder_destroy(plan)
+
+
+# ---- convenience object ------------------------------------------------------
+class Ladder:
+    """A plan plus its workspace (a torch uint8 tensor on the current device)."""
+
+    def __init__(self, o: int, v: int, naux: int, mode="bf16x6", device=None):
+        import torch
+        self.o, self.v, self.naux = o, v, naux
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        self.device = torch.device(device if device is not None else "cuda")
+        with torch.cuda.device(self.device):
+            self.plan = ladder_plan(o, v, naux, m)
+            self.mode = ladder_plan_mode(self.plan)
+            n = ladder_workspace_size(self.plan)
+            self.workspace = torch.empty(max(n, 256), dtype=torch.uint8, device=self.device)
+            ladder_set_workspace(self.plan, self.workspace)
+
+    @property
+    def flops(self) -> float:
+        return ladder_flops(self.plan)
+
+    def tau(self, t1, t2, out=None):
+        import torch
+        out = torch.empty_like(t2) if out is None else out
+        ladder_tau(self.plan, t1, t2, out)
+        return out
+
+    def apply(self, B, tau, out=None):
+        import torch
+        out = torch.empty_like(tau) if out is None else out
+        ladder_apply(self.plan, B, tau, out)
+        return out
+
+    def energy(self, R, t2, out=None):
+        import torch
+        out = torch.empty((), dtype=torch.float64, device=R.device) if out is None else out
+        ladder_energy(self.plan, R, t2, out)
+        return out
+
+    def check_device(self):
+        st, where = ladder_last_device_error(self.plan)
+        if st != 0:
+            raise LadderError("device wait (site %d)" % where, st)
+
+    def close(self):
+        if getattr(self, "plan", None) is not None:
+            ladder_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,242 @@
+// Preparation and reduction kernels of the ladder path:
+//   tau assembly (Eq. pp-Ladder-01), packing of tau into the symmetric and
+//   antisymmetric pair combinations (FP64 or BF16 slices), slicing of the RI
+//   factor into K-major BF16 slices, and the FP64 ladder energy.
+// All of these are bandwidth-bound O(o^2 v^2) or O(N v^2) passes.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ladder {
+
+// ---------------------------------------------------------------- tau
+// tau_ij^ab = t_ij^ab + t_i^a t_j^b, one thread per (i, j, a, b), FP64.
+__global__ void tau_kernel(int o, int v, const double *__restrict__ t1,
+                           const double *__restrict__ t2, double *__restrict__ tau) {
+  const size_t total = (size_t)o * o * v * v;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(idx % v);
+    size_t r = idx / v;
+    const int a = (int)(r % v);
+    r /= v;
+    const int j = (int)(r % o);
+    const int i = (int)(r / o);
+    tau[idx] = t2[idx] + t1[(size_t)i * v + a] * t1[(size_t)j * v + b];
+  }
+}
+
+void launch_tau(int o, int v, const double *t1, const double *t2, double *tau,
+                cudaStream_t s) {
+  const size_t total = (size_t)o * o * v * v;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  tau_kernel<<<blocks, 256, 0, s>>>(o, v, t1, t2, tau);
+}
+
+// ---------------------------------------------------------------- slices
+// x = s0 + s1 + s2 + ..., each s_k the BF16 rounding (to nearest) of what the
+// earlier slices leave; the remainders are exact in FP64.
+template <int S>
+__device__ __forceinline__ void split_bf16(double x, __nv_bfloat16 (&out)[S]) {
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    out[k] = __double2bfloat16(x);
+    x -= (double)__bfloat162float(out[k]);
+  }
+}
+
+// ---------------------------------------------------------------- tau pm
+// Packed pair combinations, rows = occupied pairs, columns = K slots:
+//   Tp[lam+][p*64 + cl*8 + dl] = w_p (tau_ij^cd + tau_ij^dc) / 2   (i <= j)
+//   Tm[lam-][p*64 + cl*8 + dl] = w_p (tau_ij^cd - tau_ij^dc) / 2   (i <  j)
+// with block pair p = (k, l), c = 8k + cl, d = 8l + dl, w_p = 1/2 for k = l.
+// Entries with c or d >= v are zero.  grid.x covers the K slots of one row in
+// chunks, grid.y the rows (plus rows first, then minus rows).
+// For the BF16 layout the output is [slice][row][K].
+template <typename T, int S>
+__global__ void pack_tpm_kernel(int o, int v, int K, int nlp, int nlm,
+                                const double *__restrict__ tau, T *__restrict__ Tp,
+                                T *__restrict__ Tm, size_t slice_stride_p,
+                                size_t slice_stride_m) {
+  const int row = blockIdx.y;
+  const bool plus = row < nlp;
+  int i, j;
+  if (plus)
+    lam_plus(row, i, j);
+  else
+    lam_minus(row - nlp, i, j);
+  const double *tij = tau + ((size_t)i * o + j) * v * v;
+  const int lrow = plus ? row : row - nlp;
+  T *dst = plus ? Tp : Tm;
+  const size_t sstride = plus ? slice_stride_p : slice_stride_m;
+  for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < K; col += gridDim.x * blockDim.x) {
+    const int p = col / SLOTS, s = col % SLOTS;
+    int k, l;
+    pair_of(p, k, l);
+    const int c = k * CB + s / CB, d = l * CB + s % CB;
+    double val = 0.0;
+    if (c < v && d < v) {
+      const double w = (k == l) ? 0.25 : 0.5;
+      const double x = tij[(size_t)c * v + d], y = tij[(size_t)d * v + c];
+      val = plus ? w * (x + y) : w * (x - y);
+    }
+    if constexpr (S == 0) {
+      dst[(size_t)lrow * K + col] = (T)val;
+    } else {
+      __nv_bfloat16 sl[S];
+      split_bf16<S>(val, sl);
+#pragma unroll
+      for (int q = 0; q < S; ++q) dst[q * sstride + (size_t)lrow * K + col] = sl[q];
+    }
+  }
+}
+
+void launch_pack_tpm_f64(int o, int v, int K, const double *tau, double *Tp, double *Tm,
+                         cudaStream_t s) {
+  const int nlp = ppos(o), nlm = pneg(o);
+  dim3 grid((K + 255) / 256 < 64 ? (K + 255) / 256 : 64, nlp + nlm);
+  pack_tpm_kernel<double, 0><<<grid, 256, 0, s>>>(o, v, K, nlp, nlm, tau, Tp, Tm, 0, 0);
+}
+
+void launch_pack_tpm_bf16(int o, int v, int K, int nslices, int rows_p, int rows_m,
+                          const double *tau, __nv_bfloat16 *Tp, __nv_bfloat16 *Tm,
+                          cudaStream_t s) {
+  const int nlp = ppos(o), nlm = pneg(o);
+  dim3 grid((K + 255) / 256 < 64 ? (K + 255) / 256 : 64, nlp + nlm);
+  const size_t sp = (size_t)rows_p * K, sm = (size_t)rows_m * K;
+  if (nslices == 2)
+    pack_tpm_kernel<__nv_bfloat16, 2><<<grid, 256, 0, s>>>(o, v, K, nlp, nlm, tau, Tp, Tm, sp, sm);
+  else
+    pack_tpm_kernel<__nv_bfloat16, 3><<<grid, 256, 0, s>>>(o, v, K, nlp, nlm, tau, Tp, Tm, sp, sm);
+}
+
+// ---------------------------------------------------------------- B slices
+// Bt[q][a][c][P] = slice q of B[P][a][c]; a, c < vp (zero beyond v),
+// P < Np (zero beyond N).  32x32 tiles through shared memory so both the
+// read (c fastest) and the write (P fastest) are coalesced.
+template <int S>
+__global__ void split_B_kernel(int N, int v, int vp, int Np, const double *__restrict__ B,
+                               __nv_bfloat16 *__restrict__ Bt) {
+  __shared__ double tile[32][33];
+  const int a = blockIdx.z;
+  const int c0 = blockIdx.x * 32, P0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int P = P0 + r, c = c0 + tx;
+    tile[r][tx] = (P < N && c < v && a < v) ? B[((size_t)P * v + a) * v + c] : 0.0;
+  }
+  __syncthreads();
+  const size_t slice = (size_t)vp * vp * Np;
+  for (int r = ty; r < 32; r += 8) {
+    const int c = c0 + r, P = P0 + tx;
+    if (c < vp && P < Np) {
+      __nv_bfloat16 sl[S];
+      split_bf16<S>(tile[tx][r], sl);
+      const size_t off = ((size_t)a * vp + c) * Np + P;
+#pragma unroll
+      for (int q = 0; q < S; ++q) Bt[q * slice + off] = sl[q];
+    }
+  }
+}
+
+void launch_split_B(int N, int v, int vp, int Np, int nslices, const double *B,
+                    __nv_bfloat16 *Bt, cudaStream_t s) {
+  dim3 grid((vp + 31) / 32, (Np + 31) / 32, vp), block(32, 8);
+  if (nslices == 2)
+    split_B_kernel<2><<<grid, block, 0, s>>>(N, v, vp, Np, B, Bt);
+  else
+    split_B_kernel<3><<<grid, block, 0, s>>>(N, v, vp, Np, B, Bt);
+}
+
+// ---------------------------------------------------------------- energy
+// E_L = sum_ijab R_ij^ab (2 t_ij^ab - t_ij^ba).  Stage 1: block (tile, ij)
+// sums a 32x32 (a, b) tile with the transposed t tile staged in shared memory,
+// writes one partial per block; stage 2: one block adds the partials in a
+// fixed order.  Same inputs, same bits.
+constexpr int kEnergyThreads = 256;
+
+__device__ __forceinline__ double block_sum(double x, double *red) {
+  for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  if (l == 0) red[w] = x;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x / 32); ++k) s += red[k];
+  __syncthreads();
+  return s;
+}
+
+__global__ void energy_partial_kernel(int o, int v, const double *__restrict__ R,
+                                      const double *__restrict__ t2, double *__restrict__ part) {
+  __shared__ double tt[32][33];
+  __shared__ double red[kEnergyThreads / 32];
+  const int nt = (v + 31) / 32;
+  const int ta = blockIdx.x / nt, tb = blockIdx.x % nt;
+  const int ij = blockIdx.y;
+  const size_t base = (size_t)ij * v * v;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8
+  // transposed tile: tt[b_local][a_local] = t_ij^{b a}
+  for (int r = ty; r < 32; r += 8) {
+    const int b = tb * 32 + r, a = ta * 32 + tx;
+    tt[r][tx] = (a < v && b < v) ? t2[base + (size_t)b * v + a] : 0.0;
+  }
+  __syncthreads();
+  double acc = 0.0;
+  for (int r = ty; r < 32; r += 8) {
+    const int a = ta * 32 + r, b = tb * 32 + tx;
+    if (a < v && b < v) {
+      const size_t e = base + (size_t)a * v + b;
+      acc += R[e] * (2.0 * t2[e] - tt[tx][r]);
+    }
+  }
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) part[(size_t)ij * gridDim.x + blockIdx.x] = s;
+}
+
+__global__ void energy_final_kernel(size_t n, const double *__restrict__ part,
+                                    double *__restrict__ E) {
+  __shared__ double red[kEnergyThreads / 32];
+  double acc = 0.0;
+  for (size_t k = threadIdx.x; k < n; k += blockDim.x) acc += part[k];
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) *E = s;
+}
+
+size_t energy_partials(int o, int v) {
+  const int nt = (v + 31) / 32;
+  return (size_t)nt * nt * o * o;
+}
+
+void launch_energy(int o, int v, const double *R, const double *t2, double *part, double *E,
+                   cudaStream_t s) {
+  const int nt = (v + 31) / 32;
+  dim3 grid(nt * nt, o * o);
+  energy_partial_kernel<<<grid, kEnergyThreads, 0, s>>>(o, v, R, t2, part);
+  energy_final_kernel<<<1, kEnergyThreads, 0, s>>>(energy_partials(o, v), part, E);
+}
+
+// Energy weights W = 2 t2 - t2^T (the adjoint seed of E_L with respect to R).
+__global__ void energy_weights_kernel(int o, int v, const double *__restrict__ t2,
+                                      double *__restrict__ W) {
+  const size_t total = (size_t)o * o * v * v;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(idx % v);
+    const size_t r = idx / v;
+    const int a = (int)(r % v);
+    const size_t ij = r / v;
+    W[idx] = 2.0 * t2[idx] - t2[(ij * v + b) * v + a];
+  }
+}
+
+void launch_energy_weights(int o, int v, const double *t2, double *W, cudaStream_t s) {
+  const size_t total = (size_t)o * o * v * v;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  energy_weights_kernel<<<blocks, 256, 0, s>>>(o, v, t2, W);
+}
+
+}  // namespace ladder

@@ -1,0 +1,26 @@
+"""Helpers shared by the GPU tests: device copies of synthetic inputs and the
+error measures the tolerances are stated in."""
+import numpy as np
+
+
+def rel_fro(x, ref):
+    x = np.asarray(x, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.linalg.norm(x - ref) / max(np.linalg.norm(ref), 1e-300))
+
+
+def to_dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run_forward(L, x):
+    """tau, R and E_L through the C ABI for inputs x (synthetic.Inputs)."""
+    import torch
+    t1, t2, B = to_dev(x.t1), to_dev(x.t2), to_dev(x.B)
+    tau = L.tau(t1, t2)
+    R = L.apply(B, tau)
+    E = L.energy(R, t2)
+    torch.cuda.synchronize()
+    L.check_device()
+    return tau.cpu().numpy(), R.cpu().numpy(), float(E.item())
