@@ -2,6 +2,7 @@
 #pragma once
 #include <cstddef>
 #include <cuda_runtime.h>
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -37,5 +38,35 @@ constexpr int kFp64LamTile = 64;  // max lambda+ (and lambda-) rows per chunk
 int fp64_grid(const Fp64Args &a, int sm_count);
 size_t fp64_slab_doubles(int K, int grid);
 cudaError_t launch_ladder_fp64(const Fp64Args &a, int grid, cudaStream_t s);
+
+// ---- split-BF16 fused ladder (tcgen05)
+// An occupied-pair chunk of the tensor-core kernel: lambda+ rows [lp0, lp0+np)
+// and lambda- rows [lm0, lm0+nm), padded to nps, nms (multiples of 16) TMEM
+// columns; nps + nms <= kTcMaxCols.
+constexpr int kTcMaxCols = 128;
+struct TcChunk {
+  int lp0, lm0, np, nm, nps, nms;
+};
+struct TcArgs {
+  CUtensorMap tmA;   // B slices, box (32 aux, 8 c, 16 a), 64-byte swizzle
+  CUtensorMap tmB;   // B slices, box (32 aux, 8 d, 8 b)
+  CUtensorMap tmTp;  // tau+ slices [S][lambda+][K], box (16 slots, 16 rows, 1)
+  CUtensorMap tmTm;  // tau- slices [S][lambda-][K]
+  double *R;
+  double *racc;      // FP64 accumulators, [item][col][128 lanes], racc_cols columns per item
+  int *status;
+  int o, v, vp, Np, K, nbp;
+  int nks;           // Np / 32
+  int nA, nB8;       // 16-blocks of a, 8-blocks of b
+  int ntiles, nchunks, ksplit;
+  int racc_cols;
+  int kc;            // GEMM1 K-steps (of 32 aux functions) per FP32 accumulation chain
+  int s_pieces;      // 16-slot pieces of GEMM2 per fresh S accumulator (1, 2 or 4)
+  int flush_every;   // S accumulators summed in FP32 before an FP64 flush
+  unsigned long long timeout_ns;
+  TcChunk chunks[kMaxChunks];
+};
+uint32_t tc_smem_bytes(int nslices);
+cudaError_t launch_ladder_tc(const TcArgs &a, int nslices, int grid, cudaStream_t s);
 
 }  // namespace ladder

@@ -2,12 +2,15 @@
 // launch sequences.  See include/ladder.h for the contract of each call.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdint>
 #include <cstring>
 #include <new>
 #include <vector>
 
 #include "../../include/ladder.h"
+#include <cudaTypedefs.h>
+
 #include "kernels.h"
 
 using namespace ladder;
@@ -21,6 +24,36 @@ struct Layout {
   size_t status = 0, energy = 0, Tp = 0, Tm = 0, slab = 0, Bt = 0, W = 0, total = 0;
 };
 
+int tc_slices(int mode) { return mode == LADDER_BF16X3 ? 2 : 3; }
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+bool encode3d(CUtensorMap *m, void *base, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0,
+              uint32_t b1, uint32_t b2, CUtensorMapSwizzle sw) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {d0, d1, d2};
+  const cuuint64_t strides[2] = {d0 * 2, d0 * d1 * 2};
+  const cuuint32_t box[3] = {b0, b1, b2};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 struct ladder_plan_s {
@@ -31,6 +64,10 @@ struct ladder_plan_s {
   // FP64 path
   std::vector<Chunk> chunks64;
   int grid64 = 0;
+  // split-BF16 tensor-core path
+  int S = 0, ksplit = 1, kc = 4, s_pieces = 4, flush_every = 16, ntiles_tc = 0, racc_cols = 0;
+  std::vector<TcChunk> chunks_tc;
+  CUtensorMap tmA, tmB, tmTp, tmTm;
   Layout lay;
   void *ws = nullptr;
   size_t ws_bytes = 0;
@@ -47,6 +84,32 @@ std::vector<Chunk> make_chunks(int o, int rows) {
     int j1 = j0 + 1;
     while (j1 < o && ppos(j1 + 1) - ppos(j0) <= rows && pneg(j1 + 1) - pneg(j0) <= rows) ++j1;
     out.push_back({j0, j1});
+    j0 = j1;
+  }
+  return out;
+}
+
+// Occupied-pair chunks of the tensor-core kernel (whole j ranges; padded
+// column counts with nps + nms <= kTcMaxCols).
+std::vector<TcChunk> make_tc_chunks(int o) {
+  auto pad16 = [](int x) { return (x + 15) / 16 * 16; };
+  auto fits = [&](int j0, int j1) {
+    const int np = pad16(ppos(j1) - ppos(j0)), nm = pad16(pneg(j1) - pneg(j0));
+    return np + nm <= kTcMaxCols;
+  };
+  std::vector<TcChunk> out;
+  int j0 = 0;
+  while (j0 < o) {
+    int j1 = j0 + 1;
+    while (j1 < o && fits(j0, j1 + 1)) ++j1;
+    TcChunk c;
+    c.lp0 = ppos(j0);
+    c.lm0 = pneg(j0);
+    c.np = ppos(j1) - ppos(j0);
+    c.nm = pneg(j1) - pneg(j0);
+    c.nps = pad16(c.np);
+    c.nms = pad16(c.nm);
+    out.push_back(c);
     j0 = j1;
   }
   return out;
@@ -87,6 +150,17 @@ void compute_layout(ladder_plan_s *pl) {
     off = align_up(off + (size_t)std::max(pl->nlm, 1) * pl->K * sizeof(double));
     L.slab = off;
     if (pl->chunks64.size() > 1) off = align_up(off + fp64_slab_doubles(pl->K, pl->grid64) * sizeof(double));
+  } else {
+    const size_t S = pl->S;
+    L.Bt = off;
+    off = align_up(off + S * pl->vp * pl->vp * pl->Np * 2, 1024);
+    L.Tp = off;
+    off = align_up(off + S * pl->nlp * pl->K * 2, 1024);
+    L.Tm = off;
+    off = align_up(off + S * std::max(pl->nlm, 1) * pl->K * 2, 1024);
+    L.slab = off;  // FP64 accumulators of the tensor-core kernel
+    off = align_up(off + (size_t)pl->ntiles_tc * pl->chunks_tc.size() * pl->ksplit * 128 *
+                             pl->racc_cols * sizeof(double));
   }
   L.W = off;  // backward: energy weights / scratch copies are caller-provided
   L.total = off;
@@ -116,7 +190,6 @@ ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out) 
   if (o < 1 || o > 256 || v < 1 || v > 4096 || naux < 1 || naux > 65536) return LADDER_EINVAL;
   if (mode < LADDER_FP64 || mode > LADDER_AUTO) return LADDER_EINVAL;
   if (mode == LADDER_AUTO) mode = LADDER_BF16X6;
-  if (mode != LADDER_FP64) return LADDER_ENOTSUP;
   ladder_plan_s *pl = new (std::nothrow) ladder_plan_s();
   if (!pl) return LADDER_ENOMEM;
   pl->o = o;
@@ -137,7 +210,41 @@ ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out) 
     return LADDER_ECUDA;
   }
   pl->chunks64 = make_chunks(o, kFp64LamTile);
-  if ((int)pl->chunks64.size() > kMaxChunks) {
+  if (mode != LADDER_FP64) {
+    pl->S = tc_slices(mode);
+    pl->Np = (naux + 31) / 32 * 32;
+    pl->chunks_tc = make_tc_chunks(o);
+    pl->racc_cols = 0;
+    for (auto &c : pl->chunks_tc) pl->racc_cols = std::max(pl->racc_cols, c.nps + c.nms);
+    const int nA = pl->vp / 16, nB8 = pl->vp / CB;
+    pl->ntiles_tc = 0;
+    for (int i = 0; i < nA; ++i) pl->ntiles_tc += nB8 - 2 * i;
+    // split the block pairs of small problems so that every SM has work
+    const int items = pl->ntiles_tc * (int)pl->chunks_tc.size();
+    int ks = (2 * pl->sm_count + items - 1) / items;
+    ks = std::max(1, std::min(ks, pl->nbp / 4));
+    pl->ksplit = ks;
+    // FP32 accumulation chains (see ladder_tc.cu): BF16X3 is limited by its
+    // slicing error (~4e-6), so its chains are long (24 / 12 MMAs); BF16X6 keeps
+    // them at 12 MMAs (GEMM1) and 6 MMAs (GEMM2)
+    pl->kc = pl->S == 2 ? 4 : 1;
+    pl->s_pieces = pl->S == 2 ? 4 : 1;
+    pl->flush_every = 16;
+    if (const char *e = getenv("LADDER_KC")) pl->kc = std::max(1, atoi(e));
+    if (const char *e = getenv("LADDER_SPIECES")) {
+      const int sp = atoi(e);
+      if (sp == 1 || sp == 2 || sp == 4) pl->s_pieces = sp;
+    }
+    if (const char *e = getenv("LADDER_FLUSH")) pl->flush_every = std::max(1, atoi(e));
+    if (const char *e = getenv("LADDER_KSPLIT")) pl->ksplit = std::max(1, std::min(atoi(e), pl->nbp));
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, pl->device);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, pl->device);
+    if ((int)pl->chunks_tc.size() > kMaxChunks || major != 10 || minor != 3) {
+      delete pl;
+      return LADDER_ENOTSUP;
+    }
+  } else if ((int)pl->chunks64.size() > kMaxChunks) {
     delete pl;
     return LADDER_ENOTSUP;
   }
@@ -166,6 +273,19 @@ ladder_status ladder_set_workspace(ladder_plan_t pl, void *dptr, size_t bytes) {
   if (bytes < pl->lay.total) return LADDER_EWORKSPACE;
   if (!dptr || (reinterpret_cast<uintptr_t>(dptr) % kAlign)) return LADDER_EINVAL;
   if (!dev_ptr_ok(dptr)) return LADDER_EINVAL;
+  if (pl->mode != LADDER_FP64) {
+    char *w = static_cast<char *>(dptr);
+    const uint64_t S = pl->S;
+    const bool ok =
+        encode3d(&pl->tmA, w + pl->lay.Bt, pl->Np, pl->vp, pl->vp * S, 32, 8, 16,
+                 CU_TENSOR_MAP_SWIZZLE_64B) &&
+        encode3d(&pl->tmB, w + pl->lay.Bt, pl->Np, pl->vp, pl->vp * S, 32, 8, 8,
+                 CU_TENSOR_MAP_SWIZZLE_64B) &&
+        encode3d(&pl->tmTp, w + pl->lay.Tp, pl->K, pl->nlp, S, 16, 16, 1, CU_TENSOR_MAP_SWIZZLE_32B) &&
+        encode3d(&pl->tmTm, w + pl->lay.Tm, pl->K, std::max(pl->nlm, 1), S, 16, 16, 1,
+                 CU_TENSOR_MAP_SWIZZLE_32B);
+    if (!ok) return LADDER_ECUDA;
+  }
   pl->ws = dptr;
   pl->ws_bytes = bytes;
   // the status word starts cleared; this is the plan's only synchronous copy
@@ -204,6 +324,47 @@ static ladder_status apply_fp64(ladder_plan_t pl, const double *B, const double 
   return cuda_status(launch_ladder_fp64(a, pl->grid64, s));
 }
 
+static ladder_status apply_tc(ladder_plan_t pl, const double *B, const double *tau, double *R,
+                              cudaStream_t s) {
+  auto *Bt = ws_at<__nv_bfloat16>(pl, pl->lay.Bt);
+  auto *Tp = ws_at<__nv_bfloat16>(pl, pl->lay.Tp);
+  auto *Tm = ws_at<__nv_bfloat16>(pl, pl->lay.Tm);
+  launch_split_B(pl->N, pl->v, pl->vp, pl->Np, pl->S, B, Bt, s);
+  launch_pack_tpm_bf16(pl->o, pl->v, pl->K, pl->S, pl->nlp, std::max(pl->nlm, 1), tau, Tp, Tm, s);
+  ladder_status st = cuda_status(cudaGetLastError());
+  if (st != LADDER_OK) return st;
+  TcArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.tmA = pl->tmA;
+  a.tmB = pl->tmB;
+  a.tmTp = pl->tmTp;
+  a.tmTm = pl->tmTm;
+  a.R = R;
+  a.status = ws_at<int>(pl, pl->lay.status);
+  a.o = pl->o;
+  a.v = pl->v;
+  a.vp = pl->vp;
+  a.Np = pl->Np;
+  a.K = pl->K;
+  a.nbp = pl->nbp;
+  a.nks = pl->Np / 32;
+  a.nA = pl->vp / 16;
+  a.nB8 = pl->vp / CB;
+  a.ntiles = pl->ntiles_tc;
+  a.nchunks = (int)pl->chunks_tc.size();
+  a.ksplit = pl->ksplit;
+  a.racc = ws_at<double>(pl, pl->lay.slab);
+  a.racc_cols = pl->racc_cols;
+  a.kc = pl->kc;
+  a.s_pieces = pl->s_pieces;
+  a.flush_every = pl->flush_every;
+  for (int c = 0; c < a.nchunks; ++c) a.chunks[c] = pl->chunks_tc[c];
+  // generous bound on any single wait: 2 s plus 20x the estimated item time
+  const double item_flops = 2.0 * pl->nbp * 2.0 * 128.0 * 64.0 * pl->Np * 6.0 / pl->ksplit;
+  a.timeout_ns = (unsigned long long)(2e9 + 20.0 * item_flops / 4e12 * 1e9);
+  return cuda_status(launch_ladder_tc(a, pl->S, a.ntiles * a.nchunks * a.ksplit, s));
+}
+
 ladder_status ladder_apply(ladder_plan_t pl, const double *B, const double *tau, double *R,
                            void *stream) {
   if (!pl) return LADDER_EINVAL;
@@ -212,7 +373,7 @@ ladder_status ladder_apply(ladder_plan_t pl, const double *B, const double *tau,
     return LADDER_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (pl->mode == LADDER_FP64) return apply_fp64(pl, B, tau, R, s);
-  return LADDER_ENOTSUP;
+  return apply_tc(pl, B, tau, R, s);
 }
 
 ladder_status ladder_energy(ladder_plan_t pl, const double *R, const double *t2, double *E_dev,

@@ -1,0 +1,549 @@
+// Split-BF16 fused ladder kernel on the sm_103a tensor cores (tcgen05 + TMEM + TMA).
+//
+// R_ij^ab = sum_cd (ac|bd) tau_ij^cd (Eq. pp-Ladder-0) with (ac|bd) =
+// sum_P B^P_ac B^P_bd (Eq. RIM), in the slot form of the symmetric /
+// antisymmetric pair scheme (Sec. II.C): virtual indices in blocks of 8,
+// block pairs k <= l, V+-_ab[(c,d)] = (ac|bd) +- (ad|bc), R+- = sum T+- V+-.
+// Every operand x is carried as S bfloat16 slices x = x_0 + x_1 (+ x_2) and a
+// product as the sum of the slice products x_p y_q with p + q < S.
+//
+// Accumulation.  The tensor core rounds its FP32 accumulator on every MMA
+// instruction with a bias, so the error of one accumulator grows linearly
+// with the number of MMAs that feed it.  Every FP32 accumulation chain here is
+// therefore short, and chains are summed outside the tensor core:
+//   GEMM1 (K = aux functions) runs in chains of `kc` K-steps that alternate
+//         between two TMEM buffers; the conversion warps sum the chains in
+//         registers (FP32, round to nearest);
+//   GEMM2 (K = slots) starts a fresh TMEM accumulator S every `s_pieces`
+//         pieces of 16 slots (a block pair has 4);
+//         the conversion warps add S into a TMEM running sum R (FP32, round to
+//         nearest) and every `flush_every` block pairs add R into an FP64
+//         accumulator in the workspace.
+// A separate unpack kernel turns the FP64 accumulators into R_ij^ab.
+//
+// One CTA owns 128 virtual pairs (a in a 16-block, b in an 8-block), one
+// chunk of occupied pairs (at most 128 TMEM columns) and one range of block
+// pairs.  Warp roles:
+//   warp 0    TMA producer: B slices (GEMM1 operands) and tau+- pieces into a
+//             ring of shared-memory stages;
+//   warp 1    MMA issuer (one thread): GEMM1 X[(a,c),(b,d)], Y[(a,d),(b,c)]
+//             (M=128, N=64) and GEMM2 S+-[ab][lambda] = V+-[ab][slots]
+//             T+-[lambda][slots]^T (M=128, N=lambda);
+//   warps 2-5 conversion: TMEM -> registers, exchange of Y within groups of 8
+//             lanes by shuffles, V+- = X +- Y', BF16 slicing, swizzled stores
+//             into the GEMM2 operand tile; S -> R sums; FP64 flushes.
+// The integral tiles live only in TMEM, registers and shared memory.
+#include "kernels.h"
+#include "tc_ptx.cuh"
+
+namespace ladder {
+namespace {
+using namespace tc;
+
+constexpr int kThreads = 192;
+constexpr int kEpi = 128;
+constexpr int KSTEP = 32;                             // aux functions per GEMM1 stage
+constexpr uint32_t A_TILE = 128u * KSTEP * 2u;        // 8 KB: rows (a,c), 64-byte rows
+constexpr uint32_t B_TILE = 64u * KSTEP * 2u;         // 4 KB: rows (b,d)
+constexpr int TPIECE = 16;                            // slots per tau+- stage (32-byte rows)
+constexpr uint32_t V_TILE = 128u * SLOTS * 2u;        // 16 KB: 128 ab rows x 64 slots
+constexpr uint32_t kColS = 256;                       // TMEM: XY0 [0,128), XY1 [128,256), S, R
+
+template <int S>
+struct Cfg {
+  static constexpr uint32_t kStage = 12288u * S;      // S*(A_TILE+B_TILE) >= S*kTcMaxCols*32
+  static constexpr int kStages = (S == 2) ? 5 : 3;
+  static constexpr uint32_t kRing = kStage * kStages;
+  static constexpr uint32_t kV = 2u * S * V_TILE;
+  static constexpr uint32_t kBar = 256;
+  static constexpr uint32_t kSmem = kRing + kV + kBar + 1024;
+  static constexpr int kProducts = (S == 2) ? 3 : 6;
+};
+static_assert(12288u == A_TILE + B_TILE, "stage size");
+static_assert(12288u >= kTcMaxCols * 32u, "tau stage size");
+static_assert(kColS + 2 * kTcMaxCols <= 512, "TMEM columns");
+
+// slice pairs (p, q) with p + q < S, larger terms first
+__device__ __forceinline__ constexpr int kPa(int q) { return q == 2 || q == 4 ? 1 : (q == 5 ? 2 : 0); }
+__device__ __forceinline__ constexpr int kPb(int q) { return q == 1 || q == 4 ? 1 : (q == 3 ? 2 : 0); }
+
+// 8x8 transpose across the 8 lanes of a group: lane x holds row x on entry
+// and column x on exit (three butterfly stages).
+__device__ __forceinline__ void transpose8(float (&r)[8], int x) {
+#pragma unroll
+  for (int s = 1; s < 8; s <<= 1) {
+    const bool up = (x & s) != 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (j & s) continue;
+      const float send = up ? r[j] : r[j ^ s];
+      const float recv = __shfl_xor_sync(0xffffffffu, send, s);
+      if (up)
+        r[j] = recv;
+      else
+        r[j ^ s] = recv;
+    }
+  }
+}
+
+// One BF16 slice of 8 values (round to nearest); `rem` keeps what is left.
+__device__ __forceinline__ uint4 pack_slice(float (&rem)[8]) {
+  uint32_t w[4];
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    const __nv_bfloat162 b2 = __floats2bfloat162_rn(rem[2 * h], rem[2 * h + 1]);
+    const float2 back = __bfloat1622float2(b2);
+    rem[2 * h] -= back.x;
+    rem[2 * h + 1] -= back.y;
+    w[h] = *reinterpret_cast<const uint32_t *>(&b2);
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+struct Bars {
+  uint32_t base;
+  int stages;
+  __device__ uint32_t full(int s) const { return base + 8u * s; }
+  __device__ uint32_t empty(int s) const { return base + 8u * (stages + s); }
+  __device__ uint32_t cfull(int b) const { return base + 8u * (2 * stages + b); }
+  __device__ uint32_t cfree(int b) const { return base + 8u * (2 * stages + 2 + b); }
+  __device__ uint32_t v_full() const { return base + 8u * (2 * stages + 4); }
+  __device__ uint32_t v_free() const { return base + 8u * (2 * stages + 5); }
+  __device__ uint32_t s_full() const { return base + 8u * (2 * stages + 6); }
+  __device__ uint32_t s_free() const { return base + 8u * (2 * stages + 7); }
+  __device__ uint32_t done() const { return base + 8u * (2 * stages + 8); }
+  static constexpr int kCount = 9;  // + 2 * stages
+};
+
+// A Watchdog that ignores the CTA's abort flag: used only to let copies and
+// MMAs already in flight land before the CTA releases its resources.
+struct DrainWatch {
+  int zero = 0;
+  Watchdog wd;
+  __device__ DrainWatch(int *status, uint64_t deadline) : wd{status, &zero, deadline} {}
+};
+
+template <int S>
+__global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_constant__ TcArgs A) {
+  using C = Cfg<S>;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
+  uint8_t *smem = smem_raw + pad;
+  const uint32_t ring = raw + pad;
+  const uint32_t vbase = ring + C::kRing;
+  Bars bars{vbase + C::kV, C::kStages};
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(
+      smem + C::kRing + C::kV + 8 * (2 * C::kStages + Bars::kCount));
+  int *abort_flag = reinterpret_cast<int *>(tmem_holder + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+  // ---- work item: ((a 16-block, b 8-block) tile, occupied-pair chunk, block-pair range)
+  const int item = blockIdx.x;
+  const int ksl = item % A.ksplit;
+  const int tc = item / A.ksplit;
+  const int tile = tc / A.nchunks, ch = tc % A.nchunks;
+  int iA = 0, t = tile;
+  while (t >= A.nB8 - 2 * iA) {
+    t -= A.nB8 - 2 * iA;
+    ++iA;
+  }
+  const int jB = 2 * iA + t;
+  const int A0 = iA * 16, B0 = jB * CB;
+  const TcChunk CH = A.chunks[ch];
+  const int p0 = (int)((long long)A.nbp * ksl / A.ksplit);
+  const int p1 = (int)((long long)A.nbp * (ksl + 1) / A.ksplit);
+  const uint32_t sc = (uint32_t)(CH.nps + CH.nms);  // TMEM columns of S and of R
+  double *racc = A.racc + (size_t)item * 128 * A.racc_cols;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::kStages; ++s) {
+      mbar_init(bars.full(s), 1);
+      mbar_init(bars.empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(bars.cfull(b), 1);
+      mbar_init(bars.cfree(b), kEpi);
+    }
+    mbar_init(bars.v_full(), kEpi);
+    mbar_init(bars.v_free(), 1);
+    mbar_init(bars.s_full(), 1);
+    mbar_init(bars.s_free(), kEpi);
+    mbar_init(bars.done(), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0 && lane == 0) {
+    tma_prefetch_desc(&A.tmA);
+    tma_prefetch_desc(&A.tmB);
+    tma_prefetch_desc(&A.tmTp);
+    tma_prefetch_desc(&A.tmTm);
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_holder), 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+  const Watchdog wd{A.status, abort_flag, A.timeout_ns};
+  const int kc = A.kc;
+  const int nch_full = (A.nks + kc - 1) / kc;  // GEMM1 chains per block pair
+
+  if (warp == 0) {
+    // ================================================================ TMA producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t armed = 0, armed_par = 0;  // per stage: armed at least once / parity armed last
+      const uint32_t tbytes = sc * 32u;
+      bool ok = true;
+      for (int p = p0; ok && p <= p1; ++p) {
+        if (p < p1) {
+          int k, l;
+          pair_of(p, k, l);
+          const int ntile = (k == l) ? 1 : 2;
+          for (int ks = 0; ok && ks < A.nks; ++ks)
+            for (int tt = 0; tt < ntile; ++tt) {
+              if (!(ok = mbar_wait(bars.empty(stage), phase ^ 1u, wd, kSiteTmaEmpty))) break;
+              const uint32_t dst = ring + (uint32_t)stage * C::kStage;
+              mbar_arrive_expect_tx(bars.full(stage), (uint32_t)S * (A_TILE + B_TILE));
+              armed |= 1u << stage;
+              armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+              const int ca = (tt == 0 ? k : l) * CB, cb = (tt == 0 ? l : k) * CB;
+#pragma unroll
+              for (int s = 0; s < S; ++s) {
+                tma_load_3d(dst + s * A_TILE, &A.tmA, bars.full(stage), ks * KSTEP, ca, s * A.vp + A0);
+                tma_load_3d(dst + S * A_TILE + s * B_TILE, &A.tmB, bars.full(stage), ks * KSTEP, cb,
+                            s * A.vp + B0);
+              }
+              if (++stage == C::kStages) {
+                stage = 0;
+                phase ^= 1u;
+              }
+            }
+        }
+        if (ok && p > p0) {
+          for (int piece = 0; piece < SLOTS / TPIECE; ++piece) {
+            if (!(ok = mbar_wait(bars.empty(stage), phase ^ 1u, wd, kSiteTmaEmpty))) break;
+            const uint32_t dst = ring + (uint32_t)stage * C::kStage;
+            mbar_arrive_expect_tx(bars.full(stage), (uint32_t)S * tbytes);
+            armed |= 1u << stage;
+            armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+            const int x = (p - 1) * SLOTS + piece * TPIECE;
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+              for (int r = 0; r < CH.nps; r += 16)
+                tma_load_3d(dst + s * tbytes + r * 32, &A.tmTp, bars.full(stage), x, CH.lp0 + r, s);
+              for (int r = 0; r < CH.nms; r += 16)
+                tma_load_3d(dst + s * tbytes + (CH.nps + r) * 32, &A.tmTm, bars.full(stage), x,
+                            CH.lm0 + r, s);
+            }
+            if (++stage == C::kStages) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+        }
+      }
+      if (!ok) {
+        // let the copies already issued land before the CTA leaves
+        DrainWatch dw(A.status, A.timeout_ns);
+        for (int s = 0; s < C::kStages; ++s)
+          if (armed & (1u << s)) mbar_wait(bars.full(s), (armed_par >> s) & 1u, dw.wd, kSiteTmaFull);
+      }
+    }
+  } else if (warp == 1) {
+    // ================================================================ MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t g = 0, v_use = 0, s_use = 0;  // chains issued, V tiles and S tiles consumed
+      const uint32_t id1 = idesc_bf16(128, 64);
+      const uint32_t idp = idesc_bf16(128, CH.nps > 0 ? CH.nps : 16);
+      const uint32_t idm = idesc_bf16(128, CH.nms > 0 ? CH.nms : 16);
+      const uint32_t tbytes = sc * 32u;
+      bool ok = true;
+      for (int p = p0; ok && p <= p1; ++p) {
+        if (p < p1) {
+          int k, l;
+          pair_of(p, k, l);
+          const int ntile = (k == l) ? 1 : 2;
+          for (int c = 0; ok && c < nch_full; ++c) {
+            const int buf = (int)(g & 1u);
+            if (!(ok = mbar_wait(bars.cfree(buf), ((g >> 1) & 1u) ^ 1u, wd, kSiteXYFree))) break;
+            tc_fence_after();
+            const uint32_t dX = tmem + (uint32_t)buf * 128u;
+            const int ks0 = c * kc, ks1 = min(A.nks, ks0 + kc);
+            for (int ks = ks0; ok && ks < ks1; ++ks)
+              for (int tt = 0; tt < ntile; ++tt) {
+                if (!(ok = mbar_wait(bars.full(stage), phase, wd, kSiteTmaFull))) break;
+                tc_fence_after();
+                const uint32_t st = ring + (uint32_t)stage * C::kStage;
+#pragma unroll
+                for (int kk = 0; kk < KSTEP / 16; ++kk)
+#pragma unroll
+                  for (int q = 0; q < C::kProducts; ++q) {
+                    const uint64_t ad = sdesc(st + kPa(q) * A_TILE + kk * 32, 512, kSwizzle64);
+                    const uint64_t bd =
+                        sdesc(st + S * A_TILE + kPb(q) * B_TILE + kk * 32, 512, kSwizzle64);
+                    mma_bf16(dX + (tt ? 64u : 0u), ad, bd, id1, (ks > ks0 || kk || q) ? 1u : 0u);
+                  }
+                mma_commit(bars.empty(stage));
+                if (++stage == C::kStages) {
+                  stage = 0;
+                  phase ^= 1u;
+                }
+              }
+            if (!ok) break;
+            mma_commit(bars.cfull(buf));
+            ++g;
+          }
+          if (!ok) break;
+        }
+        if (p > p0) {
+          if (!(ok = mbar_wait(bars.v_full(), v_use & 1u, wd, kSiteVFull))) break;
+          tc_fence_after();
+          for (int piece = 0; ok && piece < SLOTS / TPIECE; ++piece) {
+            const bool first = (piece % A.s_pieces) == 0;
+            if (first) {
+              // a fresh S accumulator: the previous one has been taken
+              if (!(ok = mbar_wait(bars.s_free(), (s_use & 1u) ^ 1u, wd, kSiteRFree))) break;
+              tc_fence_after();
+            }
+            if (!(ok = mbar_wait(bars.full(stage), phase, wd, kSiteTmaFull))) break;
+            tc_fence_after();
+            const uint32_t st = ring + (uint32_t)stage * C::kStage;
+#pragma unroll
+            for (int q = 0; q < C::kProducts; ++q) {
+              const uint32_t acc = (first && q == 0) ? 0u : 1u;
+              const uint64_t ap = sdesc(vbase + (0 * S + kPa(q)) * V_TILE + piece * 32, 1024, kSwizzle128);
+              const uint64_t bp = sdesc(st + kPb(q) * tbytes, 256, kSwizzle32);
+              mma_bf16(tmem + kColS, ap, bp, idp, acc);
+              if (CH.nms > 0) {
+                const uint64_t am =
+                    sdesc(vbase + (1 * S + kPa(q)) * V_TILE + piece * 32, 1024, kSwizzle128);
+                const uint64_t bm = sdesc(st + kPb(q) * tbytes + CH.nps * 32, 256, kSwizzle32);
+                mma_bf16(tmem + kColS + CH.nps, am, bm, idm, acc);
+              }
+            }
+            mma_commit(bars.empty(stage));
+            if (++stage == C::kStages) {
+              stage = 0;
+              phase ^= 1u;
+            }
+            if ((piece + 1) % A.s_pieces == 0) {
+              mma_commit(bars.s_full());
+              ++s_use;
+            }
+          }
+          if (!ok) break;
+          mma_commit(bars.v_free());
+          ++v_use;
+        }
+      }
+      // every MMA of this CTA completes before TMEM is released
+      mma_commit(bars.done());
+      DrainWatch dw(A.status, A.timeout_ns);
+      mbar_wait(bars.done(), 0, dw.wd, kSiteRFull);
+    }
+  } else {
+    // ================================================================ conversion warps
+    const int quad = warp & 3;
+    const int L = quad * 32 + lane;  // TMEM lane
+    const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
+    const int a_l = L >> 3, x_l = L & 7;
+    uint32_t g = 0, v_use = 0, s_use = 0;
+    int nacc = 0, nflush = 0;
+    bool ok = true;
+
+    // S (fresh GEMM2 result of one block pair) -> R (TMEM running sum, FP32)
+    auto take_S = [&]() -> bool {
+      if (!mbar_wait(bars.s_full(), s_use & 1u, wd, kSiteRFull)) return false;
+      ++s_use;
+      tc_fence_after();
+      for (uint32_t c0 = 0; c0 < sc; c0 += 16) {
+        float s[16], r[16];
+        tmem_ld16(tl + kColS + c0, s);
+        if (nacc > 0) tmem_ld16(tl + kColS + sc + c0, r);
+        tmem_ld_wait();
+        if (nacc > 0) {
+#pragma unroll
+          for (int u = 0; u < 16; ++u) s[u] += r[u];
+        }
+        tmem_st16(tl + kColS + sc + c0, s);
+      }
+      tmem_st_wait();
+      tc_fence_before();
+      mbar_arrive(bars.s_free());
+      ++nacc;
+      return true;
+    };
+    // R (FP32, TMEM) -> FP64 accumulator in the workspace, [col][lane]
+    auto flush_R = [&]() {
+      for (uint32_t c0 = 0; c0 < sc; c0 += 16) {
+        float r[16];
+        tmem_ld16(tl + kColS + sc + c0, r);
+        tmem_ld_wait();
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          double *dst = racc + (size_t)(c0 + u) * 128 + L;
+          *dst = (nflush ? *dst : 0.0) + (double)r[u];
+        }
+      }
+      ++nflush;
+      nacc = 0;
+    };
+
+    for (int p = p0; p < p1; ++p) {
+      int k, l;
+      pair_of(p, k, l);
+      const bool diag = (k == l);
+      float X[64], Y[64];
+      for (int c = 0; c < nch_full; ++c) {
+        const int buf = (int)(g & 1u);
+        if (!(ok = mbar_wait(bars.cfull(buf), (g >> 1) & 1u, wd, kSiteXYFull))) break;
+        ++g;
+        tc_fence_after();
+        const uint32_t cX = tl + (uint32_t)buf * 128u;
+        const uint32_t cY = diag ? cX : cX + 64u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float tx[16], ty[16];
+          tmem_ld16(cX + q * 16, tx);
+          tmem_ld16(cY + q * 16, ty);
+          tmem_ld_wait();
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            X[q * 16 + i] = c ? X[q * 16 + i] + tx[i] : tx[i];
+            Y[q * 16 + i] = c ? Y[q * 16 + i] + ty[i] : ty[i];
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(bars.cfree(buf));
+      }
+      if (!ok) break;
+      // S chains of the previous block pair (GEMM2 runs after this pair's GEMM1)
+      if (p > p0) {
+        for (int gs = 0; ok && gs < SLOTS / TPIECE / A.s_pieces; ++gs) {
+          ok = take_S();
+          if (ok && nacc >= A.flush_every) flush_R();
+        }
+        if (!ok) break;
+      }
+      // Y row of lane (a, d=x_l) holds (ad|bc) at column (b, c); after the
+      // transpose lane (a, c=x_l) holds (ad|bc) at index (b, d).
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        float r[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) r[j] = Y[b * 8 + j];
+        transpose8(r, x_l);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) Y[b * 8 + j] = r[j];
+      }
+      if (!(ok = mbar_wait(bars.v_free(), (v_use & 1u) ^ 1u, wd, kSiteVFree))) break;
+      ++v_use;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const int row = a_l * 8 + b;
+        const uint32_t off = (uint32_t)row * 128u + (uint32_t)((x_l ^ (row & 7)) * 16);
+#pragma unroll
+        for (int sg = 0; sg < 2; ++sg) {
+          float rem[8];
+#pragma unroll
+          for (int d = 0; d < 8; ++d) rem[d] = sg ? X[b * 8 + d] - Y[b * 8 + d] : X[b * 8 + d] + Y[b * 8 + d];
+#pragma unroll
+          for (int s = 0; s < S; ++s) {
+            const uint4 w = pack_slice(rem);
+            *reinterpret_cast<uint4 *>(smem + C::kRing + (uint32_t)(sg * S + s) * V_TILE + off) = w;
+          }
+        }
+      }
+      fence_async_smem();
+      mbar_arrive(bars.v_full());
+    }
+    // S chains of the last block pair, then the final FP64 flush
+    for (int gs = 0; ok && gs < SLOTS / TPIECE / A.s_pieces; ++gs) ok = take_S();
+    if (ok) flush_R();
+  }
+
+  // ---- teardown: all roles done (or given up); release TMEM
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// ---------------------------------------------------------------- unpack
+// R_ij^ab from the FP64 accumulators of every block-pair range of a
+// (tile, chunk): lane = ab slot (a = A0 + lane/8, b = B0 + lane%8),
+//   R_ij^ab = R+ + R-, R_ij^ba = R+ - R-, R_ji^ba = R_ij^ab, R_ji^ab = R_ij^ba,
+// with R- = 0 when i = j or a = b.  Every element of R is written once.
+__global__ void __launch_bounds__(128) unpack_kernel(const __grid_constant__ TcArgs A) {
+  const int tc = blockIdx.x;
+  const int tile = tc / A.nchunks, ch = tc % A.nchunks;
+  int iA = 0, t = tile;
+  while (t >= A.nB8 - 2 * iA) {
+    t -= A.nB8 - 2 * iA;
+    ++iA;
+  }
+  const int jB = 2 * iA + t;
+  const TcChunk CH = A.chunks[ch];
+  const int L = threadIdx.x;
+  const int a = iA * 16 + (L >> 3), b = jB * CB + (L & 7);
+  const bool diag_ab = (jB >> 1) == iA;
+  if (!(a < A.v && b < A.v && (!diag_ab || a <= b))) return;
+  const size_t per_item = (size_t)128 * A.racc_cols;
+  const double *base = A.racc + (size_t)tc * A.ksplit * per_item + L;
+  const size_t vv = (size_t)A.v * A.v, o = (size_t)A.o;
+  int i = 0, j = 0;
+  lam_plus(CH.lp0, i, j);
+  for (int c = 0; c < CH.np; ++c) {
+    double pv = 0.0, mv = 0.0;
+    for (int k = 0; k < A.ksplit; ++k) pv += base[k * per_item + (size_t)c * 128];
+    if (i < j && a != b) {
+      const int cm = CH.nps + (pneg(j) + i - CH.lm0);
+      for (int k = 0; k < A.ksplit; ++k) mv += base[k * per_item + (size_t)cm * 128];
+    }
+    A.R[(i * o + j) * vv + (size_t)a * A.v + b] = pv + mv;
+    A.R[(i * o + j) * vv + (size_t)b * A.v + a] = pv - mv;
+    A.R[(j * o + i) * vv + (size_t)b * A.v + a] = pv + mv;
+    A.R[(j * o + i) * vv + (size_t)a * A.v + b] = pv - mv;
+    if (++i > j) {
+      ++j;
+      i = 0;
+    }
+  }
+}
+
+}  // namespace
+
+uint32_t tc_smem_bytes(int nslices) {
+  return nslices == 2 ? Cfg<2>::kSmem : Cfg<3>::kSmem;
+}
+
+cudaError_t launch_ladder_tc(const TcArgs &a, int nslices, int grid, cudaStream_t s) {
+  cudaError_t e;
+  if (nslices == 2) {
+    e = cudaFuncSetAttribute(ladder_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Cfg<2>::kSmem);
+    if (e != cudaSuccess) return e;
+    ladder_tc_kernel<2><<<grid, kThreads, Cfg<2>::kSmem, s>>>(a);
+  } else {
+    e = cudaFuncSetAttribute(ladder_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Cfg<3>::kSmem);
+    if (e != cudaSuccess) return e;
+    ladder_tc_kernel<3><<<grid, kThreads, Cfg<3>::kSmem, s>>>(a);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  unpack_kernel<<<a.ntiles * a.nchunks, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace ladder
