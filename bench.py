@@ -1,0 +1,363 @@
+"""Benchmark of the particle-particle ladder term on GB300.
+
+One step = one pass of the whole path on one molecule's inputs already in HBM:
+tau assembly, operand slicing / pair packing, the fused ladder kernel, the
+unpacking of R, and the FP64 ladder energy.  The headline metric is ladder
+TFLOP/s (algorithmic flops of the symmetric/antisymmetric scheme / time) of
+the split-BF16 path in the mode that meets the R tolerance (BF16X6), on the
+mid-size workload (o=34, v=400, N_aux=1600).  The FP64 path and BF16X3 are
+timed on the same workload and reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank runs its own replica of the workload on its own GPU
+(the ladder term of one molecule is one GPU's work); value = all ranks' flops
+/ max-over-ranks time.  --impl reference times the plain FP64 CPU oracle on a
+bounded sample of the same workload (host cores) and prints the same line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic  # noqa: E402
+
+METRIC = "ladder TFLOP/s & ms/call, split-BF16 vs FP64 GPU path at |dE_L|<=1 uEh"
+DEFAULT_WORKLOAD = "mid_o34_v400_n1600"
+PRODUCTS = {"bf16x3": 3, "bf16x6": 6, "fp64": 1}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(x, seconds_target: float):
+    """Time the plain oracle on a bounded sample of (a, b) columns; return
+    (estimated seconds for the full term, sample description, threads)."""
+    import oracle
+    tau = oracle.tau(x.t1, x.t2)
+    nthr = oracle.threads()
+    v = x.v
+    rng = np.random.default_rng(0)
+    # calibrate with one column per thread, then size the sample
+    n0 = max(1, nthr)
+    pa, pb = rng.integers(0, v, n0), rng.integers(0, v, n0)
+    t = time.perf_counter()
+    oracle.ladder_pairs(x.B, tau, pa, pb)
+    dt = time.perf_counter() - t
+    n = max(n0, int(n0 * seconds_target / max(dt, 1e-6)))
+    n = min(n, v * v)
+    pa, pb = rng.integers(0, v, n), rng.integers(0, v, n)
+    t = time.perf_counter()
+    oracle.ladder_pairs(x.B, tau, pa, pb)
+    dt = time.perf_counter() - t
+    full = dt * (v * v) / n
+    return full, dt, "%d of %d (a,b) columns of R (all i,j), %.1f s" % (n, v * v, dt), nthr
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = synthetic.WORKLOADS[args.workload]
+    x = synthetic.make_inputs(w.o, w.v, w.naux, w.seed)
+    F = synthetic.falg(w.o, w.v, w.naux)
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    times, samples, thr = [], [], 1
+    for s in range(args.warmup + args.steps):
+        full, dt, desc, thr = oracle_sample(x, per_step)
+        if s >= args.warmup:
+            times.append(full)
+            samples.append(desc)
+    t = statistics.mean(times)
+    val = F / t / 1e12
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "o": w.o, "v": w.v, "naux": w.naux, "seed": w.seed},
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": thr, "kind": "oracle",
+                         "sample": samples[-1] + "; full-term time extrapolated"},
+        "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--mode", default="bf16x6", choices=["bf16x3", "bf16x6", "fp64"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    import paper_1810_08142_gb300 as lad
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    w = synthetic.WORKLOADS[args.workload]
+    x = synthetic.make_inputs(w.o, w.v, w.naux, w.seed)
+    F = synthetic.falg(w.o, w.v, w.naux)
+    dev = torch.device("cuda", local)
+    t1 = torch.from_numpy(x.t1).to(dev)
+    t2 = torch.from_numpy(x.t2).to(dev)
+    B = torch.from_numpy(x.B).to(dev)
+    tau = torch.empty_like(t2)
+    R = torch.empty_like(t2)
+    E = torch.empty((), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    L = lad.Ladder(w.o, w.v, w.naux, mode=args.mode, device=dev)
+    lad.ladder_set_timing(L.plan, True)
+
+    def step(Lx):
+        lad.ladder_tau(Lx.plan, t1, t2, tau)
+        lad.ladder_apply(Lx.plan, B, tau, R)
+        lad.ladder_energy(Lx.plan, R, t2, E)
+
+    for _ in range(args.warmup):
+        step(L)
+    torch.cuda.synchronize()
+    L.check_device()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fused = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(L)
+        fused.append(lad.ladder_timing(L.plan))  # waits for this step's events
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    L.check_device()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms)
+    value = world * F / (ms * 1e-3) / 1e12
+    fused_ms = statistics.mean(f[1] for f in fused)
+    prep_ms = statistics.mean(f[0] for f in fused)
+    unpack_ms = statistics.mean(f[2] for f in fused)
+    E_val = float(E.item())
+
+    # parity against stored oracle values (written by tests/golden/make_golden.py)
+    parity = None
+    gpath = os.path.join(ROOT, "tests", "golden", args.workload + ".json")
+    if os.path.exists(gpath):
+        g = json.load(open(gpath))
+        Rh = R.cpu().numpy()
+        cols = np.array(g["R_cols"])
+        got = np.stack([Rh[:, :, a, b] for a, b in zip(g["pairs_a"], g["pairs_b"])])
+        parity = {"dE_L": abs(E_val - g["E_L"]), "E_L": g["E_L"],
+                  "rel_fro_sampled_cols": float(np.linalg.norm(got - cols) / np.linalg.norm(cols)),
+                  "rel_fro_norm": abs(float(np.linalg.norm(Rh)) - g["R_fro"]) / g["R_fro"]}
+
+    pk, pk_kind = peaks()
+    prod = PRODUCTS[args.mode]
+    if args.mode == "fp64":
+        roof = {"bound": "fp64", "achieved": F / (fused_ms * 1e-3) / 1e12, "peak": None,
+                "unit": "TFLOP/s", "frac": None, "traffic": None}
+    else:
+        achieved = prod * F / (fused_ms * 1e-3) / 1e12
+        peak = pk["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "ladder_tc_kernel<%d>" % (2 if args.mode == "bf16x3" else 3),
+                "note": "achieved = %d x F_alg (bf16 tensor flops of the split scheme) / fused-kernel "
+                        "time; peak = bf16 sustained (%s)" % (prod, pk_kind)}
+
+    extra = {}
+    # the other split variant and the FP64 path, same workload, one timed step each
+    others = [] if args.mode != "bf16x6" else ["bf16x3"]
+    if not args.no_fp64 and args.mode != "fp64":
+        others.append("fp64")
+    for m in others:
+        Lm = lad.Ladder(w.o, w.v, w.naux, mode=m, device=dev)
+        lad.ladder_set_timing(Lm.plan, True)
+        if m != "fp64":
+            step(Lm)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        step(Lm)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        Lm.check_device()
+        mms = a0.elapsed_time(a1)
+        tm = lad.ladder_timing(Lm.plan)
+        ent = {"ms_per_step": mms, "tflops": F / (mms * 1e-3) / 1e12, "fused_ms": tm[1],
+               "E_L": float(E.item()), "steps": 1}
+        if parity is not None:
+            ent["dE_L"] = abs(float(E.item()) - parity["E_L"])
+        extra[m] = ent
+        Lm.close()
+        del Lm
+        torch.cuda.empty_cache()
+    if "fp64" in extra:
+        extra["speedup_vs_fp64"] = extra["fp64"]["ms_per_step"] / ms
+
+    # end to end through the public API with host buffers: inputs copied from
+    # pinned host memory each step, E_L read back each step
+    e2e = None
+    if not args.no_e2e:
+        h_t1 = torch.from_numpy(x.t1).pin_memory()
+        h_t2 = torch.from_numpy(x.t2).pin_memory()
+        h_B = torch.from_numpy(x.B).pin_memory()
+        barrier()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for _ in range(args.steps):
+            t1.copy_(h_t1, non_blocking=True)
+            t2.copy_(h_t2, non_blocking=True)
+            B.copy_(h_B, non_blocking=True)
+            step(L)
+            _ = float(E.item())
+        q1.record(stream)
+        barrier()
+        ems = max_over_ranks(q0.elapsed_time(q1) / args.steps)
+        h2d = (h_t1.numel() + h_t2.numel() + h_B.numel()) * 8
+        e2e = {"value": world * F / (ems * 1e-3) / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8, "ms_per_step": ems}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        full, dt, desc, thr = oracle_sample(x, 15.0)
+        cpu = {"value": F / full / 1e12, "unit": "TFLOP/s", "cores": thr, "kind": "oracle",
+               "sample": desc + "; full-term time extrapolated", "ms_per_step": full * 1e3}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x%d-split" % prod if args.mode != "fp64" else "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "o": w.o, "v": w.v, "naux": w.naux,
+                       "seed": w.seed, "mode": args.mode, "parallelism": "replicas",
+                       "l2": "inputs larger than L2 (B %.2f GB, tau %.2f GB)"
+                             % (B.numel() * 8 / 1e9, tau.numel() * 8 / 1e9)},
+            "stages_ms": {"prep": prep_ms, "fused": fused_ms, "unpack": unpack_ms},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": 7 * args.steps, "parity": parity, "E_L": E_val, "others": extra,
+        }
+        print(json.dumps(line), flush=True)
+    L.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

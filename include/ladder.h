@@ -119,6 +119,15 @@ ladder_status ladder_apply_batched(ladder_plan_t plan, const double *const *B,
  * first failed wait (0 if none) when where != NULL. */
 ladder_status ladder_last_device_error(ladder_plan_t plan, void *stream, int *where);
 
+/* Stage timing of ladder_apply.  With timing on, ladder_apply records CUDA
+ * events on its stream around its three stages (operand preparation: slicing
+ * and packing; the fused ladder kernel; unpacking of R).  ladder_timing waits
+ * for the events of the last ladder_apply and returns the three durations in
+ * milliseconds (any pointer may be NULL).  Timing is off by default; the
+ * events are created by ladder_set_timing (no device memory). */
+ladder_status ladder_set_timing(ladder_plan_t plan, int on);
+ladder_status ladder_timing(ladder_plan_t plan, float *prep_ms, float *fused_ms, float *unpack_ms);
+
 /* Algorithmic flop count of one ladder_apply (two flops per multiply-add of
  * the symmetric/antisymmetric scheme; identical for every mode). */
 double ladder_flops(ladder_plan_t plan);

@@ -27,7 +27,8 @@ STATUS = {0: "LADDER_OK", 1: "LADDER_EINVAL", 2: "LADDER_ENOMEM", 3: "LADDER_ECU
 EXPORTS = ("ladder_plan", "ladder_plan_mode", "ladder_workspace_size", "ladder_set_workspace",
            "ladder_tau", "ladder_apply", "ladder_energy", "ladder_backward", "ladder_apply_host",
            "ladder_plan_batched", "ladder_apply_batched", "ladder_last_device_error",
-           "ladder_flops", "ladder_status_string", "ladder_destroy")
+           "ladder_set_timing", "ladder_timing", "ladder_flops", "ladder_status_string",
+           "ladder_destroy")
 
 
 class LadderError(RuntimeError):
@@ -63,6 +64,9 @@ def load_library(path: str = LIB_PATH):
         "ladder_plan_batched": [i, ip, ip, ip, i, pp],
         "ladder_apply_batched": [_P, pp, pp, pp, _P],
         "ladder_last_device_error": [_P, _P, ip],
+        "ladder_set_timing": [_P, i],
+        "ladder_timing": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                          ctypes.POINTER(ctypes.c_float)],
         "ladder_flops": [_P],
         "ladder_status_string": [i],
         "ladder_destroy": [_P],
@@ -162,6 +166,17 @@ def ladder_last_device_error(plan, stream=None):
     where = ctypes.c_int()
     st = load_library().ladder_last_device_error(plan, _stream(stream), ctypes.byref(where))
     return st, where.value
+
+
+def ladder_set_timing(plan, on: bool) -> None:
+    _check("ladder_set_timing", load_library().ladder_set_timing(plan, 1 if on else 0))
+
+
+def ladder_timing(plan):
+    """(prep_ms, fused_ms, unpack_ms) of the last ladder_apply (waits for it)."""
+    t = [ctypes.c_float() for _ in range(3)]
+    _check("ladder_timing", load_library().ladder_timing(plan, *[ctypes.byref(x) for x in t]))
+    return tuple(x.value for x in t)
 
 
 def ladder_status_string(status: int) -> str:

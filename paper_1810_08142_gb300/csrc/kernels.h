@@ -68,5 +68,6 @@ struct TcArgs {
 };
 uint32_t tc_smem_bytes(int nslices);
 cudaError_t launch_ladder_tc(const TcArgs &a, int nslices, int grid, cudaStream_t s);
+cudaError_t launch_unpack(const TcArgs &a, cudaStream_t s);
 
 }  // namespace ladder

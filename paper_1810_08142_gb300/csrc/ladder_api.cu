@@ -69,6 +69,8 @@ struct ladder_plan_s {
   std::vector<TcChunk> chunks_tc;
   CUtensorMap tmA, tmB, tmTp, tmTm;
   Layout lay;
+  bool timing = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   void *ws = nullptr;
   size_t ws_bytes = 0;
 };
@@ -301,8 +303,13 @@ ladder_status ladder_tau(ladder_plan_t pl, const double *t1, const double *t2, d
   return cuda_status(cudaGetLastError());
 }
 
+static void mark(ladder_plan_t pl, int k, cudaStream_t s) {
+  if (pl->timing) cudaEventRecord(pl->ev[k], s);
+}
+
 static ladder_status apply_fp64(ladder_plan_t pl, const double *B, const double *tau, double *R,
                                 cudaStream_t s) {
+  mark(pl, 0, s);
   double *Tp = ws_at<double>(pl, pl->lay.Tp), *Tm = ws_at<double>(pl, pl->lay.Tm);
   launch_pack_tpm_f64(pl->o, pl->v, pl->K, tau, Tp, Tm, s);
   ladder_status st = cuda_status(cudaGetLastError());
@@ -321,11 +328,16 @@ static ladder_status apply_fp64(ladder_plan_t pl, const double *B, const double 
   a.ntiles = ppos(pl->vp / CB);
   a.nchunks = (int)pl->chunks64.size();
   for (int c = 0; c < a.nchunks; ++c) a.chunks[c] = pl->chunks64[c];
-  return cuda_status(launch_ladder_fp64(a, pl->grid64, s));
+  mark(pl, 1, s);
+  st = cuda_status(launch_ladder_fp64(a, pl->grid64, s));
+  mark(pl, 2, s);
+  mark(pl, 3, s);
+  return st;
 }
 
 static ladder_status apply_tc(ladder_plan_t pl, const double *B, const double *tau, double *R,
                               cudaStream_t s) {
+  mark(pl, 0, s);
   auto *Bt = ws_at<__nv_bfloat16>(pl, pl->lay.Bt);
   auto *Tp = ws_at<__nv_bfloat16>(pl, pl->lay.Tp);
   auto *Tm = ws_at<__nv_bfloat16>(pl, pl->lay.Tm);
@@ -362,7 +374,12 @@ static ladder_status apply_tc(ladder_plan_t pl, const double *B, const double *t
   // generous bound on any single wait: 2 s plus 20x the estimated item time
   const double item_flops = 2.0 * pl->nbp * 2.0 * 128.0 * 64.0 * pl->Np * 6.0 / pl->ksplit;
   a.timeout_ns = (unsigned long long)(2e9 + 20.0 * item_flops / 4e12 * 1e9);
-  return cuda_status(launch_ladder_tc(a, pl->S, a.ntiles * a.nchunks * a.ksplit, s));
+  mark(pl, 1, s);
+  st = cuda_status(launch_ladder_tc(a, pl->S, a.ntiles * a.nchunks * a.ksplit, s));
+  mark(pl, 2, s);
+  if (st == LADDER_OK) st = cuda_status(launch_unpack(a, s));
+  mark(pl, 3, s);
+  return st;
 }
 
 ladder_status ladder_apply(ladder_plan_t pl, const double *B, const double *tau, double *R,
@@ -436,6 +453,30 @@ ladder_status ladder_last_device_error(ladder_plan_t pl, void *stream, int *wher
   return h == 0 ? LADDER_OK : LADDER_ETIMEOUT;
 }
 
+ladder_status ladder_set_timing(ladder_plan_t pl, int on) {
+  if (!pl) return LADDER_EINVAL;
+  if (on && !pl->ev[0]) {
+    for (auto &e : pl->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return cuda_status(cudaErrorUnknown);
+  }
+  pl->timing = on != 0;
+  return LADDER_OK;
+}
+
+ladder_status ladder_timing(ladder_plan_t pl, float *prep_ms, float *fused_ms, float *unpack_ms) {
+  if (!pl) return LADDER_EINVAL;
+  if (!pl->timing || !pl->ev[0]) return LADDER_EINVAL;
+  if (cudaEventSynchronize(pl->ev[3]) != cudaSuccess) return cuda_status(cudaErrorUnknown);
+  float t[3] = {0, 0, 0};
+  for (int k = 0; k < 3; ++k)
+    if (cudaEventElapsedTime(&t[k], pl->ev[k], pl->ev[k + 1]) != cudaSuccess)
+      return cuda_status(cudaErrorUnknown);
+  if (prep_ms) *prep_ms = t[0];
+  if (fused_ms) *fused_ms = t[1];
+  if (unpack_ms) *unpack_ms = t[2];
+  return LADDER_OK;
+}
+
 double ladder_flops(ladder_plan_t pl) {
   if (!pl) return 0.0;
   const double g1 = 2.0 * ppos(pl->v) * (double)pl->v * pl->v * pl->N;
@@ -444,6 +485,11 @@ double ladder_flops(ladder_plan_t pl) {
   return g1 + g2;
 }
 
-void ladder_destroy(ladder_plan_t pl) { delete pl; }
+void ladder_destroy(ladder_plan_t pl) {
+  if (!pl) return;
+  for (auto &e : pl->ev)
+    if (e) cudaEventDestroy(e);
+  delete pl;
+}
 
 }  // extern "C"

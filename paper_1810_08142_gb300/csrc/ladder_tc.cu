@@ -540,8 +540,10 @@ cudaError_t launch_ladder_tc(const TcArgs &a, int nslices, int grid, cudaStream_
     if (e != cudaSuccess) return e;
     ladder_tc_kernel<3><<<grid, kThreads, Cfg<3>::kSmem, s>>>(a);
   }
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const TcArgs &a, cudaStream_t s) {
   unpack_kernel<<<a.ntiles * a.nchunks, 128, 0, s>>>(a);
   return cudaGetLastError();
 }

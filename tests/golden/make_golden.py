@@ -1,0 +1,56 @@
+"""Write stored oracle values for the full-size workloads.
+
+Calls only the CPU oracle (and the seeded input generator).  For each
+workload it evaluates tau, the full ladder term R and E_L with the plain FP64
+oracle and stores: E_L, the Frobenius norm of R, and the R columns
+R[:, :, a, b] of a fixed list of (a, b) pairs.  Run from the repository root:
+    python tests/golden/make_golden.py mid_o34_v400_n1600
+"""
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import oracle  # noqa: E402
+import synthetic  # noqa: E402
+
+
+def sample_pairs(v, n=12, seed=1234):
+    rng = np.random.default_rng(seed)
+    pa = rng.integers(0, v, size=n)
+    pb = rng.integers(0, v, size=n)
+    pa[0], pb[0] = 0, v - 1
+    pa[1], pb[1] = v - 1, v - 1
+    return [int(x) for x in pa], [int(x) for x in pb]
+
+
+def main(name):
+    w = synthetic.WORKLOADS[name]
+    t0 = time.time()
+    x = synthetic.make_inputs(w.o, w.v, w.naux, w.seed)
+    tau = oracle.tau(x.t1, x.t2)
+    R = oracle.ladder(x.B, tau)
+    E = oracle.energy(R, x.t2)
+    pa, pb = sample_pairs(w.v)
+    cols = [R[:, :, a, b].tolist() for a, b in zip(pa, pb)]
+    out = {
+        "workload": name, "o": w.o, "v": w.v, "naux": w.naux, "seed": w.seed,
+        "E_L": E, "R_fro": float(np.linalg.norm(R)),
+        "pairs_a": pa, "pairs_b": pb, "R_cols": cols,
+        "oracle_threads": oracle.threads(), "oracle_seconds": time.time() - t0,
+        "note": "written by tests/golden/make_golden.py from the plain FP64 CPU oracle",
+    }
+    path = os.path.join(ROOT, "tests", "golden", name + ".json")
+    with open(path, "w") as f:
+        json.dump(out, f)
+    print(name, "E_L", E, "seconds", time.time() - t0)
+
+
+if __name__ == "__main__":
+    for n in sys.argv[1:]:
+        main(n)
