@@ -90,6 +90,18 @@ ladder_status ladder_apply(ladder_plan_t plan, const double *B, const double *ta
 ladder_status ladder_energy(ladder_plan_t plan, const double *R, const double *t2,
                             double *E_dev, void *stream);
 
+/* E_L as ladder_energy computes it, for callers that cannot allocate device
+ * memory (no plan, no workspace).  The paper has no counterpart of this call.
+ * The partial sums of the reduction live in a fixed 4 MiB array owned by the
+ * library (524288 doubles; held on every device that loads the library until
+ * the process exits).  Shapes that need more partials than that, i.e.
+ * ceil(v/32)^2 * o^2 > 524288, return LADDER_ENOTSUP before any launch.
+ * The first call on a device looks up the array's device address (make it
+ * before any stream capture); calls that overlap on the GPU race on the
+ * array.  R, t2 and E_dev are device pointers as for ladder_energy. */
+ladder_status ladder_energy_noalloc(int o, int v, const double *R, const double *t2,
+                                    double *E_dev, void *stream);
+
 /* Adjoint of ladder_apply for E = sum W_ij^ab R_ij^ab with fixed weights W
  * (W must be pair symmetric, W_ij^ab = W_ji^ba; for E_L, W = 2 t2 - t2^T):
  *   dtau_ij^cd = sum_ab W_ij^ab (ac|bd)                          (transposed ladder)

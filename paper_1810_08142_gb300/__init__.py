@@ -25,7 +25,7 @@ STATUS = {0: "LADDER_OK", 1: "LADDER_EINVAL", 2: "LADDER_ENOMEM", 3: "LADDER_ECU
 
 # every entry point that include/ladder.h declares
 EXPORTS = ("ladder_plan", "ladder_plan_mode", "ladder_workspace_size", "ladder_set_workspace",
-           "ladder_tau", "ladder_apply", "ladder_energy", "ladder_backward", "ladder_apply_host",
+           "ladder_tau", "ladder_apply", "ladder_energy", "ladder_energy_noalloc", "ladder_backward", "ladder_apply_host",
            "ladder_plan_batched", "ladder_apply_batched", "ladder_last_device_error",
            "ladder_set_timing", "ladder_timing", "ladder_flops", "ladder_status_string",
            "ladder_destroy")
@@ -59,6 +59,7 @@ def load_library(path: str = LIB_PATH):
         "ladder_tau": [_P, _P, _P, _P, _P],
         "ladder_apply": [_P, _P, _P, _P, _P],
         "ladder_energy": [_P, _P, _P, _P, _P],
+        "ladder_energy_noalloc": [i, i, _P, _P, _P, _P],
         "ladder_backward": [_P, _P, _P, _P, _P, _P, _P],
         "ladder_apply_host": [_P, _P, _P, _P, _P, _P, _P, _P],
         "ladder_plan_batched": [i, ip, ip, ip, i, pp],
@@ -133,6 +134,13 @@ def ladder_apply(plan, B, tau, R, stream=None) -> None:
 
 def ladder_energy(plan, R, t2, E, stream=None) -> None:
     _check("ladder_energy", load_library().ladder_energy(plan, _ptr(R), _ptr(t2), _ptr(E), _stream(stream)))
+
+
+def ladder_energy_noalloc(o, v, R, t2, E, stream=None) -> None:
+    """E_L without a plan or workspace, for callers that cannot allocate device
+    memory; see include/ladder.h for the limit on o and v."""
+    _check("ladder_energy_noalloc", load_library().ladder_energy_noalloc(
+        int(o), int(v), _ptr(R), _ptr(t2), _ptr(E), _stream(stream)))
 
 
 def ladder_backward(plan, B, tau, W, dtau, dB, stream=None) -> None:
