@@ -61,6 +61,10 @@ typedef enum {
     LADDER_AUTO = 3         /* let the plan pick (autotuned cache, else BF16X6) */
 } ladder_mode;
 
+/* OR this into `mode` to size the workspace for ladder_backward as well
+ * (the FP64 gradient with respect to B spills tiles of Gamma^{xb}_{yd}). */
+#define LADDER_WITH_BACKWARD 16
+
 /* Create a plan for one shape.  1 <= o <= 256, 1 <= v <= 4096, 1 <= naux <= 65536.
  * The plan owns no device memory; see ladder_workspace_size. */
 ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out);
@@ -107,9 +111,19 @@ ladder_status ladder_energy_noalloc(int o, int v, const double *R, const double 
  *   dtau_ij^cd = sum_ab W_ij^ab (ac|bd)                          (transposed ladder)
  *   dB^P_xy    = sum_{ij,b,d} W_ij^{xb} tau_ij^{yd} B^P_bd
  *              + sum_{ij,a,c} W_ij^{ax} tau_ij^{cy} B^P_ac
- * Either output may be NULL to skip it.  Outputs are overwritten. */
+ * dtau runs the plan's own mode: the ladder of W with every factor B^P
+ * transposed.  dB runs in FP64 (both terms are equal under the pair symmetry
+ * of W and tau, so it evaluates 2 x the first); it needs a plan created with
+ * LADDER_WITH_BACKWARD (else LADDER_EWORKSPACE).  Either output may be NULL
+ * to skip it.  Outputs are overwritten.  dtau may not alias W or tau. */
 ladder_status ladder_backward(ladder_plan_t plan, const double *B, const double *tau,
                               const double *W, double *dtau, double *dB, void *stream);
+
+/* Y_ij^ab = alpha X_ij^ab + beta X_ij^ba over [o][o][v][v] (device arrays,
+ * Y may not alias X).  (2, -1) applied to t2 gives the energy weights
+ * W = dE_L/dR; applied to R it gives dE_L/dt2 through the weights. */
+ladder_status ladder_pair_combine(int o, int v, double alpha, double beta, const double *X,
+                                  double *Y, void *stream);
 
 /* Host-buffer convenience path: copies B and tau from host memory (pinned
  * memory recommended), runs ladder_apply and ladder_energy-free apply, and

@@ -19,13 +19,14 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libladder.so")
 
 LADDER_FP64, LADDER_BF16X3, LADDER_BF16X6, LADDER_AUTO = 0, 1, 2, 3
+LADDER_WITH_BACKWARD = 16
 MODES = {"fp64": LADDER_FP64, "bf16x3": LADDER_BF16X3, "bf16x6": LADDER_BF16X6, "auto": LADDER_AUTO}
 STATUS = {0: "LADDER_OK", 1: "LADDER_EINVAL", 2: "LADDER_ENOMEM", 3: "LADDER_ECUDA",
           4: "LADDER_ETIMEOUT", 5: "LADDER_ENOTSUP", 6: "LADDER_EWORKSPACE"}
 
 # every entry point that include/ladder.h declares
 EXPORTS = ("ladder_plan", "ladder_plan_mode", "ladder_workspace_size", "ladder_set_workspace",
-           "ladder_tau", "ladder_apply", "ladder_energy", "ladder_energy_noalloc", "ladder_backward", "ladder_apply_host",
+           "ladder_tau", "ladder_apply", "ladder_energy", "ladder_energy_noalloc", "ladder_backward", "ladder_pair_combine", "ladder_apply_host",
            "ladder_plan_batched", "ladder_apply_batched", "ladder_last_device_error",
            "ladder_set_timing", "ladder_timing", "ladder_flops", "ladder_status_string",
            "ladder_destroy")
@@ -61,6 +62,7 @@ def load_library(path: str = LIB_PATH):
         "ladder_energy": [_P, _P, _P, _P, _P],
         "ladder_energy_noalloc": [i, i, _P, _P, _P, _P],
         "ladder_backward": [_P, _P, _P, _P, _P, _P, _P],
+        "ladder_pair_combine": [i, i, ctypes.c_double, ctypes.c_double, _P, _P, _P],
         "ladder_apply_host": [_P, _P, _P, _P, _P, _P, _P, _P],
         "ladder_plan_batched": [i, ip, ip, ip, i, pp],
         "ladder_apply_batched": [_P, pp, pp, pp, _P],
@@ -148,6 +150,11 @@ def ladder_backward(plan, B, tau, W, dtau, dB, stream=None) -> None:
         plan, _ptr(B), _ptr(tau), _ptr(W), _ptr(dtau), _ptr(dB), _stream(stream)))
 
 
+def ladder_pair_combine(o, v, alpha, beta, X, Y, stream=None) -> None:
+    _check("ladder_pair_combine", load_library().ladder_pair_combine(
+        int(o), int(v), float(alpha), float(beta), _ptr(X), _ptr(Y), _stream(stream)))
+
+
 def ladder_apply_host(plan, B_host, tau_host, R_host, d_B, d_tau, d_R, stream=None) -> None:
     _check("ladder_apply_host", load_library().ladder_apply_host(
         plan, _ptr(B_host), _ptr(tau_host), _ptr(R_host), _ptr(d_B), _ptr(d_tau), _ptr(d_R),
@@ -203,10 +210,12 @@ def ladder_destroy(plan) -> None:
 class Ladder:
     """A plan plus its workspace (a torch uint8 tensor on the current device)."""
 
-    def __init__(self, o: int, v: int, naux: int, mode="bf16x6", device=None):
+    def __init__(self, o: int, v: int, naux: int, mode="bf16x6", device=None, backward=False):
         import torch
         self.o, self.v, self.naux = o, v, naux
         m = MODES[mode] if isinstance(mode, str) else int(mode)
+        if backward:
+            m |= LADDER_WITH_BACKWARD
         self.device = torch.device(device if device is not None else "cuda")
         with torch.cuda.device(self.device):
             self.plan = ladder_plan(o, v, naux, m)
@@ -236,6 +245,21 @@ class Ladder:
         out = torch.empty((), dtype=torch.float64, device=R.device) if out is None else out
         ladder_energy(self.plan, R, t2, out)
         return out
+
+    def weights(self, t2, out=None):
+        """Energy weights W = 2 t2 - t2^T (dE_L/dR)."""
+        import torch
+        out = torch.empty_like(t2) if out is None else out
+        ladder_pair_combine(self.o, self.v, 2.0, -1.0, t2, out)
+        return out
+
+    def backward(self, B, tau, W, dtau=True, dB=True):
+        """(dtau, dB) of E = sum W R; pass False to skip one."""
+        import torch
+        dt = torch.empty_like(tau) if dtau is True else (dtau or None)
+        db = torch.empty_like(B) if dB is True else (dB or None)
+        ladder_backward(self.plan, B, tau, W, dt, db)
+        return dt, db
 
     def check_device(self):
         st, where = ladder_last_device_error(self.plan)

@@ -1,0 +1,50 @@
+"""torch.autograd.Function around the ladder energy.
+
+E_L(B, tau, t2) = sum_ijab R_ij^ab (2 t2_ij^ab - t2_ij^ba) with R the ladder
+term of (B, tau).  Forward: ladder_apply + ladder_energy.  Backward, with
+W = 2 t2 - t2^T (ladder_pair_combine):
+    dE/dtau = transposed ladder of W           (ladder_backward)
+    dE/dB   = 2 sum Gamma B, Gamma = W^T tau    (ladder_backward, FP64)
+    dE/dt2  = 2 R - R^T                         (ladder_pair_combine)
+All arithmetic runs in the library's kernels; the incoming gradient (a
+scalar) is applied with an in-place multiply.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import Ladder, ladder_pair_combine
+
+
+class LadderEnergy(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, B, tau, t2, ladder: Ladder):
+        R = ladder.apply(B, tau)
+        E = ladder.energy(R, t2)
+        ctx.save_for_backward(B, tau, t2, R)
+        ctx.ladder = ladder
+        return E
+
+    @staticmethod
+    def backward(ctx, gE):
+        B, tau, t2, R = ctx.saved_tensors
+        L = ctx.ladder
+        need_B, need_tau, need_t2 = ctx.needs_input_grad[:3]
+        dB = dtau = dt2 = None
+        if need_B or need_tau:
+            W = L.weights(t2)
+            dtau, dB = L.backward(B, tau, W, dtau=bool(need_tau), dB=bool(need_B))
+        if need_t2:
+            dt2 = torch.empty_like(t2)
+            ladder_pair_combine(L.o, L.v, 2.0, -1.0, R, dt2)
+        g = gE.to(torch.float64)
+        for t in (dB, dtau, dt2):
+            if t is not None:
+                t.mul_(g)
+        return dB, dtau, dt2, None
+
+
+def ladder_energy(B, tau, t2, ladder: Ladder):
+    """Differentiable E_L(B, tau, t2) computed by `ladder` (a Ladder plan;
+    create it with backward=True when dE/dB is wanted)."""
+    return LadderEnergy.apply(B, tau, t2, ladder)

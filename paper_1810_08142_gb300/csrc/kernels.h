@@ -16,11 +16,12 @@ void launch_pack_tpm_bf16(int o, int v, int K, int nslices, int rows_p, int rows
                           const double *tau, __nv_bfloat16 *Tp, __nv_bfloat16 *Tm,
                           cudaStream_t s);
 void launch_split_B(int N, int v, int vp, int Np, int nslices, const double *B,
-                    __nv_bfloat16 *Bt, cudaStream_t s);
+                    __nv_bfloat16 *Bt, cudaStream_t s, bool transB = false);
+void launch_pair_combine(int o, int v, double alpha, double beta, const double *X, double *Y,
+                         cudaStream_t s);
 size_t energy_partials(int o, int v);
 void launch_energy(int o, int v, const double *R, const double *t2, double *part, double *E,
                    cudaStream_t s);
-void launch_energy_weights(int o, int v, const double *t2, double *W, cudaStream_t s);
 
 // ---- FP64 fused ladder (DMMA)
 struct Fp64Args {
@@ -31,6 +32,7 @@ struct Fp64Args {
   double *slab;      // spill of the V+- tiles, grid * K * 128 doubles (null if one chunk)
   int o, v, N, vp, K;
   int ntiles;        // (8-block, 8-block) ab tiles with ia <= ib
+  int transB;        // read B^P_ca for B^P_ac (adjoint: transposed ladder)
   int nchunks;
   Chunk chunks[kMaxChunks];
 };
@@ -38,6 +40,20 @@ constexpr int kFp64LamTile = 64;  // max lambda+ (and lambda-) rows per chunk
 int fp64_grid(const Fp64Args &a, int sm_count);
 size_t fp64_slab_doubles(int K, int grid);
 cudaError_t launch_ladder_fp64(const Fp64Args &a, int grid, cudaStream_t s);
+
+// ---- FP64 gradient with respect to B (adjoint, ladder_grad_fp64.cu)
+constexpr int kGradPChunk = 64;  // auxiliary functions per register-accumulator chunk
+struct GradArgs {
+  const double *B;    // [N][v][v]
+  const double *tau;  // [o][o][v][v]
+  const double *W;    // [o][o][v][v]
+  double *dB;         // [N][v][v]
+  double *slab;       // Gamma spill, grad_fp64_slab_doubles (null if one P-chunk)
+  int o, v, N, vp;
+};
+int grad_fp64_grid(int vp, int sm_count);
+size_t grad_fp64_slab_doubles(int vp, int N, int grid);
+cudaError_t launch_grad_B_fp64(const GradArgs &a, int grid, cudaStream_t s);
 
 // ---- split-BF16 fused ladder (tcgen05)
 // An occupied-pair chunk of the tensor-core kernel: lambda+ rows [lp0, lp0+np)
@@ -61,6 +77,7 @@ struct TcArgs {
   int ntiles, nchunks, ksplit;
   int racc_cols;
   int kc;            // GEMM1 K-steps (of 32 aux functions) per FP32 accumulation chain
+  int xy_split;      // GEMM1: separate accumulators for hi*hi and the smaller products
   int s_pieces;      // 16-slot pieces of GEMM2 per fresh S accumulator (1, 2 or 4)
   int flush_every;   // S accumulators summed in FP32 before an FP64 flush
   unsigned long long timeout_ns;

@@ -21,7 +21,7 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
 
 struct Layout {
-  size_t status = 0, energy = 0, Tp = 0, Tm = 0, slab = 0, Bt = 0, W = 0, total = 0;
+  size_t status = 0, energy = 0, Tp = 0, Tm = 0, slab = 0, Bt = 0, W = 0, gslab = 0, total = 0;
 };
 
 int tc_slices(int mode) { return mode == LADDER_BF16X3 ? 2 : 3; }
@@ -58,6 +58,8 @@ bool encode3d(CUtensorMap *m, void *base, uint64_t d0, uint64_t d1, uint64_t d2,
 
 struct ladder_plan_s {
   int o = 0, v = 0, N = 0, mode = 0;
+  bool backward = false;
+  int grid_grad = 0;
   int vp = 0, nb = 0, nbp = 0, K = 0, Np = 0;
   int nlp = 0, nlm = 0;
   int sm_count = 0, device = 0;
@@ -65,7 +67,7 @@ struct ladder_plan_s {
   std::vector<Chunk> chunks64;
   int grid64 = 0;
   // split-BF16 tensor-core path
-  int S = 0, ksplit = 1, kc = 4, s_pieces = 4, flush_every = 16, ntiles_tc = 0, racc_cols = 0;
+  int S = 0, ksplit = 1, kc = 4, s_pieces = 4, flush_every = 16, xy_split = 1, ntiles_tc = 0, racc_cols = 0;
   std::vector<TcChunk> chunks_tc;
   CUtensorMap tmA, tmB, tmTp, tmTm;
   Layout lay;
@@ -164,7 +166,9 @@ void compute_layout(ladder_plan_s *pl) {
     off = align_up(off + (size_t)pl->ntiles_tc * pl->chunks_tc.size() * pl->ksplit * 128 *
                              pl->racc_cols * sizeof(double));
   }
-  L.W = off;  // backward: energy weights / scratch copies are caller-provided
+  L.W = off;
+  L.gslab = off;  // FP64 dB: spill of the Gamma tiles
+  if (pl->backward) off = align_up(off + grad_fp64_slab_doubles(pl->vp, pl->N, pl->grid_grad) * sizeof(double));
   L.total = off;
   pl->lay = L;
 }
@@ -190,6 +194,8 @@ ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out) 
   if (!out) return LADDER_EINVAL;
   *out = nullptr;
   if (o < 1 || o > 256 || v < 1 || v > 4096 || naux < 1 || naux > 65536) return LADDER_EINVAL;
+  const bool with_backward = (mode & LADDER_WITH_BACKWARD) != 0;
+  mode &= ~LADDER_WITH_BACKWARD;
   if (mode < LADDER_FP64 || mode > LADDER_AUTO) return LADDER_EINVAL;
   if (mode == LADDER_AUTO) mode = LADDER_BF16X6;
   ladder_plan_s *pl = new (std::nothrow) ladder_plan_s();
@@ -198,6 +204,7 @@ ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out) 
   pl->v = v;
   pl->N = naux;
   pl->mode = mode;
+  pl->backward = with_backward;
   pl->vp = (v + VPAD - 1) / VPAD * VPAD;
   pl->nb = pl->vp / CB;
   pl->nbp = ppos(pl->nb);
@@ -226,11 +233,15 @@ ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out) 
     int ks = (2 * pl->sm_count + items - 1) / items;
     ks = std::max(1, std::min(ks, pl->nbp / 4));
     pl->ksplit = ks;
-    // FP32 accumulation chains (see ladder_tc.cu): BF16X3 is limited by its
-    // slicing error (~4e-6), so its chains are long (24 / 12 MMAs); BF16X6 keeps
-    // them at 12 MMAs (GEMM1) and 6 MMAs (GEMM2)
-    pl->kc = pl->S == 2 ? 4 : 1;
+    // FP32 accumulation chains (see ladder_tc.cu).  GEMM1: with separate
+    // hi*hi / small-product accumulators a chain of kc K-steps puts 2*kc MMAs
+    // on the large accumulator (32 for BF16X3, 8 for BF16X6).  GEMM2: a fresh
+    // S every block pair (12 MMAs, BF16X3) or every piece (6 MMAs, BF16X6).
+    pl->xy_split = 1;
+    pl->kc = pl->S == 2 ? 16 : 4;
     pl->s_pieces = pl->S == 2 ? 4 : 1;
+    if (const char *e = getenv("LADDER_XYSPLIT")) pl->xy_split = atoi(e) != 0;
+    if (!pl->xy_split) pl->kc = pl->S == 2 ? 4 : 1;
     pl->flush_every = 16;
     if (const char *e = getenv("LADDER_KC")) pl->kc = std::max(1, atoi(e));
     if (const char *e = getenv("LADDER_SPIECES")) {
@@ -253,6 +264,7 @@ ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out) 
   Fp64Args tmp{};
   tmp.ntiles = ppos(pl->vp / CB);
   pl->grid64 = fp64_grid(tmp, pl->sm_count);
+  pl->grid_grad = grad_fp64_grid(pl->vp, pl->sm_count);
   compute_layout(pl);
   *out = pl;
   return LADDER_OK;
@@ -308,7 +320,7 @@ static void mark(ladder_plan_t pl, int k, cudaStream_t s) {
 }
 
 static ladder_status apply_fp64(ladder_plan_t pl, const double *B, const double *tau, double *R,
-                                cudaStream_t s) {
+                                cudaStream_t s, bool transB = false) {
   mark(pl, 0, s);
   double *Tp = ws_at<double>(pl, pl->lay.Tp), *Tm = ws_at<double>(pl, pl->lay.Tm);
   launch_pack_tpm_f64(pl->o, pl->v, pl->K, tau, Tp, Tm, s);
@@ -326,6 +338,7 @@ static ladder_status apply_fp64(ladder_plan_t pl, const double *B, const double 
   a.vp = pl->vp;
   a.K = pl->K;
   a.ntiles = ppos(pl->vp / CB);
+  a.transB = transB ? 1 : 0;
   a.nchunks = (int)pl->chunks64.size();
   for (int c = 0; c < a.nchunks; ++c) a.chunks[c] = pl->chunks64[c];
   mark(pl, 1, s);
@@ -336,12 +349,12 @@ static ladder_status apply_fp64(ladder_plan_t pl, const double *B, const double 
 }
 
 static ladder_status apply_tc(ladder_plan_t pl, const double *B, const double *tau, double *R,
-                              cudaStream_t s) {
+                              cudaStream_t s, bool transB = false) {
   mark(pl, 0, s);
   auto *Bt = ws_at<__nv_bfloat16>(pl, pl->lay.Bt);
   auto *Tp = ws_at<__nv_bfloat16>(pl, pl->lay.Tp);
   auto *Tm = ws_at<__nv_bfloat16>(pl, pl->lay.Tm);
-  launch_split_B(pl->N, pl->v, pl->vp, pl->Np, pl->S, B, Bt, s);
+  launch_split_B(pl->N, pl->v, pl->vp, pl->Np, pl->S, B, Bt, s, transB);
   launch_pack_tpm_bf16(pl->o, pl->v, pl->K, pl->S, pl->nlp, std::max(pl->nlm, 1), tau, Tp, Tm, s);
   ladder_status st = cuda_status(cudaGetLastError());
   if (st != LADDER_OK) return st;
@@ -368,6 +381,7 @@ static ladder_status apply_tc(ladder_plan_t pl, const double *B, const double *t
   a.racc = ws_at<double>(pl, pl->lay.slab);
   a.racc_cols = pl->racc_cols;
   a.kc = pl->kc;
+  a.xy_split = pl->xy_split;
   a.s_pieces = pl->s_pieces;
   a.flush_every = pl->flush_every;
   for (int c = 0; c < a.nchunks; ++c) a.chunks[c] = pl->chunks_tc[c];
@@ -405,8 +419,43 @@ ladder_status ladder_energy(ladder_plan_t pl, const double *R, const double *t2,
 
 ladder_status ladder_backward(ladder_plan_t pl, const double *B, const double *tau,
                               const double *W, double *dtau, double *dB, void *stream) {
-  (void)pl; (void)B; (void)tau; (void)W; (void)dtau; (void)dB; (void)stream;
-  return LADDER_ENOTSUP;
+  if (!pl) return LADDER_EINVAL;
+  if (!pl->ws) return LADDER_EWORKSPACE;
+  if (!dev_ptr_ok(B) || !dev_ptr_ok(tau) || !dev_ptr_ok(W)) return LADDER_EINVAL;
+  if (dtau && (!dev_ptr_ok(dtau) || dtau == W || dtau == tau || dtau == B)) return LADDER_EINVAL;
+  if (dB && (!dev_ptr_ok(dB) || dB == B)) return LADDER_EINVAL;
+  if (dB && !pl->backward) return LADDER_EWORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (dtau) {
+    // transposed ladder: dtau = sum_ab W_ij^ab (ac|bd), i.e. the ladder of W
+    // with every factor B^P replaced by its transpose
+    const ladder_status st = pl->mode == LADDER_FP64 ? apply_fp64(pl, B, W, dtau, s, true)
+                                                     : apply_tc(pl, B, W, dtau, s, true);
+    if (st != LADDER_OK) return st;
+  }
+  if (dB) {
+    GradArgs g{};
+    g.B = B;
+    g.tau = tau;
+    g.W = W;
+    g.dB = dB;
+    g.slab = pl->N > kGradPChunk ? ws_at<double>(pl, pl->lay.gslab) : nullptr;
+    g.o = pl->o;
+    g.v = pl->v;
+    g.N = pl->N;
+    g.vp = pl->vp;
+    const ladder_status st = cuda_status(launch_grad_B_fp64(g, pl->grid_grad, s));
+    if (st != LADDER_OK) return st;
+  }
+  return LADDER_OK;
+}
+
+ladder_status ladder_pair_combine(int o, int v, double alpha, double beta, const double *X,
+                                  double *Y, void *stream) {
+  if (o < 1 || o > 256 || v < 1 || v > 4096) return LADDER_EINVAL;
+  if (!dev_ptr_ok(X) || !dev_ptr_ok(Y) || X == Y) return LADDER_EINVAL;
+  launch_pair_combine(o, v, alpha, beta, X, Y, static_cast<cudaStream_t>(stream));
+  return cuda_status(cudaGetLastError());
 }
 
 ladder_status ladder_apply_host(ladder_plan_t pl, const double *B_host, const double *tau_host,

@@ -60,7 +60,9 @@ __device__ __forceinline__ void load_panel(double *panel, const Fp64Args &A, int
     const int y = ((set == 0 || set == 3) ? k : l) * CB + r % 8;
     const int PP = P0 + P;
     const bool ok = PP < A.N && x < A.v && y < A.v;
-    const double *src = ok ? A.B + ((size_t)PP * A.v + x) * A.v + y : A.B;
+    // transB: the factor is read as B^P_yx (the transposed ladder of the adjoint)
+    const size_t off = A.transB ? ((size_t)PP * A.v + y) * A.v + x : ((size_t)PP * A.v + x) * A.v + y;
+    const double *src = ok ? A.B + off : A.B;
     cp_async8(panel + P * PSTR + set * 64 + r, src, ok ? 8 : 0);
   }
   cp_async_commit();

@@ -11,9 +11,13 @@
 // instruction with a bias, so the error of one accumulator grows linearly
 // with the number of MMAs that feed it.  Every FP32 accumulation chain here is
 // therefore short, and chains are summed outside the tensor core:
-//   GEMM1 (K = aux functions) runs in chains of `kc` K-steps that alternate
-//         between two TMEM buffers; the conversion warps sum the chains in
-//         registers (FP32, round to nearest);
+//   GEMM1 (K = aux functions) runs in chains of `kc` K-steps; the
+//         conversion warps sum the chains in registers (FP32, round to
+//         nearest).  With `xy_split` the hi*hi slice product and the smaller
+//         products go to separate accumulators: the error an MMA adds scales
+//         with the accumulator it lands in, so the small products then cost
+//         almost nothing and chains can be long; without it, chains alternate
+//         between two TMEM buffers;
 //   GEMM2 (K = slots) starts a fresh TMEM accumulator S every `s_pieces`
 //         pieces of 16 slots (a block pair has 4);
 //         the conversion warps add S into a TMEM running sum R (FP32, round to
@@ -29,7 +33,9 @@
 //   warp 1    MMA issuer (one thread): GEMM1 X[(a,c),(b,d)], Y[(a,d),(b,c)]
 //             (M=128, N=64) and GEMM2 S+-[ab][lambda] = V+-[ab][slots]
 //             T+-[lambda][slots]^T (M=128, N=lambda);
-//   warps 2-5 conversion: TMEM -> registers, exchange of Y within groups of 8
+//   warps 2-9 conversion (two per TMEM lane quadrant, each owning half of the
+//             columns: b = 0-3 or 4-7 of X and Y, every other 16 columns of S
+//             and R): TMEM -> registers, exchange of Y within groups of 8
 //             lanes by shuffles, V+- = X +- Y', BF16 slicing, swizzled stores
 //             into the GEMM2 operand tile; S -> R sums; FP64 flushes.
 // The integral tiles live only in TMEM, registers and shared memory.
@@ -40,8 +46,8 @@ namespace ladder {
 namespace {
 using namespace tc;
 
-constexpr int kThreads = 192;
-constexpr int kEpi = 128;
+constexpr int kThreads = 320;   // warp 0 TMA, warp 1 MMA, warps 2-9 conversion
+constexpr int kEpi = 256;       // two conversion warps per TMEM lane quadrant
 constexpr int KSTEP = 32;                             // aux functions per GEMM1 stage
 constexpr uint32_t A_TILE = 128u * KSTEP * 2u;        // 8 KB: rows (a,c), 64-byte rows
 constexpr uint32_t B_TILE = 64u * KSTEP * 2u;         // 4 KB: rows (b,d)
@@ -84,6 +90,15 @@ __device__ __forceinline__ void transpose8(float (&r)[8], int x) {
         r[j ^ s] = recv;
     }
   }
+}
+
+// Shared-memory descriptor from an address and a precomputed high word
+// (stride byte offset, fixed bits, layout type; see sdesc).
+__device__ __forceinline__ uint32_t desc_hi(uint32_t sbo_bytes, uint32_t layout) {
+  return ((sbo_bytes >> 4) & 0x3FFFu) | (1u << 14) | (layout << 29);
+}
+__device__ __forceinline__ uint64_t desc64(uint32_t saddr, uint32_t hi) {
+  return ((uint64_t)hi << 32) | (uint64_t)(((saddr >> 4) & 0x3FFFu) | (1u << 16));
 }
 
 // One BF16 slice of 8 values (round to nearest); `rem` keeps what is left.
@@ -191,6 +206,11 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
   const Watchdog wd{A.status, abort_flag, A.timeout_ns};
   const int kc = A.kc;
   const int nch_full = (A.nks + kc - 1) / kc;  // GEMM1 chains per block pair
+  // GEMM1 accumulators: split = one buffer with separate accumulators for the
+  // hi*hi product (cols 0-127) and the smaller products (cols 128-255);
+  // otherwise two alternating buffers of 128 columns
+  const bool split = A.xy_split != 0;
+  const uint32_t nbuf = split ? 1u : 2u;
 
   if (warp == 0) {
     // ================================================================ TMA producer
@@ -265,6 +285,8 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
       const uint32_t idp = idesc_bf16(128, CH.nps > 0 ? CH.nps : 16);
       const uint32_t idm = idesc_bf16(128, CH.nms > 0 ? CH.nms : 16);
       const uint32_t tbytes = sc * 32u;
+      const uint32_t hi64 = desc_hi(512, kSwizzle64), hi128 = desc_hi(1024, kSwizzle128),
+                     hi32 = desc_hi(256, kSwizzle32);
       bool ok = true;
       for (int p = p0; ok && p <= p1; ++p) {
         if (p < p1) {
@@ -272,24 +294,27 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
           pair_of(p, k, l);
           const int ntile = (k == l) ? 1 : 2;
           for (int c = 0; ok && c < nch_full; ++c) {
-            const int buf = (int)(g & 1u);
-            if (!(ok = mbar_wait(bars.cfree(buf), ((g >> 1) & 1u) ^ 1u, wd, kSiteXYFree))) break;
+            const int buf = (int)(g % nbuf);
+            if (!(ok = mbar_wait(bars.cfree(buf), ((g / nbuf) & 1u) ^ 1u, wd, kSiteXYFree))) break;
             tc_fence_after();
-            const uint32_t dX = tmem + (uint32_t)buf * 128u;
             const int ks0 = c * kc, ks1 = min(A.nks, ks0 + kc);
             for (int ks = ks0; ok && ks < ks1; ++ks)
               for (int tt = 0; tt < ntile; ++tt) {
                 if (!(ok = mbar_wait(bars.full(stage), phase, wd, kSiteTmaFull))) break;
                 tc_fence_after();
                 const uint32_t st = ring + (uint32_t)stage * C::kStage;
+                const uint32_t dT = tmem + (split ? 0u : (uint32_t)buf * 128u) + (tt ? 64u : 0u);
 #pragma unroll
                 for (int kk = 0; kk < KSTEP / 16; ++kk)
 #pragma unroll
                   for (int q = 0; q < C::kProducts; ++q) {
-                    const uint64_t ad = sdesc(st + kPa(q) * A_TILE + kk * 32, 512, kSwizzle64);
-                    const uint64_t bd =
-                        sdesc(st + S * A_TILE + kPb(q) * B_TILE + kk * 32, 512, kSwizzle64);
-                    mma_bf16(dX + (tt ? 64u : 0u), ad, bd, id1, (ks > ks0 || kk || q) ? 1u : 0u);
+                    const uint64_t ad = desc64(st + kPa(q) * A_TILE + kk * 32, hi64);
+                    const uint64_t bd = desc64(st + S * A_TILE + kPb(q) * B_TILE + kk * 32, hi64);
+                    // split: the hi*hi product into the "big" accumulator,
+                    // every smaller product into the "small" one (128 columns on)
+                    const bool small = split && q > 0;
+                    const bool first = (ks == ks0) && kk == 0 && (split ? (q <= 1) : (q == 0));
+                    mma_bf16(dT + (small ? 128u : 0u), ad, bd, id1, first ? 0u : 1u);
                   }
                 mma_commit(bars.empty(stage));
                 if (++stage == C::kStages) {
@@ -319,13 +344,12 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
 #pragma unroll
             for (int q = 0; q < C::kProducts; ++q) {
               const uint32_t acc = (first && q == 0) ? 0u : 1u;
-              const uint64_t ap = sdesc(vbase + (0 * S + kPa(q)) * V_TILE + piece * 32, 1024, kSwizzle128);
-              const uint64_t bp = sdesc(st + kPb(q) * tbytes, 256, kSwizzle32);
+              const uint64_t ap = desc64(vbase + (0 * S + kPa(q)) * V_TILE + piece * 32, hi128);
+              const uint64_t bp = desc64(st + kPb(q) * tbytes, hi32);
               mma_bf16(tmem + kColS, ap, bp, idp, acc);
               if (CH.nms > 0) {
-                const uint64_t am =
-                    sdesc(vbase + (1 * S + kPa(q)) * V_TILE + piece * 32, 1024, kSwizzle128);
-                const uint64_t bm = sdesc(st + kPb(q) * tbytes + CH.nps * 32, 256, kSwizzle32);
+                const uint64_t am = desc64(vbase + (1 * S + kPa(q)) * V_TILE + piece * 32, hi128);
+                const uint64_t bm = desc64(st + kPb(q) * tbytes + CH.nps * 32, hi32);
                 mma_bf16(tmem + kColS + CH.nps, am, bm, idm, acc);
               }
             }
@@ -352,7 +376,8 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
   } else {
     // ================================================================ conversion warps
     const int quad = warp & 3;
-    const int L = quad * 32 + lane;  // TMEM lane
+    const int half = (warp - 2) >> 2;  // which half of the columns this warp owns
+    const int L = quad * 32 + lane;    // TMEM lane
     const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
     const int a_l = L >> 3, x_l = L & 7;
     uint32_t g = 0, v_use = 0, s_use = 0;
@@ -364,7 +389,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
       if (!mbar_wait(bars.s_full(), s_use & 1u, wd, kSiteRFull)) return false;
       ++s_use;
       tc_fence_after();
-      for (uint32_t c0 = 0; c0 < sc; c0 += 16) {
+      for (uint32_t c0 = 16u * half; c0 < sc; c0 += 32) {
         float s[16], r[16];
         tmem_ld16(tl + kColS + c0, s);
         if (nacc > 0) tmem_ld16(tl + kColS + sc + c0, r);
@@ -383,7 +408,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
     };
     // R (FP32, TMEM) -> FP64 accumulator in the workspace, [col][lane]
     auto flush_R = [&]() {
-      for (uint32_t c0 = 0; c0 < sc; c0 += 16) {
+      for (uint32_t c0 = 16u * half; c0 < sc; c0 += 32) {
         float r[16];
         tmem_ld16(tl + kColS + sc + c0, r);
         tmem_ld_wait();
@@ -401,20 +426,32 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
       int k, l;
       pair_of(p, k, l);
       const bool diag = (k == l);
-      float X[64], Y[64];
+      float X[32], Y[32];  // columns (b, 0..7) for b in [4*half, 4*half+4)
       for (int c = 0; c < nch_full; ++c) {
-        const int buf = (int)(g & 1u);
-        if (!(ok = mbar_wait(bars.cfull(buf), (g >> 1) & 1u, wd, kSiteXYFull))) break;
+        const int buf = (int)(g % nbuf);
+        if (!(ok = mbar_wait(bars.cfull(buf), (g / nbuf) & 1u, wd, kSiteXYFull))) break;
         ++g;
         tc_fence_after();
-        const uint32_t cX = tl + (uint32_t)buf * 128u;
+        const uint32_t cX = tl + (split ? 0u : (uint32_t)buf * 128u) + 32u * half;
         const uint32_t cY = diag ? cX : cX + 64u;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 2; ++q) {
           float tx[16], ty[16];
           tmem_ld16(cX + q * 16, tx);
           tmem_ld16(cY + q * 16, ty);
-          tmem_ld_wait();
+          if (split) {
+            float sx[16], sy[16];
+            tmem_ld16(cX + 128u + q * 16, sx);
+            tmem_ld16(cY + 128u + q * 16, sy);
+            tmem_ld_wait();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              tx[i] += sx[i];
+              ty[i] += sy[i];
+            }
+          } else {
+            tmem_ld_wait();
+          }
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
             X[q * 16 + i] = c ? X[q * 16 + i] + tx[i] : tx[i];
@@ -436,7 +473,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
       // Y row of lane (a, d=x_l) holds (ad|bc) at column (b, c); after the
       // transpose lane (a, c=x_l) holds (ad|bc) at index (b, d).
 #pragma unroll
-      for (int b = 0; b < 8; ++b) {
+      for (int b = 0; b < 4; ++b) {
         float r[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) r[j] = Y[b * 8 + j];
@@ -447,8 +484,8 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
       if (!(ok = mbar_wait(bars.v_free(), (v_use & 1u) ^ 1u, wd, kSiteVFree))) break;
       ++v_use;
 #pragma unroll
-      for (int b = 0; b < 8; ++b) {
-        const int row = a_l * 8 + b;
+      for (int b = 0; b < 4; ++b) {
+        const int row = a_l * 8 + 4 * half + b;
         const uint32_t off = (uint32_t)row * 128u + (uint32_t)((x_l ^ (row & 7)) * 16);
 #pragma unroll
         for (int sg = 0; sg < 2; ++sg) {

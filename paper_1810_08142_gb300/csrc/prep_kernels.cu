@@ -117,14 +117,16 @@ void launch_pack_tpm_bf16(int o, int v, int K, int nslices, int rows_p, int rows
 // read (c fastest) and the write (P fastest) are coalesced.
 template <int S>
 __global__ void split_B_kernel(int N, int v, int vp, int Np, const double *__restrict__ B,
-                               __nv_bfloat16 *__restrict__ Bt) {
+                               __nv_bfloat16 *__restrict__ Bt, int transB) {
   __shared__ double tile[32][33];
   const int a = blockIdx.z;
   const int c0 = blockIdx.x * 32, P0 = blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   for (int r = ty; r < 32; r += 8) {
     const int P = P0 + r, c = c0 + tx;
-    tile[r][tx] = (P < N && c < v && a < v) ? B[((size_t)P * v + a) * v + c] : 0.0;
+    // transB: slice B^P_ca at position (a, c) (the transposed ladder of the adjoint)
+    const size_t src = transB ? ((size_t)P * v + c) * v + a : ((size_t)P * v + a) * v + c;
+    tile[r][tx] = (P < N && c < v && a < v) ? B[src] : 0.0;
   }
   __syncthreads();
   const size_t slice = (size_t)vp * vp * Np;
@@ -141,12 +143,12 @@ __global__ void split_B_kernel(int N, int v, int vp, int Np, const double *__res
 }
 
 void launch_split_B(int N, int v, int vp, int Np, int nslices, const double *B,
-                    __nv_bfloat16 *Bt, cudaStream_t s) {
+                    __nv_bfloat16 *Bt, cudaStream_t s, bool transB) {
   dim3 grid((vp + 31) / 32, (Np + 31) / 32, vp), block(32, 8);
   if (nslices == 2)
-    split_B_kernel<2><<<grid, block, 0, s>>>(N, v, vp, Np, B, Bt);
+    split_B_kernel<2><<<grid, block, 0, s>>>(N, v, vp, Np, B, Bt, transB ? 1 : 0);
   else
-    split_B_kernel<3><<<grid, block, 0, s>>>(N, v, vp, Np, B, Bt);
+    split_B_kernel<3><<<grid, block, 0, s>>>(N, v, vp, Np, B, Bt, transB ? 1 : 0);
 }
 
 // ---------------------------------------------------------------- energy
@@ -217,9 +219,11 @@ void launch_energy(int o, int v, const double *R, const double *t2, double *part
   energy_final_kernel<<<1, kEnergyThreads, 0, s>>>(energy_partials(o, v), part, E);
 }
 
-// Energy weights W = 2 t2 - t2^T (the adjoint seed of E_L with respect to R).
-__global__ void energy_weights_kernel(int o, int v, const double *__restrict__ t2,
-                                      double *__restrict__ W) {
+// Y_ij^ab = alpha X_ij^ab + beta X_ij^ba.  With (alpha, beta) = (2, -1) this is
+// the energy weight W = 2 t2 - t2^T (dE_L/dR) and, applied to R, the
+// derivative of E_L through its weights, dE_L/dt2 = 2 R - R^T.
+__global__ void pair_combine_kernel(int o, int v, double alpha, double beta,
+                                    const double *__restrict__ X, double *__restrict__ Y) {
   const size_t total = (size_t)o * o * v * v;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
@@ -227,16 +231,17 @@ __global__ void energy_weights_kernel(int o, int v, const double *__restrict__ t
     const size_t r = idx / v;
     const int a = (int)(r % v);
     const size_t ij = r / v;
-    W[idx] = 2.0 * t2[idx] - t2[(ij * v + b) * v + a];
+    Y[idx] = alpha * X[idx] + beta * X[(ij * v + b) * v + a];
   }
 }
 
-void launch_energy_weights(int o, int v, const double *t2, double *W, cudaStream_t s) {
+void launch_pair_combine(int o, int v, double alpha, double beta, const double *X, double *Y,
+                         cudaStream_t s) {
   const size_t total = (size_t)o * o * v * v;
   int blocks = (int)((total + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
-  energy_weights_kernel<<<blocks, 256, 0, s>>>(o, v, t2, W);
+  pair_combine_kernel<<<blocks, 256, 0, s>>>(o, v, alpha, beta, X, Y);
 }
 
 }  // namespace ladder

@@ -1,0 +1,121 @@
+"""Adjoint of the ladder term on the GPU against the CPU oracle's analytic
+gradient, and central finite differences through the autograd Function.
+
+E = sum W_ij^ab R_ij^ab is linear in tau and quadratic in B, so central
+differences have no truncation error: only rounding (about 1e-16 |E| / h)."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+from gpu_util import rel_fro, to_dev
+
+pytestmark = pytest.mark.gpu
+
+DTAU_TOL = {"fp64": 1e-12, "bf16x6": 1e-6, "bf16x3": 2e-5}
+
+
+@pytest.fixture(scope="module")
+def lad():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1810_08142_gb300 as lad
+    return lad
+
+
+@pytest.mark.parametrize("mode", ["fp64", "bf16x6", "bf16x3"])
+@pytest.mark.parametrize("o,v,n,seed", [(3, 10, 30, 3), (4, 24, 96, 0), (5, 17, 33, 12), (6, 40, 90, 21)])
+def test_backward_matches_oracle_gradient(lad, mode, o, v, n, seed):
+    import torch
+    rng = np.random.default_rng(seed)
+    B = rng.standard_normal((n, v, v)) * 0.1          # general B (no a<->c symmetry)
+    x = synthetic.make_inputs(o, v, n, seed)
+    tau = oracle.tau(x.t1, x.t2)
+    W = oracle.energy_weights(x.t2)
+    L = lad.Ladder(o, v, n, mode=mode, backward=True)
+    dtau, dB = L.backward(to_dev(B), to_dev(tau), to_dev(W))
+    torch.cuda.synchronize()
+    L.check_device()
+    e_tau = rel_fro(dtau.cpu().numpy(), oracle.grad_tau(B, W))
+    e_B = rel_fro(dB.cpu().numpy(), oracle.grad_B(B, tau, W))
+    print("%s o=%d v=%d n=%d: dtau rel-F %.3e  dB rel-F %.3e" % (mode, o, v, n, e_tau, e_B))
+    assert e_tau < DTAU_TOL[mode]
+    assert e_B < 1e-12  # dB runs in FP64 in every mode
+
+
+def test_weights_kernel_matches_oracle(lad):
+    x = synthetic.make_inputs(4, 13, 20, 5)
+    L = lad.Ladder(4, 13, 20, mode="fp64")
+    W = L.weights(to_dev(x.t2)).cpu().numpy()
+    assert np.array_equal(W, oracle.energy_weights(x.t2))
+
+
+def test_autograd_central_differences_fp64(lad):
+    """dE_L/dB, dE_L/dtau and dE_L/dt2 from LadderEnergy against central
+    differences with step 1e-6 at o=3, v=10, N_aux=30."""
+    import torch
+    from paper_1810_08142_gb300.autograd import ladder_energy
+    w = synthetic.WORKLOADS["fd_o3_v10_n30"]
+    x = synthetic.make_inputs(w.o, w.v, w.naux, w.seed)
+    L = lad.Ladder(w.o, w.v, w.naux, mode="fp64", backward=True)
+    tau0 = oracle.tau(x.t1, x.t2)
+    B = to_dev(x.B).requires_grad_(True)
+    tau = to_dev(tau0).requires_grad_(True)
+    t2 = to_dev(x.t2).requires_grad_(True)
+    E = ladder_energy(B, tau, t2, L)
+    E.backward()
+    gB, gtau, gt2 = B.grad.cpu().numpy(), tau.grad.cpu().numpy(), t2.grad.cpu().numpy()
+
+    def energy(Bn, taun, t2n):
+        with torch.no_grad():
+            return float(ladder_energy(to_dev(Bn), to_dev(taun), to_dev(t2n), L).item())
+
+    rng = np.random.default_rng(99)
+    h = 1e-6
+    for which in ("B", "tau", "t2"):
+        base = {"B": x.B, "tau": tau0, "t2": x.t2}
+        D = rng.standard_normal(base[which].shape)
+        if which in ("tau", "t2"):
+            D = 0.5 * (D + D.transpose(1, 0, 3, 2))  # stay on pair-symmetric inputs
+        plus = dict(base)
+        minus = dict(base)
+        plus[which] = base[which] + h * D
+        minus[which] = base[which] - h * D
+        fd = (energy(plus["B"], plus["tau"], plus["t2"]) -
+              energy(minus["B"], minus["tau"], minus["t2"])) / (2 * h)
+        an = float(np.sum({"B": gB, "tau": gtau, "t2": gt2}[which] * D))
+        print("FD %s: fd %.12e analytic %.12e" % (which, fd, an))
+        assert abs(fd - an) <= 1e-7 * max(abs(an), 1e-12)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "bf16x6"])
+def test_backward_full_size_sampled(lad, mode):
+    """Gradient workload o=16, v=200, N_aux=800: sampled entries of dtau and
+    dB against the oracle's entry-wise analytic gradient."""
+    import torch
+    w = synthetic.WORKLOADS["grad_o16_v200_n800"]
+    x = synthetic.make_inputs(w.o, w.v, w.naux, w.seed)
+    tau = oracle.tau(x.t1, x.t2)
+    W = oracle.energy_weights(x.t2)
+    L = lad.Ladder(w.o, w.v, w.naux, mode=mode, backward=True)
+    dtau, dB = L.backward(to_dev(x.B), to_dev(tau), to_dev(W))
+    torch.cuda.synchronize()
+    L.check_device()
+    dtau, dB = dtau.cpu().numpy(), dB.cpu().numpy()
+    rng = np.random.default_rng(7)
+    m = 24
+    i, j = rng.integers(0, w.o, m), rng.integers(0, w.o, m)
+    c, d = rng.integers(0, w.v, m), rng.integers(0, w.v, m)
+    ref = oracle.grad_tau_entries(x.B, W, i, j, c, d)
+    got = dtau[i, j, c, d]
+    e_tau = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    P, xx, yy = rng.integers(0, w.naux, m), rng.integers(0, w.v, m), rng.integers(0, w.v, m)
+    refB = oracle.grad_B_entries(x.B, tau, W, P, xx, yy)
+    gotB = dB[P, xx, yy]
+    e_B = np.linalg.norm(gotB - refB) / np.linalg.norm(refB)
+    print("%s full size: dtau sampled rel %.3e  dB sampled rel %.3e" % (mode, e_tau, e_B))
+    assert e_tau < DTAU_TOL[mode]
+    assert e_B < 1e-12
+    # the dtau output keeps the pair symmetry of the ladder
+    assert np.array_equal(dtau, dtau.transpose(1, 0, 3, 2))
