@@ -133,10 +133,20 @@ ladder_status ladder_apply_host(ladder_plan_t plan, const double *B_host, const 
                                 double *R_host, double *d_B, double *d_tau, double *d_R,
                                 void *stream);
 
-/* Ragged batch: n molecules with their own (o_k, v_k, naux_k), one plan. */
+/* Ragged batch: n molecules with their own (o_k, v_k, naux_k), one plan and one
+ * workspace; mode LADDER_BF16X3 or LADDER_BF16X6 (else LADDER_ENOTSUP).  The
+ * fused kernel of every molecule runs in one persistent launch over all
+ * molecules' work units, ordered by cost (largest first).  A batched plan
+ * serves only ladder_apply_batched (the other calls return LADDER_EINVAL);
+ * ladder_energy_noalloc gives the energy of each molecule. */
 ladder_status ladder_plan_batched(int n, const int *o, const int *v, const int *naux, int mode,
                                   ladder_plan_t *out);
-/* B[k], tau[k], R[k] are device pointers for molecule k (host arrays of n pointers). */
+/* B[k], tau[k], R[k] are device pointers for molecule k (host arrays of n
+ * pointers).  The first call with a given set of pointers records the whole
+ * batch (operand preparation of every molecule, the fused launch, the unpack)
+ * as a CUDA graph on a private stream; it synchronises `stream` and copies the
+ * per-molecule arguments into the workspace first.  Calls with the same
+ * pointers replay the graph on `stream` without synchronising. */
 ladder_status ladder_apply_batched(ladder_plan_t plan, const double *const *B,
                                    const double *const *tau, double *const *R, void *stream);
 

@@ -276,3 +276,46 @@ class Ladder:
             self.close()
         except Exception:
             pass
+
+
+class LadderBatch:
+    """A batched plan for molecules of uneven shape (one persistent fused
+    launch, replayed as a CUDA graph) plus its workspace."""
+
+    def __init__(self, shapes, mode="bf16x6", device=None):
+        import torch
+        self.shapes = [(int(o), int(v), int(n)) for o, v, n in shapes]
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        self.device = torch.device(device if device is not None else "cuda")
+        with torch.cuda.device(self.device):
+            self.plan = ladder_plan_batched([s[0] for s in self.shapes], [s[1] for s in self.shapes],
+                                            [s[2] for s in self.shapes], m)
+            n = ladder_workspace_size(self.plan)
+            self.workspace = torch.empty(max(n, 256), dtype=torch.uint8, device=self.device)
+            ladder_set_workspace(self.plan, self.workspace)
+
+    @property
+    def flops(self) -> float:
+        return ladder_flops(self.plan)
+
+    def apply(self, Bs, taus, outs=None):
+        import torch
+        outs = [torch.empty_like(t) for t in taus] if outs is None else outs
+        ladder_apply_batched(self.plan, Bs, taus, outs)
+        return outs
+
+    def check_device(self):
+        st, where = ladder_last_device_error(self.plan)
+        if st != 0:
+            raise LadderError("device wait (site %d)" % where, st)
+
+    def close(self):
+        if getattr(self, "plan", None) is not None:
+            ladder_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

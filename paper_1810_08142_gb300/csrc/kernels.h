@@ -83,8 +83,21 @@ struct TcArgs {
   unsigned long long timeout_ns;
   TcChunk chunks[kMaxChunks];
 };
+// One launch of the fused kernel: a single molecule (mols == nullptr, the
+// work units are 0..nitems-1 of `one`) or a batch (work unit k is local item
+// items[k].y of molecule items[k].x, args in device memory).  tcs lists the
+// (molecule, tile*chunk) blocks of the unpack kernel for a batch.
+struct TcLaunch {
+  TcArgs one;
+  const TcArgs *mols;
+  const int2 *items;
+  const int2 *tcs;
+  int nitems;
+  unsigned long long timeout_ns;
+};
 uint32_t tc_smem_bytes(int nslices);
-cudaError_t launch_ladder_tc(const TcArgs &a, int nslices, int grid, cudaStream_t s);
-cudaError_t launch_unpack(const TcArgs &a, cudaStream_t s);
+cudaError_t tc_init_attributes(int nslices);  // once per device, outside stream capture
+cudaError_t launch_ladder_tc(const TcLaunch &a, int nslices, int grid, cudaStream_t s);
+cudaError_t launch_unpack(const TcLaunch &a, int nblocks, cudaStream_t s);
 
 }  // namespace ladder

@@ -71,6 +71,15 @@ struct ladder_plan_s {
   std::vector<TcChunk> chunks_tc;
   CUtensorMap tmA, tmB, tmTp, tmTm;
   Layout lay;
+  // ragged batch: one sub-plan per molecule inside this plan's workspace
+  bool batched = false;
+  std::vector<ladder_plan_s *> subs;
+  std::vector<size_t> sub_off;
+  std::vector<int2> items, tcs;  // (molecule, local work unit), (molecule, tile*chunk)
+  size_t off_mols = 0, off_items = 0, off_tcs = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<const void *> gkey;  // pointers the graph was captured with
   bool timing = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   void *ws = nullptr;
@@ -190,16 +199,13 @@ const char *ladder_status_string(ladder_status s) {
   return "unknown status";
 }
 
-ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out) {
-  if (!out) return LADDER_EINVAL;
-  *out = nullptr;
+// Fills a plan for one shape; batch members get no block-pair split (the
+// batch itself keeps every SM busy).
+static ladder_status init_plan(ladder_plan_s *pl, int o, int v, int naux, int mode,
+                               bool with_backward, bool batch_member) {
   if (o < 1 || o > 256 || v < 1 || v > 4096 || naux < 1 || naux > 65536) return LADDER_EINVAL;
-  const bool with_backward = (mode & LADDER_WITH_BACKWARD) != 0;
-  mode &= ~LADDER_WITH_BACKWARD;
   if (mode < LADDER_FP64 || mode > LADDER_AUTO) return LADDER_EINVAL;
   if (mode == LADDER_AUTO) mode = LADDER_BF16X6;
-  ladder_plan_s *pl = new (std::nothrow) ladder_plan_s();
-  if (!pl) return LADDER_ENOMEM;
   pl->o = o;
   pl->v = v;
   pl->N = naux;
@@ -215,7 +221,6 @@ ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out) 
       cudaDeviceGetAttribute(&pl->sm_count, cudaDevAttrMultiProcessorCount, pl->device) !=
           cudaSuccess) {
     cudaGetLastError();
-    delete pl;
     return LADDER_ECUDA;
   }
   pl->chunks64 = make_chunks(o, kFp64LamTile);
@@ -232,7 +237,7 @@ ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out) 
     const int items = pl->ntiles_tc * (int)pl->chunks_tc.size();
     int ks = (2 * pl->sm_count + items - 1) / items;
     ks = std::max(1, std::min(ks, pl->nbp / 4));
-    pl->ksplit = ks;
+    pl->ksplit = batch_member ? 1 : ks;
     // FP32 accumulation chains (see ladder_tc.cu).  GEMM1: with separate
     // hi*hi / small-product accumulators a chain of kc K-steps puts 2*kc MMAs
     // on the large accumulator (32 for BF16X3, 8 for BF16X6).  GEMM2: a fresh
@@ -249,16 +254,13 @@ ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out) 
       if (sp == 1 || sp == 2 || sp == 4) pl->s_pieces = sp;
     }
     if (const char *e = getenv("LADDER_FLUSH")) pl->flush_every = std::max(1, atoi(e));
-    if (const char *e = getenv("LADDER_KSPLIT")) pl->ksplit = std::max(1, std::min(atoi(e), pl->nbp));
+    if (!batch_member)
+      if (const char *e = getenv("LADDER_KSPLIT")) pl->ksplit = std::max(1, std::min(atoi(e), pl->nbp));
     int major = 0, minor = 0;
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, pl->device);
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, pl->device);
-    if ((int)pl->chunks_tc.size() > kMaxChunks || major != 10 || minor != 3) {
-      delete pl;
-      return LADDER_ENOTSUP;
-    }
+    if ((int)pl->chunks_tc.size() > kMaxChunks || major != 10 || minor != 3) return LADDER_ENOTSUP;
   } else if ((int)pl->chunks64.size() > kMaxChunks) {
-    delete pl;
     return LADDER_ENOTSUP;
   }
   Fp64Args tmp{};
@@ -266,6 +268,21 @@ ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out) 
   pl->grid64 = fp64_grid(tmp, pl->sm_count);
   pl->grid_grad = grad_fp64_grid(pl->vp, pl->sm_count);
   compute_layout(pl);
+  return LADDER_OK;
+}
+
+ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out) {
+  if (!out) return LADDER_EINVAL;
+  *out = nullptr;
+  const bool with_backward = (mode & LADDER_WITH_BACKWARD) != 0;
+  mode &= ~LADDER_WITH_BACKWARD;
+  ladder_plan_s *pl = new (std::nothrow) ladder_plan_s();
+  if (!pl) return LADDER_ENOMEM;
+  const ladder_status st = init_plan(pl, o, v, naux, mode, with_backward, false);
+  if (st != LADDER_OK) {
+    delete pl;
+    return st;
+  }
   *out = pl;
   return LADDER_OK;
 }
@@ -282,34 +299,60 @@ ladder_status ladder_workspace_size(ladder_plan_t pl, size_t *bytes) {
   return LADDER_OK;
 }
 
+static ladder_status encode_maps(ladder_plan_s *pl, char *w) {
+  if (pl->mode == LADDER_FP64) return LADDER_OK;
+  const uint64_t S = pl->S;
+  const bool ok =
+      encode3d(&pl->tmA, w + pl->lay.Bt, pl->Np, pl->vp, pl->vp * S, 32, 8, 16,
+               CU_TENSOR_MAP_SWIZZLE_64B) &&
+      encode3d(&pl->tmB, w + pl->lay.Bt, pl->Np, pl->vp, pl->vp * S, 32, 8, 8,
+               CU_TENSOR_MAP_SWIZZLE_64B) &&
+      encode3d(&pl->tmTp, w + pl->lay.Tp, pl->K, pl->nlp, S, 16, 16, 1, CU_TENSOR_MAP_SWIZZLE_32B) &&
+      encode3d(&pl->tmTm, w + pl->lay.Tm, pl->K, std::max(pl->nlm, 1), S, 16, 16, 1,
+               CU_TENSOR_MAP_SWIZZLE_32B);
+  if (!ok) return LADDER_ECUDA;
+  return cuda_status(tc_init_attributes(pl->S));
+}
+
 ladder_status ladder_set_workspace(ladder_plan_t pl, void *dptr, size_t bytes) {
   if (!pl) return LADDER_EINVAL;
   if (bytes < pl->lay.total) return LADDER_EWORKSPACE;
   if (!dptr || (reinterpret_cast<uintptr_t>(dptr) % kAlign)) return LADDER_EINVAL;
   if (!dev_ptr_ok(dptr)) return LADDER_EINVAL;
-  if (pl->mode != LADDER_FP64) {
-    char *w = static_cast<char *>(dptr);
-    const uint64_t S = pl->S;
-    const bool ok =
-        encode3d(&pl->tmA, w + pl->lay.Bt, pl->Np, pl->vp, pl->vp * S, 32, 8, 16,
-                 CU_TENSOR_MAP_SWIZZLE_64B) &&
-        encode3d(&pl->tmB, w + pl->lay.Bt, pl->Np, pl->vp, pl->vp * S, 32, 8, 8,
-                 CU_TENSOR_MAP_SWIZZLE_64B) &&
-        encode3d(&pl->tmTp, w + pl->lay.Tp, pl->K, pl->nlp, S, 16, 16, 1, CU_TENSOR_MAP_SWIZZLE_32B) &&
-        encode3d(&pl->tmTm, w + pl->lay.Tm, pl->K, std::max(pl->nlm, 1), S, 16, 16, 1,
-                 CU_TENSOR_MAP_SWIZZLE_32B);
-    if (!ok) return LADDER_ECUDA;
+  char *w = static_cast<char *>(dptr);
+  if (pl->batched) {
+    for (size_t m = 0; m < pl->subs.size(); ++m) {
+      ladder_plan_s *sp = pl->subs[m];
+      sp->ws = w + pl->sub_off[m];
+      sp->ws_bytes = sp->lay.total;
+      const ladder_status st = encode_maps(sp, static_cast<char *>(sp->ws));
+      if (st != LADDER_OK) return st;
+    }
+    // work lists of the batched launch
+    if (cudaMemcpy(w + pl->off_items, pl->items.data(), pl->items.size() * sizeof(int2),
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(w + pl->off_tcs, pl->tcs.data(), pl->tcs.size() * sizeof(int2),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+      return cuda_status(cudaErrorUnknown);
+    if (pl->gexec) {
+      cudaGraphExecDestroy(pl->gexec);
+      pl->gexec = nullptr;
+      pl->gkey.clear();
+    }
+  } else {
+    const ladder_status st = encode_maps(pl, w);
+    if (st != LADDER_OK) return st;
   }
   pl->ws = dptr;
   pl->ws_bytes = bytes;
-  // the status word starts cleared; this is the plan's only synchronous copy
+  // the status word starts cleared
   if (cudaMemset(dptr, 0, sizeof(int)) != cudaSuccess) return cuda_status(cudaErrorUnknown);
   return LADDER_OK;
 }
 
 ladder_status ladder_tau(ladder_plan_t pl, const double *t1, const double *t2, double *tau,
                          void *stream) {
-  if (!pl || !dev_ptr_ok(t1) || !dev_ptr_ok(t2) || !dev_ptr_ok(tau) || tau == t2)
+  if (!pl || pl->batched || !dev_ptr_ok(t1) || !dev_ptr_ok(t2) || !dev_ptr_ok(tau) || tau == t2)
     return LADDER_EINVAL;
   launch_tau(pl->o, pl->v, t1, t2, tau, static_cast<cudaStream_t>(stream));
   return cuda_status(cudaGetLastError());
@@ -348,16 +391,13 @@ static ladder_status apply_fp64(ladder_plan_t pl, const double *B, const double 
   return st;
 }
 
-static ladder_status apply_tc(ladder_plan_t pl, const double *B, const double *tau, double *R,
-                              cudaStream_t s, bool transB = false) {
-  mark(pl, 0, s);
-  auto *Bt = ws_at<__nv_bfloat16>(pl, pl->lay.Bt);
-  auto *Tp = ws_at<__nv_bfloat16>(pl, pl->lay.Tp);
-  auto *Tm = ws_at<__nv_bfloat16>(pl, pl->lay.Tm);
-  launch_split_B(pl->N, pl->v, pl->vp, pl->Np, pl->S, B, Bt, s, transB);
-  launch_pack_tpm_bf16(pl->o, pl->v, pl->K, pl->S, pl->nlp, std::max(pl->nlm, 1), tau, Tp, Tm, s);
-  ladder_status st = cuda_status(cudaGetLastError());
-  if (st != LADDER_OK) return st;
+static double tc_timeout_ns(const ladder_plan_s *pl) {
+  // generous bound on any single wait: 2 s plus 20x the estimated item time
+  const double item_flops = 2.0 * pl->nbp * 2.0 * 128.0 * 64.0 * pl->Np * 6.0 / pl->ksplit;
+  return 2e9 + 20.0 * item_flops / 4e12 * 1e9;
+}
+
+static TcArgs tc_args(const ladder_plan_s *pl, double *R, int *status) {
   TcArgs a;
   std::memset(&a, 0, sizeof(a));
   a.tmA = pl->tmA;
@@ -365,7 +405,7 @@ static ladder_status apply_tc(ladder_plan_t pl, const double *B, const double *t
   a.tmTp = pl->tmTp;
   a.tmTm = pl->tmTm;
   a.R = R;
-  a.status = ws_at<int>(pl, pl->lay.status);
+  a.status = status;
   a.o = pl->o;
   a.v = pl->v;
   a.vp = pl->vp;
@@ -385,20 +425,41 @@ static ladder_status apply_tc(ladder_plan_t pl, const double *B, const double *t
   a.s_pieces = pl->s_pieces;
   a.flush_every = pl->flush_every;
   for (int c = 0; c < a.nchunks; ++c) a.chunks[c] = pl->chunks_tc[c];
-  // generous bound on any single wait: 2 s plus 20x the estimated item time
-  const double item_flops = 2.0 * pl->nbp * 2.0 * 128.0 * 64.0 * pl->Np * 6.0 / pl->ksplit;
-  a.timeout_ns = (unsigned long long)(2e9 + 20.0 * item_flops / 4e12 * 1e9);
+  a.timeout_ns = (unsigned long long)tc_timeout_ns(pl);
+  return a;
+}
+
+static void tc_prep(ladder_plan_t pl, const double *B, const double *tau, cudaStream_t s,
+                    bool transB) {
+  auto *Bt = ws_at<__nv_bfloat16>(pl, pl->lay.Bt);
+  auto *Tp = ws_at<__nv_bfloat16>(pl, pl->lay.Tp);
+  auto *Tm = ws_at<__nv_bfloat16>(pl, pl->lay.Tm);
+  launch_split_B(pl->N, pl->v, pl->vp, pl->Np, pl->S, B, Bt, s, transB);
+  launch_pack_tpm_bf16(pl->o, pl->v, pl->K, pl->S, pl->nlp, std::max(pl->nlm, 1), tau, Tp, Tm, s);
+}
+
+static ladder_status apply_tc(ladder_plan_t pl, const double *B, const double *tau, double *R,
+                              cudaStream_t s, bool transB = false) {
+  mark(pl, 0, s);
+  tc_prep(pl, B, tau, s, transB);
+  ladder_status st = cuda_status(cudaGetLastError());
+  if (st != LADDER_OK) return st;
+  TcLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  L.one = tc_args(pl, R, ws_at<int>(pl, pl->lay.status));
+  L.nitems = L.one.ntiles * L.one.nchunks * L.one.ksplit;
+  L.timeout_ns = L.one.timeout_ns;
   mark(pl, 1, s);
-  st = cuda_status(launch_ladder_tc(a, pl->S, a.ntiles * a.nchunks * a.ksplit, s));
+  st = cuda_status(launch_ladder_tc(L, pl->S, L.nitems, s));
   mark(pl, 2, s);
-  if (st == LADDER_OK) st = cuda_status(launch_unpack(a, s));
+  if (st == LADDER_OK) st = cuda_status(launch_unpack(L, L.one.ntiles * L.one.nchunks, s));
   mark(pl, 3, s);
   return st;
 }
 
 ladder_status ladder_apply(ladder_plan_t pl, const double *B, const double *tau, double *R,
                            void *stream) {
-  if (!pl) return LADDER_EINVAL;
+  if (!pl || pl->batched) return LADDER_EINVAL;
   if (!pl->ws) return LADDER_EWORKSPACE;
   if (!dev_ptr_ok(B) || !dev_ptr_ok(tau) || !dev_ptr_ok(R) || R == B || R == tau)
     return LADDER_EINVAL;
@@ -409,7 +470,7 @@ ladder_status ladder_apply(ladder_plan_t pl, const double *B, const double *tau,
 
 ladder_status ladder_energy(ladder_plan_t pl, const double *R, const double *t2, double *E_dev,
                             void *stream) {
-  if (!pl) return LADDER_EINVAL;
+  if (!pl || pl->batched) return LADDER_EINVAL;
   if (!pl->ws) return LADDER_EWORKSPACE;
   if (!dev_ptr_ok(R) || !dev_ptr_ok(t2) || !E_dev) return LADDER_EINVAL;
   launch_energy(pl->o, pl->v, R, t2, ws_at<double>(pl, pl->lay.energy), E_dev,
@@ -419,7 +480,7 @@ ladder_status ladder_energy(ladder_plan_t pl, const double *R, const double *t2,
 
 ladder_status ladder_backward(ladder_plan_t pl, const double *B, const double *tau,
                               const double *W, double *dtau, double *dB, void *stream) {
-  if (!pl) return LADDER_EINVAL;
+  if (!pl || pl->batched) return LADDER_EINVAL;
   if (!pl->ws) return LADDER_EWORKSPACE;
   if (!dev_ptr_ok(B) || !dev_ptr_ok(tau) || !dev_ptr_ok(W)) return LADDER_EINVAL;
   if (dtau && (!dev_ptr_ok(dtau) || dtau == W || dtau == tau || dtau == B)) return LADDER_EINVAL;
@@ -461,7 +522,7 @@ ladder_status ladder_pair_combine(int o, int v, double alpha, double beta, const
 ladder_status ladder_apply_host(ladder_plan_t pl, const double *B_host, const double *tau_host,
                                 double *R_host, double *d_B, double *d_tau, double *d_R,
                                 void *stream) {
-  if (!pl || !B_host || !tau_host || !R_host) return LADDER_EINVAL;
+  if (!pl || pl->batched || !B_host || !tau_host || !R_host) return LADDER_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t nB = (size_t)pl->N * pl->v * pl->v * sizeof(double);
   const size_t nT = (size_t)pl->o * pl->o * pl->v * pl->v * sizeof(double);
@@ -478,15 +539,134 @@ ladder_status ladder_apply_host(ladder_plan_t pl, const double *B_host, const do
 
 ladder_status ladder_plan_batched(int n, const int *o, const int *v, const int *naux, int mode,
                                   ladder_plan_t *out) {
-  (void)n; (void)o; (void)v; (void)naux; (void)mode;
-  if (out) *out = nullptr;
-  return LADDER_ENOTSUP;
+  if (!out || n < 1 || n > 4096 || !o || !v || !naux) return LADDER_EINVAL;
+  *out = nullptr;
+  if (mode & LADDER_WITH_BACKWARD) return LADDER_ENOTSUP;
+  if (mode == LADDER_AUTO) mode = LADDER_BF16X6;
+  if (mode != LADDER_BF16X3 && mode != LADDER_BF16X6) return LADDER_ENOTSUP;
+  ladder_plan_s *pl = new (std::nothrow) ladder_plan_s();
+  if (!pl) return LADDER_ENOMEM;
+  pl->batched = true;
+  pl->mode = mode;
+  pl->S = tc_slices(mode);
+  size_t off = kAlign;  // status word
+  pl->lay.status = 0;
+  pl->off_mols = off;
+  off = align_up(off + (size_t)n * sizeof(TcArgs));
+  struct Unit {
+    double cost;
+    int m, k;
+  };
+  std::vector<Unit> units;
+  for (int m = 0; m < n; ++m) {
+    ladder_plan_s *sp = new (std::nothrow) ladder_plan_s();
+    if (!sp) {
+      ladder_destroy(pl);
+      return LADDER_ENOMEM;
+    }
+    pl->subs.push_back(sp);
+    const ladder_status st = init_plan(sp, o[m], v[m], naux[m], mode, false, true);
+    if (st != LADDER_OK) {
+      ladder_destroy(pl);
+      return st;
+    }
+    pl->device = sp->device;
+    pl->sm_count = sp->sm_count;
+    const int nwork = sp->ntiles_tc * (int)sp->chunks_tc.size();
+    // cost of one work unit: block pairs x (GEMM1 K-steps + GEMM2 pieces)
+    const double cost = (double)sp->nbp * (2.0 * (sp->Np / 32) + 4.0);
+    for (int k = 0; k < nwork; ++k) {
+      units.push_back({cost, m, k});
+      pl->tcs.push_back(make_int2(m, k));
+    }
+  }
+  // largest work units first; ties keep molecule order
+  std::stable_sort(units.begin(), units.end(),
+                   [](const Unit &x, const Unit &y) { return x.cost > y.cost; });
+  for (auto &u : units) pl->items.push_back(make_int2(u.m, u.k));
+  pl->off_items = off;
+  off = align_up(off + pl->items.size() * sizeof(int2));
+  pl->off_tcs = off;
+  off = align_up(off + pl->tcs.size() * sizeof(int2));
+  for (auto *sp : pl->subs) {
+    off = align_up(off, 1024);
+    pl->sub_off.push_back(off);
+    off += sp->lay.total;
+  }
+  pl->lay.total = align_up(off);
+  *out = pl;
+  return LADDER_OK;
 }
 
 ladder_status ladder_apply_batched(ladder_plan_t pl, const double *const *B,
                                    const double *const *tau, double *const *R, void *stream) {
-  (void)pl; (void)B; (void)tau; (void)R; (void)stream;
-  return LADDER_ENOTSUP;
+  if (!pl || !pl->batched) return LADDER_EINVAL;
+  if (!pl->ws) return LADDER_EWORKSPACE;
+  if (!B || !tau || !R) return LADDER_EINVAL;
+  const size_t n = pl->subs.size();
+  std::vector<const void *> key;
+  for (size_t m = 0; m < n; ++m) {
+    if (!dev_ptr_ok(B[m]) || !dev_ptr_ok(tau[m]) || !dev_ptr_ok(R[m]) || R[m] == B[m] ||
+        R[m] == tau[m])
+      return LADDER_EINVAL;
+    key.push_back(B[m]);
+    key.push_back(tau[m]);
+    key.push_back(R[m]);
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!pl->gexec || key != pl->gkey) {
+    // (re)build: per-molecule arguments into the workspace table, then capture
+    // the whole batch (operand preparation of every molecule, one fused launch
+    // over the cost-sorted work units of all molecules, one unpack launch)
+    char *w = static_cast<char *>(pl->ws);
+    int *status = ws_at<int>(pl, pl->lay.status);
+    std::vector<TcArgs> args(n);
+    unsigned long long tmax = 0;
+    for (size_t m = 0; m < n; ++m) {
+      args[m] = tc_args(pl->subs[m], R[m], status);
+      tmax = std::max(tmax, args[m].timeout_ns);
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess ||
+        cudaMemcpy(w + pl->off_mols, args.data(), n * sizeof(TcArgs), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+      return cuda_status(cudaErrorUnknown);
+    if (!pl->cap_stream &&
+        cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return cuda_status(cudaErrorUnknown);
+    if (pl->gexec) {
+      cudaGraphExecDestroy(pl->gexec);
+      pl->gexec = nullptr;
+    }
+    TcLaunch L;
+    std::memset(&L, 0, sizeof(L));
+    L.mols = reinterpret_cast<const TcArgs *>(w + pl->off_mols);
+    L.items = reinterpret_cast<const int2 *>(w + pl->off_items);
+    L.tcs = reinterpret_cast<const int2 *>(w + pl->off_tcs);
+    L.nitems = (int)pl->items.size();
+    L.timeout_ns = tmax;
+    cudaStream_t c = pl->cap_stream;
+    if (cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return cuda_status(cudaErrorUnknown);
+    for (size_t m = 0; m < n; ++m) tc_prep(pl->subs[m], B[m], tau[m], c, false);
+    launch_ladder_tc(L, pl->S, std::min(L.nitems, pl->sm_count), c);
+    launch_unpack(L, (int)pl->tcs.size(), c);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(c, &graph);
+    if (ce != cudaSuccess || !graph) return cuda_status(ce == cudaSuccess ? cudaErrorUnknown : ce);
+    const cudaError_t ie = cudaGraphInstantiate(&pl->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      pl->gexec = nullptr;
+      return cuda_status(ie);
+    }
+    pl->gkey = key;
+  }
+  mark(pl, 0, s);
+  mark(pl, 1, s);
+  const ladder_status st = cuda_status(cudaGraphLaunch(pl->gexec, s));
+  mark(pl, 2, s);
+  mark(pl, 3, s);
+  return st;
 }
 
 ladder_status ladder_last_device_error(ladder_plan_t pl, void *stream, int *where) {
@@ -528,6 +708,11 @@ ladder_status ladder_timing(ladder_plan_t pl, float *prep_ms, float *fused_ms, f
 
 double ladder_flops(ladder_plan_t pl) {
   if (!pl) return 0.0;
+  if (pl->batched) {
+    double f = 0.0;
+    for (auto *sp : pl->subs) f += ladder_flops(sp);
+    return f;
+  }
   const double g1 = 2.0 * ppos(pl->v) * (double)pl->v * pl->v * pl->N;
   const double g2 = 2.0 * ((double)ppos(pl->o) * ppos(pl->v) * (double)ppos(pl->v) +
                            (double)pneg(pl->o) * pneg(pl->v) * (double)pneg(pl->v));
@@ -538,6 +723,9 @@ void ladder_destroy(ladder_plan_t pl) {
   if (!pl) return;
   for (auto &e : pl->ev)
     if (e) cudaEventDestroy(e);
+  for (auto *sp : pl->subs) ladder_destroy(sp);
+  if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
+  if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
   delete pl;
 }
 

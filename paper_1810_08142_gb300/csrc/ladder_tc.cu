@@ -138,8 +138,50 @@ struct DrainWatch {
   __device__ DrainWatch(int *status, uint64_t deadline) : wd{status, &zero, deadline} {}
 };
 
+// Work item of the fused kernel: an (a 16-block, b 8-block) tile, an
+// occupied-pair chunk and a range [p0, p1) of block pairs of one molecule.
+struct Item {
+  int iA, jB, A0, B0, p0, p1;
+  TcChunk CH;
+  uint32_t sc;   // TMEM columns of S and of R (nps + nms)
+  double *racc;  // this item's FP64 accumulators, [col][lane]
+};
+
+__device__ __forceinline__ Item decode_item(const TcArgs &A, int item) {
+  Item I;
+  const int ksl = item % A.ksplit;
+  const int tc = item / A.ksplit;
+  const int tile = tc / A.nchunks, ch = tc % A.nchunks;
+  int iA = 0, t = tile;
+  while (t >= A.nB8 - 2 * iA) {
+    t -= A.nB8 - 2 * iA;
+    ++iA;
+  }
+  I.iA = iA;
+  I.jB = 2 * iA + t;
+  I.A0 = iA * 16;
+  I.B0 = I.jB * CB;
+  I.CH = A.chunks[ch];
+  I.p0 = (int)((long long)A.nbp * ksl / A.ksplit);
+  I.p1 = (int)((long long)A.nbp * (ksl + 1) / A.ksplit);
+  I.sc = (uint32_t)(I.CH.nps + I.CH.nms);
+  I.racc = A.racc + (size_t)item * 128 * A.racc_cols;
+  return I;
+}
+
+// The molecule's arguments and the local item index of global work unit `it`.
+__device__ __forceinline__ const TcArgs &item_args(const TcLaunch &Lp, int it, int &local) {
+  if (Lp.mols == nullptr) {
+    local = it;
+    return Lp.one;
+  }
+  const int2 w = Lp.items[it];
+  local = w.y;
+  return Lp.mols[w.x];
+}
+
 template <int S>
-__global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_constant__ TcArgs A) {
+__global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_constant__ TcLaunch Lp) {
   using C = Cfg<S>;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -153,24 +195,6 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
   int *abort_flag = reinterpret_cast<int *>(tmem_holder + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-
-  // ---- work item: ((a 16-block, b 8-block) tile, occupied-pair chunk, block-pair range)
-  const int item = blockIdx.x;
-  const int ksl = item % A.ksplit;
-  const int tc = item / A.ksplit;
-  const int tile = tc / A.nchunks, ch = tc % A.nchunks;
-  int iA = 0, t = tile;
-  while (t >= A.nB8 - 2 * iA) {
-    t -= A.nB8 - 2 * iA;
-    ++iA;
-  }
-  const int jB = 2 * iA + t;
-  const int A0 = iA * 16, B0 = jB * CB;
-  const TcChunk CH = A.chunks[ch];
-  const int p0 = (int)((long long)A.nbp * ksl / A.ksplit);
-  const int p1 = (int)((long long)A.nbp * (ksl + 1) / A.ksplit);
-  const uint32_t sc = (uint32_t)(CH.nps + CH.nms);  // TMEM columns of S and of R
-  double *racc = A.racc + (size_t)item * 128 * A.racc_cols;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::kStages; ++s) {
@@ -189,12 +213,6 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0 && lane == 0) {
-    tma_prefetch_desc(&A.tmA);
-    tma_prefetch_desc(&A.tmB);
-    tma_prefetch_desc(&A.tmTp);
-    tma_prefetch_desc(&A.tmTm);
-  }
   if (warp == 1) {
     tmem_alloc(smem_u32(tmem_holder), 512);
     tmem_relinquish();
@@ -203,14 +221,11 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
-  const Watchdog wd{A.status, abort_flag, A.timeout_ns};
-  const int kc = A.kc;
-  const int nch_full = (A.nks + kc - 1) / kc;  // GEMM1 chains per block pair
-  // GEMM1 accumulators: split = one buffer with separate accumulators for the
-  // hi*hi product (cols 0-127) and the smaller products (cols 128-255);
-  // otherwise two alternating buffers of 128 columns
-  const bool split = A.xy_split != 0;
-  const uint32_t nbuf = split ? 1u : 2u;
+  // every role walks the same sequence of work items; barrier phases carry
+  // over from one item to the next
+  const int it0 = blockIdx.x, itstep = gridDim.x, nit = Lp.nitems;
+  const TcArgs &A0args = Lp.mols ? Lp.mols[0] : Lp.one;
+  const Watchdog wd{A0args.status, abort_flag, Lp.timeout_ns};
 
   if (warp == 0) {
     // ================================================================ TMA producer
@@ -218,59 +233,70 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
       int stage = 0;
       uint32_t phase = 0;
       uint32_t armed = 0, armed_par = 0;  // per stage: armed at least once / parity armed last
-      const uint32_t tbytes = sc * 32u;
       bool ok = true;
-      for (int p = p0; ok && p <= p1; ++p) {
-        if (p < p1) {
-          int k, l;
-          pair_of(p, k, l);
-          const int ntile = (k == l) ? 1 : 2;
-          for (int ks = 0; ok && ks < A.nks; ++ks)
-            for (int tt = 0; tt < ntile; ++tt) {
+      for (int it = it0; ok && it < nit; it += itstep) {
+        int local;
+        const TcArgs &A = item_args(Lp, it, local);
+        const Item I = decode_item(A, local);
+        const TcChunk &CH = I.CH;
+        const int A0 = I.A0, B0 = I.B0, p0 = I.p0, p1 = I.p1;
+        const uint32_t tbytes = I.sc * 32u;
+        tma_prefetch_desc(&A.tmA);
+        tma_prefetch_desc(&A.tmB);
+        tma_prefetch_desc(&A.tmTp);
+        tma_prefetch_desc(&A.tmTm);
+        for (int p = p0; ok && p <= p1; ++p) {
+          if (p < p1) {
+            int k, l;
+            pair_of(p, k, l);
+            const int ntile = (k == l) ? 1 : 2;
+            for (int ks = 0; ok && ks < A.nks; ++ks)
+              for (int tt = 0; tt < ntile; ++tt) {
+                if (!(ok = mbar_wait(bars.empty(stage), phase ^ 1u, wd, kSiteTmaEmpty))) break;
+                const uint32_t dst = ring + (uint32_t)stage * C::kStage;
+                mbar_arrive_expect_tx(bars.full(stage), (uint32_t)S * (A_TILE + B_TILE));
+                armed |= 1u << stage;
+                armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+                const int ca = (tt == 0 ? k : l) * CB, cb = (tt == 0 ? l : k) * CB;
+  #pragma unroll
+                for (int s = 0; s < S; ++s) {
+                  tma_load_3d(dst + s * A_TILE, &A.tmA, bars.full(stage), ks * KSTEP, ca, s * A.vp + A0);
+                  tma_load_3d(dst + S * A_TILE + s * B_TILE, &A.tmB, bars.full(stage), ks * KSTEP, cb,
+                              s * A.vp + B0);
+                }
+                if (++stage == C::kStages) {
+                  stage = 0;
+                  phase ^= 1u;
+                }
+              }
+          }
+          if (ok && p > p0) {
+            for (int piece = 0; piece < SLOTS / TPIECE; ++piece) {
               if (!(ok = mbar_wait(bars.empty(stage), phase ^ 1u, wd, kSiteTmaEmpty))) break;
               const uint32_t dst = ring + (uint32_t)stage * C::kStage;
-              mbar_arrive_expect_tx(bars.full(stage), (uint32_t)S * (A_TILE + B_TILE));
+              mbar_arrive_expect_tx(bars.full(stage), (uint32_t)S * tbytes);
               armed |= 1u << stage;
               armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
-              const int ca = (tt == 0 ? k : l) * CB, cb = (tt == 0 ? l : k) * CB;
-#pragma unroll
+              const int x = (p - 1) * SLOTS + piece * TPIECE;
+  #pragma unroll
               for (int s = 0; s < S; ++s) {
-                tma_load_3d(dst + s * A_TILE, &A.tmA, bars.full(stage), ks * KSTEP, ca, s * A.vp + A0);
-                tma_load_3d(dst + S * A_TILE + s * B_TILE, &A.tmB, bars.full(stage), ks * KSTEP, cb,
-                            s * A.vp + B0);
+                for (int r = 0; r < CH.nps; r += 16)
+                  tma_load_3d(dst + s * tbytes + r * 32, &A.tmTp, bars.full(stage), x, CH.lp0 + r, s);
+                for (int r = 0; r < CH.nms; r += 16)
+                  tma_load_3d(dst + s * tbytes + (CH.nps + r) * 32, &A.tmTm, bars.full(stage), x,
+                              CH.lm0 + r, s);
               }
               if (++stage == C::kStages) {
                 stage = 0;
                 phase ^= 1u;
               }
             }
-        }
-        if (ok && p > p0) {
-          for (int piece = 0; piece < SLOTS / TPIECE; ++piece) {
-            if (!(ok = mbar_wait(bars.empty(stage), phase ^ 1u, wd, kSiteTmaEmpty))) break;
-            const uint32_t dst = ring + (uint32_t)stage * C::kStage;
-            mbar_arrive_expect_tx(bars.full(stage), (uint32_t)S * tbytes);
-            armed |= 1u << stage;
-            armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
-            const int x = (p - 1) * SLOTS + piece * TPIECE;
-#pragma unroll
-            for (int s = 0; s < S; ++s) {
-              for (int r = 0; r < CH.nps; r += 16)
-                tma_load_3d(dst + s * tbytes + r * 32, &A.tmTp, bars.full(stage), x, CH.lp0 + r, s);
-              for (int r = 0; r < CH.nms; r += 16)
-                tma_load_3d(dst + s * tbytes + (CH.nps + r) * 32, &A.tmTm, bars.full(stage), x,
-                            CH.lm0 + r, s);
-            }
-            if (++stage == C::kStages) {
-              stage = 0;
-              phase ^= 1u;
-            }
           }
         }
       }
       if (!ok) {
         // let the copies already issued land before the CTA leaves
-        DrainWatch dw(A.status, A.timeout_ns);
+        DrainWatch dw(A0args.status, Lp.timeout_ns);
         for (int s = 0; s < C::kStages; ++s)
           if (armed & (1u << s)) mbar_wait(bars.full(s), (armed_par >> s) & 1u, dw.wd, kSiteTmaFull);
       }
@@ -282,95 +308,106 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
       uint32_t phase = 0;
       uint32_t g = 0, v_use = 0, s_use = 0;  // chains issued, V tiles and S tiles consumed
       const uint32_t id1 = idesc_bf16(128, 64);
-      const uint32_t idp = idesc_bf16(128, CH.nps > 0 ? CH.nps : 16);
-      const uint32_t idm = idesc_bf16(128, CH.nms > 0 ? CH.nms : 16);
-      const uint32_t tbytes = sc * 32u;
       const uint32_t hi64 = desc_hi(512, kSwizzle64), hi128 = desc_hi(1024, kSwizzle128),
                      hi32 = desc_hi(256, kSwizzle32);
       bool ok = true;
-      for (int p = p0; ok && p <= p1; ++p) {
-        if (p < p1) {
-          int k, l;
-          pair_of(p, k, l);
-          const int ntile = (k == l) ? 1 : 2;
-          for (int c = 0; ok && c < nch_full; ++c) {
-            const int buf = (int)(g % nbuf);
-            if (!(ok = mbar_wait(bars.cfree(buf), ((g / nbuf) & 1u) ^ 1u, wd, kSiteXYFree))) break;
-            tc_fence_after();
-            const int ks0 = c * kc, ks1 = min(A.nks, ks0 + kc);
-            for (int ks = ks0; ok && ks < ks1; ++ks)
-              for (int tt = 0; tt < ntile; ++tt) {
-                if (!(ok = mbar_wait(bars.full(stage), phase, wd, kSiteTmaFull))) break;
-                tc_fence_after();
-                const uint32_t st = ring + (uint32_t)stage * C::kStage;
-                const uint32_t dT = tmem + (split ? 0u : (uint32_t)buf * 128u) + (tt ? 64u : 0u);
-#pragma unroll
-                for (int kk = 0; kk < KSTEP / 16; ++kk)
-#pragma unroll
-                  for (int q = 0; q < C::kProducts; ++q) {
-                    const uint64_t ad = desc64(st + kPa(q) * A_TILE + kk * 32, hi64);
-                    const uint64_t bd = desc64(st + S * A_TILE + kPb(q) * B_TILE + kk * 32, hi64);
-                    // split: the hi*hi product into the "big" accumulator,
-                    // every smaller product into the "small" one (128 columns on)
-                    const bool small = split && q > 0;
-                    const bool first = (ks == ks0) && kk == 0 && (split ? (q <= 1) : (q == 0));
-                    mma_bf16(dT + (small ? 128u : 0u), ad, bd, id1, first ? 0u : 1u);
+      for (int it = it0; ok && it < nit; it += itstep) {
+        int local;
+        const TcArgs &A = item_args(Lp, it, local);
+        const Item I = decode_item(A, local);
+        const TcChunk &CH = I.CH;
+        const int p0 = I.p0, p1 = I.p1;
+        const uint32_t idp = idesc_bf16(128, CH.nps > 0 ? CH.nps : 16);
+        const uint32_t idm = idesc_bf16(128, CH.nms > 0 ? CH.nms : 16);
+        const uint32_t tbytes = I.sc * 32u;
+        const int kc = A.kc;
+        const int nch_full = (A.nks + kc - 1) / kc;
+        const bool split = A.xy_split != 0;
+        const uint32_t nbuf = split ? 1u : 2u;
+        for (int p = p0; ok && p <= p1; ++p) {
+          if (p < p1) {
+            int k, l;
+            pair_of(p, k, l);
+            const int ntile = (k == l) ? 1 : 2;
+            for (int c = 0; ok && c < nch_full; ++c) {
+              const int buf = (int)(g % nbuf);
+              if (!(ok = mbar_wait(bars.cfree(buf), ((g / nbuf) & 1u) ^ 1u, wd, kSiteXYFree))) break;
+              tc_fence_after();
+              const int ks0 = c * kc, ks1 = min(A.nks, ks0 + kc);
+              for (int ks = ks0; ok && ks < ks1; ++ks)
+                for (int tt = 0; tt < ntile; ++tt) {
+                  if (!(ok = mbar_wait(bars.full(stage), phase, wd, kSiteTmaFull))) break;
+                  tc_fence_after();
+                  const uint32_t st = ring + (uint32_t)stage * C::kStage;
+                  const uint32_t dT = tmem + (split ? 0u : (uint32_t)buf * 128u) + (tt ? 64u : 0u);
+  #pragma unroll
+                  for (int kk = 0; kk < KSTEP / 16; ++kk)
+  #pragma unroll
+                    for (int q = 0; q < C::kProducts; ++q) {
+                      const uint64_t ad = desc64(st + kPa(q) * A_TILE + kk * 32, hi64);
+                      const uint64_t bd = desc64(st + S * A_TILE + kPb(q) * B_TILE + kk * 32, hi64);
+                      // split: the hi*hi product into the "big" accumulator,
+                      // every smaller product into the "small" one (128 columns on)
+                      const bool small = split && q > 0;
+                      const bool first = (ks == ks0) && kk == 0 && (split ? (q <= 1) : (q == 0));
+                      mma_bf16(dT + (small ? 128u : 0u), ad, bd, id1, first ? 0u : 1u);
+                    }
+                  mma_commit(bars.empty(stage));
+                  if (++stage == C::kStages) {
+                    stage = 0;
+                    phase ^= 1u;
                   }
-                mma_commit(bars.empty(stage));
-                if (++stage == C::kStages) {
-                  stage = 0;
-                  phase ^= 1u;
+                }
+              if (!ok) break;
+              mma_commit(bars.cfull(buf));
+              ++g;
+            }
+            if (!ok) break;
+          }
+          if (p > p0) {
+            if (!(ok = mbar_wait(bars.v_full(), v_use & 1u, wd, kSiteVFull))) break;
+            tc_fence_after();
+            for (int piece = 0; ok && piece < SLOTS / TPIECE; ++piece) {
+              const bool first = (piece % A.s_pieces) == 0;
+              if (first) {
+                // a fresh S accumulator: the previous one has been taken
+                if (!(ok = mbar_wait(bars.s_free(), (s_use & 1u) ^ 1u, wd, kSiteRFree))) break;
+                tc_fence_after();
+              }
+              if (!(ok = mbar_wait(bars.full(stage), phase, wd, kSiteTmaFull))) break;
+              tc_fence_after();
+              const uint32_t st = ring + (uint32_t)stage * C::kStage;
+  #pragma unroll
+              for (int q = 0; q < C::kProducts; ++q) {
+                const uint32_t acc = (first && q == 0) ? 0u : 1u;
+                const uint64_t ap = desc64(vbase + (0 * S + kPa(q)) * V_TILE + piece * 32, hi128);
+                const uint64_t bp = desc64(st + kPb(q) * tbytes, hi32);
+                mma_bf16(tmem + kColS, ap, bp, idp, acc);
+                if (CH.nms > 0) {
+                  const uint64_t am = desc64(vbase + (1 * S + kPa(q)) * V_TILE + piece * 32, hi128);
+                  const uint64_t bm = desc64(st + kPb(q) * tbytes + CH.nps * 32, hi32);
+                  mma_bf16(tmem + kColS + CH.nps, am, bm, idm, acc);
                 }
               }
-            if (!ok) break;
-            mma_commit(bars.cfull(buf));
-            ++g;
-          }
-          if (!ok) break;
-        }
-        if (p > p0) {
-          if (!(ok = mbar_wait(bars.v_full(), v_use & 1u, wd, kSiteVFull))) break;
-          tc_fence_after();
-          for (int piece = 0; ok && piece < SLOTS / TPIECE; ++piece) {
-            const bool first = (piece % A.s_pieces) == 0;
-            if (first) {
-              // a fresh S accumulator: the previous one has been taken
-              if (!(ok = mbar_wait(bars.s_free(), (s_use & 1u) ^ 1u, wd, kSiteRFree))) break;
-              tc_fence_after();
-            }
-            if (!(ok = mbar_wait(bars.full(stage), phase, wd, kSiteTmaFull))) break;
-            tc_fence_after();
-            const uint32_t st = ring + (uint32_t)stage * C::kStage;
-#pragma unroll
-            for (int q = 0; q < C::kProducts; ++q) {
-              const uint32_t acc = (first && q == 0) ? 0u : 1u;
-              const uint64_t ap = desc64(vbase + (0 * S + kPa(q)) * V_TILE + piece * 32, hi128);
-              const uint64_t bp = desc64(st + kPb(q) * tbytes, hi32);
-              mma_bf16(tmem + kColS, ap, bp, idp, acc);
-              if (CH.nms > 0) {
-                const uint64_t am = desc64(vbase + (1 * S + kPa(q)) * V_TILE + piece * 32, hi128);
-                const uint64_t bm = desc64(st + kPb(q) * tbytes + CH.nps * 32, hi32);
-                mma_bf16(tmem + kColS + CH.nps, am, bm, idm, acc);
+              mma_commit(bars.empty(stage));
+              if (++stage == C::kStages) {
+                stage = 0;
+                phase ^= 1u;
+              }
+              if ((piece + 1) % A.s_pieces == 0) {
+                mma_commit(bars.s_full());
+                ++s_use;
               }
             }
-            mma_commit(bars.empty(stage));
-            if (++stage == C::kStages) {
-              stage = 0;
-              phase ^= 1u;
-            }
-            if ((piece + 1) % A.s_pieces == 0) {
-              mma_commit(bars.s_full());
-              ++s_use;
-            }
+            if (!ok) break;
+            mma_commit(bars.v_free());
+            ++v_use;
           }
-          if (!ok) break;
-          mma_commit(bars.v_free());
-          ++v_use;
         }
       }
       // every MMA of this CTA completes before TMEM is released
       mma_commit(bars.done());
-      DrainWatch dw(A.status, A.timeout_ns);
+      DrainWatch dw(A0args.status, Lp.timeout_ns);
       mbar_wait(bars.done(), 0, dw.wd, kSiteRFull);
     }
   } else {
@@ -381,130 +418,141 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
     const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
     const int a_l = L >> 3, x_l = L & 7;
     uint32_t g = 0, v_use = 0, s_use = 0;
-    int nacc = 0, nflush = 0;
     bool ok = true;
-
-    // S (fresh GEMM2 result of one block pair) -> R (TMEM running sum, FP32)
-    auto take_S = [&]() -> bool {
-      if (!mbar_wait(bars.s_full(), s_use & 1u, wd, kSiteRFull)) return false;
-      ++s_use;
-      tc_fence_after();
-      for (uint32_t c0 = 16u * half; c0 < sc; c0 += 32) {
-        float s[16], r[16];
-        tmem_ld16(tl + kColS + c0, s);
-        if (nacc > 0) tmem_ld16(tl + kColS + sc + c0, r);
-        tmem_ld_wait();
-        if (nacc > 0) {
-#pragma unroll
-          for (int u = 0; u < 16; ++u) s[u] += r[u];
-        }
-        tmem_st16(tl + kColS + sc + c0, s);
-      }
-      tmem_st_wait();
-      tc_fence_before();
-      mbar_arrive(bars.s_free());
-      ++nacc;
-      return true;
-    };
-    // R (FP32, TMEM) -> FP64 accumulator in the workspace, [col][lane]
-    auto flush_R = [&]() {
-      for (uint32_t c0 = 16u * half; c0 < sc; c0 += 32) {
-        float r[16];
-        tmem_ld16(tl + kColS + sc + c0, r);
-        tmem_ld_wait();
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          double *dst = racc + (size_t)(c0 + u) * 128 + L;
-          *dst = (nflush ? *dst : 0.0) + (double)r[u];
-        }
-      }
-      ++nflush;
-      nacc = 0;
-    };
-
-    for (int p = p0; p < p1; ++p) {
-      int k, l;
-      pair_of(p, k, l);
-      const bool diag = (k == l);
-      float X[32], Y[32];  // columns (b, 0..7) for b in [4*half, 4*half+4)
-      for (int c = 0; c < nch_full; ++c) {
-        const int buf = (int)(g % nbuf);
-        if (!(ok = mbar_wait(bars.cfull(buf), (g / nbuf) & 1u, wd, kSiteXYFull))) break;
-        ++g;
+    for (int it = it0; ok && it < nit; it += itstep) {
+      int local;
+      const TcArgs &A = item_args(Lp, it, local);
+      const Item I = decode_item(A, local);
+      const int p0 = I.p0, p1 = I.p1;
+      const uint32_t sc = I.sc;
+      double *racc = I.racc;
+      const int kc = A.kc;
+      const int nch_full = (A.nks + kc - 1) / kc;
+      const bool split = A.xy_split != 0;
+      const uint32_t nbuf = split ? 1u : 2u;
+      int nacc = 0, nflush = 0;
+      // S (fresh GEMM2 result of one block pair) -> R (TMEM running sum, FP32)
+      auto take_S = [&]() -> bool {
+        if (!mbar_wait(bars.s_full(), s_use & 1u, wd, kSiteRFull)) return false;
+        ++s_use;
         tc_fence_after();
-        const uint32_t cX = tl + (split ? 0u : (uint32_t)buf * 128u) + 32u * half;
-        const uint32_t cY = diag ? cX : cX + 64u;
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          float tx[16], ty[16];
-          tmem_ld16(cX + q * 16, tx);
-          tmem_ld16(cY + q * 16, ty);
-          if (split) {
-            float sx[16], sy[16];
-            tmem_ld16(cX + 128u + q * 16, sx);
-            tmem_ld16(cY + 128u + q * 16, sy);
-            tmem_ld_wait();
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              tx[i] += sx[i];
-              ty[i] += sy[i];
-            }
-          } else {
-            tmem_ld_wait();
+        for (uint32_t c0 = 16u * half; c0 < sc; c0 += 32) {
+          float s[16], r[16];
+          tmem_ld16(tl + kColS + c0, s);
+          if (nacc > 0) tmem_ld16(tl + kColS + sc + c0, r);
+          tmem_ld_wait();
+          if (nacc > 0) {
+  #pragma unroll
+            for (int u = 0; u < 16; ++u) s[u] += r[u];
           }
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            X[q * 16 + i] = c ? X[q * 16 + i] + tx[i] : tx[i];
-            Y[q * 16 + i] = c ? Y[q * 16 + i] + ty[i] : ty[i];
+          tmem_st16(tl + kColS + sc + c0, s);
+        }
+        tmem_st_wait();
+        tc_fence_before();
+        mbar_arrive(bars.s_free());
+        ++nacc;
+        return true;
+      };
+      // R (FP32, TMEM) -> FP64 accumulator in the workspace, [col][lane]
+      auto flush_R = [&]() {
+        for (uint32_t c0 = 16u * half; c0 < sc; c0 += 32) {
+          float r[16];
+          tmem_ld16(tl + kColS + sc + c0, r);
+          tmem_ld_wait();
+  #pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            double *dst = racc + (size_t)(c0 + u) * 128 + L;
+            *dst = (nflush ? *dst : 0.0) + (double)r[u];
           }
         }
-        tc_fence_before();
-        mbar_arrive(bars.cfree(buf));
-      }
-      if (!ok) break;
-      // S chains of the previous block pair (GEMM2 runs after this pair's GEMM1)
-      if (p > p0) {
-        for (int gs = 0; ok && gs < SLOTS / TPIECE / A.s_pieces; ++gs) {
-          ok = take_S();
-          if (ok && nacc >= A.flush_every) flush_R();
+        ++nflush;
+        nacc = 0;
+      };
+
+      for (int p = p0; p < p1; ++p) {
+        int k, l;
+        pair_of(p, k, l);
+        const bool diag = (k == l);
+        float X[32], Y[32];  // columns (b, 0..7) for b in [4*half, 4*half+4)
+        for (int c = 0; c < nch_full; ++c) {
+          const int buf = (int)(g % nbuf);
+          if (!(ok = mbar_wait(bars.cfull(buf), (g / nbuf) & 1u, wd, kSiteXYFull))) break;
+          ++g;
+          tc_fence_after();
+          const uint32_t cX = tl + (split ? 0u : (uint32_t)buf * 128u) + 32u * half;
+          const uint32_t cY = diag ? cX : cX + 64u;
+  #pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            float tx[16], ty[16];
+            tmem_ld16(cX + q * 16, tx);
+            tmem_ld16(cY + q * 16, ty);
+            if (split) {
+              float sx[16], sy[16];
+              tmem_ld16(cX + 128u + q * 16, sx);
+              tmem_ld16(cY + 128u + q * 16, sy);
+              tmem_ld_wait();
+  #pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                tx[i] += sx[i];
+                ty[i] += sy[i];
+              }
+            } else {
+              tmem_ld_wait();
+            }
+  #pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              X[q * 16 + i] = c ? X[q * 16 + i] + tx[i] : tx[i];
+              Y[q * 16 + i] = c ? Y[q * 16 + i] + ty[i] : ty[i];
+            }
+          }
+          tc_fence_before();
+          mbar_arrive(bars.cfree(buf));
         }
         if (!ok) break;
-      }
-      // Y row of lane (a, d=x_l) holds (ad|bc) at column (b, c); after the
-      // transpose lane (a, c=x_l) holds (ad|bc) at index (b, d).
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        float r[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) r[j] = Y[b * 8 + j];
-        transpose8(r, x_l);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) Y[b * 8 + j] = r[j];
-      }
-      if (!(ok = mbar_wait(bars.v_free(), (v_use & 1u) ^ 1u, wd, kSiteVFree))) break;
-      ++v_use;
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int row = a_l * 8 + 4 * half + b;
-        const uint32_t off = (uint32_t)row * 128u + (uint32_t)((x_l ^ (row & 7)) * 16);
-#pragma unroll
-        for (int sg = 0; sg < 2; ++sg) {
-          float rem[8];
-#pragma unroll
-          for (int d = 0; d < 8; ++d) rem[d] = sg ? X[b * 8 + d] - Y[b * 8 + d] : X[b * 8 + d] + Y[b * 8 + d];
-#pragma unroll
-          for (int s = 0; s < S; ++s) {
-            const uint4 w = pack_slice(rem);
-            *reinterpret_cast<uint4 *>(smem + C::kRing + (uint32_t)(sg * S + s) * V_TILE + off) = w;
+        // S chains of the previous block pair (GEMM2 runs after this pair's GEMM1)
+        if (p > p0) {
+          for (int gs = 0; ok && gs < SLOTS / TPIECE / A.s_pieces; ++gs) {
+            ok = take_S();
+            if (ok && nacc >= A.flush_every) flush_R();
+          }
+          if (!ok) break;
+        }
+        // Y row of lane (a, d=x_l) holds (ad|bc) at column (b, c); after the
+        // transpose lane (a, c=x_l) holds (ad|bc) at index (b, d).
+  #pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          float r[8];
+  #pragma unroll
+          for (int j = 0; j < 8; ++j) r[j] = Y[b * 8 + j];
+          transpose8(r, x_l);
+  #pragma unroll
+          for (int j = 0; j < 8; ++j) Y[b * 8 + j] = r[j];
+        }
+        if (!(ok = mbar_wait(bars.v_free(), (v_use & 1u) ^ 1u, wd, kSiteVFree))) break;
+        ++v_use;
+  #pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int row = a_l * 8 + 4 * half + b;
+          const uint32_t off = (uint32_t)row * 128u + (uint32_t)((x_l ^ (row & 7)) * 16);
+  #pragma unroll
+          for (int sg = 0; sg < 2; ++sg) {
+            float rem[8];
+  #pragma unroll
+            for (int d = 0; d < 8; ++d) rem[d] = sg ? X[b * 8 + d] - Y[b * 8 + d] : X[b * 8 + d] + Y[b * 8 + d];
+  #pragma unroll
+            for (int s = 0; s < S; ++s) {
+              const uint4 w = pack_slice(rem);
+              *reinterpret_cast<uint4 *>(smem + C::kRing + (uint32_t)(sg * S + s) * V_TILE + off) = w;
+            }
           }
         }
+        fence_async_smem();
+        mbar_arrive(bars.v_full());
       }
-      fence_async_smem();
-      mbar_arrive(bars.v_full());
+      // S chains of the last block pair, then the final FP64 flush
+      for (int gs = 0; ok && gs < SLOTS / TPIECE / A.s_pieces; ++gs) ok = take_S();
+      if (ok) flush_R();
     }
-    // S chains of the last block pair, then the final FP64 flush
-    for (int gs = 0; ok && gs < SLOTS / TPIECE / A.s_pieces; ++gs) ok = take_S();
-    if (ok) flush_R();
   }
 
   // ---- teardown: all roles done (or given up); release TMEM
@@ -521,8 +569,10 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
 // (tile, chunk): lane = ab slot (a = A0 + lane/8, b = B0 + lane%8),
 //   R_ij^ab = R+ + R-, R_ij^ba = R+ - R-, R_ji^ba = R_ij^ab, R_ji^ab = R_ij^ba,
 // with R- = 0 when i = j or a = b.  Every element of R is written once.
-__global__ void __launch_bounds__(128) unpack_kernel(const __grid_constant__ TcArgs A) {
-  const int tc = blockIdx.x;
+__global__ void __launch_bounds__(128) unpack_kernel(const __grid_constant__ TcLaunch Lp) {
+  int tc;
+  const TcArgs &A = Lp.mols ? Lp.mols[Lp.tcs[blockIdx.x].x] : Lp.one;
+  tc = Lp.mols ? Lp.tcs[blockIdx.x].y : (int)blockIdx.x;
   const int tile = tc / A.nchunks, ch = tc % A.nchunks;
   int iA = 0, t = tile;
   while (t >= A.nB8 - 2 * iA) {
@@ -564,24 +614,24 @@ uint32_t tc_smem_bytes(int nslices) {
   return nslices == 2 ? Cfg<2>::kSmem : Cfg<3>::kSmem;
 }
 
-cudaError_t launch_ladder_tc(const TcArgs &a, int nslices, int grid, cudaStream_t s) {
-  cudaError_t e;
-  if (nslices == 2) {
-    e = cudaFuncSetAttribute(ladder_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Cfg<2>::kSmem);
-    if (e != cudaSuccess) return e;
+cudaError_t tc_init_attributes(int nslices) {
+  if (nslices == 2)
+    return cudaFuncSetAttribute(ladder_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Cfg<2>::kSmem);
+  return cudaFuncSetAttribute(ladder_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Cfg<3>::kSmem);
+}
+
+cudaError_t launch_ladder_tc(const TcLaunch &a, int nslices, int grid, cudaStream_t s) {
+  if (nslices == 2)
     ladder_tc_kernel<2><<<grid, kThreads, Cfg<2>::kSmem, s>>>(a);
-  } else {
-    e = cudaFuncSetAttribute(ladder_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Cfg<3>::kSmem);
-    if (e != cudaSuccess) return e;
+  else
     ladder_tc_kernel<3><<<grid, kThreads, Cfg<3>::kSmem, s>>>(a);
-  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_unpack(const TcArgs &a, cudaStream_t s) {
-  unpack_kernel<<<a.ntiles * a.nchunks, 128, 0, s>>>(a);
+cudaError_t launch_unpack(const TcLaunch &a, int nblocks, cudaStream_t s) {
+  unpack_kernel<<<nblocks, 128, 0, s>>>(a);
   return cudaGetLastError();
 }
 
