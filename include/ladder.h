@@ -69,6 +69,24 @@ typedef enum {
  * The plan owns no device memory; see ladder_workspace_size. */
 ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out);
 
+/* Launch parameters of the split-BF16 kernel (ignored by LADDER_FP64):
+ *   kc          GEMM1 K-steps (32 auxiliary functions each) per FP32
+ *               accumulation chain, >= 1;
+ *   s_pieces    16-slot GEMM2 pieces per fresh FP32 accumulator: 1, 2 or 4;
+ *   flush_every FP32 accumulators summed before an FP64 flush, >= 1;
+ *   ksplit      block-pair ranges per work unit (more CTAs for small shapes), >= 1;
+ *   xy_split    1: separate GEMM1 accumulators for the hi*hi slice product and
+ *               the smaller products; 0: one accumulator, two buffers.
+ * Longer chains are faster and less accurate (the tensor core's FP32
+ * accumulation error grows with the MMAs per accumulator).  ladder_set_tuning
+ * must come before ladder_set_workspace (the workspace size depends on
+ * ksplit); it returns LADDER_EINVAL for out-of-range values. */
+typedef struct {
+    int kc, s_pieces, flush_every, ksplit, xy_split;
+} ladder_tuning;
+ladder_status ladder_get_tuning(ladder_plan_t plan, ladder_tuning *t);
+ladder_status ladder_set_tuning(ladder_plan_t plan, const ladder_tuning *t);
+
 /* Mode the plan resolved to (LADDER_AUTO resolves at plan time). */
 ladder_status ladder_plan_mode(ladder_plan_t plan, int *mode);
 
@@ -154,6 +172,13 @@ ladder_status ladder_apply_batched(ladder_plan_t plan, const double *const *B,
  * Returns LADDER_OK or LADDER_ETIMEOUT; *where receives the site code of the
  * first failed wait (0 if none) when where != NULL. */
 ladder_status ladder_last_device_error(ladder_plan_t plan, void *stream, int *where);
+
+/* Self-test of the device-side failure detection: one kernel waits, with the
+ * same bounded wait every pipelined kernel of the library uses, on a barrier
+ * that nothing ever signals.  After timeout_ns the wait gives up, records site
+ * code 99 in the plan's status word and the kernel returns, leaving the
+ * context usable; ladder_last_device_error then reports LADDER_ETIMEOUT. */
+ladder_status ladder_selftest_wait(ladder_plan_t plan, unsigned long long timeout_ns, void *stream);
 
 /* Stage timing of ladder_apply.  With timing on, ladder_apply records CUDA
  * events on its stream around its three stages (operand preparation: slicing

@@ -25,11 +25,20 @@ STATUS = {0: "LADDER_OK", 1: "LADDER_EINVAL", 2: "LADDER_ENOMEM", 3: "LADDER_ECU
           4: "LADDER_ETIMEOUT", 5: "LADDER_ENOTSUP", 6: "LADDER_EWORKSPACE"}
 
 # every entry point that include/ladder.h declares
-EXPORTS = ("ladder_plan", "ladder_plan_mode", "ladder_workspace_size", "ladder_set_workspace",
+EXPORTS = ("ladder_plan", "ladder_plan_mode", "ladder_get_tuning", "ladder_set_tuning", "ladder_workspace_size", "ladder_set_workspace",
            "ladder_tau", "ladder_apply", "ladder_energy", "ladder_energy_noalloc", "ladder_backward", "ladder_pair_combine", "ladder_apply_host",
-           "ladder_plan_batched", "ladder_apply_batched", "ladder_last_device_error",
+           "ladder_plan_batched", "ladder_apply_batched", "ladder_last_device_error", "ladder_selftest_wait",
            "ladder_set_timing", "ladder_timing", "ladder_flops", "ladder_status_string",
            "ladder_destroy")
+
+
+class Tuning(ctypes.Structure):
+    """Mirror of ladder_tuning (include/ladder.h)."""
+    _fields_ = [("kc", ctypes.c_int), ("s_pieces", ctypes.c_int), ("flush_every", ctypes.c_int),
+                ("ksplit", ctypes.c_int), ("xy_split", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class LadderError(RuntimeError):
@@ -55,6 +64,8 @@ def load_library(path: str = LIB_PATH):
     sig = {
         "ladder_plan": [i, i, i, i, pp],
         "ladder_plan_mode": [_P, ip],
+        "ladder_get_tuning": [_P, ctypes.POINTER(Tuning)],
+        "ladder_set_tuning": [_P, ctypes.POINTER(Tuning)],
         "ladder_workspace_size": [_P, ctypes.POINTER(sz)],
         "ladder_set_workspace": [_P, _P, sz],
         "ladder_tau": [_P, _P, _P, _P, _P],
@@ -67,6 +78,7 @@ def load_library(path: str = LIB_PATH):
         "ladder_plan_batched": [i, ip, ip, ip, i, pp],
         "ladder_apply_batched": [_P, pp, pp, pp, _P],
         "ladder_last_device_error": [_P, _P, ip],
+        "ladder_selftest_wait": [_P, ctypes.c_ulonglong, _P],
         "ladder_set_timing": [_P, i],
         "ladder_timing": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
                           ctypes.POINTER(ctypes.c_float)],
@@ -113,6 +125,16 @@ def ladder_plan_mode(plan) -> int:
     m = ctypes.c_int()
     _check("ladder_plan_mode", load_library().ladder_plan_mode(plan, ctypes.byref(m)))
     return m.value
+
+
+def ladder_get_tuning(plan) -> Tuning:
+    t = Tuning()
+    _check("ladder_get_tuning", load_library().ladder_get_tuning(plan, ctypes.byref(t)))
+    return t
+
+
+def ladder_set_tuning(plan, t: Tuning) -> None:
+    _check("ladder_set_tuning", load_library().ladder_set_tuning(plan, ctypes.byref(t)))
 
 
 def ladder_workspace_size(plan) -> int:
@@ -194,6 +216,11 @@ def ladder_timing(plan):
     return tuple(x.value for x in t)
 
 
+def ladder_selftest_wait(plan, timeout_ns: int, stream=None) -> None:
+    _check("ladder_selftest_wait", load_library().ladder_selftest_wait(plan, int(timeout_ns),
+                                                                      _stream(stream)))
+
+
 def ladder_status_string(status: int) -> str:
     return load_library().ladder_status_string(int(status)).decode()
 
@@ -210,9 +237,16 @@ def ladder_destroy(plan) -> None:
 class Ladder:
     """A plan plus its workspace (a torch uint8 tensor on the current device)."""
 
-    def __init__(self, o: int, v: int, naux: int, mode="bf16x6", device=None, backward=False):
+    def __init__(self, o: int, v: int, naux: int, mode="bf16x6", device=None, backward=False,
+                 tuning=None):
+        """mode: "fp64", "bf16x3", "bf16x6", or "tuned" (the autotuner's cached
+        choice of mode and launch parameters for this shape, see tune.py);
+        tuning: a dict of ladder_tuning fields to override."""
         import torch
         self.o, self.v, self.naux = o, v, naux
+        if mode == "tuned":
+            from .tune import lookup
+            mode, tuning = lookup(o, v, naux)
         m = MODES[mode] if isinstance(mode, str) else int(mode)
         if backward:
             m |= LADDER_WITH_BACKWARD
@@ -220,6 +254,11 @@ class Ladder:
         with torch.cuda.device(self.device):
             self.plan = ladder_plan(o, v, naux, m)
             self.mode = ladder_plan_mode(self.plan)
+            if tuning and self.mode != LADDER_FP64:
+                t = ladder_get_tuning(self.plan)
+                for k, val in tuning.items():
+                    setattr(t, k, int(val))
+                ladder_set_tuning(self.plan, t)
             n = ladder_workspace_size(self.plan)
             self.workspace = torch.empty(max(n, 256), dtype=torch.uint8, device=self.device)
             ladder_set_workspace(self.plan, self.workspace)
@@ -256,8 +295,8 @@ class Ladder:
     def backward(self, B, tau, W, dtau=True, dB=True):
         """(dtau, dB) of E = sum W R; pass False to skip one."""
         import torch
-        dt = torch.empty_like(tau) if dtau is True else (dtau or None)
-        db = torch.empty_like(B) if dB is True else (dB or None)
+        dt = torch.empty_like(tau) if dtau is True else (None if dtau is False else dtau)
+        db = torch.empty_like(B) if dB is True else (None if dB is False else dB)
         ladder_backward(self.plan, B, tau, W, dt, db)
         return dt, db
 

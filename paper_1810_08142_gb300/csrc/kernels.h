@@ -99,5 +99,7 @@ uint32_t tc_smem_bytes(int nslices);
 cudaError_t tc_init_attributes(int nslices);  // once per device, outside stream capture
 cudaError_t launch_ladder_tc(const TcLaunch &a, int nslices, int grid, cudaStream_t s);
 cudaError_t launch_unpack(const TcLaunch &a, int nblocks, cudaStream_t s);
+cudaError_t launch_selftest_wait(int *status, unsigned long long timeout_ns, int site,
+                                 cudaStream_t s);
 
 }  // namespace ladder

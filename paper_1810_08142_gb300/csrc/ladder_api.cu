@@ -293,6 +293,32 @@ ladder_status ladder_plan_mode(ladder_plan_t pl, int *mode) {
   return LADDER_OK;
 }
 
+ladder_status ladder_get_tuning(ladder_plan_t pl, ladder_tuning *t) {
+  if (!pl || !t || pl->batched) return LADDER_EINVAL;
+  t->kc = pl->kc;
+  t->s_pieces = pl->s_pieces;
+  t->flush_every = pl->flush_every;
+  t->ksplit = pl->ksplit;
+  t->xy_split = pl->xy_split;
+  return LADDER_OK;
+}
+
+ladder_status ladder_set_tuning(ladder_plan_t pl, const ladder_tuning *t) {
+  if (!pl || !t || pl->batched || pl->ws) return LADDER_EINVAL;
+  if (pl->mode == LADDER_FP64) return LADDER_OK;
+  if (t->kc < 1 || t->kc > 64 || !(t->s_pieces == 1 || t->s_pieces == 2 || t->s_pieces == 4) ||
+      t->flush_every < 1 || t->flush_every > 4096 || t->ksplit < 1 || t->ksplit > pl->nbp ||
+      (t->xy_split != 0 && t->xy_split != 1))
+    return LADDER_EINVAL;
+  pl->kc = t->kc;
+  pl->s_pieces = t->s_pieces;
+  pl->flush_every = t->flush_every;
+  pl->ksplit = t->ksplit;
+  pl->xy_split = t->xy_split;
+  compute_layout(pl);
+  return LADDER_OK;
+}
+
 ladder_status ladder_workspace_size(ladder_plan_t pl, size_t *bytes) {
   if (!pl || !bytes) return LADDER_EINVAL;
   *bytes = pl->lay.total;
@@ -680,6 +706,14 @@ ladder_status ladder_last_device_error(ladder_plan_t pl, void *stream, int *wher
     return cuda_status(cudaErrorUnknown);
   if (where) *where = h;
   return h == 0 ? LADDER_OK : LADDER_ETIMEOUT;
+}
+
+ladder_status ladder_selftest_wait(ladder_plan_t pl, unsigned long long timeout_ns, void *stream) {
+  if (!pl) return LADDER_EINVAL;
+  if (!pl->ws) return LADDER_EWORKSPACE;
+  if (timeout_ns < 1000000ull || timeout_ns > 10000000000ull) return LADDER_EINVAL;
+  return cuda_status(launch_selftest_wait(ws_at<int>(pl, pl->lay.status), timeout_ns, 99,
+                                          static_cast<cudaStream_t>(stream)));
 }
 
 ladder_status ladder_set_timing(ladder_plan_t pl, int on) {

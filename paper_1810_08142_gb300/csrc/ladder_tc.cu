@@ -170,17 +170,21 @@ __device__ __forceinline__ Item decode_item(const TcArgs &A, int item) {
 }
 
 // The molecule's arguments and the local item index of global work unit `it`.
+// A single-molecule launch reads its arguments straight from the launch
+// parameters; a batch reads them from the device table.
+template <bool kBatch>
 __device__ __forceinline__ const TcArgs &item_args(const TcLaunch &Lp, int it, int &local) {
-  if (Lp.mols == nullptr) {
+  if constexpr (!kBatch) {
     local = it;
     return Lp.one;
+  } else {
+    const int2 w = Lp.items[it];
+    local = w.y;
+    return Lp.mols[w.x];
   }
-  const int2 w = Lp.items[it];
-  local = w.y;
-  return Lp.mols[w.x];
 }
 
-template <int S>
+template <int S, bool kBatch>
 __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_constant__ TcLaunch Lp) {
   using C = Cfg<S>;
   extern __shared__ uint8_t smem_raw[];
@@ -224,7 +228,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
   // every role walks the same sequence of work items; barrier phases carry
   // over from one item to the next
   const int it0 = blockIdx.x, itstep = gridDim.x, nit = Lp.nitems;
-  const TcArgs &A0args = Lp.mols ? Lp.mols[0] : Lp.one;
+  const TcArgs &A0args = kBatch ? Lp.mols[0] : Lp.one;
   const Watchdog wd{A0args.status, abort_flag, Lp.timeout_ns};
 
   if (warp == 0) {
@@ -236,7 +240,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
       bool ok = true;
       for (int it = it0; ok && it < nit; it += itstep) {
         int local;
-        const TcArgs &A = item_args(Lp, it, local);
+        const TcArgs &A = item_args<kBatch>(Lp, it, local);
         const Item I = decode_item(A, local);
         const TcChunk &CH = I.CH;
         const int A0 = I.A0, B0 = I.B0, p0 = I.p0, p1 = I.p1;
@@ -313,7 +317,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
       bool ok = true;
       for (int it = it0; ok && it < nit; it += itstep) {
         int local;
-        const TcArgs &A = item_args(Lp, it, local);
+        const TcArgs &A = item_args<kBatch>(Lp, it, local);
         const Item I = decode_item(A, local);
         const TcChunk &CH = I.CH;
         const int p0 = I.p0, p1 = I.p1;
@@ -421,7 +425,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
     bool ok = true;
     for (int it = it0; ok && it < nit; it += itstep) {
       int local;
-      const TcArgs &A = item_args(Lp, it, local);
+      const TcArgs &A = item_args<kBatch>(Lp, it, local);
       const Item I = decode_item(A, local);
       const int p0 = I.p0, p1 = I.p1;
       const uint32_t sc = I.sc;
@@ -615,18 +619,31 @@ uint32_t tc_smem_bytes(int nslices) {
 }
 
 cudaError_t tc_init_attributes(int nslices) {
-  if (nslices == 2)
-    return cudaFuncSetAttribute(ladder_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Cfg<2>::kSmem);
-  return cudaFuncSetAttribute(ladder_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)Cfg<3>::kSmem);
+  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e;
+  if (nslices == 2) {
+    e = cudaFuncSetAttribute(ladder_tc_kernel<2, false>, at, (int)Cfg<2>::kSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(ladder_tc_kernel<2, true>, at, (int)Cfg<2>::kSmem);
+  } else {
+    e = cudaFuncSetAttribute(ladder_tc_kernel<3, false>, at, (int)Cfg<3>::kSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(ladder_tc_kernel<3, true>, at, (int)Cfg<3>::kSmem);
+  }
+  return e;
 }
 
 cudaError_t launch_ladder_tc(const TcLaunch &a, int nslices, int grid, cudaStream_t s) {
-  if (nslices == 2)
-    ladder_tc_kernel<2><<<grid, kThreads, Cfg<2>::kSmem, s>>>(a);
-  else
-    ladder_tc_kernel<3><<<grid, kThreads, Cfg<3>::kSmem, s>>>(a);
+  const bool batch = a.mols != nullptr;
+  if (nslices == 2) {
+    if (batch)
+      ladder_tc_kernel<2, true><<<grid, kThreads, Cfg<2>::kSmem, s>>>(a);
+    else
+      ladder_tc_kernel<2, false><<<grid, kThreads, Cfg<2>::kSmem, s>>>(a);
+  } else {
+    if (batch)
+      ladder_tc_kernel<3, true><<<grid, kThreads, Cfg<3>::kSmem, s>>>(a);
+    else
+      ladder_tc_kernel<3, false><<<grid, kThreads, Cfg<3>::kSmem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -635,4 +652,34 @@ cudaError_t launch_unpack(const TcLaunch &a, int nblocks, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+}  // namespace ladder
+
+namespace ladder {
+namespace {
+// One warp waits, with the library's bounded wait, on an mbarrier that
+// nothing ever arrives at; the wait gives up after `timeout_ns`, records
+// `site` in the status word and the kernel returns normally.
+__global__ void selftest_wait_kernel(int *status, unsigned long long timeout_ns, int site) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  const uint32_t b = tc::smem_u32(&bar);
+  if (threadIdx.x == 0) {
+    tc::mbar_init(b, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const tc::Watchdog wd{status, &abort_flag, timeout_ns};
+    tc::mbar_wait(b, 0, wd, site);
+  }
+  __syncthreads();
+}
+}  // namespace
+
+cudaError_t launch_selftest_wait(int *status, unsigned long long timeout_ns, int site,
+                                 cudaStream_t s) {
+  selftest_wait_kernel<<<1, 32, 0, s>>>(status, timeout_ns, site);
+  return cudaGetLastError();
+}
 }  // namespace ladder

@@ -1,0 +1,147 @@
+"""Autotuner of the split-BF16 ladder kernel.
+
+For one shape (o, v, N_aux) it tries each precision mode (BF16X3, BF16X6)
+with several launch parameters (ladder_tuning: GEMM1 chain length kc, GEMM2
+pieces per fresh accumulator, block-pair split) and keeps the fastest one
+whose relative Frobenius error in R, measured against the FP64 GPU path on
+seeded random inputs, stays below half the tolerance (a margin for inputs
+that differ from the proxy's).  The FP32 accumulation error of
+a candidate depends on its chain lengths and on N_aux, not on v, so accuracy
+is measured on a proxy with the same o and N_aux and v capped at 64 (where
+the FP64 path is quick); speed is measured on the full shape.
+
+Results go to a JSON cache ($LADDER_TUNE_CACHE, else tune_cache.json next to
+this file) keyed by "o,v,naux"; Ladder(..., mode="tuned") reads it.
+
+    python -m paper_1810_08142_gb300.tune 34 400 1600 [--tol 1e-6]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+
+CACHE_DEFAULT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.json")
+
+
+def cache_path() -> str:
+    return os.environ.get("LADDER_TUNE_CACHE", CACHE_DEFAULT)
+
+
+def _load() -> dict:
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _key(o, v, naux) -> str:
+    return "%d,%d,%d" % (o, v, naux)
+
+
+def lookup(o: int, v: int, naux: int):
+    """(mode, tuning dict or None) for a shape: the cached entry of that shape,
+    else of the nearest cached shape, else BF16X6 with its defaults."""
+    c = _load()
+    e = c.get(_key(o, v, naux))
+    if e is None and c:
+        def dist(k):
+            oo, vv, nn = (int(s) for s in k.split(","))
+            return abs(oo - o) / max(o, 1) + abs(vv - v) / max(v, 1) + abs(nn - naux) / max(naux, 1)
+        e = c[min(c, key=dist)]
+        e = dict(e)
+        e["tuning"] = {k: val for k, val in e["tuning"].items() if k != "ksplit"}
+    if e is None:
+        return "bf16x6", None
+    return e["mode"], e["tuning"]
+
+
+def candidates():
+    out = []
+    for kc in (16, 32):
+        out.append(("bf16x3", {"kc": kc, "s_pieces": 4, "xy_split": 1}))
+    for kc in (2, 4, 8):
+        for sp in (1, 2):
+            out.append(("bf16x6", {"kc": kc, "s_pieces": sp, "xy_split": 1}))
+    return out
+
+
+def _inputs(o, v, naux, seed, device):
+    import torch
+    g = torch.Generator(device=device).manual_seed(seed)
+    B = torch.randn(naux, v, v, generator=g, device=device, dtype=torch.float64)
+    B *= torch.exp(-3.0 * torch.arange(naux, device=device, dtype=torch.float64) / naux)[:, None, None] * 0.1
+    tau = torch.randn(o, o, v, v, generator=g, device=device, dtype=torch.float64) * 1e-2
+    tau = 0.5 * (tau + tau.permute(1, 0, 3, 2))
+    return B.contiguous(), tau.contiguous()
+
+
+def _time_ms(L, B, tau, R, reps):
+    import torch
+    L.apply(B, tau, R)
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        L.apply(B, tau, R)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def tune(o: int, v: int, naux: int, tol: float = 1e-6, reps: int = 2, seed: int = 0,
+         write: bool = True, verbose: bool = True) -> dict:
+    import torch
+    from . import Ladder
+    dev = torch.device("cuda")
+    # accuracy proxy: same o and N_aux, v <= 64, against the FP64 path
+    vp = min(v, 64)
+    Bp, taup = _inputs(o, vp, naux, seed, dev)
+    ref = Ladder(o, vp, naux, mode="fp64", device=dev).apply(Bp, taup)
+    nref = torch.linalg.vector_norm(ref).item()
+    B, tau = _inputs(o, v, naux, seed + 1, dev)
+    R = torch.empty_like(tau)
+    results = []
+    for mode, tun in candidates():
+        Lp = Ladder(o, vp, naux, mode=mode, device=dev, tuning=tun)
+        err = torch.linalg.vector_norm(Lp.apply(Bp, taup) - ref).item() / nref
+        Lp.close()
+        L = Ladder(o, v, naux, mode=mode, device=dev, tuning=tun)
+        from . import ladder_get_tuning
+        full = ladder_get_tuning(L.plan).as_dict()
+        ms = _time_ms(L, B, tau, R, reps)
+        L.close()
+        del L
+        torch.cuda.empty_cache()
+        results.append({"mode": mode, "tuning": full, "ms": ms, "err": err})
+        if verbose:
+            print("%-7s %-60s %9.3f ms  rel-F %.2e" % (mode, full, ms, err), flush=True)
+    # the proxy's inputs are not the caller's: keep a factor of two in hand
+    ok = [r for r in results if r["err"] <= 0.5 * tol]
+    best = min(ok, key=lambda r: r["ms"]) if ok else min(results, key=lambda r: r["err"])
+    entry = dict(best, tol=tol, candidates=len(results))
+    if write:
+        c = _load()
+        c[_key(o, v, naux)] = entry
+        with open(cache_path(), "w") as f:
+            json.dump(c, f, indent=1, sort_keys=True)
+    return entry
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("o", type=int)
+    ap.add_argument("v", type=int)
+    ap.add_argument("naux", type=int)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--reps", type=int, default=2)
+    a = ap.parse_args()
+    e = tune(a.o, a.v, a.naux, tol=a.tol, reps=a.reps)
+    print(json.dumps(e))
+
+
+if __name__ == "__main__":
+    main()
