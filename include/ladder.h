@@ -129,9 +129,10 @@ ladder_status ladder_energy_noalloc(int o, int v, const double *R, const double 
  *   dtau_ij^cd = sum_ab W_ij^ab (ac|bd)                          (transposed ladder)
  *   dB^P_xy    = sum_{ij,b,d} W_ij^{xb} tau_ij^{yd} B^P_bd
  *              + sum_{ij,a,c} W_ij^{ax} tau_ij^{cy} B^P_ac
- * dtau runs the plan's own mode: the ladder of W with every factor B^P
- * transposed.  dB runs in FP64 (both terms are equal under the pair symmetry
- * of W and tau, so it evaluates 2 x the first); it needs a plan created with
+ * Both run in the plan's mode.  dtau is the ladder of W with every factor
+ * B^P transposed.  dB evaluates 2 x the first term (both terms are equal
+ * under the pair symmetry of W and tau) as Gamma^{xb}_{yd} = sum_ij W_ij^{xb}
+ * tau_ij^{yd} tiles contracted with B^P_bd; it needs a plan created with
  * LADDER_WITH_BACKWARD (else LADDER_EWORKSPACE).  Either output may be NULL
  * to skip it.  Outputs are overwritten.  dtau may not alias W or tau. */
 ladder_status ladder_backward(ladder_plan_t plan, const double *B, const double *tau,

@@ -19,6 +19,10 @@ void launch_split_B(int N, int v, int vp, int Np, int nslices, const double *B,
                     __nv_bfloat16 *Bt, cudaStream_t s, bool transB = false);
 void launch_pair_combine(int o, int v, double alpha, double beta, const double *X, double *Y,
                          cudaStream_t s);
+void launch_split_pairs(int o, int v, int vp, int IJp, int nslices, const double *X,
+                        __nv_bfloat16 *Xt, cudaStream_t s);
+void launch_split_B_rows(int N, int v, int vp, int Np, int nslices, const double *B,
+                         __nv_bfloat16 *Bs, cudaStream_t s);
 size_t energy_partials(int o, int v);
 void launch_energy(int o, int v, const double *R, const double *t2, double *part, double *E,
                    cudaStream_t s);
@@ -54,6 +58,22 @@ struct GradArgs {
 int grad_fp64_grid(int vp, int sm_count);
 size_t grad_fp64_slab_doubles(int vp, int N, int grid);
 cudaError_t launch_grad_B_fp64(const GradArgs &a, int grid, cudaStream_t s);
+
+// ---- split-BF16 gradient with respect to B (adjoint, ladder_grad_tc.cu)
+constexpr int kGradTcPChunk = 128;  // auxiliary functions per work unit (TMEM columns)
+struct GradTcArgs {
+  CUtensorMap tmW;   // W slices [S][x][b][ij], box (32 ij, 8 b, 16 x), 64-byte swizzle
+  CUtensorMap tmT;   // tau slices [S][y][d][ij], box (32 ij, 8 d, 8 y)
+  CUtensorMap tmBs;  // B slices [S][P][D][b][dl], box (16 (b,dl), 1 D, 16 P), 32-byte swizzle
+  double *dB;        // [N][v][v]
+  double *racc;      // FP64 sums, [item][128 cols][128 lanes]
+  int *status;
+  int o, v, N, vp, Np, IJp, nks, nY8, ntiles, npc;
+  int kc, s_pieces, flush_every;
+  unsigned long long timeout_ns;
+};
+cudaError_t grad_tc_init_attributes(int nslices);
+cudaError_t launch_grad_B_tc(const GradTcArgs &a, int nslices, cudaStream_t s);
 
 // ---- split-BF16 fused ladder (tcgen05)
 // An occupied-pair chunk of the tensor-core kernel: lambda+ rows [lp0, lp0+np)

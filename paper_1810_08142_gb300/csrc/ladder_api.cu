@@ -22,6 +22,7 @@ inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a
 
 struct Layout {
   size_t status = 0, energy = 0, Tp = 0, Tm = 0, slab = 0, Bt = 0, W = 0, gslab = 0, total = 0;
+  size_t gWt = 0, gTt = 0, gBs = 0, gacc = 0;  // split-BF16 dB
 };
 
 int tc_slices(int mode) { return mode == LADDER_BF16X3 ? 2 : 3; }
@@ -70,6 +71,8 @@ struct ladder_plan_s {
   int S = 0, ksplit = 1, kc = 4, s_pieces = 4, flush_every = 16, xy_split = 1, ntiles_tc = 0, racc_cols = 0;
   std::vector<TcChunk> chunks_tc;
   CUtensorMap tmA, tmB, tmTp, tmTm;
+  CUtensorMap tmGW, tmGT, tmGBs;  // split-BF16 dB operands
+  int g_IJp = 0, g_Np = 0, g_ntiles = 0, g_npc = 0;
   Layout lay;
   // ragged batch: one sub-plan per molecule inside this plan's workspace
   bool batched = false;
@@ -177,7 +180,23 @@ void compute_layout(ladder_plan_s *pl) {
   }
   L.W = off;
   L.gslab = off;  // FP64 dB: spill of the Gamma tiles
-  if (pl->backward) off = align_up(off + grad_fp64_slab_doubles(pl->vp, pl->N, pl->grid_grad) * sizeof(double));
+  if (pl->backward && pl->mode == LADDER_FP64)
+    off = align_up(off + grad_fp64_slab_doubles(pl->vp, pl->N, pl->grid_grad) * sizeof(double));
+  if (pl->backward && pl->mode != LADDER_FP64) {
+    const size_t S = pl->S, vp = pl->vp;
+    pl->g_IJp = (pl->o * pl->o + 31) / 32 * 32;
+    pl->g_Np = (pl->N + 15) / 16 * 16;
+    pl->g_ntiles = (pl->vp / 16) * (pl->vp / CB);
+    pl->g_npc = (pl->g_Np + kGradTcPChunk - 1) / kGradTcPChunk;
+    L.gWt = align_up(off, 1024);
+    off = L.gWt + S * vp * vp * pl->g_IJp * 2;
+    L.gTt = align_up(off, 1024);
+    off = L.gTt + S * vp * vp * pl->g_IJp * 2;
+    L.gBs = align_up(off, 1024);
+    off = L.gBs + S * (size_t)pl->g_Np * vp * vp * 2;
+    L.gacc = align_up(off, 1024);
+    off = align_up(L.gacc + (size_t)pl->g_ntiles * pl->g_npc * 128 * kGradTcPChunk * sizeof(double));
+  }
   L.total = off;
   pl->lay = L;
 }
@@ -337,6 +356,19 @@ static ladder_status encode_maps(ladder_plan_s *pl, char *w) {
       encode3d(&pl->tmTm, w + pl->lay.Tm, pl->K, std::max(pl->nlm, 1), S, 16, 16, 1,
                CU_TENSOR_MAP_SWIZZLE_32B);
   if (!ok) return LADDER_ECUDA;
+  if (pl->backward) {
+    const uint64_t vp = pl->vp;
+    const bool okg =
+        encode3d(&pl->tmGW, w + pl->lay.gWt, pl->g_IJp, vp, vp * S, 32, 8, 16,
+                 CU_TENSOR_MAP_SWIZZLE_64B) &&
+        encode3d(&pl->tmGT, w + pl->lay.gTt, pl->g_IJp, vp, vp * S, 32, 8, 8,
+                 CU_TENSOR_MAP_SWIZZLE_64B) &&
+        encode3d(&pl->tmGBs, w + pl->lay.gBs, vp * CB, vp / CB, (uint64_t)pl->g_Np * S, 16, 1, 16,
+                 CU_TENSOR_MAP_SWIZZLE_32B);
+    if (!okg) return LADDER_ECUDA;
+    const ladder_status st = cuda_status(grad_tc_init_attributes(pl->S));
+    if (st != LADDER_OK) return st;
+  }
   return cuda_status(tc_init_attributes(pl->S));
 }
 
@@ -520,7 +552,7 @@ ladder_status ladder_backward(ladder_plan_t pl, const double *B, const double *t
                                                      : apply_tc(pl, B, W, dtau, s, true);
     if (st != LADDER_OK) return st;
   }
-  if (dB) {
+  if (dB && pl->mode == LADDER_FP64) {
     GradArgs g{};
     g.B = B;
     g.tau = tau;
@@ -532,6 +564,41 @@ ladder_status ladder_backward(ladder_plan_t pl, const double *B, const double *t
     g.N = pl->N;
     g.vp = pl->vp;
     const ladder_status st = cuda_status(launch_grad_B_fp64(g, pl->grid_grad, s));
+    if (st != LADDER_OK) return st;
+  } else if (dB) {
+    auto *Wt = ws_at<__nv_bfloat16>(pl, pl->lay.gWt);
+    auto *Tt = ws_at<__nv_bfloat16>(pl, pl->lay.gTt);
+    auto *Bs = ws_at<__nv_bfloat16>(pl, pl->lay.gBs);
+    launch_split_pairs(pl->o, pl->v, pl->vp, pl->g_IJp, pl->S, W, Wt, s);
+    launch_split_pairs(pl->o, pl->v, pl->vp, pl->g_IJp, pl->S, tau, Tt, s);
+    launch_split_B_rows(pl->N, pl->v, pl->vp, pl->g_Np, pl->S, B, Bs, s);
+    ladder_status st = cuda_status(cudaGetLastError());
+    if (st != LADDER_OK) return st;
+    GradTcArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.tmW = pl->tmGW;
+    g.tmT = pl->tmGT;
+    g.tmBs = pl->tmGBs;
+    g.dB = dB;
+    g.racc = ws_at<double>(pl, pl->lay.gacc);
+    g.status = ws_at<int>(pl, pl->lay.status);
+    g.o = pl->o;
+    g.v = pl->v;
+    g.N = pl->N;
+    g.vp = pl->vp;
+    g.Np = pl->g_Np;
+    g.IJp = pl->g_IJp;
+    g.nks = pl->g_IJp / 32;
+    g.nY8 = pl->vp / CB;
+    g.ntiles = pl->g_ntiles;
+    g.npc = pl->g_npc;
+    g.kc = pl->kc;
+    g.s_pieces = pl->s_pieces;
+    g.flush_every = pl->flush_every;
+    const double item_flops = 2.0 * (pl->vp / CB) * (pl->vp / CB) * 128.0 * 64.0 *
+                              (pl->g_IJp + 2.0 * kGradTcPChunk) * 6.0;
+    g.timeout_ns = (unsigned long long)(2e9 + 20.0 * item_flops / 4e12 * 1e9);
+    st = cuda_status(launch_grad_B_tc(g, pl->S, s));
     if (st != LADDER_OK) return st;
   }
   return LADDER_OK;

@@ -245,3 +245,85 @@ void launch_pair_combine(int o, int v, double alpha, double beta, const double *
 }
 
 }  // namespace ladder
+
+namespace ladder {
+
+// ---------------------------------------------------------------- adjoint slices
+// Xt[q][x][b][ij] = slice q of X_ij^{xb} (X = W or tau), K-major over the
+// occupied pairs ij = i*o + j; x, b < vp (zero beyond v), ij < IJp (zero
+// beyond o^2).  32x32 tiles through shared memory (read b fastest, write ij
+// fastest).
+template <int S>
+__global__ void split_pairs_kernel(int o, int v, int vp, int IJp, const double *__restrict__ X,
+                                   __nv_bfloat16 *__restrict__ Xt) {
+  __shared__ double tile[32][33];
+  const int x = blockIdx.z;
+  const int b0 = blockIdx.x * 32, ij0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const int o2 = o * o;
+  for (int r = ty; r < 32; r += 8) {
+    const int ij = ij0 + r, b = b0 + tx;
+    tile[r][tx] = (ij < o2 && b < v && x < v) ? X[((size_t)ij * v + x) * v + b] : 0.0;
+  }
+  __syncthreads();
+  const size_t slice = (size_t)vp * vp * IJp;
+  for (int r = ty; r < 32; r += 8) {
+    const int b = b0 + r, ij = ij0 + tx;
+    if (b < vp && ij < IJp) {
+      __nv_bfloat16 sl[S];
+      split_bf16<S>(tile[tx][r], sl);
+      const size_t off = ((size_t)x * vp + b) * IJp + ij;
+#pragma unroll
+      for (int q = 0; q < S; ++q) Xt[q * slice + off] = sl[q];
+    }
+  }
+}
+
+void launch_split_pairs(int o, int v, int vp, int IJp, int nslices, const double *X,
+                        __nv_bfloat16 *Xt, cudaStream_t s) {
+  dim3 grid((vp + 31) / 32, (IJp + 31) / 32, vp), block(32, 8);
+  if (nslices == 2)
+    split_pairs_kernel<2><<<grid, block, 0, s>>>(o, v, vp, IJp, X, Xt);
+  else
+    split_pairs_kernel<3><<<grid, block, 0, s>>>(o, v, vp, IJp, X, Xt);
+}
+
+// Bs[q][P][D][b][dl] = slice q of B^P_{b, 8D+dl}: for each auxiliary function
+// P and each 8-block D of d, the (b, d) slots of that block with b-major order,
+// so that the 16 slots (b, 8D..8D+7), (b+1, 8D..8D+7) of a GEMM piece are
+// contiguous (one 32-byte TMA row).  Padded to vp (zero beyond v) and to Np
+// auxiliary functions (zero beyond N).
+template <int S>
+__global__ void split_B_rows_kernel(int N, int v, int vp, int Np, const double *__restrict__ B,
+                                    __nv_bfloat16 *__restrict__ Bs) {
+  const size_t total = (size_t)Np * vp * vp;
+  const size_t slice = total;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int dl = (int)(idx % CB);
+    size_t r = idx / CB;
+    const int b = (int)(r % vp);
+    r /= vp;
+    const int D = (int)(r % (vp / CB));
+    const int P = (int)(r / (vp / CB));
+    const int d = D * CB + dl;
+    const double val = (P < N && b < v && d < v) ? B[((size_t)P * v + b) * v + d] : 0.0;
+    __nv_bfloat16 sl[S];
+    split_bf16<S>(val, sl);
+#pragma unroll
+    for (int q = 0; q < S; ++q) Bs[q * slice + idx] = sl[q];
+  }
+}
+
+void launch_split_B_rows(int N, int v, int vp, int Np, int nslices, const double *B,
+                         __nv_bfloat16 *Bs, cudaStream_t s) {
+  const size_t total = (size_t)Np * vp * vp;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (nslices == 2)
+    split_B_rows_kernel<2><<<blocks, 256, 0, s>>>(N, v, vp, Np, B, Bs);
+  else
+    split_B_rows_kernel<3><<<blocks, 256, 0, s>>>(N, v, vp, Np, B, Bs);
+}
+
+}  // namespace ladder

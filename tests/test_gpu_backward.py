@@ -12,6 +12,7 @@ from gpu_util import rel_fro, to_dev
 
 pytestmark = pytest.mark.gpu
 
+# relative Frobenius tolerances of dtau and dB, per mode (as for R)
 DTAU_TOL = {"fp64": 1e-12, "bf16x6": 1e-6, "bf16x3": 2e-5}
 
 
@@ -41,7 +42,7 @@ def test_backward_matches_oracle_gradient(lad, mode, o, v, n, seed):
     e_B = rel_fro(dB.cpu().numpy(), oracle.grad_B(B, tau, W))
     print("%s o=%d v=%d n=%d: dtau rel-F %.3e  dB rel-F %.3e" % (mode, o, v, n, e_tau, e_B))
     assert e_tau < DTAU_TOL[mode]
-    assert e_B < 1e-12  # dB runs in FP64 in every mode
+    assert e_B < DTAU_TOL[mode]  # dB runs in the plan's mode as well
 
 
 def test_weights_kernel_matches_oracle(lad):
@@ -116,6 +117,6 @@ def test_backward_full_size_sampled(lad, mode):
     e_B = np.linalg.norm(gotB - refB) / np.linalg.norm(refB)
     print("%s full size: dtau sampled rel %.3e  dB sampled rel %.3e" % (mode, e_tau, e_B))
     assert e_tau < DTAU_TOL[mode]
-    assert e_B < 1e-12
+    assert e_B < DTAU_TOL[mode]
     # the dtau output keeps the pair symmetry of the ladder
     assert np.array_equal(dtau, dtau.transpose(1, 0, 3, 2))
