@@ -130,6 +130,15 @@ def oracle_sample(x, seconds_target: float):
     return full, dt, "%d of %d (a,b) columns of R (all i,j), %.1f s" % (n, v * v, dt), nthr
 
 
+def tuned_for(w, mode):
+    """The autotuner's cached launch parameters for this shape and mode, if any."""
+    if mode == "fp64":
+        return None
+    from paper_1810_08142_gb300 import tune
+    e = tune._load().get(tune._key(w.o, w.v, w.naux))
+    return e["tuning"] if e and e.get("mode") == mode else None
+
+
 def cpu_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -267,7 +276,8 @@ def main():
     E = torch.empty((), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
 
-    L = lad.Ladder(w.o, w.v, w.naux, mode=args.mode, device=dev)
+    tuning = tuned_for(w, args.mode)
+    L = lad.Ladder(w.o, w.v, w.naux, mode=args.mode, device=dev, tuning=tuning)
     lad.ladder_set_timing(L.plan, True)
 
     def step(Lx):
@@ -329,7 +339,7 @@ def main():
 
     extra = {}
     # the other split variant and the FP64 path, same workload, one timed step each
-    others = [] if args.mode != "bf16x6" else ["bf16x3"]
+    others = [] if args.mode != "bf16x6" or args.no_fp64 else ["bf16x3"]
     if not args.no_fp64 and args.mode != "fp64":
         others.append("fp64")
     for m in others:
@@ -395,6 +405,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": args.workload, "o": w.o, "v": w.v, "naux": w.naux,
                        "seed": w.seed, "mode": args.mode, "parallelism": "replicas",
+                       "tuning": lad.ladder_get_tuning(L.plan).as_dict() if args.mode != "fp64" else None,
                        "l2": "inputs larger than L2 (B %.2f GB, tau %.2f GB)"
                              % (B.numel() * 8 / 1e9, tau.numel() * 8 / 1e9)},
             "stages_ms": {"prep": prep_ms, "fused": fused_ms, "unpack": unpack_ms},
