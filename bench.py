@@ -294,11 +294,12 @@ def main():
     clocks.start()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    fused = []
+    fused, passes = [], []
     e0.record(stream)
     for _ in range(args.steps):
         step(L)
         fused.append(lad.ladder_timing(L.plan))  # waits for this step's events
+        passes.append(lad.ladder_timing_passes(L.plan))
     e1.record(stream)
     barrier()
     clk = clocks.stop()
@@ -309,6 +310,10 @@ def main():
     fused_ms = statistics.mean(f[1] for f in fused)
     prep_ms = statistics.mean(f[0] for f in fused)
     unpack_ms = statistics.mean(f[2] for f in fused)
+    pass1_ms = statistics.mean(f[0] for f in passes)
+    pass2_ms = statistics.mean(f[1] for f in passes)
+    tun = lad.ladder_get_tuning(L.plan).as_dict() if args.mode != "fp64" else None
+    two_pass = bool(tun and tun["two_pass"])
     E_val = float(E.item())
 
     # parity against stored oracle values (written by tests/golden/make_golden.py)
@@ -328,12 +333,30 @@ def main():
     if args.mode == "fp64":
         roof = {"bound": "fp64", "achieved": F / (fused_ms * 1e-3) / 1e12, "peak": None,
                 "unit": "TFLOP/s", "frac": None, "traffic": None}
+    elif two_pass:
+        # dominant kernel of the two-pass form: GEMM1 with the V+- store, or
+        # GEMM2 from the stored tiles, whichever takes longer
+        F1 = synthetic.falg_gemm1(w.o, w.v, w.naux)
+        nS = 2 if args.mode == "bf16x3" else 3
+        if pass1_ms >= pass2_ms:
+            kname, kflops, kms = "ladder_tc_kernel<%d,false,true> (GEMM1 + V store)" % nS, F1, pass1_ms
+        else:
+            kname, kflops, kms = "ladder_gemm2_kernel<%d> (GEMM2 from stored V)" % nS, F - F1, pass2_ms
+        achieved = prod * kflops / (kms * 1e-3) / 1e12
+        peak = pk["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": kname,
+                "kernel_ms": kms,
+                "both_passes_frac": prod * F / ((pass1_ms + pass2_ms) * 1e-3) / 1e12 / peak,
+                "note": "achieved = %d x (that pass's share of F_alg: 2 P+(v) v^2 N for GEMM1, the "
+                        "rest for GEMM2) / its CUDA-event time; peak = bf16 sustained (%s)"
+                        % (prod, pk_kind)}
     else:
         achieved = prod * F / (fused_ms * 1e-3) / 1e12
         peak = pk["bf16_tflops_sustained"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "ladder_tc_kernel<%d>" % (2 if args.mode == "bf16x3" else 3),
+                "kernel": "ladder_tc_kernel<%d,false,false>" % (2 if args.mode == "bf16x3" else 3),
                 "note": "achieved = %d x F_alg (bf16 tensor flops of the split scheme) / fused-kernel "
                         "time; peak = bf16 sustained (%s)" % (prod, pk_kind)}
 
@@ -342,8 +365,13 @@ def main():
     others = [] if args.mode != "bf16x6" or args.no_fp64 else ["bf16x3"]
     if not args.no_fp64 and args.mode != "fp64":
         others.append("fp64")
+    if two_pass and not args.no_fp64:
+        others.insert(0, args.mode + "_fused")  # the same mode in the one-kernel form
     for m in others:
-        Lm = lad.Ladder(w.o, w.v, w.naux, mode=m, device=dev)
+        if m.endswith("_fused"):
+            Lm = lad.Ladder(w.o, w.v, w.naux, mode=m[:-6], device=dev, tuning={**tun, "two_pass": 0, "ksplit": 0})
+        else:
+            Lm = lad.Ladder(w.o, w.v, w.naux, mode=m, device=dev)
         lad.ladder_set_timing(Lm.plan, True)
         if m != "fp64":
             step(Lm)
@@ -405,12 +433,14 @@ def main():
             "data": "synthetic",
             "config": {"workload": args.workload, "o": w.o, "v": w.v, "naux": w.naux,
                        "seed": w.seed, "mode": args.mode, "parallelism": "replicas",
-                       "tuning": lad.ladder_get_tuning(L.plan).as_dict() if args.mode != "fp64" else None,
+                       "tuning": tun,
                        "l2": "inputs larger than L2 (B %.2f GB, tau %.2f GB)"
                              % (B.numel() * 8 / 1e9, tau.numel() * 8 / 1e9)},
-            "stages_ms": {"prep": prep_ms, "fused": fused_ms, "unpack": unpack_ms},
+            "stages_ms": {"prep": prep_ms, "ladder": fused_ms, "unpack": unpack_ms,
+                          "pass1": pass1_ms if two_pass else None,
+                          "pass2": pass2_ms if two_pass else None},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": 7 * args.steps, "parity": parity, "E_L": E_val, "others": extra,
+            "gpu_launches": (9 if two_pass else 7) * args.steps, "parity": parity, "E_L": E_val, "others": extra,
         }
         print(json.dumps(line), flush=True)
     L.close()

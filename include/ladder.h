@@ -76,13 +76,21 @@ ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out);
  *   flush_every FP32 accumulators summed before an FP64 flush, >= 1;
  *   ksplit      block-pair ranges per work unit (more CTAs for small shapes), >= 1;
  *   xy_split    1: separate GEMM1 accumulators for the hi*hi slice product and
- *               the smaller products; 0: one accumulator, two buffers.
+ *               the smaller products; 0: one accumulator, two buffers;
+ *   two_pass    0: one fused kernel (the integral tiles never leave the chip;
+ *               GEMM1 is recomputed for every chunk of at most 128 occupied
+ *               pairs); 1: GEMM1 once per (ab tile, block pair) with the
+ *               sliced V+- tiles stored in the workspace (2S x 16 KiB per
+ *               tile and block pair), then GEMM2 from the stored tiles in
+ *               chunks of up to 192 occupied pairs.  The plan picks 1 when the
+ *               fused kernel would need more than one chunk and the stored
+ *               tiles take at most 128 GiB.
  * Longer chains are faster and less accurate (the tensor core's FP32
  * accumulation error grows with the MMAs per accumulator).  ladder_set_tuning
  * must come before ladder_set_workspace (the workspace size depends on
- * ksplit); it returns LADDER_EINVAL for out-of-range values. */
+ * ksplit and two_pass); it returns LADDER_EINVAL for out-of-range values. */
 typedef struct {
-    int kc, s_pieces, flush_every, ksplit, xy_split;
+    int kc, s_pieces, flush_every, ksplit, xy_split, two_pass;
 } ladder_tuning;
 ladder_status ladder_get_tuning(ladder_plan_t plan, ladder_tuning *t);
 ladder_status ladder_set_tuning(ladder_plan_t plan, const ladder_tuning *t);
@@ -189,6 +197,11 @@ ladder_status ladder_selftest_wait(ladder_plan_t plan, unsigned long long timeou
  * events are created by ladder_set_timing (no device memory). */
 ladder_status ladder_set_timing(ladder_plan_t plan, int on);
 ladder_status ladder_timing(ladder_plan_t plan, float *prep_ms, float *fused_ms, float *unpack_ms);
+
+/* The ladder kernels of the last ladder_apply split by pass (timing on): in
+ * the two-pass form the storing GEMM1 pass and the GEMM2 pass; otherwise the
+ * fused kernel and 0. */
+ladder_status ladder_timing_passes(ladder_plan_t plan, float *pass1_ms, float *pass2_ms);
 
 /* Algorithmic flop count of one ladder_apply (two flops per multiply-add of
  * the symmetric/antisymmetric scheme; identical for every mode). */

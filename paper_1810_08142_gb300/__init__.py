@@ -28,14 +28,14 @@ STATUS = {0: "LADDER_OK", 1: "LADDER_EINVAL", 2: "LADDER_ENOMEM", 3: "LADDER_ECU
 EXPORTS = ("ladder_plan", "ladder_plan_mode", "ladder_get_tuning", "ladder_set_tuning", "ladder_workspace_size", "ladder_set_workspace",
            "ladder_tau", "ladder_apply", "ladder_energy", "ladder_energy_noalloc", "ladder_backward", "ladder_pair_combine", "ladder_apply_host",
            "ladder_plan_batched", "ladder_apply_batched", "ladder_last_device_error", "ladder_selftest_wait",
-           "ladder_set_timing", "ladder_timing", "ladder_flops", "ladder_status_string",
+           "ladder_set_timing", "ladder_timing", "ladder_timing_passes", "ladder_flops", "ladder_status_string",
            "ladder_destroy")
 
 
 class Tuning(ctypes.Structure):
     """Mirror of ladder_tuning (include/ladder.h)."""
     _fields_ = [("kc", ctypes.c_int), ("s_pieces", ctypes.c_int), ("flush_every", ctypes.c_int),
-                ("ksplit", ctypes.c_int), ("xy_split", ctypes.c_int)]
+                ("ksplit", ctypes.c_int), ("xy_split", ctypes.c_int), ("two_pass", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -82,6 +82,7 @@ def load_library(path: str = LIB_PATH):
         "ladder_set_timing": [_P, i],
         "ladder_timing": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
                           ctypes.POINTER(ctypes.c_float)],
+        "ladder_timing_passes": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)],
         "ladder_flops": [_P],
         "ladder_status_string": [i],
         "ladder_destroy": [_P],
@@ -216,6 +217,14 @@ def ladder_timing(plan):
     return tuple(x.value for x in t)
 
 
+def ladder_timing_passes(plan):
+    """(pass1_ms, pass2_ms) of the last ladder_apply: the storing GEMM1 pass
+    and the GEMM2 pass of the two-pass form, else (fused kernel, 0)."""
+    t = [ctypes.c_float() for _ in range(2)]
+    _check("ladder_timing_passes", load_library().ladder_timing_passes(plan, *[ctypes.byref(x) for x in t]))
+    return tuple(x.value for x in t)
+
+
 def ladder_selftest_wait(plan, timeout_ns: int, stream=None) -> None:
     _check("ladder_selftest_wait", load_library().ladder_selftest_wait(plan, int(timeout_ns),
                                                                       _stream(stream)))
@@ -258,6 +267,8 @@ class Ladder:
                 t = ladder_get_tuning(self.plan)
                 for k, val in tuning.items():
                     setattr(t, k, int(val))
+                if "two_pass" in tuning and "ksplit" not in tuning:
+                    t.ksplit = 0  # the plan's own block-pair split for the chosen form
                 ladder_set_tuning(self.plan, t)
             n = ladder_workspace_size(self.plan)
             self.workspace = torch.empty(max(n, 256), dtype=torch.uint8, device=self.device)

@@ -80,14 +80,22 @@ cudaError_t launch_grad_B_tc(const GradTcArgs &a, int nslices, cudaStream_t s);
 // and lambda- rows [lm0, lm0+nm), padded to nps, nms (multiples of 16) TMEM
 // columns; nps + nms <= kTcMaxCols.
 constexpr int kTcMaxCols = 128;
+// Chunks of the GEMM2 kernel of the two-pass form (TMEM holds no GEMM1 tiles):
+// lambda+ or lambda- columns only, at most kTcMaxColsV each.
+constexpr int kTcMaxColsV = 192;
 struct TcChunk {
   int lp0, lm0, np, nm, nps, nms;
+  long long t2off;  // two-pass GEMM2: byte offset of the chunk's tau+- copy (pack_t2)
 };
 struct TcArgs {
   CUtensorMap tmA;   // B slices, box (32 aux, 8 c, 16 a), 64-byte swizzle
   CUtensorMap tmB;   // B slices, box (32 aux, 8 d, 8 b)
   CUtensorMap tmTp;  // tau+ slices [S][lambda+][K], box (16 slots, 16 rows, 1)
   CUtensorMap tmTm;  // tau- slices [S][lambda-][K]
+  CUtensorMap tmVs;  // stored V+- planes [tile][pair][sign][slice][128 rows][64 slots]:
+                     // store box (64, 128, 2S), 128-byte swizzle
+  CUtensorMap tmVl;  // the same planes, load box (16 slots, 128 rows, S): one sign, 32-byte swizzle
+  const uint8_t *T2; // two-pass GEMM2: chunk-major tau+- (pack_t2)
   double *R;
   double *racc;      // FP64 accumulators, [item][col][128 lanes], racc_cols columns per item
   int *status;
@@ -100,9 +108,20 @@ struct TcArgs {
   int xy_split;      // GEMM1: separate accumulators for hi*hi and the smaller products
   int s_pieces;      // 16-slot pieces of GEMM2 per fresh S accumulator (1, 2 or 4)
   int flush_every;   // S accumulators summed in FP32 before an FP64 flush
+  int nplus, wplus, wminus;  // two-pass GEMM2: plus chunks first, lambda columns per chunk
   unsigned long long timeout_ns;
   TcChunk chunks[kMaxChunks];
 };
+// Chunk-major, pre-swizzled tau+- for the GEMM2 pass (prep_kernels.cu).
+struct T2Args {
+  const __nv_bfloat16 *Tp, *Tm;  // [S][rows_p][K], [S][rows_m][K]
+  __nv_bfloat16 *T2;
+  int K, S, rows_p, rows_m, nchunks;
+  TcChunk chunks[kMaxChunks];
+  long long off[kMaxChunks];     // element offset of each chunk in T2
+};
+void launch_pack_t2(const T2Args &a, cudaStream_t s);
+
 // One launch of the fused kernel: a single molecule (mols == nullptr, the
 // work units are 0..nitems-1 of `one`) or a batch (work unit k is local item
 // items[k].y of molecule items[k].x, args in device memory).  tcs lists the
@@ -118,7 +137,12 @@ struct TcLaunch {
 uint32_t tc_smem_bytes(int nslices);
 cudaError_t tc_init_attributes(int nslices);  // once per device, outside stream capture
 cudaError_t launch_ladder_tc(const TcLaunch &a, int nslices, int grid, cudaStream_t s);
+// Two-pass form (single molecule): GEMM1 once per (tile, block pair) with the
+// V+- slices stored to global memory, then GEMM2 from the stored tiles.
+cudaError_t launch_ladder_vstore(const TcLaunch &a, int nslices, int grid, cudaStream_t s);
+cudaError_t launch_ladder_gemm2(const TcLaunch &a, int nslices, int grid, cudaStream_t s);
 cudaError_t launch_unpack(const TcLaunch &a, int nblocks, cudaStream_t s);
+cudaError_t launch_unpack2(const TcLaunch &a, cudaStream_t s);  // two-pass form
 cudaError_t launch_selftest_wait(int *status, unsigned long long timeout_ns, int site,
                                  cudaStream_t s);
 

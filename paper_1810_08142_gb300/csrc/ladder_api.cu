@@ -23,7 +23,11 @@ inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a
 struct Layout {
   size_t status = 0, energy = 0, Tp = 0, Tm = 0, slab = 0, Bt = 0, W = 0, gslab = 0, total = 0;
   size_t gWt = 0, gTt = 0, gBs = 0, gacc = 0;  // split-BF16 dB
+  size_t Vg = 0, T2 = 0;                       // two-pass form: stored V+- tiles, tau+- per chunk
 };
+
+// Two-pass form: at most this many bytes of stored V+- tiles by default.
+constexpr double kVStoreDefaultCap = 128.0 * (1ull << 30);
 
 int tc_slices(int mode) { return mode == LADDER_BF16X3 ? 2 : 3; }
 
@@ -70,7 +74,12 @@ struct ladder_plan_s {
   // split-BF16 tensor-core path
   int S = 0, ksplit = 1, kc = 4, s_pieces = 4, flush_every = 16, xy_split = 1, ntiles_tc = 0, racc_cols = 0;
   std::vector<TcChunk> chunks_tc;
-  CUtensorMap tmA, tmB, tmTp, tmTm;
+  // two-pass form: GEMM2 chunks (up to kTcMaxColsV columns), block-pair
+  // ranges per tile of the storing pass
+  int two_pass = 0, vsplit = 1, racc_cols_v = 0, nplus = 0, wplus = 0, wminus = 0;
+  bool last_two_pass = false;
+  std::vector<TcChunk> chunks_v;
+  CUtensorMap tmA, tmB, tmTp, tmTm, tmVs, tmVl;
   CUtensorMap tmGW, tmGT, tmGBs;  // split-BF16 dB operands
   int g_IJp = 0, g_Np = 0, g_ntiles = 0, g_npc = 0;
   Layout lay;
@@ -84,7 +93,7 @@ struct ladder_plan_s {
   cudaGraphExec_t gexec = nullptr;
   std::vector<const void *> gkey;  // pointers the graph was captured with
   bool timing = false;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   void *ws = nullptr;
   size_t ws_bytes = 0;
 };
@@ -105,13 +114,13 @@ std::vector<Chunk> make_chunks(int o, int rows) {
   return out;
 }
 
-// Occupied-pair chunks of the tensor-core kernel (whole j ranges; padded
-// column counts with nps + nms <= kTcMaxCols).
-std::vector<TcChunk> make_tc_chunks(int o) {
+// Occupied-pair chunks of the tensor-core kernels (whole j ranges; padded
+// column counts with nps + nms <= maxcols).
+std::vector<TcChunk> make_tc_chunks_greedy(int o, int maxcols) {
   auto pad16 = [](int x) { return (x + 15) / 16 * 16; };
   auto fits = [&](int j0, int j1) {
     const int np = pad16(ppos(j1) - ppos(j0)), nm = pad16(pneg(j1) - pneg(j0));
-    return np + nm <= kTcMaxCols;
+    return np + nm <= maxcols;
   };
   std::vector<TcChunk> out;
   int j0 = 0;
@@ -127,6 +136,48 @@ std::vector<TcChunk> make_tc_chunks(int o) {
     c.nms = pad16(c.nm);
     out.push_back(c);
     j0 = j1;
+  }
+  return out;
+}
+
+// As few chunks as the greedy split at `maxcols` gives, with the smallest
+// column cap that keeps that count (so the chunks come out even).
+std::vector<TcChunk> make_tc_chunks(int o, int maxcols) {
+  const size_t n = make_tc_chunks_greedy(o, maxcols).size();
+  for (int m = 32; m < maxcols; m += 16) {
+    auto c = make_tc_chunks_greedy(o, m);
+    if (c.size() == n) return c;
+  }
+  return make_tc_chunks_greedy(o, maxcols);
+}
+
+// Chunks of the two-pass GEMM2 kernel: lambda+ columns in nplus chunks of
+// wplus, then lambda- columns in chunks of wminus (balanced, multiples of 16,
+// at most maxcols).
+std::vector<TcChunk> make_sign_chunks(int o, int maxcols, int &nplus, int &wplus, int &wminus) {
+  auto pad16 = [](int x) { return (x + 15) / 16 * 16; };
+  std::vector<TcChunk> out;
+  const int nlp = ppos(o), nlm = pneg(o);
+  nplus = (nlp + maxcols - 1) / maxcols;
+  wplus = pad16((nlp + nplus - 1) / nplus);
+  for (int c = 0; c < nplus; ++c) {
+    TcChunk t{};
+    t.lp0 = c * wplus;
+    t.np = std::min(wplus, nlp - t.lp0);
+    t.nps = pad16(t.np);
+    out.push_back(t);
+  }
+  wminus = 16;
+  if (nlm > 0) {
+    const int nminus = (nlm + maxcols - 1) / maxcols;
+    wminus = pad16((nlm + nminus - 1) / nminus);
+    for (int c = 0; c < nminus; ++c) {
+      TcChunk t{};
+      t.lm0 = c * wminus;
+      t.nm = std::min(wminus, nlm - t.lm0);
+      t.nms = pad16(t.nm);
+      out.push_back(t);
+    }
   }
   return out;
 }
@@ -175,8 +226,20 @@ void compute_layout(ladder_plan_s *pl) {
     L.Tm = off;
     off = align_up(off + S * std::max(pl->nlm, 1) * pl->K * 2, 1024);
     L.slab = off;  // FP64 accumulators of the tensor-core kernel
-    off = align_up(off + (size_t)pl->ntiles_tc * pl->chunks_tc.size() * pl->ksplit * 128 *
-                             pl->racc_cols * sizeof(double));
+    const size_t nch = pl->two_pass ? pl->chunks_v.size() : pl->chunks_tc.size();
+    const size_t cols = pl->two_pass ? pl->racc_cols_v : pl->racc_cols;
+    off = align_up(off + (size_t)pl->ntiles_tc * nch * pl->ksplit * 128 * cols * sizeof(double), 1024);
+    if (pl->two_pass) {
+      L.Vg = off;
+      off = align_up(off + (size_t)pl->ntiles_tc * pl->nbp * 2 * S * 128 * SLOTS * 2, 1024);
+      L.T2 = off;
+      size_t t2 = 0;
+      for (auto &c : pl->chunks_v) {
+        c.t2off = (long long)t2;
+        t2 += (size_t)S * (c.nps + c.nms) * pl->K * 2;
+      }
+      off = align_up(off + t2, 1024);
+    }
   }
   L.W = off;
   L.gslab = off;  // FP64 dB: spill of the Gamma tiles
@@ -218,6 +281,21 @@ const char *ladder_status_string(ladder_status s) {
   return "unknown status";
 }
 
+// Block-pair ranges per (tile, chunk) so that small problems give every SM work.
+static int auto_ksplit(const ladder_plan_s *pl) {
+  const int nch = (int)(pl->two_pass ? pl->chunks_v.size() : pl->chunks_tc.size());
+  const int items = pl->ntiles_tc * nch;
+  const int ks = (2 * pl->sm_count + items - 1) / items;
+  return std::max(1, std::min(ks, pl->nbp / 4));
+}
+
+// Block-pair ranges per tile of the storing pass (no accumulators depend on
+// them): enough work units for about eight per SM.
+static int auto_vsplit(const ladder_plan_s *pl) {
+  const int vs = (8 * pl->sm_count + pl->ntiles_tc - 1) / pl->ntiles_tc;
+  return std::max(1, std::min(vs, pl->nbp));
+}
+
 // Fills a plan for one shape; batch members get no block-pair split (the
 // batch itself keeps every SM busy).
 static ladder_status init_plan(ladder_plan_s *pl, int o, int v, int naux, int mode,
@@ -246,17 +324,21 @@ static ladder_status init_plan(ladder_plan_s *pl, int o, int v, int naux, int mo
   if (mode != LADDER_FP64) {
     pl->S = tc_slices(mode);
     pl->Np = (naux + 31) / 32 * 32;
-    pl->chunks_tc = make_tc_chunks(o);
-    pl->racc_cols = 0;
+    pl->chunks_tc = make_tc_chunks(o, kTcMaxCols);
+    pl->chunks_v = make_sign_chunks(o, kTcMaxColsV, pl->nplus, pl->wplus, pl->wminus);
+    pl->racc_cols = pl->racc_cols_v = 0;
     for (auto &c : pl->chunks_tc) pl->racc_cols = std::max(pl->racc_cols, c.nps + c.nms);
+    for (auto &c : pl->chunks_v) pl->racc_cols_v = std::max(pl->racc_cols_v, c.nps + c.nms);
     const int nA = pl->vp / 16, nB8 = pl->vp / CB;
     pl->ntiles_tc = 0;
     for (int i = 0; i < nA; ++i) pl->ntiles_tc += nB8 - 2 * i;
-    // split the block pairs of small problems so that every SM has work
-    const int items = pl->ntiles_tc * (int)pl->chunks_tc.size();
-    int ks = (2 * pl->sm_count + items - 1) / items;
-    ks = std::max(1, std::min(ks, pl->nbp / 4));
-    pl->ksplit = batch_member ? 1 : ks;
+    // two-pass form when the fused kernel would recompute GEMM1 and the
+    // stored tiles fit the default cap
+    const double vbytes = (double)pl->ntiles_tc * pl->nbp * 2 * pl->S * 128 * SLOTS * 2;
+    pl->two_pass = (!batch_member && pl->chunks_tc.size() > 1 && vbytes <= kVStoreDefaultCap) ? 1 : 0;
+    if (!batch_member)
+      if (const char *e = getenv("LADDER_TWOPASS")) pl->two_pass = atoi(e) != 0;
+    pl->ksplit = batch_member ? 1 : auto_ksplit(pl);
     // FP32 accumulation chains (see ladder_tc.cu).  GEMM1: with separate
     // hi*hi / small-product accumulators a chain of kc K-steps puts 2*kc MMAs
     // on the large accumulator (32 for BF16X3, 8 for BF16X6).  GEMM2: a fresh
@@ -278,7 +360,9 @@ static ladder_status init_plan(ladder_plan_s *pl, int o, int v, int naux, int mo
     int major = 0, minor = 0;
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, pl->device);
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, pl->device);
-    if ((int)pl->chunks_tc.size() > kMaxChunks || major != 10 || minor != 3) return LADDER_ENOTSUP;
+    if ((int)pl->chunks_tc.size() > kMaxChunks || (int)pl->chunks_v.size() > kMaxChunks ||
+        major != 10 || minor != 3)
+      return LADDER_ENOTSUP;
   } else if ((int)pl->chunks64.size() > kMaxChunks) {
     return LADDER_ENOTSUP;
   }
@@ -319,6 +403,7 @@ ladder_status ladder_get_tuning(ladder_plan_t pl, ladder_tuning *t) {
   t->flush_every = pl->flush_every;
   t->ksplit = pl->ksplit;
   t->xy_split = pl->xy_split;
+  t->two_pass = pl->two_pass;
   return LADDER_OK;
 }
 
@@ -326,14 +411,15 @@ ladder_status ladder_set_tuning(ladder_plan_t pl, const ladder_tuning *t) {
   if (!pl || !t || pl->batched || pl->ws) return LADDER_EINVAL;
   if (pl->mode == LADDER_FP64) return LADDER_OK;
   if (t->kc < 1 || t->kc > 64 || !(t->s_pieces == 1 || t->s_pieces == 2 || t->s_pieces == 4) ||
-      t->flush_every < 1 || t->flush_every > 4096 || t->ksplit < 1 || t->ksplit > pl->nbp ||
-      (t->xy_split != 0 && t->xy_split != 1))
+      t->flush_every < 1 || t->flush_every > 4096 || t->ksplit < 0 || t->ksplit > pl->nbp ||
+      (t->xy_split != 0 && t->xy_split != 1) || (t->two_pass != 0 && t->two_pass != 1))
     return LADDER_EINVAL;
   pl->kc = t->kc;
   pl->s_pieces = t->s_pieces;
   pl->flush_every = t->flush_every;
-  pl->ksplit = t->ksplit;
   pl->xy_split = t->xy_split;
+  pl->two_pass = t->two_pass;
+  pl->ksplit = t->ksplit ? t->ksplit : auto_ksplit(pl);
   compute_layout(pl);
   return LADDER_OK;
 }
@@ -356,6 +442,14 @@ static ladder_status encode_maps(ladder_plan_s *pl, char *w) {
       encode3d(&pl->tmTm, w + pl->lay.Tm, pl->K, std::max(pl->nlm, 1), S, 16, 16, 1,
                CU_TENSOR_MAP_SWIZZLE_32B);
   if (!ok) return LADDER_ECUDA;
+  if (pl->two_pass) {
+    const uint64_t planes = (uint64_t)pl->ntiles_tc * pl->nbp * 2 * S;
+    const bool okv = encode3d(&pl->tmVs, w + pl->lay.Vg, SLOTS, 128, planes, SLOTS, 128,
+                              (uint32_t)(2 * S), CU_TENSOR_MAP_SWIZZLE_128B) &&
+                     encode3d(&pl->tmVl, w + pl->lay.Vg, SLOTS, 128, planes, 16, 128, (uint32_t)S,
+                              CU_TENSOR_MAP_SWIZZLE_32B);
+    if (!okv) return LADDER_ECUDA;
+  }
   if (pl->backward) {
     const uint64_t vp = pl->vp;
     const bool okg =
@@ -422,6 +516,7 @@ static void mark(ladder_plan_t pl, int k, cudaStream_t s) {
 
 static ladder_status apply_fp64(ladder_plan_t pl, const double *B, const double *tau, double *R,
                                 cudaStream_t s, bool transB = false) {
+  pl->last_two_pass = false;
   mark(pl, 0, s);
   double *Tp = ws_at<double>(pl, pl->lay.Tp), *Tm = ws_at<double>(pl, pl->lay.Tm);
   launch_pack_tpm_f64(pl->o, pl->v, pl->K, tau, Tp, Tm, s);
@@ -462,6 +557,9 @@ static TcArgs tc_args(const ladder_plan_s *pl, double *R, int *status) {
   a.tmB = pl->tmB;
   a.tmTp = pl->tmTp;
   a.tmTm = pl->tmTm;
+  a.tmVs = pl->tmVs;
+  a.tmVl = pl->tmVl;
+  a.T2 = pl->two_pass ? ws_at<uint8_t>(pl, pl->lay.T2) : nullptr;
   a.R = R;
   a.status = status;
   a.o = pl->o;
@@ -505,12 +603,54 @@ static ladder_status apply_tc(ladder_plan_t pl, const double *B, const double *t
   TcLaunch L;
   std::memset(&L, 0, sizeof(L));
   L.one = tc_args(pl, R, ws_at<int>(pl, pl->lay.status));
-  L.nitems = L.one.ntiles * L.one.nchunks * L.one.ksplit;
   L.timeout_ns = L.one.timeout_ns;
-  mark(pl, 1, s);
-  st = cuda_status(launch_ladder_tc(L, pl->S, L.nitems, s));
+  pl->last_two_pass = pl->two_pass != 0;
+  if (pl->two_pass) {
+    // pass 1: GEMM1 and the V+- slices of every (tile, block pair) to the workspace
+    TcLaunch L1 = L;
+    L1.one.nchunks = 1;
+    std::memset(&L1.one.chunks[0], 0, sizeof(TcChunk));
+    L1.one.ksplit = pl->vsplit = auto_vsplit(pl);
+    L1.one.racc = nullptr;
+    L1.nitems = L1.one.ntiles * L1.one.ksplit;
+    // pass 2: GEMM2 in chunks of up to kTcMaxColsV occupied pairs
+    L.one.nchunks = (int)pl->chunks_v.size();
+    for (int c = 0; c < L.one.nchunks; ++c) L.one.chunks[c] = pl->chunks_v[c];
+    L.one.racc_cols = pl->racc_cols_v;
+    L.one.nplus = pl->nplus;
+    L.one.wplus = pl->wplus;
+    L.one.wminus = pl->wminus;
+    L.nitems = L.one.ntiles * L.one.nchunks * L.one.ksplit;
+    T2Args t2;
+    std::memset(&t2, 0, sizeof(t2));
+    t2.Tp = ws_at<__nv_bfloat16>(pl, pl->lay.Tp);
+    t2.Tm = ws_at<__nv_bfloat16>(pl, pl->lay.Tm);
+    t2.T2 = ws_at<__nv_bfloat16>(pl, pl->lay.T2);
+    t2.K = pl->K;
+    t2.S = pl->S;
+    t2.rows_p = pl->nlp;
+    t2.rows_m = std::max(pl->nlm, 1);
+    t2.nchunks = (int)pl->chunks_v.size();
+    for (int c = 0; c < t2.nchunks; ++c) {
+      t2.chunks[c] = pl->chunks_v[c];
+      t2.off[c] = pl->chunks_v[c].t2off / 2;
+    }
+    launch_pack_t2(t2, s);
+    st = cuda_status(cudaGetLastError());
+    if (st != LADDER_OK) return st;
+    mark(pl, 1, s);
+    st = cuda_status(launch_ladder_vstore(L1, pl->S, L1.nitems, s));
+    mark(pl, 4, s);
+    if (st == LADDER_OK) st = cuda_status(launch_ladder_gemm2(L, pl->S, L.nitems, s));
+  } else {
+    L.nitems = L.one.ntiles * L.one.nchunks * L.one.ksplit;
+    mark(pl, 1, s);
+    st = cuda_status(launch_ladder_tc(L, pl->S, L.nitems, s));
+  }
   mark(pl, 2, s);
-  if (st == LADDER_OK) st = cuda_status(launch_unpack(L, L.one.ntiles * L.one.nchunks, s));
+  if (st == LADDER_OK)
+    st = cuda_status(pl->two_pass ? launch_unpack2(L, s)
+                                  : launch_unpack(L, L.one.ntiles * L.one.nchunks, s));
   mark(pl, 3, s);
   return st;
 }
@@ -754,6 +894,7 @@ ladder_status ladder_apply_batched(ladder_plan_t pl, const double *const *B,
     }
     pl->gkey = key;
   }
+  pl->last_two_pass = false;
   mark(pl, 0, s);
   mark(pl, 1, s);
   const ladder_status st = cuda_status(cudaGraphLaunch(pl->gexec, s));
@@ -804,6 +945,22 @@ ladder_status ladder_timing(ladder_plan_t pl, float *prep_ms, float *fused_ms, f
   if (prep_ms) *prep_ms = t[0];
   if (fused_ms) *fused_ms = t[1];
   if (unpack_ms) *unpack_ms = t[2];
+  return LADDER_OK;
+}
+
+ladder_status ladder_timing_passes(ladder_plan_t pl, float *pass1_ms, float *pass2_ms) {
+  if (!pl || !pl->timing || !pl->ev[0]) return LADDER_EINVAL;
+  if (cudaEventSynchronize(pl->ev[3]) != cudaSuccess) return cuda_status(cudaErrorUnknown);
+  float t1 = 0.f, t2 = 0.f;
+  if (pl->last_two_pass) {
+    if (cudaEventElapsedTime(&t1, pl->ev[1], pl->ev[4]) != cudaSuccess ||
+        cudaEventElapsedTime(&t2, pl->ev[4], pl->ev[2]) != cudaSuccess)
+      return cuda_status(cudaErrorUnknown);
+  } else if (cudaEventElapsedTime(&t1, pl->ev[1], pl->ev[2]) != cudaSuccess) {
+    return cuda_status(cudaErrorUnknown);
+  }
+  if (pass1_ms) *pass1_ms = t1;
+  if (pass2_ms) *pass2_ms = t2;
   return LADDER_OK;
 }
 

@@ -291,6 +291,7 @@ __global__ void __launch_bounds__(kThreads, 1) grad_B_tc_kernel(const __grid_con
     const int L = quad * 32 + lane;    // TMEM lane
     const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
     const int x_l = L >> 3, b_l = L & 7;
+    const uint64_t pol = l2_evict_last_policy();
     uint32_t g = 0, g_use = 0, s_use = 0;
     int nacc = 0, nflush = 0;
     bool ok = true;
@@ -321,11 +322,7 @@ __global__ void __launch_bounds__(kThreads, 1) grad_B_tc_kernel(const __grid_con
         float r[16];
         tmem_ld16(tl + kColS + ncol + c0, r);
         tmem_ld_wait();
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          double *dst = racc + (size_t)(c0 + u) * 128 + L;
-          *dst = (nflush ? *dst : 0.0) + (double)r[u];
-        }
+        flush16_f64(racc + (size_t)c0 * 128 + L, r, nflush != 0, pol);
       }
       ++nflush;
       nacc = 0;

@@ -141,7 +141,7 @@ struct DrainWatch {
 // Work item of the fused kernel: an (a 16-block, b 8-block) tile, an
 // occupied-pair chunk and a range [p0, p1) of block pairs of one molecule.
 struct Item {
-  int iA, jB, A0, B0, p0, p1;
+  int tile, iA, jB, A0, B0, p0, p1;
   TcChunk CH;
   uint32_t sc;   // TMEM columns of S and of R (nps + nms)
   double *racc;  // this item's FP64 accumulators, [col][lane]
@@ -157,6 +157,7 @@ __device__ __forceinline__ Item decode_item(const TcArgs &A, int item) {
     t -= A.nB8 - 2 * iA;
     ++iA;
   }
+  I.tile = tile;
   I.iA = iA;
   I.jB = 2 * iA + t;
   I.A0 = iA * 16;
@@ -184,7 +185,7 @@ __device__ __forceinline__ const TcArgs &item_args(const TcLaunch &Lp, int it, i
   }
 }
 
-template <int S, bool kBatch>
+template <int S, bool kBatch, bool kStoreV>
 __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_constant__ TcLaunch Lp) {
   using C = Cfg<S>;
   extern __shared__ uint8_t smem_raw[];
@@ -247,8 +248,10 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
         const uint32_t tbytes = I.sc * 32u;
         tma_prefetch_desc(&A.tmA);
         tma_prefetch_desc(&A.tmB);
-        tma_prefetch_desc(&A.tmTp);
-        tma_prefetch_desc(&A.tmTm);
+        if (!kStoreV) {
+          tma_prefetch_desc(&A.tmTp);
+          tma_prefetch_desc(&A.tmTm);
+        }
         for (int p = p0; ok && p <= p1; ++p) {
           if (p < p1) {
             int k, l;
@@ -274,7 +277,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
                 }
               }
           }
-          if (ok && p > p0) {
+          if (!kStoreV && ok && p > p0) {
             for (int piece = 0; piece < SLOTS / TPIECE; ++piece) {
               if (!(ok = mbar_wait(bars.empty(stage), phase ^ 1u, wd, kSiteTmaEmpty))) break;
               const uint32_t dst = ring + (uint32_t)stage * C::kStage;
@@ -327,7 +330,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
         const int kc = A.kc;
         const int nch_full = (A.nks + kc - 1) / kc;
         const bool split = A.xy_split != 0;
-        const uint32_t nbuf = split ? 1u : 2u;
+        const uint32_t nbuf = (kStoreV || split) ? 1u : 2u;
         for (int p = p0; ok && p <= p1; ++p) {
           if (p < p1) {
             int k, l;
@@ -343,19 +346,38 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
                   if (!(ok = mbar_wait(bars.full(stage), phase, wd, kSiteTmaFull))) break;
                   tc_fence_after();
                   const uint32_t st = ring + (uint32_t)stage * C::kStage;
-                  const uint32_t dT = tmem + (split ? 0u : (uint32_t)buf * 128u) + (tt ? 64u : 0u);
+                  if constexpr (kStoreV) {
+                    // The S slices of B sit back to back (64 rows each), so
+                    // slice p of A times slices 0..S-1-p of B is one MMA of
+                    // N = 64 (S - p) at column offset 64 p: the products of
+                    // slice order p + q land in the 64-column block p + q.
+                    // Block 0 (hi*hi) is the large accumulator, blocks 1 and
+                    // 2 the small ones; X at columns [0, 64 S), Y after it.
+                    const uint32_t dT = tmem + (tt ? (uint32_t)(64 * S) : 0u);
   #pragma unroll
-                  for (int kk = 0; kk < KSTEP / 16; ++kk)
+                    for (int kk = 0; kk < KSTEP / 16; ++kk)
   #pragma unroll
-                    for (int q = 0; q < C::kProducts; ++q) {
-                      const uint64_t ad = desc64(st + kPa(q) * A_TILE + kk * 32, hi64);
-                      const uint64_t bd = desc64(st + S * A_TILE + kPb(q) * B_TILE + kk * 32, hi64);
-                      // split: the hi*hi product into the "big" accumulator,
-                      // every smaller product into the "small" one (128 columns on)
-                      const bool small = split && q > 0;
-                      const bool first = (ks == ks0) && kk == 0 && (split ? (q <= 1) : (q == 0));
-                      mma_bf16(dT + (small ? 128u : 0u), ad, bd, id1, first ? 0u : 1u);
-                    }
+                      for (int pa = 0; pa < S; ++pa) {
+                        const uint64_t ad = desc64(st + pa * A_TILE + kk * 32, hi64);
+                        const uint64_t bd = desc64(st + S * A_TILE + kk * 32, hi64);
+                        const bool first = (ks == ks0) && kk == 0 && pa == 0;
+                        mma_bf16(dT + 64u * pa, ad, bd, idesc_bf16(128, 64 * (S - pa)), first ? 0u : 1u);
+                      }
+                  } else {
+                    const uint32_t dT = tmem + (split ? 0u : (uint32_t)buf * 128u) + (tt ? 64u : 0u);
+  #pragma unroll
+                    for (int kk = 0; kk < KSTEP / 16; ++kk)
+  #pragma unroll
+                      for (int q = 0; q < C::kProducts; ++q) {
+                        const uint64_t ad = desc64(st + kPa(q) * A_TILE + kk * 32, hi64);
+                        const uint64_t bd = desc64(st + S * A_TILE + kPb(q) * B_TILE + kk * 32, hi64);
+                        // split: the hi*hi product into the "big" accumulator,
+                        // every smaller product into the "small" one (128 columns on)
+                        const bool small = split && q > 0;
+                        const bool first = (ks == ks0) && kk == 0 && (split ? (q <= 1) : (q == 0));
+                        mma_bf16(dT + (small ? 128u : 0u), ad, bd, id1, first ? 0u : 1u);
+                      }
+                  }
                   mma_commit(bars.empty(stage));
                   if (++stage == C::kStages) {
                     stage = 0;
@@ -368,7 +390,16 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
             }
             if (!ok) break;
           }
-          if (p > p0) {
+          if (kStoreV && p > p0) {
+            // the V+- tile of block pair p-1 goes to global memory: one tiled
+            // store of its 2S planes; the tile is free again once read
+            if (!(ok = mbar_wait(bars.v_full(), v_use & 1u, wd, kSiteVFull))) break;
+            tma_store_3d(&A.tmVs, vbase, 0, 0, ((I.tile * A.nbp + (p - 1)) * 2) * S);
+            bulk_commit();
+            bulk_wait_read0();
+            mbar_arrive(bars.v_free());
+            ++v_use;
+          } else if (p > p0) {
             if (!(ok = mbar_wait(bars.v_full(), v_use & 1u, wd, kSiteVFull))) break;
             tc_fence_after();
             for (int piece = 0; ok && piece < SLOTS / TPIECE; ++piece) {
@@ -409,6 +440,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
           }
         }
       }
+      if (kStoreV) bulk_wait0();
       // every MMA of this CTA completes before TMEM is released
       mma_commit(bars.done());
       DrainWatch dw(A0args.status, Lp.timeout_ns);
@@ -421,6 +453,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
     const int L = quad * 32 + lane;    // TMEM lane
     const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
     const int a_l = L >> 3, x_l = L & 7;
+    const uint64_t pol = l2_evict_last_policy();
     uint32_t g = 0, v_use = 0, s_use = 0;
     bool ok = true;
     for (int it = it0; ok && it < nit; it += itstep) {
@@ -433,7 +466,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
       const int kc = A.kc;
       const int nch_full = (A.nks + kc - 1) / kc;
       const bool split = A.xy_split != 0;
-      const uint32_t nbuf = split ? 1u : 2u;
+      const uint32_t nbuf = (kStoreV || split) ? 1u : 2u;
       int nacc = 0, nflush = 0;
       // S (fresh GEMM2 result of one block pair) -> R (TMEM running sum, FP32)
       auto take_S = [&]() -> bool {
@@ -463,11 +496,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
           float r[16];
           tmem_ld16(tl + kColS + sc + c0, r);
           tmem_ld_wait();
-  #pragma unroll
-          for (int u = 0; u < 16; ++u) {
-            double *dst = racc + (size_t)(c0 + u) * 128 + L;
-            *dst = (nflush ? *dst : 0.0) + (double)r[u];
-          }
+          flush16_f64(racc + (size_t)c0 * 128 + L, r, nflush != 0, pol);
         }
         ++nflush;
         nacc = 0;
@@ -483,6 +512,32 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
           if (!(ok = mbar_wait(bars.cfull(buf), (g / nbuf) & 1u, wd, kSiteXYFull))) break;
           ++g;
           tc_fence_after();
+          if constexpr (kStoreV) {
+            // X = block 0 + (block 1 [+ block 2]) of the merged slice products
+            const uint32_t cX = tl + 32u * half;
+            const uint32_t cY = diag ? cX : cX + (uint32_t)(64 * S);
+  #pragma unroll
+            for (int q = 0; q < 2; ++q) {
+  #pragma unroll
+              for (int xy = 0; xy < 2; ++xy) {
+                float b0[16], b1[16], b2[16];
+                const uint32_t ca = (xy ? cY : cX) + q * 16;
+                tmem_ld16(ca, b0);
+                tmem_ld16(ca + 64u, b1);
+                if (S == 3) tmem_ld16(ca + 128u, b2);
+                tmem_ld_wait();
+                float *dst = xy ? Y : X;
+  #pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                  const float t = b0[i] + (S == 3 ? b1[i] + b2[i] : b1[i]);
+                  dst[q * 16 + i] = c ? dst[q * 16 + i] + t : t;
+                }
+              }
+            }
+            tc_fence_before();
+            mbar_arrive(bars.cfree(buf));
+            continue;
+          }
           const uint32_t cX = tl + (split ? 0u : (uint32_t)buf * 128u) + 32u * half;
           const uint32_t cY = diag ? cX : cX + 64u;
   #pragma unroll
@@ -514,7 +569,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
         }
         if (!ok) break;
         // S chains of the previous block pair (GEMM2 runs after this pair's GEMM1)
-        if (p > p0) {
+        if (!kStoreV && p > p0) {
           for (int gs = 0; ok && gs < SLOTS / TPIECE / A.s_pieces; ++gs) {
             ok = take_S();
             if (ok && nacc >= A.flush_every) flush_R();
@@ -554,8 +609,10 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
         mbar_arrive(bars.v_full());
       }
       // S chains of the last block pair, then the final FP64 flush
-      for (int gs = 0; ok && gs < SLOTS / TPIECE / A.s_pieces; ++gs) ok = take_S();
-      if (ok) flush_R();
+      if (!kStoreV) {
+        for (int gs = 0; ok && gs < SLOTS / TPIECE / A.s_pieces; ++gs) ok = take_S();
+        if (ok) flush_R();
+      }
     }
   }
 
@@ -612,43 +669,337 @@ __global__ void __launch_bounds__(128) unpack_kernel(const __grid_constant__ TcL
   }
 }
 
+// ---------------------------------------------------------------- GEMM2 from stored V+-
+// Second pass of the two-pass form.  The store mode of the fused kernel has
+// written the V+- slices of every (tile, block pair) to global memory, as
+// planes [tile][pair][sign][slice] of 128 ab rows x 64 slots.  This kernel
+// contracts them with tau+- for one chunk of up to kTcMaxColsV occupied
+// pairs of one sign (lambda+ or lambda-), so each MMA is N = the chunk's
+// columns wide and only that sign's planes are read; GEMM1 thus runs once per
+// tile instead of once per chunk.
+// Accumulation: a fresh FP32 accumulator S every s_pieces pieces (as in the
+// fused kernel), double-buffered in TMEM so that the next pieces' MMAs run
+// while the conversion warps take the last S; the running FP32 sum R lives in
+// the conversion warps' registers and is added into the FP64 accumulators in
+// the workspace every flush_every S.
+//   warp 0    TMA: per 16-slot piece, the S V planes of the sign (one 3-D box) and the
+//             chunk's tau+- rows (one bulk copy from the chunk-major copy);
+//   warp 1    MMA issuer: S+-[ab][lambda] (+)= V+-[ab][piece] T+-[lambda][piece]^T;
+//   warps 2-9 S -> R (registers) and FP64 flushes; lane = ab row, each warp
+//             owns every other group of 16 columns.
+constexpr uint32_t VP_PLANE = 128u * TPIECE * 2u;  // 4 KB: 128 ab rows x 16 slots
+constexpr uint32_t kColS1 = 256;                   // TMEM: S0 [0, 192), S1 [256, 448)
+constexpr int kGroupsV = kTcMaxColsV / 32;         // 16-column groups per conversion warp
+
+template <int S>
+struct Cfg2 {
+  static constexpr uint32_t kV = (uint32_t)S * VP_PLANE;
+  static constexpr uint32_t kT = (uint32_t)S * kTcMaxColsV * 32u;
+  static constexpr uint32_t kStage = (kV + kT + 1023u) / 1024u * 1024u;
+  static constexpr int kStages = (229376u / kStage) < 10u ? (int)(229376u / kStage) : 10;  // <= 224 KB
+  static constexpr uint32_t kRing = kStage * kStages;
+  static constexpr uint32_t kSmem = kRing + 256 + 1024;
+  static constexpr int kProducts = (S == 2) ? 3 : 6;
+};
+static_assert(kColS1 + kTcMaxColsV <= 512, "TMEM columns of the GEMM2 kernel");
+static_assert(kTcMaxColsV % 32 == 0, "column groups");
+static_assert(8 * (2 * 10 + Bars::kCount) + 8 <= 256, "barrier area");
+
+template <int S>
+__global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_constant__ TcLaunch Lp) {
+  using C = Cfg2<S>;
+  static_assert(C::kStages >= 3 && C::kStages <= 10, "ring depth");
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
+  uint8_t *smem = smem_raw + pad;
+  const uint32_t ring = raw + pad;
+  Bars bars{ring + C::kRing, C::kStages};
+  uint32_t *tmem_holder =
+      reinterpret_cast<uint32_t *>(smem + C::kRing + 8 * (2 * C::kStages + Bars::kCount));
+  int *abort_flag = reinterpret_cast<int *>(tmem_holder + 1);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::kStages; ++s) {
+      mbar_init(bars.full(s), 1);
+      mbar_init(bars.empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(bars.cfull(b), 1);     // S buffer b holds a finished accumulator
+      mbar_init(bars.cfree(b), kEpi);  // S buffer b has been taken
+    }
+    mbar_init(bars.done(), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_holder), 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+  const int it0 = blockIdx.x, itstep = gridDim.x, nit = Lp.nitems;
+  const TcArgs &A = Lp.one;
+  const Watchdog wd{A.status, abort_flag, Lp.timeout_ns};
+  constexpr int kPieces = SLOTS / TPIECE;
+
+  if (warp == 0) {
+    // ================================================================ TMA producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t armed = 0, armed_par = 0;
+      bool ok = true;
+      tma_prefetch_desc(&A.tmVl);
+      for (int it = it0; ok && it < nit; it += itstep) {
+        const Item I = decode_item(A, it);
+        const TcChunk &CH = I.CH;
+        const uint32_t tbytes = I.sc * 32u;
+        const int sg = CH.nps > 0 ? 0 : 1;  // the chunk's sign
+        for (int p = I.p0; ok && p < I.p1; ++p) {
+          const int z = ((I.tile * A.nbp + p) * 2 + sg) * S;
+          for (int piece = 0; piece < kPieces; ++piece) {
+            if (!(ok = mbar_wait(bars.empty(stage), phase ^ 1u, wd, kSiteTmaEmpty))) break;
+            const uint32_t dst = ring + (uint32_t)stage * C::kStage;
+            mbar_arrive_expect_tx(bars.full(stage), C::kV + (uint32_t)S * tbytes);
+            armed |= 1u << stage;
+            armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+            tma_load_3d(dst, &A.tmVl, bars.full(stage), piece * TPIECE, 0, z);
+            // the chunk's tau+- rows of this piece, every slice: one bulk copy
+            bulk_load(dst + C::kV,
+                      A.T2 + CH.t2off + (size_t)(p * kPieces + piece) * S * tbytes,
+                      (uint32_t)S * tbytes, bars.full(stage));
+            if (++stage == C::kStages) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+        }
+      }
+      if (!ok) {
+        DrainWatch dw(A.status, Lp.timeout_ns);
+        for (int s = 0; s < C::kStages; ++s)
+          if (armed & (1u << s)) mbar_wait(bars.full(s), (armed_par >> s) & 1u, dw.wd, kSiteTmaFull);
+      }
+    }
+  } else if (warp == 1) {
+    // ================================================================ MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0, g = 0;  // g: S accumulators started
+      const uint32_t hi32 = desc_hi(256, kSwizzle32);
+      bool ok = true;
+      for (int it = it0; ok && it < nit; it += itstep) {
+        const Item I = decode_item(A, it);
+        const TcChunk &CH = I.CH;
+        const uint32_t id = idesc_bf16(128, (int)I.sc);
+        const uint32_t tbytes = I.sc * 32u;
+        for (int p = I.p0; ok && p < I.p1; ++p)
+          for (int piece = 0; ok && piece < kPieces; ++piece) {
+            const bool first = (piece % A.s_pieces) == 0;
+            const uint32_t buf = g & 1u;
+            if (first) {
+              if (!(ok = mbar_wait(bars.cfree(buf), ((g >> 1) & 1u) ^ 1u, wd, kSiteRFree))) break;
+              tc_fence_after();
+            }
+            if (!(ok = mbar_wait(bars.full(stage), phase, wd, kSiteTmaFull))) break;
+            tc_fence_after();
+            const uint32_t st = ring + (uint32_t)stage * C::kStage;
+            const uint32_t dS = tmem + buf * kColS1;
+#pragma unroll
+            for (int q = 0; q < C::kProducts; ++q)
+              mma_bf16(dS, desc64(st + (uint32_t)kPa(q) * VP_PLANE, hi32),
+                       desc64(st + C::kV + kPb(q) * tbytes, hi32), id, (first && q == 0) ? 0u : 1u);
+            mma_commit(bars.empty(stage));
+            if (++stage == C::kStages) {
+              stage = 0;
+              phase ^= 1u;
+            }
+            if ((piece + 1) % A.s_pieces == 0) {
+              mma_commit(bars.cfull(buf));
+              ++g;
+            }
+          }
+      }
+      mma_commit(bars.done());
+      DrainWatch dw(A.status, Lp.timeout_ns);
+      mbar_wait(bars.done(), 0, dw.wd, kSiteRFull);
+    }
+  } else {
+    // ================================================================ S -> R -> FP64
+    const int quad = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int L = quad * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
+    uint32_t g = 0;
+    bool ok = true;
+    const uint64_t pol = l2_evict_last_policy();
+    float R[kGroupsV * 16];
+    for (int it = it0; ok && it < nit; it += itstep) {
+      const Item I = decode_item(A, it);
+      const int sc = (int)I.sc;
+      const int ng = (sc - 16 * half + 31) / 32;  // this warp's groups: columns 16*half + 32*k
+      double *racc = I.racc + L;
+      int nacc = 0, nflush = 0;
+#pragma unroll
+      for (int u = 0; u < kGroupsV * 16; ++u) R[u] = 0.f;
+      const int ntake = (I.p1 - I.p0) * (kPieces / A.s_pieces);
+      for (int t = 0; ok && t < ntake; ++t) {
+        const uint32_t buf = g & 1u;
+        if (!(ok = mbar_wait(bars.cfull(buf), (g >> 1) & 1u, wd, kSiteRFull))) break;
+        ++g;
+        tc_fence_after();
+        const uint32_t cS = tl + buf * kColS1 + 16u * half;
+#pragma unroll
+        for (int k = 0; k < kGroupsV; k += 2) {
+          float a[16], b[16];
+          if (k < ng) tmem_ld16(cS + 32u * k, a);
+          if (k + 1 < ng) tmem_ld16(cS + 32u * (k + 1), b);
+          tmem_ld_wait();
+          if (k < ng) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) R[k * 16 + u] += a[u];
+          }
+          if (k + 1 < ng) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) R[(k + 1) * 16 + u] += b[u];
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(bars.cfree(buf));
+        if (++nacc >= A.flush_every || t + 1 == ntake) {
+#pragma unroll
+          for (int k = 0; k < kGroupsV; ++k)
+            if (k < ng) flush16_f64(racc + (size_t)(16 * half + 32 * k) * 128, &R[k * 16], nflush != 0, pol);
+#pragma unroll
+          for (int u = 0; u < kGroupsV * 16; ++u) R[u] = 0.f;
+          ++nflush;
+          nacc = 0;
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// ---------------------------------------------------------------- unpack (two-pass)
+// R_ij^ab from the FP64 accumulators of the GEMM2 pass, whose chunks hold
+// lambda+ columns [c wplus, (c+1) wplus) or lambda- columns [c wminus, ...):
+// block (tile, plus chunk c) writes every (i <= j) of that lambda+ range,
+// taking R- from the minus chunk of lambda- = j(j-1)/2 + i.  Lane = ab slot,
+// as in unpack_kernel; every element of R is written once.
+__global__ void __launch_bounds__(128) unpack2_kernel(const __grid_constant__ TcLaunch Lp) {
+  const TcArgs &A = Lp.one;
+  const int tile = blockIdx.x / A.nplus, cp = blockIdx.x % A.nplus;
+  int iA = 0, t = tile;
+  while (t >= A.nB8 - 2 * iA) {
+    t -= A.nB8 - 2 * iA;
+    ++iA;
+  }
+  const int jB = 2 * iA + t;
+  const int L = threadIdx.x;
+  const int a = iA * 16 + (L >> 3), b = jB * CB + (L & 7);
+  const bool diag_ab = (jB >> 1) == iA;
+  if (!(a < A.v && b < A.v && (!diag_ab || a <= b))) return;
+  const size_t per_item = (size_t)128 * A.racc_cols;
+  // work item (tile, chunk, range k) sits at ((tile * nchunks + chunk) * ksplit + k)
+  const double *base = A.racc + (size_t)tile * A.nchunks * A.ksplit * per_item + L;
+  const size_t vv = (size_t)A.v * A.v, o = (size_t)A.o;
+  const TcChunk CH = A.chunks[cp];
+  int i = 0, j = 0;
+  lam_plus(CH.lp0, i, j);
+  for (int c = 0; c < CH.np; ++c) {
+    double pv = 0.0, mv = 0.0;
+    const double *bp = base + ((size_t)cp * A.ksplit) * per_item + (size_t)c * 128;
+    for (int k = 0; k < A.ksplit; ++k) pv += bp[k * per_item];
+    if (i < j && a != b) {
+      const int lm = pneg(j) + i;
+      const int cm = A.nplus + lm / A.wminus;
+      const double *bm = base + ((size_t)cm * A.ksplit) * per_item + (size_t)(lm % A.wminus) * 128;
+      for (int k = 0; k < A.ksplit; ++k) mv += bm[k * per_item];
+    }
+    A.R[(i * o + j) * vv + (size_t)a * A.v + b] = pv + mv;
+    A.R[(i * o + j) * vv + (size_t)b * A.v + a] = pv - mv;
+    A.R[(j * o + i) * vv + (size_t)b * A.v + a] = pv + mv;
+    A.R[(j * o + i) * vv + (size_t)a * A.v + b] = pv - mv;
+    if (++i > j) {
+      ++j;
+      i = 0;
+    }
+  }
+}
+
 }  // namespace
 
 uint32_t tc_smem_bytes(int nslices) {
   return nslices == 2 ? Cfg<2>::kSmem : Cfg<3>::kSmem;
 }
 
-cudaError_t tc_init_attributes(int nslices) {
+template <int S>
+static cudaError_t set_smem_attrs() {
   const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e;
-  if (nslices == 2) {
-    e = cudaFuncSetAttribute(ladder_tc_kernel<2, false>, at, (int)Cfg<2>::kSmem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(ladder_tc_kernel<2, true>, at, (int)Cfg<2>::kSmem);
-  } else {
-    e = cudaFuncSetAttribute(ladder_tc_kernel<3, false>, at, (int)Cfg<3>::kSmem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(ladder_tc_kernel<3, true>, at, (int)Cfg<3>::kSmem);
-  }
+  cudaError_t e = cudaFuncSetAttribute(ladder_tc_kernel<S, false, false>, at, (int)Cfg<S>::kSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(ladder_tc_kernel<S, true, false>, at, (int)Cfg<S>::kSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(ladder_tc_kernel<S, false, true>, at, (int)Cfg<S>::kSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(ladder_gemm2_kernel<S>, at, (int)Cfg2<S>::kSmem);
   return e;
+}
+
+cudaError_t tc_init_attributes(int nslices) {
+  return nslices == 2 ? set_smem_attrs<2>() : set_smem_attrs<3>();
 }
 
 cudaError_t launch_ladder_tc(const TcLaunch &a, int nslices, int grid, cudaStream_t s) {
   const bool batch = a.mols != nullptr;
   if (nslices == 2) {
     if (batch)
-      ladder_tc_kernel<2, true><<<grid, kThreads, Cfg<2>::kSmem, s>>>(a);
+      ladder_tc_kernel<2, true, false><<<grid, kThreads, Cfg<2>::kSmem, s>>>(a);
     else
-      ladder_tc_kernel<2, false><<<grid, kThreads, Cfg<2>::kSmem, s>>>(a);
+      ladder_tc_kernel<2, false, false><<<grid, kThreads, Cfg<2>::kSmem, s>>>(a);
   } else {
     if (batch)
-      ladder_tc_kernel<3, true><<<grid, kThreads, Cfg<3>::kSmem, s>>>(a);
+      ladder_tc_kernel<3, true, false><<<grid, kThreads, Cfg<3>::kSmem, s>>>(a);
     else
-      ladder_tc_kernel<3, false><<<grid, kThreads, Cfg<3>::kSmem, s>>>(a);
+      ladder_tc_kernel<3, false, false><<<grid, kThreads, Cfg<3>::kSmem, s>>>(a);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ladder_vstore(const TcLaunch &a, int nslices, int grid, cudaStream_t s) {
+  if (a.mols) return cudaErrorInvalidValue;
+  if (nslices == 2)
+    ladder_tc_kernel<2, false, true><<<grid, kThreads, Cfg<2>::kSmem, s>>>(a);
+  else
+    ladder_tc_kernel<3, false, true><<<grid, kThreads, Cfg<3>::kSmem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ladder_gemm2(const TcLaunch &a, int nslices, int grid, cudaStream_t s) {
+  if (a.mols) return cudaErrorInvalidValue;
+  if (nslices == 2)
+    ladder_gemm2_kernel<2><<<grid, kThreads, Cfg2<2>::kSmem, s>>>(a);
+  else
+    ladder_gemm2_kernel<3><<<grid, kThreads, Cfg2<3>::kSmem, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_unpack(const TcLaunch &a, int nblocks, cudaStream_t s) {
   unpack_kernel<<<nblocks, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack2(const TcLaunch &a, cudaStream_t s) {
+  if (a.mols) return cudaErrorInvalidValue;
+  unpack2_kernel<<<a.one.ntiles * a.one.nplus, 128, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -111,6 +111,43 @@ void launch_pack_tpm_bf16(int o, int v, int K, int nslices, int rows_p, int rows
     pack_tpm_kernel<__nv_bfloat16, 3><<<grid, 256, 0, s>>>(o, v, K, nlp, nlm, tau, Tp, Tm, sp, sm);
 }
 
+// ---------------------------------------------------------------- tau+- per chunk
+// Chunk-major copy of the tau+- slices for the GEMM2 pass of the two-pass
+// form: for chunk c, 16-slot piece x and slice s, the chunk's sc rows
+// (lambda+ rows, padding, lambda- rows, padding) of 32 bytes each, stored
+// contiguously and already in the 32-byte-swizzled order of shared memory
+// (the two 16-byte halves of row r swapped when bit 2 of r is set), so one
+// bulk copy per piece fills a GEMM2 operand.  Padding rows are zero.
+__global__ void pack_t2_kernel(const __grid_constant__ T2Args a) {
+  const TcChunk CH = a.chunks[blockIdx.y];
+  const int sc = CH.nps + CH.nms;
+  const size_t units = (size_t)(a.K / 16) * a.S * sc * 2;
+  const uint4 *Tp = reinterpret_cast<const uint4 *>(a.Tp);
+  const uint4 *Tm = reinterpret_cast<const uint4 *>(a.Tm);
+  uint4 *dst = reinterpret_cast<uint4 *>(a.T2 + a.off[blockIdx.y]);
+  const size_t K8 = (size_t)a.K / 8;  // 16-byte units per row of Tp / Tm
+  for (size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x; u < units;
+       u += (size_t)gridDim.x * blockDim.x) {
+    const int h = (int)(u & 1);
+    size_t t = u >> 1;
+    const int row = (int)(t % sc);
+    t /= sc;
+    const int s = (int)(t % a.S);
+    const size_t xp = t / a.S;
+    uint4 val = make_uint4(0, 0, 0, 0);
+    if (row < CH.np)
+      val = Tp[((size_t)s * a.rows_p + CH.lp0 + row) * K8 + xp * 2 + h];
+    else if (row >= CH.nps && row - CH.nps < CH.nm)
+      val = Tm[((size_t)s * a.rows_m + CH.lm0 + (row - CH.nps)) * K8 + xp * 2 + h];
+    dst[((xp * a.S + s) * sc + row) * 2 + (h ^ ((row >> 2) & 1))] = val;
+  }
+}
+
+void launch_pack_t2(const T2Args &a, cudaStream_t s) {
+  dim3 grid(1024, a.nchunks);
+  pack_t2_kernel<<<grid, 256, 0, s>>>(a);
+}
+
 // ---------------------------------------------------------------- B slices
 // Bt[q][a][c][P] = slice q of B[P][a][c]; a, c < vp (zero beyond v),
 // P < Np (zero beyond N).  32x32 tiles through shared memory so both the

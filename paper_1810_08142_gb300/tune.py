@@ -2,7 +2,8 @@
 
 For one shape (o, v, N_aux) it tries each precision mode (BF16X3, BF16X6)
 with several launch parameters (ladder_tuning: GEMM1 chain length kc, GEMM2
-pieces per fresh accumulator, block-pair split) and keeps the fastest one
+pieces per fresh accumulator; the fused or the two-pass form where the shape
+needs several occupied-pair chunks) and keeps the fastest one
 whose relative Frobenius error in R, measured against the FP64 GPU path on
 seeded random inputs, stays below half the tolerance (a margin for inputs
 that differ from the proxy's).  The FP32 accumulation error of
@@ -57,13 +58,15 @@ def lookup(o: int, v: int, naux: int):
     return e["mode"], e["tuning"]
 
 
-def candidates():
+def candidates(forms=(0,)):
+    """(mode, tuning) pairs; `forms` lists the two_pass values to try."""
     out = []
-    for kc in (16, 32):
-        out.append(("bf16x3", {"kc": kc, "s_pieces": 4, "xy_split": 1}))
-    for kc in (2, 4, 8):
-        for sp in (1, 2):
-            out.append(("bf16x6", {"kc": kc, "s_pieces": sp, "xy_split": 1}))
+    for tp in forms:
+        for kc in (16, 32):
+            out.append(("bf16x3", {"kc": kc, "s_pieces": 4, "xy_split": 1, "two_pass": tp}))
+        for kc in (2, 4, 8):
+            for sp in (1, 2):
+                out.append(("bf16x6", {"kc": kc, "s_pieces": sp, "xy_split": 1, "two_pass": tp}))
     return out
 
 
@@ -104,13 +107,18 @@ def tune(o: int, v: int, naux: int, tol: float = 1e-6, reps: int = 2, seed: int 
     nref = torch.linalg.vector_norm(ref).item()
     B, tau = _inputs(o, v, naux, seed + 1, dev)
     R = torch.empty_like(tau)
+    # the two-pass form is a candidate where the plan would choose it (the
+    # fused kernel needs several chunks and the stored tiles fit)
+    from . import ladder_get_tuning
+    L0 = Ladder(o, v, naux, mode="bf16x6", device=dev)
+    forms = (0, 1) if ladder_get_tuning(L0.plan).two_pass else (0,)
+    L0.close()
     results = []
-    for mode, tun in candidates():
+    for mode, tun in candidates(forms):
         Lp = Ladder(o, vp, naux, mode=mode, device=dev, tuning=tun)
         err = torch.linalg.vector_norm(Lp.apply(Bp, taup) - ref).item() / nref
         Lp.close()
         L = Ladder(o, v, naux, mode=mode, device=dev, tuning=tun)
-        from . import ladder_get_tuning
         full = ladder_get_tuning(L.plan).as_dict()
         ms = _time_ms(L, B, tau, R, reps)
         L.close()

@@ -138,6 +138,11 @@ def falg(o: int, v: int, naux: int) -> float:
     return g1 + g2
 
 
+def falg_gemm1(o: int, v: int, naux: int) -> float:
+    """The integral-tile part of falg: 2 P+(v) v^2 N_aux."""
+    return 2.0 * _ppos(v) * v * v * naux
+
+
 def dense_flops(o: int, v: int, naux: int) -> float:
     """Flops of the plain definition (all ordered index pairs): 2 v^4 N + 2 o^2 v^4."""
     return 2.0 * v ** 4 * naux + 2.0 * o * o * v ** 4

@@ -66,3 +66,43 @@ def test_tc_dimer_full(lad, mode):
     err = rel_fro(R_g, R_o)
     print("%s dimer: rel-F %.3e  |dE| %.3e  E %.6e" % (mode, err, abs(E_g - E_o), E_o))
     assert err < TOL[mode]
+
+
+# Shapes whose occupied pairs need several chunks of the fused kernel: both
+# forms (fused with GEMM1 recomputed per chunk, and the two-pass form with the
+# V+- tiles stored in the workspace) are checked against the oracle.
+MULTI_CHUNK = [
+    (12, 32, 40, 13),    # two chunks in the fused form, one in the two-pass form
+    (20, 40, 50, 16),
+    (24, 17, 33, 9),     # ragged v (one 16-block, padded)
+    (34, 24, 60, 5),     # the mid workload's o: ten fused chunks, five two-pass
+]
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "bf16x6"])
+@pytest.mark.parametrize("two_pass", [0, 1])
+@pytest.mark.parametrize("o,v,n,seed", MULTI_CHUNK)
+def test_tc_forms_match_oracle(lad, mode, two_pass, o, v, n, seed):
+    x = synthetic.make_inputs(o, v, n, seed)
+    L = lad.Ladder(o, v, n, mode=mode, tuning={"two_pass": two_pass})
+    assert lad.ladder_get_tuning(L.plan).two_pass == two_pass
+    _, R_g, E_g = run_forward(L, x)
+    R_o = oracle.ladder(x.B, oracle.tau(x.t1, x.t2))
+    err = rel_fro(R_g, R_o)
+    print("%s two_pass=%d o=%d v=%d n=%d: rel-F %.3e" % (mode, two_pass, o, v, n, err))
+    assert err < TOL[mode]
+    assert np.array_equal(R_g, R_g.transpose(1, 0, 3, 2))
+
+
+@pytest.mark.parametrize("ksplit", [1, 3])
+def test_two_pass_block_pair_split(lad, ksplit):
+    """The GEMM2 pass with its block pairs split over work units (FP64 sums
+    of the ranges in the unpack kernel) against the unsplit pass."""
+    o, v, n, seed = 16, 48, 64, 21
+    x = synthetic.make_inputs(o, v, n, seed)
+    L = lad.Ladder(o, v, n, mode="bf16x6", tuning={"two_pass": 1, "ksplit": ksplit})
+    _, R_g, _ = run_forward(L, x)
+    R_o = oracle.ladder(x.B, oracle.tau(x.t1, x.t2))
+    err = rel_fro(R_g, R_o)
+    print("two_pass ksplit=%d: rel-F %.3e" % (ksplit, err))
+    assert err < TOL["bf16x6"]
