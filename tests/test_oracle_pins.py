@@ -162,6 +162,22 @@ def _E(B, tau, W):
     return float(np.sum(W * oracle.ladder(B, tau)))
 
 
+def test_energy_sum_is_compensated():
+    """E_L of terms 1e16, 1, -1e16, 1 (o = 1, v = 2, symmetric t2 = 1 so that
+    W = t2): the exact sum is 2; a plain running sum in FP64 gives 1 (1e16 + 1
+    rounds back to 1e16).  The oracle's sum must give 2."""
+    R = np.array([1e16, 1.0, -1e16, 1.0]).reshape(1, 1, 2, 2)
+    t2 = np.ones((1, 1, 2, 2))
+    assert oracle.energy(R, t2) == 2.0
+    # and a long sum: n copies of (big, small, -big) leave exactly n * small
+    n = 1000
+    R = np.tile(np.array([1e15, 0.25, -1e15, 0.25]), n).reshape(1, 1, 2 * n, 2)
+    t2 = np.ones((1, 1, 2 * n, 2 * n))
+    Rf = np.zeros((1, 1, 2 * n, 2 * n))
+    Rf[0, 0, :, :2] = R[0, 0]
+    assert oracle.energy(Rf, t2) == 0.5 * n
+
+
 def test_grad_euler_identities(grad_case):
     B, tau, W = grad_case
     E = _E(B, tau, W)
