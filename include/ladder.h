@@ -73,7 +73,8 @@ ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out);
  *   kc          GEMM1 K-steps (32 auxiliary functions each) per FP32
  *               accumulation chain, >= 1;
  *   s_pieces    16-slot GEMM2 pieces per fresh FP32 accumulator: 1, 2 or 4;
- *   flush_every FP32 accumulators summed before an FP64 flush, >= 1;
+ *   flush_every FP32 accumulators summed before a flush into the
+ *               double-single (FP32 pair, about 48-bit) sums, >= 1;
  *   ksplit      block-pair ranges per work unit (more CTAs for small shapes), >= 1;
  *   xy_split    1: separate GEMM1 accumulators for the hi*hi slice product and
  *               the smaller products; 0: one accumulator, two buffers;

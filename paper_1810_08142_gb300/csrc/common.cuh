@@ -59,6 +59,9 @@ constexpr int kMaxChunks = 64;
 // each of which may itself suspend for a hardware-defined time).
 constexpr uint32_t kSpinLimit = 1u << 26;
 
+// Value of a double-single accumulator (hi, lo).
+__host__ __device__ inline double ds_value(float2 v) { return (double)v.x + (double)v.y; }
+
 __device__ __forceinline__ void record_status(int *status, int site) {
   if (status) atomicCAS(status, 0, site);
 }

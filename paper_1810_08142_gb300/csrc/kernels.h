@@ -66,7 +66,7 @@ struct GradTcArgs {
   CUtensorMap tmT;   // tau slices [S][y][d][ij], box (32 ij, 8 d, 8 y)
   CUtensorMap tmBs;  // B slices [S][P][D][b][dl], box (16 (b,dl), 1 D, 16 P), 32-byte swizzle
   double *dB;        // [N][v][v]
-  double *racc;      // FP64 sums, [item][128 cols][128 lanes]
+  float2 *racc;      // double-single sums, [item][128 cols][128 lanes]
   int *status;
   int o, v, N, vp, Np, IJp, nks, nY8, ntiles, npc;
   int kc, s_pieces, flush_every;
@@ -92,12 +92,12 @@ struct TcArgs {
   CUtensorMap tmB;   // B slices, box (32 aux, 8 d, 8 b)
   CUtensorMap tmTp;  // tau+ slices [S][lambda+][K], box (16 slots, 16 rows, 1)
   CUtensorMap tmTm;  // tau- slices [S][lambda-][K]
-  CUtensorMap tmVs;  // stored V+- planes [tile][pair][sign][slice][128 rows][64 slots]:
-                     // store box (64, 128, 2S), 128-byte swizzle
-  CUtensorMap tmVl;  // the same planes, load box (16 slots, 128 rows, S): one sign, 32-byte swizzle
+  CUtensorMap tmVl;  // stored V+- planes [tile][pair][sign][slice][128 rows][64 slots],
+                     // load box (16 slots, 128 rows, S): one sign, 32-byte swizzle
+  __nv_bfloat16 *Vst;  // the same planes, written by the storing pass
   const uint8_t *T2; // two-pass GEMM2: chunk-major tau+- (pack_t2)
   double *R;
-  double *racc;      // FP64 accumulators, [item][col][128 lanes], racc_cols columns per item
+  float2 *racc;      // double-single accumulators, [item][col][128 lanes], racc_cols columns per item
   int *status;
   int o, v, vp, Np, K, nbp;
   int nks;           // Np / 32
@@ -107,7 +107,7 @@ struct TcArgs {
   int kc;            // GEMM1 K-steps (of 32 aux functions) per FP32 accumulation chain
   int xy_split;      // GEMM1: separate accumulators for hi*hi and the smaller products
   int s_pieces;      // 16-slot pieces of GEMM2 per fresh S accumulator (1, 2 or 4)
-  int flush_every;   // S accumulators summed in FP32 before an FP64 flush
+  int flush_every;   // S accumulators summed in FP32 before a flush to the double-single sums
   int nplus, wplus, wminus;  // two-pass GEMM2: plus chunks first, lambda columns per chunk
   unsigned long long timeout_ns;
   TcChunk chunks[kMaxChunks];

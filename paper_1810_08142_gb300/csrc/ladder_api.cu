@@ -79,7 +79,7 @@ struct ladder_plan_s {
   int two_pass = 0, vsplit = 1, racc_cols_v = 0, nplus = 0, wplus = 0, wminus = 0;
   bool last_two_pass = false;
   std::vector<TcChunk> chunks_v;
-  CUtensorMap tmA, tmB, tmTp, tmTm, tmVs, tmVl;
+  CUtensorMap tmA, tmB, tmTp, tmTm, tmVl;
   CUtensorMap tmGW, tmGT, tmGBs;  // split-BF16 dB operands
   int g_IJp = 0, g_Np = 0, g_ntiles = 0, g_npc = 0;
   Layout lay;
@@ -225,7 +225,7 @@ void compute_layout(ladder_plan_s *pl) {
     off = align_up(off + S * pl->nlp * pl->K * 2, 1024);
     L.Tm = off;
     off = align_up(off + S * std::max(pl->nlm, 1) * pl->K * 2, 1024);
-    L.slab = off;  // FP64 accumulators of the tensor-core kernel
+    L.slab = off;  // double-single accumulators of the tensor-core kernels
     const size_t nch = pl->two_pass ? pl->chunks_v.size() : pl->chunks_tc.size();
     const size_t cols = pl->two_pass ? pl->racc_cols_v : pl->racc_cols;
     off = align_up(off + (size_t)pl->ntiles_tc * nch * pl->ksplit * 128 * cols * sizeof(double), 1024);
@@ -281,12 +281,16 @@ const char *ladder_status_string(ladder_status s) {
   return "unknown status";
 }
 
-// Block-pair ranges per (tile, chunk) so that small problems give every SM work.
+// Block-pair ranges per (tile, chunk): enough work units that small problems
+// give every SM work; in the two-pass form also ranges of about 160 block
+// pairs, which the GEMM2 kernel walks range-major so that the resident CTAs
+// share their tau+- and V+- reads in L2.
 static int auto_ksplit(const ladder_plan_s *pl) {
   const int nch = (int)(pl->two_pass ? pl->chunks_v.size() : pl->chunks_tc.size());
   const int items = pl->ntiles_tc * nch;
-  const int ks = (2 * pl->sm_count + items - 1) / items;
-  return std::max(1, std::min(ks, pl->nbp / 4));
+  int ks = (2 * pl->sm_count + items - 1) / items;
+  if (pl->two_pass) ks = std::max(ks, pl->nbp / 160);
+  return std::max(1, std::min(ks, std::max(1, pl->nbp / 4)));
 }
 
 // Block-pair ranges per tile of the storing pass (no accumulators depend on
@@ -444,9 +448,7 @@ static ladder_status encode_maps(ladder_plan_s *pl, char *w) {
   if (!ok) return LADDER_ECUDA;
   if (pl->two_pass) {
     const uint64_t planes = (uint64_t)pl->ntiles_tc * pl->nbp * 2 * S;
-    const bool okv = encode3d(&pl->tmVs, w + pl->lay.Vg, SLOTS, 128, planes, SLOTS, 128,
-                              (uint32_t)(2 * S), CU_TENSOR_MAP_SWIZZLE_128B) &&
-                     encode3d(&pl->tmVl, w + pl->lay.Vg, SLOTS, 128, planes, 16, 128, (uint32_t)S,
+    const bool okv = encode3d(&pl->tmVl, w + pl->lay.Vg, SLOTS, 128, planes, 16, 128, (uint32_t)S,
                               CU_TENSOR_MAP_SWIZZLE_32B);
     if (!okv) return LADDER_ECUDA;
   }
@@ -557,8 +559,8 @@ static TcArgs tc_args(const ladder_plan_s *pl, double *R, int *status) {
   a.tmB = pl->tmB;
   a.tmTp = pl->tmTp;
   a.tmTm = pl->tmTm;
-  a.tmVs = pl->tmVs;
   a.tmVl = pl->tmVl;
+  a.Vst = pl->two_pass ? ws_at<__nv_bfloat16>(pl, pl->lay.Vg) : nullptr;
   a.T2 = pl->two_pass ? ws_at<uint8_t>(pl, pl->lay.T2) : nullptr;
   a.R = R;
   a.status = status;
@@ -574,7 +576,7 @@ static TcArgs tc_args(const ladder_plan_s *pl, double *R, int *status) {
   a.ntiles = pl->ntiles_tc;
   a.nchunks = (int)pl->chunks_tc.size();
   a.ksplit = pl->ksplit;
-  a.racc = ws_at<double>(pl, pl->lay.slab);
+  a.racc = ws_at<float2>(pl, pl->lay.slab);
   a.racc_cols = pl->racc_cols;
   a.kc = pl->kc;
   a.xy_split = pl->xy_split;
@@ -720,7 +722,7 @@ ladder_status ladder_backward(ladder_plan_t pl, const double *B, const double *t
     g.tmT = pl->tmGT;
     g.tmBs = pl->tmGBs;
     g.dB = dB;
-    g.racc = ws_at<double>(pl, pl->lay.gacc);
+    g.racc = ws_at<float2>(pl, pl->lay.gacc);
     g.status = ws_at<int>(pl, pl->lay.status);
     g.o = pl->o;
     g.v = pl->v;

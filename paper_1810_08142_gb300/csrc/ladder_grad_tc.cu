@@ -18,7 +18,7 @@
 //       conversion warps into a TMEM running sum and flushed to FP64.
 // Accumulation chains are short for the same reason as in the forward kernel
 // (the tensor core's FP32 accumulation error grows with the MMAs per
-// accumulator).  An unpack kernel writes dB = 2 x the FP64 sums.
+// accumulator).  An unpack kernel writes dB = 2 x the double-single sums.
 #include "kernels.h"
 #include "tc_ptx.cuh"
 
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kThreads, 1) grad_B_tc_kernel(const __grid_con
   const int P0 = pc * kGradTcPChunk;
   const uint32_t ncol = (uint32_t)min(kGradTcPChunk, A.Np - P0);  // multiple of 16
   const int nb = A.vp / CB, nq = nb * nb;                          // (b, d) blocks
-  double *racc = A.racc + (size_t)item * 128 * kGradTcPChunk;
+  float2 *racc = A.racc + (size_t)item * 128 * kGradTcPChunk;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::kStages; ++s) {
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(kThreads, 1) grad_B_tc_kernel(const __grid_con
         float r[16];
         tmem_ld16(tl + kColS + ncol + c0, r);
         tmem_ld_wait();
-        flush16_f64(racc + (size_t)c0 * 128 + L, r, nflush != 0, pol);
+        flush16_ds(racc + (size_t)c0 * 128 + L, r, nflush != 0, pol);
       }
       ++nflush;
       nacc = 0;
@@ -387,18 +387,18 @@ __global__ void __launch_bounds__(kThreads, 1) grad_B_tc_kernel(const __grid_con
   }
 }
 
-// dB[P][x][y] = 2 x the FP64 sum of work unit (tile, chunk); lane = (x, y).
+// dB[P][x][y] = 2 x the double-single sum of work unit (tile, chunk); lane = (x, y).
 __global__ void __launch_bounds__(128) grad_unpack_kernel(const __grid_constant__ GradTcArgs A) {
   const int item = blockIdx.x;
   const int pc = item % A.npc, tile = item / A.npc;
   const int L = threadIdx.x;
   const int x = (tile / A.nY8) * 16 + (L >> 3), y = (tile % A.nY8) * CB + (L & 7);
   if (x >= A.v || y >= A.v) return;
-  const double *src = A.racc + (size_t)item * 128 * kGradTcPChunk + L;
+  const float2 *src = A.racc + (size_t)item * 128 * kGradTcPChunk + L;
   const int P0 = pc * kGradTcPChunk;
   const int n = min(kGradTcPChunk, A.N - P0);
   for (int c = 0; c < n; ++c)
-    A.dB[((size_t)(P0 + c) * A.v + x) * A.v + y] = 2.0 * src[(size_t)c * 128];
+    A.dB[((size_t)(P0 + c) * A.v + x) * A.v + y] = 2.0 * ds_value(src[(size_t)c * 128]);
 }
 
 }  // namespace

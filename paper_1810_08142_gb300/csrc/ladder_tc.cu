@@ -21,9 +21,9 @@
 //   GEMM2 (K = slots) starts a fresh TMEM accumulator S every `s_pieces`
 //         pieces of 16 slots (a block pair has 4);
 //         the conversion warps add S into a TMEM running sum R (FP32, round to
-//         nearest) and every `flush_every` block pairs add R into an FP64
-//         accumulator in the workspace.
-// A separate unpack kernel turns the FP64 accumulators into R_ij^ab.
+//         nearest) and every `flush_every` S add R into a double-single
+//         accumulator (an FP32 pair updated with TwoSum) in the workspace.
+// A separate unpack kernel turns the accumulators into R_ij^ab in FP64.
 //
 // One CTA owns 128 virtual pairs (a in a 16-block, b in an 8-block), one
 // chunk of occupied pairs (at most 128 TMEM columns) and one range of block
@@ -37,7 +37,7 @@
 //             columns: b = 0-3 or 4-7 of X and Y, every other 16 columns of S
 //             and R): TMEM -> registers, exchange of Y within groups of 8
 //             lanes by shuffles, V+- = X +- Y', BF16 slicing, swizzled stores
-//             into the GEMM2 operand tile; S -> R sums; FP64 flushes.
+//             into the GEMM2 operand tile; S -> R sums; flushes.
 // The integral tiles live only in TMEM, registers and shared memory.
 #include "kernels.h"
 #include "tc_ptx.cuh"
@@ -55,12 +55,15 @@ constexpr int TPIECE = 16;                            // slots per tau+- stage (
 constexpr uint32_t V_TILE = 128u * SLOTS * 2u;        // 16 KB: 128 ab rows x 64 slots
 constexpr uint32_t kColS = 256;                       // TMEM: XY0 [0,128), XY1 [128,256), S, R
 
-template <int S>
+// Shared memory of the fused kernel: a ring of TMA stages and the V+- tile
+// (the GEMM2 operand).  The storing pass writes V+- straight to global
+// memory, so its ring takes the whole budget.
+template <int S, bool kStoreV>
 struct Cfg {
   static constexpr uint32_t kStage = 12288u * S;      // S*(A_TILE+B_TILE) >= S*kTcMaxCols*32
-  static constexpr int kStages = (S == 2) ? 5 : 3;
+  static constexpr int kStages = kStoreV ? (int)((232448u - 2048u) / kStage) : ((S == 2) ? 5 : 3);
   static constexpr uint32_t kRing = kStage * kStages;
-  static constexpr uint32_t kV = 2u * S * V_TILE;
+  static constexpr uint32_t kV = kStoreV ? 0u : 2u * S * V_TILE;
   static constexpr uint32_t kBar = 256;
   static constexpr uint32_t kSmem = kRing + kV + kBar + 1024;
   static constexpr int kProducts = (S == 2) ? 3 : 6;
@@ -144,7 +147,7 @@ struct Item {
   int tile, iA, jB, A0, B0, p0, p1;
   TcChunk CH;
   uint32_t sc;   // TMEM columns of S and of R (nps + nms)
-  double *racc;  // this item's FP64 accumulators, [col][lane]
+  float2 *racc;  // this item's double-single accumulators, [col][lane]
 };
 
 __device__ __forceinline__ Item decode_item(const TcArgs &A, int item) {
@@ -187,7 +190,8 @@ __device__ __forceinline__ const TcArgs &item_args(const TcLaunch &Lp, int it, i
 
 template <int S, bool kBatch, bool kStoreV>
 __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_constant__ TcLaunch Lp) {
-  using C = Cfg<S>;
+  using C = Cfg<S, kStoreV>;
+  static_assert(C::kStages >= 3 && 8 * (2 * C::kStages + Bars::kCount) + 8 <= C::kBar, "ring");
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
@@ -390,16 +394,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
             }
             if (!ok) break;
           }
-          if (kStoreV && p > p0) {
-            // the V+- tile of block pair p-1 goes to global memory: one tiled
-            // store of its 2S planes; the tile is free again once read
-            if (!(ok = mbar_wait(bars.v_full(), v_use & 1u, wd, kSiteVFull))) break;
-            tma_store_3d(&A.tmVs, vbase, 0, 0, ((I.tile * A.nbp + (p - 1)) * 2) * S);
-            bulk_commit();
-            bulk_wait_read0();
-            mbar_arrive(bars.v_free());
-            ++v_use;
-          } else if (p > p0) {
+          if (!kStoreV && p > p0) {
             if (!(ok = mbar_wait(bars.v_full(), v_use & 1u, wd, kSiteVFull))) break;
             tc_fence_after();
             for (int piece = 0; ok && piece < SLOTS / TPIECE; ++piece) {
@@ -440,7 +435,6 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
           }
         }
       }
-      if (kStoreV) bulk_wait0();
       // every MMA of this CTA completes before TMEM is released
       mma_commit(bars.done());
       DrainWatch dw(A0args.status, Lp.timeout_ns);
@@ -462,7 +456,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
       const Item I = decode_item(A, local);
       const int p0 = I.p0, p1 = I.p1;
       const uint32_t sc = I.sc;
-      double *racc = I.racc;
+      float2 *racc = I.racc;
       const int kc = A.kc;
       const int nch_full = (A.nks + kc - 1) / kc;
       const bool split = A.xy_split != 0;
@@ -490,13 +484,13 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
         ++nacc;
         return true;
       };
-      // R (FP32, TMEM) -> FP64 accumulator in the workspace, [col][lane]
+      // R (FP32, TMEM) -> double-single accumulator in the workspace, [col][lane]
       auto flush_R = [&]() {
         for (uint32_t c0 = 16u * half; c0 < sc; c0 += 32) {
           float r[16];
           tmem_ld16(tl + kColS + sc + c0, r);
           tmem_ld_wait();
-          flush16_f64(racc + (size_t)c0 * 128 + L, r, nflush != 0, pol);
+          flush16_ds(racc + (size_t)c0 * 128 + L, r, nflush != 0, pol);
         }
         ++nflush;
         nacc = 0;
@@ -587,6 +581,29 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
   #pragma unroll
           for (int j = 0; j < 8; ++j) Y[b * 8 + j] = r[j];
         }
+        if constexpr (kStoreV) {
+          // V+- slices straight to the planes [tile][pair][sign][slice][128
+          // rows][64 slots]: a warp writes whole 128-byte rows
+          __nv_bfloat16 *vp = A.Vst + (size_t)(I.tile * A.nbp + p) * 2 * S * (128 * SLOTS);
+  #pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int row = a_l * 8 + 4 * half + b;
+  #pragma unroll
+            for (int sg = 0; sg < 2; ++sg) {
+              float rem[8];
+  #pragma unroll
+              for (int d = 0; d < 8; ++d) rem[d] = sg ? X[b * 8 + d] - Y[b * 8 + d] : X[b * 8 + d] + Y[b * 8 + d];
+  #pragma unroll
+              for (int s = 0; s < S; ++s) {
+                const uint4 w = pack_slice(rem);
+                __stcs(reinterpret_cast<uint4 *>(vp + (size_t)(sg * S + s) * (128 * SLOTS) + row * SLOTS +
+                                                 x_l * CB),
+                       w);
+              }
+            }
+          }
+          continue;
+        }
         if (!(ok = mbar_wait(bars.v_free(), (v_use & 1u) ^ 1u, wd, kSiteVFree))) break;
         ++v_use;
   #pragma unroll
@@ -608,7 +625,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
         fence_async_smem();
         mbar_arrive(bars.v_full());
       }
-      // S chains of the last block pair, then the final FP64 flush
+      // S chains of the last block pair, then the final flush
       if (!kStoreV) {
         for (int gs = 0; ok && gs < SLOTS / TPIECE / A.s_pieces; ++gs) ok = take_S();
         if (ok) flush_R();
@@ -626,7 +643,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
 }
 
 // ---------------------------------------------------------------- unpack
-// R_ij^ab from the FP64 accumulators of every block-pair range of a
+// R_ij^ab from the accumulators of every block-pair range of a
 // (tile, chunk): lane = ab slot (a = A0 + lane/8, b = B0 + lane%8),
 //   R_ij^ab = R+ + R-, R_ij^ba = R+ - R-, R_ji^ba = R_ij^ab, R_ji^ab = R_ij^ba,
 // with R- = 0 when i = j or a = b.  Every element of R is written once.
@@ -647,16 +664,16 @@ __global__ void __launch_bounds__(128) unpack_kernel(const __grid_constant__ TcL
   const bool diag_ab = (jB >> 1) == iA;
   if (!(a < A.v && b < A.v && (!diag_ab || a <= b))) return;
   const size_t per_item = (size_t)128 * A.racc_cols;
-  const double *base = A.racc + (size_t)tc * A.ksplit * per_item + L;
+  const float2 *base = A.racc + (size_t)tc * A.ksplit * per_item + L;
   const size_t vv = (size_t)A.v * A.v, o = (size_t)A.o;
   int i = 0, j = 0;
   lam_plus(CH.lp0, i, j);
   for (int c = 0; c < CH.np; ++c) {
     double pv = 0.0, mv = 0.0;
-    for (int k = 0; k < A.ksplit; ++k) pv += base[k * per_item + (size_t)c * 128];
+    for (int k = 0; k < A.ksplit; ++k) pv += ds_value(base[k * per_item + (size_t)c * 128]);
     if (i < j && a != b) {
       const int cm = CH.nps + (pneg(j) + i - CH.lm0);
-      for (int k = 0; k < A.ksplit; ++k) mv += base[k * per_item + (size_t)cm * 128];
+      for (int k = 0; k < A.ksplit; ++k) mv += ds_value(base[k * per_item + (size_t)cm * 128]);
     }
     A.R[(i * o + j) * vv + (size_t)a * A.v + b] = pv + mv;
     A.R[(i * o + j) * vv + (size_t)b * A.v + a] = pv - mv;
@@ -680,12 +697,12 @@ __global__ void __launch_bounds__(128) unpack_kernel(const __grid_constant__ TcL
 // Accumulation: a fresh FP32 accumulator S every s_pieces pieces (as in the
 // fused kernel), double-buffered in TMEM so that the next pieces' MMAs run
 // while the conversion warps take the last S; the running FP32 sum R lives in
-// the conversion warps' registers and is added into the FP64 accumulators in
+// the conversion warps' registers and is added into the accumulators in
 // the workspace every flush_every S.
 //   warp 0    TMA: per 16-slot piece, the S V planes of the sign (one 3-D box) and the
 //             chunk's tau+- rows (one bulk copy from the chunk-major copy);
 //   warp 1    MMA issuer: S+-[ab][lambda] (+)= V+-[ab][piece] T+-[lambda][piece]^T;
-//   warps 2-9 S -> R (registers) and FP64 flushes; lane = ab row, each warp
+//   warps 2-9 S -> R (registers) and flushes; lane = ab row, each warp
 //             owns every other group of 16 columns.
 constexpr uint32_t VP_PLANE = 128u * TPIECE * 2u;  // 4 KB: 128 ab rows x 16 slots
 constexpr uint32_t kColS1 = 256;                   // TMEM: S0 [0, 192), S1 [256, 448)
@@ -704,6 +721,16 @@ struct Cfg2 {
 static_assert(kColS1 + kTcMaxColsV <= 512, "TMEM columns of the GEMM2 kernel");
 static_assert(kTcMaxColsV % 32 == 0, "column groups");
 static_assert(8 * (2 * 10 + Bars::kCount) + 8 <= 256, "barrier area");
+
+// Work units of the GEMM2 kernel in range-major order: unit u takes block-pair
+// range u / (tiles * chunks) of (tile, chunk) u % (tiles * chunks), so the CTAs
+// resident at one time share one window of block pairs (and with it the
+// tau+- rows and V+- planes they read from L2).  Returns the accumulator
+// slot of the unit, which decode_item maps to (tile, chunk, range).
+__device__ __forceinline__ int gemm2_slot(const TcArgs &A, int u) {
+  const int tcs = A.ntiles * A.nchunks;
+  return (u % tcs) * A.ksplit + u / tcs;
+}
 
 template <int S>
 __global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_constant__ TcLaunch Lp) {
@@ -755,7 +782,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_
       bool ok = true;
       tma_prefetch_desc(&A.tmVl);
       for (int it = it0; ok && it < nit; it += itstep) {
-        const Item I = decode_item(A, it);
+        const Item I = decode_item(A, gemm2_slot(A, it));
         const TcChunk &CH = I.CH;
         const uint32_t tbytes = I.sc * 32u;
         const int sg = CH.nps > 0 ? 0 : 1;  // the chunk's sign
@@ -793,7 +820,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_
       const uint32_t hi32 = desc_hi(256, kSwizzle32);
       bool ok = true;
       for (int it = it0; ok && it < nit; it += itstep) {
-        const Item I = decode_item(A, it);
+        const Item I = decode_item(A, gemm2_slot(A, it));
         const TcChunk &CH = I.CH;
         const uint32_t id = idesc_bf16(128, (int)I.sc);
         const uint32_t tbytes = I.sc * 32u;
@@ -829,7 +856,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_
       mbar_wait(bars.done(), 0, dw.wd, kSiteRFull);
     }
   } else {
-    // ================================================================ S -> R -> FP64
+    // ================================================================ S -> R -> accumulators
     const int quad = warp & 3;
     const int half = (warp - 2) >> 2;
     const int L = quad * 32 + lane;
@@ -839,10 +866,10 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_
     const uint64_t pol = l2_evict_last_policy();
     float R[kGroupsV * 16];
     for (int it = it0; ok && it < nit; it += itstep) {
-      const Item I = decode_item(A, it);
+      const Item I = decode_item(A, gemm2_slot(A, it));
       const int sc = (int)I.sc;
       const int ng = (sc - 16 * half + 31) / 32;  // this warp's groups: columns 16*half + 32*k
-      double *racc = I.racc + L;
+      float2 *racc = I.racc + L;
       int nacc = 0, nflush = 0;
 #pragma unroll
       for (int u = 0; u < kGroupsV * 16; ++u) R[u] = 0.f;
@@ -873,7 +900,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_
         if (++nacc >= A.flush_every || t + 1 == ntake) {
 #pragma unroll
           for (int k = 0; k < kGroupsV; ++k)
-            if (k < ng) flush16_f64(racc + (size_t)(16 * half + 32 * k) * 128, &R[k * 16], nflush != 0, pol);
+            if (k < ng) flush16_ds(racc + (size_t)(16 * half + 32 * k) * 128, &R[k * 16], nflush != 0, pol);
 #pragma unroll
           for (int u = 0; u < kGroupsV * 16; ++u) R[u] = 0.f;
           ++nflush;
@@ -892,7 +919,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_
 }
 
 // ---------------------------------------------------------------- unpack (two-pass)
-// R_ij^ab from the FP64 accumulators of the GEMM2 pass, whose chunks hold
+// R_ij^ab from the accumulators of the GEMM2 pass, whose chunks hold
 // lambda+ columns [c wplus, (c+1) wplus) or lambda- columns [c wminus, ...):
 // block (tile, plus chunk c) writes every (i <= j) of that lambda+ range,
 // taking R- from the minus chunk of lambda- = j(j-1)/2 + i.  Lane = ab slot,
@@ -912,20 +939,20 @@ __global__ void __launch_bounds__(128) unpack2_kernel(const __grid_constant__ Tc
   if (!(a < A.v && b < A.v && (!diag_ab || a <= b))) return;
   const size_t per_item = (size_t)128 * A.racc_cols;
   // work item (tile, chunk, range k) sits at ((tile * nchunks + chunk) * ksplit + k)
-  const double *base = A.racc + (size_t)tile * A.nchunks * A.ksplit * per_item + L;
+  const float2 *base = A.racc + (size_t)tile * A.nchunks * A.ksplit * per_item + L;
   const size_t vv = (size_t)A.v * A.v, o = (size_t)A.o;
   const TcChunk CH = A.chunks[cp];
   int i = 0, j = 0;
   lam_plus(CH.lp0, i, j);
   for (int c = 0; c < CH.np; ++c) {
     double pv = 0.0, mv = 0.0;
-    const double *bp = base + ((size_t)cp * A.ksplit) * per_item + (size_t)c * 128;
-    for (int k = 0; k < A.ksplit; ++k) pv += bp[k * per_item];
+    const float2 *bp = base + ((size_t)cp * A.ksplit) * per_item + (size_t)c * 128;
+    for (int k = 0; k < A.ksplit; ++k) pv += ds_value(bp[k * per_item]);
     if (i < j && a != b) {
       const int lm = pneg(j) + i;
       const int cm = A.nplus + lm / A.wminus;
-      const double *bm = base + ((size_t)cm * A.ksplit) * per_item + (size_t)(lm % A.wminus) * 128;
-      for (int k = 0; k < A.ksplit; ++k) mv += bm[k * per_item];
+      const float2 *bm = base + ((size_t)cm * A.ksplit) * per_item + (size_t)(lm % A.wminus) * 128;
+      for (int k = 0; k < A.ksplit; ++k) mv += ds_value(bm[k * per_item]);
     }
     A.R[(i * o + j) * vv + (size_t)a * A.v + b] = pv + mv;
     A.R[(i * o + j) * vv + (size_t)b * A.v + a] = pv - mv;
@@ -941,15 +968,17 @@ __global__ void __launch_bounds__(128) unpack2_kernel(const __grid_constant__ Tc
 }  // namespace
 
 uint32_t tc_smem_bytes(int nslices) {
-  return nslices == 2 ? Cfg<2>::kSmem : Cfg<3>::kSmem;
+  return nslices == 2 ? Cfg<2, false>::kSmem : Cfg<3, false>::kSmem;
 }
 
 template <int S>
 static cudaError_t set_smem_attrs() {
   const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(ladder_tc_kernel<S, false, false>, at, (int)Cfg<S>::kSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(ladder_tc_kernel<S, true, false>, at, (int)Cfg<S>::kSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(ladder_tc_kernel<S, false, true>, at, (int)Cfg<S>::kSmem);
+  cudaError_t e = cudaFuncSetAttribute(ladder_tc_kernel<S, false, false>, at, (int)Cfg<S, false>::kSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(ladder_tc_kernel<S, true, false>, at, (int)Cfg<S, false>::kSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(ladder_tc_kernel<S, false, true>, at, (int)Cfg<S, true>::kSmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(ladder_gemm2_kernel<S>, at, (int)Cfg2<S>::kSmem);
   return e;
 }
@@ -962,14 +991,14 @@ cudaError_t launch_ladder_tc(const TcLaunch &a, int nslices, int grid, cudaStrea
   const bool batch = a.mols != nullptr;
   if (nslices == 2) {
     if (batch)
-      ladder_tc_kernel<2, true, false><<<grid, kThreads, Cfg<2>::kSmem, s>>>(a);
+      ladder_tc_kernel<2, true, false><<<grid, kThreads, Cfg<2, false>::kSmem, s>>>(a);
     else
-      ladder_tc_kernel<2, false, false><<<grid, kThreads, Cfg<2>::kSmem, s>>>(a);
+      ladder_tc_kernel<2, false, false><<<grid, kThreads, Cfg<2, false>::kSmem, s>>>(a);
   } else {
     if (batch)
-      ladder_tc_kernel<3, true, false><<<grid, kThreads, Cfg<3>::kSmem, s>>>(a);
+      ladder_tc_kernel<3, true, false><<<grid, kThreads, Cfg<3, false>::kSmem, s>>>(a);
     else
-      ladder_tc_kernel<3, false, false><<<grid, kThreads, Cfg<3>::kSmem, s>>>(a);
+      ladder_tc_kernel<3, false, false><<<grid, kThreads, Cfg<3, false>::kSmem, s>>>(a);
   }
   return cudaGetLastError();
 }
@@ -977,9 +1006,9 @@ cudaError_t launch_ladder_tc(const TcLaunch &a, int nslices, int grid, cudaStrea
 cudaError_t launch_ladder_vstore(const TcLaunch &a, int nslices, int grid, cudaStream_t s) {
   if (a.mols) return cudaErrorInvalidValue;
   if (nslices == 2)
-    ladder_tc_kernel<2, false, true><<<grid, kThreads, Cfg<2>::kSmem, s>>>(a);
+    ladder_tc_kernel<2, false, true><<<grid, kThreads, Cfg<2, true>::kSmem, s>>>(a);
   else
-    ladder_tc_kernel<3, false, true><<<grid, kThreads, Cfg<3>::kSmem, s>>>(a);
+    ladder_tc_kernel<3, false, true><<<grid, kThreads, Cfg<3, true>::kSmem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -194,31 +194,49 @@ __device__ __forceinline__ uint64_t l2_evict_last_policy() {
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
   return pol;
 }
-__device__ __forceinline__ double ld_f64_hint(const double *p, uint64_t pol) {
-  double v;
-  asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol) : "memory");
+__device__ __forceinline__ float2 ld_f2_hint(const float2 *p, uint64_t pol) {
+  float2 v;
+  asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
+               : "=f"(v.x), "=f"(v.y)
+               : "l"(p), "l"(pol)
+               : "memory");
   return v;
 }
-__device__ __forceinline__ void st_f64_hint(double *p, double v, uint64_t pol) {
-  asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
+__device__ __forceinline__ void st_f2_hint(float2 *p, float2 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y),
+               "l"(pol)
+               : "memory");
 }
 
-// dst[u * 128] (+)= r[u] for u < 16 in FP64 (accumulators laid out [column][128
+// Double-single accumulators: a sum carried as an unevaluated pair hi + lo
+// of FP32 numbers.  Adding x uses Knuth's TwoSum (s = hi + x exactly split
+// into s and its rounding error e), so hi + lo keeps about 48 significant
+// bits while every operation runs on the FP32 pipe (the FP64 pipe of this
+// part is too slow for the flush rate of the tensor-core kernels).  Readers
+// form (double)hi + (double)lo.
+__device__ __forceinline__ float2 ds_add(float2 acc, float x) {
+  const float s = acc.x + x;
+  const float bb = s - acc.x;
+  const float e = (acc.x - (s - bb)) + (x - bb);
+  return make_float2(s, acc.y + e);
+}
+
+// dst[u * 128] (+)= r[u] for u < 16 (accumulators laid out [column][128
 // lanes]): all 16 loads are issued before the first add, so one flush of a
 // 16-column group costs one memory latency, not sixteen; the accumulators are
 // kept in L2 (evict-last) so that this latency is an L2 hit.
-__device__ __forceinline__ void flush16_f64(double *dst, const float *r, bool accumulate,
-                                            uint64_t pol) {
-  double old[16];
+__device__ __forceinline__ void flush16_ds(float2 *dst, const float *r, bool accumulate,
+                                           uint64_t pol) {
+  float2 old[16];
   if (accumulate) {
 #pragma unroll
-    for (int u = 0; u < 16; ++u) old[u] = ld_f64_hint(dst + u * 128, pol);
+    for (int u = 0; u < 16; ++u) old[u] = ld_f2_hint(dst + u * 128, pol);
   } else {
 #pragma unroll
-    for (int u = 0; u < 16; ++u) old[u] = 0.0;
+    for (int u = 0; u < 16; ++u) old[u] = make_float2(0.f, 0.f);
   }
 #pragma unroll
-  for (int u = 0; u < 16; ++u) st_f64_hint(dst + u * 128, old[u] + (double)r[u], pol);
+  for (int u = 0; u < 16; ++u) st_f2_hint(dst + u * 128, ds_add(old[u], r[u]), pol);
 }
 
 // Shared-memory matrix descriptor, K-major operand with the given swizzle:

@@ -64,8 +64,9 @@ def candidates(forms=(0,)):
     for tp in forms:
         for kc in (16, 32):
             out.append(("bf16x3", {"kc": kc, "s_pieces": 4, "xy_split": 1, "two_pass": tp}))
-        for kc in (2, 4, 8):
-            for sp in (1, 2):
+        # the two-pass form keeps S double-buffered, so longer S chains pay off there
+        for kc in ((4, 8) if tp else (2, 4, 8)):
+            for sp in ((1, 2, 4) if tp else (1, 2)):
                 out.append(("bf16x6", {"kc": kc, "s_pieces": sp, "xy_split": 1, "two_pass": tp}))
     return out
 
