@@ -669,12 +669,14 @@ __global__ void __launch_bounds__(128) unpack_kernel(const __grid_constant__ TcL
   int i = 0, j = 0;
   lam_plus(CH.lp0, i, j);
   for (int c = 0; c < CH.np; ++c) {
-    double pv = 0.0, mv = 0.0;
-    for (int k = 0; k < A.ksplit; ++k) pv += ds_value(base[k * per_item + (size_t)c * 128]);
+    // the ranges' partial sums added in double-single form, then widened once
+    float2 ps = base[(size_t)c * 128], ms = make_float2(0.f, 0.f);
+    for (int k = 1; k < A.ksplit; ++k) ps = ds_add2(ps, base[k * per_item + (size_t)c * 128]);
     if (i < j && a != b) {
       const int cm = CH.nps + (pneg(j) + i - CH.lm0);
-      for (int k = 0; k < A.ksplit; ++k) mv += ds_value(base[k * per_item + (size_t)cm * 128]);
+      for (int k = 0; k < A.ksplit; ++k) ms = ds_add2(ms, base[k * per_item + (size_t)cm * 128]);
     }
+    const double pv = ds_value(ps), mv = ds_value(ms);
     A.R[(i * o + j) * vv + (size_t)a * A.v + b] = pv + mv;
     A.R[(i * o + j) * vv + (size_t)b * A.v + a] = pv - mv;
     A.R[(j * o + i) * vv + (size_t)b * A.v + a] = pv + mv;
@@ -945,15 +947,17 @@ __global__ void __launch_bounds__(128) unpack2_kernel(const __grid_constant__ Tc
   int i = 0, j = 0;
   lam_plus(CH.lp0, i, j);
   for (int c = 0; c < CH.np; ++c) {
-    double pv = 0.0, mv = 0.0;
+    // the ranges' partial sums added in double-single form, then widened once
     const float2 *bp = base + ((size_t)cp * A.ksplit) * per_item + (size_t)c * 128;
-    for (int k = 0; k < A.ksplit; ++k) pv += ds_value(bp[k * per_item]);
+    float2 ps = bp[0], ms = make_float2(0.f, 0.f);
+    for (int k = 1; k < A.ksplit; ++k) ps = ds_add2(ps, bp[k * per_item]);
     if (i < j && a != b) {
       const int lm = pneg(j) + i;
       const int cm = A.nplus + lm / A.wminus;
       const float2 *bm = base + ((size_t)cm * A.ksplit) * per_item + (size_t)(lm % A.wminus) * 128;
-      for (int k = 0; k < A.ksplit; ++k) mv += ds_value(bm[k * per_item]);
+      for (int k = 0; k < A.ksplit; ++k) ms = ds_add2(ms, bm[k * per_item]);
     }
+    const double pv = ds_value(ps), mv = ds_value(ms);
     A.R[(i * o + j) * vv + (size_t)a * A.v + b] = pv + mv;
     A.R[(i * o + j) * vv + (size_t)b * A.v + a] = pv - mv;
     A.R[(j * o + i) * vv + (size_t)b * A.v + a] = pv + mv;

@@ -221,6 +221,14 @@ __device__ __forceinline__ float2 ds_add(float2 acc, float x) {
   return make_float2(s, acc.y + e);
 }
 
+// Sum of two double-single values (TwoSum of the high parts, low parts added).
+__device__ __forceinline__ float2 ds_add2(float2 a, float2 b) {
+  const float s = a.x + b.x;
+  const float bb = s - a.x;
+  const float e = (a.x - (s - bb)) + (b.x - bb);
+  return make_float2(s, (a.y + b.y) + e);
+}
+
 // dst[u * 128] (+)= r[u] for u < 16 (accumulators laid out [column][128
 // lanes]): all 16 loads are issued before the first add, so one flush of a
 // 16-column group costs one memory latency, not sixteen; the accumulators are
