@@ -193,6 +193,45 @@ def run_ragged(args):
     return 0
 
 
+class Replicas:
+    """Rank bookkeeping of a replica run: one process per GPU (torchrun sets
+    WORLD_SIZE / RANK / LOCAL_RANK), no collective on the data path, a barrier
+    around the timed region and the maximum over ranks of its time."""
+
+    def __init__(self, backend: str):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self, sync=None) -> None:
+        if self.dist is not None:
+            self.dist.barrier()
+        if sync is not None:
+            sync()
+
+    def max(self, x: float, device="cpu") -> float:
+        if self.dist is None:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def job_value(self, units_per_rank: float, max_ms: float) -> float:
+        """Whole-job throughput: every rank's units over the slowest rank's time."""
+        return self.world * units_per_rank / (max_ms * 1e-3)
+
+    def close(self) -> None:
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -235,6 +274,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--form", default="auto", choices=["auto", "fused", "two-pass"],
+                    help="split-BF16 form: the plan's (or tuner's) choice, the one-kernel fused form "
+                         "(integral tiles stay on chip), or the two-pass form (V+- stored in HBM)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -242,27 +284,17 @@ def main():
         return run_ragged(args)
 
     import torch
-    import torch.distributed as dist
     import paper_1810_08142_gb300 as lad
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    rep = Replicas("nccl")
+    world, rank, local = rep.world, rep.rank, rep.local
 
     def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
+        rep.barrier(torch.cuda.synchronize)
 
     def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return rep.max(x, device="cuda")
 
     w = synthetic.WORKLOADS[args.workload]
     x = synthetic.make_inputs(w.o, w.v, w.naux, w.seed)
@@ -277,6 +309,8 @@ def main():
     stream = torch.cuda.current_stream()
 
     tuning = tuned_for(w, args.mode)
+    if args.form != "auto" and args.mode != "fp64":
+        tuning = dict(tuning or {}, two_pass=int(args.form == "two-pass"), ksplit=0)
     L = lad.Ladder(w.o, w.v, w.naux, mode=args.mode, device=dev, tuning=tuning)
     lad.ladder_set_timing(L.plan, True)
 
@@ -306,7 +340,7 @@ def main():
     L.check_device()
     ms = e0.elapsed_time(e1) / args.steps
     ms = max_over_ranks(ms)
-    value = world * F / (ms * 1e-3) / 1e12
+    value = rep.job_value(F, ms) / 1e12
     fused_ms = statistics.mean(f[1] for f in fused)
     prep_ms = statistics.mean(f[0] for f in fused)
     unpack_ms = statistics.mean(f[2] for f in fused)
@@ -415,7 +449,7 @@ def main():
         barrier()
         ems = max_over_ranks(q0.elapsed_time(q1) / args.steps)
         h2d = (h_t1.numel() + h_t2.numel() + h_B.numel()) * 8
-        e2e = {"value": world * F / (ems * 1e-3) / 1e12, "unit": "TFLOP/s",
+        e2e = {"value": rep.job_value(F, ems) / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8, "ms_per_step": ems}
 
     cpu = None
@@ -434,6 +468,8 @@ def main():
             "config": {"workload": args.workload, "o": w.o, "v": w.v, "naux": w.naux,
                        "seed": w.seed, "mode": args.mode, "parallelism": "replicas",
                        "tuning": tun,
+                       "form": None if tun is None else ("two-pass (V+- stored in HBM)" if two_pass
+                                                         else "fused (integral tiles on chip)"),
                        "l2": "inputs larger than L2 (B %.2f GB, tau %.2f GB)"
                              % (B.numel() * 8 / 1e9, tau.numel() * 8 / 1e9)},
             "stages_ms": {"prep": prep_ms, "ladder": fused_ms, "unpack": unpack_ms,
@@ -444,8 +480,7 @@ def main():
         }
         print(json.dumps(line), flush=True)
     L.close()
-    if world > 1:
-        dist.destroy_process_group()
+    rep.close()
     return 0
 
 
