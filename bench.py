@@ -193,6 +193,16 @@ def run_ragged(args):
     return 0
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# dominant kernel, from one single-pass ncu capture of the same kernel build
+# on the same workload and tuning (profiles/dram_traffic_mid_o34_v400_n1600_bf16x6.md).
+# A configuration not listed here reports traffic null.
+TRAFFIC = {
+    ("mid_o34_v400_n1600", "bf16x6", "pass1", (4, 2, 7)): 771.01e9 + 81.47e9,
+    ("mid_o34_v400_n1600", "bf16x6", "pass2", (4, 2, 7)): 444.05e9 + 70.66e9,
+}
+
+
 class Replicas:
     """Rank bookkeeping of a replica run: one process per GPU (torchrun sets
     WORLD_SIZE / RANK / LOCAL_RANK), no collective on the data path, a barrier
@@ -373,14 +383,16 @@ def main():
         F1 = synthetic.falg_gemm1(w.o, w.v, w.naux)
         nS = 2 if args.mode == "bf16x3" else 3
         if pass1_ms >= pass2_ms:
-            kname, kflops, kms = "ladder_tc_kernel<%d,false,true> (GEMM1 + V store)" % nS, F1, pass1_ms
+            kname, kflops, kms, kkey = ("ladder_tc_kernel<%d,false,true> (GEMM1 + V store)" % nS, F1,
+                                        pass1_ms, "pass1")
         else:
-            kname, kflops, kms = "ladder_gemm2_kernel<%d> (GEMM2 from stored V)" % nS, F - F1, pass2_ms
+            kname, kflops, kms, kkey = "ladder_gemm2_kernel<%d> (GEMM2 from stored V)" % nS, F - F1, pass2_ms, "pass2"
+        traffic = TRAFFIC.get((args.workload, args.mode, kkey, (tun["kc"], tun["s_pieces"], tun["ksplit"])))
         achieved = prod * kflops / (kms * 1e-3) / 1e12
         peak = pk["bf16_tflops_sustained"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": kname,
-                "kernel_ms": kms,
+                "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
+                "kernel": kname, "kernel_ms": kms,
                 "both_passes_frac": prod * F / ((pass1_ms + pass2_ms) * 1e-3) / 1e12 / peak,
                 "note": "achieved = %d x (that pass's share of F_alg: 2 P+(v) v^2 N for GEMM1, the "
                         "rest for GEMM2) / its CUDA-event time; peak = bf16 sustained (%s)"

@@ -294,9 +294,12 @@ static int auto_ksplit(const ladder_plan_s *pl) {
 }
 
 // Block-pair ranges per tile of the storing pass (no accumulators depend on
-// them): enough work units for about eight per SM.
+// them): at least about eight work units per SM, and ranges of at most about
+// 128 block pairs, which the kernel walks range-major.
 static int auto_vsplit(const ladder_plan_s *pl) {
-  const int vs = (8 * pl->sm_count + pl->ntiles_tc - 1) / pl->ntiles_tc;
+  int vs = (8 * pl->sm_count + pl->ntiles_tc - 1) / pl->ntiles_tc;
+  if (const char *e = getenv("LADDER_VSPLIT")) vs = atoi(e);
+  else vs = std::max(vs, (pl->nbp + 127) / 128);
   return std::max(1, std::min(vs, pl->nbp));
 }
 

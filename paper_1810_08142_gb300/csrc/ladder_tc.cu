@@ -188,6 +188,15 @@ __device__ __forceinline__ const TcArgs &item_args(const TcLaunch &Lp, int it, i
   }
 }
 
+// Work units of the storing pass in range-major order: unit u takes
+// block-pair range u / tiles of tile u % tiles, so the CTAs resident at one
+// time work in one window of block pairs and share its B-slice panels in L2.
+// (The storing pass keeps no accumulators, so any order gives the same
+// result.)  Returns the slot that decode_item maps to (tile, range).
+__device__ __forceinline__ int vstore_slot(const TcArgs &A, int u) {
+  return (u % A.ntiles) * A.ksplit + u / A.ntiles;
+}
+
 template <int S, bool kBatch, bool kStoreV>
 __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_constant__ TcLaunch Lp) {
   using C = Cfg<S, kStoreV>;
@@ -246,7 +255,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
       for (int it = it0; ok && it < nit; it += itstep) {
         int local;
         const TcArgs &A = item_args<kBatch>(Lp, it, local);
-        const Item I = decode_item(A, local);
+        const Item I = decode_item(A, kStoreV ? vstore_slot(A, local) : local);
         const TcChunk &CH = I.CH;
         const int A0 = I.A0, B0 = I.B0, p0 = I.p0, p1 = I.p1;
         const uint32_t tbytes = I.sc * 32u;
@@ -325,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
       for (int it = it0; ok && it < nit; it += itstep) {
         int local;
         const TcArgs &A = item_args<kBatch>(Lp, it, local);
-        const Item I = decode_item(A, local);
+        const Item I = decode_item(A, kStoreV ? vstore_slot(A, local) : local);
         const TcChunk &CH = I.CH;
         const int p0 = I.p0, p1 = I.p1;
         const uint32_t idp = idesc_bf16(128, CH.nps > 0 ? CH.nps : 16);
@@ -453,7 +462,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
     for (int it = it0; ok && it < nit; it += itstep) {
       int local;
       const TcArgs &A = item_args<kBatch>(Lp, it, local);
-      const Item I = decode_item(A, local);
+      const Item I = decode_item(A, kStoreV ? vstore_slot(A, local) : local);
       const int p0 = I.p0, p1 = I.p1;
       const uint32_t sc = I.sc;
       float2 *racc = I.racc;
@@ -796,10 +805,11 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_
             mbar_arrive_expect_tx(bars.full(stage), C::kV + (uint32_t)S * tbytes);
             armed |= 1u << stage;
             armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+            // (default L2 policy for both: marking the tau+- copy evict-last
+            // or the V+- planes evict-first measured slower)
             tma_load_3d(dst, &A.tmVl, bars.full(stage), piece * TPIECE, 0, z);
             // the chunk's tau+- rows of this piece, every slice: one bulk copy
-            bulk_load(dst + C::kV,
-                      A.T2 + CH.t2off + (size_t)(p * kPieces + piece) * S * tbytes,
+            bulk_load(dst + C::kV, A.T2 + CH.t2off + (size_t)(p * kPieces + piece) * S * tbytes,
                       (uint32_t)S * tbytes, bars.full(stage));
             if (++stage == C::kStages) {
               stage = 0;
