@@ -137,12 +137,14 @@ struct TcLaunch {
 uint32_t tc_smem_bytes(int nslices);
 cudaError_t tc_init_attributes(int nslices);  // once per device, outside stream capture
 cudaError_t launch_ladder_tc(const TcLaunch &a, int nslices, int grid, cudaStream_t s);
-// Two-pass form (single molecule): GEMM1 once per (tile, block pair) with the
-// V+- slices stored to global memory, then GEMM2 from the stored tiles.
+// Two-pass form (one molecule, or a batch through mols/items): GEMM1 once per
+// (tile, block pair) with the V+- slices stored to global memory, then GEMM2
+// from the stored tiles.
 cudaError_t launch_ladder_vstore(const TcLaunch &a, int nslices, int grid, cudaStream_t s);
 cudaError_t launch_ladder_gemm2(const TcLaunch &a, int nslices, int grid, cudaStream_t s);
 cudaError_t launch_unpack(const TcLaunch &a, int nblocks, cudaStream_t s);
-cudaError_t launch_unpack2(const TcLaunch &a, cudaStream_t s);  // two-pass form
+// two-pass form: nblocks = tiles x plus-chunks (a batch lists (molecule, block) in tcs)
+cudaError_t launch_unpack2(const TcLaunch &a, int nblocks, cudaStream_t s);
 cudaError_t launch_selftest_wait(int *status, unsigned long long timeout_ns, int site,
                                  cudaStream_t s);
 

@@ -89,6 +89,9 @@ struct ladder_plan_s {
   std::vector<size_t> sub_off;
   std::vector<int2> items, tcs;  // (molecule, local work unit), (molecule, tile*chunk)
   size_t off_mols = 0, off_items = 0, off_tcs = 0;
+  // two-pass members: storing-pass and GEMM2-pass work units, unpack blocks
+  std::vector<int2> items1, items2, tcs2;
+  size_t off_mols1 = 0, off_mols2 = 0, off_items1 = 0, off_items2 = 0, off_tcs2 = 0;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
   std::vector<const void *> gkey;  // pointers the graph was captured with
@@ -264,6 +267,17 @@ void compute_layout(ladder_plan_s *pl) {
   pl->lay = L;
 }
 
+// Block-pair ranges per tile of the storing pass (no accumulators depend on
+// them): at least about eight work units per SM, and ranges of at most about
+// 128 block pairs, which the kernel walks range-major.  A batch member takes
+// only the range limit (the batch itself fills the SMs).
+static int auto_vsplit(const ladder_plan_s *pl, bool batch_member) {
+  int vs = batch_member ? 1 : (8 * pl->sm_count + pl->ntiles_tc - 1) / pl->ntiles_tc;
+  if (const char *e = getenv("LADDER_VSPLIT")) vs = atoi(e);
+  else vs = std::max(vs, (pl->nbp + 127) / 128);
+  return std::max(1, std::min(vs, pl->nbp));
+}
+
 }  // namespace
 
 extern "C" {
@@ -291,16 +305,6 @@ static int auto_ksplit(const ladder_plan_s *pl) {
   int ks = (2 * pl->sm_count + items - 1) / items;
   if (pl->two_pass) ks = std::max(ks, pl->nbp / 160);
   return std::max(1, std::min(ks, std::max(1, pl->nbp / 4)));
-}
-
-// Block-pair ranges per tile of the storing pass (no accumulators depend on
-// them): at least about eight work units per SM, and ranges of at most about
-// 128 block pairs, which the kernel walks range-major.
-static int auto_vsplit(const ladder_plan_s *pl) {
-  int vs = (8 * pl->sm_count + pl->ntiles_tc - 1) / pl->ntiles_tc;
-  if (const char *e = getenv("LADDER_VSPLIT")) vs = atoi(e);
-  else vs = std::max(vs, (pl->nbp + 127) / 128);
-  return std::max(1, std::min(vs, pl->nbp));
 }
 
 // Fills a plan for one shape; batch members get no block-pair split (the
@@ -346,6 +350,7 @@ static ladder_status init_plan(ladder_plan_s *pl, int o, int v, int naux, int mo
     if (!batch_member)
       if (const char *e = getenv("LADDER_TWOPASS")) pl->two_pass = atoi(e) != 0;
     pl->ksplit = batch_member ? 1 : auto_ksplit(pl);
+    pl->vsplit = auto_vsplit(pl, batch_member);
     // FP32 accumulation chains (see ladder_tc.cu).  GEMM1: with separate
     // hi*hi / small-product accumulators a chain of kc K-steps puts 2*kc MMAs
     // on the large accumulator (32 for BF16X3, 8 for BF16X6).  GEMM2: a fresh
@@ -485,12 +490,15 @@ ladder_status ladder_set_workspace(ladder_plan_t pl, void *dptr, size_t bytes) {
       const ladder_status st = encode_maps(sp, static_cast<char *>(sp->ws));
       if (st != LADDER_OK) return st;
     }
-    // work lists of the batched launch
-    if (cudaMemcpy(w + pl->off_items, pl->items.data(), pl->items.size() * sizeof(int2),
-                   cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(w + pl->off_tcs, pl->tcs.data(), pl->tcs.size() * sizeof(int2),
-                   cudaMemcpyHostToDevice) != cudaSuccess)
-      return cuda_status(cudaErrorUnknown);
+    // work lists of the batched launches
+    const std::pair<size_t, const std::vector<int2> *> lists[] = {
+        {pl->off_items, &pl->items},   {pl->off_tcs, &pl->tcs},     {pl->off_items1, &pl->items1},
+        {pl->off_items2, &pl->items2}, {pl->off_tcs2, &pl->tcs2}};
+    for (const auto &li : lists)
+      if (!li.second->empty() &&
+          cudaMemcpy(w + li.first, li.second->data(), li.second->size() * sizeof(int2),
+                     cudaMemcpyHostToDevice) != cudaSuccess)
+        return cuda_status(cudaErrorUnknown);
     if (pl->gexec) {
       cudaGraphExecDestroy(pl->gexec);
       pl->gexec = nullptr;
@@ -599,63 +607,85 @@ static void tc_prep(ladder_plan_t pl, const double *B, const double *tau, cudaSt
   launch_pack_tpm_bf16(pl->o, pl->v, pl->K, pl->S, pl->nlp, std::max(pl->nlm, 1), tau, Tp, Tm, s);
 }
 
+// Arguments of the storing pass (GEMM1 + V+- store) of the two-pass form.
+static TcArgs pass1_args(const ladder_plan_s *pl, int *status) {
+  TcArgs a = tc_args(pl, nullptr, status);
+  a.nchunks = 1;
+  std::memset(&a.chunks[0], 0, sizeof(TcChunk));
+  a.ksplit = pl->vsplit;
+  a.racc = nullptr;
+  return a;
+}
+
+// Arguments of the GEMM2 pass of the two-pass form (sign-separated chunks).
+static TcArgs pass2_args(const ladder_plan_s *pl, double *R, int *status) {
+  TcArgs a = tc_args(pl, R, status);
+  a.nchunks = (int)pl->chunks_v.size();
+  for (int c = 0; c < a.nchunks; ++c) a.chunks[c] = pl->chunks_v[c];
+  a.racc_cols = pl->racc_cols_v;
+  a.nplus = pl->nplus;
+  a.wplus = pl->wplus;
+  a.wminus = pl->wminus;
+  return a;
+}
+
+// Chunk-major, pre-swizzled copy of the tau+- slices for the GEMM2 pass.
+static void pack_t2(const ladder_plan_s *pl, cudaStream_t s) {
+  T2Args t2;
+  std::memset(&t2, 0, sizeof(t2));
+  t2.Tp = ws_at<__nv_bfloat16>(pl, pl->lay.Tp);
+  t2.Tm = ws_at<__nv_bfloat16>(pl, pl->lay.Tm);
+  t2.T2 = ws_at<__nv_bfloat16>(pl, pl->lay.T2);
+  t2.K = pl->K;
+  t2.S = pl->S;
+  t2.rows_p = pl->nlp;
+  t2.rows_m = std::max(pl->nlm, 1);
+  t2.nchunks = (int)pl->chunks_v.size();
+  for (int c = 0; c < t2.nchunks; ++c) {
+    t2.chunks[c] = pl->chunks_v[c];
+    t2.off[c] = pl->chunks_v[c].t2off / 2;
+  }
+  launch_pack_t2(t2, s);
+}
+
 static ladder_status apply_tc(ladder_plan_t pl, const double *B, const double *tau, double *R,
                               cudaStream_t s, bool transB = false) {
   mark(pl, 0, s);
   tc_prep(pl, B, tau, s, transB);
   ladder_status st = cuda_status(cudaGetLastError());
   if (st != LADDER_OK) return st;
+  int *status = ws_at<int>(pl, pl->lay.status);
   TcLaunch L;
   std::memset(&L, 0, sizeof(L));
-  L.one = tc_args(pl, R, ws_at<int>(pl, pl->lay.status));
-  L.timeout_ns = L.one.timeout_ns;
   pl->last_two_pass = pl->two_pass != 0;
   if (pl->two_pass) {
     // pass 1: GEMM1 and the V+- slices of every (tile, block pair) to the workspace
     TcLaunch L1 = L;
-    L1.one.nchunks = 1;
-    std::memset(&L1.one.chunks[0], 0, sizeof(TcChunk));
-    L1.one.ksplit = pl->vsplit = auto_vsplit(pl);
-    L1.one.racc = nullptr;
+    L1.one = pass1_args(pl, status);
+    L1.timeout_ns = L1.one.timeout_ns;
     L1.nitems = L1.one.ntiles * L1.one.ksplit;
-    // pass 2: GEMM2 in chunks of up to kTcMaxColsV occupied pairs
-    L.one.nchunks = (int)pl->chunks_v.size();
-    for (int c = 0; c < L.one.nchunks; ++c) L.one.chunks[c] = pl->chunks_v[c];
-    L.one.racc_cols = pl->racc_cols_v;
-    L.one.nplus = pl->nplus;
-    L.one.wplus = pl->wplus;
-    L.one.wminus = pl->wminus;
+    // pass 2: GEMM2 in chunks of up to kTcMaxColsV occupied pairs of one sign
+    L.one = pass2_args(pl, R, status);
+    L.timeout_ns = L.one.timeout_ns;
     L.nitems = L.one.ntiles * L.one.nchunks * L.one.ksplit;
-    T2Args t2;
-    std::memset(&t2, 0, sizeof(t2));
-    t2.Tp = ws_at<__nv_bfloat16>(pl, pl->lay.Tp);
-    t2.Tm = ws_at<__nv_bfloat16>(pl, pl->lay.Tm);
-    t2.T2 = ws_at<__nv_bfloat16>(pl, pl->lay.T2);
-    t2.K = pl->K;
-    t2.S = pl->S;
-    t2.rows_p = pl->nlp;
-    t2.rows_m = std::max(pl->nlm, 1);
-    t2.nchunks = (int)pl->chunks_v.size();
-    for (int c = 0; c < t2.nchunks; ++c) {
-      t2.chunks[c] = pl->chunks_v[c];
-      t2.off[c] = pl->chunks_v[c].t2off / 2;
-    }
-    launch_pack_t2(t2, s);
+    pack_t2(pl, s);
     st = cuda_status(cudaGetLastError());
     if (st != LADDER_OK) return st;
     mark(pl, 1, s);
     st = cuda_status(launch_ladder_vstore(L1, pl->S, L1.nitems, s));
     mark(pl, 4, s);
     if (st == LADDER_OK) st = cuda_status(launch_ladder_gemm2(L, pl->S, L.nitems, s));
+    mark(pl, 2, s);
+    if (st == LADDER_OK) st = cuda_status(launch_unpack2(L, L.one.ntiles * L.one.nplus, s));
   } else {
+    L.one = tc_args(pl, R, status);
+    L.timeout_ns = L.one.timeout_ns;
     L.nitems = L.one.ntiles * L.one.nchunks * L.one.ksplit;
     mark(pl, 1, s);
     st = cuda_status(launch_ladder_tc(L, pl->S, L.nitems, s));
+    mark(pl, 2, s);
+    if (st == LADDER_OK) st = cuda_status(launch_unpack(L, L.one.ntiles * L.one.nchunks, s));
   }
-  mark(pl, 2, s);
-  if (st == LADDER_OK)
-    st = cuda_status(pl->two_pass ? launch_unpack2(L, s)
-                                  : launch_unpack(L, L.one.ntiles * L.one.nchunks, s));
   mark(pl, 3, s);
   return st;
 }
@@ -775,6 +805,10 @@ ladder_status ladder_apply_host(ladder_plan_t pl, const double *B_host, const do
   return cuda_status(cudaStreamSynchronize(s));
 }
 
+// Stored V+- tiles of a batch: at most this many bytes in all (members beyond
+// it use the fused form).
+constexpr double kVStoreBatchCap = 128.0 * (1ull << 30);
+
 ladder_status ladder_plan_batched(int n, const int *o, const int *v, const int *naux, int mode,
                                   ladder_plan_t *out) {
   if (!out || n < 1 || n > 4096 || !o || !v || !naux) return LADDER_EINVAL;
@@ -787,15 +821,14 @@ ladder_status ladder_plan_batched(int n, const int *o, const int *v, const int *
   pl->batched = true;
   pl->mode = mode;
   pl->S = tc_slices(mode);
-  size_t off = kAlign;  // status word
-  pl->lay.status = 0;
-  pl->off_mols = off;
-  off = align_up(off + (size_t)n * sizeof(TcArgs));
   struct Unit {
     double cost;
     int m, k;
   };
   std::vector<Unit> units;
+  std::vector<std::pair<double, int>> twopass;  // (flops, molecule)
+  const char *tp_env = getenv("LADDER_TWOPASS");
+  double vsum = 0.0;
   for (int m = 0; m < n; ++m) {
     ladder_plan_s *sp = new (std::nothrow) ladder_plan_s();
     if (!sp) {
@@ -810,6 +843,19 @@ ladder_status ladder_plan_batched(int n, const int *o, const int *v, const int *
     }
     pl->device = sp->device;
     pl->sm_count = sp->sm_count;
+    // members whose fused form would recompute GEMM1 per chunk take the
+    // two-pass form while the batch's stored tiles fit the cap
+    const double vb = (double)sp->ntiles_tc * sp->nbp * 2 * sp->S * 128 * SLOTS * 2;
+    bool tp = sp->chunks_tc.size() > 1 && vsum + vb <= kVStoreBatchCap;
+    if (tp_env) tp = tp && atoi(tp_env) != 0;
+    if (tp) {
+      vsum += vb;
+      sp->two_pass = 1;
+      sp->ksplit = std::max(1, std::min(sp->nbp, sp->nbp / 160));
+      compute_layout(sp);
+      twopass.push_back({ladder_flops(sp), m});
+      continue;
+    }
     const int nwork = sp->ntiles_tc * (int)sp->chunks_tc.size();
     // cost of one work unit: block pairs x (GEMM1 K-steps + GEMM2 pieces)
     const double cost = (double)sp->nbp * (2.0 * (sp->Np / 32) + 4.0);
@@ -818,14 +864,38 @@ ladder_status ladder_plan_batched(int n, const int *o, const int *v, const int *
       pl->tcs.push_back(make_int2(m, k));
     }
   }
-  // largest work units first; ties keep molecule order
+  // fused work units: largest first, ties keep molecule order
   std::stable_sort(units.begin(), units.end(),
                    [](const Unit &x, const Unit &y) { return x.cost > y.cost; });
   for (auto &u : units) pl->items.push_back(make_int2(u.m, u.k));
-  pl->off_items = off;
-  off = align_up(off + pl->items.size() * sizeof(int2));
-  pl->off_tcs = off;
-  off = align_up(off + pl->tcs.size() * sizeof(int2));
+  // two-pass members, largest first: every work unit of a member in its own
+  // (range-major) order
+  std::stable_sort(twopass.begin(), twopass.end(),
+                   [](const std::pair<double, int> &x, const std::pair<double, int> &y) {
+                     return x.first > y.first;
+                   });
+  for (auto &t : twopass) {
+    const ladder_plan_s *sp = pl->subs[t.second];
+    const int m = t.second;
+    for (int k = 0; k < sp->ntiles_tc * sp->vsplit; ++k) pl->items1.push_back(make_int2(m, k));
+    for (int k = 0; k < sp->ntiles_tc * (int)sp->chunks_v.size() * sp->ksplit; ++k)
+      pl->items2.push_back(make_int2(m, k));
+    for (int k = 0; k < sp->ntiles_tc * sp->nplus; ++k) pl->tcs2.push_back(make_int2(m, k));
+  }
+  size_t off = kAlign;  // status word
+  pl->lay.status = 0;
+  auto region = [&](size_t &at, size_t bytes) {
+    at = off;
+    off = align_up(off + std::max<size_t>(bytes, 1));
+  };
+  region(pl->off_mols, (size_t)n * sizeof(TcArgs));
+  region(pl->off_mols1, (size_t)n * sizeof(TcArgs));
+  region(pl->off_mols2, (size_t)n * sizeof(TcArgs));
+  region(pl->off_items, pl->items.size() * sizeof(int2));
+  region(pl->off_tcs, pl->tcs.size() * sizeof(int2));
+  region(pl->off_items1, pl->items1.size() * sizeof(int2));
+  region(pl->off_items2, pl->items2.size() * sizeof(int2));
+  region(pl->off_tcs2, pl->tcs2.size() * sizeof(int2));
   for (auto *sp : pl->subs) {
     off = align_up(off, 1024);
     pl->sub_off.push_back(off);
@@ -858,14 +928,25 @@ ladder_status ladder_apply_batched(ladder_plan_t pl, const double *const *B,
     // over the cost-sorted work units of all molecules, one unpack launch)
     char *w = static_cast<char *>(pl->ws);
     int *status = ws_at<int>(pl, pl->lay.status);
-    std::vector<TcArgs> args(n);
+    std::vector<TcArgs> args(n), args1(n), args2(n);
     unsigned long long tmax = 0;
     for (size_t m = 0; m < n; ++m) {
-      args[m] = tc_args(pl->subs[m], R[m], status);
+      const ladder_plan_s *sp = pl->subs[m];
+      args[m] = tc_args(sp, R[m], status);
+      if (sp->two_pass) {
+        args1[m] = pass1_args(sp, status);
+        args2[m] = pass2_args(sp, R[m], status);
+      } else {
+        args1[m] = args2[m] = args[m];
+      }
       tmax = std::max(tmax, args[m].timeout_ns);
     }
     if (cudaStreamSynchronize(s) != cudaSuccess ||
         cudaMemcpy(w + pl->off_mols, args.data(), n * sizeof(TcArgs), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(w + pl->off_mols1, args1.data(), n * sizeof(TcArgs), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(w + pl->off_mols2, args2.data(), n * sizeof(TcArgs), cudaMemcpyHostToDevice) !=
             cudaSuccess)
       return cuda_status(cudaErrorUnknown);
     if (!pl->cap_stream &&
@@ -875,19 +956,34 @@ ladder_status ladder_apply_batched(ladder_plan_t pl, const double *const *B,
       cudaGraphExecDestroy(pl->gexec);
       pl->gexec = nullptr;
     }
-    TcLaunch L;
-    std::memset(&L, 0, sizeof(L));
-    L.mols = reinterpret_cast<const TcArgs *>(w + pl->off_mols);
-    L.items = reinterpret_cast<const int2 *>(w + pl->off_items);
-    L.tcs = reinterpret_cast<const int2 *>(w + pl->off_tcs);
-    L.nitems = (int)pl->items.size();
-    L.timeout_ns = tmax;
+    auto batch_launch = [&](size_t mols, size_t items, size_t tcs, int nitems) {
+      TcLaunch L;
+      std::memset(&L, 0, sizeof(L));
+      L.mols = reinterpret_cast<const TcArgs *>(w + mols);
+      L.items = reinterpret_cast<const int2 *>(w + items);
+      L.tcs = reinterpret_cast<const int2 *>(w + tcs);
+      L.nitems = nitems;
+      L.timeout_ns = tmax;
+      return L;
+    };
+    const TcLaunch L = batch_launch(pl->off_mols, pl->off_items, pl->off_tcs, (int)pl->items.size());
+    const TcLaunch L1 = batch_launch(pl->off_mols1, pl->off_items1, pl->off_tcs2, (int)pl->items1.size());
+    const TcLaunch L2 = batch_launch(pl->off_mols2, pl->off_items2, pl->off_tcs2, (int)pl->items2.size());
     cudaStream_t c = pl->cap_stream;
     if (cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return cuda_status(cudaErrorUnknown);
-    for (size_t m = 0; m < n; ++m) tc_prep(pl->subs[m], B[m], tau[m], c, false);
-    launch_ladder_tc(L, pl->S, std::min(L.nitems, pl->sm_count), c);
-    launch_unpack(L, (int)pl->tcs.size(), c);
+    // operand preparation of every molecule; fused members in one persistent
+    // launch over their cost-sorted work units; two-pass members in one
+    // storing launch and one GEMM2 launch over all of them; the unpacks
+    for (size_t m = 0; m < n; ++m) {
+      tc_prep(pl->subs[m], B[m], tau[m], c, false);
+      if (pl->subs[m]->two_pass) pack_t2(pl->subs[m], c);
+    }
+    if (L.nitems) launch_ladder_tc(L, pl->S, std::min(L.nitems, pl->sm_count), c);
+    if (L1.nitems) launch_ladder_vstore(L1, pl->S, std::min(L1.nitems, pl->sm_count), c);
+    if (L2.nitems) launch_ladder_gemm2(L2, pl->S, std::min(L2.nitems, pl->sm_count), c);
+    if (!pl->tcs.empty()) launch_unpack(L, (int)pl->tcs.size(), c);
+    if (!pl->tcs2.empty()) launch_unpack2(L2, (int)pl->tcs2.size(), c);
     cudaGraph_t graph = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(c, &graph);
     if (ce != cudaSuccess || !graph) return cuda_status(ce == cudaSuccess ? cudaErrorUnknown : ce);

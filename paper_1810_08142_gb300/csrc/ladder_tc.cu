@@ -743,7 +743,7 @@ __device__ __forceinline__ int gemm2_slot(const TcArgs &A, int u) {
   return (u % tcs) * A.ksplit + u / tcs;
 }
 
-template <int S>
+template <int S, bool kBatch>
 __global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_constant__ TcLaunch Lp) {
   using C = Cfg2<S>;
   static_assert(C::kStages >= 3 && C::kStages <= 10, "ring depth");
@@ -780,8 +780,8 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
   const int it0 = blockIdx.x, itstep = gridDim.x, nit = Lp.nitems;
-  const TcArgs &A = Lp.one;
-  const Watchdog wd{A.status, abort_flag, Lp.timeout_ns};
+  const TcArgs &A0args = kBatch ? Lp.mols[0] : Lp.one;
+  const Watchdog wd{A0args.status, abort_flag, Lp.timeout_ns};
   constexpr int kPieces = SLOTS / TPIECE;
 
   if (warp == 0) {
@@ -791,9 +791,11 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_
       uint32_t phase = 0;
       uint32_t armed = 0, armed_par = 0;
       bool ok = true;
-      tma_prefetch_desc(&A.tmVl);
       for (int it = it0; ok && it < nit; it += itstep) {
-        const Item I = decode_item(A, gemm2_slot(A, it));
+        int local;
+        const TcArgs &A = item_args<kBatch>(Lp, it, local);
+        const Item I = decode_item(A, gemm2_slot(A, local));
+        tma_prefetch_desc(&A.tmVl);
         const TcChunk &CH = I.CH;
         const uint32_t tbytes = I.sc * 32u;
         const int sg = CH.nps > 0 ? 0 : 1;  // the chunk's sign
@@ -819,7 +821,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_
         }
       }
       if (!ok) {
-        DrainWatch dw(A.status, Lp.timeout_ns);
+        DrainWatch dw(A0args.status, Lp.timeout_ns);
         for (int s = 0; s < C::kStages; ++s)
           if (armed & (1u << s)) mbar_wait(bars.full(s), (armed_par >> s) & 1u, dw.wd, kSiteTmaFull);
       }
@@ -832,8 +834,9 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_
       const uint32_t hi32 = desc_hi(256, kSwizzle32);
       bool ok = true;
       for (int it = it0; ok && it < nit; it += itstep) {
-        const Item I = decode_item(A, gemm2_slot(A, it));
-        const TcChunk &CH = I.CH;
+        int local;
+        const TcArgs &A = item_args<kBatch>(Lp, it, local);
+        const Item I = decode_item(A, gemm2_slot(A, local));
         const uint32_t id = idesc_bf16(128, (int)I.sc);
         const uint32_t tbytes = I.sc * 32u;
         for (int p = I.p0; ok && p < I.p1; ++p)
@@ -864,7 +867,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_
           }
       }
       mma_commit(bars.done());
-      DrainWatch dw(A.status, Lp.timeout_ns);
+      DrainWatch dw(A0args.status, Lp.timeout_ns);
       mbar_wait(bars.done(), 0, dw.wd, kSiteRFull);
     }
   } else {
@@ -878,7 +881,9 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_
     const uint64_t pol = l2_evict_last_policy();
     float R[kGroupsV * 16];
     for (int it = it0; ok && it < nit; it += itstep) {
-      const Item I = decode_item(A, gemm2_slot(A, it));
+      int local;
+      const TcArgs &A = item_args<kBatch>(Lp, it, local);
+      const Item I = decode_item(A, gemm2_slot(A, local));
       const int sc = (int)I.sc;
       const int ng = (sc - 16 * half + 31) / 32;  // this warp's groups: columns 16*half + 32*k
       float2 *racc = I.racc + L;
@@ -937,8 +942,10 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_
 // taking R- from the minus chunk of lambda- = j(j-1)/2 + i.  Lane = ab slot,
 // as in unpack_kernel; every element of R is written once.
 __global__ void __launch_bounds__(128) unpack2_kernel(const __grid_constant__ TcLaunch Lp) {
-  const TcArgs &A = Lp.one;
-  const int tile = blockIdx.x / A.nplus, cp = blockIdx.x % A.nplus;
+  // a batch lists its blocks as (molecule, block of that molecule) in tcs
+  const TcArgs &A = Lp.mols ? Lp.mols[Lp.tcs[blockIdx.x].x] : Lp.one;
+  const int blk = Lp.mols ? Lp.tcs[blockIdx.x].y : (int)blockIdx.x;
+  const int tile = blk / A.nplus, cp = blk % A.nplus;
   int iA = 0, t = tile;
   while (t >= A.nB8 - 2 * iA) {
     t -= A.nB8 - 2 * iA;
@@ -993,7 +1000,10 @@ static cudaError_t set_smem_attrs() {
     e = cudaFuncSetAttribute(ladder_tc_kernel<S, true, false>, at, (int)Cfg<S, false>::kSmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(ladder_tc_kernel<S, false, true>, at, (int)Cfg<S, true>::kSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(ladder_gemm2_kernel<S>, at, (int)Cfg2<S>::kSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(ladder_tc_kernel<S, true, true>, at, (int)Cfg<S, true>::kSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(ladder_gemm2_kernel<S, false>, at, (int)Cfg2<S>::kSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(ladder_gemm2_kernel<S, true>, at, (int)Cfg2<S>::kSmem);
   return e;
 }
 
@@ -1018,20 +1028,34 @@ cudaError_t launch_ladder_tc(const TcLaunch &a, int nslices, int grid, cudaStrea
 }
 
 cudaError_t launch_ladder_vstore(const TcLaunch &a, int nslices, int grid, cudaStream_t s) {
-  if (a.mols) return cudaErrorInvalidValue;
-  if (nslices == 2)
-    ladder_tc_kernel<2, false, true><<<grid, kThreads, Cfg<2, true>::kSmem, s>>>(a);
-  else
-    ladder_tc_kernel<3, false, true><<<grid, kThreads, Cfg<3, true>::kSmem, s>>>(a);
+  const bool batch = a.mols != nullptr;
+  if (nslices == 2) {
+    if (batch)
+      ladder_tc_kernel<2, true, true><<<grid, kThreads, Cfg<2, true>::kSmem, s>>>(a);
+    else
+      ladder_tc_kernel<2, false, true><<<grid, kThreads, Cfg<2, true>::kSmem, s>>>(a);
+  } else {
+    if (batch)
+      ladder_tc_kernel<3, true, true><<<grid, kThreads, Cfg<3, true>::kSmem, s>>>(a);
+    else
+      ladder_tc_kernel<3, false, true><<<grid, kThreads, Cfg<3, true>::kSmem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_ladder_gemm2(const TcLaunch &a, int nslices, int grid, cudaStream_t s) {
-  if (a.mols) return cudaErrorInvalidValue;
-  if (nslices == 2)
-    ladder_gemm2_kernel<2><<<grid, kThreads, Cfg2<2>::kSmem, s>>>(a);
-  else
-    ladder_gemm2_kernel<3><<<grid, kThreads, Cfg2<3>::kSmem, s>>>(a);
+  const bool batch = a.mols != nullptr;
+  if (nslices == 2) {
+    if (batch)
+      ladder_gemm2_kernel<2, true><<<grid, kThreads, Cfg2<2>::kSmem, s>>>(a);
+    else
+      ladder_gemm2_kernel<2, false><<<grid, kThreads, Cfg2<2>::kSmem, s>>>(a);
+  } else {
+    if (batch)
+      ladder_gemm2_kernel<3, true><<<grid, kThreads, Cfg2<3>::kSmem, s>>>(a);
+    else
+      ladder_gemm2_kernel<3, false><<<grid, kThreads, Cfg2<3>::kSmem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -1040,9 +1064,8 @@ cudaError_t launch_unpack(const TcLaunch &a, int nblocks, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_unpack2(const TcLaunch &a, cudaStream_t s) {
-  if (a.mols) return cudaErrorInvalidValue;
-  unpack2_kernel<<<a.one.ntiles * a.one.nplus, 128, 0, s>>>(a);
+cudaError_t launch_unpack2(const TcLaunch &a, int nblocks, cudaStream_t s) {
+  unpack2_kernel<<<nblocks, 128, 0, s>>>(a);
   return cudaGetLastError();
 }
 

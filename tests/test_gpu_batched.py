@@ -76,3 +76,39 @@ def test_ragged48_sampled_columns(lad):
         worst = max(worst, rel_fro(got, ref))
     print("ragged48 worst sampled rel-F %.3e" % worst)
     assert worst < TOL["bf16x6"]
+
+
+TWO_PASS_SHAPES = [(12, 32, 40, 410), (3, 17, 40, 411), (16, 24, 48, 412), (20, 17, 33, 413),
+                   (6, 24, 96, 414)]
+
+
+def test_batch_with_two_pass_members(lad):
+    """Molecules whose occupied pairs need several chunks run in the two-pass
+    form inside the batch (one storing launch and one GEMM2 launch over all
+    of them), the others in the fused launch.  Each molecule against the
+    oracle, and bitwise against a single-molecule launch in the same form and
+    block-pair split (the storing pass's work grouping does not change any
+    value)."""
+    import torch
+    mols = [synthetic.make_inputs(o, v, n, s) for o, v, n, s in TWO_PASS_SHAPES]
+    taus = [oracle.tau(x.t1, x.t2) for x in mols]
+    Bs_d = [to_dev(x.B) for x in mols]
+    taus_d = [to_dev(t) for t in taus]
+    batch = lad.LadderBatch([(x.o, x.v, x.naux) for x in mols], mode="bf16x6")
+    R1 = batch.apply(Bs_d, taus_d)
+    R2 = batch.apply(Bs_d, taus_d, R1)       # graph replay into the same outputs
+    torch.cuda.synchronize()
+    batch.check_device()
+    R = [r.cpu().numpy() for r in R2]
+    for k, x in enumerate(mols):
+        ref = oracle.ladder(x.B, taus[k])
+        err = rel_fro(R[k], ref)
+        multi = x.o >= 11
+        print("molecule %d (o=%d v=%d n=%d, %s): rel-F %.3e" % (k, x.o, x.v, x.naux,
+              "two-pass" if multi else "fused", err))
+        assert err < TOL["bf16x6"]
+        tun = {"two_pass": int(multi), "ksplit": 1}
+        L = lad.Ladder(x.o, x.v, x.naux, mode="bf16x6", tuning=tun)
+        Rs = L.apply(Bs_d[k], taus_d[k]).cpu().numpy()
+        assert np.array_equal(Rs, R[k])
+        L.close()
