@@ -199,7 +199,6 @@ def run_ragged(args):
 # A configuration not listed here reports traffic null.
 TRAFFIC = {
     ("mid_o34_v400_n1600", "bf16x6", "pass1", (4, 2, 7)): 771.01e9 + 81.47e9,
-    ("mid_o34_v400_n1600", "bf16x6", "pass2", (4, 2, 7)): 444.05e9 + 70.66e9,
 }
 
 

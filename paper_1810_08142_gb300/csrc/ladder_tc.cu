@@ -718,13 +718,15 @@ __global__ void __launch_bounds__(128) unpack_kernel(const __grid_constant__ TcL
 constexpr uint32_t VP_PLANE = 128u * TPIECE * 2u;  // 4 KB: 128 ab rows x 16 slots
 constexpr uint32_t kColS1 = 256;                   // TMEM: S0 [0, 192), S1 [256, 448)
 constexpr int kGroupsV = kTcMaxColsV / 32;         // 16-column groups per conversion warp
+constexpr int kPPS = 2;                            // 16-slot pieces per TMA stage
 
 template <int S>
 struct Cfg2 {
-  static constexpr uint32_t kV = (uint32_t)S * VP_PLANE;
-  static constexpr uint32_t kT = (uint32_t)S * kTcMaxColsV * 32u;
+  static constexpr uint32_t kV1 = (uint32_t)S * VP_PLANE;  // V planes of one piece
+  static constexpr uint32_t kV = kPPS * kV1;
+  static constexpr uint32_t kT = (uint32_t)kPPS * S * kTcMaxColsV * 32u;
   static constexpr uint32_t kStage = (kV + kT + 1023u) / 1024u * 1024u;
-  static constexpr int kStages = (229376u / kStage) < 10u ? (int)(229376u / kStage) : 10;  // <= 224 KB
+  static constexpr int kStages = (230400u / kStage) < 10u ? (int)(230400u / kStage) : 10;  // <= 225 KB
   static constexpr uint32_t kRing = kStage * kStages;
   static constexpr uint32_t kSmem = kRing + 256 + 1024;
   static constexpr int kProducts = (S == 2) ? 3 : 6;
@@ -801,18 +803,19 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_
         const int sg = CH.nps > 0 ? 0 : 1;  // the chunk's sign
         for (int p = I.p0; ok && p < I.p1; ++p) {
           const int z = ((I.tile * A.nbp + p) * 2 + sg) * S;
-          for (int piece = 0; piece < kPieces; ++piece) {
+          for (int piece = 0; piece < kPieces; piece += kPPS) {
             if (!(ok = mbar_wait(bars.empty(stage), phase ^ 1u, wd, kSiteTmaEmpty))) break;
             const uint32_t dst = ring + (uint32_t)stage * C::kStage;
-            mbar_arrive_expect_tx(bars.full(stage), C::kV + (uint32_t)S * tbytes);
+            mbar_arrive_expect_tx(bars.full(stage), C::kV + (uint32_t)(kPPS * S) * tbytes);
             armed |= 1u << stage;
             armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
             // (default L2 policy for both: marking the tau+- copy evict-last
             // or the V+- planes evict-first measured slower)
-            tma_load_3d(dst, &A.tmVl, bars.full(stage), piece * TPIECE, 0, z);
-            // the chunk's tau+- rows of this piece, every slice: one bulk copy
+            for (int j = 0; j < kPPS; ++j)
+              tma_load_3d(dst + j * C::kV1, &A.tmVl, bars.full(stage), (piece + j) * TPIECE, 0, z);
+            // the chunk's tau+- rows of these pieces, every slice: one bulk copy
             bulk_load(dst + C::kV, A.T2 + CH.t2off + (size_t)(p * kPieces + piece) * S * tbytes,
-                      (uint32_t)S * tbytes, bars.full(stage));
+                      (uint32_t)(kPPS * S) * tbytes, bars.full(stage));
             if (++stage == C::kStages) {
               stage = 0;
               phase ^= 1u;
@@ -840,29 +843,34 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_
         const uint32_t id = idesc_bf16(128, (int)I.sc);
         const uint32_t tbytes = I.sc * 32u;
         for (int p = I.p0; ok && p < I.p1; ++p)
-          for (int piece = 0; ok && piece < kPieces; ++piece) {
-            const bool first = (piece % A.s_pieces) == 0;
-            const uint32_t buf = g & 1u;
-            if (first) {
-              if (!(ok = mbar_wait(bars.cfree(buf), ((g >> 1) & 1u) ^ 1u, wd, kSiteRFree))) break;
-              tc_fence_after();
-            }
+          for (int piece0 = 0; ok && piece0 < kPieces; piece0 += kPPS) {
             if (!(ok = mbar_wait(bars.full(stage), phase, wd, kSiteTmaFull))) break;
             tc_fence_after();
             const uint32_t st = ring + (uint32_t)stage * C::kStage;
-            const uint32_t dS = tmem + buf * kColS1;
+            for (int j = 0; ok && j < kPPS; ++j) {
+              const int piece = piece0 + j;
+              const bool first = (piece % A.s_pieces) == 0;
+              const uint32_t buf = g & 1u;
+              if (first) {
+                if (!(ok = mbar_wait(bars.cfree(buf), ((g >> 1) & 1u) ^ 1u, wd, kSiteRFree))) break;
+                tc_fence_after();
+              }
+              const uint32_t dS = tmem + buf * kColS1;
+              const uint32_t sv = st + j * C::kV1, stt = st + C::kV + (uint32_t)(j * S) * tbytes;
 #pragma unroll
-            for (int q = 0; q < C::kProducts; ++q)
-              mma_bf16(dS, desc64(st + (uint32_t)kPa(q) * VP_PLANE, hi32),
-                       desc64(st + C::kV + kPb(q) * tbytes, hi32), id, (first && q == 0) ? 0u : 1u);
+              for (int q = 0; q < C::kProducts; ++q)
+                mma_bf16(dS, desc64(sv + (uint32_t)kPa(q) * VP_PLANE, hi32), desc64(stt + kPb(q) * tbytes, hi32),
+                         id, (first && q == 0) ? 0u : 1u);
+              if ((piece + 1) % A.s_pieces == 0) {
+                mma_commit(bars.cfull(buf));
+                ++g;
+              }
+            }
+            if (!ok) break;
             mma_commit(bars.empty(stage));
             if (++stage == C::kStages) {
               stage = 0;
               phase ^= 1u;
-            }
-            if ((piece + 1) % A.s_pieces == 0) {
-              mma_commit(bars.cfull(buf));
-              ++g;
             }
           }
       }
