@@ -88,8 +88,8 @@ struct TcChunk {
   long long t2off;  // two-pass GEMM2: byte offset of the chunk's tau+- copy (pack_t2)
 };
 struct TcArgs {
-  CUtensorMap tmA;   // B slices, box (32 aux, 8 c, 16 a), 64-byte swizzle
-  CUtensorMap tmB;   // B slices, box (32 aux, 8 d, 8 b)
+  CUtensorMap tmA;   // B slices [S][a][c][P] as 4-D, box (32 aux, 8 c, 16 a, S), 64-byte swizzle
+  CUtensorMap tmB;   // the same, box (32 aux, 8 d, 8 b, S)
   CUtensorMap tmTp;  // tau+ slices [S][lambda+][K], box (16 slots, 16 rows, 1)
   CUtensorMap tmTm;  // tau- slices [S][lambda-][K]
   CUtensorMap tmVl;  // stored V+- planes [tile][pair][sign][slice][128 rows][64 slots],

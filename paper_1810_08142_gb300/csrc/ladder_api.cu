@@ -59,6 +59,20 @@ bool encode3d(CUtensorMap *m, void *base, uint64_t d0, uint64_t d1, uint64_t d2,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 4-D bf16 map: dims (d0, d1, d2, d3), d0 contiguous, box (b0, b1, b2, b3).
+bool encode4d(CUtensorMap *m, void *base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t d3,
+              uint32_t b0, uint32_t b1, uint32_t b2, uint32_t b3, CUtensorMapSwizzle sw) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[4] = {d0, d1, d2, d3};
+  const cuuint64_t strides[3] = {d0 * 2, d0 * d1 * 2, d0 * d1 * d2 * 2};
+  const cuuint32_t box[4] = {b0, b1, b2, b3};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 struct ladder_plan_s {
@@ -446,9 +460,9 @@ static ladder_status encode_maps(ladder_plan_s *pl, char *w) {
   if (pl->mode == LADDER_FP64) return LADDER_OK;
   const uint64_t S = pl->S;
   const bool ok =
-      encode3d(&pl->tmA, w + pl->lay.Bt, pl->Np, pl->vp, pl->vp * S, 32, 8, 16,
+      encode4d(&pl->tmA, w + pl->lay.Bt, pl->Np, pl->vp, pl->vp, S, 32, 8, 16, (uint32_t)S,
                CU_TENSOR_MAP_SWIZZLE_64B) &&
-      encode3d(&pl->tmB, w + pl->lay.Bt, pl->Np, pl->vp, pl->vp * S, 32, 8, 8,
+      encode4d(&pl->tmB, w + pl->lay.Bt, pl->Np, pl->vp, pl->vp, S, 32, 8, 8, (uint32_t)S,
                CU_TENSOR_MAP_SWIZZLE_64B) &&
       encode3d(&pl->tmTp, w + pl->lay.Tp, pl->K, pl->nlp, S, 16, 16, 1, CU_TENSOR_MAP_SWIZZLE_32B) &&
       encode3d(&pl->tmTm, w + pl->lay.Tm, pl->K, std::max(pl->nlm, 1), S, 16, 16, 1,

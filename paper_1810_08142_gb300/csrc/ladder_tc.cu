@@ -278,12 +278,9 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
                 armed |= 1u << stage;
                 armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
                 const int ca = (tt == 0 ? k : l) * CB, cb = (tt == 0 ? l : k) * CB;
-  #pragma unroll
-                for (int s = 0; s < S; ++s) {
-                  tma_load_3d(dst + s * A_TILE, &A.tmA, bars.full(stage), ks * KSTEP, ca, s * A.vp + A0);
-                  tma_load_3d(dst + S * A_TILE + s * B_TILE, &A.tmB, bars.full(stage), ks * KSTEP, cb,
-                              s * A.vp + B0);
-                }
+                // all S slices of each operand tile in one 4-D box
+                tma_load_4d(dst, &A.tmA, bars.full(stage), ks * KSTEP, ca, A0, 0);
+                tma_load_4d(dst + S * A_TILE, &A.tmB, bars.full(stage), ks * KSTEP, cb, B0, 0);
                 if (++stage == C::kStages) {
                   stage = 0;
                   phase ^= 1u;
