@@ -353,8 +353,9 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
               const int ks0 = c * kc, ks1 = min(A.nks, ks0 + kc);
               for (int ks = ks0; ok && ks < ks1; ++ks)
                 for (int tt = 0; tt < ntile; ++tt) {
+                  // operands written by TMA and read by the MMA (both async
+                  // proxy): the barrier's transaction count orders them
                   if (!(ok = mbar_wait(bars.full(stage), phase, wd, kSiteTmaFull))) break;
-                  tc_fence_after();
                   const uint32_t st = ring + (uint32_t)stage * C::kStage;
                   if constexpr (kStoreV) {
                     // The S slices of B sit back to back (64 rows each), so
@@ -842,7 +843,6 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_
         for (int p = I.p0; ok && p < I.p1; ++p)
           for (int piece0 = 0; ok && piece0 < kPieces; piece0 += kPPS) {
             if (!(ok = mbar_wait(bars.full(stage), phase, wd, kSiteTmaFull))) break;
-            tc_fence_after();
             const uint32_t st = ring + (uint32_t)stage * C::kStage;
             for (int j = 0; ok && j < kPPS; ++j) {
               const int piece = piece0 + j;
