@@ -1,12 +1,14 @@
 """Benchmark of the particle-particle ladder term on GB300.
 
 One step = one pass of the whole path on one molecule's inputs already in HBM:
-tau assembly, operand slicing / pair packing, the fused ladder kernel, the
-unpacking of R, and the FP64 ladder energy.  The headline metric is ladder
-TFLOP/s (algorithmic flops of the symmetric/antisymmetric scheme / time) of
-the split-BF16 path in the mode that meets the R tolerance (BF16X6), on the
-mid-size workload (o=34, v=400, N_aux=1600).  The FP64 path and BF16X3 are
-timed on the same workload and reported beside it.
+tau assembly, operand slicing / pair packing, the ladder kernels (the fused
+kernel, or the storing and GEMM2 passes of the two-pass form, as the plan or
+the autotuner's cache chooses; --form forces one), the unpacking of R, and the
+FP64 ladder energy.  The headline metric is ladder TFLOP/s (algorithmic flops
+of the symmetric/antisymmetric scheme / time) of the split-BF16 path in the
+mode that meets the R tolerance (BF16X6), on the mid-size workload (o=34,
+v=400, N_aux=1600).  The other form, BF16X3 and the FP64 path are timed on the
+same workload and reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -402,7 +404,7 @@ def main():
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
                 "kernel": "ladder_tc_kernel<%d,false,false>" % (2 if args.mode == "bf16x3" else 3),
-                "note": "achieved = %d x F_alg (bf16 tensor flops of the split scheme) / fused-kernel "
+                "note": "achieved = %d x F_alg (bf16 tensor flops of the split scheme) / ladder-kernel "
                         "time; peak = bf16 sustained (%s)" % (prod, pk_kind)}
 
     extra = {}

@@ -162,19 +162,23 @@ ladder_status ladder_apply_host(ladder_plan_t plan, const double *B_host, const 
                                 void *stream);
 
 /* Ragged batch: n molecules with their own (o_k, v_k, naux_k), one plan and one
- * workspace; mode LADDER_BF16X3 or LADDER_BF16X6 (else LADDER_ENOTSUP).  The
- * fused kernel of every molecule runs in one persistent launch over all
- * molecules' work units, ordered by cost (largest first).  A batched plan
+ * workspace; mode LADDER_BF16X3 or LADDER_BF16X6 (else LADDER_ENOTSUP).
+ * Molecules whose occupied pairs fit one chunk of the fused kernel run in one
+ * persistent fused launch over all their work units, ordered by cost (largest
+ * first); molecules that need several chunks take the two-pass form (see
+ * ladder_tuning) while their stored V+- tiles fit 128 GiB in all, with one
+ * storing launch and one GEMM2 launch over all of them.  A batched plan
  * serves only ladder_apply_batched (the other calls return LADDER_EINVAL);
  * ladder_energy_noalloc gives the energy of each molecule. */
 ladder_status ladder_plan_batched(int n, const int *o, const int *v, const int *naux, int mode,
                                   ladder_plan_t *out);
 /* B[k], tau[k], R[k] are device pointers for molecule k (host arrays of n
  * pointers).  The first call with a given set of pointers records the whole
- * batch (operand preparation of every molecule, the fused launch, the unpack)
- * as a CUDA graph on a private stream; it synchronises `stream` and copies the
- * per-molecule arguments into the workspace first.  Calls with the same
- * pointers replay the graph on `stream` without synchronising. */
+ * batch (operand preparation of every molecule, the fused, storing and GEMM2
+ * launches, the unpacks) as a CUDA graph on a private stream; it synchronises
+ * `stream` and copies the per-molecule arguments into the workspace first.
+ * Calls with the same pointers replay the graph on `stream` without
+ * synchronising. */
 ladder_status ladder_apply_batched(ladder_plan_t plan, const double *const *B,
                                    const double *const *tau, double *const *R, void *stream);
 
@@ -192,7 +196,7 @@ ladder_status ladder_selftest_wait(ladder_plan_t plan, unsigned long long timeou
 
 /* Stage timing of ladder_apply.  With timing on, ladder_apply records CUDA
  * events on its stream around its three stages (operand preparation: slicing
- * and packing; the fused ladder kernel; unpacking of R).  ladder_timing waits
+ * and packing; the ladder kernels, fused or both passes; unpacking of R).  ladder_timing waits
  * for the events of the last ladder_apply and returns the three durations in
  * milliseconds (any pointer may be NULL).  Timing is off by default; the
  * events are created by ladder_set_timing (no device memory). */

@@ -211,7 +211,8 @@ def ladder_set_timing(plan, on: bool) -> None:
 
 
 def ladder_timing(plan):
-    """(prep_ms, fused_ms, unpack_ms) of the last ladder_apply (waits for it)."""
+    """(prep_ms, ladder_ms, unpack_ms) of the last ladder_apply (waits for it);
+    ladder_ms covers the fused kernel or both passes of the two-pass form."""
     t = [ctypes.c_float() for _ in range(3)]
     _check("ladder_timing", load_library().ladder_timing(plan, *[ctypes.byref(x) for x in t]))
     return tuple(x.value for x in t)
@@ -329,8 +330,9 @@ class Ladder:
 
 
 class LadderBatch:
-    """A batched plan for molecules of uneven shape (one persistent fused
-    launch, replayed as a CUDA graph) plus its workspace."""
+    """A batched plan for molecules of uneven shape (persistent launches over
+    all molecules' work units, fused or two-pass per molecule, replayed as a
+    CUDA graph) plus its workspace."""
 
     def __init__(self, shapes, mode="bf16x6", device=None):
         import torch
