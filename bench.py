@@ -442,28 +442,60 @@ def main():
     if "fp64" in extra:
         extra["speedup_vs_fp64"] = extra["fp64"]["ms_per_step"] / ms
 
-    # end to end through the public API with host buffers: inputs copied from
-    # pinned host memory each step, E_L read back each step
+    # end to end through the public API with host buffers: every step copies
+    # its inputs from pinned host memory and reads E_L back.  The device
+    # inputs are double-buffered: step k+1's copies run on a copy stream while
+    # step k computes (the copy of a buffer waits until the step that last
+    # used it is done), all inside the timed region.
     e2e = None
     if not args.no_e2e:
         h_t1 = torch.from_numpy(x.t1).pin_memory()
         h_t2 = torch.from_numpy(x.t2).pin_memory()
         h_B = torch.from_numpy(x.B).pin_memory()
+        bufs = [(t1, t2, B), (torch.empty_like(t1), torch.empty_like(t2), torch.empty_like(B))]
+        cstream = torch.cuda.Stream(device=dev)
+        copied = [torch.cuda.Event() for _ in range(2)]
+        free = [torch.cuda.Event() for _ in range(2)]
+        used = [False, False]
+
+        def copy_in(k):
+            i = k % 2
+            with torch.cuda.stream(cstream):
+                if used[i]:
+                    cstream.wait_event(free[i])
+                bufs[i][0].copy_(h_t1, non_blocking=True)
+                bufs[i][1].copy_(h_t2, non_blocking=True)
+                bufs[i][2].copy_(h_B, non_blocking=True)
+                copied[i].record(cstream)
+
+        def step_on(k):
+            i = k % 2
+            stream.wait_event(copied[i])
+            lad.ladder_tau(L.plan, bufs[i][0], bufs[i][1], tau)
+            lad.ladder_apply(L.plan, bufs[i][2], tau, R)
+            lad.ladder_energy(L.plan, R, bufs[i][1], E)
+            free[i].record(stream)
+            used[i] = True
+
         barrier()
         q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         q0.record(stream)
-        for _ in range(args.steps):
-            t1.copy_(h_t1, non_blocking=True)
-            t2.copy_(h_t2, non_blocking=True)
-            B.copy_(h_B, non_blocking=True)
-            step(L)
+        cstream.wait_event(q0)
+        copy_in(0)
+        for k in range(args.steps):
+            if k + 1 < args.steps:
+                copy_in(k + 1)
+            step_on(k)
             _ = float(E.item())
         q1.record(stream)
         barrier()
         ems = max_over_ranks(q0.elapsed_time(q1) / args.steps)
         h2d = (h_t1.numel() + h_t2.numel() + h_B.numel()) * 8
         e2e = {"value": rep.job_value(F, ems) / 1e12, "unit": "TFLOP/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8, "ms_per_step": ems}
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8, "ms_per_step": ems,
+               "note": "inputs double-buffered on the device; copies overlap the previous step"}
+        del bufs
+        torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and not args.no_cpu:
