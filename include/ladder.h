@@ -84,8 +84,7 @@ ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out);
  *               sliced V+- tiles stored in the workspace (2S x 16 KiB per
  *               tile and block pair), then GEMM2 from the stored tiles in
  *               chunks of up to 192 occupied pairs.  The plan picks 1 when the
- *               fused kernel would need more than one chunk and the stored
- *               tiles take at most 128 GiB.
+ *               stored tiles take at most 128 GiB.
  * Longer chains are faster and less accurate (the tensor core's FP32
  * accumulation error grows with the MMAs per accumulator).  ladder_set_tuning
  * must come before ladder_set_workspace (the workspace size depends on

@@ -108,18 +108,23 @@ def tune(o: int, v: int, naux: int, tol: float = 1e-6, reps: int = 2, seed: int 
     nref = torch.linalg.vector_norm(ref).item()
     B, tau = _inputs(o, v, naux, seed + 1, dev)
     R = torch.empty_like(tau)
-    # the two-pass form is a candidate where the plan would choose it (the
-    # fused kernel needs several chunks and the stored tiles fit)
+    # both forms are candidates: the two-pass form can win even where the
+    # fused kernel needs one chunk (its storing pass issues wider MMAs);
+    # a form whose workspace does not fit the device is skipped below
     from . import ladder_get_tuning
-    L0 = Ladder(o, v, naux, mode="bf16x6", device=dev)
-    forms = (0, 1) if ladder_get_tuning(L0.plan).two_pass else (0,)
-    L0.close()
+    forms = (0, 1)
     results = []
     for mode, tun in candidates(forms):
+        try:
+            L = Ladder(o, v, naux, mode=mode, device=dev, tuning=tun)
+        except (RuntimeError, MemoryError) as exc:  # workspace too large for the device
+            if verbose:
+                print("%-7s %-60s skipped (%s)" % (mode, tun, str(exc).splitlines()[0][:60]), flush=True)
+            torch.cuda.empty_cache()
+            continue
         Lp = Ladder(o, vp, naux, mode=mode, device=dev, tuning=tun)
         err = torch.linalg.vector_norm(Lp.apply(Bp, taup) - ref).item() / nref
         Lp.close()
-        L = Ladder(o, v, naux, mode=mode, device=dev, tuning=tun)
         full = ladder_get_tuning(L.plan).as_dict()
         ms = _time_ms(L, B, tau, R, reps)
         L.close()
