@@ -25,22 +25,25 @@ def lad():
     return lad
 
 
-@pytest.mark.parametrize("mode", ["fp64", "bf16x6", "bf16x3"])
-@pytest.mark.parametrize("o,v,n,seed", [(3, 10, 30, 3), (4, 24, 96, 0), (5, 17, 33, 12), (6, 40, 90, 21)])
-def test_backward_matches_oracle_gradient(lad, mode, o, v, n, seed):
+@pytest.mark.parametrize("mode,two_pass", [("fp64", 0), ("bf16x6", 0), ("bf16x6", 1), ("bf16x3", 1)])
+@pytest.mark.parametrize("o,v,n,seed", [(3, 10, 30, 3), (4, 24, 96, 0), (5, 17, 33, 12), (6, 40, 90, 21),
+                                         (12, 24, 40, 22)])
+def test_backward_matches_oracle_gradient(lad, mode, two_pass, o, v, n, seed):
+    """dtau runs the transposed ladder in the plan's form (fused or two-pass)."""
     import torch
     rng = np.random.default_rng(seed)
     B = rng.standard_normal((n, v, v)) * 0.1          # general B (no a<->c symmetry)
     x = synthetic.make_inputs(o, v, n, seed)
     tau = oracle.tau(x.t1, x.t2)
     W = oracle.energy_weights(x.t2)
-    L = lad.Ladder(o, v, n, mode=mode, backward=True)
+    L = lad.Ladder(o, v, n, mode=mode, backward=True,
+                   tuning=None if mode == "fp64" else {"two_pass": two_pass})
     dtau, dB = L.backward(to_dev(B), to_dev(tau), to_dev(W))
     torch.cuda.synchronize()
     L.check_device()
     e_tau = rel_fro(dtau.cpu().numpy(), oracle.grad_tau(B, W))
     e_B = rel_fro(dB.cpu().numpy(), oracle.grad_B(B, tau, W))
-    print("%s o=%d v=%d n=%d: dtau rel-F %.3e  dB rel-F %.3e" % (mode, o, v, n, e_tau, e_B))
+    print("%s two_pass=%d o=%d v=%d n=%d: dtau rel-F %.3e  dB rel-F %.3e" % (mode, two_pass, o, v, n, e_tau, e_B))
     assert e_tau < DTAU_TOL[mode]
     assert e_B < DTAU_TOL[mode]  # dB runs in the plan's mode as well
 

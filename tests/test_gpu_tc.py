@@ -39,16 +39,19 @@ def lad():
 
 
 @pytest.mark.parametrize("mode", ["bf16x3", "bf16x6"])
+@pytest.mark.parametrize("two_pass", [0, 1])
 @pytest.mark.parametrize("o,v,n,seed", SHAPES)
-def test_tc_matches_oracle(lad, mode, o, v, n, seed):
+def test_tc_matches_oracle(lad, mode, two_pass, o, v, n, seed):
+    """Both forms (fused kernel, two-pass) on every shape."""
     x = synthetic.make_inputs(o, v, n, seed)
-    L = lad.Ladder(o, v, n, mode=mode)
+    L = lad.Ladder(o, v, n, mode=mode, tuning={"two_pass": two_pass})
     _, R_g, E_g = run_forward(L, x)
     tau_o = oracle.tau(x.t1, x.t2)
     R_o = oracle.ladder(x.B, tau_o)
     E_o = oracle.energy(R_o, x.t2)
     err = rel_fro(R_g, R_o)
-    print("%s o=%d v=%d n=%d: rel-F %.3e  |dE| %.3e  E %.6e" % (mode, o, v, n, err, abs(E_g - E_o), E_o))
+    print("%s two_pass=%d o=%d v=%d n=%d: rel-F %.3e  |dE| %.3e  E %.6e" % (mode, two_pass, o, v, n, err,
+                                                                          abs(E_g - E_o), E_o))
     assert err < TOL[mode]
     # pair symmetry of the output holds by construction of the unpacking
     assert np.array_equal(R_g, R_g.transpose(1, 0, 3, 2))
