@@ -67,6 +67,8 @@ struct GradTcArgs {
   CUtensorMap tmBs;  // B slices [S][P][D][b][dl], box (16 (b,dl), 1 D, 16 P), 32-byte swizzle
   double *dB;        // [N][v][v]
   float2 *racc;      // double-single sums, [item][128 cols][128 lanes]
+  __nv_bfloat16 *Gst;  // two-pass dB: Gamma planes [tile][(b,d) block][slice][128][64]
+  int qsplit;          // two-pass dB: (b,d)-block ranges per tile of the storing pass
   int *status;
   int o, v, N, vp, Np, IJp, nks, nY8, ntiles, npc;
   int kc, s_pieces, flush_every;
@@ -74,6 +76,9 @@ struct GradTcArgs {
 };
 cudaError_t grad_tc_init_attributes(int nslices);
 cudaError_t launch_grad_B_tc(const GradTcArgs &a, int nslices, cudaStream_t s);
+// Two-pass dB: the Gamma tiles of every (x,y) tile and (b,d) block stored once
+// (the contraction with B then runs in the GEMM2 kernel, see TcArgs::square).
+cudaError_t launch_grad_gamma_store(const GradTcArgs &a, int nslices, cudaStream_t s);
 
 // ---- split-BF16 fused ladder (tcgen05)
 // An occupied-pair chunk of the tensor-core kernel: lambda+ rows [lp0, lp0+np)
@@ -109,6 +114,8 @@ struct TcArgs {
   int s_pieces;      // 16-slot pieces of GEMM2 per fresh S accumulator (1, 2 or 4)
   int flush_every;   // S accumulators summed in FP32 before a flush to the double-single sums
   int nplus, wplus, wminus;  // two-pass GEMM2: plus chunks first, lambda columns per chunk
+  int square;        // GEMM2 kernel: tiles cover every (16-block, 8-block) pair (two-pass dB)
+  int nsign;         // GEMM2 kernel: stored planes per (tile, block) = nsign * S
   unsigned long long timeout_ns;
   TcChunk chunks[kMaxChunks];
 };
@@ -121,6 +128,17 @@ struct T2Args {
   long long off[kMaxChunks];     // element offset of each chunk in T2
 };
 void launch_pack_t2(const T2Args &a, cudaStream_t s);
+
+// Per-chunk, pre-swizzled copy of the B slices as the GEMM2 kernel's second
+// operand: for aux chunk c, (b,d) block q and 16-slot piece, rows P of the
+// chunk; slot (b_l, d_l) of block q holds slice s of B^P_{8Bb+b_l, 8Dd+d_l}.
+struct BpackArgs {
+  const double *B;    // [N][v][v]
+  __nv_bfloat16 *T2;
+  int N, v, nb, S, nchunks;
+  TcChunk chunks[kMaxChunks];  // lp0 = first P, np = P count, nps = padded rows
+};
+void launch_pack_b2(const BpackArgs &a, cudaStream_t s);
 
 // One launch of the fused kernel: a single molecule (mols == nullptr, the
 // work units are 0..nitems-1 of `one`) or a batch (work unit k is local item
@@ -145,6 +163,8 @@ cudaError_t launch_ladder_gemm2(const TcLaunch &a, int nslices, int grid, cudaSt
 cudaError_t launch_unpack(const TcLaunch &a, int nblocks, cudaStream_t s);
 // two-pass form: nblocks = tiles x plus-chunks (a batch lists (molecule, block) in tcs)
 cudaError_t launch_unpack2(const TcLaunch &a, int nblocks, cudaStream_t s);
+// two-pass dB: dB[P][x][y] = 2 x the sums of the GEMM2 kernel, blocks = tiles x chunks
+cudaError_t launch_grad_unpack2(const TcLaunch &a, double *dB, int N, int nblocks, cudaStream_t s);
 cudaError_t launch_selftest_wait(int *status, unsigned long long timeout_ns, int site,
                                  cudaStream_t s);
 

@@ -24,6 +24,7 @@ struct Layout {
   size_t status = 0, energy = 0, Tp = 0, Tm = 0, slab = 0, Bt = 0, W = 0, gslab = 0, total = 0;
   size_t gWt = 0, gTt = 0, gBs = 0, gacc = 0;  // split-BF16 dB
   size_t Vg = 0, T2 = 0;                       // two-pass form: stored V+- tiles, tau+- per chunk
+  size_t gG = 0, gT2 = 0, gacc2 = 0;           // two-pass dB: Gamma planes, B per chunk, sums
 };
 
 // Two-pass form: at most this many bytes of stored V+- tiles by default.
@@ -96,6 +97,11 @@ struct ladder_plan_s {
   CUtensorMap tmA, tmB, tmTp, tmTm, tmVl;
   CUtensorMap tmGW, tmGT, tmGBs;  // split-BF16 dB operands
   int g_IJp = 0, g_Np = 0, g_ntiles = 0, g_npc = 0;
+  // two-pass dB: Gamma stored once, contraction in the GEMM2 kernel
+  bool g2 = false;
+  int g2_ksplit = 1, g2_qsplit = 1, g2_cols = 0;
+  std::vector<TcChunk> g2_chunks;
+  CUtensorMap tmGl;
   Layout lay;
   // ragged batch: one sub-plan per molecule inside this plan's workspace
   bool batched = false;
@@ -272,10 +278,46 @@ void compute_layout(ladder_plan_s *pl) {
     off = L.gWt + S * vp * vp * pl->g_IJp * 2;
     L.gTt = align_up(off, 1024);
     off = L.gTt + S * vp * vp * pl->g_IJp * 2;
-    L.gBs = align_up(off, 1024);
-    off = L.gBs + S * (size_t)pl->g_Np * vp * vp * 2;
-    L.gacc = align_up(off, 1024);
-    off = align_up(L.gacc + (size_t)pl->g_ntiles * pl->g_npc * 128 * kGradTcPChunk * sizeof(double));
+    const size_t nq = (vp / CB) * (vp / CB);
+    const double gbytes = (double)pl->g_ntiles * nq * S * 128 * SLOTS * 2;
+    pl->g2 = gbytes <= 64.0 * (1ull << 30) &&
+             (pl->N + kTcMaxColsV - 1) / kTcMaxColsV <= kMaxChunks;
+    if (const char *e = getenv("LADDER_DB2")) pl->g2 = pl->g2 && atoi(e) != 0;
+    if (pl->g2) {
+      // aux chunks of up to kTcMaxColsV rows, balanced
+      pl->g2_chunks.clear();
+      const int n = (pl->N + kTcMaxColsV - 1) / kTcMaxColsV;
+      const int w = (((pl->N + n - 1) / n) + 15) / 16 * 16;
+      pl->g2_cols = 0;
+      size_t t2 = 0;
+      for (int c = 0; c < n; ++c) {
+        TcChunk t{};
+        t.lp0 = c * w;
+        t.np = std::min(w, pl->N - t.lp0);
+        t.nps = (t.np + 15) / 16 * 16;
+        t.t2off = (long long)t2;
+        t2 += (size_t)nq * 4 * S * t.nps * 32;
+        pl->g2_cols = std::max(pl->g2_cols, t.nps);
+        pl->g2_chunks.push_back(t);
+      }
+      const int items = pl->g_ntiles * n;
+      pl->g2_ksplit = std::max(1, std::min((int)nq, std::max((int)nq / 160,
+                                                             (2 * pl->sm_count + items - 1) / items)));
+      pl->g2_qsplit = std::max(1, std::min((int)nq, std::max((int)nq / 128,
+                                                             (8 * pl->sm_count + pl->g_ntiles - 1) /
+                                                                 pl->g_ntiles)));
+      L.gG = align_up(off, 1024);
+      off = L.gG + (size_t)gbytes;
+      L.gT2 = align_up(off, 1024);
+      off = L.gT2 + t2;
+      L.gacc2 = align_up(off, 1024);
+      off = align_up(L.gacc2 + (size_t)items * pl->g2_ksplit * 128 * pl->g2_cols * sizeof(double));
+    } else {
+      L.gBs = align_up(off, 1024);
+      off = L.gBs + S * (size_t)pl->g_Np * vp * vp * 2;
+      L.gacc = align_up(off, 1024);
+      off = align_up(L.gacc + (size_t)pl->g_ntiles * pl->g_npc * 128 * kGradTcPChunk * sizeof(double));
+    }
   }
   L.total = off;
   pl->lay = L;
@@ -483,8 +525,11 @@ static ladder_status encode_maps(ladder_plan_s *pl, char *w) {
                  CU_TENSOR_MAP_SWIZZLE_64B) &&
         encode3d(&pl->tmGT, w + pl->lay.gTt, pl->g_IJp, vp, vp * S, 32, 8, 8,
                  CU_TENSOR_MAP_SWIZZLE_64B) &&
-        encode3d(&pl->tmGBs, w + pl->lay.gBs, vp * CB, vp / CB, (uint64_t)pl->g_Np * S, 16, 1, 16,
-                 CU_TENSOR_MAP_SWIZZLE_32B);
+        (pl->g2 ? encode3d(&pl->tmGl, w + pl->lay.gG, SLOTS, 128,
+                           (uint64_t)pl->g_ntiles * (vp / CB) * (vp / CB) * S, 16, 128, (uint32_t)S,
+                           CU_TENSOR_MAP_SWIZZLE_32B)
+                : encode3d(&pl->tmGBs, w + pl->lay.gBs, vp * CB, vp / CB, (uint64_t)pl->g_Np * S, 16, 1, 16,
+                           CU_TENSOR_MAP_SWIZZLE_32B));
     if (!okg) return LADDER_ECUDA;
     const ladder_status st = cuda_status(grad_tc_init_attributes(pl->S));
     if (st != LADDER_OK) return st;
@@ -611,6 +656,7 @@ static TcArgs tc_args(const ladder_plan_s *pl, double *R, int *status) {
   a.flush_every = pl->flush_every;
   for (int c = 0; c < a.nchunks; ++c) a.chunks[c] = pl->chunks_tc[c];
   a.timeout_ns = (unsigned long long)tc_timeout_ns(pl);
+  a.nsign = 2;
   return a;
 }
 
@@ -756,6 +802,77 @@ ladder_status ladder_backward(ladder_plan_t pl, const double *B, const double *t
     g.vp = pl->vp;
     const ladder_status st = cuda_status(launch_grad_B_fp64(g, pl->grid_grad, s));
     if (st != LADDER_OK) return st;
+  } else if (dB && pl->g2) {
+    // two-pass dB: Gamma tiles stored once, then their contraction with the
+    // B slices in the GEMM2 kernel (square tiles, one sign), then dB = 2 x sums
+    auto *Wt = ws_at<__nv_bfloat16>(pl, pl->lay.gWt);
+    auto *Tt = ws_at<__nv_bfloat16>(pl, pl->lay.gTt);
+    launch_split_pairs(pl->o, pl->v, pl->vp, pl->g_IJp, pl->S, W, Wt, s);
+    launch_split_pairs(pl->o, pl->v, pl->vp, pl->g_IJp, pl->S, tau, Tt, s);
+    BpackArgs bp;
+    std::memset(&bp, 0, sizeof(bp));
+    bp.B = B;
+    bp.T2 = ws_at<__nv_bfloat16>(pl, pl->lay.gT2);
+    bp.N = pl->N;
+    bp.v = pl->v;
+    bp.nb = pl->vp / CB;
+    bp.S = pl->S;
+    bp.nchunks = (int)pl->g2_chunks.size();
+    for (int c = 0; c < bp.nchunks; ++c) bp.chunks[c] = pl->g2_chunks[c];
+    launch_pack_b2(bp, s);
+    ladder_status st = cuda_status(cudaGetLastError());
+    if (st != LADDER_OK) return st;
+    int *status = ws_at<int>(pl, pl->lay.status);
+    GradTcArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.tmW = pl->tmGW;
+    g.tmT = pl->tmGT;
+    g.Gst = ws_at<__nv_bfloat16>(pl, pl->lay.gG);
+    g.qsplit = pl->g2_qsplit;
+    g.status = status;
+    g.o = pl->o;
+    g.v = pl->v;
+    g.N = pl->N;
+    g.vp = pl->vp;
+    g.IJp = pl->g_IJp;
+    g.nks = pl->g_IJp / 32;
+    g.nY8 = pl->vp / CB;
+    g.ntiles = pl->g_ntiles;
+    g.kc = pl->kc;
+    const int nq = (pl->vp / CB) * (pl->vp / CB);
+    const double unit_flops = 2.0 * 128.0 * 64.0 * pl->g_IJp * 6.0 * ((double)nq / pl->g2_qsplit);
+    g.timeout_ns = (unsigned long long)(2e9 + 20.0 * unit_flops / 4e12 * 1e9);
+    st = cuda_status(launch_grad_gamma_store(g, pl->S, s));
+    if (st != LADDER_OK) return st;
+    TcLaunch L;
+    std::memset(&L, 0, sizeof(L));
+    TcArgs &a = L.one;
+    a.tmVl = pl->tmGl;
+    a.T2 = ws_at<uint8_t>(pl, pl->lay.gT2);
+    a.status = status;
+    a.o = pl->o;
+    a.v = pl->v;
+    a.vp = pl->vp;
+    a.nbp = nq;
+    a.nA = pl->vp / 16;
+    a.nB8 = pl->vp / CB;
+    a.ntiles = pl->g_ntiles;
+    a.nchunks = (int)pl->g2_chunks.size();
+    for (int c = 0; c < a.nchunks; ++c) a.chunks[c] = pl->g2_chunks[c];
+    a.ksplit = pl->g2_ksplit;
+    a.racc = ws_at<float2>(pl, pl->lay.gacc2);
+    a.racc_cols = pl->g2_cols;
+    a.s_pieces = pl->s_pieces;
+    a.flush_every = pl->flush_every;
+    a.square = 1;
+    a.nsign = 1;
+    const double item_flops = 2.0 * 128.0 * pl->g2_cols * 64.0 * 6.0 * ((double)nq / pl->g2_ksplit);
+    a.timeout_ns = (unsigned long long)(2e9 + 20.0 * item_flops / 4e12 * 1e9);
+    L.timeout_ns = a.timeout_ns;
+    L.nitems = a.ntiles * a.nchunks * a.ksplit;
+    st = cuda_status(launch_ladder_gemm2(L, pl->S, L.nitems, s));
+    if (st != LADDER_OK) return st;
+    return cuda_status(launch_grad_unpack2(L, dB, pl->N, a.ntiles * a.nchunks, s));
   } else if (dB) {
     auto *Wt = ws_at<__nv_bfloat16>(pl, pl->lay.gWt);
     auto *Tt = ws_at<__nv_bfloat16>(pl, pl->lay.gTt);

@@ -387,6 +387,198 @@ __global__ void __launch_bounds__(kThreads, 1) grad_B_tc_kernel(const __grid_con
   }
 }
 
+// ---------------------------------------------------------------- two-pass dB, storing pass
+// Gamma^{xb}_{yd} of every (x 16-block, y 8-block) tile and (b, d) block,
+// computed once (Gamma2 as above, K = occupied pairs) and stored as S bf16
+// slices in the layout of the GEMM2 kernel's first operand: plane
+// ((tile * nq + q) * S + s), 128 rows (x, y) x 64 slots (b, d).  The
+// contraction with B^P then runs in that kernel over aux chunks of up to 192,
+// without recomputing Gamma per chunk.  A work unit is a tile and a range of
+// (b, d) blocks (no accumulator depends on the grouping).
+template <int S>
+struct CfgG {
+  static constexpr uint32_t kStage = 12288u * S;
+  static constexpr int kStages = (int)((230400u) / kStage);
+  static constexpr uint32_t kRing = kStage * kStages;
+  static constexpr uint32_t kBar = 256;
+  static constexpr uint32_t kSmem = kRing + kBar + 1024;
+  static constexpr int kProducts = (S == 2) ? 3 : 6;
+};
+
+template <int S>
+__global__ void __launch_bounds__(kThreads, 1) grad_gamma_store_kernel(const __grid_constant__ GradTcArgs A) {
+  using C = CfgG<S>;
+  static_assert(8 * (2 * C::kStages + Bars::kCount) + 8 <= C::kBar, "barrier area");
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
+  uint8_t *smem = smem_raw + pad;
+  const uint32_t ring = raw + pad;
+  Bars bars{ring + C::kRing, C::kStages};
+  uint32_t *tmem_holder =
+      reinterpret_cast<uint32_t *>(smem + C::kRing + 8 * (2 * C::kStages + Bars::kCount));
+  int *abort_flag = reinterpret_cast<int *>(tmem_holder + 1);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+  const int nb = A.vp / CB, nq = nb * nb;
+  const int item = blockIdx.x;
+  const int tile = item / A.qsplit, r = item % A.qsplit;
+  const int q0 = (int)((long long)nq * r / A.qsplit), q1 = (int)((long long)nq * (r + 1) / A.qsplit);
+  const int X0 = (tile / A.nY8) * 16, Y0 = (tile % A.nY8) * CB;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::kStages; ++s) {
+      mbar_init(bars.full(s), 1);
+      mbar_init(bars.empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(bars.cfull(b), 1);
+      mbar_init(bars.cfree(b), kEpi);
+    }
+    mbar_init(bars.done(), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_holder), 256);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+  const Watchdog wd{A.status, abort_flag, A.timeout_ns};
+  const int kc = A.kc;
+  const int nch = (A.nks + kc - 1) / kc;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      tma_prefetch_desc(&A.tmW);
+      tma_prefetch_desc(&A.tmT);
+      int stage = 0;
+      uint32_t phase = 0, armed = 0, armed_par = 0;
+      bool ok = true;
+      for (int q = q0; ok && q < q1; ++q) {
+        const int Bb0 = (q / nb) * CB, Dd0 = (q % nb) * CB;
+        for (int ks = 0; ok && ks < A.nks; ++ks) {
+          if (!(ok = mbar_wait(bars.empty(stage), phase ^ 1u, wd, kSiteTmaEmpty))) break;
+          const uint32_t dst = ring + (uint32_t)stage * C::kStage;
+          mbar_arrive_expect_tx(bars.full(stage), (uint32_t)S * (A_TILE + B_TILE));
+          armed |= 1u << stage;
+          armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+#pragma unroll
+          for (int s = 0; s < S; ++s) {
+            tma_load_3d(dst + s * A_TILE, &A.tmW, bars.full(stage), ks * KSTEP, Bb0, s * A.vp + X0);
+            tma_load_3d(dst + S * A_TILE + s * B_TILE, &A.tmT, bars.full(stage), ks * KSTEP, Dd0,
+                        s * A.vp + Y0);
+          }
+          if (++stage == C::kStages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (!ok) {
+        DrainWatch dw(A.status, A.timeout_ns);
+        for (int s = 0; s < C::kStages; ++s)
+          if (armed & (1u << s)) mbar_wait(bars.full(s), (armed_par >> s) & 1u, dw.wd, kSiteTmaFull);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0, g = 0;
+      const uint32_t id1 = idesc_bf16(128, 64);
+      const uint32_t hi64 = desc_hi(512, kSwizzle64);
+      bool ok = true;
+      for (int q = q0; ok && q < q1; ++q)
+        for (int c = 0; ok && c < nch; ++c) {
+          const int buf = (int)(g & 1u);
+          if (!(ok = mbar_wait(bars.cfree(buf), ((g >> 1) & 1u) ^ 1u, wd, kSiteXYFree))) break;
+          tc_fence_after();
+          const int ks0 = c * kc, ks1 = min(A.nks, ks0 + kc);
+          for (int ks = ks0; ok && ks < ks1; ++ks) {
+            if (!(ok = mbar_wait(bars.full(stage), phase, wd, kSiteTmaFull))) break;
+            const uint32_t st = ring + (uint32_t)stage * C::kStage;
+            const uint32_t dT = tmem + (uint32_t)buf * 128u;
+#pragma unroll
+            for (int kk = 0; kk < KSTEP / 16; ++kk)
+#pragma unroll
+              for (int qq = 0; qq < C::kProducts; ++qq) {
+                const uint64_t ad = desc64(st + kPa(qq) * A_TILE + kk * 32, hi64);
+                const uint64_t bd = desc64(st + S * A_TILE + kPb(qq) * B_TILE + kk * 32, hi64);
+                const bool small = qq > 0;
+                const bool first = (ks == ks0) && kk == 0 && qq <= 1;
+                mma_bf16(dT + (small ? 64u : 0u), ad, bd, id1, first ? 0u : 1u);
+              }
+            mma_commit(bars.empty(stage));
+            if (++stage == C::kStages) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+          if (!ok) break;
+          mma_commit(bars.cfull(buf));
+          ++g;
+        }
+      mma_commit(bars.done());
+      DrainWatch dw(A.status, A.timeout_ns);
+      mbar_wait(bars.done(), 0, dw.wd, kSiteRFull);
+    }
+  } else {
+    const int quad = warp & 3;
+    const int half = (warp - 2) >> 2;  // y in [4*half, 4*half+4)
+    const int L = quad * 32 + lane;    // TMEM lane = (x, b)
+    const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
+    const int x_l = L >> 3, b_l = L & 7;
+    uint32_t g = 0;
+    bool ok = true;
+    for (int q = q0; ok && q < q1; ++q) {
+      float X[32];  // Gamma2 row of lane (x, b): columns (y, d) for y in this half
+      for (int c = 0; c < nch; ++c) {
+        const int buf = (int)(g & 1u);
+        if (!(ok = mbar_wait(bars.cfull(buf), (g >> 1) & 1u, wd, kSiteXYFull))) break;
+        ++g;
+        tc_fence_after();
+        const uint32_t cX = tl + (uint32_t)buf * 128u + 32u * half;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float tb[16], ts[16];
+          tmem_ld16(cX + h * 16, tb);
+          tmem_ld16(cX + 64u + h * 16, ts);
+          tmem_ld_wait();
+#pragma unroll
+          for (int i = 0; i < 16; ++i) X[h * 16 + i] = c ? X[h * 16 + i] + (tb[i] + ts[i]) : tb[i] + ts[i];
+        }
+        tc_fence_before();
+        mbar_arrive(bars.cfree(buf));
+      }
+      if (!ok) break;
+      // row (x, y) of plane (tile, q, s), slots (b_l, 0..7): whole 128-byte rows per warp
+      __nv_bfloat16 *gp = A.Gst + (size_t)(tile * nq + q) * S * (128 * SLOTS);
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int row = x_l * 8 + 4 * half + y;
+        float rem[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) rem[d] = X[y * 8 + d];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          const uint4 w = pack_slice(rem);
+          __stcs(reinterpret_cast<uint4 *>(gp + (size_t)s * (128 * SLOTS) + row * SLOTS + b_l * CB), w);
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 256);
+  }
+}
+
 // dB[P][x][y] = 2 x the double-single sum of work unit (tile, chunk); lane = (x, y).
 __global__ void __launch_bounds__(128) grad_unpack_kernel(const __grid_constant__ GradTcArgs A) {
   const int item = blockIdx.x;
@@ -405,8 +597,24 @@ __global__ void __launch_bounds__(128) grad_unpack_kernel(const __grid_constant_
 
 cudaError_t grad_tc_init_attributes(int nslices) {
   const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  if (nslices == 2) return cudaFuncSetAttribute(grad_B_tc_kernel<2>, at, (int)Cfg<2>::kSmem);
-  return cudaFuncSetAttribute(grad_B_tc_kernel<3>, at, (int)Cfg<3>::kSmem);
+  cudaError_t e;
+  if (nslices == 2) {
+    e = cudaFuncSetAttribute(grad_B_tc_kernel<2>, at, (int)Cfg<2>::kSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(grad_gamma_store_kernel<2>, at, (int)CfgG<2>::kSmem);
+  } else {
+    e = cudaFuncSetAttribute(grad_B_tc_kernel<3>, at, (int)Cfg<3>::kSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(grad_gamma_store_kernel<3>, at, (int)CfgG<3>::kSmem);
+  }
+  return e;
+}
+
+cudaError_t launch_grad_gamma_store(const GradTcArgs &a, int nslices, cudaStream_t s) {
+  const int items = a.ntiles * a.qsplit;
+  if (nslices == 2)
+    grad_gamma_store_kernel<2><<<items, kThreads, CfgG<2>::kSmem, s>>>(a);
+  else
+    grad_gamma_store_kernel<3><<<items, kThreads, CfgG<3>::kSmem, s>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_grad_B_tc(const GradTcArgs &a, int nslices, cudaStream_t s) {

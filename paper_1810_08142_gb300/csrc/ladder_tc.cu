@@ -156,9 +156,14 @@ __device__ __forceinline__ Item decode_item(const TcArgs &A, int item) {
   const int tc = item / A.ksplit;
   const int tile = tc / A.nchunks, ch = tc % A.nchunks;
   int iA = 0, t = tile;
-  while (t >= A.nB8 - 2 * iA) {
-    t -= A.nB8 - 2 * iA;
-    ++iA;
+  if (A.square) {
+    iA = tile / A.nB8;
+    t = tile % A.nB8 - 2 * iA;
+  } else {
+    while (t >= A.nB8 - 2 * iA) {
+      t -= A.nB8 - 2 * iA;
+      ++iA;
+    }
   }
   I.tile = tile;
   I.iA = iA;
@@ -800,7 +805,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_
         const uint32_t tbytes = I.sc * 32u;
         const int sg = CH.nps > 0 ? 0 : 1;  // the chunk's sign
         for (int p = I.p0; ok && p < I.p1; ++p) {
-          const int z = ((I.tile * A.nbp + p) * 2 + sg) * S;
+          const int z = ((I.tile * A.nbp + p) * A.nsign + sg) * S;
           for (int piece = 0; piece < kPieces; piece += kPPS) {
             if (!(ok = mbar_wait(bars.empty(stage), phase ^ 1u, wd, kSiteTmaEmpty))) break;
             const uint32_t dst = ring + (uint32_t)stage * C::kStage;
@@ -991,7 +996,32 @@ __global__ void __launch_bounds__(128) unpack2_kernel(const __grid_constant__ Tc
   }
 }
 
+// ---------------------------------------------------------------- unpack (two-pass dB)
+// dB[P][x][y] = 2 x the block-range sums of the GEMM2 kernel's accumulators
+// for tile (x 16-block, y 8-block) and aux chunk; lane = (x, y).
+__global__ void __launch_bounds__(128) grad_unpack2_kernel(const __grid_constant__ TcLaunch Lp, double *dB,
+                                                           int N) {
+  const TcArgs &A = Lp.one;
+  const int tc = blockIdx.x, tile = tc / A.nchunks, ch = tc % A.nchunks;
+  const int L = threadIdx.x;
+  const int x = (tile / A.nB8) * 16 + (L >> 3), y = (tile % A.nB8) * CB + (L & 7);
+  if (x >= A.v || y >= A.v) return;
+  const TcChunk CH = A.chunks[ch];
+  const size_t per_item = (size_t)128 * A.racc_cols;
+  const float2 *base = A.racc + (size_t)tc * A.ksplit * per_item + L;
+  for (int c = 0; c < CH.np && CH.lp0 + c < N; ++c) {
+    float2 acc = base[(size_t)c * 128];
+    for (int k = 1; k < A.ksplit; ++k) acc = ds_add2(acc, base[k * per_item + (size_t)c * 128]);
+    dB[((size_t)(CH.lp0 + c) * A.v + x) * A.v + y] = 2.0 * ds_value(acc);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_grad_unpack2(const TcLaunch &a, double *dB, int N, int nblocks, cudaStream_t s) {
+  grad_unpack2_kernel<<<nblocks, 128, 0, s>>>(a, dB, N);
+  return cudaGetLastError();
+}
 
 uint32_t tc_smem_bytes(int nslices) {
   return nslices == 2 ? Cfg<2, false>::kSmem : Cfg<3, false>::kSmem;

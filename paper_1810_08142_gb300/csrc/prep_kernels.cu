@@ -148,6 +148,55 @@ void launch_pack_t2(const T2Args &a, cudaStream_t s) {
   pack_t2_kernel<<<grid, 256, 0, s>>>(a);
 }
 
+// ---------------------------------------------------------------- B per aux chunk (two-pass dB)
+// Second operand of the GEMM2 kernel in the two-pass dB: for aux chunk c,
+// (b, d) block q = (Bb, Dd) and 16-slot piece, the chunk's rows P (padding
+// rows zero) of 32 bytes, slot (b_l, d_l) = 8 (2 piece + h) + d_l holding
+// slice s of B^P_{8 Bb + b_l, 8 Dd + d_l}, in the 32-byte-swizzled order of
+// shared memory (the two 16-byte halves of row r swapped when bit 2 of r is
+// set) so that one bulk copy per piece fills the operand.
+template <int S>
+__global__ void pack_b2_kernel(const __grid_constant__ BpackArgs a) {
+  const TcChunk CH = a.chunks[blockIdx.y];
+  const int nq = a.nb * a.nb, rows = CH.nps;
+  const size_t units = (size_t)nq * 4 * rows * 2;  // (q, piece, row, half)
+  uint4 *dst = reinterpret_cast<uint4 *>(a.T2 + CH.t2off / 2);
+  for (size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x; u < units;
+       u += (size_t)gridDim.x * blockDim.x) {
+    const int h = (int)(u & 1);
+    size_t t = u >> 1;
+    const int r = (int)(t % rows);
+    t /= rows;
+    const int piece = (int)(t % 4);
+    const int q = (int)(t / 4);
+    const int P = CH.lp0 + r;
+    const int b = (q / a.nb) * CB + 2 * piece + h, d0 = (q % a.nb) * CB;
+    __nv_bfloat16 sl[S][8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int d = d0 + e;
+      const double x = (r < CH.np && P < a.N && b < a.v && d < a.v) ? a.B[((size_t)P * a.v + b) * a.v + d] : 0.0;
+      __nv_bfloat16 xs[S];
+      split_bf16<S>(x, xs);
+#pragma unroll
+      for (int s = 0; s < S; ++s) sl[s][e] = xs[s];
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const size_t row = ((size_t)(q * 4 + piece) * S + s) * rows + r;
+      dst[row * 2 + (h ^ ((r >> 2) & 1))] = *reinterpret_cast<const uint4 *>(sl[s]);
+    }
+  }
+}
+
+void launch_pack_b2(const BpackArgs &a, cudaStream_t s) {
+  dim3 grid(1024, a.nchunks);
+  if (a.S == 2)
+    pack_b2_kernel<2><<<grid, 256, 0, s>>>(a);
+  else
+    pack_b2_kernel<3><<<grid, 256, 0, s>>>(a);
+}
+
 // ---------------------------------------------------------------- B slices
 // Bt[q][a][c][P] = slice q of B[P][a][c]; a, c < vp (zero beyond v),
 // P < Np (zero beyond N).  32x32 tiles through shared memory so both the
