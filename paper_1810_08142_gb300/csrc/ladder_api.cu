@@ -412,10 +412,11 @@ static ladder_status init_plan(ladder_plan_s *pl, int o, int v, int naux, int mo
     // FP32 accumulation chains (see ladder_tc.cu).  GEMM1: with separate
     // hi*hi / small-product accumulators a chain of kc K-steps puts 2*kc MMAs
     // on the large accumulator (32 for BF16X3, 8 for BF16X6).  GEMM2: a fresh
-    // S every block pair (12 MMAs, BF16X3) or every piece (6 MMAs, BF16X6).
+    // S every block pair (12 MMAs, BF16X3) or every two pieces (12 MMAs,
+    // BF16X6; the autotuner's choice on every shape it was run on).
     pl->xy_split = 1;
     pl->kc = pl->S == 2 ? 16 : 4;
-    pl->s_pieces = pl->S == 2 ? 4 : 1;
+    pl->s_pieces = pl->S == 2 ? 4 : 2;
     if (const char *e = getenv("LADDER_XYSPLIT")) pl->xy_split = atoi(e) != 0;
     if (!pl->xy_split) pl->kc = pl->S == 2 ? 4 : 1;
     pl->flush_every = 16;
