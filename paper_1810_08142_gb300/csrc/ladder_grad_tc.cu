@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(kThreads, 1) grad_gamma_store_kernel(const __g
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
-    tmem_alloc(smem_u32(tmem_holder), 256);
+    tmem_alloc(smem_u32(tmem_holder), 512);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -488,7 +488,6 @@ __global__ void __launch_bounds__(kThreads, 1) grad_gamma_store_kernel(const __g
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0, g = 0;
-      const uint32_t id1 = idesc_bf16(128, 64);
       const uint32_t hi64 = desc_hi(512, kSwizzle64);
       bool ok = true;
       for (int q = q0; ok && q < q1; ++q)
@@ -500,16 +499,20 @@ __global__ void __launch_bounds__(kThreads, 1) grad_gamma_store_kernel(const __g
           for (int ks = ks0; ok && ks < ks1; ++ks) {
             if (!(ok = mbar_wait(bars.full(stage), phase, wd, kSiteTmaFull))) break;
             const uint32_t st = ring + (uint32_t)stage * C::kStage;
-            const uint32_t dT = tmem + (uint32_t)buf * 128u;
+            // merged slice products (as in the forward storing pass): slice
+            // pa of W times tau slices 0..S-1-pa, back to back in shared
+            // memory, is one MMA of N = 64 (S - pa) at column 64 pa, so the
+            // products of slice order pa + qb land in 64-column block pa + qb
+            // (block 0 = hi*hi, the large accumulator); buffers at 0 and 256
+            const uint32_t dT = tmem + (uint32_t)buf * 256u;
 #pragma unroll
             for (int kk = 0; kk < KSTEP / 16; ++kk)
 #pragma unroll
-              for (int qq = 0; qq < C::kProducts; ++qq) {
-                const uint64_t ad = desc64(st + kPa(qq) * A_TILE + kk * 32, hi64);
-                const uint64_t bd = desc64(st + S * A_TILE + kPb(qq) * B_TILE + kk * 32, hi64);
-                const bool small = qq > 0;
-                const bool first = (ks == ks0) && kk == 0 && qq <= 1;
-                mma_bf16(dT + (small ? 64u : 0u), ad, bd, id1, first ? 0u : 1u);
+              for (int pa = 0; pa < S; ++pa) {
+                const uint64_t ad = desc64(st + pa * A_TILE + kk * 32, hi64);
+                const uint64_t bd = desc64(st + S * A_TILE + kk * 32, hi64);
+                const bool first = (ks == ks0) && kk == 0 && pa == 0;
+                mma_bf16(dT + 64u * pa, ad, bd, idesc_bf16(128, 64 * (S - pa)), first ? 0u : 1u);
               }
             mma_commit(bars.empty(stage));
             if (++stage == C::kStages) {
@@ -540,15 +543,19 @@ __global__ void __launch_bounds__(kThreads, 1) grad_gamma_store_kernel(const __g
         if (!(ok = mbar_wait(bars.cfull(buf), (g >> 1) & 1u, wd, kSiteXYFull))) break;
         ++g;
         tc_fence_after();
-        const uint32_t cX = tl + (uint32_t)buf * 128u + 32u * half;
+        const uint32_t cX = tl + (uint32_t)buf * 256u + 32u * half;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          float tb[16], ts[16];
-          tmem_ld16(cX + h * 16, tb);
-          tmem_ld16(cX + 64u + h * 16, ts);
+          float b0[16], b1[16], b2[16];
+          tmem_ld16(cX + h * 16, b0);
+          tmem_ld16(cX + 64u + h * 16, b1);
+          if (S == 3) tmem_ld16(cX + 128u + h * 16, b2);
           tmem_ld_wait();
 #pragma unroll
-          for (int i = 0; i < 16; ++i) X[h * 16 + i] = c ? X[h * 16 + i] + (tb[i] + ts[i]) : tb[i] + ts[i];
+          for (int i = 0; i < 16; ++i) {
+            const float t = b0[i] + (S == 3 ? b1[i] + b2[i] : b1[i]);
+            X[h * 16 + i] = c ? X[h * 16 + i] + t : t;
+          }
         }
         tc_fence_before();
         mbar_arrive(bars.cfree(buf));
@@ -575,7 +582,7 @@ __global__ void __launch_bounds__(kThreads, 1) grad_gamma_store_kernel(const __g
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, 256);
+    tmem_dealloc(tmem, 512);
   }
 }
 
