@@ -11,6 +11,9 @@ Functions and the passages they follow (arxiv 1810.08142):
   ladder_pairs     selected (a,b) columns of the same sum
   energy           E_L = sum R_ij^ab (2 t_ij^ab - t_ij^ba)  (the closed-shell
                    energy weighting of Sec. II.A applied to the ladder term)
+  ladder_dressed   Eq. pp-Ladder-0 with the t1-dressed integrals of Eq. pp-Ladder-2
+                   and Eq. pp-Ladder-21 (v^{kb}_{cd} from the same RI factors)
+  ladder_dressed_pairs  selected (a,b) columns of the same
   grad_tau, grad_B and their *_entries variants: derivatives of
                    sum W_ij^ab R_ij^ab, written out term by term.
 Every function is pinned by tests/test_oracle_pins.py.
@@ -61,6 +64,11 @@ def _load():
                                                                      _I, _I, _I, _I, _D]
         lib.oracle_grad_B_entries.argtypes = [ctypes.c_int] * 3 + [_D, _D, _D, ctypes.c_int,
                                                                    _I, _I, _I, _D]
+        lib.oracle_ladder_dressed.argtypes = [ctypes.c_int] * 3 + [_D] * 5
+        lib.oracle_ladder_dressed.restype = ctypes.c_int
+        lib.oracle_ladder_dressed_pairs.argtypes = [ctypes.c_int] * 3 + [_D] * 4 + [
+            ctypes.c_int, _I, _I, _D]
+        lib.oracle_ladder_dressed_pairs.restype = ctypes.c_int
         lib.oracle_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -191,4 +199,40 @@ def grad_B_entries(B, tau_, W, P, x, y):
     out = np.empty(len(arrs[0][0]))
     _load().oracle_grad_B_entries(o, v, n, pB, pt, pW, len(out), *[p for _, p in arrs],
                                   out.ctypes.data_as(_D))
+    return out
+
+
+def _shape_dressed(B, B_ov, t1, tau_):
+    n, v = _shape_B(B)
+    o = tau_.shape[0]
+    assert tau_.shape == (o, o, v, v) and B_ov.shape == (n, o, v) and t1.shape == (o, v)
+    return o, v, n
+
+
+def ladder_dressed(B, B_ov, t1, tau_):
+    """R_ij^ab = sum_cd b^{ab}_{cd} tau_ij^cd with the dressed b of Eq. pp-Ladder-2."""
+    o, v, n = _shape_dressed(B, B_ov, t1, tau_)
+    B, pB = _d(B)
+    B_ov, pO = _d(B_ov)
+    t1, p1 = _d(t1)
+    tau_, pt = _d(tau_)
+    R = np.empty((o, o, v, v))
+    if _load().oracle_ladder_dressed(o, v, n, pB, pO, p1, pt, R.ctypes.data_as(_D)) != 0:
+        raise MemoryError("oracle_ladder_dressed")
+    return R
+
+
+def ladder_dressed_pairs(B, B_ov, t1, tau_, pa, pb):
+    """Dressed R[:, :, pa[k], pb[k]] for each k, shape [len(pa)][o][o]."""
+    o, v, n = _shape_dressed(B, B_ov, t1, tau_)
+    B, pB = _d(B)
+    B_ov, pO = _d(B_ov)
+    t1, p1 = _d(t1)
+    tau_, pt = _d(tau_)
+    pa, ppa = _i(pa)
+    pb, ppb = _i(pb)
+    out = np.empty((len(pa), o, o))
+    if _load().oracle_ladder_dressed_pairs(o, v, n, pB, pO, p1, pt, len(pa), ppa, ppb,
+                                           out.ctypes.data_as(_D)) != 0:
+        raise MemoryError("oracle_ladder_dressed_pairs")
     return out

@@ -294,6 +294,143 @@ void oracle_grad_B_entries(int o, int v, int n, const double *B, const double *t
     }
 }
 
+/* ---------------------------------------------------------------------------
+ * t1-dressed ladder (Eq. pp-Ladder-0 with the dressed integrals of
+ * Eq. pp-Ladder-2 and the intermediate of Eq. pp-Ladder-21):
+ *
+ *   mbar^P_bd      = sum_k m^P_kd t_k^b                                (Eq. pp-Ladder-21)
+ *   b^{ab}_{cd}    = sum_P m^P_ac (m^P_bd - mbar^P_bd) - sum_k t_k^a v^{kb}_{cd}   (Eq. pp-Ladder-2)
+ *   R_ij^ab        = sum_cd b^{ab}_{cd} tau_ij^cd                      (Eq. pp-Ladder-0)
+ *
+ * with m^P_pq the RI factor of the orbital pair (p,q): the virtual block
+ * B[P][a][c] and the occupied-virtual block Bov[P][k][c].  The integrals with
+ * one occupied index, v^{kb}_{cd} = (kc|bd), come from the same factors
+ * (Eq. RIM with Eq. eri): the paper keeps them pre-stored, built from the one
+ * RI tensor before the iterations.
+ *
+ * Extra arrays: Bov [n][o][v], t1 [o][v].
+ * ------------------------------------------------------------------------- */
+#define IDX3O(P, k, c, o, v) (((size_t)(P) * (o) + (k)) * (v) + (c))
+
+/* Eq. pp-Ladder-21: mbar[P][b][d] = sum_k Bov[P][k][d] t1[k][b]. */
+static void dressed_mbar(int o, int v, int n, const double *Bov, const double *t1, double *mbar)
+{
+    #pragma omp parallel for schedule(static)
+    for (int P = 0; P < n; ++P)
+        for (int b = 0; b < v; ++b)
+            for (int d = 0; d < v; ++d) {
+                double s = 0.0;
+                for (int k = 0; k < o; ++k)
+                    s += Bov[IDX3O(P, k, d, o, v)] * t1[(size_t)k * v + b];
+                mbar[IDX3(P, b, d, v)] = s;
+            }
+}
+
+/* One (a,b) column of b^{ab}_{cd} (Eq. pp-Ladder-2) into V[c][d].  With
+ * ovvv != NULL the pre-stored v^{kb}_{cd} = ovvv[k][c][b][d] is used,
+ * otherwise it is formed from the factors for this b. */
+static void dressed_integrals_ab(int o, int v, int n, const double *B, const double *Bov,
+                                 const double *t1, const double *mbar, const double *ovvv,
+                                 int a, int b, double *V)
+{
+    memset(V, 0, sizeof(double) * (size_t)v * v);
+    for (int P = 0; P < n; ++P)
+        for (int c = 0; c < v; ++c) {
+            const double mac = B[IDX3(P, a, c, v)];
+            for (int d = 0; d < v; ++d)
+                V[(size_t)c * v + d] += mac * (B[IDX3(P, b, d, v)] - mbar[IDX3(P, b, d, v)]);
+        }
+    for (int k = 0; k < o; ++k) {
+        const double tka = t1[(size_t)k * v + a];
+        for (int c = 0; c < v; ++c)
+            for (int d = 0; d < v; ++d) {
+                double vkb;
+                if (ovvv) {
+                    vkb = ovvv[(((size_t)k * v + c) * v + b) * v + d];
+                } else {
+                    vkb = 0.0;
+                    for (int P = 0; P < n; ++P)
+                        vkb += Bov[IDX3O(P, k, c, o, v)] * B[IDX3(P, b, d, v)];
+                }
+                V[(size_t)c * v + d] -= tka * vkb;
+            }
+    }
+}
+
+/* The dressed term for every i, j, a, b.  Returns -1 if the pre-stored
+ * integrals (o v^3 doubles) cannot be allocated. */
+int oracle_ladder_dressed(int o, int v, int n, const double *B, const double *Bov,
+                          const double *t1, const double *tau, double *R)
+{
+    double *mbar = (double *)malloc(sizeof(double) * (size_t)n * v * v);
+    double *ovvv = (double *)malloc(sizeof(double) * (size_t)o * v * v * v);
+    if (!mbar || !ovvv) { free(mbar); free(ovvv); return -1; }
+    dressed_mbar(o, v, n, Bov, t1, mbar);
+    /* v^{kb}_{cd} = (kc|bd) = sum_P m^P_kc m^P_bd, stored as ovvv[k][c][b][d] */
+    #pragma omp parallel for schedule(dynamic)
+    for (int kc = 0; kc < o * v; ++kc) {
+        const int k = kc / v, c = kc % v;
+        for (int b = 0; b < v; ++b)
+            for (int d = 0; d < v; ++d) {
+                double s = 0.0;
+                for (int P = 0; P < n; ++P)
+                    s += Bov[IDX3O(P, k, c, o, v)] * B[IDX3(P, b, d, v)];
+                ovvv[(((size_t)k * v + c) * v + b) * v + d] = s;
+            }
+    }
+    #pragma omp parallel
+    {
+        double *V = (double *)malloc(sizeof(double) * (size_t)v * v);
+        #pragma omp for schedule(dynamic)
+        for (int ab = 0; ab < v * v; ++ab) {
+            const int a = ab / v, b = ab % v;
+            dressed_integrals_ab(o, v, n, B, Bov, t1, mbar, ovvv, a, b, V);
+            for (int i = 0; i < o; ++i)
+                for (int j = 0; j < o; ++j) {
+                    double s = 0.0;
+                    for (int c = 0; c < v; ++c)
+                        for (int d = 0; d < v; ++d)
+                            s += V[(size_t)c * v + d] * tau[IDX4(i, j, c, d, o, v)];
+                    R[IDX4(i, j, a, b, o, v)] = s;
+                }
+        }
+        free(V);
+    }
+    free(ovvv);
+    free(mbar);
+    return 0;
+}
+
+/* Selected (a,b) columns of the dressed term: Rsel[k][i][j] = R_ij^{a_k b_k},
+ * forming v^{kb}_{cd} for each selected b instead of storing all of them. */
+int oracle_ladder_dressed_pairs(int o, int v, int n, const double *B, const double *Bov,
+                                const double *t1, const double *tau, int npairs,
+                                const int *pa, const int *pb, double *Rsel)
+{
+    double *mbar = (double *)malloc(sizeof(double) * (size_t)n * v * v);
+    if (!mbar) return -1;
+    dressed_mbar(o, v, n, Bov, t1, mbar);
+    #pragma omp parallel
+    {
+        double *V = (double *)malloc(sizeof(double) * (size_t)v * v);
+        #pragma omp for schedule(dynamic)
+        for (int q = 0; q < npairs; ++q) {
+            dressed_integrals_ab(o, v, n, B, Bov, t1, mbar, NULL, pa[q], pb[q], V);
+            for (int i = 0; i < o; ++i)
+                for (int j = 0; j < o; ++j) {
+                    double s = 0.0;
+                    for (int c = 0; c < v; ++c)
+                        for (int d = 0; d < v; ++d)
+                            s += V[(size_t)c * v + d] * tau[IDX4(i, j, c, d, o, v)];
+                    Rsel[((size_t)q * o + i) * o + j] = s;
+                }
+        }
+        free(V);
+    }
+    free(mbar);
+    return 0;
+}
+
 int oracle_threads(void)
 {
 #ifdef _OPENMP
