@@ -286,6 +286,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dressed", action="store_true",
+                    help="also time the t1-dressed term (Eq. pp-Ladder-2) on the same workload")
     ap.add_argument("--form", default="auto", choices=["auto", "fused", "two-pass"],
                     help="split-BF16 form: the plan's (or tuner's) choice, the one-kernel fused form "
                          "(integral tiles stay on chip), or the two-pass form (V+- stored in HBM)")
@@ -415,18 +417,30 @@ def main():
         others.append("fp64")
     if two_pass and not args.no_fp64:
         others.insert(0, args.mode + "_fused")  # the same mode in the one-kernel form
+    if args.dressed and args.mode != "fp64":
+        others.insert(0, args.mode + "_dressed")  # the t1-dressed term (Eq. pp-Ladder-2)
+    B_ov = None
     for m in others:
-        if m.endswith("_fused"):
+        if m.endswith("_dressed"):
+            Lm = lad.Ladder(w.o, w.v, w.naux, mode=m[:-8], device=dev, tuning=tun, dressed=True)
+            B_ov = torch.from_numpy(x.B_ov).to(dev)
+        elif m.endswith("_fused"):
             Lm = lad.Ladder(w.o, w.v, w.naux, mode=m[:-6], device=dev, tuning={**tun, "two_pass": 0, "ksplit": 0})
         else:
             Lm = lad.Ladder(w.o, w.v, w.naux, mode=m, device=dev)
         lad.ladder_set_timing(Lm.plan, True)
+        run = step
+        if m.endswith("_dressed"):
+            def run(Lx):
+                lad.ladder_tau(Lx.plan, t1, t2, tau)
+                lad.ladder_apply_dressed(Lx.plan, B, B_ov, t1, tau, R)
+                lad.ladder_energy(Lx.plan, R, t2, E)
         if m != "fp64":
-            step(Lm)
+            run(Lm)
         torch.cuda.synchronize()
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(stream)
-        step(Lm)
+        run(Lm)
         a1.record(stream)
         torch.cuda.synchronize()
         Lm.check_device()
@@ -434,8 +448,11 @@ def main():
         tm = lad.ladder_timing(Lm.plan)
         ent = {"ms_per_step": mms, "tflops": F / (mms * 1e-3) / 1e12, "fused_ms": tm[1],
                "E_L": float(E.item()), "steps": 1}
-        if parity is not None:
+        if parity is not None and not m.endswith("_dressed"):
             ent["dE_L"] = abs(float(E.item()) - parity["E_L"])
+        if m.endswith("_dressed"):
+            # tau, B - mbar, the rank-o correction and the energy
+            ent["outside_ladder_ms"] = mms - tm[0] - tm[1] - tm[2]
         extra[m] = ent
         Lm.close()
         del Lm

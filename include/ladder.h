@@ -64,6 +64,9 @@ typedef enum {
 /* OR this into `mode` to size the workspace for ladder_backward as well
  * (the FP64 gradient with respect to B spills tiles of Gamma^{xb}_{yd}). */
 #define LADDER_WITH_BACKWARD 16
+/* OR this into `mode` to size the workspace for ladder_apply_dressed as well
+ * (B - mbar in FP64, the integrals (kc|ld) and two small intermediates). */
+#define LADDER_WITH_DRESSING 32
 
 /* Create a plan for one shape.  1 <= o <= 256, 1 <= v <= 4096, 1 <= naux <= 65536.
  * The plan owns no device memory; see ladder_workspace_size. */
@@ -114,6 +117,25 @@ ladder_status ladder_tau(ladder_plan_t plan, const double *t1, const double *t2,
  * tile by tile on chip and never written to memory. */
 ladder_status ladder_apply(ladder_plan_t plan, const double *B, const double *tau,
                            double *R, void *stream);
+
+/* The t1-dressed term, Eq. pp-Ladder-0 with the integrals of Eq. pp-Ladder-2:
+ *   R_ij^ab = sum_cd b^{ab}_{cd} tau_ij^cd,
+ *   b^{ab}_{cd} = sum_P B^P_ac (B^P_bd - mbar^P_bd) - sum_k t_k^a (kc|bd),
+ *   mbar^P_bd = sum_k Bov^P_kd t_k^b   (Eq. pp-Ladder-21),
+ * with (kc|bd) = sum_P Bov^P_kc B^P_bd from the same factors.
+ *   B    [naux][v][v]  RI factor of the virtual block (as for ladder_apply)
+ *   Bov  [naux][o][v]  RI factor of the occupied-virtual block, Bov[P][k][c]
+ *   t1   [o][v]        singles t_k^a
+ *   tau  [o][o][v][v]  as for ladder_apply (from ladder_tau)
+ *   R    [o][o][v][v]  overwritten; may not alias an input
+ * FP64, C-contiguous device arrays.  The plan must have been created with
+ * LADDER_WITH_DRESSING (else LADDER_EINVAL) and is not a batch plan.  The
+ * term runs as the undressed ladder of B - mbar (in the plan's mode) minus the
+ * correction sum_kl t_k^a t_l^b sum_cd (kc|ld) tau_ij^cd, which costs
+ * O(o^2 v^2 N + o^4 v^2) and is formed in FP64 (LADDER_FP64) or FP32. */
+ladder_status ladder_apply_dressed(ladder_plan_t plan, const double *B, const double *Bov,
+                                   const double *t1, const double *tau, double *R,
+                                   void *stream);
 
 /* E_L = sum_ijab R_ij^ab (2 t_ij^ab - t_ij^ba), reduced in FP64 in a fixed
  * order (bitwise reproducible); writes one double at E_dev (device memory). */

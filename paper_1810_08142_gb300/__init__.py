@@ -20,13 +20,14 @@ LIB_PATH = os.path.join(HERE, "libladder.so")
 
 LADDER_FP64, LADDER_BF16X3, LADDER_BF16X6, LADDER_AUTO = 0, 1, 2, 3
 LADDER_WITH_BACKWARD = 16
+LADDER_WITH_DRESSING = 32
 MODES = {"fp64": LADDER_FP64, "bf16x3": LADDER_BF16X3, "bf16x6": LADDER_BF16X6, "auto": LADDER_AUTO}
 STATUS = {0: "LADDER_OK", 1: "LADDER_EINVAL", 2: "LADDER_ENOMEM", 3: "LADDER_ECUDA",
           4: "LADDER_ETIMEOUT", 5: "LADDER_ENOTSUP", 6: "LADDER_EWORKSPACE"}
 
 # every entry point that include/ladder.h declares
 EXPORTS = ("ladder_plan", "ladder_plan_mode", "ladder_get_tuning", "ladder_set_tuning", "ladder_workspace_size", "ladder_set_workspace",
-           "ladder_tau", "ladder_apply", "ladder_energy", "ladder_energy_noalloc", "ladder_backward", "ladder_pair_combine", "ladder_apply_host",
+           "ladder_tau", "ladder_apply", "ladder_apply_dressed", "ladder_energy", "ladder_energy_noalloc", "ladder_backward", "ladder_pair_combine", "ladder_apply_host",
            "ladder_plan_batched", "ladder_apply_batched", "ladder_last_device_error", "ladder_selftest_wait",
            "ladder_set_timing", "ladder_timing", "ladder_timing_passes", "ladder_flops", "ladder_status_string",
            "ladder_destroy")
@@ -70,6 +71,7 @@ def load_library(path: str = LIB_PATH):
         "ladder_set_workspace": [_P, _P, sz],
         "ladder_tau": [_P, _P, _P, _P, _P],
         "ladder_apply": [_P, _P, _P, _P, _P],
+        "ladder_apply_dressed": [_P, _P, _P, _P, _P, _P, _P],
         "ladder_energy": [_P, _P, _P, _P, _P],
         "ladder_energy_noalloc": [i, i, _P, _P, _P, _P],
         "ladder_backward": [_P, _P, _P, _P, _P, _P, _P],
@@ -155,6 +157,12 @@ def ladder_tau(plan, t1, t2, tau, stream=None) -> None:
 
 def ladder_apply(plan, B, tau, R, stream=None) -> None:
     _check("ladder_apply", load_library().ladder_apply(plan, _ptr(B), _ptr(tau), _ptr(R), _stream(stream)))
+
+
+def ladder_apply_dressed(plan, B, B_ov, t1, tau, R, stream=None) -> None:
+    _check("ladder_apply_dressed",
+           load_library().ladder_apply_dressed(plan, _ptr(B), _ptr(B_ov), _ptr(t1), _ptr(tau), _ptr(R),
+                                               _stream(stream)))
 
 
 def ladder_energy(plan, R, t2, E, stream=None) -> None:
@@ -248,10 +256,11 @@ class Ladder:
     """A plan plus its workspace (a torch uint8 tensor on the current device)."""
 
     def __init__(self, o: int, v: int, naux: int, mode="bf16x6", device=None, backward=False,
-                 tuning=None):
+                 tuning=None, dressed=False):
         """mode: "fp64", "bf16x3", "bf16x6", or "tuned" (the autotuner's cached
         choice of mode and launch parameters for this shape, see tune.py);
-        tuning: a dict of ladder_tuning fields to override."""
+        tuning: a dict of ladder_tuning fields to override; dressed: size the
+        workspace for apply_dressed (the t1-dressed term) as well."""
         import torch
         self.o, self.v, self.naux = o, v, naux
         if mode == "tuned":
@@ -260,6 +269,8 @@ class Ladder:
         m = MODES[mode] if isinstance(mode, str) else int(mode)
         if backward:
             m |= LADDER_WITH_BACKWARD
+        if dressed:
+            m |= LADDER_WITH_DRESSING
         self.device = torch.device(device if device is not None else "cuda")
         with torch.cuda.device(self.device):
             self.plan = ladder_plan(o, v, naux, m)
@@ -289,6 +300,13 @@ class Ladder:
         import torch
         out = torch.empty_like(tau) if out is None else out
         ladder_apply(self.plan, B, tau, out)
+        return out
+
+    def apply_dressed(self, B, B_ov, t1, tau, out=None):
+        """The t1-dressed term (Eq. pp-Ladder-2); the Ladder needs dressed=True."""
+        import torch
+        out = torch.empty_like(tau) if out is None else out
+        ladder_apply_dressed(self.plan, B, B_ov, t1, tau, out)
         return out
 
     def energy(self, R, t2, out=None):

@@ -1,0 +1,275 @@
+// t1-dressed ladder (Eq. pp-Ladder-2 with Eq. pp-Ladder-21).
+//
+// The dressed integrals are
+//   b^{ab}_{cd} = sum_P m^P_ac (m^P_bd - mbar^P_bd) - sum_k t_k^a v^{kb}_{cd},
+//   mbar^P_bd   = sum_k m^P_kd t_k^b,
+// with v^{kb}_{cd} = (kc|bd) = sum_P m^P_kc m^P_bd from the same RI factors.
+// Since sum_k t_k^a v^{kb}_{cd} = sum_P mbar^P_ac m^P_bd, completing the
+// square gives
+//   b^{ab}_{cd} = sum_P Bd^P_ac Bd^P_bd - sum_P mbar^P_ac mbar^P_bd,   Bd = B - mbar,
+// so the dressed term is the undressed ladder of Bd (the fused / two-pass
+// kernels unchanged, with Bd for B) minus a correction of rank o in each
+// virtual index:
+//   C_ij^ab = sum_kl t_k^a t_l^b X_ij^kl,
+//   X_ij^kl = sum_cd G[(k,l)][(c,d)] tau_ij^cd,   G[(k,l)][(c,d)] = (kc|ld) = sum_P m^P_kc m^P_ld.
+// G costs 2 (ov)^2 N flops (half of it with its symmetry), X 2 o^4 v^2: both
+// O(o^2 v^2 N + o^4 v^2), against the ladder's O(v^4 N + o^2 v^4).
+//
+// This file holds the three kernels of that correction:
+//   dress_B_kernel  Bd = B - mbar (FP64 result; mbar accumulated in T)
+//   gemm_kernel     a CUDA-core GEMM C(m,n) = sum_k A(m,k) B(n,k) with free
+//                   strides, split-K / batch in z, and three epilogues
+//   reduce_kernel   sums split-K partials
+// T is double for the FP64 path and float for the split-BF16 paths (the
+// correction is about 1e-4 of R there, so FP32 keeps it far inside their
+// tolerance).
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace ladder {
+namespace {
+
+// ---------------------------------------------------------------- Bd = B - mbar
+constexpr int kDB = 32;    // b rows per CTA
+constexpr int kDD = 128;   // d columns per CTA
+constexpr int kDK = 32;    // occupied indices per shared-memory chunk
+
+template <typename T>
+__global__ void __launch_bounds__(256) dress_B_kernel(int o, int v, const double *__restrict__ B,
+                                                      const double *__restrict__ Bov,
+                                                      const double *__restrict__ t1,
+                                                      double *__restrict__ Bd) {
+  __shared__ T sO[kDK][kDD];   // Bov[P][k][d-tile]
+  __shared__ T sT[kDK][kDB];   // t1[k][b-tile]
+  const int nd = (v + kDD - 1) / kDD;
+  const int P = blockIdx.x / nd;
+  const int b0 = blockIdx.y * kDB, d0 = (blockIdx.x % nd) * kDD;
+  const int tid = threadIdx.x;
+  const int dl = tid % kDD, bq = tid / kDD;  // each thread: one d, b rows bq, bq+2, ...
+  T acc[kDB / 2];
+#pragma unroll
+  for (int r = 0; r < kDB / 2; ++r) acc[r] = T(0);
+  const double *O = Bov + (size_t)P * o * v;
+  for (int k0 = 0; k0 < o; k0 += kDK) {
+    for (int e = tid; e < kDK * kDD; e += 256) {
+      const int k = k0 + e / kDD, d = d0 + e % kDD;
+      sO[e / kDD][e % kDD] = (k < o && d < v) ? (T)O[(size_t)k * v + d] : T(0);
+    }
+    for (int e = tid; e < kDK * kDB; e += 256) {
+      const int k = k0 + e / kDB, b = b0 + e % kDB;
+      sT[e / kDB][e % kDB] = (k < o && b < v) ? (T)t1[(size_t)k * v + b] : T(0);
+    }
+    __syncthreads();
+    const int kn = min(kDK, o - k0);
+    for (int k = 0; k < kn; ++k) {
+      const T x = sO[k][dl];
+#pragma unroll
+      for (int r = 0; r < kDB / 2; ++r) acc[r] += sT[k][bq + 2 * r] * x;
+    }
+    __syncthreads();
+  }
+  const int d = d0 + dl;
+  if (d < v) {
+#pragma unroll
+    for (int r = 0; r < kDB / 2; ++r) {
+      const int b = b0 + bq + 2 * r;
+      if (b < v) {
+        const size_t idx = ((size_t)P * v + b) * v + d;
+        Bd[idx] = B[idx] - (double)acc[r];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- CUDA-core GEMM
+constexpr int kBM = 128, kBN = 128, kBK = 8;
+constexpr int kPadF = 4;  // row padding of the shared tiles (elements)
+
+__device__ __forceinline__ void load4(const float *p, float *r) {
+  const float4 x = *reinterpret_cast<const float4 *>(p);
+  r[0] = x.x; r[1] = x.y; r[2] = x.z; r[3] = x.w;
+}
+__device__ __forceinline__ void load4(const double *p, double *r) {
+  const double2 x = *reinterpret_cast<const double2 *>(p);
+  const double2 y = *reinterpret_cast<const double2 *>(p + 2);
+  r[0] = x.x; r[1] = x.y; r[2] = y.x; r[3] = y.y;
+}
+
+// Operand loader: element (row, k) of a [rows x K] operand at
+// base[row * srow + k * sk].  Each thread stages four elements per K-step;
+// the mapping keeps whichever index is contiguous in memory on adjacent
+// threads.
+template <typename TM, typename T>
+__device__ __forceinline__ void gemm_fetch(const TM *__restrict__ base, long long srow,
+                                           long long sk, int rows, int row0, int k0, int kend,
+                                           bool kfast, T (&reg)[4]) {
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int e = threadIdx.x + 256 * r;
+    const int rr = kfast ? e / kBK : e % kBM;
+    const int kk = kfast ? e % kBK : e / kBM;
+    const int row = row0 + rr, k = k0 + kk;
+    reg[r] = (row < rows && k < kend) ? (T)base[(long long)row * srow + (long long)k * sk] : T(0);
+  }
+}
+template <typename T>
+__device__ __forceinline__ void gemm_stage(T (*tile)[kBM + kPadF], bool kfast, const T (&reg)[4]) {
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int e = threadIdx.x + 256 * r;
+    const int rr = kfast ? e / kBK : e % kBM;
+    const int kk = kfast ? e % kBK : e / kBM;
+    tile[kk][rr] = reg[r];
+  }
+}
+
+template <typename TA, typename TB, typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) gemm_kernel(const GemmArgs g) {
+  __shared__ __align__(16) T sA[2][kBK][kBM + kPadF];
+  __shared__ __align__(16) T sB[2][kBK][kBN + kPadF];
+  int mt, nt;
+  if (g.sym) {
+    // upper triangle of tiles only (mt <= nt); the epilogue mirrors
+    int t = blockIdx.x, r = 0, w = g.ntn;
+    while (t >= w) { t -= w; ++r; --w; }
+    mt = r;
+    nt = r + t;
+  } else {
+    mt = blockIdx.x / g.ntn;
+    nt = blockIdx.x % g.ntn;
+  }
+  const int z = blockIdx.z + g.zoff;
+  const int batch = z / g.ksplit, split = z % g.ksplit;
+  const int k0 = split * g.kchunk, k1 = min(g.K, k0 + g.kchunk);
+  const TA *A = static_cast<const TA *>(g.A) + (long long)batch * g.sa_batch;
+  const TB *Bm = static_cast<const TB *>(g.B) + (long long)batch * g.sb_batch;
+  const bool akf = g.sak == 1, bkf = g.sbk == 1;
+  const int m0 = mt * kBM, n0 = nt * kBN;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+
+  T acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
+
+  T ra[4], rb[4];
+  const int nkt = k1 > k0 ? (k1 - k0 + kBK - 1) / kBK : 0;
+  if (nkt > 0) {
+    gemm_fetch(A, g.sam, g.sak, g.M, m0, k0, k1, akf, ra);
+    gemm_fetch(Bm, g.sbn, g.sbk, g.N, n0, k0, k1, bkf, rb);
+    gemm_stage(sA[0], akf, ra);
+    gemm_stage(sB[0], bkf, rb);
+  }
+  __syncthreads();
+  for (int kt = 0; kt < nkt; ++kt) {
+    const int buf = kt & 1;
+    if (kt + 1 < nkt) {
+      gemm_fetch(A, g.sam, g.sak, g.M, m0, k0 + (kt + 1) * kBK, k1, akf, ra);
+      gemm_fetch(Bm, g.sbn, g.sbk, g.N, n0, k0 + (kt + 1) * kBK, k1, bkf, rb);
+    }
+#pragma unroll
+    for (int kk = 0; kk < kBK; ++kk) {
+      T a[8], b[8];
+      load4(&sA[buf][kk][ty * 4], a);
+      load4(&sA[buf][kk][64 + ty * 4], a + 4);
+      load4(&sB[buf][kk][tx * 4], b);
+      load4(&sB[buf][kk][64 + tx * 4], b + 4);
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] += a[i] * b[j];
+    }
+    if (kt + 1 < nkt) {
+      gemm_stage(sA[buf ^ 1], akf, ra);
+      gemm_stage(sB[buf ^ 1], bkf, rb);
+    }
+    __syncthreads();
+  }
+
+  // epilogue: thread rows ty*4+i (i<4) and 64+ty*4+i, columns likewise with tx
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+    if (m >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+      if (n >= g.N) continue;
+      const T val = acc[i][j];
+      if (g.epi == kEpiStore) {
+        static_cast<T *>(g.Out)[(long long)z * g.so_batch + (long long)m * g.ldo + n] = val;
+      } else if (g.epi == kEpiPerm) {
+        // m = (k, c), n = (l, d) -> G[(k, l)][(c, d)]; mirrored for the symmetric product
+        const int k = m / g.pv, c = m % g.pv, l = n / g.pv, d = n % g.pv;
+        T *G = static_cast<T *>(g.Out);
+        const long long vv = (long long)g.pv * g.pv;
+        G[((long long)k * g.po + l) * vv + (long long)c * g.pv + d] = val;
+        if (g.sym) G[((long long)l * g.po + k) * vv + (long long)d * g.pv + c] = val;
+      } else {  // kEpiSubR: R -= val (FP64 result)
+        double *R = static_cast<double *>(g.Out);
+        R[(long long)batch * g.so_batch + (long long)m * g.ldo + n] -= (double)val;
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void reduce_kernel(T *__restrict__ X, long long n, int parts) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    T s = X[e];
+    for (int p = 1; p < parts; ++p) s += X[(long long)p * n + e];
+    X[e] = s;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_dress_B(int o, int v, int N, const double *B, const double *Bov,
+                           const double *t1, double *Bd, bool fp32_mbar, cudaStream_t s) {
+  const dim3 grid((unsigned)(N * ((v + kDD - 1) / kDD)), (v + kDB - 1) / kDB);
+  if (fp32_mbar)
+    dress_B_kernel<float><<<grid, 256, 0, s>>>(o, v, B, Bov, t1, Bd);
+  else
+    dress_B_kernel<double><<<grid, 256, 0, s>>>(o, v, B, Bov, t1, Bd);
+  return cudaGetLastError();
+}
+
+template <typename TA, typename TB, typename T>
+cudaError_t launch_gemm(const GemmArgs &g, int batch, cudaStream_t s) {
+  GemmArgs a = g;
+  a.ntm = (a.M + kBM - 1) / kBM;
+  a.ntn = (a.N + kBN - 1) / kBN;
+  if (a.ksplit < 1) a.ksplit = 1;
+  if (a.kchunk < 1) a.kchunk = a.K;
+  if (a.sym && a.M != a.N) return cudaErrorInvalidValue;
+  const long long tiles = a.sym ? (long long)a.ntm * (a.ntm + 1) / 2 : (long long)a.ntm * a.ntn;
+  const long long nz = (long long)batch * a.ksplit;
+  if (tiles == 0 || nz == 0) return cudaSuccess;
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  // z = batch * ksplit + split, launched in slices of at most 65535
+  for (long long z0 = 0; z0 < nz; z0 += 65535) {
+    a.zoff = (int)z0;
+    const dim3 grid((unsigned)tiles, 1, (unsigned)std::min<long long>(65535, nz - z0));
+    gemm_kernel<TA, TB, T><<<grid, 256, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_gemm<double, double, double>(const GemmArgs &, int, cudaStream_t);
+template cudaError_t launch_gemm<double, double, float>(const GemmArgs &, int, cudaStream_t);
+template cudaError_t launch_gemm<double, float, float>(const GemmArgs &, int, cudaStream_t);
+template cudaError_t launch_gemm<float, double, float>(const GemmArgs &, int, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_reduce(T *X, long long n, int parts, cudaStream_t s) {
+  if (parts <= 1 || n == 0) return cudaSuccess;
+  const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+  reduce_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(X, n, parts);
+  return cudaGetLastError();
+}
+template cudaError_t launch_reduce<double>(double *, long long, int, cudaStream_t);
+template cudaError_t launch_reduce<float>(float *, long long, int, cudaStream_t);
+
+}  // namespace ladder

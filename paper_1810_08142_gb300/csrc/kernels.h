@@ -27,6 +27,30 @@ size_t energy_partials(int o, int v);
 void launch_energy(int o, int v, const double *R, const double *t2, double *part, double *E,
                    cudaStream_t s);
 
+// ---- t1-dressed ladder: Bd = B - mbar and the rank-o correction (dress.cu)
+cudaError_t launch_dress_B(int o, int v, int N, const double *B, const double *Bov,
+                           const double *t1, double *Bd, bool fp32_mbar, cudaStream_t s);
+enum : int { kEpiStore = 0, kEpiPerm = 1, kEpiSubR = 2 };
+// C(m, n) = sum_k A(m, k) B(n, k), A(m, k) = A[m*sam + k*sak], B(n, k) = B[n*sbn + k*sbk]
+// (one of the two strides of each operand is 1); z = batch * ksplit + split.
+struct GemmArgs {
+  const void *A, *B;
+  void *Out;
+  long long sam, sak, sbn, sbk;
+  long long sa_batch, sb_batch, so_batch;  // per batch (A, B, kEpiSubR) or per z (kEpiStore)
+  int M, N, K;
+  int ksplit, kchunk;
+  int ldo;
+  int epi;
+  int sym;     // A == B: compute the tiles with m-tile <= n-tile, mirror in the epilogue
+  int po, pv;  // kEpiPerm: m = (k, c), n = (l, d) -> Out[((k * po + l) * pv + c) * pv + d]
+  int ntm, ntn, zoff;  // set by the launcher
+};
+template <typename TA, typename TB, typename T>
+cudaError_t launch_gemm(const GemmArgs &g, int batch, cudaStream_t s);
+template <typename T>
+cudaError_t launch_reduce(T *X, long long n, int parts, cudaStream_t s);
+
 // ---- FP64 fused ladder (DMMA)
 struct Fp64Args {
   const double *B;   // [N][v][v]

@@ -25,6 +25,7 @@ struct Layout {
   size_t gWt = 0, gTt = 0, gBs = 0, gacc = 0;  // split-BF16 dB
   size_t Vg = 0, T2 = 0;                       // two-pass form: stored V+- tiles, tau+- per chunk
   size_t gG = 0, gT2 = 0, gacc2 = 0;           // two-pass dB: Gamma planes, B per chunk, sums
+  size_t dBd = 0, dG = 0, dX = 0, dY = 0;      // t1 dressing: B - mbar, (kc|ld), X, Y
 };
 
 // Two-pass form: at most this many bytes of stored V+- tiles by default.
@@ -79,6 +80,8 @@ bool encode4d(CUtensorMap *m, void *base, uint64_t d0, uint64_t d1, uint64_t d2,
 struct ladder_plan_s {
   int o = 0, v = 0, N = 0, mode = 0;
   bool backward = false;
+  bool dressed = false;  // workspace sized for ladder_apply_dressed
+  int dx_ksplit = 1;     // K splits of the X_ij^kl contraction
   int grid_grad = 0;
   int vp = 0, nb = 0, nbp = 0, K = 0, Np = 0;
   int nlp = 0, nlm = 0;
@@ -319,6 +322,25 @@ void compute_layout(ladder_plan_s *pl) {
       off = align_up(L.gacc + (size_t)pl->g_ntiles * pl->g_npc * 128 * kGradTcPChunk * sizeof(double));
     }
   }
+  if (pl->dressed) {
+    // t1 dressing (dress.cu): Bd [N][v][v] f64, then the correction in T
+    // (double for FP64, float for the split modes): G [(k,l)][(c,d)],
+    // X partials [dx_ksplit][(i,j)][(k,l)], Y [(i,j,k)][b]
+    const size_t tsz = pl->mode == LADDER_FP64 ? sizeof(double) : sizeof(float);
+    const size_t o = pl->o, v = pl->v, oo = o * o;
+    const long long xt = (long long)((oo + 127) / 128) * ((oo + 127) / 128);
+    int ks = (int)((3LL * pl->sm_count + xt - 1) / xt);
+    ks = std::max(1, std::min(ks, std::min(64, (int)std::max<size_t>(1, v * v / 1024))));
+    pl->dx_ksplit = ks;
+    L.dBd = align_up(off);
+    off = L.dBd + (size_t)pl->N * v * v * sizeof(double);
+    L.dG = align_up(off);
+    off = L.dG + oo * v * v * tsz;
+    L.dX = align_up(off);
+    off = L.dX + (size_t)ks * oo * oo * tsz;
+    L.dY = align_up(off);
+    off = align_up(L.dY + oo * o * v * tsz);
+  }
   L.total = off;
   pl->lay = L;
 }
@@ -332,6 +354,93 @@ static int auto_vsplit(const ladder_plan_s *pl, bool batch_member) {
   if (const char *e = getenv("LADDER_VSPLIT")) vs = atoi(e);
   else vs = std::max(vs, (pl->nbp + 127) / 128);
   return std::max(1, std::min(vs, pl->nbp));
+}
+
+// Correction of the dressed term (dress.cu): R -= sum_kl t_k^a t_l^b X_ij^kl with
+// X_ij^kl = sum_cd (kc|ld) tau_ij^cd, (kc|ld) = sum_P Bov^P_kc Bov^P_ld.
+template <typename T>
+ladder_status dress_correct(const ladder_plan_s *pl, const double *Bov, const double *t1,
+                                   const double *tau, double *R, cudaStream_t s) {
+  const int o = pl->o, v = pl->v;
+  const long long ov = (long long)o * v, vv = (long long)v * v, oo = (long long)o * o;
+  T *G = ws_at<T>(pl, pl->lay.dG), *X = ws_at<T>(pl, pl->lay.dX), *Y = ws_at<T>(pl, pl->lay.dY);
+  // 1. G[(k,l)][(c,d)] = sum_P Bov[P][k][c] Bov[P][l][d]: M = N = o v, K = N_aux, symmetric
+  GemmArgs g;
+  std::memset(&g, 0, sizeof(g));
+  g.A = Bov;
+  g.B = Bov;
+  g.Out = G;
+  g.sam = 1;
+  g.sak = ov;
+  g.sbn = 1;
+  g.sbk = ov;
+  g.M = g.N = (int)ov;
+  g.K = pl->N;
+  g.ksplit = 1;
+  g.kchunk = pl->N;
+  g.epi = kEpiPerm;
+  g.sym = 1;
+  g.po = o;
+  g.pv = v;
+  cudaError_t e = launch_gemm<double, double, T>(g, 1, s);
+  // 2. X[(i,j)][(k,l)] = sum_(c,d) tau[(i,j)][(c,d)] G[(k,l)][(c,d)], split over (c,d)
+  GemmArgs x;
+  std::memset(&x, 0, sizeof(x));
+  const int ks = pl->dx_ksplit;
+  x.A = tau;
+  x.B = G;
+  x.Out = X;
+  x.sam = vv;
+  x.sak = 1;
+  x.sbn = vv;
+  x.sbk = 1;
+  x.M = x.N = (int)oo;
+  x.K = (int)vv;
+  x.ksplit = ks;
+  x.kchunk = (int)((vv + ks - 1) / ks + 7) / 8 * 8;
+  x.ldo = (int)oo;
+  x.so_batch = oo * oo;
+  x.epi = kEpiStore;
+  if (e == cudaSuccess) e = launch_gemm<double, T, T>(x, 1, s);
+  if (e == cudaSuccess) e = launch_reduce<T>(X, oo * oo, ks, s);
+  // 3. Y[(i,j,k)][b] = sum_l X[(i,j,k)][l] t1[l][b]: M = o^3, N = v, K = o
+  GemmArgs y;
+  std::memset(&y, 0, sizeof(y));
+  y.A = X;
+  y.B = t1;
+  y.Out = Y;
+  y.sam = o;
+  y.sak = 1;
+  y.sbn = 1;
+  y.sbk = v;
+  y.M = (int)(oo * o);
+  y.N = v;
+  y.K = o;
+  y.ksplit = 1;
+  y.kchunk = o;
+  y.ldo = v;
+  y.epi = kEpiStore;
+  if (e == cudaSuccess) e = launch_gemm<T, double, T>(y, 1, s);
+  // 4. R[(i,j)][a][b] -= sum_k t1[k][a] Y[(i,j)][k][b]: one v x v product per (i,j), K = o
+  GemmArgs c;
+  std::memset(&c, 0, sizeof(c));
+  c.A = t1;
+  c.B = Y;
+  c.Out = R;
+  c.sam = 1;
+  c.sak = v;
+  c.sbn = 1;
+  c.sbk = v;
+  c.sb_batch = ov;
+  c.so_batch = vv;
+  c.M = c.N = v;
+  c.K = o;
+  c.ksplit = 1;
+  c.kchunk = o;
+  c.ldo = v;
+  c.epi = kEpiSubR;
+  if (e == cudaSuccess) e = launch_gemm<double, T, T>(c, (int)oo, s);
+  return cuda_status(e);
 }
 
 }  // namespace
@@ -366,7 +475,7 @@ static int auto_ksplit(const ladder_plan_s *pl) {
 // Fills a plan for one shape; batch members get no block-pair split (the
 // batch itself keeps every SM busy).
 static ladder_status init_plan(ladder_plan_s *pl, int o, int v, int naux, int mode,
-                               bool with_backward, bool batch_member) {
+                               bool with_backward, bool batch_member, bool with_dressing = false) {
   if (o < 1 || o > 256 || v < 1 || v > 4096 || naux < 1 || naux > 65536) return LADDER_EINVAL;
   if (mode < LADDER_FP64 || mode > LADDER_AUTO) return LADDER_EINVAL;
   if (mode == LADDER_AUTO) mode = LADDER_BF16X6;
@@ -375,6 +484,7 @@ static ladder_status init_plan(ladder_plan_s *pl, int o, int v, int naux, int mo
   pl->N = naux;
   pl->mode = mode;
   pl->backward = with_backward;
+  pl->dressed = with_dressing;
   pl->vp = (v + VPAD - 1) / VPAD * VPAD;
   pl->nb = pl->vp / CB;
   pl->nbp = ppos(pl->nb);
@@ -449,10 +559,11 @@ ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out) 
   if (!out) return LADDER_EINVAL;
   *out = nullptr;
   const bool with_backward = (mode & LADDER_WITH_BACKWARD) != 0;
-  mode &= ~LADDER_WITH_BACKWARD;
+  const bool with_dressing = (mode & LADDER_WITH_DRESSING) != 0;
+  mode &= ~(LADDER_WITH_BACKWARD | LADDER_WITH_DRESSING);
   ladder_plan_s *pl = new (std::nothrow) ladder_plan_s();
   if (!pl) return LADDER_ENOMEM;
-  const ladder_status st = init_plan(pl, o, v, naux, mode, with_backward, false);
+  const ladder_status st = init_plan(pl, o, v, naux, mode, with_backward, false, with_dressing);
   if (st != LADDER_OK) {
     delete pl;
     return st;
@@ -762,6 +873,24 @@ ladder_status ladder_apply(ladder_plan_t pl, const double *B, const double *tau,
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (pl->mode == LADDER_FP64) return apply_fp64(pl, B, tau, R, s);
   return apply_tc(pl, B, tau, R, s);
+}
+
+ladder_status ladder_apply_dressed(ladder_plan_t pl, const double *B, const double *Bov,
+                                   const double *t1, const double *tau, double *R, void *stream) {
+  if (!pl || pl->batched || !pl->dressed) return LADDER_EINVAL;
+  if (!pl->ws) return LADDER_EWORKSPACE;
+  if (!dev_ptr_ok(B) || !dev_ptr_ok(Bov) || !dev_ptr_ok(t1) || !dev_ptr_ok(tau) || !dev_ptr_ok(R) ||
+      R == B || R == tau || R == Bov || R == t1)
+    return LADDER_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool f64 = pl->mode == LADDER_FP64;
+  double *Bd = ws_at<double>(pl, pl->lay.dBd);
+  ladder_status st = cuda_status(launch_dress_B(pl->o, pl->v, pl->N, B, Bov, t1, Bd, !f64, s));
+  if (st != LADDER_OK) return st;
+  st = f64 ? apply_fp64(pl, Bd, tau, R, s) : apply_tc(pl, Bd, tau, R, s);
+  if (st != LADDER_OK) return st;
+  return f64 ? dress_correct<double>(pl, Bov, t1, tau, R, s)
+             : dress_correct<float>(pl, Bov, t1, tau, R, s);
 }
 
 ladder_status ladder_energy(ladder_plan_t pl, const double *R, const double *t2, double *E_dev,
