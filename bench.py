@@ -286,6 +286,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--lambda-only", action="store_true",
+                    help="also time the paper's lambda-only contraction (ablation of the +- split)")
     ap.add_argument("--dressed", action="store_true",
                     help="also time the t1-dressed term (Eq. pp-Ladder-2) on the same workload")
     ap.add_argument("--form", default="auto", choices=["auto", "fused", "two-pass"],
@@ -419,11 +421,16 @@ def main():
         others.insert(0, args.mode + "_fused")  # the same mode in the one-kernel form
     if args.dressed and args.mode != "fp64":
         others.insert(0, args.mode + "_dressed")  # the t1-dressed term (Eq. pp-Ladder-2)
+    if args.lambda_only and args.mode != "fp64":
+        others.insert(0, args.mode + "_lambda")  # the paper's lambda-only contraction (ablation)
     B_ov = None
     for m in others:
         if m.endswith("_dressed"):
             Lm = lad.Ladder(w.o, w.v, w.naux, mode=m[:-8], device=dev, tuning=tun, dressed=True)
             B_ov = torch.from_numpy(x.B_ov).to(dev)
+        elif m.endswith("_lambda"):
+            Lm = lad.Ladder(w.o, w.v, w.naux, mode=m[:-7], device=dev,
+                            tuning={**tun, "two_pass": 1, "lambda_only": 1, "ksplit": 0})
         elif m.endswith("_fused"):
             Lm = lad.Ladder(w.o, w.v, w.naux, mode=m[:-6], device=dev, tuning={**tun, "two_pass": 0, "ksplit": 0})
         else:
@@ -450,6 +457,9 @@ def main():
                "E_L": float(E.item()), "steps": 1}
         if parity is not None and not m.endswith("_dressed"):
             ent["dE_L"] = abs(float(E.item()) - parity["E_L"])
+        if m.endswith("_lambda"):
+            p1, p2 = lad.ladder_timing_passes(Lm.plan)
+            ent["pass1_ms"], ent["pass2_ms"] = p1, p2
         if m.endswith("_dressed"):
             # tau, B - mbar, the rank-o correction and the energy
             ent["outside_ladder_ms"] = mms - tm[0] - tm[1] - tm[2]

@@ -88,12 +88,18 @@ ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out);
  *               tile and block pair), then GEMM2 from the stored tiles in
  *               chunks of up to 192 occupied pairs.  The plan picks 1 when the
  *               stored tiles take at most 128 GiB.
+ *   lambda_only 1: the paper's own contraction, which uses only the pair
+ *               symmetry R_ij^ab = R_ji^ba (Sec. II.C), as an ablation of the
+ *               +- split: the storing pass keeps (ac|bd) and (ad|bc) instead
+ *               of their +- combinations, and GEMM2 runs over all o^2 ordered
+ *               occupied pairs against both (twice the GEMM2 work).  Needs
+ *               two_pass = 1; 0 (default) is the +- form.
  * Longer chains are faster and less accurate (the tensor core's FP32
  * accumulation error grows with the MMAs per accumulator).  ladder_set_tuning
  * must come before ladder_set_workspace (the workspace size depends on
  * ksplit and two_pass); it returns LADDER_EINVAL for out-of-range values. */
 typedef struct {
-    int kc, s_pieces, flush_every, ksplit, xy_split, two_pass;
+    int kc, s_pieces, flush_every, ksplit, xy_split, two_pass, lambda_only;
 } ladder_tuning;
 ladder_status ladder_get_tuning(ladder_plan_t plan, ladder_tuning *t);
 ladder_status ladder_set_tuning(ladder_plan_t plan, const ladder_tuning *t);

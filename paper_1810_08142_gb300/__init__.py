@@ -36,7 +36,8 @@ EXPORTS = ("ladder_plan", "ladder_plan_mode", "ladder_get_tuning", "ladder_set_t
 class Tuning(ctypes.Structure):
     """Mirror of ladder_tuning (include/ladder.h)."""
     _fields_ = [("kc", ctypes.c_int), ("s_pieces", ctypes.c_int), ("flush_every", ctypes.c_int),
-                ("ksplit", ctypes.c_int), ("xy_split", ctypes.c_int), ("two_pass", ctypes.c_int)]
+                ("ksplit", ctypes.c_int), ("xy_split", ctypes.c_int), ("two_pass", ctypes.c_int),
+                ("lambda_only", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

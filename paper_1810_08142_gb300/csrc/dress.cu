@@ -15,10 +15,11 @@
 // G costs 2 (ov)^2 N flops (half of it with its symmetry), X 2 o^4 v^2: both
 // O(o^2 v^2 N + o^4 v^2), against the ladder's O(v^4 N + o^2 v^4).
 //
-// This file holds the three kernels of that correction:
-//   dress_B_kernel  Bd = B - mbar (FP64 result; mbar accumulated in T)
+// This file holds the two kernels of the dressing:
 //   gemm_kernel     a CUDA-core GEMM C(m,n) = sum_k A(m,k) B(n,k) with free
-//                   strides, split-K / batch in z, and three epilogues
+//                   strides, split-K / batch in z, and four epilogues; it
+//                   forms Bd = B - mbar (one v x v product per P, K = o),
+//                   (kc|ld), X and the two t1 contractions of the correction
 //   reduce_kernel   sums split-K partials
 // T is double for the FP64 path and float for the split-BF16 paths (the
 // correction is about 1e-4 of R there, so FP32 keeps it far inside their
@@ -29,58 +30,6 @@
 
 namespace ladder {
 namespace {
-
-// ---------------------------------------------------------------- Bd = B - mbar
-constexpr int kDB = 32;    // b rows per CTA
-constexpr int kDD = 128;   // d columns per CTA
-constexpr int kDK = 32;    // occupied indices per shared-memory chunk
-
-template <typename T>
-__global__ void __launch_bounds__(256) dress_B_kernel(int o, int v, const double *__restrict__ B,
-                                                      const double *__restrict__ Bov,
-                                                      const double *__restrict__ t1,
-                                                      double *__restrict__ Bd) {
-  __shared__ T sO[kDK][kDD];   // Bov[P][k][d-tile]
-  __shared__ T sT[kDK][kDB];   // t1[k][b-tile]
-  const int nd = (v + kDD - 1) / kDD;
-  const int P = blockIdx.x / nd;
-  const int b0 = blockIdx.y * kDB, d0 = (blockIdx.x % nd) * kDD;
-  const int tid = threadIdx.x;
-  const int dl = tid % kDD, bq = tid / kDD;  // each thread: one d, b rows bq, bq+2, ...
-  T acc[kDB / 2];
-#pragma unroll
-  for (int r = 0; r < kDB / 2; ++r) acc[r] = T(0);
-  const double *O = Bov + (size_t)P * o * v;
-  for (int k0 = 0; k0 < o; k0 += kDK) {
-    for (int e = tid; e < kDK * kDD; e += 256) {
-      const int k = k0 + e / kDD, d = d0 + e % kDD;
-      sO[e / kDD][e % kDD] = (k < o && d < v) ? (T)O[(size_t)k * v + d] : T(0);
-    }
-    for (int e = tid; e < kDK * kDB; e += 256) {
-      const int k = k0 + e / kDB, b = b0 + e % kDB;
-      sT[e / kDB][e % kDB] = (k < o && b < v) ? (T)t1[(size_t)k * v + b] : T(0);
-    }
-    __syncthreads();
-    const int kn = min(kDK, o - k0);
-    for (int k = 0; k < kn; ++k) {
-      const T x = sO[k][dl];
-#pragma unroll
-      for (int r = 0; r < kDB / 2; ++r) acc[r] += sT[k][bq + 2 * r] * x;
-    }
-    __syncthreads();
-  }
-  const int d = d0 + dl;
-  if (d < v) {
-#pragma unroll
-    for (int r = 0; r < kDB / 2; ++r) {
-      const int b = b0 + bq + 2 * r;
-      if (b < v) {
-        const size_t idx = ((size_t)P * v + b) * v + d;
-        Bd[idx] = B[idx] - (double)acc[r];
-      }
-    }
-  }
-}
 
 // ---------------------------------------------------------------- CUDA-core GEMM
 constexpr int kBM = 128, kBN = 128, kBK = 8;
@@ -207,9 +156,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) gemm_kernel(const
         const long long vv = (long long)g.pv * g.pv;
         G[((long long)k * g.po + l) * vv + (long long)c * g.pv + d] = val;
         if (g.sym) G[((long long)l * g.po + k) * vv + (long long)d * g.pv + c] = val;
-      } else {  // kEpiSubR: R -= val (FP64 result)
+      } else if (g.epi == kEpiSubR) {  // R -= val (FP64 result)
         double *R = static_cast<double *>(g.Out);
         R[(long long)batch * g.so_batch + (long long)m * g.ldo + n] -= (double)val;
+      } else {  // kEpiFromSrc: Out = Src - val (FP64)
+        const long long at = (long long)batch * g.so_batch + (long long)m * g.ldo + n;
+        static_cast<double *>(g.Out)[at] = g.Src[at] - (double)val;
       }
     }
   }
@@ -226,16 +178,6 @@ __global__ void reduce_kernel(T *__restrict__ X, long long n, int parts) {
 }
 
 }  // namespace
-
-cudaError_t launch_dress_B(int o, int v, int N, const double *B, const double *Bov,
-                           const double *t1, double *Bd, bool fp32_mbar, cudaStream_t s) {
-  const dim3 grid((unsigned)(N * ((v + kDD - 1) / kDD)), (v + kDB - 1) / kDB);
-  if (fp32_mbar)
-    dress_B_kernel<float><<<grid, 256, 0, s>>>(o, v, B, Bov, t1, Bd);
-  else
-    dress_B_kernel<double><<<grid, 256, 0, s>>>(o, v, B, Bov, t1, Bd);
-  return cudaGetLastError();
-}
 
 template <typename TA, typename TB, typename T>
 cudaError_t launch_gemm(const GemmArgs &g, int batch, cudaStream_t s) {

@@ -28,16 +28,17 @@ void launch_energy(int o, int v, const double *R, const double *t2, double *part
                    cudaStream_t s);
 
 // ---- t1-dressed ladder: Bd = B - mbar and the rank-o correction (dress.cu)
-cudaError_t launch_dress_B(int o, int v, int N, const double *B, const double *Bov,
-                           const double *t1, double *Bd, bool fp32_mbar, cudaStream_t s);
-enum : int { kEpiStore = 0, kEpiPerm = 1, kEpiSubR = 2 };
+// kEpiStore: Out (T) = C; kEpiPerm: Out (T) = C in the permuted (k,l)(c,d) layout;
+// kEpiSubR: Out (double) -= C; kEpiFromSrc: Out (double) = Src - C.
+enum : int { kEpiStore = 0, kEpiPerm = 1, kEpiSubR = 2, kEpiFromSrc = 3 };
 // C(m, n) = sum_k A(m, k) B(n, k), A(m, k) = A[m*sam + k*sak], B(n, k) = B[n*sbn + k*sbk]
 // (one of the two strides of each operand is 1); z = batch * ksplit + split.
 struct GemmArgs {
   const void *A, *B;
   void *Out;
+  const double *Src;  // kEpiFromSrc
   long long sam, sak, sbn, sbk;
-  long long sa_batch, sb_batch, so_batch;  // per batch (A, B, kEpiSubR) or per z (kEpiStore)
+  long long sa_batch, sb_batch, so_batch;  // per batch (A, B, kEpiSubR/FromSrc) or per z (kEpiStore)
   int M, N, K;
   int ksplit, kchunk;
   int ldo;
@@ -140,6 +141,10 @@ struct TcArgs {
   int nplus, wplus, wminus;  // two-pass GEMM2: plus chunks first, lambda columns per chunk
   int square;        // GEMM2 kernel: tiles cover every (16-block, 8-block) pair (two-pass dB)
   int nsign;         // GEMM2 kernel: stored planes per (tile, block) = nsign * S
+  int lam_only;      // the paper's lambda-only contraction (an ablation of the +- split):
+                     // the storing pass keeps X = (ac|bd) and Y' = (ad|bc) instead of
+                     // V+- = X +- Y', and each GEMM2 piece multiplies both planes into
+                     // one accumulator, X by tau^cd and Y' by tau^dc, for all ordered ij
   unsigned long long timeout_ns;
   TcChunk chunks[kMaxChunks];
 };
@@ -152,6 +157,18 @@ struct T2Args {
   long long off[kMaxChunks];     // element offset of each chunk in T2
 };
 void launch_pack_t2(const T2Args &a, cudaStream_t s);
+// lambda-only GEMM2 operand, straight from tau: for chunk c (ordered pairs
+// ij = lp0 .. lp0 + np - 1, padded to nps rows), global 16-slot piece x and
+// plane j, slice s of w tau_ij^cd (j = 0) or w tau_ij^dc (j = 1), w = 1/2 on
+// diagonal block pairs and 1 elsewhere, 32-byte swizzled rows; chunk c starts
+// at byte t2off.
+struct T2LamArgs {
+  const double *tau;  // [o][o][v][v]
+  __nv_bfloat16 *T2;
+  int o, v, K, S, nchunks;
+  TcChunk chunks[kMaxChunks];
+};
+void launch_pack_t2_lam(const T2LamArgs &a, cudaStream_t s);
 
 // Per-chunk, pre-swizzled copy of the B slices as the GEMM2 kernel's second
 // operand: for aux chunk c, (b,d) block q and 16-slot piece, rows P of the
@@ -187,6 +204,8 @@ cudaError_t launch_ladder_gemm2(const TcLaunch &a, int nslices, int grid, cudaSt
 cudaError_t launch_unpack(const TcLaunch &a, int nblocks, cudaStream_t s);
 // two-pass form: nblocks = tiles x plus-chunks (a batch lists (molecule, block) in tcs)
 cudaError_t launch_unpack2(const TcLaunch &a, int nblocks, cudaStream_t s);
+// lambda-only form: one block per (tile, chunk); R_ij^ab and R_ji^ba from one column
+cudaError_t launch_unpack_lam(const TcLaunch &a, int nblocks, cudaStream_t s);
 // two-pass dB: dB[P][x][y] = 2 x the sums of the GEMM2 kernel, blocks = tiles x chunks
 cudaError_t launch_grad_unpack2(const TcLaunch &a, double *dB, int N, int nblocks, cudaStream_t s);
 cudaError_t launch_selftest_wait(int *status, unsigned long long timeout_ns, int site,

@@ -95,6 +95,7 @@ struct ladder_plan_s {
   // two-pass form: GEMM2 chunks (up to kTcMaxColsV columns), block-pair
   // ranges per tile of the storing pass
   int two_pass = 0, vsplit = 1, racc_cols_v = 0, nplus = 0, wplus = 0, wminus = 0;
+  int lam_only = 0;  // the paper's lambda-only contraction (two-pass form only)
   bool last_two_pass = false;
   std::vector<TcChunk> chunks_v;
   CUtensorMap tmA, tmB, tmTp, tmTm, tmVl;
@@ -180,6 +181,24 @@ std::vector<TcChunk> make_tc_chunks(int o, int maxcols) {
 // Chunks of the two-pass GEMM2 kernel: lambda+ columns in nplus chunks of
 // wplus, then lambda- columns in chunks of wminus (balanced, multiples of 16,
 // at most maxcols).
+// Lambda-only form: the ordered occupied pairs ij = i*o + j in balanced
+// chunks of at most maxcols columns (multiples of 16).
+std::vector<TcChunk> make_lam_chunks(int o, int maxcols, int &n, int &w) {
+  const int cols = o * o;
+  n = (cols + maxcols - 1) / maxcols;
+  w = (((cols + n - 1) / n) + 15) / 16 * 16;
+  std::vector<TcChunk> out;
+  for (int c = 0; c * w < cols; ++c) {
+    TcChunk t{};
+    t.lp0 = c * w;
+    t.np = std::min(w, cols - t.lp0);
+    t.nps = (t.np + 15) / 16 * 16;
+    out.push_back(t);
+  }
+  n = (int)out.size();
+  return out;
+}
+
 std::vector<TcChunk> make_sign_chunks(int o, int maxcols, int &nplus, int &wplus, int &wminus) {
   auto pad16 = [](int x) { return (x + 15) / 16 * 16; };
   std::vector<TcChunk> out;
@@ -262,7 +281,7 @@ void compute_layout(ladder_plan_s *pl) {
       size_t t2 = 0;
       for (auto &c : pl->chunks_v) {
         c.t2off = (long long)t2;
-        t2 += (size_t)S * (c.nps + c.nms) * pl->K * 2;
+        t2 += (size_t)S * (c.nps + c.nms) * pl->K * 2 * (pl->lam_only ? 2 : 1);
       }
       off = align_up(off + t2, 1024);
     }
@@ -329,7 +348,7 @@ void compute_layout(ladder_plan_s *pl) {
     const size_t tsz = pl->mode == LADDER_FP64 ? sizeof(double) : sizeof(float);
     const size_t o = pl->o, v = pl->v, oo = o * o;
     const long long xt = (long long)((oo + 127) / 128) * ((oo + 127) / 128);
-    int ks = (int)((3LL * pl->sm_count + xt - 1) / xt);
+    int ks = (int)((8LL * pl->sm_count + xt - 1) / xt);
     ks = std::max(1, std::min(ks, std::min(64, (int)std::max<size_t>(1, v * v / 1024))));
     pl->dx_ksplit = ks;
     L.dBd = align_up(off);
@@ -586,6 +605,7 @@ ladder_status ladder_get_tuning(ladder_plan_t pl, ladder_tuning *t) {
   t->ksplit = pl->ksplit;
   t->xy_split = pl->xy_split;
   t->two_pass = pl->two_pass;
+  t->lambda_only = pl->lam_only;
   return LADDER_OK;
 }
 
@@ -594,8 +614,21 @@ ladder_status ladder_set_tuning(ladder_plan_t pl, const ladder_tuning *t) {
   if (pl->mode == LADDER_FP64) return LADDER_OK;
   if (t->kc < 1 || t->kc > 64 || !(t->s_pieces == 1 || t->s_pieces == 2 || t->s_pieces == 4) ||
       t->flush_every < 1 || t->flush_every > 4096 || t->ksplit < 0 || t->ksplit > pl->nbp ||
-      (t->xy_split != 0 && t->xy_split != 1) || (t->two_pass != 0 && t->two_pass != 1))
+      (t->xy_split != 0 && t->xy_split != 1) || (t->two_pass != 0 && t->two_pass != 1) ||
+      (t->lambda_only != 0 && t->lambda_only != 1) || (t->lambda_only && !t->two_pass))
     return LADDER_EINVAL;
+  if (t->lambda_only != pl->lam_only) {
+    pl->lam_only = t->lambda_only;
+    if (pl->lam_only) {
+      pl->chunks_v = make_lam_chunks(pl->o, kTcMaxColsV, pl->nplus, pl->wplus);
+      pl->wminus = 16;
+    } else {
+      pl->chunks_v = make_sign_chunks(pl->o, kTcMaxColsV, pl->nplus, pl->wplus, pl->wminus);
+    }
+    if ((int)pl->chunks_v.size() > kMaxChunks) return LADDER_ENOTSUP;
+    pl->racc_cols_v = 0;
+    for (auto &c : pl->chunks_v) pl->racc_cols_v = std::max(pl->racc_cols_v, c.nps + c.nms);
+  }
   pl->kc = t->kc;
   pl->s_pieces = t->s_pieces;
   pl->flush_every = t->flush_every;
@@ -769,6 +802,7 @@ static TcArgs tc_args(const ladder_plan_s *pl, double *R, int *status) {
   for (int c = 0; c < a.nchunks; ++c) a.chunks[c] = pl->chunks_tc[c];
   a.timeout_ns = (unsigned long long)tc_timeout_ns(pl);
   a.nsign = 2;
+  a.lam_only = pl->lam_only;
   return a;
 }
 
@@ -778,6 +812,21 @@ static void tc_prep(ladder_plan_t pl, const double *B, const double *tau, cudaSt
   auto *Tp = ws_at<__nv_bfloat16>(pl, pl->lay.Tp);
   auto *Tm = ws_at<__nv_bfloat16>(pl, pl->lay.Tm);
   launch_split_B(pl->N, pl->v, pl->vp, pl->Np, pl->S, B, Bt, s, transB);
+  if (pl->lam_only && pl->two_pass) {
+    // the lambda-only GEMM2 operand comes straight from tau (pack_t2_lam)
+    T2LamArgs t;
+    std::memset(&t, 0, sizeof(t));
+    t.tau = tau;
+    t.T2 = ws_at<__nv_bfloat16>(pl, pl->lay.T2);
+    t.o = pl->o;
+    t.v = pl->v;
+    t.K = pl->K;
+    t.S = pl->S;
+    t.nchunks = (int)pl->chunks_v.size();
+    for (int c = 0; c < t.nchunks; ++c) t.chunks[c] = pl->chunks_v[c];
+    launch_pack_t2_lam(t, s);
+    return;
+  }
   launch_pack_tpm_bf16(pl->o, pl->v, pl->K, pl->S, pl->nlp, std::max(pl->nlm, 1), tau, Tp, Tm, s);
 }
 
@@ -842,7 +891,7 @@ static ladder_status apply_tc(ladder_plan_t pl, const double *B, const double *t
     L.one = pass2_args(pl, R, status);
     L.timeout_ns = L.one.timeout_ns;
     L.nitems = L.one.ntiles * L.one.nchunks * L.one.ksplit;
-    pack_t2(pl, s);
+    if (!pl->lam_only) pack_t2(pl, s);
     st = cuda_status(cudaGetLastError());
     if (st != LADDER_OK) return st;
     mark(pl, 1, s);
@@ -850,7 +899,9 @@ static ladder_status apply_tc(ladder_plan_t pl, const double *B, const double *t
     mark(pl, 4, s);
     if (st == LADDER_OK) st = cuda_status(launch_ladder_gemm2(L, pl->S, L.nitems, s));
     mark(pl, 2, s);
-    if (st == LADDER_OK) st = cuda_status(launch_unpack2(L, L.one.ntiles * L.one.nplus, s));
+    if (st == LADDER_OK)
+      st = cuda_status(pl->lam_only ? launch_unpack_lam(L, L.one.ntiles * L.one.nchunks, s)
+                                    : launch_unpack2(L, L.one.ntiles * L.one.nplus, s));
   } else {
     L.one = tc_args(pl, R, status);
     L.timeout_ns = L.one.timeout_ns;
@@ -885,7 +936,27 @@ ladder_status ladder_apply_dressed(ladder_plan_t pl, const double *B, const doub
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bool f64 = pl->mode == LADDER_FP64;
   double *Bd = ws_at<double>(pl, pl->lay.dBd);
-  ladder_status st = cuda_status(launch_dress_B(pl->o, pl->v, pl->N, B, Bov, t1, Bd, !f64, s));
+  // Bd[P][b][d] = B[P][b][d] - sum_k t1[k][b] Bov[P][k][d]: one v x v product per P, K = o
+  GemmArgs g;
+  std::memset(&g, 0, sizeof(g));
+  g.A = t1;
+  g.B = Bov;
+  g.Out = Bd;
+  g.Src = B;
+  g.sam = 1;
+  g.sak = pl->v;
+  g.sbn = 1;
+  g.sbk = pl->v;
+  g.sb_batch = (long long)pl->o * pl->v;
+  g.so_batch = (long long)pl->v * pl->v;
+  g.M = g.N = pl->v;
+  g.K = pl->o;
+  g.ksplit = 1;
+  g.kchunk = pl->o;
+  g.ldo = pl->v;
+  g.epi = kEpiFromSrc;
+  ladder_status st = cuda_status(f64 ? launch_gemm<double, double, double>(g, pl->N, s)
+                                     : launch_gemm<double, double, float>(g, pl->N, s));
   if (st != LADDER_OK) return st;
   st = f64 ? apply_fp64(pl, Bd, tau, R, s) : apply_tc(pl, Bd, tau, R, s);
   if (st != LADDER_OK) return st;

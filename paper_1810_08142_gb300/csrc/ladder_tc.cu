@@ -596,7 +596,9 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
         if constexpr (kStoreV) {
           // V+- slices straight to the planes [tile][pair][sign][slice][128
           // rows][64 slots]: a warp writes whole 128-byte rows
+          // (lambda-only form: X and Y' themselves, no +- combination)
           __nv_bfloat16 *vp = A.Vst + (size_t)(I.tile * A.nbp + p) * 2 * S * (128 * SLOTS);
+          const bool lam = A.lam_only != 0;
   #pragma unroll
           for (int b = 0; b < 4; ++b) {
             const int row = a_l * 8 + 4 * half + b;
@@ -604,7 +606,9 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_tc_kernel(const __grid_con
             for (int sg = 0; sg < 2; ++sg) {
               float rem[8];
   #pragma unroll
-              for (int d = 0; d < 8; ++d) rem[d] = sg ? X[b * 8 + d] - Y[b * 8 + d] : X[b * 8 + d] + Y[b * 8 + d];
+              for (int d = 0; d < 8; ++d)
+                rem[d] = lam ? (sg ? Y[b * 8 + d] : X[b * 8 + d])
+                             : (sg ? X[b * 8 + d] - Y[b * 8 + d] : X[b * 8 + d] + Y[b * 8 + d]);
   #pragma unroll
               for (int s = 0; s < S; ++s) {
                 const uint4 w = pack_slice(rem);
@@ -722,6 +726,7 @@ constexpr uint32_t VP_PLANE = 128u * TPIECE * 2u;  // 4 KB: 128 ab rows x 16 slo
 constexpr uint32_t kColS1 = 256;                   // TMEM: S0 [0, 192), S1 [256, 448)
 constexpr int kGroupsV = kTcMaxColsV / 32;         // 16-column groups per conversion warp
 constexpr int kPPS = 2;                            // 16-slot pieces per TMA stage
+static_assert(kPPS == 2, "the lambda-only form puts its two planes where the two pieces go");
 
 template <int S>
 struct Cfg2 {
@@ -804,9 +809,13 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_
         const TcChunk &CH = I.CH;
         const uint32_t tbytes = I.sc * 32u;
         const int sg = CH.nps > 0 ? 0 : 1;  // the chunk's sign
+        // a stage holds kPPS pieces of the chunk's sign, or (lambda-only) one
+        // piece of both planes; the bytes are the same
+        const bool lam = A.lam_only != 0;
+        const int pstep = lam ? 1 : kPPS;
         for (int p = I.p0; ok && p < I.p1; ++p) {
-          const int z = ((I.tile * A.nbp + p) * A.nsign + sg) * S;
-          for (int piece = 0; piece < kPieces; piece += kPPS) {
+          const int zb = (I.tile * A.nbp + p) * A.nsign;
+          for (int piece = 0; piece < kPieces; piece += pstep) {
             if (!(ok = mbar_wait(bars.empty(stage), phase ^ 1u, wd, kSiteTmaEmpty))) break;
             const uint32_t dst = ring + (uint32_t)stage * C::kStage;
             mbar_arrive_expect_tx(bars.full(stage), C::kV + (uint32_t)(kPPS * S) * tbytes);
@@ -815,9 +824,10 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_
             // (default L2 policy for both: marking the tau+- copy evict-last
             // or the V+- planes evict-first measured slower)
             for (int j = 0; j < kPPS; ++j)
-              tma_load_3d(dst + j * C::kV1, &A.tmVl, bars.full(stage), (piece + j) * TPIECE, 0, z);
-            // the chunk's tau+- rows of these pieces, every slice: one bulk copy
-            bulk_load(dst + C::kV, A.T2 + CH.t2off + (size_t)(p * kPieces + piece) * S * tbytes,
+              tma_load_3d(dst + j * C::kV1, &A.tmVl, bars.full(stage), (lam ? piece : piece + j) * TPIECE, 0,
+                          (zb + (lam ? j : sg)) * S);
+            // the chunk's tau rows of these pieces, every slice: one bulk copy
+            bulk_load(dst + C::kV, A.T2 + CH.t2off + (size_t)(p * kPieces + piece) * (lam ? 2 : 1) * S * tbytes,
                       (uint32_t)(kPPS * S) * tbytes, bars.full(stage));
             if (++stage == C::kStages) {
               stage = 0;
@@ -845,13 +855,16 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_
         const Item I = decode_item(A, gemm2_slot(A, local));
         const uint32_t id = idesc_bf16(128, (int)I.sc);
         const uint32_t tbytes = I.sc * 32u;
+        const bool lam = A.lam_only != 0;
+        const int pstep = lam ? 1 : kPPS;
         for (int p = I.p0; ok && p < I.p1; ++p)
-          for (int piece0 = 0; ok && piece0 < kPieces; piece0 += kPPS) {
+          for (int piece0 = 0; ok && piece0 < kPieces; piece0 += pstep) {
             if (!(ok = mbar_wait(bars.full(stage), phase, wd, kSiteTmaFull))) break;
             const uint32_t st = ring + (uint32_t)stage * C::kStage;
             for (int j = 0; ok && j < kPPS; ++j) {
-              const int piece = piece0 + j;
-              const bool first = (piece % A.s_pieces) == 0;
+              // lambda-only: j is the plane (X by tau^cd, Y' by tau^dc) of one piece
+              const int piece = lam ? piece0 : piece0 + j;
+              const bool first = (piece % A.s_pieces) == 0 && (!lam || j == 0);
               const uint32_t buf = g & 1u;
               if (first) {
                 if (!(ok = mbar_wait(bars.cfree(buf), ((g >> 1) & 1u) ^ 1u, wd, kSiteRFree))) break;
@@ -863,7 +876,7 @@ __global__ void __launch_bounds__(kThreads, 1) ladder_gemm2_kernel(const __grid_
               for (int q = 0; q < C::kProducts; ++q)
                 mma_bf16(dS, desc64(sv + (uint32_t)kPa(q) * VP_PLANE, hi32), desc64(stt + kPb(q) * tbytes, hi32),
                          id, (first && q == 0) ? 0u : 1u);
-              if ((piece + 1) % A.s_pieces == 0) {
+              if ((piece + 1) % A.s_pieces == 0 && (!lam || j == kPPS - 1)) {
                 mma_commit(bars.cfull(buf));
                 ++g;
               }
@@ -996,6 +1009,39 @@ __global__ void __launch_bounds__(128) unpack2_kernel(const __grid_constant__ Tc
   }
 }
 
+// ---------------------------------------------------------------- unpack (lambda-only)
+// One block per (tile, chunk) of the lambda-only form; lane = ab slot with
+// a <= b.  Column c of the chunk is the ordered pair ij = lp0 + c, and
+//   R_ij^ab = sum over the block-pair ranges,  R_ji^ba = R_ij^ab,
+// which writes every element of R once (a = b is written from ij and ji).
+__global__ void __launch_bounds__(128) unpack_lam_kernel(const __grid_constant__ TcLaunch Lp) {
+  const TcArgs &A = Lp.one;
+  const int tc = blockIdx.x, tile = tc / A.nchunks, ch = tc % A.nchunks;
+  int iA = 0, t = tile;
+  while (t >= A.nB8 - 2 * iA) {
+    t -= A.nB8 - 2 * iA;
+    ++iA;
+  }
+  const int jB = 2 * iA + t;
+  const int L = threadIdx.x;
+  const int a = iA * 16 + (L >> 3), b = jB * CB + (L & 7);
+  const bool diag_ab = (jB >> 1) == iA;
+  if (!(a < A.v && b < A.v && (!diag_ab || a <= b))) return;
+  const size_t per_item = (size_t)128 * A.racc_cols;
+  const float2 *base = A.racc + (size_t)tc * A.ksplit * per_item + L;
+  const size_t vv = (size_t)A.v * A.v, o = (size_t)A.o;
+  const TcChunk CH = A.chunks[ch];
+  for (int c = 0; c < CH.np; ++c) {
+    const float2 *bp = base + (size_t)c * 128;
+    float2 acc = bp[0];
+    for (int k = 1; k < A.ksplit; ++k) acc = ds_add2(acc, bp[k * per_item]);
+    const size_t ij = (size_t)CH.lp0 + c, i = ij / o, j = ij % o;
+    const double val = ds_value(acc);
+    A.R[(i * o + j) * vv + (size_t)a * A.v + b] = val;
+    A.R[(j * o + i) * vv + (size_t)b * A.v + a] = val;
+  }
+}
+
 // ---------------------------------------------------------------- unpack (two-pass dB)
 // dB[P][x][y] = 2 x the block-range sums of the GEMM2 kernel's accumulators
 // for tile (x 16-block, y 8-block) and aux chunk; lane = (x, y).
@@ -1096,6 +1142,11 @@ cudaError_t launch_ladder_gemm2(const TcLaunch &a, int nslices, int grid, cudaSt
 
 cudaError_t launch_unpack(const TcLaunch &a, int nblocks, cudaStream_t s) {
   unpack_kernel<<<nblocks, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_lam(const TcLaunch &a, int nblocks, cudaStream_t s) {
+  if (nblocks > 0) unpack_lam_kernel<<<nblocks, 128, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -148,6 +148,58 @@ void launch_pack_t2(const T2Args &a, cudaStream_t s) {
   pack_t2_kernel<<<grid, 256, 0, s>>>(a);
 }
 
+// ---------------------------------------------------------------- lambda-only tau per chunk
+// Operand of the lambda-only GEMM2 (T2LamArgs): layout [piece x][plane j][slice
+// s][row][32 bytes], rows 32-byte swizzled like pack_t2, so one bulk copy per
+// piece fills both planes.  Half h of the row of piece x (block pair (k, l),
+// local piece x % 4) holds slots 16 (x % 4) + 8 h + e, i.e. c = 8 k + 2 (x % 4) + h
+// and d = 8 l + e for e = 0..7.
+template <int S>
+__global__ void pack_t2_lam_kernel(const __grid_constant__ T2LamArgs a) {
+  const TcChunk CH = a.chunks[blockIdx.y];
+  const int sc = CH.nps;
+  const size_t units = (size_t)(a.K / 16) * 2 * sc * 2;  // (piece, plane, row, half)
+  uint4 *dst = reinterpret_cast<uint4 *>(a.T2 + CH.t2off / 2);
+  for (size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x; u < units;
+       u += (size_t)gridDim.x * blockDim.x) {
+    const int h = (int)(u & 1);
+    size_t t = u >> 1;
+    const int row = (int)(t % sc);
+    t /= sc;
+    const int j = (int)(t & 1);
+    const size_t x = t >> 1;
+    int k, l;
+    pair_of((int)(x / 4), k, l);
+    const int c = k * CB + 2 * (int)(x % 4) + h, d0 = l * CB;
+    const double w = (k == l) ? 0.5 : 1.0;
+    const bool live = row < CH.np;
+    const double *tij = a.tau + (size_t)(live ? CH.lp0 + row : 0) * a.v * a.v;
+    __nv_bfloat16 sl[S][8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int d = d0 + e;
+      double val = 0.0;
+      if (live && c < a.v && d < a.v) val = w * (j ? tij[(size_t)d * a.v + c] : tij[(size_t)c * a.v + d]);
+      __nv_bfloat16 xs[S];
+      split_bf16<S>(val, xs);
+#pragma unroll
+      for (int q = 0; q < S; ++q) sl[q][e] = xs[q];
+    }
+#pragma unroll
+    for (int q = 0; q < S; ++q)
+      dst[(((x * 2 + j) * S + q) * sc + row) * 2 + (h ^ ((row >> 2) & 1))] =
+          *reinterpret_cast<const uint4 *>(sl[q]);
+  }
+}
+
+void launch_pack_t2_lam(const T2LamArgs &a, cudaStream_t s) {
+  dim3 grid(1024, a.nchunks);
+  if (a.S == 2)
+    pack_t2_lam_kernel<2><<<grid, 256, 0, s>>>(a);
+  else
+    pack_t2_lam_kernel<3><<<grid, 256, 0, s>>>(a);
+}
+
 // ---------------------------------------------------------------- B per aux chunk (two-pass dB)
 // Second operand of the GEMM2 kernel in the two-pass dB: for aux chunk c,
 // (b, d) block q = (Bb, Dd) and 16-slot piece, the chunk's rows P (padding
