@@ -11,6 +11,11 @@ v=400, N_aux=1600).  The other form, BF16X3 and the FP64 path are timed on the
 same workload and reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--dressed] [--lambda-only]
+
+--dressed also times the t1-dressed term (Eq. pp-Ladder-2) and --lambda-only
+the paper's lambda-only contraction (the ablation of the +- split), one step
+each on the same workload, under "others".
 
 Under torchrun each rank runs its own replica of the workload on its own GPU
 (the ladder term of one molecule is one GPU's work); value = all ranks' flops
