@@ -43,6 +43,9 @@ import synthetic  # noqa: E402
 METRIC = "ladder TFLOP/s & ms/call, split-BF16 vs FP64 GPU path at |dE_L|<=1 uEh"
 DEFAULT_WORKLOAD = "mid_o34_v400_n1600"
 PRODUCTS = {"bf16x3": 3, "bf16x6": 6, "fp64": 1}
+# FP32 CUDA-core peak of one GB300, from the unit counts and the maximum SM
+# clock: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def peaks():
@@ -468,6 +471,17 @@ def main():
         if m.endswith("_dressed"):
             # tau, B - mbar, the rank-o correction and the energy
             ent["outside_ladder_ms"] = mms - tm[0] - tm[1] - tm[2]
+            bd_ms, corr_ms = lad.ladder_timing_dressing(Lm.plan)
+            o_, v_, n_ = w.o, w.v, w.naux
+            ov = o_ * v_
+            # algorithmic flops of the correction: (kc|ld) (symmetric), X, Y, C
+            fc = 2.0 * (ov * (ov + 1) / 2 * n_ + o_ ** 4 * v_ ** 2 + o_ ** 4 * v_ + o_ ** 3 * v_ ** 2)
+            ent["bd_ms"], ent["correction_ms"] = bd_ms, corr_ms
+            ent["bd_gbs"] = 16.0 * n_ * v_ * v_ / (bd_ms * 1e-3) / 1e9
+            ent["correction_roofline"] = {
+                "bound": "alu", "achieved": fc / (corr_ms * 1e-3) / 1e12, "peak": FP32_ALU_TFLOPS,
+                "unit": "TFLOP/s", "frac": fc / (corr_ms * 1e-3) / 1e12 / FP32_ALU_TFLOPS,
+                "note": "FP32 CUDA-core GEMMs; peak = 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}
         extra[m] = ent
         Lm.close()
         del Lm

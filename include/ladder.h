@@ -234,6 +234,10 @@ ladder_status ladder_timing(ladder_plan_t plan, float *prep_ms, float *fused_ms,
  * the two-pass form the storing GEMM1 pass and the GEMM2 pass; otherwise the
  * fused kernel and 0. */
 ladder_status ladder_timing_passes(ladder_plan_t plan, float *pass1_ms, float *pass2_ms);
+/* The last ladder_apply_dressed (waits for it): the B - mbar product and the
+ * rank-o correction after the ladder.  LADDER_EINVAL if the plan has no
+ * dressing or timing is off. */
+ladder_status ladder_timing_dressing(ladder_plan_t plan, float *bd_ms, float *correction_ms);
 
 /* Algorithmic flop count of one ladder_apply (two flops per multiply-add of
  * the symmetric/antisymmetric scheme; identical for every mode). */

@@ -29,7 +29,7 @@ STATUS = {0: "LADDER_OK", 1: "LADDER_EINVAL", 2: "LADDER_ENOMEM", 3: "LADDER_ECU
 EXPORTS = ("ladder_plan", "ladder_plan_mode", "ladder_get_tuning", "ladder_set_tuning", "ladder_workspace_size", "ladder_set_workspace",
            "ladder_tau", "ladder_apply", "ladder_apply_dressed", "ladder_energy", "ladder_energy_noalloc", "ladder_backward", "ladder_pair_combine", "ladder_apply_host",
            "ladder_plan_batched", "ladder_apply_batched", "ladder_last_device_error", "ladder_selftest_wait",
-           "ladder_set_timing", "ladder_timing", "ladder_timing_passes", "ladder_flops", "ladder_status_string",
+           "ladder_set_timing", "ladder_timing", "ladder_timing_passes", "ladder_timing_dressing", "ladder_flops", "ladder_status_string",
            "ladder_destroy")
 
 
@@ -86,6 +86,7 @@ def load_library(path: str = LIB_PATH):
         "ladder_timing": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
                           ctypes.POINTER(ctypes.c_float)],
         "ladder_timing_passes": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)],
+        "ladder_timing_dressing": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)],
         "ladder_flops": [_P],
         "ladder_status_string": [i],
         "ladder_destroy": [_P],
@@ -232,6 +233,14 @@ def ladder_timing_passes(plan):
     and the GEMM2 pass of the two-pass form, else (fused kernel, 0)."""
     t = [ctypes.c_float() for _ in range(2)]
     _check("ladder_timing_passes", load_library().ladder_timing_passes(plan, *[ctypes.byref(x) for x in t]))
+    return tuple(x.value for x in t)
+
+
+def ladder_timing_dressing(plan):
+    """(bd_ms, correction_ms) of the last ladder_apply_dressed: the B - mbar
+    product and the rank-o correction after the ladder."""
+    t = [ctypes.c_float() for _ in range(2)]
+    _check("ladder_timing_dressing", load_library().ladder_timing_dressing(plan, *[ctypes.byref(x) for x in t]))
     return tuple(x.value for x in t)
 
 

@@ -120,7 +120,9 @@ struct ladder_plan_s {
   cudaGraphExec_t gexec = nullptr;
   std::vector<const void *> gkey;  // pointers the graph was captured with
   bool timing = false;
-  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // 0..3: prep / ladder / unpack boundaries, 4: between the two passes,
+  // 5..7: dressed call (start, Bd done, correction done)
+  cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   void *ws = nullptr;
   size_t ws_bytes = 0;
 };
@@ -935,6 +937,7 @@ ladder_status ladder_apply_dressed(ladder_plan_t pl, const double *B, const doub
     return LADDER_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bool f64 = pl->mode == LADDER_FP64;
+  mark(pl, 5, s);
   double *Bd = ws_at<double>(pl, pl->lay.dBd);
   // Bd[P][b][d] = B[P][b][d] - sum_k t1[k][b] Bov[P][k][d]: one v x v product per P, K = o
   GemmArgs g;
@@ -958,10 +961,12 @@ ladder_status ladder_apply_dressed(ladder_plan_t pl, const double *B, const doub
   ladder_status st = cuda_status(f64 ? launch_gemm<double, double, double>(g, pl->N, s)
                                      : launch_gemm<double, double, float>(g, pl->N, s));
   if (st != LADDER_OK) return st;
+  mark(pl, 6, s);
   st = f64 ? apply_fp64(pl, Bd, tau, R, s) : apply_tc(pl, Bd, tau, R, s);
   if (st != LADDER_OK) return st;
-  return f64 ? dress_correct<double>(pl, Bov, t1, tau, R, s)
-             : dress_correct<float>(pl, Bov, t1, tau, R, s);
+  st = f64 ? dress_correct<double>(pl, Bov, t1, tau, R, s) : dress_correct<float>(pl, Bov, t1, tau, R, s);
+  mark(pl, 7, s);
+  return st;
 }
 
 ladder_status ladder_energy(ladder_plan_t pl, const double *R, const double *t2, double *E_dev,
@@ -1396,6 +1401,18 @@ ladder_status ladder_timing_passes(ladder_plan_t pl, float *pass1_ms, float *pas
   }
   if (pass1_ms) *pass1_ms = t1;
   if (pass2_ms) *pass2_ms = t2;
+  return LADDER_OK;
+}
+
+ladder_status ladder_timing_dressing(ladder_plan_t pl, float *bd_ms, float *correction_ms) {
+  if (!pl || !pl->timing || !pl->ev[0] || !pl->dressed) return LADDER_EINVAL;
+  if (cudaEventSynchronize(pl->ev[7]) != cudaSuccess) return cuda_status(cudaErrorUnknown);
+  float t1 = 0.f, t2 = 0.f;
+  if (cudaEventElapsedTime(&t1, pl->ev[5], pl->ev[6]) != cudaSuccess ||
+      cudaEventElapsedTime(&t2, pl->ev[3], pl->ev[7]) != cudaSuccess)
+    return cuda_status(cudaErrorUnknown);
+  if (bd_ms) *bd_ms = t1;
+  if (correction_ms) *correction_ms = t2;
   return LADDER_OK;
 }
 

@@ -5,6 +5,10 @@ workload it evaluates tau, the full ladder term R and E_L with the plain FP64
 oracle and stores: E_L, the Frobenius norm of R, and the R columns
 R[:, :, a, b] of a fixed list of (a, b) pairs.  Run from the repository root:
     python tests/golden/make_golden.py mid_o34_v400_n1600
+With --dressed it stores the same columns of the t1-dressed term
+(Eq. pp-Ladder-2) instead, from the oracle's per-column evaluation, in
+<workload>_dressed.json:
+    python tests/golden/make_golden.py --dressed mid_o34_v400_n1600
 """
 import json
 import os
@@ -51,6 +55,29 @@ def main(name):
     print(name, "E_L", E, "seconds", time.time() - t0)
 
 
+def main_dressed(name):
+    w = synthetic.WORKLOADS[name]
+    t0 = time.time()
+    x = synthetic.make_inputs(w.o, w.v, w.naux, w.seed)
+    tau = oracle.tau(x.t1, x.t2)
+    pa, pb = sample_pairs(w.v)
+    cols = oracle.ladder_dressed_pairs(x.B, x.B_ov, x.t1, tau, pa, pb)
+    out = {
+        "workload": name, "o": w.o, "v": w.v, "naux": w.naux, "seed": w.seed,
+        "pairs_a": pa, "pairs_b": pb, "R_cols": cols.tolist(),
+        "oracle_threads": oracle.threads(), "oracle_seconds": time.time() - t0,
+        "note": "t1-dressed term; written by tests/golden/make_golden.py --dressed from the "
+                "plain FP64 CPU oracle",
+    }
+    path = os.path.join(ROOT, "tests", "golden", name + "_dressed.json")
+    with open(path, "w") as f:
+        json.dump(out, f)
+    print(name, "dressed columns, seconds", time.time() - t0)
+
+
 if __name__ == "__main__":
-    for n in sys.argv[1:]:
-        main(n)
+    args = sys.argv[1:]
+    dressed = "--dressed" in args
+    for n in args:
+        if n != "--dressed":
+            (main_dressed if dressed else main)(n)

@@ -24,3 +24,15 @@ def run_forward(L, x):
     torch.cuda.synchronize()
     L.check_device()
     return tau.cpu().numpy(), R.cpu().numpy(), float(E.item())
+
+
+def run_dressed(L, x):
+    """tau, the t1-dressed R and its E_L through the C ABI (L built with dressed=True)."""
+    import torch
+    t1, t2, B, Bov = to_dev(x.t1), to_dev(x.t2), to_dev(x.B), to_dev(x.B_ov)
+    tau = L.tau(t1, t2)
+    R = L.apply_dressed(B, Bov, t1, tau)
+    E = L.energy(R, t2)
+    torch.cuda.synchronize()
+    L.check_device()
+    return tau.cpu().numpy(), R.cpu().numpy(), float(E.item())

@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 import synthetic
-from gpu_util import rel_fro, to_dev
+from gpu_util import rel_fro, run_dressed, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -34,17 +34,6 @@ def lad():
         pytest.skip("no CUDA device")
     import paper_1810_08142_gb300 as lad
     return lad
-
-
-def run_dressed(L, x):
-    import torch
-    t1, t2, B, Bov = to_dev(x.t1), to_dev(x.t2), to_dev(x.B), to_dev(x.B_ov)
-    tau = L.tau(t1, t2)
-    R = L.apply_dressed(B, Bov, t1, tau)
-    E = L.energy(R, t2)
-    torch.cuda.synchronize()
-    L.check_device()
-    return tau.cpu().numpy(), R.cpu().numpy(), float(E.item())
 
 
 @pytest.mark.parametrize("mode", ["fp64", "bf16x3", "bf16x6"])

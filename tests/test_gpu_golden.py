@@ -8,7 +8,9 @@ the benchmark times.
 
 Bars: FP64 mode |dE_L| <= 1 microhartree and the sampled columns to 1e-12
 relative; split-BF16 modes the sampled columns and ||R||_F to their relative
-Frobenius tolerance (BF16X6 1e-6, BF16X3 2e-5)."""
+Frobenius tolerance (BF16X6 1e-6, BF16X3 2e-5).  The same bars hold for the
+lambda-only form against the same values, and for the t1-dressed term against
+<workload>_dressed.json (sampled columns only)."""
 import json
 import os
 
@@ -16,7 +18,7 @@ import numpy as np
 import pytest
 
 import synthetic
-from gpu_util import rel_fro, run_forward
+from gpu_util import rel_fro, run_dressed, run_forward
 
 pytestmark = pytest.mark.gpu
 
@@ -67,3 +69,44 @@ def test_full_size_against_stored_oracle(lad, name, mode):
         assert dE <= 1e-6
     # the ladder term keeps the pair symmetry R_ij^ab = R_ji^ba exactly
     assert np.array_equal(R, R.transpose(1, 0, 3, 2))
+
+
+@pytest.mark.parametrize("name", ["mid_o34_v400_n1600"])
+def test_lambda_only_full_size_against_stored_oracle(lad, name):
+    """The lambda-only ablation at the bench workload, against the same values."""
+    g = _golden(name)
+    w = synthetic.WORKLOADS[name]
+    x = synthetic.make_inputs(w.o, w.v, w.naux, w.seed)
+    L = lad.Ladder(w.o, w.v, w.naux, mode="bf16x6", tuning={"two_pass": 1, "lambda_only": 1})
+    _, R, E = run_forward(L, x)
+    L.close()
+    got = np.stack([R[:, :, a, b] for a, b in zip(g["pairs_a"], g["pairs_b"])])
+    e_cols = rel_fro(got, np.asarray(g["R_cols"]))
+    e_fro = abs(float(np.linalg.norm(R)) - g["R_fro"]) / g["R_fro"]
+    print("%s lambda-only bf16x6: columns rel-F %.3e  |R|_F rel %.3e  dE_L %.3e" % (
+        name, e_cols, e_fro, abs(E - g["E_L"])))
+    assert e_cols < TOL["bf16x6"]
+    assert e_fro < TOL["bf16x6"]
+
+
+DRESSED_CASES = [("grad_o16_v200_n800", m) for m in ("fp64", "bf16x6")] + \
+                [("mid_o34_v400_n1600", m) for m in ("bf16x6", "fp64")]
+
+
+@pytest.mark.parametrize("name,mode", DRESSED_CASES)
+def test_dressed_full_size_against_stored_oracle(lad, name, mode):
+    g = _golden(name + "_dressed")
+    w = synthetic.WORKLOADS[name]
+    assert (g["o"], g["v"], g["naux"], g["seed"]) == (w.o, w.v, w.naux, w.seed)
+    x = synthetic.make_inputs(w.o, w.v, w.naux, w.seed)
+    L = lad.Ladder(w.o, w.v, w.naux, mode=mode, dressed=True)
+    _, R, _ = run_dressed(L, x)
+    L.close()
+    got = np.stack([R[:, :, a, b] for a, b in zip(g["pairs_a"], g["pairs_b"])])
+    e_cols = rel_fro(got, np.asarray(g["R_cols"]))
+    asym = float(np.abs(R - R.transpose(1, 0, 3, 2)).max() / np.abs(R).max())
+    print("%s dressed %s: columns rel-F %.3e  pair asymmetry %.1e" % (name, mode, e_cols, asym))
+    assert e_cols < TOL[mode]
+    # the ladder part is mirrored exactly; the correction is summed per (i,j)
+    # in its own order, so R_ij^ab = R_ji^ba holds to rounding
+    assert asym < 1e-9
