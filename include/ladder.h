@@ -199,6 +199,14 @@ ladder_status ladder_apply_host(ladder_plan_t plan, const double *B_host, const 
  * ladder_energy_noalloc gives the energy of each molecule. */
 ladder_status ladder_plan_batched(int n, const int *o, const int *v, const int *naux, int mode,
                                   ladder_plan_t *out);
+/* Launch parameters of member m of a batch plan (0 <= m < n), before
+ * ladder_set_workspace: kc, s_pieces, flush_every, xy_split and two_pass as in
+ * ladder_tuning (ksplit is the plan's own; lambda_only must be 0).  A member
+ * moved to the two-pass form must keep the batch's stored tiles within the
+ * batch cap (else LADDER_ENOTSUP).  The autotuner's per-shape choices are
+ * applied to a batch through this call. */
+ladder_status ladder_set_member_tuning(ladder_plan_t plan, int m, const ladder_tuning *t);
+
 /* B[k], tau[k], R[k] are device pointers for molecule k (host arrays of n
  * pointers).  The first call with a given set of pointers records the whole
  * batch (operand preparation of every molecule, the fused, storing and GEMM2

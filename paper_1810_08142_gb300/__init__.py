@@ -28,7 +28,7 @@ STATUS = {0: "LADDER_OK", 1: "LADDER_EINVAL", 2: "LADDER_ENOMEM", 3: "LADDER_ECU
 # every entry point that include/ladder.h declares
 EXPORTS = ("ladder_plan", "ladder_plan_mode", "ladder_get_tuning", "ladder_set_tuning", "ladder_workspace_size", "ladder_set_workspace",
            "ladder_tau", "ladder_apply", "ladder_apply_dressed", "ladder_energy", "ladder_energy_noalloc", "ladder_backward", "ladder_pair_combine", "ladder_apply_host",
-           "ladder_plan_batched", "ladder_apply_batched", "ladder_last_device_error", "ladder_selftest_wait",
+           "ladder_plan_batched", "ladder_set_member_tuning", "ladder_apply_batched", "ladder_last_device_error", "ladder_selftest_wait",
            "ladder_set_timing", "ladder_timing", "ladder_timing_passes", "ladder_timing_dressing", "ladder_flops", "ladder_status_string",
            "ladder_destroy")
 
@@ -79,6 +79,7 @@ def load_library(path: str = LIB_PATH):
         "ladder_pair_combine": [i, i, ctypes.c_double, ctypes.c_double, _P, _P, _P],
         "ladder_apply_host": [_P, _P, _P, _P, _P, _P, _P, _P],
         "ladder_plan_batched": [i, ip, ip, ip, i, pp],
+        "ladder_set_member_tuning": [_P, i, ctypes.POINTER(Tuning)],
         "ladder_apply_batched": [_P, pp, pp, pp, _P],
         "ladder_last_device_error": [_P, _P, ip],
         "ladder_selftest_wait": [_P, ctypes.c_ulonglong, _P],
@@ -201,6 +202,10 @@ def ladder_plan_batched(o, v, naux, mode: int) -> ctypes.c_void_p:
     _check("ladder_plan_batched",
            load_library().ladder_plan_batched(n, arr(o), arr(v), arr(naux), mode, ctypes.byref(h)))
     return h
+
+
+def ladder_set_member_tuning(plan, m: int, t: Tuning) -> None:
+    _check("ladder_set_member_tuning", load_library().ladder_set_member_tuning(plan, m, ctypes.byref(t)))
 
 
 def ladder_apply_batched(plan, Bs, taus, Rs, stream=None) -> None:
@@ -362,14 +367,42 @@ class LadderBatch:
     all molecules' work units, fused or two-pass per molecule, replayed as a
     CUDA graph) plus its workspace."""
 
-    def __init__(self, shapes, mode="bf16x6", device=None):
+    def __init__(self, shapes, mode="bf16x6", device=None, tunings=None):
+        """mode: "bf16x3", "bf16x6", or "tuned" (BF16X6 with each member's
+        launch parameters and form from the autotuner's cache, see tune.py);
+        tunings: optional list of per-member dicts of ladder_tuning fields
+        (None entries keep the plan's choice)."""
         import torch
         self.shapes = [(int(o), int(v), int(n)) for o, v, n in shapes]
+        if mode == "tuned":
+            from .tune import lookup
+            mode = "bf16x6"
+            tunings = []
+            for o, v, n in self.shapes:
+                mm, tun = lookup(o, v, n)
+                tunings.append(tun if mm == mode else None)
         m = MODES[mode] if isinstance(mode, str) else int(mode)
         self.device = torch.device(device if device is not None else "cuda")
+        self.tunings = []
         with torch.cuda.device(self.device):
             self.plan = ladder_plan_batched([s[0] for s in self.shapes], [s[1] for s in self.shapes],
                                             [s[2] for s in self.shapes], m)
+            for k, tun in enumerate(tunings or []):
+                if not tun:
+                    self.tunings.append(None)
+                    continue
+                t = Tuning(kc=4, s_pieces=2, flush_every=16, ksplit=0, xy_split=1, two_pass=0, lambda_only=0)
+                for key, val in tun.items():
+                    if key in ("kc", "s_pieces", "flush_every", "xy_split", "two_pass"):
+                        setattr(t, key, int(val))
+                try:
+                    ladder_set_member_tuning(self.plan, k, t)
+                    self.tunings.append(t.as_dict())
+                except LadderError:
+                    # the two-pass form would overflow the batch's tile cap: keep the plan's form
+                    t.two_pass = 0
+                    ladder_set_member_tuning(self.plan, k, t)
+                    self.tunings.append(t.as_dict())
             n = ladder_workspace_size(self.plan)
             self.workspace = torch.empty(max(n, 256), dtype=torch.uint8, device=self.device)
             ladder_set_workspace(self.plan, self.workspace)

@@ -1148,50 +1148,26 @@ ladder_status ladder_apply_host(ladder_plan_t pl, const double *B_host, const do
 // it use the fused form).
 constexpr double kVStoreBatchCap = 128.0 * (1ull << 30);
 
-ladder_status ladder_plan_batched(int n, const int *o, const int *v, const int *naux, int mode,
-                                  ladder_plan_t *out) {
-  if (!out || n < 1 || n > 4096 || !o || !v || !naux) return LADDER_EINVAL;
-  *out = nullptr;
-  if (mode & LADDER_WITH_BACKWARD) return LADDER_ENOTSUP;
-  if (mode == LADDER_AUTO) mode = LADDER_BF16X6;
-  if (mode != LADDER_BF16X3 && mode != LADDER_BF16X6) return LADDER_ENOTSUP;
-  ladder_plan_s *pl = new (std::nothrow) ladder_plan_s();
-  if (!pl) return LADDER_ENOMEM;
-  pl->batched = true;
-  pl->mode = mode;
-  pl->S = tc_slices(mode);
+// (Re)builds a batch plan's work lists and workspace layout from its
+// members' current forms: fused members' work units cost-sorted, largest
+// first; two-pass members largest first, each in its own range-major order.
+static void batch_finalize(ladder_plan_s *pl) {
   struct Unit {
     double cost;
     int m, k;
   };
   std::vector<Unit> units;
   std::vector<std::pair<double, int>> twopass;  // (flops, molecule)
-  const char *tp_env = getenv("LADDER_TWOPASS");
-  double vsum = 0.0;
+  pl->items.clear();
+  pl->tcs.clear();
+  pl->items1.clear();
+  pl->items2.clear();
+  pl->tcs2.clear();
+  pl->sub_off.clear();
+  const int n = (int)pl->subs.size();
   for (int m = 0; m < n; ++m) {
-    ladder_plan_s *sp = new (std::nothrow) ladder_plan_s();
-    if (!sp) {
-      ladder_destroy(pl);
-      return LADDER_ENOMEM;
-    }
-    pl->subs.push_back(sp);
-    const ladder_status st = init_plan(sp, o[m], v[m], naux[m], mode, false, true);
-    if (st != LADDER_OK) {
-      ladder_destroy(pl);
-      return st;
-    }
-    pl->device = sp->device;
-    pl->sm_count = sp->sm_count;
-    // members whose fused form would recompute GEMM1 per chunk take the
-    // two-pass form while the batch's stored tiles fit the cap
-    const double vb = (double)sp->ntiles_tc * sp->nbp * 2 * sp->S * 128 * SLOTS * 2;
-    // LADDER_TWOPASS=1 puts every member that fits in the two-pass form, 0 none
-    bool tp = (tp_env ? atoi(tp_env) != 0 : sp->chunks_tc.size() > 1) && vsum + vb <= kVStoreBatchCap;
-    if (tp) {
-      vsum += vb;
-      sp->two_pass = 1;
-      sp->ksplit = std::max(1, std::min(sp->nbp, sp->nbp / 160));
-      compute_layout(sp);
+    ladder_plan_s *sp = pl->subs[m];
+    if (sp->two_pass) {
       twopass.push_back({ladder_flops(sp), m});
       continue;
     }
@@ -1207,8 +1183,6 @@ ladder_status ladder_plan_batched(int n, const int *o, const int *v, const int *
   std::stable_sort(units.begin(), units.end(),
                    [](const Unit &x, const Unit &y) { return x.cost > y.cost; });
   for (auto &u : units) pl->items.push_back(make_int2(u.m, u.k));
-  // two-pass members, largest first: every work unit of a member in its own
-  // (range-major) order
   std::stable_sort(twopass.begin(), twopass.end(),
                    [](const std::pair<double, int> &x, const std::pair<double, int> &y) {
                      return x.first > y.first;
@@ -1241,7 +1215,83 @@ ladder_status ladder_plan_batched(int n, const int *o, const int *v, const int *
     off += sp->lay.total;
   }
   pl->lay.total = align_up(off);
+}
+
+// Stored V+- bytes of a member in the two-pass form.
+static double member_vbytes(const ladder_plan_s *sp) {
+  return (double)sp->ntiles_tc * sp->nbp * 2 * sp->S * 128 * SLOTS * 2;
+}
+
+// A member's form: the two-pass form keeps block-pair ranges of about 160
+// for its GEMM2 units; a fused member runs whole tiles.
+static void set_member_form(ladder_plan_s *sp, bool two_pass) {
+  sp->two_pass = two_pass ? 1 : 0;
+  sp->ksplit = two_pass ? std::max(1, std::min(sp->nbp, sp->nbp / 160)) : 1;
+  compute_layout(sp);
+}
+
+ladder_status ladder_plan_batched(int n, const int *o, const int *v, const int *naux, int mode,
+                                  ladder_plan_t *out) {
+  if (!out || n < 1 || n > 4096 || !o || !v || !naux) return LADDER_EINVAL;
+  *out = nullptr;
+  if (mode & LADDER_WITH_BACKWARD) return LADDER_ENOTSUP;
+  if (mode == LADDER_AUTO) mode = LADDER_BF16X6;
+  if (mode != LADDER_BF16X3 && mode != LADDER_BF16X6) return LADDER_ENOTSUP;
+  ladder_plan_s *pl = new (std::nothrow) ladder_plan_s();
+  if (!pl) return LADDER_ENOMEM;
+  pl->batched = true;
+  pl->mode = mode;
+  pl->S = tc_slices(mode);
+  const char *tp_env = getenv("LADDER_TWOPASS");
+  double vsum = 0.0;
+  for (int m = 0; m < n; ++m) {
+    ladder_plan_s *sp = new (std::nothrow) ladder_plan_s();
+    if (!sp) {
+      ladder_destroy(pl);
+      return LADDER_ENOMEM;
+    }
+    pl->subs.push_back(sp);
+    const ladder_status st = init_plan(sp, o[m], v[m], naux[m], mode, false, true);
+    if (st != LADDER_OK) {
+      ladder_destroy(pl);
+      return st;
+    }
+    pl->device = sp->device;
+    pl->sm_count = sp->sm_count;
+    // members whose fused form would recompute GEMM1 per chunk take the
+    // two-pass form while the batch's stored tiles fit the cap
+    const double vb = member_vbytes(sp);
+    // LADDER_TWOPASS=1 puts every member that fits in the two-pass form, 0 none
+    const bool tp = (tp_env ? atoi(tp_env) != 0 : sp->chunks_tc.size() > 1) && vsum + vb <= kVStoreBatchCap;
+    if (tp) {
+      vsum += vb;
+      set_member_form(sp, true);
+    }
+  }
+  batch_finalize(pl);
   *out = pl;
+  return LADDER_OK;
+}
+
+ladder_status ladder_set_member_tuning(ladder_plan_t pl, int m, const ladder_tuning *t) {
+  if (!pl || !t || !pl->batched || pl->ws || m < 0 || m >= (int)pl->subs.size()) return LADDER_EINVAL;
+  if (t->kc < 1 || t->kc > 64 || !(t->s_pieces == 1 || t->s_pieces == 2 || t->s_pieces == 4) ||
+      t->flush_every < 1 || t->flush_every > 4096 || (t->xy_split != 0 && t->xy_split != 1) ||
+      (t->two_pass != 0 && t->two_pass != 1) || t->lambda_only != 0)
+    return LADDER_EINVAL;
+  ladder_plan_s *sp = pl->subs[m];
+  if (t->two_pass && !sp->two_pass) {
+    double vsum = member_vbytes(sp);
+    for (auto *q : pl->subs)
+      if (q->two_pass) vsum += member_vbytes(q);
+    if (vsum > kVStoreBatchCap) return LADDER_ENOTSUP;
+  }
+  sp->kc = t->kc;
+  sp->s_pieces = t->s_pieces;
+  sp->flush_every = t->flush_every;
+  sp->xy_split = t->xy_split;
+  set_member_form(sp, t->two_pass != 0);
+  batch_finalize(pl);
   return LADDER_OK;
 }
 

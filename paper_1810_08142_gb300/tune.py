@@ -147,14 +147,20 @@ def tune(o: int, v: int, naux: int, tol: float = 1e-6, reps: int = 2, seed: int 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("o", type=int)
-    ap.add_argument("v", type=int)
-    ap.add_argument("naux", type=int)
+    ap.add_argument("o", type=int, nargs="?")
+    ap.add_argument("v", type=int, nargs="?")
+    ap.add_argument("naux", type=int, nargs="?")
+    ap.add_argument("--shapes", default="",
+                    help="several shapes at once: 'o,v,naux o,v,naux ...'")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--reps", type=int, default=2)
     a = ap.parse_args()
-    e = tune(a.o, a.v, a.naux, tol=a.tol, reps=a.reps)
-    print(json.dumps(e))
+    shapes = [tuple(int(x) for x in t.split(",")) for t in a.shapes.split()]
+    if a.o is not None:
+        shapes.insert(0, (a.o, a.v, a.naux))
+    for o, v, n in shapes:
+        e = tune(o, v, n, tol=a.tol, reps=a.reps, verbose=len(shapes) == 1)
+        print(json.dumps({"shape": [o, v, n], **e}), flush=True)
 
 
 if __name__ == "__main__":

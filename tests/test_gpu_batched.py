@@ -113,3 +113,46 @@ def test_batch_with_two_pass_members(lad):
         Rs = L.apply(Bs_d[k], taus_d[k]).cpu().numpy()
         assert np.array_equal(Rs, R[k])
         L.close()
+
+
+def test_batch_member_tunings(lad):
+    """Per-member launch parameters and forms (what the autotuner's per-shape
+    choices set): every member against the oracle, and a two-pass member
+    bitwise against its single-molecule launch in the same form and split."""
+    import torch
+    tunings = [{"kc": 2, "s_pieces": 1, "two_pass": 1}, {"kc": 8, "s_pieces": 2, "two_pass": 0},
+               {"kc": 4, "s_pieces": 4, "two_pass": 1}, {"kc": 1, "s_pieces": 2, "two_pass": 0},
+               None, {"kc": 4, "s_pieces": 2, "two_pass": 1}]
+    mols = [synthetic.make_inputs(o, v, n, s) for o, v, n, s in SHAPES]
+    taus = [oracle.tau(x.t1, x.t2) for x in mols]
+    Bs_d = [to_dev(x.B) for x in mols]
+    taus_d = [to_dev(t) for t in taus]
+    batch = lad.LadderBatch([(x.o, x.v, x.naux) for x in mols], mode="bf16x6", tunings=tunings)
+    R = [r.cpu().numpy() for r in batch.apply(Bs_d, taus_d)]
+    torch.cuda.synchronize()
+    batch.check_device()
+    for k, x in enumerate(mols):
+        err = rel_fro(R[k], oracle.ladder(x.B, taus[k]))
+        print("member %d %s: rel-F %.3e" % (k, tunings[k], err))
+        assert err < TOL["bf16x6"]
+    # member 0 (two-pass, kc 2, one piece per S): the batch's storing pass and
+    # GEMM2 pass give the single-molecule launch's bits
+    x = mols[0]
+    L = lad.Ladder(x.o, x.v, x.naux, mode="bf16x6",
+                   tuning={"kc": 2, "s_pieces": 1, "two_pass": 1, "ksplit": 1})
+    Rs = L.apply(Bs_d[0], taus_d[0]).cpu().numpy()
+    assert np.array_equal(Rs, R[0])
+
+
+def test_batch_tuned_mode(lad):
+    """mode="tuned": each member's choices from the autotuner's cache."""
+    import torch
+    mols = [synthetic.make_inputs(o, v, n, s) for o, v, n, s in SHAPES]
+    taus = [oracle.tau(x.t1, x.t2) for x in mols]
+    batch = lad.LadderBatch([(x.o, x.v, x.naux) for x in mols], mode="tuned")
+    assert len(batch.tunings) == len(mols)
+    R = batch.apply([to_dev(x.B) for x in mols], [to_dev(t) for t in taus])
+    torch.cuda.synchronize()
+    batch.check_device()
+    for k, x in enumerate(mols):
+        assert rel_fro(R[k].cpu().numpy(), oracle.ladder(x.B, taus[k])) < TOL["bf16x6"]
