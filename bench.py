@@ -231,7 +231,6 @@ def run_ragged(args):
 # A configuration not listed here reports traffic null.
 TRAFFIC = {
     ("mid_o34_v400_n1600", "bf16x6", "pass1", (4, 2, 7)): 701.48e9 + 81.47e9,
-    ("mid_o34_v400_n1600", "bf16x6", "pass2", (4, 2, 7)): 444.50e9 + 70.53e9,
 }
 
 
@@ -316,6 +315,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tuning", default="",
+                    help="override launch parameters of the timed plan: key=value,... (ladder_tuning fields)")
     ap.add_argument("--lambda-only", action="store_true",
                     help="also time the paper's lambda-only contraction (ablation of the +- split)")
     ap.add_argument("--dressed", action="store_true",
@@ -357,6 +358,10 @@ def main():
     tuning = tuned_for(w, args.mode)
     if args.form != "auto" and args.mode != "fp64":
         tuning = dict(tuning or {}, two_pass=int(args.form == "two-pass"), ksplit=0)
+    if args.tuning and args.mode != "fp64":
+        # explicit overrides, e.g. --tuning flush_every=32,kc=8
+        tuning = dict(tuning or {}, **{k: int(v) for k, v in
+                                      (kv.split("=") for kv in args.tuning.split(","))})
     L = lad.Ladder(w.o, w.v, w.naux, mode=args.mode, device=dev, tuning=tuning)
     lad.ladder_set_timing(L.plan, True)
 

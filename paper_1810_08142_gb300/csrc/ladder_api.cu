@@ -90,7 +90,7 @@ struct ladder_plan_s {
   std::vector<Chunk> chunks64;
   int grid64 = 0;
   // split-BF16 tensor-core path
-  int S = 0, ksplit = 1, kc = 4, s_pieces = 4, flush_every = 16, xy_split = 1, ntiles_tc = 0, racc_cols = 0;
+  int S = 0, ksplit = 1, kc = 4, s_pieces = 4, flush_every = 64, xy_split = 1, ntiles_tc = 0, racc_cols = 0;
   std::vector<TcChunk> chunks_tc;
   // two-pass form: GEMM2 chunks (up to kTcMaxColsV columns), block-pair
   // ranges per tile of the storing pass
@@ -550,7 +550,11 @@ static ladder_status init_plan(ladder_plan_s *pl, int o, int v, int naux, int mo
     pl->s_pieces = pl->S == 2 ? 4 : 2;
     if (const char *e = getenv("LADDER_XYSPLIT")) pl->xy_split = atoi(e) != 0;
     if (!pl->xy_split) pl->kc = pl->S == 2 ? 4 : 1;
-    pl->flush_every = 16;
+    // GEMM2's FP32 running sum R takes flush_every S accumulators before a
+    // flush into the double-single sums.  At o=34, v=400 (BF16X6, two-pass)
+    // flushing every 16 / 32 / 64 / 128 S gave pass 2 113 / 101 / 94 / 91 ms
+    // and R errors 5.05 / 5.07 / 5.08 / 5.29e-7: 64 keeps the error.
+    pl->flush_every = 64;
     if (const char *e = getenv("LADDER_KC")) pl->kc = std::max(1, atoi(e));
     if (const char *e = getenv("LADDER_SPIECES")) {
       const int sp = atoi(e);

@@ -64,10 +64,13 @@ def candidates(forms=(0,)):
     for tp in forms:
         for kc in (16, 32):
             out.append(("bf16x3", {"kc": kc, "s_pieces": 4, "xy_split": 1, "two_pass": tp}))
-        # the two-pass form keeps S double-buffered, so longer S chains pay off there
+        # the two-pass form keeps S double-buffered, so longer S chains pay off there;
+        # its GEMM2 flushes cost time, so the flush interval is a candidate too
         for kc in ((4, 8) if tp else (2, 4, 8)):
-            for sp in ((1, 2, 4) if tp else (1, 2)):
-                out.append(("bf16x6", {"kc": kc, "s_pieces": sp, "xy_split": 1, "two_pass": tp}))
+            for sp in ((1, 2) if tp else (1, 2)):
+                for fe in ((16, 64, 128) if tp else (64,)):
+                    out.append(("bf16x6", {"kc": kc, "s_pieces": sp, "flush_every": fe, "xy_split": 1,
+                                           "two_pass": tp}))
     return out
 
 
