@@ -230,7 +230,8 @@ def run_ragged(args):
 # on the same workload and tuning (profiles/dram_traffic_mid_o34_v400_n1600_bf16x6.md).
 # A configuration not listed here reports traffic null.
 TRAFFIC = {
-    ("mid_o34_v400_n1600", "bf16x6", "pass1", (4, 2, 7)): 701.48e9 + 81.47e9,
+    ("mid_o34_v400_n1600", "bf16x6", "pass1", (4, 2, 7, 128)): 705.02e9 + 81.46e9,
+    ("mid_o34_v400_n1600", "bf16x6", "pass2", (4, 2, 7, 128)): 278.50e9 + 11.65e9,
 }
 
 
@@ -428,7 +429,8 @@ def main():
                                         pass1_ms, "pass1")
         else:
             kname, kflops, kms, kkey = "ladder_gemm2_kernel<%d> (GEMM2 from stored V)" % nS, F - F1, pass2_ms, "pass2"
-        traffic = TRAFFIC.get((args.workload, args.mode, kkey, (tun["kc"], tun["s_pieces"], tun["ksplit"])))
+        traffic = TRAFFIC.get((args.workload, args.mode, kkey,
+                               (tun["kc"], tun["s_pieces"], tun["ksplit"], tun["flush_every"])))
         achieved = prod * kflops / (kms * 1e-3) / 1e12
         peak = pk["bf16_tflops_sustained"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
