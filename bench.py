@@ -11,11 +11,12 @@ v=400, N_aux=1600).  The other form, BF16X3 and the FP64 path are timed on the
 same workload and reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--dressed] [--lambda-only]
+                    [--dressed] [--lambda-only] [--backward] [--tuning k=v,...]
 
---dressed also times the t1-dressed term (Eq. pp-Ladder-2) and --lambda-only
-the paper's lambda-only contraction (the ablation of the +- split), one step
-each on the same workload, under "others".
+--dressed also times the t1-dressed term (Eq. pp-Ladder-2), --lambda-only
+the paper's lambda-only contraction (the ablation of the +- split) and
+--backward the adjoint (dE/dtau, dE/dB), one step each on the same workload,
+under "others"; --tuning overrides the timed plan's launch parameters.
 
 Under torchrun each rank runs its own replica of the workload on its own GPU
 (the ladder term of one molecule is one GPU's work); value = all ranks' flops
@@ -320,6 +321,8 @@ def main():
                     help="override launch parameters of the timed plan: key=value,... (ladder_tuning fields)")
     ap.add_argument("--lambda-only", action="store_true",
                     help="also time the paper's lambda-only contraction (ablation of the +- split)")
+    ap.add_argument("--backward", action="store_true",
+                    help="also time the adjoint (dE/dtau and dE/dB for W = 2t - t^T) on the same workload")
     ap.add_argument("--dressed", action="store_true",
                     help="also time the t1-dressed term (Eq. pp-Ladder-2) on the same workload")
     ap.add_argument("--form", default="auto", choices=["auto", "fused", "two-pass"],
@@ -517,6 +520,29 @@ def main():
         torch.cuda.empty_cache()
     if "fp64" in extra:
         extra["speedup_vs_fp64"] = extra["fp64"]["ms_per_step"] / ms
+    if args.backward and args.mode != "fp64":
+        # the adjoint of E_L in the same mode and tuning: dE/dtau (the
+        # transposed ladder) and dE/dB (Gamma stored once, then contracted)
+        Lb = lad.Ladder(w.o, w.v, w.naux, mode=args.mode, device=dev, tuning=tun, backward=True)
+        Wt = Lb.weights(t2)
+        dt, db = torch.empty_like(tau), torch.empty_like(B)
+        bw = {}
+        for name, a, b in (("dtau", dt, None), ("dB", None, db), ("both", dt, db)):
+            lad.ladder_backward(Lb.plan, B, tau, Wt, a, b)  # warm-up
+            torch.cuda.synchronize()
+            b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            b0.record(stream)
+            lad.ladder_backward(Lb.plan, B, tau, Wt, a, b)
+            b1.record(stream)
+            torch.cuda.synchronize()
+            bw[name + "_ms"] = b0.elapsed_time(b1)
+        Lb.check_device()
+        bw["dtau_tflops"] = F / (bw["dtau_ms"] * 1e-3) / 1e12
+        bw["note"] = "dtau_tflops counts F_alg (the transposed ladder has the forward's flops)"
+        extra["backward"] = bw
+        Lb.close()
+        del Lb
+        torch.cuda.empty_cache()
 
     # end to end through the public API with host buffers: every step copies
     # its inputs from pinned host memory and reads E_L back.  The device
