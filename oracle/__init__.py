@@ -14,6 +14,9 @@ Functions and the passages they follow (arxiv 1810.08142):
   ladder_dressed   Eq. pp-Ladder-0 with the t1-dressed integrals of Eq. pp-Ladder-2
                    and Eq. pp-Ladder-21 (v^{kb}_{cd} from the same RI factors)
   ladder_dressed_pairs  selected (a,b) columns of the same
+  triples          the perturbative triples energy E(T) of Sec. II.A (W, V, D as
+                   printed there; integrals from the RI factors)
+  triples_wv       W_ijk^abc and V_ijk^abc of one (i,j,k)
   grad_tau, grad_B and their *_entries variants: derivatives of
                    sum W_ij^ab R_ij^ab, written out term by term.
 Every function is pinned by tests/test_oracle_pins.py.
@@ -69,6 +72,10 @@ def _load():
         lib.oracle_ladder_dressed_pairs.argtypes = [ctypes.c_int] * 3 + [_D] * 4 + [
             ctypes.c_int, _I, _I, _D]
         lib.oracle_ladder_dressed_pairs.restype = ctypes.c_int
+        lib.oracle_triples.argtypes = [ctypes.c_int] * 3 + [_D] * 7
+        lib.oracle_triples.restype = ctypes.c_double
+        lib.oracle_triples_wv.argtypes = [ctypes.c_int] * 3 + [_D] * 5 + [ctypes.c_int] * 3 + [_D, _D]
+        lib.oracle_triples_wv.restype = ctypes.c_int
         lib.oracle_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -236,3 +243,33 @@ def ladder_dressed_pairs(B, B_ov, t1, tau_, pa, pb):
                                            out.ctypes.data_as(_D)) != 0:
         raise MemoryError("oracle_ladder_dressed_pairs")
     return out
+
+
+def _triples_args(B, B_ov, B_oo, t1, t2):
+    n, v = _shape_B(B)
+    o = t1.shape[0]
+    assert B_ov.shape == (n, o, v) and B_oo.shape == (n, o, o) and t2.shape == (o, o, v, v)
+    arrs = [_d(x) for x in (B, B_ov, B_oo, t1, t2)]
+    return o, v, n, arrs
+
+
+def triples(B, B_ov, B_oo, t1, t2, e_occ, e_vir):
+    """E(T) (Sec. II.A) for the given amplitudes, factors and orbital energies."""
+    o, v, n, arrs = _triples_args(B, B_ov, B_oo, t1, t2)
+    eo, peo = _d(e_occ)
+    ev, pev = _d(e_vir)
+    E = float(_load().oracle_triples(o, v, n, *[p for _, p in arrs], peo, pev))
+    if E != E:
+        raise MemoryError("oracle_triples")
+    return E
+
+
+def triples_wv(B, B_ov, B_oo, t1, t2, i, j, k):
+    """(W, V) of the triple (i, j, k), each [v][v][v] indexed [a][b][c]."""
+    o, v, n, arrs = _triples_args(B, B_ov, B_oo, t1, t2)
+    W = np.empty((v, v, v))
+    V = np.empty((v, v, v))
+    if _load().oracle_triples_wv(o, v, n, *[p for _, p in arrs], int(i), int(j), int(k),
+                                 W.ctypes.data_as(_D), V.ctypes.data_as(_D)) != 0:
+        raise MemoryError("oracle_triples_wv")
+    return W, V

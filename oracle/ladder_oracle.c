@@ -431,6 +431,183 @@ int oracle_ladder_dressed_pairs(int o, int v, int n, const double *B, const doub
     return 0;
 }
 
+/* ---------------------------------------------------------------------------
+ * Perturbative triples, closed shell (Sec. II.A, the (T) energy):
+ *
+ *   E(T) = sum_ijk sum_abc (4 W_ijk^abc + W_ijk^bca + W_ijk^cab)
+ *                          (V_ijk^abc - V_ijk^cba) / (3 D_ijk^abc)
+ *   W_ijk^abc = P_ijk^abc ( sum_d v_di^ba t_kj^cd - sum_l v_kl^cj t_il^ab )
+ *   V_ijk^abc = W_ijk^abc + v_jk^bc t_i^a + v_ik^ac t_j^b + v_ij^ab t_k^c
+ *   D_ijk^abc = e_i + e_j + e_k - e_a - e_b - e_c
+ *
+ * with P_ijk^abc f(ijk,abc) = f(ijk,abc) + f(ikj,acb) + f(kij,cab) +
+ * f(kji,cba) + f(jki,bca) + f(jik,bac), and the integrals v^{pq}_{rs} =
+ * (pr|qs) = sum_P m^P_pr m^P_qs (Eq. eri under Eq. RIM) from the RI factors
+ * of the orbital pairs: Bvv[P][a][c] = m^P_ac, Bov[P][i][a] = m^P_ia = m^P_ai
+ * (real orbitals), Boo[P][k][l] = m^P_kl.  The three kinds used:
+ *   v_di^ba = (bd|ai),  v_kl^cj = (ck|jl),  v_jk^bc = (bj|ck).
+ * Extra arrays: Boo [n][o][o], e_occ [o], e_vir [v].
+ * ------------------------------------------------------------------------- */
+#define IDX3OO(P, k, l, o) (((size_t)(P) * (o) + (k)) * (o) + (l))
+
+typedef struct {
+    int o, v;
+    double *ovvv;  /* [i][d][b][a] = v_di^ba = (bd|ai) */
+    double *ooov;  /* [k][l][c][j] = v_kl^cj = (ck|jl) */
+    double *oovv;  /* [j][k][b][c] = v_jk^bc = (bj|ck) */
+} TriplesInts;
+
+static int triples_integrals(int o, int v, int n, const double *Bvv, const double *Bov,
+                             const double *Boo, TriplesInts *I)
+{
+    I->o = o;
+    I->v = v;
+    I->ovvv = (double *)malloc(sizeof(double) * (size_t)o * v * v * v);
+    I->ooov = (double *)malloc(sizeof(double) * (size_t)o * o * o * v);
+    I->oovv = (double *)malloc(sizeof(double) * (size_t)o * o * v * v);
+    if (!I->ovvv || !I->ooov || !I->oovv) return -1;
+    #pragma omp parallel for schedule(dynamic)
+    for (int id = 0; id < o * v; ++id) {
+        const int i = id / v, d = id % v;
+        for (int b = 0; b < v; ++b)
+            for (int a = 0; a < v; ++a) {
+                double s = 0.0;
+                for (int P = 0; P < n; ++P)
+                    s += Bvv[IDX3(P, b, d, v)] * Bov[IDX3O(P, i, a, o, v)];
+                I->ovvv[(((size_t)i * v + d) * v + b) * v + a] = s;
+            }
+    }
+    for (int k = 0; k < o; ++k)
+        for (int l = 0; l < o; ++l)
+            for (int c = 0; c < v; ++c)
+                for (int j = 0; j < o; ++j) {
+                    double s = 0.0;
+                    for (int P = 0; P < n; ++P)
+                        s += Bov[IDX3O(P, k, c, o, v)] * Boo[IDX3OO(P, j, l, o)];
+                    I->ooov[(((size_t)k * o + l) * v + c) * o + j] = s;
+                }
+    for (int j = 0; j < o; ++j)
+        for (int k = 0; k < o; ++k)
+            for (int b = 0; b < v; ++b)
+                for (int c = 0; c < v; ++c) {
+                    double s = 0.0;
+                    for (int P = 0; P < n; ++P)
+                        s += Bov[IDX3O(P, j, b, o, v)] * Bov[IDX3O(P, k, c, o, v)];
+                    I->oovv[(((size_t)j * o + k) * v + b) * v + c] = s;
+                }
+    return 0;
+}
+
+static void triples_free(TriplesInts *I)
+{
+    free(I->ovvv);
+    free(I->ooov);
+    free(I->oovv);
+}
+
+/* The unsymmetrised term sum_d v_di^ba t_kj^cd - sum_l v_kl^cj t_il^ab. */
+static double triples_raw(const TriplesInts *I, const double *t2, int i, int j, int k, int a,
+                          int b, int c)
+{
+    const int o = I->o, v = I->v;
+    double s = 0.0;
+    for (int d = 0; d < v; ++d)
+        s += I->ovvv[(((size_t)i * v + d) * v + b) * v + a] * t2[IDX4(k, j, c, d, o, v)];
+    for (int l = 0; l < o; ++l)
+        s -= I->ooov[(((size_t)k * o + l) * v + c) * o + j] * t2[IDX4(i, l, a, b, o, v)];
+    return s;
+}
+
+/* W_ijk^abc and V_ijk^abc for one (i,j,k), every (a,b,c): W[a][b][c], V[a][b][c]. */
+static void triples_wv(const TriplesInts *I, const double *t1, const double *t2, int i, int j,
+                       int k, double *W, double *V)
+{
+    const int o = I->o, v = I->v;
+    for (int a = 0; a < v; ++a)
+        for (int b = 0; b < v; ++b)
+            for (int c = 0; c < v; ++c) {
+                const double w = triples_raw(I, t2, i, j, k, a, b, c) +
+                                 triples_raw(I, t2, i, k, j, a, c, b) +
+                                 triples_raw(I, t2, k, i, j, c, a, b) +
+                                 triples_raw(I, t2, k, j, i, c, b, a) +
+                                 triples_raw(I, t2, j, k, i, b, c, a) +
+                                 triples_raw(I, t2, j, i, k, b, a, c);
+                const size_t e = ((size_t)a * v + b) * v + c;
+                W[e] = w;
+                V[e] = w + I->oovv[(((size_t)j * o + k) * v + b) * v + c] * t1[(size_t)i * v + a] +
+                       I->oovv[(((size_t)i * o + k) * v + a) * v + c] * t1[(size_t)j * v + b] +
+                       I->oovv[(((size_t)i * o + j) * v + a) * v + b] * t1[(size_t)k * v + c];
+            }
+}
+
+/* W and V of one triple (i,j,k), for the tests.  Returns -1 on allocation failure. */
+int oracle_triples_wv(int o, int v, int n, const double *Bvv, const double *Bov,
+                      const double *Boo, const double *t1, const double *t2, int i, int j, int k,
+                      double *W, double *V)
+{
+    TriplesInts I;
+    if (triples_integrals(o, v, n, Bvv, Bov, Boo, &I) != 0) {
+        triples_free(&I);
+        return -1;
+    }
+    triples_wv(&I, t1, t2, i, j, k, W, V);
+    triples_free(&I);
+    return 0;
+}
+
+/* E(T); per-(i,j,k) sums in index order, the o^3 partial sums added with
+ * Neumaier's compensated summation.  Returns NAN on allocation failure. */
+double oracle_triples(int o, int v, int n, const double *Bvv, const double *Bov,
+                      const double *Boo, const double *t1, const double *t2,
+                      const double *e_occ, const double *e_vir)
+{
+    TriplesInts I;
+    if (triples_integrals(o, v, n, Bvv, Bov, Boo, &I) != 0) {
+        triples_free(&I);
+        return NAN;
+    }
+    double *part = (double *)calloc((size_t)o * o * o, sizeof(double));
+    int bad = part == NULL;
+    #pragma omp parallel
+    {
+        double *W = (double *)malloc(sizeof(double) * (size_t)v * v * v);
+        double *V = (double *)malloc(sizeof(double) * (size_t)v * v * v);
+        if (!W || !V) {
+            #pragma omp atomic write
+            bad = 1;
+        }
+        #pragma omp for schedule(dynamic)
+        for (int ijk = 0; ijk < o * o * o; ++ijk) {
+            if (bad) continue;
+            const int i = ijk / (o * o), j = (ijk / o) % o, k = ijk % o;
+            triples_wv(&I, t1, t2, i, j, k, W, V);
+            double s = 0.0;
+            for (int a = 0; a < v; ++a)
+                for (int b = 0; b < v; ++b)
+                    for (int c = 0; c < v; ++c) {
+                        const double D = e_occ[i] + e_occ[j] + e_occ[k] - e_vir[a] - e_vir[b] - e_vir[c];
+                        const double w = 4.0 * W[((size_t)a * v + b) * v + c] +
+                                         W[((size_t)b * v + c) * v + a] + W[((size_t)c * v + a) * v + b];
+                        const double y = V[((size_t)a * v + b) * v + c] - V[((size_t)c * v + b) * v + a];
+                        s += w * y / (3.0 * D);
+                    }
+            part[ijk] = s;
+        }
+        free(W);
+        free(V);
+    }
+    double s = 0.0, c = 0.0;
+    if (!bad)
+        for (int q = 0; q < o * o * o; ++q) {
+            const double x = part[q], t = s + x;
+            c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
+            s = t;
+        }
+    free(part);
+    triples_free(&I);
+    return bad ? NAN : s + c;
+}
+
 int oracle_threads(void)
 {
 #ifdef _OPENMP

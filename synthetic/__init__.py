@@ -16,8 +16,11 @@ random tensors with the paper's shapes stand in for them):
 * doubles  t2[i,j,a,b] = sum_P B_ov[P,i,a] B_ov[P,j,b] / (e_i + e_j - e_a - e_b),
   then made exactly pair symmetric, t2[i,j,a,b] == t2[j,i,b,a] bit for bit
 * singles  t1[i,a] ~ N(0, 1e-3^2)
+* occupied-occupied factors B_oo[P,k,l] from the same decay law, symmetrised
+  like B (used only by the perturbative triples)
 
-Draw order from ``numpy.random.default_rng(seed)``: e_occ, e_vir, X (vv), X (ov), t1.
+Draw order from ``numpy.random.default_rng(seed)``: e_occ, e_vir, X (vv), X (ov), t1,
+X (oo).  X (oo) is drawn last, so the earlier arrays do not depend on it.
 All arrays are float64 and C-contiguous.
 """
 from __future__ import annotations
@@ -61,6 +64,7 @@ class Inputs:
     B_ov: np.ndarray   # [naux][o][v]
     t1: np.ndarray     # [o][v]
     t2: np.ndarray     # [o][o][v][v]
+    B_oo: np.ndarray = None  # [naux][o][o]
 
 
 def sigma(naux: int) -> np.ndarray:
@@ -86,8 +90,10 @@ def _draw(rng: np.random.Generator, o: int, v: int, naux: int) -> Inputs:
            - e_vir[None, None, :, None] - e_vir[None, None, None, :])
     t2 = num / den
     t2 = 0.5 * (t2 + t2.transpose(1, 0, 3, 2))  # exact pair symmetry
+    X_oo = rng.standard_normal(size=(naux, o, o)) * s[:, None, None]
+    B_oo = np.ascontiguousarray(0.5 * (X_oo + X_oo.transpose(0, 2, 1)))
     return Inputs(o, v, naux, e_occ, e_vir, B, np.ascontiguousarray(B_ov),
-                  np.ascontiguousarray(t1), np.ascontiguousarray(t2))
+                  np.ascontiguousarray(t1), np.ascontiguousarray(t2), B_oo)
 
 
 def make_inputs(o: int, v: int, naux: int, seed: int) -> Inputs:
