@@ -11,12 +11,13 @@ v=400, N_aux=1600).  The other form, BF16X3 and the FP64 path are timed on the
 same workload and reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--dressed] [--lambda-only] [--backward] [--tuning k=v,...]
+                    [--dressed] [--lambda-only] [--backward] [--triples] [--tuning k=v,...]
 
 --dressed also times the t1-dressed term (Eq. pp-Ladder-2), --lambda-only
 the paper's lambda-only contraction (the ablation of the +- split) and
---backward the adjoint (dE/dtau, dE/dB), one step each on the same workload,
-under "others"; --tuning overrides the timed plan's launch parameters.
+--backward the adjoint (dE/dtau, dE/dB) and --triples the perturbative
+triples energy E(T), one step each on the same workload, under "others";
+--tuning overrides the timed plan's launch parameters.
 
 Under torchrun each rank runs its own replica of the workload on its own GPU
 (the ladder term of one molecule is one GPU's work); value = all ranks' flops
@@ -321,6 +322,8 @@ def main():
                     help="override launch parameters of the timed plan: key=value,... (ladder_tuning fields)")
     ap.add_argument("--lambda-only", action="store_true",
                     help="also time the paper's lambda-only contraction (ablation of the +- split)")
+    ap.add_argument("--triples", action="store_true",
+                    help="also time the perturbative triples energy E(T) (Sec. II.A) on the same molecule")
     ap.add_argument("--backward", action="store_true",
                     help="also time the adjoint (dE/dtau and dE/dB for W = 2t - t^T) on the same workload")
     ap.add_argument("--dressed", action="store_true",
@@ -520,6 +523,39 @@ def main():
         torch.cuda.empty_cache()
     if "fp64" in extra:
         extra["speedup_vs_fp64"] = extra["fp64"]["ms_per_step"] / ms
+    if args.triples:
+        # the perturbative triples energy E(T) on the same molecule (CUDA-core
+        # GEMMs): FP32 always, FP64 where its work stays below ~5 TFLOP
+        B_ov = torch.from_numpy(x.B_ov).to(dev)
+        B_oo = torch.from_numpy(x.B_oo).to(dev)
+        e_occ = torch.from_numpy(x.e_occ).to(dev)
+        e_vir = torch.from_numpy(x.e_vir).to(dev)
+        ft = 12.0 * w.o ** 3 * w.v ** 3 * (w.v + w.o)
+        tr = {"flops": ft, "note": "flops = 12 o^3 v^3 (v + o), the W contractions"}
+        for prec in ("fp32", "fp64"):
+            if prec == "fp64" and ft > 5e12:
+                continue
+            n_ws = lad.ladder_triples_workspace_size(w.o, w.v, w.naux, lad.TRIPLES_PRECISION[prec])
+            ws = torch.empty(n_ws, dtype=torch.uint8, device=dev)
+            args_t = (B, B_ov, B_oo, t1, t2, e_occ, e_vir)
+            Et = lad.triples(*args_t, precision=prec, workspace=ws)  # warm-up
+            torch.cuda.synchronize()
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            Et = lad.triples(*args_t, precision=prec, workspace=ws)
+            c1.record(stream)
+            torch.cuda.synchronize()
+            tms = c0.elapsed_time(c1)
+            tr[prec] = {"ms": tms, "tflops": ft / (tms * 1e-3) / 1e12, "E_T": float(Et.item())}
+            if prec == "fp32":
+                tr[prec]["roofline"] = {"bound": "alu", "achieved": ft / (tms * 1e-3) / 1e12,
+                                        "peak": FP32_ALU_TFLOPS, "unit": "TFLOP/s",
+                                        "frac": ft / (tms * 1e-3) / 1e12 / FP32_ALU_TFLOPS}
+            del ws
+            torch.cuda.empty_cache()
+        if "fp64" in tr:
+            tr["fp32_rel_diff"] = abs(tr["fp32"]["E_T"] - tr["fp64"]["E_T"]) / abs(tr["fp64"]["E_T"])
+        extra["triples"] = tr
     if args.backward and args.mode != "fp64":
         # the adjoint of E_L in the same mode and tuning: dE/dtau (the
         # transposed ladder) and dE/dB (Gamma stored once, then contracted)

@@ -143,6 +143,34 @@ ladder_status ladder_apply_dressed(ladder_plan_t plan, const double *B, const do
                                    const double *t1, const double *tau, double *R,
                                    void *stream);
 
+/* The perturbative triples energy of Sec. II.A (no plan needed):
+ *   E(T) = sum_ijk sum_abc (4 W_ijk^abc + W_ijk^bca + W_ijk^cab)
+ *                          (V_ijk^abc - V_ijk^cba) / (3 D_ijk^abc),
+ *   W_ijk^abc = P_ijk^abc ( sum_d v_di^ba t_kj^cd - sum_l v_kl^cj t_il^ab ),
+ *   V_ijk^abc = W_ijk^abc + v_jk^bc t_i^a + v_ik^ac t_j^b + v_ij^ab t_k^c,
+ *   D_ijk^abc = e_i + e_j + e_k - e_a - e_b - e_c,
+ * P the sum over the six simultaneous orderings of (i,j,k) and (a,b,c), and
+ * the integrals v^{pq}_{rs} = (pr|qs) = sum_P m^P_pr m^P_qs from the RI
+ * factors of the orbital pairs (m^P_ai = m^P_ia):
+ *   B [naux][v][v], Bov [naux][o][v], Boo [naux][o][o]   factors m^P
+ *   t1 [o][v], t2 [o][o][v][v]                          amplitudes
+ *   e_occ [o], e_vir [v]                                orbital energies
+ * E_dev: one double (device memory).  precision LADDER_TRIPLES_FP64 forms W
+ * in FP64; LADDER_TRIPLES_FP32 forms the integrals and W in FP32 (the energy
+ * sums stay FP64).  The contractions run on the CUDA cores; the work is
+ * 12 o^3 v^3 (v + o) flops.  The caller supplies a workspace of at least
+ * ladder_triples_workspace_size bytes (256-byte aligned): the integrals
+ * (o v^3 + o^3 v + o^2 v^2 elements), W for one (i, j) (o v^3) and the
+ * reduction partials.  Asynchronous on `stream`; the result is reduced in a
+ * fixed order (bitwise reproducible). */
+#define LADDER_TRIPLES_FP64 0
+#define LADDER_TRIPLES_FP32 1
+ladder_status ladder_triples_workspace_size(int o, int v, int naux, int precision, size_t *bytes);
+ladder_status ladder_triples(int o, int v, int naux, int precision, const double *B, const double *Bov,
+                             const double *Boo, const double *t1, const double *t2, const double *e_occ,
+                             const double *e_vir, double *E_dev, void *workspace, size_t ws_bytes,
+                             void *stream);
+
 /* E_L = sum_ijab R_ij^ab (2 t_ij^ab - t_ij^ba), reduced in FP64 in a fixed
  * order (bitwise reproducible); writes one double at E_dev (device memory). */
 ladder_status ladder_energy(ladder_plan_t plan, const double *R, const double *t2,

@@ -27,7 +27,8 @@ STATUS = {0: "LADDER_OK", 1: "LADDER_EINVAL", 2: "LADDER_ENOMEM", 3: "LADDER_ECU
 
 # every entry point that include/ladder.h declares
 EXPORTS = ("ladder_plan", "ladder_plan_mode", "ladder_get_tuning", "ladder_set_tuning", "ladder_workspace_size", "ladder_set_workspace",
-           "ladder_tau", "ladder_apply", "ladder_apply_dressed", "ladder_energy", "ladder_energy_noalloc", "ladder_backward", "ladder_pair_combine", "ladder_apply_host",
+           "ladder_tau", "ladder_apply", "ladder_apply_dressed", "ladder_triples_workspace_size",
+           "ladder_triples", "ladder_energy", "ladder_energy_noalloc", "ladder_backward", "ladder_pair_combine", "ladder_apply_host",
            "ladder_plan_batched", "ladder_set_member_tuning", "ladder_apply_batched", "ladder_last_device_error", "ladder_selftest_wait",
            "ladder_set_timing", "ladder_timing", "ladder_timing_passes", "ladder_timing_dressing", "ladder_flops", "ladder_status_string",
            "ladder_destroy")
@@ -73,6 +74,8 @@ def load_library(path: str = LIB_PATH):
         "ladder_tau": [_P, _P, _P, _P, _P],
         "ladder_apply": [_P, _P, _P, _P, _P],
         "ladder_apply_dressed": [_P, _P, _P, _P, _P, _P, _P],
+        "ladder_triples_workspace_size": [i, i, i, i, ctypes.POINTER(sz)],
+        "ladder_triples": [i, i, i, i] + [_P] * 9 + [sz, _P],
         "ladder_energy": [_P, _P, _P, _P, _P],
         "ladder_energy_noalloc": [i, i, _P, _P, _P, _P],
         "ladder_backward": [_P, _P, _P, _P, _P, _P, _P],
@@ -166,6 +169,38 @@ def ladder_apply_dressed(plan, B, B_ov, t1, tau, R, stream=None) -> None:
     _check("ladder_apply_dressed",
            load_library().ladder_apply_dressed(plan, _ptr(B), _ptr(B_ov), _ptr(t1), _ptr(tau), _ptr(R),
                                                _stream(stream)))
+
+
+TRIPLES_PRECISION = {"fp64": 0, "fp32": 1}
+
+
+def ladder_triples_workspace_size(o: int, v: int, naux: int, precision: int) -> int:
+    n = ctypes.c_size_t()
+    _check("ladder_triples_workspace_size",
+           load_library().ladder_triples_workspace_size(o, v, naux, precision, ctypes.byref(n)))
+    return n.value
+
+
+def ladder_triples(o, v, naux, precision, B, B_ov, B_oo, t1, t2, e_occ, e_vir, E, ws, stream=None) -> None:
+    _check("ladder_triples", load_library().ladder_triples(
+        o, v, naux, precision, _ptr(B), _ptr(B_ov), _ptr(B_oo), _ptr(t1), _ptr(t2), _ptr(e_occ),
+        _ptr(e_vir), _ptr(E), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def triples(B, B_ov, B_oo, t1, t2, e_occ, e_vir, precision="fp64", workspace=None):
+    """The perturbative triples energy E(T) of Sec. II.A on the device (FP64
+    device tensors in, one FP64 device scalar out); precision "fp64" or
+    "fp32" (integrals and W in FP32, energy sums in FP64)."""
+    import torch
+    naux, v, _ = B.shape
+    o = t1.shape[0]
+    prec = TRIPLES_PRECISION[precision]
+    if workspace is None:
+        n = ladder_triples_workspace_size(o, v, naux, prec)
+        workspace = torch.empty(max(n, 256), dtype=torch.uint8, device=B.device)
+    E = torch.empty((), dtype=torch.float64, device=B.device)
+    ladder_triples(o, v, naux, prec, B, B_ov, B_oo, t1, t2, e_occ, e_vir, E, workspace)
+    return E
 
 
 def ladder_energy(plan, R, t2, E, stream=None) -> None:

@@ -15,6 +15,9 @@
 // G costs 2 (ov)^2 N flops (half of it with its symmetry), X 2 o^4 v^2: both
 // O(o^2 v^2 N + o^4 v^2), against the ladder's O(v^4 N + o^2 v^4).
 //
+// The GEMM kernel also serves the perturbative triples (triples.cu), whose
+// W terms it accumulates with the kEpiAcc3 epilogue.
+//
 // This file holds the two kernels of the dressing:
 //   gemm_kernel     a CUDA-core GEMM C(m,n) = sum_k A(m,k) B(n,k) with free
 //                   strides, split-K / batch in z, and four epilogues; it
@@ -151,11 +154,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) gemm_kernel(const
         static_cast<T *>(g.Out)[(long long)z * g.so_batch + (long long)m * g.ldo + n] = val;
       } else if (g.epi == kEpiPerm) {
         // m = (k, c), n = (l, d) -> G[(k, l)][(c, d)]; mirrored for the symmetric product
-        const int k = m / g.pv, c = m % g.pv, l = n / g.pv, d = n % g.pv;
+        const int pn = g.pn ? g.pn : g.pv;
+        const int k = m / g.pv, c = m % g.pv, l = n / pn, d = n % pn;
         T *G = static_cast<T *>(g.Out);
-        const long long vv = (long long)g.pv * g.pv;
-        G[((long long)k * g.po + l) * vv + (long long)c * g.pv + d] = val;
-        if (g.sym) G[((long long)l * g.po + k) * vv + (long long)d * g.pv + c] = val;
+        const long long cd = (long long)g.pv * pn;
+        G[((long long)k * g.po + l) * cd + (long long)c * pn + d] = val;
+        if (g.sym) G[((long long)l * g.po + k) * cd + (long long)d * pn + c] = val;
+      } else if (g.epi == kEpiAcc3) {
+        T *O = static_cast<T *>(g.Out) + (long long)batch * g.so_batch + (long long)(m / g.pv) * g.s1 +
+               (long long)(m % g.pv) * g.s2 + (long long)n * g.s3;
+        const T x = (T)g.alpha * val;
+        *O = g.acc ? *O + x : x;
       } else if (g.epi == kEpiSubR) {  // R -= val (FP64 result)
         double *R = static_cast<double *>(g.Out);
         R[(long long)batch * g.so_batch + (long long)m * g.ldo + n] -= (double)val;

@@ -29,8 +29,10 @@ void launch_energy(int o, int v, const double *R, const double *t2, double *part
 
 // ---- t1-dressed ladder: Bd = B - mbar and the rank-o correction (dress.cu)
 // kEpiStore: Out (T) = C; kEpiPerm: Out (T) = C in the permuted (k,l)(c,d) layout;
-// kEpiSubR: Out (double) -= C; kEpiFromSrc: Out (double) = Src - C.
-enum : int { kEpiStore = 0, kEpiPerm = 1, kEpiSubR = 2, kEpiFromSrc = 3 };
+// kEpiSubR: Out (double) -= C; kEpiFromSrc: Out (double) = Src - C;
+// kEpiAcc3: Out (T) at (m / pv) s1 + (m % pv) s2 + n s3 (+ batch * so_batch)
+// gets alpha C (acc = 0) or alpha C added (acc = 1).
+enum : int { kEpiStore = 0, kEpiPerm = 1, kEpiSubR = 2, kEpiFromSrc = 3, kEpiAcc3 = 4 };
 // C(m, n) = sum_k A(m, k) B(n, k), A(m, k) = A[m*sam + k*sak], B(n, k) = B[n*sbn + k*sbk]
 // (one of the two strides of each operand is 1); z = batch * ksplit + split.
 struct GemmArgs {
@@ -44,13 +46,29 @@ struct GemmArgs {
   int ldo;
   int epi;
   int sym;     // A == B: compute the tiles with m-tile <= n-tile, mirror in the epilogue
-  int po, pv;  // kEpiPerm: m = (k, c), n = (l, d) -> Out[((k * po + l) * pv + c) * pv + d]
+  int po, pv;  // kEpiPerm: m = (k, c), n = (l, d) -> Out[((k * po + l) * pv + c) * pn + d],
+  int pn;      //   c = m % pv, d = n % pn (pn = 0: pn = pv)
+  long long s1, s2, s3;  // kEpiAcc3 strides
+  int acc;
+  double alpha;
   int ntm, ntn, zoff;  // set by the launcher
 };
 template <typename TA, typename TB, typename T>
 cudaError_t launch_gemm(const GemmArgs &g, int batch, cudaStream_t s);
 template <typename T>
 cudaError_t launch_reduce(T *X, long long n, int parts, cudaStream_t s);
+
+// ---- perturbative triples (triples.cu); W from launch_gemm with kEpiAcc3
+struct TriplesArgs {
+  const void *oovv;  // [j][k][b][c] = v_jk^bc = (bj|ck), element type T of the energy kernel
+  const double *t1, *e_occ, *e_vir;
+  int o, v;
+};
+int triples_energy_blocks(int v);
+template <typename T>
+cudaError_t launch_triples_energy(const TriplesArgs &a, const T *W, int i, int j, double *part,
+                                  cudaStream_t s);
+cudaError_t launch_triples_final(const double *part, long long n, double *E, cudaStream_t s);
 
 // ---- FP64 fused ladder (DMMA)
 struct Fp64Args {

@@ -464,6 +464,181 @@ ladder_status dress_correct(const ladder_plan_s *pl, const double *Bov, const do
   return cuda_status(e);
 }
 
+// ---- perturbative triples (Sec. II.A): workspace and launch sequence
+struct TriplesLayout {
+  size_t ovvv = 0, Q = 0, oovv = 0, W = 0, part = 0, total = 0;
+};
+
+TriplesLayout triples_layout(int o, int v, bool fp32) {
+  const size_t t = fp32 ? sizeof(float) : sizeof(double);
+  const size_t ov = (size_t)o * v, v3 = (size_t)v * v * v;
+  TriplesLayout L;
+  size_t off = 0;
+  L.ovvv = off;
+  off = align_up(off + o * v3 * t);
+  L.Q = off;
+  off = align_up(off + (size_t)o * o * ov * t);
+  L.oovv = off;
+  off = align_up(off + ov * ov * t);
+  L.W = off;
+  off = align_up(off + o * v3 * t);
+  L.part = off;
+  off = align_up(off + (size_t)o * o * o * triples_energy_blocks(v) * sizeof(double));
+  L.total = off;
+  return L;
+}
+
+// E(T) = sum over (i, j) of one batched pass over k:
+//   W[k] = P applied to  sum_d v_di^ba t_kj^cd - sum_l v_kl^cj t_il^ab
+// as twelve GEMMs (two per ordering of P), each written into W[k][a][b][c]
+// through the kEpiAcc3 epilogue, then the energy kernel on W[k].
+template <typename T>
+cudaError_t triples_run(int o, int v, int n, const double *B, const double *Bov, const double *Boo,
+                        const double *t1, const double *t2, const double *e_occ, const double *e_vir,
+                        double *E, char *ws, const TriplesLayout &L, cudaStream_t s) {
+  T *ovvv = reinterpret_cast<T *>(ws + L.ovvv);
+  T *Q = reinterpret_cast<T *>(ws + L.Q);
+  T *oovv = reinterpret_cast<T *>(ws + L.oovv);
+  T *W = reinterpret_cast<T *>(ws + L.W);
+  double *part = reinterpret_cast<double *>(ws + L.part);
+  const long long ov = (long long)o * v, vv = (long long)v * v, v3 = vv * v;
+  auto base = [](GemmArgs &g) {
+    std::memset(&g, 0, sizeof(g));
+    g.ksplit = 1;
+    g.alpha = 1.0;
+  };
+  GemmArgs g;
+  // ovvv[i][b][a][d] = (bd|ai) = v_di^ba = sum_P Bov[P][i][a] Bvv[P][b][d]
+  base(g);
+  g.A = Bov;
+  g.B = B;
+  g.Out = ovvv;
+  g.sam = 1;
+  g.sak = ov;
+  g.sbn = 1;
+  g.sbk = vv;
+  g.M = (int)ov;
+  g.N = (int)vv;
+  g.K = n;
+  g.kchunk = n;
+  g.epi = kEpiPerm;
+  g.po = v;
+  g.pv = v;
+  g.pn = v;
+  cudaError_t e = launch_gemm<double, double, T>(g, 1, s);
+  // Q[k][j][c][l] = (ck|jl) = v_kl^cj = sum_P Bov[P][k][c] Boo[P][j][l]
+  base(g);
+  g.A = Bov;
+  g.B = Boo;
+  g.Out = Q;
+  g.sam = 1;
+  g.sak = ov;
+  g.sbn = 1;
+  g.sbk = (long long)o * o;
+  g.M = (int)ov;
+  g.N = o * o;
+  g.K = n;
+  g.kchunk = n;
+  g.epi = kEpiPerm;
+  g.po = o;
+  g.pv = v;
+  g.pn = o;
+  if (e == cudaSuccess) e = launch_gemm<double, double, T>(g, 1, s);
+  // oovv[j][k][b][c] = (bj|ck) = v_jk^bc = sum_P Bov[P][j][b] Bov[P][k][c] (symmetric)
+  base(g);
+  g.A = Bov;
+  g.B = Bov;
+  g.Out = oovv;
+  g.sam = 1;
+  g.sak = ov;
+  g.sbn = 1;
+  g.sbk = ov;
+  g.M = g.N = (int)ov;
+  g.K = n;
+  g.kchunk = n;
+  g.epi = kEpiPerm;
+  g.sym = 1;
+  g.po = o;
+  g.pv = v;
+  g.pn = v;
+  if (e == cudaSuccess) e = launch_gemm<double, double, T>(g, 1, s);
+  // the six orderings of P: (x, y, z) = (I[p0], I[p1], I[p2]) with I = (i, j, k),
+  // and (alpha, beta, gamma) = (A[p0], A[p1], A[p2]) with A = (a, b, c)
+  static const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {2, 0, 1}, {2, 1, 0}, {1, 2, 0}, {1, 0, 2}};
+  const long long wstride[3] = {vv, v, 1};  // W[k][a][b][c]
+  TriplesArgs ta;
+  ta.oovv = oovv;
+  ta.t1 = t1;
+  ta.e_occ = e_occ;
+  ta.e_vir = e_vir;
+  ta.o = o;
+  ta.v = v;
+  for (int i = 0; e == cudaSuccess && i < o; ++i)
+    for (int j = 0; e == cudaSuccess && j < o; ++j) {
+      const int I[3] = {i, j, 0};
+      for (int q = 0; e == cudaSuccess && q < 6; ++q) {
+        const int *p = perm[q];
+        // index of the ordering's x, y, z (k varies with the batch)
+        const long long x = I[p[0]], y = I[p[1]], z = I[p[2]];
+        const bool xk = p[0] == 2, yk = p[1] == 2, zk = p[2] == 2;
+        // first contraction: rows (beta, alpha), columns gamma, K = d:
+        //   sum_d ovvv[x][beta][alpha][d] t2[z][y][gamma][d]
+        base(g);
+        g.A = ovvv + (xk ? 0 : x * v3);
+        g.sa_batch = xk ? v3 : 0;
+        g.B = t2 + (zk ? 0 : z * o * vv) + (yk ? 0 : y * vv);
+        g.sb_batch = (zk ? (long long)o * vv : 0) + (yk ? vv : 0);
+        g.sam = v;
+        g.sak = 1;
+        g.sbn = v;
+        g.sbk = 1;
+        g.M = (int)vv;
+        g.N = v;
+        g.K = v;
+        g.kchunk = v;
+        g.Out = W;
+        g.so_batch = v3;
+        g.epi = kEpiAcc3;
+        g.pv = v;
+        g.s1 = wstride[p[1]];
+        g.s2 = wstride[p[0]];
+        g.s3 = wstride[p[2]];
+        g.acc = q > 0;
+        e = launch_gemm<T, double, T>(g, o, s);
+        if (e != cudaSuccess) break;
+        // second contraction, subtracted: rows (alpha, beta), columns gamma, K = l:
+        //   sum_l t2[x][l][alpha][beta] Q[z][y][gamma][l]
+        base(g);
+        g.A = t2 + (xk ? 0 : x * o * vv);
+        g.sa_batch = xk ? (long long)o * vv : 0;
+        g.B = Q + (zk ? 0 : z * o * ov) + (yk ? 0 : y * ov);
+        g.sb_batch = (zk ? (long long)o * ov : 0) + (yk ? ov : 0);
+        g.sam = 1;
+        g.sak = vv;
+        g.sbn = o;
+        g.sbk = 1;
+        g.M = (int)vv;
+        g.N = v;
+        g.K = o;
+        g.kchunk = o;
+        g.Out = W;
+        g.so_batch = v3;
+        g.epi = kEpiAcc3;
+        g.pv = v;
+        g.s1 = wstride[p[0]];
+        g.s2 = wstride[p[1]];
+        g.s3 = wstride[p[2]];
+        g.acc = 1;
+        g.alpha = -1.0;
+        e = launch_gemm<double, T, T>(g, o, s);
+      }
+      if (e == cudaSuccess) e = launch_triples_energy<T>(ta, W, i, j, part, s);
+    }
+  if (e == cudaSuccess)
+    e = launch_triples_final(part, (long long)o * o * o * triples_energy_blocks(v), E, s);
+  return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -971,6 +1146,34 @@ ladder_status ladder_apply_dressed(ladder_plan_t pl, const double *B, const doub
   st = f64 ? dress_correct<double>(pl, Bov, t1, tau, R, s) : dress_correct<float>(pl, Bov, t1, tau, R, s);
   mark(pl, 7, s);
   return st;
+}
+
+ladder_status ladder_triples_workspace_size(int o, int v, int naux, int precision, size_t *bytes) {
+  if (!bytes || o < 1 || o > 256 || v < 1 || v > 4096 || naux < 1 || naux > 65536 ||
+      (precision != LADDER_TRIPLES_FP64 && precision != LADDER_TRIPLES_FP32))
+    return LADDER_EINVAL;
+  *bytes = triples_layout(o, v, precision == LADDER_TRIPLES_FP32).total;
+  return LADDER_OK;
+}
+
+ladder_status ladder_triples(int o, int v, int naux, int precision, const double *B, const double *Bov,
+                             const double *Boo, const double *t1, const double *t2, const double *e_occ,
+                             const double *e_vir, double *E_dev, void *workspace, size_t ws_bytes,
+                             void *stream) {
+  size_t need = 0;
+  const ladder_status st = ladder_triples_workspace_size(o, v, naux, precision, &need);
+  if (st != LADDER_OK) return st;
+  if (!workspace || ws_bytes < need) return LADDER_EWORKSPACE;
+  if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return LADDER_EINVAL;
+  const void *ptrs[] = {B, Bov, Boo, t1, t2, e_occ, e_vir, E_dev, workspace};
+  for (const void *q : ptrs)
+    if (!dev_ptr_ok(q)) return LADDER_EINVAL;
+  const TriplesLayout L = triples_layout(o, v, precision == LADDER_TRIPLES_FP32);
+  char *ws = static_cast<char *>(workspace);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return cuda_status(precision == LADDER_TRIPLES_FP32
+                         ? triples_run<float>(o, v, naux, B, Bov, Boo, t1, t2, e_occ, e_vir, E_dev, ws, L, s)
+                         : triples_run<double>(o, v, naux, B, Bov, Boo, t1, t2, e_occ, e_vir, E_dev, ws, L, s));
 }
 
 ladder_status ladder_energy(ladder_plan_t pl, const double *R, const double *t2, double *E_dev,
