@@ -78,8 +78,10 @@ __device__ __forceinline__ void gemm_stage(T (*tile)[kBM + kPadF], bool kfast, c
 
 template <typename TA, typename TB, typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) gemm_kernel(const GemmArgs g) {
-  __shared__ __align__(16) T sA[2][kBK][kBM + kPadF];
-  __shared__ __align__(16) T sB[2][kBK][kBN + kPadF];
+  // the two operand rings, one buffer: the row-major epilogue reuses it
+  __shared__ __align__(16) T sAB[2 * 2 * kBK * (kBM + kPadF)];
+  T(*sA)[kBK][kBM + kPadF] = reinterpret_cast<T(*)[kBK][kBM + kPadF]>(sAB);
+  T(*sB)[kBK][kBN + kPadF] = reinterpret_cast<T(*)[kBK][kBN + kPadF]>(sAB + 2 * kBK * (kBM + kPadF));
   int mt, nt;
   if (g.sym) {
     // upper triangle of tiles only (mt <= nt); the epilogue mirrors
@@ -140,6 +142,41 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) gemm_kernel(const
     __syncthreads();
   }
 
+  if (g.epi == kEpiAcc3 && g.s2 == 1 && g.s3 != 1) {
+    // the output's contiguous index is the row's (m % pv): stage 32-row slabs
+    // of the tile in shared memory and walk them rows fastest, so a warp's
+    // read-modify-writes fall on consecutive addresses
+    static_assert(32 * (kBN + 1) <= 2 * 2 * kBK * (kBM + kPadF), "stage fits the operand rings");
+    T *stage = sAB;
+    T *O = static_cast<T *>(g.Out) + (long long)batch * g.so_batch;
+    const T alpha = (T)g.alpha;
+    for (int sl = 0; sl < 4; ++sl) {
+      // rows 32 sl .. 32 sl + 31 belong to ty in [8 (sl & 1), 8 (sl & 1) + 8), half sl >> 1
+      if ((ty >> 3) == (sl & 1)) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int r = ((sl >> 1) ? 64 : 0) + ty * 4 + i - 32 * sl;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int c = j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4);
+            stage[r * (kBN + 1) + c] = acc[(sl >> 1) ? 4 + i : i][j];
+          }
+        }
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < 32 * kBN; e += 256) {
+        const int rl = e % 32, c = e / 32;
+        const int m = m0 + 32 * sl + rl, n = n0 + c;
+        if (m < g.M && n < g.N) {
+          T *w = O + (long long)(m / g.pv) * g.s1 + (long long)(m % g.pv) + (long long)n * g.s3;
+          const T x = alpha * stage[rl * (kBN + 1) + c];
+          *w = g.acc ? *w + x : x;
+        }
+      }
+      __syncthreads();
+    }
+    return;
+  }
   // epilogue: thread rows ty*4+i (i<4) and 64+ty*4+i, columns likewise with tx
 #pragma unroll
   for (int i = 0; i < 8; ++i) {

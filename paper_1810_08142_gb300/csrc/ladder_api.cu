@@ -466,7 +466,7 @@ ladder_status dress_correct(const ladder_plan_s *pl, const double *Bov, const do
 
 // ---- perturbative triples (Sec. II.A): workspace and launch sequence
 struct TriplesLayout {
-  size_t ovvv = 0, Q = 0, oovv = 0, W = 0, part = 0, total = 0;
+  size_t ovvv = 0, ovvvT = 0, Q = 0, oovv = 0, W = 0, part = 0, total = 0;
 };
 
 TriplesLayout triples_layout(int o, int v, bool fp32) {
@@ -475,6 +475,8 @@ TriplesLayout triples_layout(int o, int v, bool fp32) {
   TriplesLayout L;
   size_t off = 0;
   L.ovvv = off;
+  off = align_up(off + o * v3 * t);
+  L.ovvvT = off;
   off = align_up(off + o * v3 * t);
   L.Q = off;
   off = align_up(off + (size_t)o * o * ov * t);
@@ -497,6 +499,7 @@ cudaError_t triples_run(int o, int v, int n, const double *B, const double *Bov,
                         const double *t1, const double *t2, const double *e_occ, const double *e_vir,
                         double *E, char *ws, const TriplesLayout &L, cudaStream_t s) {
   T *ovvv = reinterpret_cast<T *>(ws + L.ovvv);
+  T *ovvvT = reinterpret_cast<T *>(ws + L.ovvvT);
   T *Q = reinterpret_cast<T *>(ws + L.Q);
   T *oovv = reinterpret_cast<T *>(ws + L.oovv);
   T *W = reinterpret_cast<T *>(ws + L.W);
@@ -526,6 +529,23 @@ cudaError_t triples_run(int o, int v, int n, const double *B, const double *Bov,
   g.pv = v;
   g.pn = v;
   cudaError_t e = launch_gemm<double, double, T>(g, 1, s);
+  // the same integrals as ovvvT[i][a][b][d] (rows (a, b)), for the orderings
+  // whose b-index lands on W's contiguous index
+  base(g);
+  g.A = Bov;
+  g.B = B;
+  g.Out = ovvvT;
+  g.sam = 1;
+  g.sak = ov;
+  g.sbn = 1;
+  g.sbk = vv;
+  g.M = (int)ov;
+  g.N = (int)vv;
+  g.K = n;
+  g.kchunk = n;
+  g.ldo = (int)vv;
+  g.epi = kEpiStore;
+  if (e == cudaSuccess) e = launch_gemm<double, double, T>(g, 1, s);
   // Q[k][j][c][l] = (ck|jl) = v_kl^cj = sum_P Bov[P][k][c] Boo[P][j][l]
   base(g);
   g.A = Bov;
@@ -583,8 +603,10 @@ cudaError_t triples_run(int o, int v, int n, const double *B, const double *Bov,
         const bool xk = p[0] == 2, yk = p[1] == 2, zk = p[2] == 2;
         // first contraction: rows (beta, alpha), columns gamma, K = d:
         //   sum_d ovvv[x][beta][alpha][d] t2[z][y][gamma][d]
+        // (rows (alpha, beta) from ovvvT when beta is W's contiguous index c)
+        const bool rowsT = p[1] == 2;
         base(g);
-        g.A = ovvv + (xk ? 0 : x * v3);
+        g.A = (rowsT ? ovvvT : ovvv) + (xk ? 0 : x * v3);
         g.sa_batch = xk ? v3 : 0;
         g.B = t2 + (zk ? 0 : z * o * vv) + (yk ? 0 : y * vv);
         g.sb_batch = (zk ? (long long)o * vv : 0) + (yk ? vv : 0);
@@ -600,8 +622,8 @@ cudaError_t triples_run(int o, int v, int n, const double *B, const double *Bov,
         g.so_batch = v3;
         g.epi = kEpiAcc3;
         g.pv = v;
-        g.s1 = wstride[p[1]];
-        g.s2 = wstride[p[0]];
+        g.s1 = wstride[rowsT ? p[0] : p[1]];
+        g.s2 = wstride[rowsT ? p[1] : p[0]];
         g.s3 = wstride[p[2]];
         g.acc = q > 0;
         e = launch_gemm<T, double, T>(g, o, s);
