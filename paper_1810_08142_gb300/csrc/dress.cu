@@ -108,21 +108,38 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) gemm_kernel(const
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
 
+  // an optional second K segment (A2, B2, K2; B2 scaled by beta2) follows
+  // the first in the same accumulators
+  const TA *A2 = static_cast<const TA *>(g.A2) + (long long)batch * g.sa2_batch;
+  const TB *B2 = static_cast<const TB *>(g.B2) + (long long)batch * g.sb2_batch;
+  const bool akf2 = g.sak2 == 1, bkf2 = g.sbk2 == 1;
   T ra[4], rb[4];
-  const int nkt = k1 > k0 ? (k1 - k0 + kBK - 1) / kBK : 0;
-  if (nkt > 0) {
-    gemm_fetch(A, g.sam, g.sak, g.M, m0, k0, k1, akf, ra);
-    gemm_fetch(Bm, g.sbn, g.sbk, g.N, n0, k0, k1, bkf, rb);
-    gemm_stage(sA[0], akf, ra);
-    gemm_stage(sB[0], bkf, rb);
-  }
+  const int nkt1 = k1 > k0 ? (k1 - k0 + kBK - 1) / kBK : 0;
+  const int nkt2 = g.A2 ? (g.K2 + kBK - 1) / kBK : 0;
+  const int nkt = nkt1 + nkt2;
+  auto fetch = [&](int kt) -> bool {  // true: a tile of the second segment
+    if (kt < nkt1) {
+      gemm_fetch(A, g.sam, g.sak, g.M, m0, k0 + kt * kBK, k1, akf, ra);
+      gemm_fetch(Bm, g.sbn, g.sbk, g.N, n0, k0 + kt * kBK, k1, bkf, rb);
+      return false;
+    }
+    const int kk = (kt - nkt1) * kBK;
+    gemm_fetch(A2, g.sam2, g.sak2, g.M, m0, kk, g.K2, akf2, ra);
+    gemm_fetch(B2, g.sbn2, g.sbk2, g.N, n0, kk, g.K2, bkf2, rb);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) rb[r] *= (T)g.beta2;
+    return true;
+  };
+  auto stage = [&](int buf, bool seg2) {
+    gemm_stage(sA[buf], seg2 ? akf2 : akf, ra);
+    gemm_stage(sB[buf], seg2 ? bkf2 : bkf, rb);
+  };
+  if (nkt > 0) stage(0, fetch(0));
   __syncthreads();
   for (int kt = 0; kt < nkt; ++kt) {
     const int buf = kt & 1;
-    if (kt + 1 < nkt) {
-      gemm_fetch(A, g.sam, g.sak, g.M, m0, k0 + (kt + 1) * kBK, k1, akf, ra);
-      gemm_fetch(Bm, g.sbn, g.sbk, g.N, n0, k0 + (kt + 1) * kBK, k1, bkf, rb);
-    }
+    bool seg2 = false;
+    if (kt + 1 < nkt) seg2 = fetch(kt + 1);
 #pragma unroll
     for (int kk = 0; kk < kBK; ++kk) {
       T a[8], b[8];
@@ -135,10 +152,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) gemm_kernel(const
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] += a[i] * b[j];
     }
-    if (kt + 1 < nkt) {
-      gemm_stage(sA[buf ^ 1], akf, ra);
-      gemm_stage(sB[buf ^ 1], bkf, rb);
-    }
+    if (kt + 1 < nkt) stage(buf ^ 1, seg2);
     __syncthreads();
   }
 
@@ -249,6 +263,7 @@ template cudaError_t launch_gemm<double, double, double>(const GemmArgs &, int, 
 template cudaError_t launch_gemm<double, double, float>(const GemmArgs &, int, cudaStream_t);
 template cudaError_t launch_gemm<double, float, float>(const GemmArgs &, int, cudaStream_t);
 template cudaError_t launch_gemm<float, double, float>(const GemmArgs &, int, cudaStream_t);
+template cudaError_t launch_gemm<float, float, float>(const GemmArgs &, int, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_reduce(T *X, long long n, int parts, cudaStream_t s) {

@@ -49,6 +49,12 @@ struct GemmArgs {
   int po, pv;  // kEpiPerm: m = (k, c), n = (l, d) -> Out[((k * po + l) * pv + c) * pn + d],
   int pn;      //   c = m % pv, d = n % pn (pn = 0: pn = pv)
   long long s1, s2, s3;  // kEpiAcc3 strides
+  // optional second K segment in the same accumulators: A2 (m, k) = A2[m*sam2 + k*sak2],
+  // B2 (n, k) = beta2 * B2[n*sbn2 + k*sbk2], k < K2 (ksplit must be 1)
+  const void *A2, *B2;
+  long long sam2, sak2, sbn2, sbk2, sa2_batch, sb2_batch;
+  int K2;
+  double beta2;
   int acc;
   double alpha;
   int ntm, ntn, zoff;  // set by the launcher
@@ -68,6 +74,8 @@ int triples_energy_blocks(int v);
 template <typename T>
 cudaError_t launch_triples_energy(const TriplesArgs &a, const T *W, int i, int j, double *part,
                                   cudaStream_t s);
+template <typename T>
+cudaError_t launch_triples_t2(int o, int v, const double *t2, T *t2c, T *t2T, cudaStream_t s);
 cudaError_t launch_triples_final(const double *part, long long n, double *E, cudaStream_t s);
 
 // ---- FP64 fused ladder (DMMA)

@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/ladder.h"
@@ -466,7 +467,7 @@ ladder_status dress_correct(const ladder_plan_s *pl, const double *Bov, const do
 
 // ---- perturbative triples (Sec. II.A): workspace and launch sequence
 struct TriplesLayout {
-  size_t ovvv = 0, ovvvT = 0, Q = 0, oovv = 0, W = 0, part = 0, total = 0;
+  size_t ovvv = 0, ovvvT = 0, Q = 0, oovv = 0, t2c = 0, t2T = 0, W = 0, part = 0, total = 0;
 };
 
 TriplesLayout triples_layout(int o, int v, bool fp32) {
@@ -481,6 +482,10 @@ TriplesLayout triples_layout(int o, int v, bool fp32) {
   L.Q = off;
   off = align_up(off + (size_t)o * o * ov * t);
   L.oovv = off;
+  off = align_up(off + ov * ov * t);
+  L.t2c = off;  // FP32 only
+  if (fp32) off = align_up(off + ov * ov * t);
+  L.t2T = off;
   off = align_up(off + ov * ov * t);
   L.W = off;
   off = align_up(off + o * v3 * t);
@@ -582,6 +587,11 @@ cudaError_t triples_run(int o, int v, int n, const double *B, const double *Bov,
   g.pv = v;
   g.pn = v;
   if (e == cudaSuccess) e = launch_gemm<double, double, T>(g, 1, s);
+  // t2 in T (FP32 only) and with a <-> b exchanged
+  T *t2c = std::is_same<T, double>::value ? nullptr : reinterpret_cast<T *>(ws + L.t2c);
+  T *t2T = reinterpret_cast<T *>(ws + L.t2T);
+  if (e == cudaSuccess) e = launch_triples_t2<T>(o, v, t2, t2c, t2T, s);
+  const T *t2x = t2c ? t2c : reinterpret_cast<const T *>(t2);
   // the six orderings of P: (x, y, z) = (I[p0], I[p1], I[p2]) with I = (i, j, k),
   // and (alpha, beta, gamma) = (A[p0], A[p1], A[p2]) with A = (a, b, c)
   static const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {2, 0, 1}, {2, 1, 0}, {1, 2, 0}, {1, 0, 2}};
@@ -598,61 +608,47 @@ cudaError_t triples_run(int o, int v, int n, const double *B, const double *Bov,
       const int I[3] = {i, j, 0};
       for (int q = 0; e == cudaSuccess && q < 6; ++q) {
         const int *p = perm[q];
-        // index of the ordering's x, y, z (k varies with the batch)
+        // x, y, z of the ordering; the one that is k varies with the batch
         const long long x = I[p[0]], y = I[p[1]], z = I[p[2]];
         const bool xk = p[0] == 2, yk = p[1] == 2, zk = p[2] == 2;
-        // first contraction: rows (beta, alpha), columns gamma, K = d:
-        //   sum_d ovvv[x][beta][alpha][d] t2[z][y][gamma][d]
-        // (rows (alpha, beta) from ovvvT when beta is W's contiguous index c)
-        const bool rowsT = p[1] == 2;
+        // One GEMM per ordering, columns gamma, two K segments into the same
+        // accumulators:  sum_d (bd|ai) t_zy^{gamma d}  over d, then
+        // - sum_l t_xl^{alpha beta} (gamma z|y l)  over l.  The rows are
+        // (beta, alpha) when alpha is W's contiguous index c, else (alpha, beta),
+        // so the epilogue's row-fastest writes stay contiguous.
+        const bool rowsBA = p[0] == 2;
         base(g);
-        g.A = (rowsT ? ovvvT : ovvv) + (xk ? 0 : x * v3);
+        g.A = (rowsBA ? ovvv : ovvvT) + (xk ? 0 : x * v3);
         g.sa_batch = xk ? v3 : 0;
-        g.B = t2 + (zk ? 0 : z * o * vv) + (yk ? 0 : y * vv);
-        g.sb_batch = (zk ? (long long)o * vv : 0) + (yk ? vv : 0);
         g.sam = v;
         g.sak = 1;
+        g.B = t2x + (zk ? 0 : z * o * vv) + (yk ? 0 : y * vv);
+        g.sb_batch = (zk ? (long long)o * vv : 0) + (yk ? vv : 0);
         g.sbn = v;
         g.sbk = 1;
         g.M = (int)vv;
         g.N = v;
         g.K = v;
         g.kchunk = v;
+        g.A2 = (rowsBA ? (const T *)t2T : t2x) + (xk ? 0 : x * o * vv);
+        g.sa2_batch = xk ? (long long)o * vv : 0;
+        g.sam2 = 1;
+        g.sak2 = vv;
+        g.B2 = Q + (zk ? 0 : z * o * ov) + (yk ? 0 : y * ov);
+        g.sb2_batch = (zk ? (long long)o * ov : 0) + (yk ? ov : 0);
+        g.sbn2 = o;
+        g.sbk2 = 1;
+        g.K2 = o;
+        g.beta2 = -1.0;
         g.Out = W;
         g.so_batch = v3;
         g.epi = kEpiAcc3;
         g.pv = v;
-        g.s1 = wstride[rowsT ? p[0] : p[1]];
-        g.s2 = wstride[rowsT ? p[1] : p[0]];
+        g.s1 = wstride[rowsBA ? p[1] : p[0]];
+        g.s2 = wstride[rowsBA ? p[0] : p[1]];
         g.s3 = wstride[p[2]];
         g.acc = q > 0;
-        e = launch_gemm<T, double, T>(g, o, s);
-        if (e != cudaSuccess) break;
-        // second contraction, subtracted: rows (alpha, beta), columns gamma, K = l:
-        //   sum_l t2[x][l][alpha][beta] Q[z][y][gamma][l]
-        base(g);
-        g.A = t2 + (xk ? 0 : x * o * vv);
-        g.sa_batch = xk ? (long long)o * vv : 0;
-        g.B = Q + (zk ? 0 : z * o * ov) + (yk ? 0 : y * ov);
-        g.sb_batch = (zk ? (long long)o * ov : 0) + (yk ? ov : 0);
-        g.sam = 1;
-        g.sak = vv;
-        g.sbn = o;
-        g.sbk = 1;
-        g.M = (int)vv;
-        g.N = v;
-        g.K = o;
-        g.kchunk = o;
-        g.Out = W;
-        g.so_batch = v3;
-        g.epi = kEpiAcc3;
-        g.pv = v;
-        g.s1 = wstride[p[0]];
-        g.s2 = wstride[p[1]];
-        g.s3 = wstride[p[2]];
-        g.acc = 1;
-        g.alpha = -1.0;
-        e = launch_gemm<double, T, T>(g, o, s);
+        e = launch_gemm<T, T, T>(g, o, s);
       }
       if (e == cudaSuccess) e = launch_triples_energy<T>(ta, W, i, j, part, s);
     }
