@@ -9,6 +9,9 @@ With --dressed it stores the same columns of the t1-dressed term
 (Eq. pp-Ladder-2) instead, from the oracle's per-column evaluation, in
 <workload>_dressed.json:
     python tests/golden/make_golden.py --dressed mid_o34_v400_n1600
+With --triples it stores the perturbative triples energy E(T) of Sec. II.A
+in <workload>_triples.json:
+    python tests/golden/make_golden.py --triples dimer_o10_v120_n480
 """
 import json
 import os
@@ -75,9 +78,26 @@ def main_dressed(name):
     print(name, "dressed columns, seconds", time.time() - t0)
 
 
+def main_triples(name):
+    w = synthetic.WORKLOADS[name]
+    t0 = time.time()
+    x = synthetic.make_inputs(w.o, w.v, w.naux, w.seed)
+    E = oracle.triples(x.B, x.B_ov, x.B_oo, x.t1, x.t2, x.e_occ, x.e_vir)
+    out = {
+        "workload": name, "o": w.o, "v": w.v, "naux": w.naux, "seed": w.seed, "E_T": E,
+        "oracle_threads": oracle.threads(), "oracle_seconds": time.time() - t0,
+        "note": "perturbative triples E(T); written by tests/golden/make_golden.py --triples from "
+                "the plain FP64 CPU oracle",
+    }
+    path = os.path.join(ROOT, "tests", "golden", name + "_triples.json")
+    with open(path, "w") as f:
+        json.dump(out, f)
+    print(name, "E(T)", E, "seconds", time.time() - t0)
+
+
 if __name__ == "__main__":
     args = sys.argv[1:]
-    dressed = "--dressed" in args
+    run = main_dressed if "--dressed" in args else main_triples if "--triples" in args else main
     for n in args:
-        if n != "--dressed":
-            (main_dressed if dressed else main)(n)
+        if not n.startswith("--"):
+            run(n)

@@ -67,3 +67,23 @@ def test_triples_rejects_a_small_workspace(lad):
     with pytest.raises(lad.LadderError):
         lad.ladder_triples(3, 5, 4, 0, to_dev(x.B), to_dev(x.B_ov), to_dev(x.B_oo), to_dev(x.t1),
                            to_dev(x.t2), to_dev(x.e_occ), to_dev(x.e_vir), E, ws)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_triples_dimer_against_stored_oracle(lad, precision):
+    """The water-dimer-sized workload (o=10, v=120, N_aux=480) against E(T)
+    stored by tests/golden/make_golden.py --triples."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "dimer_o10_v120_n480_triples.json")
+    if not os.path.exists(path):
+        pytest.skip("no stored E(T)")
+    with open(path) as f:
+        g = json.load(f)
+    w = synthetic.WORKLOADS["dimer_o10_v120_n480"]
+    assert (g["o"], g["v"], g["naux"], g["seed"]) == (w.o, w.v, w.naux, w.seed)
+    E_g = run(lad, synthetic.make_inputs(w.o, w.v, w.naux, w.seed), precision)
+    err = abs(E_g - g["E_T"]) / abs(g["E_T"])
+    print("triples dimer %s: E(T) %.12e  rel err %.3e" % (precision, g["E_T"], err))
+    assert err < TOL[precision]
