@@ -28,6 +28,7 @@
 // correction is about 1e-4 of R there, so FP32 keeps it far inside their
 // tolerance).
 #include <algorithm>
+#include <type_traits>
 
 #include "kernels.h"
 
@@ -76,12 +77,26 @@ __device__ __forceinline__ void gemm_stage(T (*tile)[kBM + kPadF], bool kfast, c
   }
 }
 
+template <int N>
+__device__ __forceinline__ void cp_async_n(void *smem, const void *gmem, int src_bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(sa), "l"(gmem), "n"(N), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
 template <typename TA, typename TB, typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) gemm_kernel(const GemmArgs g) {
-  // the two operand rings, one buffer: the row-major epilogue reuses it
-  __shared__ __align__(16) T sAB[2 * 2 * kBK * (kBM + kPadF)];
+  // Operands already in the accumulation type are copied global -> shared
+  // with cp.async into a ring of kStg tiles; the others are converted in
+  // registers on the way (two tiles).  One buffer holds both rings; the
+  // row-major epilogue reuses it.
+  constexpr bool kAsync = std::is_same<TA, T>::value && std::is_same<TB, T>::value;
+  constexpr int kStg = (kAsync && sizeof(T) == 4) ? 3 : 2;
+  __shared__ __align__(16) T sAB[kStg * 2 * kBK * (kBM + kPadF)];
   T(*sA)[kBK][kBM + kPadF] = reinterpret_cast<T(*)[kBK][kBM + kPadF]>(sAB);
-  T(*sB)[kBK][kBN + kPadF] = reinterpret_cast<T(*)[kBK][kBN + kPadF]>(sAB + 2 * kBK * (kBM + kPadF));
+  T(*sB)[kBK][kBN + kPadF] = reinterpret_cast<T(*)[kBK][kBN + kPadF]>(sAB + kStg * kBK * (kBM + kPadF));
   int mt, nt;
   if (g.sym) {
     // upper triangle of tiles only (mt <= nt); the epilogue mirrors
@@ -134,12 +149,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) gemm_kernel(const
     gemm_stage(sA[buf], seg2 ? akf2 : akf, ra);
     gemm_stage(sB[buf], seg2 ? bkf2 : bkf, rb);
   };
-  if (nkt > 0) stage(0, fetch(0));
-  __syncthreads();
-  for (int kt = 0; kt < nkt; ++kt) {
-    const int buf = kt & 1;
-    bool seg2 = false;
-    if (kt + 1 < nkt) seg2 = fetch(kt + 1);
+  auto mma_tile = [&](int buf) {
 #pragma unroll
     for (int kk = 0; kk < kBK; ++kk) {
       T a[8], b[8];
@@ -152,8 +162,61 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) gemm_kernel(const
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] += a[i] * b[j];
     }
-    if (kt + 1 < nkt) stage(buf ^ 1, seg2);
+  };
+  if constexpr (kAsync) {
+    // (the second segment's B is used unscaled on this path: beta2 must be 1)
+    auto issue = [&](int kt, int st) {
+      const bool seg2 = kt >= nkt1;
+      const T *Ab = seg2 ? reinterpret_cast<const T *>(A2) : reinterpret_cast<const T *>(A);
+      const T *Bb = seg2 ? reinterpret_cast<const T *>(B2) : reinterpret_cast<const T *>(Bm);
+      const long long am = seg2 ? g.sam2 : g.sam, ak = seg2 ? g.sak2 : g.sak;
+      const long long bn = seg2 ? g.sbn2 : g.sbn, bk = seg2 ? g.sbk2 : g.sbk;
+      const bool af = seg2 ? akf2 : akf, bf = seg2 ? bkf2 : bkf;
+      const int kb = seg2 ? (kt - nkt1) * kBK : k0 + kt * kBK;
+      const int ke = seg2 ? g.K2 : k1;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int e = threadIdx.x + 256 * r;
+        int rr = af ? e / kBK : e % kBM, kk = af ? e % kBK : e / kBM;
+        int row = m0 + rr, k = kb + kk;
+        bool ok = row < g.M && k < ke;
+        cp_async_n<sizeof(T)>(&sA[st][kk][rr], ok ? Ab + (long long)row * am + (long long)k * ak : Ab,
+                              ok ? (int)sizeof(T) : 0);
+        rr = bf ? e / kBK : e % kBN;
+        kk = bf ? e % kBK : e / kBN;
+        row = n0 + rr;
+        k = kb + kk;
+        ok = row < g.N && k < ke;
+        cp_async_n<sizeof(T)>(&sB[st][kk][rr], ok ? Bb + (long long)row * bn + (long long)k * bk : Bb,
+                              ok ? (int)sizeof(T) : 0);
+      }
+    };
+#pragma unroll
+    for (int st = 0; st < kStg - 1; ++st) {
+      if (st < nkt) issue(st, st);
+      cp_async_commit_group();
+    }
+    for (int kt = 0; kt < nkt; ++kt) {
+      cp_async_wait_group<kStg - 2>();  // tile kt has landed
+      __syncthreads();                  // ... for every thread; tile kt - 1 is free
+      const int nx = kt + kStg - 1;
+      if (nx < nkt) issue(nx, nx % kStg);
+      cp_async_commit_group();
+      mma_tile(kt % kStg);
+    }
+    cp_async_wait_group<0>();
     __syncthreads();
+  } else {
+    if (nkt > 0) stage(0, fetch(0));
+    __syncthreads();
+    for (int kt = 0; kt < nkt; ++kt) {
+      const int buf = kt & 1;
+      bool seg2 = false;
+      if (kt + 1 < nkt) seg2 = fetch(kt + 1);
+      mma_tile(buf);
+      if (kt + 1 < nkt) stage(buf ^ 1, seg2);
+      __syncthreads();
+    }
   }
 
   if (g.epi == kEpiAcc3 && g.s2 == 1 && g.s3 != 1) {

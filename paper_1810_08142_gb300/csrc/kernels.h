@@ -76,6 +76,8 @@ cudaError_t launch_triples_energy(const TriplesArgs &a, const T *W, int i, int j
                                   cudaStream_t s);
 template <typename T>
 cudaError_t launch_triples_t2(int o, int v, const double *t2, T *t2c, T *t2T, cudaStream_t s);
+template <typename T>
+cudaError_t launch_triples_negate(T *x, long long n, cudaStream_t s);
 cudaError_t launch_triples_final(const double *part, long long n, double *E, cudaStream_t s);
 
 // ---- FP64 fused ladder (DMMA)

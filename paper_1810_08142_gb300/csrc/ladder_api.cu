@@ -551,7 +551,7 @@ cudaError_t triples_run(int o, int v, int n, const double *B, const double *Bov,
   g.ldo = (int)vv;
   g.epi = kEpiStore;
   if (e == cudaSuccess) e = launch_gemm<double, double, T>(g, 1, s);
-  // Q[k][j][c][l] = (ck|jl) = v_kl^cj = sum_P Bov[P][k][c] Boo[P][j][l]
+  // Q[k][j][c][l] = (ck|jl) = v_kl^cj = sum_P Bov[P][k][c] Boo[P][j][l] (negated below)
   base(g);
   g.A = Bov;
   g.B = Boo;
@@ -591,6 +591,9 @@ cudaError_t triples_run(int o, int v, int n, const double *B, const double *Bov,
   T *t2c = std::is_same<T, double>::value ? nullptr : reinterpret_cast<T *>(ws + L.t2c);
   T *t2T = reinterpret_cast<T *>(ws + L.t2T);
   if (e == cudaSuccess) e = launch_triples_t2<T>(o, v, t2, t2c, t2T, s);
+  // the second contraction enters W with a minus sign: keep -Q, so the GEMM
+  // adds both of its K segments unscaled
+  if (e == cudaSuccess) e = launch_triples_negate<T>(Q, (long long)o * o * ov, s);
   const T *t2x = t2c ? t2c : reinterpret_cast<const T *>(t2);
   // the six orderings of P: (x, y, z) = (I[p0], I[p1], I[p2]) with I = (i, j, k),
   // and (alpha, beta, gamma) = (A[p0], A[p1], A[p2]) with A = (a, b, c)
@@ -639,7 +642,7 @@ cudaError_t triples_run(int o, int v, int n, const double *B, const double *Bov,
         g.sbn2 = o;
         g.sbk2 = 1;
         g.K2 = o;
-        g.beta2 = -1.0;
+        g.beta2 = 1.0;  // Q holds -(ck|jl)
         g.Out = W;
         g.so_batch = v3;
         g.epi = kEpiAcc3;

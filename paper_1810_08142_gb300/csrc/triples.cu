@@ -80,6 +80,13 @@ __global__ void triples_t2_kernel(long long n, int v, const double *__restrict__
   }
 }
 
+template <typename T>
+__global__ void triples_negate_kernel(T *__restrict__ x, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    x[e] = -x[e];
+}
+
 // One block: thread t sums partials t, t + 1024, ... in order, then a tree.
 __global__ void __launch_bounds__(1024) triples_final_kernel(const double *__restrict__ part, long long n,
                                                              double *__restrict__ E) {
@@ -123,6 +130,15 @@ cudaError_t launch_triples_t2(int o, int v, const double *t2, T *t2c, T *t2T, cu
 }
 template cudaError_t launch_triples_t2<double>(int, int, const double *, double *, double *, cudaStream_t);
 template cudaError_t launch_triples_t2<float>(int, int, const double *, float *, float *, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_triples_negate(T *x, long long n, cudaStream_t s) {
+  const long long blocks = std::min<long long>((n + 255) / 256, 8192);
+  if (blocks > 0) triples_negate_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(x, n);
+  return cudaGetLastError();
+}
+template cudaError_t launch_triples_negate<double>(double *, long long, cudaStream_t);
+template cudaError_t launch_triples_negate<float>(float *, long long, cudaStream_t);
 
 cudaError_t launch_triples_final(const double *part, long long n, double *E, cudaStream_t s) {
   triples_final_kernel<<<1, 1024, 0, s>>>(part, n, E);
