@@ -53,3 +53,21 @@ def test_status_strings_and_null_arguments(lib):
     assert lib.ladder_plan(4, 24, 96, 9, ctypes.byref(out)) == 1
     lib.ladder_apply.argtypes = [ctypes.c_void_p] * 5
     assert lib.ladder_apply(None, None, None, None, None) == 1
+
+
+def test_triples_workspace_size_is_host_logic(lib):
+    """ladder_triples_workspace_size needs no device: it covers the integrals,
+    W for one (i, j) and the partial sums, and rejects bad arguments."""
+    size = ctypes.c_size_t()
+    f = lib.ladder_triples_workspace_size
+    f.argtypes = [ctypes.c_int] * 4 + [ctypes.POINTER(ctypes.c_size_t)]
+    f.restype = ctypes.c_int
+    assert f(10, 120, 480, 0, ctypes.byref(size)) == 0
+    b64 = size.value
+    assert f(10, 120, 480, 1, ctypes.byref(size)) == 0
+    b32 = size.value
+    o, v = 10, 120
+    floor64 = 8 * (2 * o * v ** 3 + o ** 3 * v + o ** 2 * v ** 2 + o * v ** 3)
+    assert b64 >= floor64 and b32 >= floor64 // 2 and b32 < b64
+    assert f(0, 120, 480, 0, ctypes.byref(size)) == 1       # LADDER_EINVAL
+    assert f(10, 120, 480, 7, ctypes.byref(size)) == 1
