@@ -27,8 +27,11 @@
  *     default stream).  No call synchronises the device or allocates device
  *     memory after ladder_set_workspace.
  *   - Argument errors are returned synchronously and nothing is enqueued.
- *     Errors found on the device (a bounded wait that ran out) are recorded in
- *     a status word inside the workspace; ladder_last_device_error reads it.
+ *     Errors found on the device (a bounded wait that ran out, a NaN or an
+ *     infinity in B or tau) are recorded in a status word inside the
+ *     workspace; ladder_last_device_error reads it.
+ *   - The library reads no environment variables: every launch parameter is
+ *     set through ladder_set_tuning.
  *   - A plan is not thread safe: one host thread at a time per plan, and calls
  *     that share a plan's workspace must not overlap on the device (enqueue
  *     them on one stream).
@@ -51,15 +54,34 @@ typedef enum {
     LADDER_ECUDA = 3,       /* a CUDA runtime or driver call failed */
     LADDER_ETIMEOUT = 4,    /* a bounded device wait ran out (device status) */
     LADDER_ENOTSUP = 5,     /* mode or shape not supported on this device */
-    LADDER_EWORKSPACE = 6   /* workspace missing or too small */
+    LADDER_EWORKSPACE = 6,  /* workspace missing or too small */
+    LADDER_ENONFINITE = 7   /* an input element was NaN or infinite (device status) */
 } ladder_status;
 
 typedef enum {
     LADDER_FP64 = 0,        /* plain method: FP64 tensor-core (DMMA) path, exact to rounding */
     LADDER_BF16X3 = 1,      /* split BF16, two slices (hi, lo), three products, FP32 accumulation */
     LADDER_BF16X6 = 2,      /* split BF16, three slices, six products, FP32 accumulation */
-    LADDER_AUTO = 3         /* let the plan pick (autotuned cache, else BF16X6) */
+    LADDER_AUTO = 3,        /* let the plan pick (autotuned cache, else BF16X6) */
+    LADDER_OZAKI = 4        /* error-free split BF16: FP64-class R and E_L from the tensor cores */
 } ladder_mode;
+
+/* LADDER_OZAKI follows the error-free splitting of Ozaki, Ogita, Oishi and
+ * Rump (Numer. Algorithms 59, 2012) on the BF16 tensor cores.  Each operand
+ * row (a row (a,c) of B over P; a row (i,j) of tau+- or (a,b) of V+- over the
+ * slots of one block pair) is held as `oz_slices` (5 or 6) fixed-point BF16
+ * slices under one power-of-two scale, so every slice product is exact; the
+ * products of each slice order 0, 1, 2 accumulate in their own FP32 tensor-core
+ * accumulator over windows short enough (128 auxiliary functions, one block
+ * pair of 64 slots) that no partial sum is rounded, and the windows are
+ * summed in double-single form (about 48 bits).  The only errors left are the
+ * truncation of the slice expansion (about 2^-40 of each row's largest element
+ * with 5 slices, 2^-48 with 6) and the double-single sums.  The mode always
+ * runs the two-pass form and stores its sliced V+- tiles (S x 32 KiB per ab
+ * tile and block pair: 136 GB at o=34, v=400, N_aux=1600 with 5 slices);
+ * shapes whose tiles exceed 200 GiB return LADDER_ENOTSUP, as do
+ * ladder_backward and batch plans.  ladder_apply_dressed runs its correction
+ * in FP64 in this mode. */
 
 /* OR this into `mode` to size the workspace for ladder_backward as well
  * (the FP64 gradient with respect to B spills tiles of Gamma^{xb}_{yd}). */
@@ -69,7 +91,8 @@ typedef enum {
 #define LADDER_WITH_DRESSING 32
 
 /* Create a plan for one shape.  1 <= o <= 256, 1 <= v <= 4096, 1 <= naux <= 65536.
- * The plan owns no device memory; see ladder_workspace_size. */
+ * The plan owns no device memory; see ladder_workspace_size.  LADDER_OZAKI
+ * with LADDER_WITH_BACKWARD returns LADDER_ENOTSUP. */
 ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out);
 
 /* Launch parameters of the split-BF16 kernel (ignored by LADDER_FP64):
@@ -87,19 +110,22 @@ ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out);
  *               sliced V+- tiles stored in the workspace (2S x 16 KiB per
  *               tile and block pair), then GEMM2 from the stored tiles in
  *               chunks of up to 192 occupied pairs.  The plan picks 1 when the
- *               stored tiles take at most 128 GiB.
+ *               stored tiles take at most 128 GiB (LADDER_OZAKI: always 1).
  *   lambda_only 1: the paper's own contraction, which uses only the pair
  *               symmetry R_ij^ab = R_ji^ba (Sec. II.C), as an ablation of the
  *               +- split: the storing pass keeps (ac|bd) and (ad|bc) instead
  *               of their +- combinations, and GEMM2 runs over all o^2 ordered
  *               occupied pairs against both (twice the GEMM2 work).  Needs
  *               two_pass = 1; 0 (default) is the +- form.
+ *   oz_slices   LADDER_OZAKI only: fixed-point slices per operand, 5 (default)
+ *               or 6; 0 keeps the plan's value.  The other fields of
+ *               LADDER_OZAKI plans are fixed, except ksplit.
  * Longer chains are faster and less accurate (the tensor core's FP32
  * accumulation error grows with the MMAs per accumulator).  ladder_set_tuning
  * must come before ladder_set_workspace (the workspace size depends on
  * ksplit and two_pass); it returns LADDER_EINVAL for out-of-range values. */
 typedef struct {
-    int kc, s_pieces, flush_every, ksplit, xy_split, two_pass, lambda_only;
+    int kc, s_pieces, flush_every, ksplit, xy_split, two_pass, lambda_only, oz_slices;
 } ladder_tuning;
 ladder_status ladder_get_tuning(ladder_plan_t plan, ladder_tuning *t);
 ladder_status ladder_set_tuning(ladder_plan_t plan, const ladder_tuning *t);
@@ -120,7 +146,11 @@ ladder_status ladder_tau(ladder_plan_t plan, const double *t1, const double *t2,
 
 /* Eq. pp-Ladder-0: R_ij^ab = sum_cd (ac|bd) tau_ij^cd.  R is overwritten (not
  * accumulated); R may not alias B or tau.  The (ac|bd) integrals are formed
- * tile by tile on chip and never written to memory. */
+ * tile by tile on the tensor cores.  LADDER_FP64 and the fused split-BF16 form
+ * (two_pass = 0) never write them to memory; the two-pass form (the split-BF16
+ * default where it fits, and LADDER_OZAKI) writes their sliced symmetric and
+ * antisymmetric combinations V+- to the workspace once and reads them back in
+ * its GEMM2 pass. */
 ladder_status ladder_apply(ladder_plan_t plan, const double *B, const double *tau,
                            double *R, void *stream);
 
@@ -246,8 +276,11 @@ ladder_status ladder_apply_batched(ladder_plan_t plan, const double *const *B,
                                    const double *const *tau, double *const *R, void *stream);
 
 /* Reads and clears the device status word (synchronises `stream`).
- * Returns LADDER_OK or LADDER_ETIMEOUT; *where receives the site code of the
- * first failed wait (0 if none) when where != NULL. */
+ * Returns LADDER_OK, LADDER_ETIMEOUT (a bounded wait ran out; *where receives
+ * the site code of the first one) or LADDER_ENONFINITE (the slicing or packing
+ * of B or tau met a NaN or an infinity, site code 50; the tensor-core modes and
+ * LADDER_OZAKI check, the FP64 path lets them propagate into R).  *where is 0
+ * when nothing was recorded. */
 ladder_status ladder_last_device_error(ladder_plan_t plan, void *stream, int *where);
 
 /* Self-test of the device-side failure detection: one kernel waits, with the

@@ -18,12 +18,13 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libladder.so")
 
-LADDER_FP64, LADDER_BF16X3, LADDER_BF16X6, LADDER_AUTO = 0, 1, 2, 3
+LADDER_FP64, LADDER_BF16X3, LADDER_BF16X6, LADDER_AUTO, LADDER_OZAKI = 0, 1, 2, 3, 4
 LADDER_WITH_BACKWARD = 16
 LADDER_WITH_DRESSING = 32
-MODES = {"fp64": LADDER_FP64, "bf16x3": LADDER_BF16X3, "bf16x6": LADDER_BF16X6, "auto": LADDER_AUTO}
+MODES = {"fp64": LADDER_FP64, "bf16x3": LADDER_BF16X3, "bf16x6": LADDER_BF16X6, "auto": LADDER_AUTO,
+         "ozaki": LADDER_OZAKI}
 STATUS = {0: "LADDER_OK", 1: "LADDER_EINVAL", 2: "LADDER_ENOMEM", 3: "LADDER_ECUDA",
-          4: "LADDER_ETIMEOUT", 5: "LADDER_ENOTSUP", 6: "LADDER_EWORKSPACE"}
+          4: "LADDER_ETIMEOUT", 5: "LADDER_ENOTSUP", 6: "LADDER_EWORKSPACE", 7: "LADDER_ENONFINITE"}
 
 # every entry point that include/ladder.h declares
 EXPORTS = ("ladder_plan", "ladder_plan_mode", "ladder_get_tuning", "ladder_set_tuning", "ladder_workspace_size", "ladder_set_workspace",
@@ -38,7 +39,7 @@ class Tuning(ctypes.Structure):
     """Mirror of ladder_tuning (include/ladder.h)."""
     _fields_ = [("kc", ctypes.c_int), ("s_pieces", ctypes.c_int), ("flush_every", ctypes.c_int),
                 ("ksplit", ctypes.c_int), ("xy_split", ctypes.c_int), ("two_pass", ctypes.c_int),
-                ("lambda_only", ctypes.c_int)]
+                ("lambda_only", ctypes.c_int), ("oz_slices", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -307,7 +308,8 @@ class Ladder:
 
     def __init__(self, o: int, v: int, naux: int, mode="bf16x6", device=None, backward=False,
                  tuning=None, dressed=False):
-        """mode: "fp64", "bf16x3", "bf16x6", or "tuned" (the autotuner's cached
+        """mode: "fp64", "bf16x3", "bf16x6", "ozaki" (the error-free split, FP64-class
+        accuracy from the BF16 tensor cores), or "tuned" (the autotuner's cached
         choice of mode and launch parameters for this shape, see tune.py);
         tuning: a dict of ladder_tuning fields to override; dressed: size the
         workspace for apply_dressed (the t1-dressed term) as well."""

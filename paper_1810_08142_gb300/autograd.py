@@ -4,8 +4,10 @@ E_L(B, tau, t2) = sum_ijab R_ij^ab (2 t2_ij^ab - t2_ij^ba) with R the ladder
 term of (B, tau).  Forward: ladder_apply + ladder_energy.  Backward, with
 W = 2 t2 - t2^T (ladder_pair_combine):
     dE/dtau = transposed ladder of W           (ladder_backward)
-    dE/dB   = 2 sum Gamma B, Gamma = W^T tau    (ladder_backward, FP64)
+    dE/dB   = 2 sum Gamma B, Gamma = W^T tau    (ladder_backward)
     dE/dt2  = 2 R - R^T                         (ladder_pair_combine)
+Both ladder_backward terms run in the plan's mode (FP64, BF16X3 or BF16X6;
+the error-free mode has no adjoint).
 All arithmetic runs in the library's kernels; the incoming gradient (a
 scalar) is applied with an in-place multiply.
 """

@@ -23,6 +23,7 @@ enum : int {
   kSiteVFree = 6,
   kSiteRFull = 7,
   kSiteRFree = 8,
+  kSiteNonFinite = 50,  // an input element was NaN or infinite (not a wait)
 };
 
 __host__ __device__ inline int ppos(int n) { return n * (n + 1) / 2; }

@@ -51,6 +51,9 @@ extern "C" ladder_status ladder_energy_noalloc(int o, int v, const double *R, co
   // the reduction writes one partial per (32x32 tile of (a,b), pair (i,j))
   if (ladder::energy_partials(o, v) > kNoAllocPartials) return LADDER_ENOTSUP;
   if (!device_pointer(R) || !device_pointer(t2) || !device_pointer(E_dev)) return LADDER_EINVAL;
+  // clear an error left on this thread by an earlier, unrelated call, so that
+  // the check after the launch reports this call's launch only
+  cudaGetLastError();
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();

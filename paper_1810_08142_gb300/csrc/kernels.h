@@ -12,11 +12,12 @@ namespace ladder {
 void launch_tau(int o, int v, const double *t1, const double *t2, double *tau, cudaStream_t s);
 void launch_pack_tpm_f64(int o, int v, int K, const double *tau, double *Tp, double *Tm,
                          cudaStream_t s);
+// status (nullable): a NaN or infinite input element records kSiteNonFinite
 void launch_pack_tpm_bf16(int o, int v, int K, int nslices, int rows_p, int rows_m,
                           const double *tau, __nv_bfloat16 *Tp, __nv_bfloat16 *Tm,
-                          cudaStream_t s);
+                          cudaStream_t s, int *status = nullptr);
 void launch_split_B(int N, int v, int vp, int Np, int nslices, const double *B,
-                    __nv_bfloat16 *Bt, cudaStream_t s, bool transB = false);
+                    __nv_bfloat16 *Bt, cudaStream_t s, bool transB = false, int *status = nullptr);
 void launch_pair_combine(int o, int v, double alpha, double beta, const double *X, double *Y,
                          cudaStream_t s);
 void launch_split_pairs(int o, int v, int vp, int IJp, int nslices, const double *X,
@@ -208,6 +209,55 @@ struct BpackArgs {
   TcChunk chunks[kMaxChunks];  // lp0 = first P, np = P count, nps = padded rows
 };
 void launch_pack_b2(const BpackArgs &a, cudaStream_t s);
+
+// ---- error-free split-BF16 mode (ladder_oz.cu)
+// Every operand row is carried as S fixed-point BF16 slices under one
+// power-of-two scale per row: x = scale * sum_s x_s 2^(-8 s), x_0 an integer in
+// [-256, 256], x_s (s >= 1) integers in [-129, 129].  Slice products are then
+// exact, and a TMEM accumulator that only ever receives products of one slice
+// order p + q sums integers (in units of 2^(-8 (p + q))) that stay below 2^24
+// within an exactness window, so the tensor core's FP32 accumulation makes no
+// rounding error there.  Orders 0, 1 and 2 each have their own accumulator,
+// orders >= 3 share one (they sit 2^-24 below the result).  Windows are summed
+// in double-single form (an FP32 pair, about 48 bits) by the conversion warps.
+constexpr int kOzGroups = 4;      // TMEM accumulators per tile: orders 0, 1, 2, >= 3
+constexpr int kOzKc = 4;          // GEMM1 window: K-steps of 32 aux functions (128)
+constexpr int kOzMaxCols = 128;   // GEMM2 chunk width (four groups fill TMEM)
+struct OzArgs {
+  CUtensorMap tmA, tmB;  // fixed-point B slices [S][a][c][P]: boxes (32, 8, 16, S), (32, 8, 8, S)
+  CUtensorMap tmVl;      // stored V+- planes [tile][pair][sign][slice][128][64], box (16, 128, S)
+  __nv_bfloat16 *Vst;    // the same planes, written by pass 1
+  float *sV;             // [tile][pair][sign][128 rows] scale of each stored V+- row
+  const float *rsB;      // [vp][vp] scale of each B row (a, c) (0 for zero rows)
+  const uint8_t *T2;     // per-chunk tau+- slices (oz_pack_t2), byte offset chunks[c].t2off
+  const float *sT;       // [chunk][pair][kOzMaxCols] scale of each tau+- row
+  float2 *racc;          // double-single sums, [item][col][128 lanes]
+  int *status;
+  int o, v, vp, Np, nbp, nks;
+  int nB8, ntiles, nchunks, ksplit, racc_cols;
+  int nitems;
+  unsigned long long timeout_ns;
+  TcChunk chunks[kMaxChunks];
+};
+// tau+- of every GEMM2 chunk as fixed-point slices with one scale per (row,
+// block pair), in the per-chunk, pre-swizzled layout of pack_t2.
+struct OzPackArgs {
+  const double *tau;
+  uint8_t *T2;
+  float *sT;
+  int *status;
+  int o, v, nbp, S, nchunks;
+  TcChunk chunks[kMaxChunks];
+};
+// Row scales of B (and a non-finite check), then the fixed-point slices.
+void launch_oz_rowscale(int N, int v, int vp, const double *B, float *rs, int *status, cudaStream_t s);
+void launch_oz_split_B(int N, int v, int vp, int Np, int nslices, const double *B, const float *rs,
+                       __nv_bfloat16 *Bt, cudaStream_t s);
+void launch_oz_pack_t2(const OzPackArgs &a, cudaStream_t s);
+uint32_t oz_smem_bytes(int pass, int nslices);
+cudaError_t oz_init_attributes(int nslices);
+cudaError_t launch_oz_vstore(const OzArgs &a, int nslices, cudaStream_t s);
+cudaError_t launch_oz_gemm2(const OzArgs &a, int nslices, cudaStream_t s);
 
 // One launch of the fused kernel: a single molecule (mols == nullptr, the
 // work units are 0..nitems-1 of `one`) or a batch (work unit k is local item

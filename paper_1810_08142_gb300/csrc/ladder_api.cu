@@ -27,10 +27,15 @@ struct Layout {
   size_t Vg = 0, T2 = 0;                       // two-pass form: stored V+- tiles, tau+- per chunk
   size_t gG = 0, gT2 = 0, gacc2 = 0;           // two-pass dB: Gamma planes, B per chunk, sums
   size_t dBd = 0, dG = 0, dX = 0, dY = 0;      // t1 dressing: B - mbar, (kc|ld), X, Y
+  size_t ozRs = 0, ozSV = 0, ozST = 0;         // error-free mode: B row scales, V+- and tau+- row scales
 };
 
 // Two-pass form: at most this many bytes of stored V+- tiles by default.
 constexpr double kVStoreDefaultCap = 128.0 * (1ull << 30);
+// The error-free mode has no fused form: shapes whose stored V+- slices
+// exceed this are not supported.
+constexpr double kVStoreOzCap = 200.0 * (1ull << 30);
+constexpr int kOzDefaultSlices = 5;
 
 int tc_slices(int mode) { return mode == LADDER_BF16X3 ? 2 : 3; }
 
@@ -97,6 +102,7 @@ struct ladder_plan_s {
   // ranges per tile of the storing pass
   int two_pass = 0, vsplit = 1, racc_cols_v = 0, nplus = 0, wplus = 0, wminus = 0;
   int lam_only = 0;  // the paper's lambda-only contraction (two-pass form only)
+  int oz_slices = kOzDefaultSlices;  // error-free mode: fixed-point slices per operand
   bool last_two_pass = false;
   std::vector<TcChunk> chunks_v;
   CUtensorMap tmA, tmB, tmTp, tmTm, tmVl;
@@ -230,8 +236,10 @@ std::vector<TcChunk> make_sign_chunks(int o, int maxcols, int &nplus, int &wplus
   return out;
 }
 
-bool dev_ptr_ok(const void *p) {
-  if (!p || (reinterpret_cast<uintptr_t>(p) & 15u)) return false;
+// A device (or managed) pointer aligned to `align` bytes (16 for arrays, 8 for
+// a single double).
+bool dev_ptr_ok(const void *p, uintptr_t align = 16) {
+  if (!p || (reinterpret_cast<uintptr_t>(p) & (align - 1))) return false;
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
@@ -258,7 +266,32 @@ void compute_layout(ladder_plan_s *pl) {
   off += kAlign;
   L.energy = off;
   off = align_up(off + energy_partials(pl->o, pl->v) * sizeof(double));
-  if (pl->mode == LADDER_FP64) {
+  if (pl->mode == LADDER_OZAKI) {
+    // fixed-point B slices and row scales, V+- planes and their row scales,
+    // tau+- per GEMM2 chunk and its row scales, the double-single sums
+    const size_t S = pl->S;
+    L.Bt = off;
+    off = align_up(off + S * pl->vp * pl->vp * pl->Np * 2, 1024);
+    L.ozRs = off;
+    off = align_up(off + (size_t)pl->vp * pl->vp * sizeof(float));
+    L.slab = off;
+    off = align_up(off + (size_t)pl->ntiles_tc * pl->chunks_v.size() * pl->ksplit * 128 * pl->racc_cols_v *
+                             sizeof(float2),
+                   1024);
+    L.Vg = off;
+    off = align_up(off + (size_t)pl->ntiles_tc * pl->nbp * 2 * S * 128 * SLOTS * 2, 1024);
+    L.ozSV = off;
+    off = align_up(off + (size_t)pl->ntiles_tc * pl->nbp * 2 * 128 * sizeof(float));
+    L.T2 = off;
+    size_t t2 = 0;
+    for (auto &c : pl->chunks_v) {
+      c.t2off = (long long)t2;
+      t2 += (size_t)S * (c.nps + c.nms) * pl->K * 2;
+    }
+    off = align_up(off + t2, 1024);
+    L.ozST = off;
+    off = align_up(off + pl->chunks_v.size() * pl->nbp * kOzMaxCols * sizeof(float));
+  } else if (pl->mode == LADDER_FP64) {
     L.Tp = off;
     off = align_up(off + (size_t)pl->nlp * pl->K * sizeof(double));
     L.Tm = off;
@@ -307,7 +340,6 @@ void compute_layout(ladder_plan_s *pl) {
     const double gbytes = (double)pl->g_ntiles * nq * S * 128 * SLOTS * 2;
     pl->g2 = gbytes <= 64.0 * (1ull << 30) &&
              (pl->N + kTcMaxColsV - 1) / kTcMaxColsV <= kMaxChunks;
-    if (const char *e = getenv("LADDER_DB2")) pl->g2 = pl->g2 && atoi(e) != 0;
     if (pl->g2) {
       // aux chunks of up to kTcMaxColsV rows, balanced
       pl->g2_chunks.clear();
@@ -348,7 +380,7 @@ void compute_layout(ladder_plan_s *pl) {
     // t1 dressing (dress.cu): Bd [N][v][v] f64, then the correction in T
     // (double for FP64, float for the split modes): G [(k,l)][(c,d)],
     // X partials [dx_ksplit][(i,j)][(k,l)], Y [(i,j,k)][b]
-    const size_t tsz = pl->mode == LADDER_FP64 ? sizeof(double) : sizeof(float);
+    const size_t tsz = (pl->mode == LADDER_FP64 || pl->mode == LADDER_OZAKI) ? sizeof(double) : sizeof(float);
     const size_t o = pl->o, v = pl->v, oo = o * o;
     const long long xt = (long long)((oo + 127) / 128) * ((oo + 127) / 128);
     int ks = (int)((8LL * pl->sm_count + xt - 1) / xt);
@@ -373,8 +405,7 @@ void compute_layout(ladder_plan_s *pl) {
 // only the range limit (the batch itself fills the SMs).
 static int auto_vsplit(const ladder_plan_s *pl, bool batch_member) {
   int vs = batch_member ? 1 : (8 * pl->sm_count + pl->ntiles_tc - 1) / pl->ntiles_tc;
-  if (const char *e = getenv("LADDER_VSPLIT")) vs = atoi(e);
-  else vs = std::max(vs, (pl->nbp + 127) / 128);
+  vs = std::max(vs, (pl->nbp + 127) / 128);
   return std::max(1, std::min(vs, pl->nbp));
 }
 
@@ -673,6 +704,7 @@ const char *ladder_status_string(ladder_status s) {
     case LADDER_ETIMEOUT: return "bounded device wait ran out";
     case LADDER_ENOTSUP: return "mode or shape not supported";
     case LADDER_EWORKSPACE: return "workspace missing or too small";
+    case LADDER_ENONFINITE: return "an input holds a NaN or an infinity";
   }
   return "unknown status";
 }
@@ -694,8 +726,9 @@ static int auto_ksplit(const ladder_plan_s *pl) {
 static ladder_status init_plan(ladder_plan_s *pl, int o, int v, int naux, int mode,
                                bool with_backward, bool batch_member, bool with_dressing = false) {
   if (o < 1 || o > 256 || v < 1 || v > 4096 || naux < 1 || naux > 65536) return LADDER_EINVAL;
-  if (mode < LADDER_FP64 || mode > LADDER_AUTO) return LADDER_EINVAL;
+  if (mode < LADDER_FP64 || mode > LADDER_OZAKI) return LADDER_EINVAL;
   if (mode == LADDER_AUTO) mode = LADDER_BF16X6;
+  if (mode == LADDER_OZAKI && (batch_member || with_backward)) return LADDER_ENOTSUP;
   pl->o = o;
   pl->v = v;
   pl->N = naux;
@@ -715,7 +748,26 @@ static ladder_status init_plan(ladder_plan_s *pl, int o, int v, int naux, int mo
     return LADDER_ECUDA;
   }
   pl->chunks64 = make_chunks(o, kFp64LamTile);
-  if (mode != LADDER_FP64) {
+  if (mode == LADDER_OZAKI) {
+    // error-free split: always the two-pass form, GEMM2 chunks of <= 128 pairs
+    pl->S = pl->oz_slices;
+    pl->Np = (naux + 31) / 32 * 32;
+    pl->chunks_v = make_sign_chunks(o, kOzMaxCols, pl->nplus, pl->wplus, pl->wminus);
+    pl->racc_cols_v = 0;
+    for (auto &c : pl->chunks_v) pl->racc_cols_v = std::max(pl->racc_cols_v, c.nps + c.nms);
+    const int nA = pl->vp / 16, nB8 = pl->vp / CB;
+    pl->ntiles_tc = 0;
+    for (int i = 0; i < nA; ++i) pl->ntiles_tc += nB8 - 2 * i;
+    pl->two_pass = 1;
+    pl->ksplit = auto_ksplit(pl);
+    pl->vsplit = auto_vsplit(pl, false);
+    const double vbytes = (double)pl->ntiles_tc * pl->nbp * 2 * 6 * 128 * SLOTS * 2;
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, pl->device);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, pl->device);
+    if ((int)pl->chunks_v.size() > kMaxChunks || vbytes * pl->S / 6 > kVStoreOzCap || major != 10 || minor != 3)
+      return LADDER_ENOTSUP;
+  } else if (mode != LADDER_FP64) {
     pl->S = tc_slices(mode);
     pl->Np = (naux + 31) / 32 * 32;
     pl->chunks_tc = make_tc_chunks(o, kTcMaxCols);
@@ -732,8 +784,6 @@ static ladder_status init_plan(ladder_plan_s *pl, int o, int v, int naux, int mo
     // (o=10, v=120: 1.60 vs 2.44 ms)
     const double vbytes = (double)pl->ntiles_tc * pl->nbp * 2 * pl->S * 128 * SLOTS * 2;
     pl->two_pass = (!batch_member && vbytes <= kVStoreDefaultCap) ? 1 : 0;
-    if (!batch_member)
-      if (const char *e = getenv("LADDER_TWOPASS")) pl->two_pass = atoi(e) != 0;
     pl->ksplit = batch_member ? 1 : auto_ksplit(pl);
     pl->vsplit = auto_vsplit(pl, batch_member);
     // FP32 accumulation chains (see ladder_tc.cu).  GEMM1: with separate
@@ -744,21 +794,11 @@ static ladder_status init_plan(ladder_plan_s *pl, int o, int v, int naux, int mo
     pl->xy_split = 1;
     pl->kc = pl->S == 2 ? 16 : 4;
     pl->s_pieces = pl->S == 2 ? 4 : 2;
-    if (const char *e = getenv("LADDER_XYSPLIT")) pl->xy_split = atoi(e) != 0;
-    if (!pl->xy_split) pl->kc = pl->S == 2 ? 4 : 1;
     // GEMM2's FP32 running sum R takes flush_every S accumulators before a
     // flush into the double-single sums.  At o=34, v=400 (BF16X6, two-pass)
     // flushing every 16 / 32 / 64 / 128 S gave pass 2 113 / 101 / 94 / 91 ms
     // and R errors 5.05 / 5.07 / 5.08 / 5.29e-7: 64 keeps the error.
     pl->flush_every = 64;
-    if (const char *e = getenv("LADDER_KC")) pl->kc = std::max(1, atoi(e));
-    if (const char *e = getenv("LADDER_SPIECES")) {
-      const int sp = atoi(e);
-      if (sp == 1 || sp == 2 || sp == 4) pl->s_pieces = sp;
-    }
-    if (const char *e = getenv("LADDER_FLUSH")) pl->flush_every = std::max(1, atoi(e));
-    if (!batch_member)
-      if (const char *e = getenv("LADDER_KSPLIT")) pl->ksplit = std::max(1, std::min(atoi(e), pl->nbp));
     int major = 0, minor = 0;
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, pl->device);
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, pl->device);
@@ -808,12 +848,23 @@ ladder_status ladder_get_tuning(ladder_plan_t pl, ladder_tuning *t) {
   t->xy_split = pl->xy_split;
   t->two_pass = pl->two_pass;
   t->lambda_only = pl->lam_only;
+  t->oz_slices = pl->mode == LADDER_OZAKI ? pl->oz_slices : 0;
   return LADDER_OK;
 }
 
 ladder_status ladder_set_tuning(ladder_plan_t pl, const ladder_tuning *t) {
   if (!pl || !t || pl->batched || pl->ws) return LADDER_EINVAL;
   if (pl->mode == LADDER_FP64) return LADDER_OK;
+  if (pl->mode == LADDER_OZAKI) {
+    // only the slice count and the block-pair split apply
+    if ((t->oz_slices != 0 && t->oz_slices != 5 && t->oz_slices != 6) || t->ksplit < 0 || t->ksplit > pl->nbp ||
+        t->two_pass != 1 || t->lambda_only != 0)
+      return LADDER_EINVAL;
+    if (t->oz_slices) pl->oz_slices = pl->S = t->oz_slices;
+    pl->ksplit = t->ksplit ? t->ksplit : auto_ksplit(pl);
+    compute_layout(pl);
+    return LADDER_OK;
+  }
   if (t->kc < 1 || t->kc > 64 || !(t->s_pieces == 1 || t->s_pieces == 2 || t->s_pieces == 4) ||
       t->flush_every < 1 || t->flush_every > 4096 || t->ksplit < 0 || t->ksplit > pl->nbp ||
       (t->xy_split != 0 && t->xy_split != 1) || (t->two_pass != 0 && t->two_pass != 1) ||
@@ -849,6 +900,18 @@ ladder_status ladder_workspace_size(ladder_plan_t pl, size_t *bytes) {
 
 static ladder_status encode_maps(ladder_plan_s *pl, char *w) {
   if (pl->mode == LADDER_FP64) return LADDER_OK;
+  if (pl->mode == LADDER_OZAKI) {
+    const uint64_t S = pl->S;
+    const uint64_t planes = (uint64_t)pl->ntiles_tc * pl->nbp * 2 * S;
+    const bool ok =
+        encode4d(&pl->tmA, w + pl->lay.Bt, pl->Np, pl->vp, pl->vp, S, 32, 8, 16, (uint32_t)S,
+                 CU_TENSOR_MAP_SWIZZLE_64B) &&
+        encode4d(&pl->tmB, w + pl->lay.Bt, pl->Np, pl->vp, pl->vp, S, 32, 8, 8, (uint32_t)S,
+                 CU_TENSOR_MAP_SWIZZLE_64B) &&
+        encode3d(&pl->tmVl, w + pl->lay.Vg, SLOTS, 128, planes, 16, 128, (uint32_t)S, CU_TENSOR_MAP_SWIZZLE_32B);
+    if (!ok) return LADDER_ECUDA;
+    return cuda_status(oz_init_attributes(pl->S));
+  }
   const uint64_t S = pl->S;
   const bool ok =
       encode4d(&pl->tmA, w + pl->lay.Bt, pl->Np, pl->vp, pl->vp, S, 32, 8, 16, (uint32_t)S,
@@ -1008,12 +1071,13 @@ static TcArgs tc_args(const ladder_plan_s *pl, double *R, int *status) {
   return a;
 }
 
+// status: the device status word that a NaN or infinite input is reported to
 static void tc_prep(ladder_plan_t pl, const double *B, const double *tau, cudaStream_t s,
-                    bool transB) {
+                    bool transB, int *status) {
   auto *Bt = ws_at<__nv_bfloat16>(pl, pl->lay.Bt);
   auto *Tp = ws_at<__nv_bfloat16>(pl, pl->lay.Tp);
   auto *Tm = ws_at<__nv_bfloat16>(pl, pl->lay.Tm);
-  launch_split_B(pl->N, pl->v, pl->vp, pl->Np, pl->S, B, Bt, s, transB);
+  launch_split_B(pl->N, pl->v, pl->vp, pl->Np, pl->S, B, Bt, s, transB, status);
   if (pl->lam_only && pl->two_pass) {
     // the lambda-only GEMM2 operand comes straight from tau (pack_t2_lam)
     T2LamArgs t;
@@ -1029,7 +1093,7 @@ static void tc_prep(ladder_plan_t pl, const double *B, const double *tau, cudaSt
     launch_pack_t2_lam(t, s);
     return;
   }
-  launch_pack_tpm_bf16(pl->o, pl->v, pl->K, pl->S, pl->nlp, std::max(pl->nlm, 1), tau, Tp, Tm, s);
+  launch_pack_tpm_bf16(pl->o, pl->v, pl->K, pl->S, pl->nlp, std::max(pl->nlm, 1), tau, Tp, Tm, s, status);
 }
 
 // Arguments of the storing pass (GEMM1 + V+- store) of the two-pass form.
@@ -1076,10 +1140,10 @@ static void pack_t2(const ladder_plan_s *pl, cudaStream_t s) {
 static ladder_status apply_tc(ladder_plan_t pl, const double *B, const double *tau, double *R,
                               cudaStream_t s, bool transB = false) {
   mark(pl, 0, s);
-  tc_prep(pl, B, tau, s, transB);
+  int *status = ws_at<int>(pl, pl->lay.status);
+  tc_prep(pl, B, tau, s, transB, status);
   ladder_status st = cuda_status(cudaGetLastError());
   if (st != LADDER_OK) return st;
-  int *status = ws_at<int>(pl, pl->lay.status);
   TcLaunch L;
   std::memset(&L, 0, sizeof(L));
   pl->last_two_pass = pl->two_pass != 0;
@@ -1117,6 +1181,81 @@ static ladder_status apply_tc(ladder_plan_t pl, const double *B, const double *t
   return st;
 }
 
+// The error-free mode: operand preparation (B row scales and fixed-point
+// slices, tau+- slices per GEMM2 chunk), the storing pass, the GEMM2 pass and
+// the unpack of the two-pass form.
+static ladder_status apply_oz(ladder_plan_t pl, const double *B, const double *tau, double *R,
+                              cudaStream_t s) {
+  pl->last_two_pass = true;
+  mark(pl, 0, s);
+  int *status = ws_at<int>(pl, pl->lay.status);
+  float *rsB = ws_at<float>(pl, pl->lay.ozRs);
+  launch_oz_rowscale(pl->N, pl->v, pl->vp, B, rsB, status, s);
+  launch_oz_split_B(pl->N, pl->v, pl->vp, pl->Np, pl->S, B, rsB, ws_at<__nv_bfloat16>(pl, pl->lay.Bt), s);
+  OzPackArgs pk;
+  std::memset(&pk, 0, sizeof(pk));
+  pk.tau = tau;
+  pk.T2 = ws_at<uint8_t>(pl, pl->lay.T2);
+  pk.sT = ws_at<float>(pl, pl->lay.ozST);
+  pk.status = status;
+  pk.o = pl->o;
+  pk.v = pl->v;
+  pk.nbp = pl->nbp;
+  pk.S = pl->S;
+  pk.nchunks = (int)pl->chunks_v.size();
+  for (int c = 0; c < pk.nchunks; ++c) pk.chunks[c] = pl->chunks_v[c];
+  launch_oz_pack_t2(pk, s);
+  ladder_status st = cuda_status(cudaGetLastError());
+  if (st != LADDER_OK) return st;
+  OzArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.tmA = pl->tmA;
+  a.tmB = pl->tmB;
+  a.tmVl = pl->tmVl;
+  a.Vst = ws_at<__nv_bfloat16>(pl, pl->lay.Vg);
+  a.sV = ws_at<float>(pl, pl->lay.ozSV);
+  a.rsB = rsB;
+  a.T2 = ws_at<uint8_t>(pl, pl->lay.T2);
+  a.sT = ws_at<float>(pl, pl->lay.ozST);
+  a.status = status;
+  a.o = pl->o;
+  a.v = pl->v;
+  a.vp = pl->vp;
+  a.Np = pl->Np;
+  a.nbp = pl->nbp;
+  a.nks = pl->Np / 32;
+  a.nB8 = pl->vp / CB;
+  a.ntiles = pl->ntiles_tc;
+  a.nchunks = (int)pl->chunks_v.size();
+  for (int c = 0; c < a.nchunks; ++c) a.chunks[c] = pl->chunks_v[c];
+  a.racc_cols = pl->racc_cols_v;
+  // every single wait is far shorter than a pass; 2 s plus 20x a work unit's estimate
+  const double unit_flops = 2.0 * 128.0 * 64.0 * 2.0 * pl->Np * 21.0 * ((double)pl->nbp / pl->vsplit);
+  a.timeout_ns = (unsigned long long)(2e9 + 20.0 * unit_flops / 4e12 * 1e9);
+  // pass 1: GEMM1 of every (tile, block pair), V+- slices and scales stored
+  a.ksplit = pl->vsplit;
+  a.nitems = a.ntiles * pl->vsplit;
+  a.racc = nullptr;
+  mark(pl, 1, s);
+  st = cuda_status(launch_oz_vstore(a, pl->S, s));
+  mark(pl, 4, s);
+  // pass 2: GEMM2 per (tile, chunk, block-pair range)
+  a.ksplit = pl->ksplit;
+  a.nitems = a.ntiles * a.nchunks * pl->ksplit;
+  a.racc = ws_at<float2>(pl, pl->lay.slab);
+  if (st == LADDER_OK) st = cuda_status(launch_oz_gemm2(a, pl->S, s));
+  mark(pl, 2, s);
+  if (st == LADDER_OK) {
+    TcLaunch L;
+    std::memset(&L, 0, sizeof(L));
+    L.one = pass2_args(pl, R, status);
+    L.one.ntiles = pl->ntiles_tc;
+    st = cuda_status(launch_unpack2(L, pl->ntiles_tc * pl->nplus, s));
+  }
+  mark(pl, 3, s);
+  return st;
+}
+
 ladder_status ladder_apply(ladder_plan_t pl, const double *B, const double *tau, double *R,
                            void *stream) {
   if (!pl || pl->batched) return LADDER_EINVAL;
@@ -1125,6 +1264,7 @@ ladder_status ladder_apply(ladder_plan_t pl, const double *B, const double *tau,
     return LADDER_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (pl->mode == LADDER_FP64) return apply_fp64(pl, B, tau, R, s);
+  if (pl->mode == LADDER_OZAKI) return apply_oz(pl, B, tau, R, s);
   return apply_tc(pl, B, tau, R, s);
 }
 
@@ -1136,7 +1276,8 @@ ladder_status ladder_apply_dressed(ladder_plan_t pl, const double *B, const doub
       R == B || R == tau || R == Bov || R == t1)
     return LADDER_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const bool f64 = pl->mode == LADDER_FP64;
+  // the error-free mode keeps FP64 for the dressing as the FP64 path does
+  const bool f64 = pl->mode == LADDER_FP64 || pl->mode == LADDER_OZAKI;
   mark(pl, 5, s);
   double *Bd = ws_at<double>(pl, pl->lay.dBd);
   // Bd[P][b][d] = B[P][b][d] - sum_k t1[k][b] Bov[P][k][d]: one v x v product per P, K = o
@@ -1162,7 +1303,9 @@ ladder_status ladder_apply_dressed(ladder_plan_t pl, const double *B, const doub
                                      : launch_gemm<double, double, float>(g, pl->N, s));
   if (st != LADDER_OK) return st;
   mark(pl, 6, s);
-  st = f64 ? apply_fp64(pl, Bd, tau, R, s) : apply_tc(pl, Bd, tau, R, s);
+  st = pl->mode == LADDER_FP64 ? apply_fp64(pl, Bd, tau, R, s)
+       : pl->mode == LADDER_OZAKI ? apply_oz(pl, Bd, tau, R, s)
+                                  : apply_tc(pl, Bd, tau, R, s);
   if (st != LADDER_OK) return st;
   st = f64 ? dress_correct<double>(pl, Bov, t1, tau, R, s) : dress_correct<float>(pl, Bov, t1, tau, R, s);
   mark(pl, 7, s);
@@ -1201,7 +1344,7 @@ ladder_status ladder_energy(ladder_plan_t pl, const double *R, const double *t2,
                             void *stream) {
   if (!pl || pl->batched) return LADDER_EINVAL;
   if (!pl->ws) return LADDER_EWORKSPACE;
-  if (!dev_ptr_ok(R) || !dev_ptr_ok(t2) || !E_dev) return LADDER_EINVAL;
+  if (!dev_ptr_ok(R) || !dev_ptr_ok(t2) || !dev_ptr_ok(E_dev, 8)) return LADDER_EINVAL;
   launch_energy(pl->o, pl->v, R, t2, ws_at<double>(pl, pl->lay.energy), E_dev,
                 static_cast<cudaStream_t>(stream));
   return cuda_status(cudaGetLastError());
@@ -1215,6 +1358,7 @@ ladder_status ladder_backward(ladder_plan_t pl, const double *B, const double *t
   if (dtau && (!dev_ptr_ok(dtau) || dtau == W || dtau == tau || dtau == B)) return LADDER_EINVAL;
   if (dB && (!dev_ptr_ok(dB) || dB == B)) return LADDER_EINVAL;
   if (dB && !pl->backward) return LADDER_EWORKSPACE;
+  if (pl->mode == LADDER_OZAKI) return LADDER_ENOTSUP;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (dtau) {
     // transposed ladder: dtau = sum_ab W_ij^ab (ac|bd), i.e. the ladder of W
@@ -1464,13 +1608,12 @@ ladder_status ladder_plan_batched(int n, const int *o, const int *v, const int *
   *out = nullptr;
   if (mode & LADDER_WITH_BACKWARD) return LADDER_ENOTSUP;
   if (mode == LADDER_AUTO) mode = LADDER_BF16X6;
-  if (mode != LADDER_BF16X3 && mode != LADDER_BF16X6) return LADDER_ENOTSUP;
+  if (mode != LADDER_BF16X3 && mode != LADDER_BF16X6) return LADDER_ENOTSUP;  // incl. LADDER_OZAKI
   ladder_plan_s *pl = new (std::nothrow) ladder_plan_s();
   if (!pl) return LADDER_ENOMEM;
   pl->batched = true;
   pl->mode = mode;
   pl->S = tc_slices(mode);
-  const char *tp_env = getenv("LADDER_TWOPASS");
   double vsum = 0.0;
   for (int m = 0; m < n; ++m) {
     ladder_plan_s *sp = new (std::nothrow) ladder_plan_s();
@@ -1489,8 +1632,7 @@ ladder_status ladder_plan_batched(int n, const int *o, const int *v, const int *
     // members whose fused form would recompute GEMM1 per chunk take the
     // two-pass form while the batch's stored tiles fit the cap
     const double vb = member_vbytes(sp);
-    // LADDER_TWOPASS=1 puts every member that fits in the two-pass form, 0 none
-    const bool tp = (tp_env ? atoi(tp_env) != 0 : sp->chunks_tc.size() > 1) && vsum + vb <= kVStoreBatchCap;
+    const bool tp = sp->chunks_tc.size() > 1 && vsum + vb <= kVStoreBatchCap;
     if (tp) {
       vsum += vb;
       set_member_form(sp, true);
@@ -1593,7 +1735,7 @@ ladder_status ladder_apply_batched(ladder_plan_t pl, const double *const *B,
     // launch over their cost-sorted work units; two-pass members in one
     // storing launch and one GEMM2 launch over all of them; the unpacks
     for (size_t m = 0; m < n; ++m) {
-      tc_prep(pl->subs[m], B[m], tau[m], c, false);
+      tc_prep(pl->subs[m], B[m], tau[m], c, false, status);
       if (pl->subs[m]->two_pass) pack_t2(pl->subs[m], c);
     }
     if (L.nitems) launch_ladder_tc(L, pl->S, std::min(L.nitems, pl->sm_count), c);
@@ -1631,6 +1773,7 @@ ladder_status ladder_last_device_error(ladder_plan_t pl, void *stream, int *wher
       cudaMemsetAsync(d, 0, sizeof(int), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
     return cuda_status(cudaErrorUnknown);
   if (where) *where = h;
+  if (h == kSiteNonFinite) return LADDER_ENONFINITE;
   return h == 0 ? LADDER_OK : LADDER_ETIMEOUT;
 }
 

@@ -1,0 +1,885 @@
+// Error-free split-BF16 ladder (LADDER_OZAKI): the two-pass form of the
+// tensor-core path with an error-free splitting of every operand, after the
+// scheme of Ozaki, Ogita, Oishi and Rump (Numer. Algorithms 59, 2012), so that
+// R and E_L come out with FP64-class accuracy from BF16 tensor-core products.
+//
+// R_ij^ab = sum_cd (ac|bd) tau_ij^cd (Eq. pp-Ladder-0), (ac|bd) = sum_P
+// B^P_ac B^P_bd (Eq. RIM), in the slot form of the symmetric / antisymmetric
+// pair scheme (Sec. II.C) used by the other tensor-core kernels: virtual
+// indices in blocks of 8, block pairs k <= l, V+-_ab[(c,d)] = (ac|bd) +-
+// (ad|bc), R+- = sum T+- V+-.
+//
+// Splitting.  A row x of an operand (the K index running along it) is held as
+// S slices of fixed-point numbers under one power-of-two scale per row:
+//   x = scale * sum_s x_s 2^(-8 s),  x_0 in [-256, 256], x_s in [-129, 129],
+// each x_s an integer, stored as the BF16 number x_s 2^(-8 s) (exact: at most
+// 8 significant bits).  A product of slices p and q is exact in FP32 and is an
+// integer multiple of 2^(-8 (p + q)) below 2^16 of that unit.
+//
+// Accumulation.  The tensor core rounds its FP32 accumulator with a bias, so a
+// sum of products is exact only while every partial sum is representable.  A
+// TMEM accumulator here receives products of one slice order p + q only
+// (orders 0, 1 and 2 each in their own, orders >= 3 together, 2^-24 below the
+// result where rounding no longer matters), over an exactness window short
+// enough that its partial sums stay below 2^24 units:
+//   GEMM1 (K = aux functions): windows of 128 (4 K-steps of 32); every row of
+//         B has one scale over all P, so windows add without rescaling;
+//   GEMM2 (K = slots): one block pair (64 slots) per window; V+- and tau+-
+//         rows have one scale per block pair, applied when the window's four
+//         accumulators are drained.
+// The conversion warps drain each window's four accumulators into a
+// double-single sum (an FP32 pair kept with TwoSum, about 48 bits).
+//
+// Pass 1 (oz_vstore_kernel): per (ab tile, block pair): X = (ac|bd) and
+// Y = (ad|bc) windows alternate between two TMEM halves (X drains while Y's
+// MMAs run); at the end V+- = X +- Y' (Y transposed across lanes), cut into S
+// fixed-point slices with one scale per (ab row, block pair), stored to the
+// workspace with their scales.  Pass 2 (oz_gemm2_kernel): per (tile, chunk of
+// <= 128 occupied pairs of one sign, block-pair range): the S x S slice
+// products of every 16-slot piece with p + q < S, drained once per block
+// pair.  The unpack kernel of the two-pass form then writes R.
+//
+// Warp roles (576 threads): warp 0 TMA producer, warp 1 MMA issuer (one
+// thread), warps 2-17 conversion (four per TMEM lane quadrant, each owning a
+// quarter of the columns).
+#include "kernels.h"
+#include "tc_ptx.cuh"
+
+namespace ladder {
+namespace {
+using namespace tc;
+
+constexpr int kThreads = 576;
+constexpr int kEpi = 512;
+constexpr int KSTEP = 32;                             // aux functions per GEMM1 stage
+constexpr uint32_t A_TILE = 128u * KSTEP * 2u;        // 8 KB: rows (a,c), 64-byte rows
+constexpr uint32_t B_TILE = 64u * KSTEP * 2u;         // 4 KB: rows (b,d)
+constexpr int TPIECE = 16;                            // slots per GEMM2 piece
+constexpr uint32_t VP_PLANE = 128u * TPIECE * 2u;     // 4 KB: 128 ab rows x 16 slots
+constexpr uint32_t kSmemBudget = 230400u;             // ring bytes available per CTA
+
+// round to the nearest integer (ties to even) for |x| <= 2^22, on the FP32 pipe
+__device__ __forceinline__ float rint_small(float x) {
+  return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f);
+}
+
+// s + e = a + b exactly (Knuth's TwoSum)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Value of one exactness window from its four order accumulators, as a
+// double-single (h, l) renormalised so that |l| <= ulp(h) / 2.  In units of
+// the order-0 products: h + e = g0 + g1 exactly (TwoSum); e is a multiple of
+// 2^-8 below 1/2 and g2 a multiple of 2^-16 below 2^7, so e + g2 is exact in
+// FP32; the TwoSum with h then leaves a remainder of at most ulp(h) / 2, to
+// which the tail orders (2^-24 below h) are added with a rounding 2^-48 below
+// h.  (Adding g2 straight into the low word would round it 2^-40 below h.)
+__device__ __forceinline__ void window_value(float g0, float g1, float g2, float g3, float &h, float &l) {
+  float h0, e;
+  two_sum(g0, g1, h0, e);
+  two_sum(h0, __fadd_rn(e, g2), h, l);
+  l = __fadd_rn(l, g3);
+}
+
+// acc (H, L) += (h, l)
+__device__ __forceinline__ void ds_acc(float2 &acc, float h, float l) {
+  float s, e;
+  two_sum(acc.x, h, s, e);
+  acc.x = s;
+  acc.y = __fadd_rn(acc.y, __fadd_rn(l, e));
+}
+
+// 2^e as a float for -126 <= e <= 127
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+
+// Exponent E with m < 2^E for m > 0 (m finite, normal).
+__device__ __forceinline__ int exp_above(float m) { return ((__float_as_int(m) >> 23) & 0xff) - 126; }
+
+// 8x8 transpose across the 8 lanes of a group (lane x holds row x on entry,
+// column x on exit).
+__device__ __forceinline__ void transpose8(float (&r)[8], int x) {
+#pragma unroll
+  for (int s = 1; s < 8; s <<= 1) {
+    const bool up = (x & s) != 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (j & s) continue;
+      const float send = up ? r[j] : r[j ^ s];
+      const float recv = __shfl_xor_sync(0xffffffffu, send, s);
+      if (up)
+        r[j] = recv;
+      else
+        r[j ^ s] = recv;
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t desc_hi(uint32_t sbo_bytes, uint32_t layout) {
+  return ((sbo_bytes >> 4) & 0x3FFFu) | (1u << 14) | (layout << 29);
+}
+__device__ __forceinline__ uint64_t desc64(uint32_t saddr, uint32_t hi) {
+  return ((uint64_t)hi << 32) | (uint64_t)(((saddr >> 4) & 0x3FFFu) | (1u << 16));
+}
+
+struct DrainWatch {
+  int zero = 0;
+  Watchdog wd;
+  __device__ DrainWatch(int *status, uint64_t deadline) : wd{status, &zero, deadline} {}
+};
+
+// Work unit (tile, chunk, range) as in the other tensor-core kernels: tile =
+// (a 16-block iA, b 8-block jB >= 2 iA), range [p0, p1) of block pairs.
+struct Item {
+  int tile, ch, A0, B0, p0, p1;
+  TcChunk CH;
+  float2 *racc;
+};
+__device__ __forceinline__ Item decode(const OzArgs &A, int slot, int nchunks) {
+  Item I;
+  const int ksl = slot % A.ksplit;
+  const int tc = slot / A.ksplit;
+  const int tile = tc / nchunks;
+  I.ch = tc % nchunks;
+  int iA = 0, t = tile;
+  while (t >= A.nB8 - 2 * iA) {
+    t -= A.nB8 - 2 * iA;
+    ++iA;
+  }
+  I.tile = tile;
+  I.A0 = iA * 16;
+  I.B0 = (2 * iA + t) * CB;
+  I.CH = A.chunks[I.ch];
+  I.p0 = (int)((long long)A.nbp * ksl / A.ksplit);
+  I.p1 = (int)((long long)A.nbp * (ksl + 1) / A.ksplit);
+  I.racc = A.racc ? A.racc + (size_t)slot * 128 * A.racc_cols : nullptr;
+  return I;
+}
+
+struct Bars {
+  uint32_t base;
+  int stages;
+  __device__ uint32_t full(int s) const { return base + 8u * s; }
+  __device__ uint32_t empty(int s) const { return base + 8u * (stages + s); }
+  __device__ uint32_t cfull(int b) const { return base + 8u * (2 * stages + b); }
+  __device__ uint32_t cfree(int b) const { return base + 8u * (2 * stages + 2 + b); }
+  __device__ uint32_t done() const { return base + 8u * (2 * stages + 4); }
+  static constexpr int kCount = 5;  // + 2 * stages
+};
+
+template <int S>
+struct Cfg1 {
+  static constexpr uint32_t kStage = (uint32_t)S * (A_TILE + B_TILE);
+  static constexpr int kStages = (int)(kSmemBudget / kStage);
+  static constexpr uint32_t kRing = kStage * kStages;
+  static constexpr uint32_t kSmem = kRing + 256 + 1024;
+};
+template <int S>
+struct Cfg2 {
+  static constexpr uint32_t kStage = (uint32_t)S * (VP_PLANE + kOzMaxCols * 32u);
+  static constexpr int kStages = (int)(kSmemBudget / kStage) < 8 ? (int)(kSmemBudget / kStage) : 8;
+  static constexpr uint32_t kRing = kStage * kStages;
+  static constexpr uint32_t kSmem = kRing + 256 + 1024;
+};
+
+// ============================================================================ pass 1
+// GEMM1 of every (tile, block pair) in exact windows, V+- = X +- Y', fixed-point
+// slices of V+- to the workspace.  Work units walk range-major (unit u: range
+// u / tiles of tile u % tiles) so the resident CTAs share B panels in L2.
+template <int S>
+__global__ void __launch_bounds__(kThreads, 1) oz_vstore_kernel(const __grid_constant__ OzArgs A) {
+  using C = Cfg1<S>;
+  static_assert(C::kStages >= 3 && 8 * (2 * C::kStages + Bars::kCount) + 8 <= 256, "ring");
+  static_assert(S >= 4 && S <= 6, "slices");
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
+  uint8_t *smem = smem_raw + pad;
+  const uint32_t ring = raw + pad;
+  Bars bars{ring + C::kRing, C::kStages};
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(smem + C::kRing + 8 * (2 * C::kStages + Bars::kCount));
+  int *abort_flag = reinterpret_cast<int *>(tmem_holder + 1);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::kStages; ++s) {
+      mbar_init(bars.full(s), 1);
+      mbar_init(bars.empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(bars.cfull(b), 1);
+      mbar_init(bars.cfree(b), kEpi);
+    }
+    mbar_init(bars.done(), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_holder), 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+  const Watchdog wd{A.status, abort_flag, A.timeout_ns};
+  const int nwin = (A.nks + kOzKc - 1) / kOzKc;
+  auto unit_slot = [&](int u) { return (u % A.ntiles) * A.ksplit + u / A.ntiles; };
+
+  if (warp == 0) {
+    // ================================================================ TMA producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0, armed = 0, armed_par = 0;
+      bool ok = true;
+      tma_prefetch_desc(&A.tmA);
+      tma_prefetch_desc(&A.tmB);
+      for (int u = blockIdx.x; ok && u < A.nitems; u += gridDim.x) {
+        const Item I = decode(A, unit_slot(u), 1);
+        for (int p = I.p0; ok && p < I.p1; ++p) {
+          int k, l;
+          pair_of(p, k, l);
+          const int ntile = (k == l) ? 1 : 2;
+          for (int w = 0; ok && w < nwin; ++w)
+            for (int tt = 0; ok && tt < ntile; ++tt)
+              for (int ks = w * kOzKc; ok && ks < min(A.nks, (w + 1) * kOzKc); ++ks) {
+                if (!(ok = mbar_wait(bars.empty(stage), phase ^ 1u, wd, kSiteTmaEmpty))) break;
+                const uint32_t dst = ring + (uint32_t)stage * C::kStage;
+                mbar_arrive_expect_tx(bars.full(stage), C::kStage);
+                armed |= 1u << stage;
+                armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+                // X: rows (a, c in block k) x (b, d in block l); Y: the blocks swapped
+                const int ca = (tt == 0 ? k : l) * CB, cb = (tt == 0 ? l : k) * CB;
+                tma_load_4d(dst, &A.tmA, bars.full(stage), ks * KSTEP, ca, I.A0, 0);
+                tma_load_4d(dst + S * A_TILE, &A.tmB, bars.full(stage), ks * KSTEP, cb, I.B0, 0);
+                if (++stage == C::kStages) {
+                  stage = 0;
+                  phase ^= 1u;
+                }
+              }
+        }
+      }
+      if (!ok) {
+        DrainWatch dw(A.status, A.timeout_ns);
+        for (int s = 0; s < C::kStages; ++s)
+          if (armed & (1u << s)) mbar_wait(bars.full(s), (armed_par >> s) & 1u, dw.wd, kSiteTmaFull);
+      }
+    }
+  } else if (warp == 1) {
+    // ================================================================ MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t use[2] = {0, 0};
+      const uint32_t hi64 = desc_hi(512, kSwizzle64);
+      const uint32_t id64 = idesc_bf16(128, 64);
+      bool ok = true;
+      for (int u = blockIdx.x; ok && u < A.nitems; u += gridDim.x) {
+        const Item I = decode(A, unit_slot(u), 1);
+        for (int p = I.p0; ok && p < I.p1; ++p) {
+          int k, l;
+          pair_of(p, k, l);
+          const int ntile = (k == l) ? 1 : 2;
+          for (int w = 0; ok && w < nwin; ++w)
+            for (int tt = 0; ok && tt < ntile; ++tt) {
+              if (!(ok = mbar_wait(bars.cfree(tt), (use[tt] & 1u) ^ 1u, wd, kSiteXYFree))) break;
+              tc_fence_after();
+              const uint32_t dT = tmem + 256u * tt;
+              const int ks0 = w * kOzKc;
+              for (int ks = ks0; ok && ks < min(A.nks, ks0 + kOzKc); ++ks) {
+                if (!(ok = mbar_wait(bars.full(stage), phase, wd, kSiteTmaFull))) break;
+                const uint32_t st = ring + (uint32_t)stage * C::kStage;
+                const uint32_t sb = st + S * A_TILE;
+#pragma unroll
+                for (int kk = 0; kk < KSTEP / 16; ++kk) {
+#pragma unroll
+                  for (int pa = 0; pa < S; ++pa) {
+                    const uint64_t ad = desc64(st + pa * A_TILE + kk * 32, hi64);
+                    // slices q <= 3 - pa of B sit back to back: one MMA of
+                    // N = 64 (4 - pa) puts order pa + q into column block pa + q
+                    if (pa <= 3) {
+                      const bool first = ks == ks0 && kk == 0 && pa == 0;
+                      mma_bf16(dT + 64u * pa, ad, desc64(sb + kk * 32, hi64), idesc_bf16(128, 64 * (4 - pa)),
+                               first ? 0u : 1u);
+                    }
+                    // the remaining products of order >= 4 into block 3
+#pragma unroll
+                    for (int q = (pa <= 4 ? 4 - pa : 0); q <= S - 1 - pa; ++q)
+                      mma_bf16(dT + 192u, ad, desc64(sb + q * B_TILE + kk * 32, hi64), id64, 1u);
+                  }
+                }
+                mma_commit(bars.empty(stage));
+                if (++stage == C::kStages) {
+                  stage = 0;
+                  phase ^= 1u;
+                }
+              }
+              if (!ok) break;
+              mma_commit(bars.cfull(tt));
+              ++use[tt];
+            }
+        }
+      }
+      mma_commit(bars.done());
+      DrainWatch dw(A.status, A.timeout_ns);
+      mbar_wait(bars.done(), 0, dw.wd, kSiteRFull);
+    }
+  } else {
+    // ================================================================ conversion warps
+    const int quad = warp & 3;
+    const int qw = (warp - 2) >> 2;      // columns 16 qw .. 16 qw + 15 of each block: b = 2 qw + j
+    const int L = quad * 32 + lane;      // TMEM lane = A row (a, c): a = A0 + L / 8, c = 8 k + L % 8
+    const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + 16u * qw;
+    const int a_l = L >> 3, x_l = L & 7;
+    uint32_t use[2] = {0, 0};
+    bool ok = true;
+    for (int u = blockIdx.x; ok && u < A.nitems; u += gridDim.x) {
+      const Item I = decode(A, unit_slot(u), 1);
+      const int a = I.A0 + a_l;
+      for (int p = I.p0; ok && p < I.p1; ++p) {
+        int k, l;
+        pair_of(p, k, l);
+        const bool diag = (k == l);
+        float2 X[16], Y[16];  // (hi, lo) sums of columns (b = 2 qw + j, d = 0..7), j = e / 8
+#pragma unroll
+        for (int e = 0; e < 16; ++e) X[e] = Y[e] = make_float2(0.f, 0.f);
+        for (int w = 0; ok && w < nwin; ++w)
+          for (int tt = 0; tt < (diag ? 1 : 2); ++tt) {
+            if (!(ok = mbar_wait(bars.cfull(tt), use[tt] & 1u, wd, kSiteXYFull))) break;
+            ++use[tt];
+            tc_fence_after();
+            float2 *acc = tt ? Y : X;
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              float g0[4], g1[4], g2[4], g3[4];
+              const uint32_t c0 = tl + 256u * tt + 4u * h;
+              tmem_ld4(c0, g0);
+              tmem_ld4(c0 + 64u, g1);
+              tmem_ld4(c0 + 128u, g2);
+              tmem_ld4(c0 + 192u, g3);
+              tmem_ld_wait();
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                float hh, ll;
+                window_value(g0[e], g1[e], g2[e], g3[e], hh, ll);
+                ds_acc(acc[4 * h + e], hh, ll);
+              }
+            }
+            tc_fence_before();
+            mbar_arrive(bars.cfree(tt));
+          }
+        if (!ok) break;
+        // scale to B units: X[(a, c), (b, d)] by scale(a, c) scale(b, d), c = 8k + x_l, d = 8l + e;
+        // Y[(a, d'), (b, c')] with d' = 8l + x_l, c' = 8k + e
+        const float rX = A.rsB[(size_t)a * A.vp + k * CB + x_l];
+        const float rY = A.rsB[(size_t)a * A.vp + l * CB + x_l];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int b = I.B0 + 2 * qw + j;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const float sx = rX * A.rsB[(size_t)b * A.vp + l * CB + e];
+            X[8 * j + e].x *= sx;
+            X[8 * j + e].y *= sx;
+            if (!diag) {
+              const float sy = rY * A.rsB[(size_t)b * A.vp + k * CB + e];
+              Y[8 * j + e].x *= sy;
+              Y[8 * j + e].y *= sy;
+            }
+          }
+        }
+        // Y' : lane (a, c = 8k + x_l) gets (ad|bc) for d = 8l + e (transpose across the 8 lanes)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          float rh[8], rl[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            rh[e] = diag ? X[8 * j + e].x : Y[8 * j + e].x;
+            rl[e] = diag ? X[8 * j + e].y : Y[8 * j + e].y;
+          }
+          transpose8(rh, x_l);
+          transpose8(rl, x_l);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) Y[8 * j + e] = make_float2(rh[e], rl[e]);
+        }
+        // V+ = X + Y' into X, V- = X - Y' into Y (double-single, renormalised)
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const float2 x = X[e], y = Y[e];
+          float s, er, lo;
+          two_sum(x.x, y.x, s, er);
+          lo = __fadd_rn(__fadd_rn(x.y, y.y), er);
+          two_sum(s, lo, X[e].x, X[e].y);
+          two_sum(x.x, -y.x, s, er);
+          lo = __fadd_rn(__fsub_rn(x.y, y.y), er);
+          two_sum(s, lo, Y[e].x, Y[e].y);
+        }
+        // one scale per (ab row, sign): the row's 64 slots are the 8 values of
+        // this thread for its b and the 8 lanes x_l
+        __nv_bfloat16 *vbase = A.Vst + (size_t)(I.tile * A.nbp + p) * 2 * S * (128 * SLOTS);
+        float *sbase = A.sV + (size_t)(I.tile * A.nbp + p) * 2 * 128;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int row = a_l * 8 + 2 * qw + j;
+#pragma unroll
+          for (int sg = 0; sg < 2; ++sg) {
+            const float2 *V = sg ? Y + 8 * j : X + 8 * j;
+            float m = 0.f;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) m = fmaxf(m, fabsf(V[e].x));
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
+            // rows below 2^-119 (far under any integral of interest) count as zero,
+            // which keeps both powers of two normal floats
+            float inv = 0.f, scale = 0.f;
+            const int E = exp_above(m);
+            if (m > 0.f && E >= -118) {
+              inv = pow2f(8 - E);
+              scale = pow2f(E - 8);
+            }
+            uint4 out[S];
+#pragma unroll
+            for (int e2 = 0; e2 < 4; ++e2) {
+              float hs[2], ls[2];
+#pragma unroll
+              for (int z = 0; z < 2; ++z) {
+                hs[z] = V[2 * e2 + z].x * inv;
+                ls[z] = V[2 * e2 + z].y * inv;
+              }
+#pragma unroll
+              for (int s = 0; s < S; ++s) {
+                float xs[2];
+#pragma unroll
+                for (int z = 0; z < 2; ++z) {
+                  xs[z] = rint_small(hs[z]);
+                  float r, er;
+                  two_sum(__fsub_rn(hs[z], xs[z]), ls[z], r, er);
+                  hs[z] = r * 256.f;
+                  ls[z] = er * 256.f;
+                  xs[z] *= pow2f(-8 * s);
+                }
+                const __nv_bfloat162 b2 = __floats2bfloat162_rn(xs[0], xs[1]);
+                (&out[s].x)[e2] = *reinterpret_cast<const uint32_t *>(&b2);
+              }
+            }
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+              __stcs(reinterpret_cast<uint4 *>(vbase + (size_t)(sg * S + s) * (128 * SLOTS) + row * SLOTS + x_l * CB),
+                     out[s]);
+            if (x_l == 0) sbase[sg * 128 + row] = scale;
+          }
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// ============================================================================ pass 2
+// GEMM2 of one (tile, chunk of <= 128 occupied pairs of one sign, block-pair
+// range): per 16-slot piece the slice products V_p T_q^T (p + q < S) into the
+// four order accumulators (columns 0, 128, 256, 384), drained once per block
+// pair with the pair's row scales into double-single sums in registers.
+// Work units walk range-major (unit u: range u / (tiles * chunks)).
+template <int S>
+__global__ void __launch_bounds__(kThreads, 1) oz_gemm2_kernel(const __grid_constant__ OzArgs A) {
+  using C = Cfg2<S>;
+  static_assert(C::kStages >= 3 && 8 * (2 * C::kStages + Bars::kCount) + 8 <= 256, "ring");
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
+  uint8_t *smem = smem_raw + pad;
+  const uint32_t ring = raw + pad;
+  Bars bars{ring + C::kRing, C::kStages};
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(smem + C::kRing + 8 * (2 * C::kStages + Bars::kCount));
+  int *abort_flag = reinterpret_cast<int *>(tmem_holder + 1);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::kStages; ++s) {
+      mbar_init(bars.full(s), 1);
+      mbar_init(bars.empty(s), 1);
+    }
+    mbar_init(bars.cfull(0), 1);
+    mbar_init(bars.cfree(0), kEpi);
+    mbar_init(bars.done(), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_holder), 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+  const Watchdog wd{A.status, abort_flag, A.timeout_ns};
+  constexpr int kPieces = SLOTS / TPIECE;
+  const int tcs = A.ntiles * A.nchunks;
+  auto unit_slot = [&](int u) { return (u % tcs) * A.ksplit + u / tcs; };
+
+  if (warp == 0) {
+    // ================================================================ TMA producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0, armed = 0, armed_par = 0;
+      bool ok = true;
+      tma_prefetch_desc(&A.tmVl);
+      for (int u = blockIdx.x; ok && u < A.nitems; u += gridDim.x) {
+        const Item I = decode(A, unit_slot(u), A.nchunks);
+        const uint32_t sc = (uint32_t)(I.CH.nps + I.CH.nms);
+        const int sg = I.CH.nps > 0 ? 0 : 1;
+        const uint32_t tbytes = (uint32_t)S * sc * 32u;
+        for (int p = I.p0; ok && p < I.p1; ++p) {
+          const int plane0 = ((I.tile * A.nbp + p) * 2 + sg) * S;
+          for (int piece = 0; piece < kPieces; ++piece) {
+            if (!(ok = mbar_wait(bars.empty(stage), phase ^ 1u, wd, kSiteTmaEmpty))) break;
+            const uint32_t dst = ring + (uint32_t)stage * C::kStage;
+            mbar_arrive_expect_tx(bars.full(stage), (uint32_t)S * VP_PLANE + tbytes);
+            armed |= 1u << stage;
+            armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+            tma_load_3d(dst, &A.tmVl, bars.full(stage), piece * TPIECE, 0, plane0);
+            bulk_load(dst + S * VP_PLANE, A.T2 + I.CH.t2off + (size_t)(p * kPieces + piece) * tbytes, tbytes,
+                      bars.full(stage));
+            if (++stage == C::kStages) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+        }
+      }
+      if (!ok) {
+        DrainWatch dw(A.status, A.timeout_ns);
+        for (int s = 0; s < C::kStages; ++s)
+          if (armed & (1u << s)) mbar_wait(bars.full(s), (armed_par >> s) & 1u, dw.wd, kSiteTmaFull);
+      }
+    }
+  } else if (warp == 1) {
+    // ================================================================ MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0, g = 0;
+      const uint32_t hi32 = desc_hi(256, kSwizzle32);
+      bool ok = true;
+      for (int u = blockIdx.x; ok && u < A.nitems; u += gridDim.x) {
+        const Item I = decode(A, unit_slot(u), A.nchunks);
+        const uint32_t sc = (uint32_t)(I.CH.nps + I.CH.nms);
+        const uint32_t id = idesc_bf16(128, (int)sc);
+        for (int p = I.p0; ok && p < I.p1; ++p) {
+          // the four accumulators are free once the last pair has been drained
+          if (!(ok = mbar_wait(bars.cfree(0), (g & 1u) ^ 1u, wd, kSiteRFree))) break;
+          tc_fence_after();
+          for (int piece = 0; ok && piece < kPieces; ++piece) {
+            if (!(ok = mbar_wait(bars.full(stage), phase, wd, kSiteTmaFull))) break;
+            const uint32_t st = ring + (uint32_t)stage * C::kStage;
+            const uint32_t stt = st + S * VP_PLANE;
+#pragma unroll
+            for (int pa = 0; pa < S; ++pa)
+#pragma unroll
+              for (int q = 0; q < S - pa; ++q) {
+                const int grp = pa + q < 3 ? pa + q : 3;
+                const bool first = piece == 0 && pa == 0 && q <= 3;
+                mma_bf16(tmem + 128u * grp, desc64(st + pa * VP_PLANE, hi32), desc64(stt + q * sc * 32u, hi32), id,
+                         first ? 0u : 1u);
+              }
+            mma_commit(bars.empty(stage));
+            if (++stage == C::kStages) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+          if (!ok) break;
+          mma_commit(bars.cfull(0));
+          ++g;
+        }
+      }
+      mma_commit(bars.done());
+      DrainWatch dw(A.status, A.timeout_ns);
+      mbar_wait(bars.done(), 0, dw.wd, kSiteRFull);
+    }
+  } else {
+    // ================================================================ drains -> sums
+    const int quad = warp & 3;
+    const int qw = (warp - 2) >> 2;  // columns 32 qw .. 32 qw + 31
+    const int L = quad * 32 + lane;  // TMEM lane = ab row of the tile
+    const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + 32u * qw;
+    uint32_t g = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; ok && u < A.nitems; u += gridDim.x) {
+      const Item I = decode(A, unit_slot(u), A.nchunks);
+      const int sc = I.CH.nps + I.CH.nms;
+      const int sg = I.CH.nps > 0 ? 0 : 1;
+      const int ng = min(8, max(0, (sc - 32 * qw) / 4));  // this thread's 4-column groups
+      float2 acc[32];
+#pragma unroll
+      for (int e = 0; e < 32; ++e) acc[e] = make_float2(0.f, 0.f);
+      for (int p = I.p0; ok && p < I.p1; ++p) {
+        if (!(ok = mbar_wait(bars.cfull(0), g & 1u, wd, kSiteRFull))) break;
+        ++g;
+        tc_fence_after();
+        const float sv = A.sV[((size_t)(I.tile * A.nbp + p) * 2 + sg) * 128 + L];
+        const float *st = A.sT + ((size_t)I.ch * A.nbp + p) * kOzMaxCols + 32 * qw;
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+          if (h < ng) {
+            float g0[4], g1[4], g2[4], g3[4];
+            const uint32_t c0 = tl + 4u * h;
+            tmem_ld4(c0, g0);
+            tmem_ld4(c0 + 128u, g1);
+            tmem_ld4(c0 + 256u, g2);
+            tmem_ld4(c0 + 384u, g3);
+            const float4 t0 = *reinterpret_cast<const float4 *>(st + 4 * h);
+            const float ts[4] = {t0.x, t0.y, t0.z, t0.w};
+            tmem_ld_wait();
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              float hh, ll;
+              window_value(g0[e], g1[e], g2[e], g3[e], hh, ll);
+              const float s = sv * ts[e];
+              ds_acc(acc[4 * h + e], hh * s, ll * s);
+            }
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(bars.cfree(0));
+      }
+      if (!ok) break;
+      // this unit's sums, [col][lane]
+#pragma unroll
+      for (int h = 0; h < 8; ++h)
+        if (h < ng)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) I.racc[(size_t)(32 * qw + 4 * h + e) * 128 + L] = acc[4 * h + e];
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// ============================================================================ preparation
+// One thread per row (a, c) of B: the smallest E with max_P |B^P_ac| < 2^E
+// gives the row's scale 2^(E - 8) (0 for a zero row or a padding row).
+// A NaN or infinite element records kSiteNonFinite in the status word.
+__global__ void oz_rowscale_kernel(int N, int v, int vp, const double *__restrict__ B, float *__restrict__ rs,
+                                   int *status) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= vp * vp) return;
+  const int a = idx / vp, c = idx % vp;
+  double m = 0.0;
+  bool bad = false;
+  if (a < v && c < v)
+    for (int P = 0; P < N; ++P) {
+      const double x = B[((size_t)P * v + a) * v + c];
+      bad |= !isfinite(x);
+      m = fmax(m, fabs(x));
+    }
+  if (bad) record_status(status, kSiteNonFinite);
+  float r = 0.f;
+  if (m > 0.0 && !bad) {
+    int E;
+    frexp(m, &E);  // m = f 2^E, 1/2 <= f < 1
+    r = (float)ldexp(1.0, E - 8);
+  }
+  rs[idx] = r;
+}
+
+// x = scale (x_0 + x_1 2^-8 + ...) with x_s = nearest integer of what is left:
+// slice s stored as the BF16 number x_s 2^(-8 s) (exact).
+template <int S>
+__device__ __forceinline__ void fixed_slices(double y, __nv_bfloat16 (&out)[S]) {
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const double x = rint(y);
+    out[s] = __float2bfloat16_rn((float)ldexp(x, -8 * s));
+    y = (y - x) * 256.0;
+  }
+}
+
+// Bt[s][a][c][P] = slice s of B^P_ac / scale(a, c), 32x32 tiles through shared
+// memory (read c fastest, write P fastest); zero beyond v and N.
+template <int S>
+__global__ void oz_split_B_kernel(int N, int v, int vp, int Np, const double *__restrict__ B,
+                                  const float *__restrict__ rs, __nv_bfloat16 *__restrict__ Bt) {
+  __shared__ double tile[32][33];
+  const int a = blockIdx.z;
+  const int c0 = blockIdx.x * 32, P0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int P = P0 + r, c = c0 + tx;
+    tile[r][tx] = (P < N && c < v && a < v) ? B[((size_t)P * v + a) * v + c] : 0.0;
+  }
+  __syncthreads();
+  const size_t slice = (size_t)vp * vp * Np;
+  for (int r = ty; r < 32; r += 8) {
+    const int c = c0 + r, P = P0 + tx;
+    if (c < vp && P < Np) {
+      const float sc = rs[(size_t)a * vp + c];
+      __nv_bfloat16 sl[S];
+      fixed_slices<S>(sc > 0.f ? tile[tx][r] / (double)sc : 0.0, sl);
+      const size_t off = ((size_t)a * vp + c) * Np + P;
+#pragma unroll
+      for (int q = 0; q < S; ++q) Bt[q * slice + off] = sl[q];
+    }
+  }
+}
+
+// GEMM2 operand: for chunk c, 16-slot piece x (block pair x / 4) and slice s,
+// the chunk's rows (lambda+ rows, padding, lambda- rows, padding) of 32 bytes,
+// stored [x][s][row] in the 32-byte-swizzled order of shared memory, as
+// pack_t2 does.  Eight threads share one (row, block pair): thread cl takes
+// c = 8k + cl, d = 8l + 0..7 (piece cl / 2, half cl % 2), the group's maximum
+// gives the row's scale for the pair, written to sT[c][pair][row].
+//   tau+ = w (tau^cd + tau^dc),  tau- = w (tau^cd - tau^dc),  w = 1/4 (k = l), 1/2.
+template <int S>
+__global__ void oz_pack_t2_kernel(const __grid_constant__ OzPackArgs a) {
+  const TcChunk CH = a.chunks[blockIdx.y];
+  const int sc = CH.nps + CH.nms;
+  const size_t groups = (size_t)sc * a.nbp;
+  uint4 *dst = reinterpret_cast<uint4 *>(a.T2 + CH.t2off);
+  const int cl = threadIdx.x & 7;
+  const size_t g0 = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  const size_t gstep = ((size_t)gridDim.x * blockDim.x) >> 3;
+  const size_t vv = (size_t)a.v * a.v;
+  // every thread runs the same number of iterations (the shuffles below take
+  // the whole warp)
+  const size_t niter = (groups + gstep - 1) / gstep;
+  for (size_t it = 0; it < niter; ++it) {
+    const size_t gi = g0 + it * gstep;
+    const bool live_g = gi < groups;
+    const int row = live_g ? (int)(gi % sc) : 0;
+    const int p = live_g ? (int)(gi / sc) : 0;
+    int k, l;
+    pair_of(p, k, l);
+    int i = 0, j = 0;
+    bool live = false, plus = true;
+    if (live_g && row < CH.np) {
+      lam_plus(CH.lp0 + row, i, j);
+      live = true;
+    } else if (live_g && row >= CH.nps && row - CH.nps < CH.nm) {
+      lam_minus(CH.lm0 + (row - CH.nps), i, j);
+      live = true;
+      plus = false;
+    }
+    const int c = k * CB + cl;
+    const double w = (k == l) ? 0.25 : 0.5;
+    const double *tij = a.tau + ((size_t)i * a.o + j) * vv;
+    double val[8];
+    double m = 0.0;
+    bool bad = false;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int d = l * CB + e;
+      double x = 0.0;
+      if (live && c < a.v && d < a.v) {
+        const double t_cd = tij[(size_t)c * a.v + d], t_dc = tij[(size_t)d * a.v + c];
+        bad |= !(isfinite(t_cd) && isfinite(t_dc));
+        x = plus ? w * (t_cd + t_dc) : w * (t_cd - t_dc);
+      }
+      val[e] = x;
+      m = fmax(m, fabs(x));
+    }
+    if (bad) record_status(a.status, kSiteNonFinite);
+    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, 1));
+    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, 2));
+    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, 4));
+    if (!live_g) continue;
+    double inv = 0.0;
+    float scale = 0.f;
+    if (m > 0.0 && isfinite(m)) {
+      int E;
+      frexp(m, &E);
+      inv = ldexp(1.0, 8 - E);
+      scale = (float)ldexp(1.0, E - 8);
+    }
+    __nv_bfloat16 sl[S][8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      __nv_bfloat16 xs[S];
+      fixed_slices<S>(val[e] * inv, xs);
+#pragma unroll
+      for (int s = 0; s < S; ++s) sl[s][e] = xs[s];
+    }
+    const size_t x = (size_t)p * 4 + cl / 2;
+    const int h = cl & 1;
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+      dst[((x * S + s) * sc + row) * 2 + (h ^ ((row >> 2) & 1))] = *reinterpret_cast<const uint4 *>(sl[s]);
+    if (cl == 0) a.sT[((size_t)blockIdx.y * a.nbp + p) * kOzMaxCols + row] = scale;
+  }
+}
+
+}  // namespace
+
+void launch_oz_rowscale(int N, int v, int vp, const double *B, float *rs, int *status, cudaStream_t s) {
+  const int n = vp * vp;
+  oz_rowscale_kernel<<<(n + 255) / 256, 256, 0, s>>>(N, v, vp, B, rs, status);
+}
+
+void launch_oz_split_B(int N, int v, int vp, int Np, int nslices, const double *B, const float *rs,
+                       __nv_bfloat16 *Bt, cudaStream_t s) {
+  dim3 grid((vp + 31) / 32, (Np + 31) / 32, vp), block(32, 8);
+  if (nslices == 5)
+    oz_split_B_kernel<5><<<grid, block, 0, s>>>(N, v, vp, Np, B, rs, Bt);
+  else
+    oz_split_B_kernel<6><<<grid, block, 0, s>>>(N, v, vp, Np, B, rs, Bt);
+}
+
+void launch_oz_pack_t2(const OzPackArgs &a, cudaStream_t s) {
+  dim3 grid(512, a.nchunks);
+  if (a.S == 5)
+    oz_pack_t2_kernel<5><<<grid, 256, 0, s>>>(a);
+  else
+    oz_pack_t2_kernel<6><<<grid, 256, 0, s>>>(a);
+}
+
+uint32_t oz_smem_bytes(int pass, int nslices) {
+  if (pass == 1) return nslices == 5 ? Cfg1<5>::kSmem : Cfg1<6>::kSmem;
+  return nslices == 5 ? Cfg2<5>::kSmem : Cfg2<6>::kSmem;
+}
+
+cudaError_t oz_init_attributes(int nslices) {
+  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if (nslices == 5) {
+    cudaError_t e = cudaFuncSetAttribute(oz_vstore_kernel<5>, at, (int)Cfg1<5>::kSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(oz_gemm2_kernel<5>, at, (int)Cfg2<5>::kSmem);
+    return e;
+  }
+  cudaError_t e = cudaFuncSetAttribute(oz_vstore_kernel<6>, at, (int)Cfg1<6>::kSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(oz_gemm2_kernel<6>, at, (int)Cfg2<6>::kSmem);
+  return e;
+}
+
+cudaError_t launch_oz_vstore(const OzArgs &a, int nslices, cudaStream_t s) {
+  if (a.nitems <= 0) return cudaSuccess;
+  if (nslices == 5)
+    oz_vstore_kernel<5><<<a.nitems, kThreads, Cfg1<5>::kSmem, s>>>(a);
+  else
+    oz_vstore_kernel<6><<<a.nitems, kThreads, Cfg1<6>::kSmem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oz_gemm2(const OzArgs &a, int nslices, cudaStream_t s) {
+  if (a.nitems <= 0) return cudaSuccess;
+  if (nslices == 5)
+    oz_gemm2_kernel<5><<<a.nitems, kThreads, Cfg2<5>::kSmem, s>>>(a);
+  else
+    oz_gemm2_kernel<6><<<a.nitems, kThreads, Cfg2<6>::kSmem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace ladder

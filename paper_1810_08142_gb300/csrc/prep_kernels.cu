@@ -54,11 +54,12 @@ __device__ __forceinline__ void split_bf16(double x, __nv_bfloat16 (&out)[S]) {
 // Entries with c or d >= v are zero.  grid.x covers the K slots of one row in
 // chunks, grid.y the rows (plus rows first, then minus rows).
 // For the BF16 layout the output is [slice][row][K].
+// A NaN or infinite tau element records kSiteNonFinite in *status (if given).
 template <typename T, int S>
 __global__ void pack_tpm_kernel(int o, int v, int K, int nlp, int nlm,
                                 const double *__restrict__ tau, T *__restrict__ Tp,
                                 T *__restrict__ Tm, size_t slice_stride_p,
-                                size_t slice_stride_m) {
+                                size_t slice_stride_m, int *status) {
   const int row = blockIdx.y;
   const bool plus = row < nlp;
   int i, j;
@@ -79,6 +80,7 @@ __global__ void pack_tpm_kernel(int o, int v, int K, int nlp, int nlm,
     if (c < v && d < v) {
       const double w = (k == l) ? 0.25 : 0.5;
       const double x = tij[(size_t)c * v + d], y = tij[(size_t)d * v + c];
+      if (status && !(isfinite(x) && isfinite(y))) record_status(status, kSiteNonFinite);
       val = plus ? w * (x + y) : w * (x - y);
     }
     if constexpr (S == 0) {
@@ -96,19 +98,19 @@ void launch_pack_tpm_f64(int o, int v, int K, const double *tau, double *Tp, dou
                          cudaStream_t s) {
   const int nlp = ppos(o), nlm = pneg(o);
   dim3 grid((K + 255) / 256 < 64 ? (K + 255) / 256 : 64, nlp + nlm);
-  pack_tpm_kernel<double, 0><<<grid, 256, 0, s>>>(o, v, K, nlp, nlm, tau, Tp, Tm, 0, 0);
+  pack_tpm_kernel<double, 0><<<grid, 256, 0, s>>>(o, v, K, nlp, nlm, tau, Tp, Tm, 0, 0, nullptr);
 }
 
 void launch_pack_tpm_bf16(int o, int v, int K, int nslices, int rows_p, int rows_m,
                           const double *tau, __nv_bfloat16 *Tp, __nv_bfloat16 *Tm,
-                          cudaStream_t s) {
+                          cudaStream_t s, int *status) {
   const int nlp = ppos(o), nlm = pneg(o);
   dim3 grid((K + 255) / 256 < 64 ? (K + 255) / 256 : 64, nlp + nlm);
   const size_t sp = (size_t)rows_p * K, sm = (size_t)rows_m * K;
   if (nslices == 2)
-    pack_tpm_kernel<__nv_bfloat16, 2><<<grid, 256, 0, s>>>(o, v, K, nlp, nlm, tau, Tp, Tm, sp, sm);
+    pack_tpm_kernel<__nv_bfloat16, 2><<<grid, 256, 0, s>>>(o, v, K, nlp, nlm, tau, Tp, Tm, sp, sm, status);
   else
-    pack_tpm_kernel<__nv_bfloat16, 3><<<grid, 256, 0, s>>>(o, v, K, nlp, nlm, tau, Tp, Tm, sp, sm);
+    pack_tpm_kernel<__nv_bfloat16, 3><<<grid, 256, 0, s>>>(o, v, K, nlp, nlm, tau, Tp, Tm, sp, sm, status);
 }
 
 // ---------------------------------------------------------------- tau+- per chunk
@@ -253,9 +255,10 @@ void launch_pack_b2(const BpackArgs &a, cudaStream_t s) {
 // Bt[q][a][c][P] = slice q of B[P][a][c]; a, c < vp (zero beyond v),
 // P < Np (zero beyond N).  32x32 tiles through shared memory so both the
 // read (c fastest) and the write (P fastest) are coalesced.
+// A NaN or infinite element records kSiteNonFinite in *status (if given).
 template <int S>
 __global__ void split_B_kernel(int N, int v, int vp, int Np, const double *__restrict__ B,
-                               __nv_bfloat16 *__restrict__ Bt, int transB) {
+                               __nv_bfloat16 *__restrict__ Bt, int transB, int *status) {
   __shared__ double tile[32][33];
   const int a = blockIdx.z;
   const int c0 = blockIdx.x * 32, P0 = blockIdx.y * 32;
@@ -264,7 +267,9 @@ __global__ void split_B_kernel(int N, int v, int vp, int Np, const double *__res
     const int P = P0 + r, c = c0 + tx;
     // transB: slice B^P_ca at position (a, c) (the transposed ladder of the adjoint)
     const size_t src = transB ? ((size_t)P * v + c) * v + a : ((size_t)P * v + a) * v + c;
-    tile[r][tx] = (P < N && c < v && a < v) ? B[src] : 0.0;
+    const double x = (P < N && c < v && a < v) ? B[src] : 0.0;
+    if (status && !isfinite(x)) record_status(status, kSiteNonFinite);
+    tile[r][tx] = x;
   }
   __syncthreads();
   const size_t slice = (size_t)vp * vp * Np;
@@ -281,19 +286,20 @@ __global__ void split_B_kernel(int N, int v, int vp, int Np, const double *__res
 }
 
 void launch_split_B(int N, int v, int vp, int Np, int nslices, const double *B,
-                    __nv_bfloat16 *Bt, cudaStream_t s, bool transB) {
+                    __nv_bfloat16 *Bt, cudaStream_t s, bool transB, int *status) {
   dim3 grid((vp + 31) / 32, (Np + 31) / 32, vp), block(32, 8);
   if (nslices == 2)
-    split_B_kernel<2><<<grid, block, 0, s>>>(N, v, vp, Np, B, Bt, transB ? 1 : 0);
+    split_B_kernel<2><<<grid, block, 0, s>>>(N, v, vp, Np, B, Bt, transB ? 1 : 0, status);
   else
-    split_B_kernel<3><<<grid, block, 0, s>>>(N, v, vp, Np, B, Bt, transB ? 1 : 0);
+    split_B_kernel<3><<<grid, block, 0, s>>>(N, v, vp, Np, B, Bt, transB ? 1 : 0, status);
 }
 
 // ---------------------------------------------------------------- energy
 // E_L = sum_ijab R_ij^ab (2 t_ij^ab - t_ij^ba).  Stage 1: block (tile, ij)
 // sums a 32x32 (a, b) tile with the transposed t tile staged in shared memory,
 // writes one partial per block; stage 2: one block adds the partials in a
-// fixed order.  Same inputs, same bits.
+// fixed order.  Same inputs, same bits.  The grid is one-dimensional,
+// blockIdx.x = ij * tiles + tile (o^2 can exceed the 65535 limit of grid.y).
 constexpr int kEnergyThreads = 256;
 
 __device__ __forceinline__ double block_sum(double x, double *red) {
@@ -313,9 +319,10 @@ __global__ void energy_partial_kernel(int o, int v, const double *__restrict__ R
   __shared__ double tt[32][33];
   __shared__ double red[kEnergyThreads / 32];
   const int nt = (v + 31) / 32;
-  const int ta = blockIdx.x / nt, tb = blockIdx.x % nt;
-  const int ij = blockIdx.y;
-  const size_t base = (size_t)ij * v * v;
+  const unsigned tile = blockIdx.x % (unsigned)(nt * nt);
+  const int ta = (int)tile / nt, tb = (int)tile % nt;
+  const size_t ij = blockIdx.x / (unsigned)(nt * nt);
+  const size_t base = ij * v * v;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8
   // transposed tile: tt[b_local][a_local] = t_ij^{b a}
   for (int r = ty; r < 32; r += 8) {
@@ -332,7 +339,7 @@ __global__ void energy_partial_kernel(int o, int v, const double *__restrict__ R
     }
   }
   const double s = block_sum(acc, red);
-  if (threadIdx.x == 0) part[(size_t)ij * gridDim.x + blockIdx.x] = s;
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
 __global__ void energy_final_kernel(size_t n, const double *__restrict__ part,
@@ -352,8 +359,8 @@ size_t energy_partials(int o, int v) {
 void launch_energy(int o, int v, const double *R, const double *t2, double *part, double *E,
                    cudaStream_t s) {
   const int nt = (v + 31) / 32;
-  dim3 grid(nt * nt, o * o);
-  energy_partial_kernel<<<grid, kEnergyThreads, 0, s>>>(o, v, R, t2, part);
+  const unsigned blocks = (unsigned)(nt * nt) * (unsigned)(o * o);  // <= 2^30 for o <= 256, v <= 4096
+  energy_partial_kernel<<<blocks, kEnergyThreads, 0, s>>>(o, v, R, t2, part);
   energy_final_kernel<<<1, kEnergyThreads, 0, s>>>(energy_partials(o, v), part, E);
 }
 

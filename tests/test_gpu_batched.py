@@ -28,7 +28,7 @@ def lad():
 
 
 @pytest.mark.parametrize("mode", ["bf16x6", "bf16x3"])
-def test_batch_matches_oracle_and_single_launches(lad, mode, monkeypatch):
+def test_batch_matches_oracle_and_single_launches(lad, mode):
     import torch
     mols = [synthetic.make_inputs(o, v, n, s) for o, v, n, s in SHAPES]
     taus = [oracle.tau(x.t1, x.t2) for x in mols]
@@ -44,7 +44,6 @@ def test_batch_matches_oracle_and_single_launches(lad, mode, monkeypatch):
     torch.cuda.synchronize()
     batch.check_device()
     R2 = [r.cpu().numpy() for r in R2]
-    monkeypatch.setenv("LADDER_KSPLIT", "1")  # the batch does not split block pairs
     for k, x in enumerate(mols):
         ref = oracle.ladder(x.B, taus[k])
         err = rel_fro(R1[k], ref)
