@@ -5,10 +5,12 @@ tau assembly, operand slicing / pair packing, the ladder kernels (the fused
 kernel, or the storing and GEMM2 passes of the two-pass form, as the plan or
 the autotuner's cache chooses; --form forces one), the unpacking of R, and the
 FP64 ladder energy.  The headline metric is ladder TFLOP/s (algorithmic flops
-of the symmetric/antisymmetric scheme / time) of the split-BF16 path in the
-mode that meets the R tolerance (BF16X6), on the mid-size workload (o=34,
-v=400, N_aux=1600).  The other form, BF16X3 and the FP64 path are timed on the
-same workload and reported beside it.
+of the symmetric/antisymmetric scheme / time) on the mid-size workload (o=34,
+v=400, N_aux=1600) of the tensor-core mode that meets both tolerances, R to
+1e-6 and |dE_L| <= 1 microhartree: the error-free split (LADDER_OZAKI, five
+fixed-point BF16 slices).  BF16X6 (meets the R tolerance only), its one-kernel
+fused form, BF16X3 and the FP64 path are timed on the same workload and
+reported beside it, each with its measured |dE_L| and tolerance verdicts.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                     [--dressed] [--lambda-only] [--backward] [--triples] [--tuning k=v,...]
@@ -45,6 +47,39 @@ import synthetic  # noqa: E402
 METRIC = "ladder TFLOP/s & ms/call, split-BF16 vs FP64 GPU path at |dE_L|<=1 uEh"
 DEFAULT_WORKLOAD = "mid_o34_v400_n1600"
 PRODUCTS = {"bf16x3": 3, "bf16x6": 6, "fp64": 1}
+TOL_R = 1e-6      # relative Frobenius error of R, split modes
+TOL_E = 1e-6      # |dE_L| in Hartree
+
+
+def products(mode, tun):
+    """Slice products per multiply-add of a mode (issued tensor flops / F_alg)."""
+    if mode == "ozaki":
+        S = tun["oz_slices"]
+        return S * (S + 1) // 2
+    return PRODUCTS[mode]
+
+
+def fp64_peak(dev):
+    """FP64 DGEMM rate of this GPU (torch.matmul float64, n = 8192, best of
+    3 after a warm-up), the roofline of the plain FP64 path."""
+    import torch
+    n = 8192
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev)
+    c = a @ b
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b, out=c)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del a, b, c
+    torch.cuda.empty_cache()
+    return {"tflops": 2.0 * n ** 3 / (best * 1e-3) / 1e12, "how": "torch.matmul float64 %d^3, best of 3" % n}
 # FP32 CUDA-core peak of one GB300, from the unit counts and the maximum SM
 # clock: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -228,9 +263,8 @@ def run_ragged(args):
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# dominant kernel, from one single-pass ncu capture of the same kernel build
-# on the same workload and tuning (profiles/dram_traffic_mid_o34_v400_n1600_bf16x6.md).
-# A configuration not listed here reports traffic null.
+# dominant kernel, from an ncu capture of the same kernel build on the same
+# workload and tuning.  A configuration not listed here reports traffic null.
 TRAFFIC = {
     ("mid_o34_v400_n1600", "bf16x6", "pass1", (4, 2, 7, 128)): 705.02e9 + 81.46e9,
     ("mid_o34_v400_n1600", "bf16x6", "pass2", (4, 2, 7, 128)): 278.50e9 + 11.65e9,
@@ -314,8 +348,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    ap.add_argument("--mode", default="bf16x6", choices=["bf16x3", "bf16x6", "fp64"])
+    ap.add_argument("--mode", default="ozaki", choices=["ozaki", "bf16x3", "bf16x6", "fp64"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
+    ap.add_argument("--no-others", action="store_true", help="skip every comparison mode")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tuning", default="",
@@ -353,6 +388,7 @@ def main():
     w = synthetic.WORKLOADS[args.workload]
     x = synthetic.make_inputs(w.o, w.v, w.naux, w.seed)
     F = synthetic.falg(w.o, w.v, w.naux)
+    F1 = synthetic.falg_gemm1(w.o, w.v, w.naux)
     dev = torch.device("cuda", local)
     t1 = torch.from_numpy(x.t1).to(dev)
     t2 = torch.from_numpy(x.t2).to(dev)
@@ -361,22 +397,87 @@ def main():
     R = torch.empty_like(t2)
     E = torch.empty((), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
+    pk, pk_kind = peaks()
 
-    tuning = tuned_for(w, args.mode)
-    if args.form != "auto" and args.mode != "fp64":
-        tuning = dict(tuning or {}, two_pass=int(args.form == "two-pass"), ksplit=0)
-    if args.tuning and args.mode != "fp64":
-        # explicit overrides, e.g. --tuning flush_every=32,kc=8
-        tuning = dict(tuning or {}, **{k: int(v) for k, v in
-                                      (kv.split("=") for kv in args.tuning.split(","))})
-    L = lad.Ladder(w.o, w.v, w.naux, mode=args.mode, device=dev, tuning=tuning)
-    lad.ladder_set_timing(L.plan, True)
+    # stored oracle values of this workload (tests/golden/make_golden.py)
+    gold = None
+    gpath = os.path.join(ROOT, "tests", "golden", args.workload + ".json")
+    if os.path.exists(gpath):
+        with open(gpath) as f:
+            gold = json.load(f)
+
+    def parity_of(E_val):
+        """|dE_L| and the sampled-column error of R against the stored oracle
+        values, with the two tolerance verdicts."""
+        if gold is None:
+            return None
+        Rh = R.cpu().numpy()
+        cols = np.array(gold["R_cols"])
+        got = np.stack([Rh[:, :, a, b] for a, b in zip(gold["pairs_a"], gold["pairs_b"])])
+        rel = float(np.linalg.norm(got - cols) / np.linalg.norm(cols))
+        dE = abs(E_val - gold["E_L"])
+        return {"dE_L": dE, "E_L": gold["E_L"], "rel_fro_sampled_cols": rel,
+                "max_rel_sampled_cols": float(np.abs(got - cols).max() / np.abs(cols).max()),
+                "rel_fro_norm": abs(float(np.linalg.norm(Rh)) - gold["R_fro"]) / gold["R_fro"],
+                "R_tol": TOL_R, "dE_L_tol": TOL_E, "R_tol_met": rel <= TOL_R, "dE_L_tol_met": dE <= TOL_E}
+
+    def plan_tuning(mode, form="auto"):
+        tun = tuned_for(w, mode)
+        if form != "auto" and mode in ("bf16x3", "bf16x6"):
+            tun = dict(tun or {}, two_pass=int(form == "two-pass"), ksplit=0)
+        return tun
 
     def step(Lx):
         lad.ladder_tau(Lx.plan, t1, t2, tau)
         lad.ladder_apply(Lx.plan, B, tau, R)
         lad.ladder_energy(Lx.plan, R, t2, E)
 
+    def roofline(mode, tun, pass1_ms, pass2_ms, ladder_ms, two_pass):
+        """The dominant kernel against its peak (bf16 sustained for the tensor
+        modes, the measured DGEMM rate for the FP64 path)."""
+        prod = products(mode, tun)
+        if mode == "fp64":
+            return {"bound": "fp64", "achieved": F / (ladder_ms * 1e-3) / 1e12, "peak": None,
+                    "unit": "TFLOP/s", "frac": None, "traffic": None}
+        peak = pk["bf16_tflops_sustained"]
+        if two_pass:
+            nS = tun["oz_slices"] if mode == "ozaki" else (2 if mode == "bf16x3" else 3)
+            k1 = ("oz_vstore_kernel<%d> (GEMM1 + V+- store)" % nS if mode == "ozaki"
+                  else "ladder_tc_kernel<%d,false,true> (GEMM1 + V store)" % nS)
+            k2 = ("oz_gemm2_kernel<%d> (GEMM2 from stored V+-)" % nS if mode == "ozaki"
+                  else "ladder_gemm2_kernel<%d> (GEMM2 from stored V)" % nS)
+            if pass1_ms >= pass2_ms:
+                kname, kflops, kms, kkey = k1, F1, pass1_ms, "pass1"
+            else:
+                kname, kflops, kms, kkey = k2, F - F1, pass2_ms, "pass2"
+            key = (args.workload, mode, kkey, tuple(tun.get(k) for k in ("kc", "s_pieces", "ksplit", "flush_every"))
+                   if mode != "ozaki" else (tun["oz_slices"], tun["ksplit"]))
+            achieved = prod * kflops / (kms * 1e-3) / 1e12
+            return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": TRAFFIC.get(key), "traffic_unit": "bytes per launch",
+                    "kernel": kname, "kernel_ms": kms,
+                    "other_pass": {"kernel": k2 if kkey == "pass1" else k1,
+                                   "ms": pass2_ms if kkey == "pass1" else pass1_ms,
+                                   "frac": prod * ((F - F1) if kkey == "pass1" else F1) /
+                                   ((pass2_ms if kkey == "pass1" else pass1_ms) * 1e-3) / 1e12 / peak},
+                    "both_passes_frac": prod * F / ((pass1_ms + pass2_ms) * 1e-3) / 1e12 / peak,
+                    "note": "achieved = %d slice products x (that pass's share of F_alg: 2 P+(v) v^2 N for "
+                            "GEMM1, the rest for GEMM2) / its CUDA-event time; peak = bf16 sustained (%s)"
+                            % (prod, pk_kind)}
+        achieved = prod * F / (ladder_ms * 1e-3) / 1e12
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "ladder_tc_kernel<%d,false,false>" % (2 if mode == "bf16x3" else 3),
+                "note": "achieved = %d x F_alg / fused-kernel time; peak = bf16 sustained (%s)" % (prod, pk_kind)}
+
+    # ---------------------------------------------------------------- headline
+    tuning = plan_tuning(args.mode, args.form)
+    if args.tuning and args.mode != "fp64":
+        # explicit overrides, e.g. --tuning flush_every=32,kc=8 or oz_slices=6
+        tuning = dict(tuning or {}, **{k: int(v) for k, v in
+                                      (kv.split("=") for kv in args.tuning.split(","))})
+    L = lad.Ladder(w.o, w.v, w.naux, mode=args.mode, device=dev, tuning=tuning)
+    lad.ladder_set_timing(L.plan, True)
     for _ in range(args.warmup):
         step(L)
     torch.cuda.synchronize()
@@ -386,11 +487,11 @@ def main():
     clocks.start()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    fused, passes = [], []
+    stages, passes = [], []
     e0.record(stream)
     for _ in range(args.steps):
         step(L)
-        fused.append(lad.ladder_timing(L.plan))  # waits for this step's events
+        stages.append(lad.ladder_timing(L.plan))  # waits for this step's events
         passes.append(lad.ladder_timing_passes(L.plan))
     e1.record(stream)
     barrier()
@@ -399,85 +500,84 @@ def main():
     ms = e0.elapsed_time(e1) / args.steps
     ms = max_over_ranks(ms)
     value = rep.job_value(F, ms) / 1e12
-    fused_ms = statistics.mean(f[1] for f in fused)
-    prep_ms = statistics.mean(f[0] for f in fused)
-    unpack_ms = statistics.mean(f[2] for f in fused)
+    ladder_ms = statistics.mean(f[1] for f in stages)
+    prep_ms = statistics.mean(f[0] for f in stages)
+    unpack_ms = statistics.mean(f[2] for f in stages)
     pass1_ms = statistics.mean(f[0] for f in passes)
     pass2_ms = statistics.mean(f[1] for f in passes)
     tun = lad.ladder_get_tuning(L.plan).as_dict() if args.mode != "fp64" else None
     two_pass = bool(tun and tun["two_pass"])
     E_val = float(E.item())
+    parity = parity_of(E_val)
+    roof = roofline(args.mode, tun, pass1_ms, pass2_ms, ladder_ms, two_pass)
+    prod = products(args.mode, tun) if tun else 1
 
-    # parity against stored oracle values (written by tests/golden/make_golden.py)
-    parity = None
-    gpath = os.path.join(ROOT, "tests", "golden", args.workload + ".json")
-    if os.path.exists(gpath):
-        g = json.load(open(gpath))
-        Rh = R.cpu().numpy()
-        cols = np.array(g["R_cols"])
-        got = np.stack([Rh[:, :, a, b] for a, b in zip(g["pairs_a"], g["pairs_b"])])
-        parity = {"dE_L": abs(E_val - g["E_L"]), "E_L": g["E_L"],
-                  "rel_fro_sampled_cols": float(np.linalg.norm(got - cols) / np.linalg.norm(cols)),
-                  "rel_fro_norm": abs(float(np.linalg.norm(Rh)) - g["R_fro"]) / g["R_fro"]}
+    # ---------------------------------------------------------------- end to end
+    # through the C ABI's host-buffer call: every step copies B and tau from
+    # pinned host memory, runs the ladder, copies R back to pinned host memory
+    # and synchronises (ladder_apply_host), then forms E_L from the device
+    # copy of R and reads it back.  tau's host copy is an input here (made
+    # once on the device before the timed region).
+    e2e = None
+    if not args.no_e2e:
+        lad.ladder_tau(L.plan, t1, t2, tau)
+        h_B = torch.from_numpy(x.B).pin_memory()
+        h_tau = tau.cpu().pin_memory()
+        h_R = torch.empty_like(h_tau).pin_memory()
+        d_B, d_tau, d_R = torch.empty_like(B), torch.empty_like(tau), torch.empty_like(R)
 
-    pk, pk_kind = peaks()
-    prod = PRODUCTS[args.mode]
-    if args.mode == "fp64":
-        roof = {"bound": "fp64", "achieved": F / (fused_ms * 1e-3) / 1e12, "peak": None,
-                "unit": "TFLOP/s", "frac": None, "traffic": None}
-    elif two_pass:
-        # dominant kernel of the two-pass form: GEMM1 with the V+- store, or
-        # GEMM2 from the stored tiles, whichever takes longer
-        F1 = synthetic.falg_gemm1(w.o, w.v, w.naux)
-        nS = 2 if args.mode == "bf16x3" else 3
-        if pass1_ms >= pass2_ms:
-            kname, kflops, kms, kkey = ("ladder_tc_kernel<%d,false,true> (GEMM1 + V store)" % nS, F1,
-                                        pass1_ms, "pass1")
-        else:
-            kname, kflops, kms, kkey = "ladder_gemm2_kernel<%d> (GEMM2 from stored V)" % nS, F - F1, pass2_ms, "pass2"
-        traffic = TRAFFIC.get((args.workload, args.mode, kkey,
-                               (tun["kc"], tun["s_pieces"], tun["ksplit"], tun["flush_every"])))
-        achieved = prod * kflops / (kms * 1e-3) / 1e12
-        peak = pk["bf16_tflops_sustained"]
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
-                "kernel": kname, "kernel_ms": kms,
-                "both_passes_frac": prod * F / ((pass1_ms + pass2_ms) * 1e-3) / 1e12 / peak,
-                "note": "achieved = %d x (that pass's share of F_alg: 2 P+(v) v^2 N for GEMM1, the "
-                        "rest for GEMM2) / its CUDA-event time; peak = bf16 sustained (%s)"
-                        % (prod, pk_kind)}
-    else:
-        achieved = prod * F / (fused_ms * 1e-3) / 1e12
-        peak = pk["bf16_tflops_sustained"]
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": "ladder_tc_kernel<%d,false,false>" % (2 if args.mode == "bf16x3" else 3),
-                "note": "achieved = %d x F_alg (bf16 tensor flops of the split scheme) / ladder-kernel "
-                        "time; peak = bf16 sustained (%s)" % (prod, pk_kind)}
+        def e2e_step():
+            lad.ladder_apply_host(L.plan, h_B, h_tau, h_R, d_B, d_tau, d_R)
+            lad.ladder_energy(L.plan, d_R, t2, E)
+            return float(E.item())
 
+        e2e_step()
+        barrier()
+        q0 = time.perf_counter()
+        for _ in range(args.steps):
+            E_e2e = e2e_step()
+        barrier()
+        ems = max_over_ranks((time.perf_counter() - q0) * 1e3 / args.steps)
+        e2e = {"value": rep.job_value(F, ems) / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": (h_B.numel() + h_tau.numel()) * 8,
+               "d2h_bytes_per_step": h_R.numel() * 8 + 8, "ms_per_step": ems,
+               "call": "ladder_apply_host (B, tau in; R out; synchronises) + ladder_energy",
+               "R_host_matches_device": bool(torch.equal(h_R, R.cpu())), "E_L": E_e2e}
+        del d_B, d_tau, d_R, h_B, h_tau, h_R
+    L.close()
+    del L
+    torch.cuda.empty_cache()
+
+    # ---------------------------------------------------------------- other modes
     extra = {}
-    # the other split variant and the FP64 path, same workload, one timed step each
-    others = [] if args.mode != "bf16x6" or args.no_fp64 else ["bf16x3"]
-    if not args.no_fp64 and args.mode != "fp64":
-        others.append("fp64")
-    if two_pass and not args.no_fp64:
-        others.insert(0, args.mode + "_fused")  # the same mode in the one-kernel form
-    if args.dressed and args.mode != "fp64":
-        others.insert(0, args.mode + "_dressed")  # the t1-dressed term (Eq. pp-Ladder-2)
-    if args.lambda_only and args.mode != "fp64":
-        others.insert(0, args.mode + "_lambda")  # the paper's lambda-only contraction (ablation)
+    others = []
+    if not args.no_others:
+        if args.mode != "bf16x6":
+            others.append("bf16x6")
+        if args.mode in ("ozaki", "bf16x6"):
+            others.append("bf16x6_fused")  # the one-kernel form (integral tiles on chip)
+            others.append("bf16x3")
+        if args.mode != "fp64" and not args.no_fp64:
+            others.append("fp64")
+        if args.dressed and args.mode != "fp64":
+            others.insert(0, args.mode + "_dressed")  # the t1-dressed term (Eq. pp-Ladder-2)
+        if args.lambda_only and args.mode in ("bf16x3", "bf16x6"):
+            others.insert(0, args.mode + "_lambda")  # the paper's lambda-only contraction (ablation)
     B_ov = None
     for m in others:
+        base = m.split("_")[0]
+        mt = plan_tuning(base) if base != "fp64" else None
         if m.endswith("_dressed"):
-            Lm = lad.Ladder(w.o, w.v, w.naux, mode=m[:-8], device=dev, tuning=tun, dressed=True)
+            Lm = lad.Ladder(w.o, w.v, w.naux, mode=base, device=dev, tuning=tun, dressed=True)
             B_ov = torch.from_numpy(x.B_ov).to(dev)
         elif m.endswith("_lambda"):
-            Lm = lad.Ladder(w.o, w.v, w.naux, mode=m[:-7], device=dev,
-                            tuning={**tun, "two_pass": 1, "lambda_only": 1, "ksplit": 0})
+            Lm = lad.Ladder(w.o, w.v, w.naux, mode=base, device=dev,
+                            tuning={**(mt or {}), "two_pass": 1, "lambda_only": 1, "ksplit": 0})
         elif m.endswith("_fused"):
-            Lm = lad.Ladder(w.o, w.v, w.naux, mode=m[:-6], device=dev, tuning={**tun, "two_pass": 0, "ksplit": 0})
+            Lm = lad.Ladder(w.o, w.v, w.naux, mode=base, device=dev,
+                            tuning={**(mt or {}), "two_pass": 0, "ksplit": 0})
         else:
-            Lm = lad.Ladder(w.o, w.v, w.naux, mode=m, device=dev)
+            Lm = lad.Ladder(w.o, w.v, w.naux, mode=base, device=dev, tuning=mt)
         lad.ladder_set_timing(Lm.plan, True)
         run = step
         if m.endswith("_dressed"):
@@ -485,7 +585,7 @@ def main():
                 lad.ladder_tau(Lx.plan, t1, t2, tau)
                 lad.ladder_apply_dressed(Lx.plan, B, B_ov, t1, tau, R)
                 lad.ladder_energy(Lx.plan, R, t2, E)
-        if m != "fp64":
+        if base != "fp64":
             run(Lm)
         torch.cuda.synchronize()
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -496,13 +596,18 @@ def main():
         Lm.check_device()
         mms = a0.elapsed_time(a1)
         tm = lad.ladder_timing(Lm.plan)
-        ent = {"ms_per_step": mms, "tflops": F / (mms * 1e-3) / 1e12, "fused_ms": tm[1],
-               "E_L": float(E.item()), "steps": 1}
-        if parity is not None and not m.endswith("_dressed"):
-            ent["dE_L"] = abs(float(E.item()) - parity["E_L"])
-        if m.endswith("_lambda"):
-            p1, p2 = lad.ladder_timing_passes(Lm.plan)
+        p1, p2 = lad.ladder_timing_passes(Lm.plan)
+        mtun = lad.ladder_get_tuning(Lm.plan).as_dict() if base != "fp64" else None
+        m_two = bool(mtun and mtun["two_pass"])
+        ent = {"ms_per_step": mms, "tflops": F / (mms * 1e-3) / 1e12, "ladder_ms": tm[1],
+               "E_L": float(E.item()), "steps": 1, "tuning": mtun,
+               "form": None if mtun is None else ("two-pass" if m_two else "fused")}
+        if m_two:
             ent["pass1_ms"], ent["pass2_ms"] = p1, p2
+        if not m.endswith("_dressed"):
+            ent["parity"] = parity_of(float(E.item()))
+        if not m.endswith("_dressed") and not m.endswith("_lambda"):
+            ent["roofline"] = roofline(base, mtun, p1, p2, tm[1], m_two)
         if m.endswith("_dressed"):
             # tau, B - mbar, the rank-o correction and the energy
             ent["outside_ladder_ms"] = mms - tm[0] - tm[1] - tm[2]
@@ -516,13 +621,16 @@ def main():
             ent["correction_roofline"] = {
                 "bound": "alu", "achieved": fc / (corr_ms * 1e-3) / 1e12, "peak": FP32_ALU_TFLOPS,
                 "unit": "TFLOP/s", "frac": fc / (corr_ms * 1e-3) / 1e12 / FP32_ALU_TFLOPS,
-                "note": "FP32 CUDA-core GEMMs; peak = 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}
+                "note": "CUDA-core GEMMs; peak = 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}
         extra[m] = ent
         Lm.close()
         del Lm
         torch.cuda.empty_cache()
     if "fp64" in extra:
         extra["speedup_vs_fp64"] = extra["fp64"]["ms_per_step"] / ms
+        dg = fp64_peak(dev)
+        extra["fp64"]["roofline"].update({"peak": dg["tflops"], "frac": extra["fp64"]["roofline"]["achieved"] / dg["tflops"],
+                                          "peak_how": dg["how"] + " (measured in this run)"})
     if args.triples:
         # the perturbative triples energy E(T) on the same molecule (CUDA-core
         # GEMMs): FP32 always, FP64 where its work stays below ~5 TFLOP
@@ -556,10 +664,11 @@ def main():
         if "fp64" in tr:
             tr["fp32_rel_diff"] = abs(tr["fp32"]["E_T"] - tr["fp64"]["E_T"]) / abs(tr["fp64"]["E_T"])
         extra["triples"] = tr
-    if args.backward and args.mode != "fp64":
+    if args.backward and args.mode in ("bf16x3", "bf16x6"):
         # the adjoint of E_L in the same mode and tuning: dE/dtau (the
         # transposed ladder) and dE/dB (Gamma stored once, then contracted)
         Lb = lad.Ladder(w.o, w.v, w.naux, mode=args.mode, device=dev, tuning=tun, backward=True)
+        lad.ladder_tau(Lb.plan, t1, t2, tau)
         Wt = Lb.weights(t2)
         dt, db = torch.empty_like(tau), torch.empty_like(B)
         bw = {}
@@ -580,61 +689,6 @@ def main():
         del Lb
         torch.cuda.empty_cache()
 
-    # end to end through the public API with host buffers: every step copies
-    # its inputs from pinned host memory and reads E_L back.  The device
-    # inputs are double-buffered: step k+1's copies run on a copy stream while
-    # step k computes (the copy of a buffer waits until the step that last
-    # used it is done), all inside the timed region.
-    e2e = None
-    if not args.no_e2e:
-        h_t1 = torch.from_numpy(x.t1).pin_memory()
-        h_t2 = torch.from_numpy(x.t2).pin_memory()
-        h_B = torch.from_numpy(x.B).pin_memory()
-        bufs = [(t1, t2, B), (torch.empty_like(t1), torch.empty_like(t2), torch.empty_like(B))]
-        cstream = torch.cuda.Stream(device=dev)
-        copied = [torch.cuda.Event() for _ in range(2)]
-        free = [torch.cuda.Event() for _ in range(2)]
-        used = [False, False]
-
-        def copy_in(k):
-            i = k % 2
-            with torch.cuda.stream(cstream):
-                if used[i]:
-                    cstream.wait_event(free[i])
-                bufs[i][0].copy_(h_t1, non_blocking=True)
-                bufs[i][1].copy_(h_t2, non_blocking=True)
-                bufs[i][2].copy_(h_B, non_blocking=True)
-                copied[i].record(cstream)
-
-        def step_on(k):
-            i = k % 2
-            stream.wait_event(copied[i])
-            lad.ladder_tau(L.plan, bufs[i][0], bufs[i][1], tau)
-            lad.ladder_apply(L.plan, bufs[i][2], tau, R)
-            lad.ladder_energy(L.plan, R, bufs[i][1], E)
-            free[i].record(stream)
-            used[i] = True
-
-        barrier()
-        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        q0.record(stream)
-        cstream.wait_event(q0)
-        copy_in(0)
-        for k in range(args.steps):
-            if k + 1 < args.steps:
-                copy_in(k + 1)
-            step_on(k)
-            _ = float(E.item())
-        q1.record(stream)
-        barrier()
-        ems = max_over_ranks(q0.elapsed_time(q1) / args.steps)
-        h2d = (h_t1.numel() + h_t2.numel() + h_B.numel()) * 8
-        e2e = {"value": rep.job_value(F, ems) / 1e12, "unit": "TFLOP/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8, "ms_per_step": ems,
-               "note": "inputs double-buffered on the device; copies overlap the previous step"}
-        del bufs
-        torch.cuda.empty_cache()
-
     cpu = None
     if rank == 0 and not args.no_cpu:
         full, dt, desc, thr = oracle_sample(x, 15.0)
@@ -642,27 +696,28 @@ def main():
                "sample": desc + "; full-term time extrapolated", "ms_per_step": full * 1e3}
 
     if rank == 0:
+        launches = {"ozaki": 9, "fp64": 4}.get(args.mode, 9 if two_pass else 7)
         line = {
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16x%d-split" % prod if args.mode != "fp64" else "f64",
+            "dtype": ("bf16 fixed-point x%d slices, exact FP32 windows" % tun["oz_slices"] if args.mode == "ozaki"
+                      else "bf16x%d-split" % prod if args.mode != "fp64" else "f64"),
             "data": "synthetic",
             "config": {"workload": args.workload, "o": w.o, "v": w.v, "naux": w.naux,
                        "seed": w.seed, "mode": args.mode, "parallelism": "replicas",
-                       "tuning": tun,
+                       "tuning": tun, "slice_products": prod,
                        "form": None if tun is None else ("two-pass (V+- stored in HBM)" if two_pass
                                                          else "fused (integral tiles on chip)"),
                        "l2": "inputs larger than L2 (B %.2f GB, tau %.2f GB)"
                              % (B.numel() * 8 / 1e9, tau.numel() * 8 / 1e9)},
-            "stages_ms": {"prep": prep_ms, "ladder": fused_ms, "unpack": unpack_ms,
+            "stages_ms": {"prep": prep_ms, "ladder": ladder_ms, "unpack": unpack_ms,
                           "pass1": pass1_ms if two_pass else None,
                           "pass2": pass2_ms if two_pass else None},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": (9 if two_pass else 7) * args.steps, "parity": parity, "E_L": E_val, "others": extra,
+            "gpu_launches": launches * args.steps, "parity": parity, "E_L": E_val, "others": extra,
         }
         print(json.dumps(line), flush=True)
-    L.close()
     rep.close()
     return 0
 

@@ -12,6 +12,10 @@ With --dressed it stores the same columns of the t1-dressed term
 With --triples it stores the perturbative triples energy E(T) of Sec. II.A
 in <workload>_triples.json:
     python tests/golden/make_golden.py --triples dimer_o10_v120_n480
+With --grad it stores 1024 seeded entries each of dE_L/dtau and dE_L/dB (the
+oracle's entry-wise analytic gradient, weights W = 2 t2 - t2^T) in
+<workload>_grad.json:
+    python tests/golden/make_golden.py --grad grad_o16_v200_n800
 """
 import json
 import os
@@ -95,9 +99,36 @@ def main_triples(name):
     print(name, "E(T)", E, "seconds", time.time() - t0)
 
 
+def main_grad(name, m=1024):
+    w = synthetic.WORKLOADS[name]
+    t0 = time.time()
+    x = synthetic.make_inputs(w.o, w.v, w.naux, w.seed)
+    tau = oracle.tau(x.t1, x.t2)
+    W = oracle.energy_weights(x.t2)
+    rng = np.random.default_rng(4321)
+    i, j = rng.integers(0, w.o, m), rng.integers(0, w.o, m)
+    c, d = rng.integers(0, w.v, m), rng.integers(0, w.v, m)
+    P, xx, yy = rng.integers(0, w.naux, m), rng.integers(0, w.v, m), rng.integers(0, w.v, m)
+    dtau = oracle.grad_tau_entries(x.B, W, i, j, c, d)
+    dB = oracle.grad_B_entries(x.B, tau, W, P, xx, yy)
+    out = {
+        "workload": name, "o": w.o, "v": w.v, "naux": w.naux, "seed": w.seed,
+        "dtau_index": [[int(a) for a in t] for t in (i, j, c, d)], "dtau": dtau.tolist(),
+        "dB_index": [[int(a) for a in t] for t in (P, xx, yy)], "dB": dB.tolist(),
+        "oracle_threads": oracle.threads(), "oracle_seconds": time.time() - t0,
+        "note": "entries of dE_L/dtau and dE_L/dB for W = 2 t2 - t2^T; written by "
+                "tests/golden/make_golden.py --grad from the plain FP64 CPU oracle",
+    }
+    path = os.path.join(ROOT, "tests", "golden", name + "_grad.json")
+    with open(path, "w") as f:
+        json.dump(out, f)
+    print(name, "gradient entries, seconds", time.time() - t0)
+
+
 if __name__ == "__main__":
     args = sys.argv[1:]
-    run = main_dressed if "--dressed" in args else main_triples if "--triples" in args else main
+    run = (main_dressed if "--dressed" in args else main_triples if "--triples" in args
+           else main_grad if "--grad" in args else main)
     for n in args:
         if not n.startswith("--"):
             run(n)

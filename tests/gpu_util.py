@@ -9,6 +9,20 @@ def rel_fro(x, ref):
     return float(np.linalg.norm(x - ref) / max(np.linalg.norm(ref), 1e-300))
 
 
+def max_rel(x, ref):
+    """max |x - ref| / max |ref|: the worst element against the scale of ref."""
+    x = np.asarray(x, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.max(np.abs(x - ref)) / max(float(np.max(np.abs(ref))), 1e-300))
+
+
+def rel_err(x, ref):
+    """The larger of the relative Frobenius error and max_rel, so that one
+    tolerance bounds both the aggregate and the worst element (a few wrong
+    entries, e.g. an unwritten tile edge, cannot hide inside a norm)."""
+    return max(rel_fro(x, ref), max_rel(x, ref))
+
+
 def to_dev(a):
     import torch
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()

@@ -71,3 +71,31 @@ def test_triples_workspace_size_is_host_logic(lib):
     assert b64 >= floor64 and b32 >= floor64 // 2 and b32 < b64
     assert f(0, 120, 480, 0, ctypes.byref(size)) == 1       # LADDER_EINVAL
     assert f(10, 120, 480, 7, ctypes.byref(size)) == 1
+
+
+def test_noalloc_energy_size_limit_is_host_logic(lib):
+    """ladder_energy_noalloc checks its shape against the fixed array of
+    524288 partial sums before it touches a pointer or the device:
+    ceil(v/32)^2 o^2 = 4^2 * 182^2 = 529984 is refused (LADDER_ENOTSUP),
+    4^2 * 181^2 = 524176 passes the size check and fails on the null pointers
+    (LADDER_EINVAL); so does o = 256, v = 32 (65536 pairs)."""
+    f = lib.ladder_energy_noalloc
+    f.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 4
+    f.restype = ctypes.c_int
+    assert f(182, 100, None, None, None, None) == 5
+    assert f(181, 100, None, None, None, None) == 1
+    assert f(256, 32, None, None, None, None) == 1
+    assert f(257, 32, None, None, None, None) == 1
+    assert f(120, 200, None, None, None, None) == 5
+
+
+def test_ozaki_mode_and_nonfinite_status_are_exposed(lib):
+    import paper_1810_08142_gb300 as lad
+    lib.ladder_status_string.restype = ctypes.c_char_p
+    assert lad.MODES["ozaki"] == 4
+    assert lad.STATUS[7] == "LADDER_ENONFINITE"
+    assert b"NaN" in lib.ladder_status_string(7)
+    assert [f for f, _ in lad.Tuning._fields_][-1] == "oz_slices"
+    # mode 5 is out of range
+    out = ctypes.c_void_p()
+    assert lib.ladder_plan(4, 24, 96, 5, ctypes.byref(out)) == 1

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import synthetic
-from gpu_util import rel_fro, to_dev
+from gpu_util import rel_err, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -41,8 +41,8 @@ def test_backward_matches_oracle_gradient(lad, mode, two_pass, o, v, n, seed):
     dtau, dB = L.backward(to_dev(B), to_dev(tau), to_dev(W))
     torch.cuda.synchronize()
     L.check_device()
-    e_tau = rel_fro(dtau.cpu().numpy(), oracle.grad_tau(B, W))
-    e_B = rel_fro(dB.cpu().numpy(), oracle.grad_B(B, tau, W))
+    e_tau = rel_err(dtau.cpu().numpy(), oracle.grad_tau(B, W))
+    e_B = rel_err(dB.cpu().numpy(), oracle.grad_B(B, tau, W))
     print("%s two_pass=%d o=%d v=%d n=%d: dtau rel-F %.3e  dB rel-F %.3e" % (mode, two_pass, o, v, n, e_tau, e_B))
     assert e_tau < DTAU_TOL[mode]
     assert e_B < DTAU_TOL[mode]  # dB runs in the plan's mode as well
@@ -95,10 +95,21 @@ def test_autograd_central_differences_fp64(lad):
 
 @pytest.mark.parametrize("mode", ["fp64", "bf16x6"])
 def test_backward_full_size_sampled(lad, mode):
-    """Gradient workload o=16, v=200, N_aux=800: sampled entries of dtau and
-    dB against the oracle's entry-wise analytic gradient."""
+    """Gradient workload o=16, v=200, N_aux=800: 1024 entries each of dtau and
+    dB against the oracle's entry-wise analytic gradient, stored in
+    tests/golden/grad_o16_v200_n800_grad.json by make_golden.py --grad; both
+    the relative Frobenius error of the sample and its worst entry (against
+    the sample's largest) stay within the mode's bar."""
+    import json
+    import os
     import torch
     w = synthetic.WORKLOADS["grad_o16_v200_n800"]
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", w.name + "_grad.json")
+    if not os.path.exists(path):
+        pytest.skip("no stored gradient entries")
+    with open(path) as f:
+        g = json.load(f)
+    assert (g["o"], g["v"], g["naux"], g["seed"]) == (w.o, w.v, w.naux, w.seed)
     x = synthetic.make_inputs(w.o, w.v, w.naux, w.seed)
     tau = oracle.tau(x.t1, x.t2)
     W = oracle.energy_weights(x.t2)
@@ -107,18 +118,12 @@ def test_backward_full_size_sampled(lad, mode):
     torch.cuda.synchronize()
     L.check_device()
     dtau, dB = dtau.cpu().numpy(), dB.cpu().numpy()
-    rng = np.random.default_rng(7)
-    m = 24
-    i, j = rng.integers(0, w.o, m), rng.integers(0, w.o, m)
-    c, d = rng.integers(0, w.v, m), rng.integers(0, w.v, m)
-    ref = oracle.grad_tau_entries(x.B, W, i, j, c, d)
-    got = dtau[i, j, c, d]
-    e_tau = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-    P, xx, yy = rng.integers(0, w.naux, m), rng.integers(0, w.v, m), rng.integers(0, w.v, m)
-    refB = oracle.grad_B_entries(x.B, tau, W, P, xx, yy)
-    gotB = dB[P, xx, yy]
-    e_B = np.linalg.norm(gotB - refB) / np.linalg.norm(refB)
-    print("%s full size: dtau sampled rel %.3e  dB sampled rel %.3e" % (mode, e_tau, e_B))
+    i, j, c, d = (np.asarray(t) for t in g["dtau_index"])
+    P, xx, yy = (np.asarray(t) for t in g["dB_index"])
+    e_tau = rel_err(dtau[i, j, c, d], np.asarray(g["dtau"]))
+    e_B = rel_err(dB[P, xx, yy], np.asarray(g["dB"]))
+    print("%s full size: dtau %d entries rel %.3e  dB %d entries rel %.3e" % (mode, len(i), e_tau, len(P), e_B))
+    assert len(i) >= 1000 and len(P) >= 1000
     assert e_tau < DTAU_TOL[mode]
     assert e_B < DTAU_TOL[mode]
     # the dtau output keeps the pair symmetry of the ladder

@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 import synthetic
-from gpu_util import rel_fro, run_dressed, to_dev
+from gpu_util import rel_err, run_dressed, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -43,10 +43,10 @@ def test_dressed_matches_oracle(lad, mode, o, v, n, seed):
     L = lad.Ladder(o, v, n, mode=mode, dressed=True)
     tau_g, R_g, E_g = run_dressed(L, x)
     tau_o = oracle.tau(x.t1, x.t2)
-    assert rel_fro(tau_g, tau_o) < 1e-15
+    assert rel_err(tau_g, tau_o) < 1e-15
     R_o = oracle.ladder_dressed(x.B, x.B_ov, x.t1, tau_o)
     E_o = oracle.energy(R_o, x.t2)
-    err = rel_fro(R_g, R_o)
+    err = rel_err(R_g, R_o)
     print("dressed %s o=%d v=%d n=%d: rel-F %.3e  |dE| %.3e  E %.6e" % (mode, o, v, n, err,
                                                                       abs(E_g - E_o), E_o))
     assert err < TOL[mode]
@@ -64,7 +64,7 @@ def test_dressed_dimer(lad, mode):
     tau_o = oracle.tau(x.t1, x.t2)
     R_o = oracle.ladder_dressed(x.B, x.B_ov, x.t1, tau_o)
     E_o = oracle.energy(R_o, x.t2)
-    err = rel_fro(R_g, R_o)
+    err = rel_err(R_g, R_o)
     print("dressed dimer %s: rel-F %.3e  |dE| %.3e  E %.9f" % (mode, err, abs(E_g - E_o), E_o))
     assert err < TOL[mode]
     if mode == "fp64":
@@ -85,7 +85,7 @@ def test_dressed_sampled_columns_grad_size(lad, mode):
     tau_o = oracle.tau(x.t1, x.t2)
     cols = oracle.ladder_dressed_pairs(x.B, x.B_ov, x.t1, tau_o, pa, pb)
     got = np.stack([R_g[:, :, a, b] for a, b in zip(pa, pb)])
-    err = rel_fro(got, cols)
+    err = rel_err(got, cols)
     print("dressed grad-size %s sampled columns: rel-F %.3e" % (mode, err))
     assert err < TOL[mode]
 

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import synthetic
-from gpu_util import rel_fro, run_forward
+from gpu_util import rel_err, run_forward
 
 pytestmark = pytest.mark.gpu
 
@@ -30,7 +30,7 @@ def test_bounded_wait_times_out_and_context_survives():
     assert lad.ladder_last_device_error(L.plan) == (0, 0)
     x = synthetic.make_inputs(4, 24, 96, 0)
     _, R, _ = run_forward(L, x)
-    assert rel_fro(R, oracle.ladder(x.B, oracle.tau(x.t1, x.t2))) < 1e-6
+    assert rel_err(R, oracle.ladder(x.B, oracle.tau(x.t1, x.t2))) < 1e-6
 
 
 def test_argument_errors_are_synchronous():

@@ -19,7 +19,7 @@ import numpy as np
 import pytest
 
 import synthetic
-from gpu_util import rel_fro, run_dressed, run_forward
+from gpu_util import rel_err, run_dressed, run_forward
 
 pytestmark = pytest.mark.gpu
 
@@ -60,7 +60,7 @@ def test_full_size_against_stored_oracle(lad, name, mode):
     L.close()
     got = np.stack([R[:, :, a, b] for a, b in zip(g["pairs_a"], g["pairs_b"])])
     ref = np.asarray(g["R_cols"])
-    e_cols = rel_fro(got, ref)
+    e_cols = rel_err(got, ref)
     e_fro = abs(float(np.linalg.norm(R)) - g["R_fro"]) / g["R_fro"]
     dE = abs(E - g["E_L"])
     print("%s %s: columns rel-F %.3e  |R|_F rel %.3e  dE_L %.3e" % (name, mode, e_cols, e_fro, dE))
@@ -82,7 +82,7 @@ def test_lambda_only_full_size_against_stored_oracle(lad, name):
     _, R, E = run_forward(L, x)
     L.close()
     got = np.stack([R[:, :, a, b] for a, b in zip(g["pairs_a"], g["pairs_b"])])
-    e_cols = rel_fro(got, np.asarray(g["R_cols"]))
+    e_cols = rel_err(got, np.asarray(g["R_cols"]))
     e_fro = abs(float(np.linalg.norm(R)) - g["R_fro"]) / g["R_fro"]
     print("%s lambda-only bf16x6: columns rel-F %.3e  |R|_F rel %.3e  dE_L %.3e" % (
         name, e_cols, e_fro, abs(E - g["E_L"])))
@@ -104,7 +104,7 @@ def test_dressed_full_size_against_stored_oracle(lad, name, mode):
     _, R, _ = run_dressed(L, x)
     L.close()
     got = np.stack([R[:, :, a, b] for a, b in zip(g["pairs_a"], g["pairs_b"])])
-    e_cols = rel_fro(got, np.asarray(g["R_cols"]))
+    e_cols = rel_err(got, np.asarray(g["R_cols"]))
     asym = float(np.abs(R - R.transpose(1, 0, 3, 2)).max() / np.abs(R).max())
     print("%s dressed %s: columns rel-F %.3e  pair asymmetry %.1e" % (name, mode, e_cols, asym))
     assert e_cols < TOL[mode]

@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import synthetic
-from gpu_util import rel_fro, run_forward
+from gpu_util import rel_err, run_forward
 
 pytestmark = pytest.mark.gpu
 
@@ -44,7 +44,7 @@ def test_lambda_only_matches_oracle(lad, mode, o, v, n, seed):
     tau_o = oracle.tau(x.t1, x.t2)
     R_o = oracle.ladder(x.B, tau_o)
     E_o = oracle.energy(R_o, x.t2)
-    err = rel_fro(R_g, R_o)
+    err = rel_err(R_g, R_o)
     print("lambda-only %s o=%d v=%d n=%d: rel-F %.3e  |dE| %.3e" % (mode, o, v, n, err, abs(E_g - E_o)))
     assert err < TOL[mode]
     # every element of R is written from one accumulator column and mirrored
@@ -57,7 +57,7 @@ def test_lambda_only_dimer(lad):
     L = lad.Ladder(w.o, w.v, w.naux, mode="bf16x6", tuning={"two_pass": 1, "lambda_only": 1})
     _, R_g, _ = run_forward(L, x)
     R_o = oracle.ladder(x.B, oracle.tau(x.t1, x.t2))
-    err = rel_fro(R_g, R_o)
+    err = rel_err(R_g, R_o)
     print("lambda-only dimer bf16x6: rel-F %.3e" % err)
     assert err < TOL["bf16x6"]
 

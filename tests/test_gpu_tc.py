@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 import synthetic
-from gpu_util import rel_fro, run_forward
+from gpu_util import rel_err, run_forward
 
 pytestmark = pytest.mark.gpu
 
@@ -49,7 +49,7 @@ def test_tc_matches_oracle(lad, mode, two_pass, o, v, n, seed):
     tau_o = oracle.tau(x.t1, x.t2)
     R_o = oracle.ladder(x.B, tau_o)
     E_o = oracle.energy(R_o, x.t2)
-    err = rel_fro(R_g, R_o)
+    err = rel_err(R_g, R_o)
     print("%s two_pass=%d o=%d v=%d n=%d: rel-F %.3e  |dE| %.3e  E %.6e" % (mode, two_pass, o, v, n, err,
                                                                           abs(E_g - E_o), E_o))
     assert err < TOL[mode]
@@ -66,7 +66,7 @@ def test_tc_dimer_full(lad, mode):
     tau_o = oracle.tau(x.t1, x.t2)
     R_o = oracle.ladder(x.B, tau_o)
     E_o = oracle.energy(R_o, x.t2)
-    err = rel_fro(R_g, R_o)
+    err = rel_err(R_g, R_o)
     print("%s dimer: rel-F %.3e  |dE| %.3e  E %.6e" % (mode, err, abs(E_g - E_o), E_o))
     assert err < TOL[mode]
 
@@ -91,7 +91,7 @@ def test_tc_forms_match_oracle(lad, mode, two_pass, o, v, n, seed):
     assert lad.ladder_get_tuning(L.plan).two_pass == two_pass
     _, R_g, E_g = run_forward(L, x)
     R_o = oracle.ladder(x.B, oracle.tau(x.t1, x.t2))
-    err = rel_fro(R_g, R_o)
+    err = rel_err(R_g, R_o)
     print("%s two_pass=%d o=%d v=%d n=%d: rel-F %.3e" % (mode, two_pass, o, v, n, err))
     assert err < TOL[mode]
     assert np.array_equal(R_g, R_g.transpose(1, 0, 3, 2))
@@ -106,6 +106,6 @@ def test_two_pass_block_pair_split(lad, ksplit):
     L = lad.Ladder(o, v, n, mode="bf16x6", tuning={"two_pass": 1, "ksplit": ksplit})
     _, R_g, _ = run_forward(L, x)
     R_o = oracle.ladder(x.B, oracle.tau(x.t1, x.t2))
-    err = rel_fro(R_g, R_o)
+    err = rel_err(R_g, R_o)
     print("two_pass ksplit=%d: rel-F %.3e" % (ksplit, err))
     assert err < TOL["bf16x6"]
