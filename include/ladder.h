@@ -133,6 +133,28 @@ ladder_status ladder_set_tuning(ladder_plan_t plan, const ladder_tuning *t);
 /* Mode the plan resolved to (LADDER_AUTO resolves at plan time). */
 ladder_status ladder_plan_mode(ladder_plan_t plan, int *mode);
 
+/* Multi-GPU partition of one molecule's term (the GPU analogue of the
+ * paper's split of the virtual pairs over domains, Sec. II.D, Eq. pp-Ladder-3).
+ * The split-BF16 and error-free modes evaluate R in tiles of 128 virtual
+ * pairs {a, b} (a in a block of 16, b in a block of 8, a <= b); every tile
+ * costs the same and writes R_ij^ab and R_ij^ba for all (i, j) of its pairs
+ * and nothing else.  ladder_tile_count gives the shape's tile count;
+ * ladder_set_tile_range (before ladder_set_workspace) restricts the plan to
+ * tiles [tile_lo, tile_hi): ladder_apply then reads all of B and tau, writes
+ * only those tiles' entries of R (the rest of R is left as it was) and needs
+ * a workspace for those tiles only.  Ranks holding B and tau in full that
+ * zero R, apply disjoint ranges covering [0, ntiles) and add their R
+ * (all-reduce) assemble the full term; ladder_energy of a rank's R is its
+ * share of E_L.  Tiles are enumerated a-block major: a in [16 iA, 16 iA + 16),
+ * b in [8 jB, 8 jB + 8) for iA = 0, 1, ... and jB = 2 iA .. vp/8 - 1 (vp = v
+ * rounded up to 16).  LADDER_FP64 plans return LADDER_ENOTSUP; a plan with a
+ * partial range refuses ladder_backward and ladder_apply_dressed
+ * (LADDER_ENOTSUP).  The range also sets the plan's block-pair splits
+ * (ksplit) anew; set ksplit afterwards with ladder_set_tuning to match
+ * another plan's. */
+ladder_status ladder_tile_count(ladder_plan_t plan, int *ntiles);
+ladder_status ladder_set_tile_range(ladder_plan_t plan, int tile_lo, int tile_hi);
+
 /* Bytes of device scratch the plan needs (slices of B and tau, packed pair
  * combinations, reduction partials, the device status word).  The caller
  * allocates it and hands it over with ladder_set_workspace; the plan keeps
@@ -253,7 +275,8 @@ ladder_status ladder_apply_host(ladder_plan_t plan, const double *B_host, const 
  * first); molecules that need several chunks take the two-pass form (see
  * ladder_tuning) while their stored V+- tiles fit 128 GiB in all, with one
  * storing launch and one GEMM2 launch over all of them.  A batched plan
- * serves only ladder_apply_batched (the other calls return LADDER_EINVAL);
+ * serves only ladder_apply_batched and ladder_step_batched (the other calls
+ * return LADDER_EINVAL);
  * ladder_energy_noalloc gives the energy of each molecule. */
 ladder_status ladder_plan_batched(int n, const int *o, const int *v, const int *naux, int mode,
                                   ladder_plan_t *out);
@@ -274,6 +297,20 @@ ladder_status ladder_set_member_tuning(ladder_plan_t plan, int m, const ladder_t
  * synchronising. */
 ladder_status ladder_apply_batched(ladder_plan_t plan, const double *const *B,
                                    const double *const *tau, double *const *R, void *stream);
+
+/* One whole step per molecule of a batch, in one CUDA graph:
+ *   tau[k] = t2[k] + t1[k] (x) t1[k]                       (Eq. pp-Ladder-01)
+ *   R[k]_ij^ab = sum_cd (ac|bd) tau[k]_ij^cd                (Eq. pp-Ladder-0)
+ *   E[k] = sum_ijab R[k]_ij^ab (2 t2[k]_ij^ab - t2[k]_ij^ba)
+ * B[k], t1[k] [o_k][v_k], t2[k], tau[k] (written), R[k] (written) are device
+ * pointers for molecule k (host arrays of n pointers); E is a device array of
+ * n doubles.  tau[k] may not alias t2[k].  As for ladder_apply_batched, the
+ * first call with a set of pointers records the graph (synchronising
+ * `stream`) and later calls with the same pointers replay it; the energies
+ * use each member's share of the batch workspace for their partial sums. */
+ladder_status ladder_step_batched(ladder_plan_t plan, const double *const *B, const double *const *t1,
+                                  const double *const *t2, double *const *tau, double *const *R,
+                                  double *E, void *stream);
 
 /* Reads and clears the device status word (synchronises `stream`).
  * Returns LADDER_OK, LADDER_ETIMEOUT (a bounded wait ran out; *where receives

@@ -27,10 +27,11 @@ STATUS = {0: "LADDER_OK", 1: "LADDER_EINVAL", 2: "LADDER_ENOMEM", 3: "LADDER_ECU
           4: "LADDER_ETIMEOUT", 5: "LADDER_ENOTSUP", 6: "LADDER_EWORKSPACE", 7: "LADDER_ENONFINITE"}
 
 # every entry point that include/ladder.h declares
-EXPORTS = ("ladder_plan", "ladder_plan_mode", "ladder_get_tuning", "ladder_set_tuning", "ladder_workspace_size", "ladder_set_workspace",
+EXPORTS = ("ladder_plan", "ladder_plan_mode", "ladder_get_tuning", "ladder_set_tuning", "ladder_tile_count",
+           "ladder_set_tile_range", "ladder_workspace_size", "ladder_set_workspace",
            "ladder_tau", "ladder_apply", "ladder_apply_dressed", "ladder_triples_workspace_size",
            "ladder_triples", "ladder_energy", "ladder_energy_noalloc", "ladder_backward", "ladder_pair_combine", "ladder_apply_host",
-           "ladder_plan_batched", "ladder_set_member_tuning", "ladder_apply_batched", "ladder_last_device_error", "ladder_selftest_wait",
+           "ladder_plan_batched", "ladder_set_member_tuning", "ladder_apply_batched", "ladder_step_batched", "ladder_last_device_error", "ladder_selftest_wait",
            "ladder_set_timing", "ladder_timing", "ladder_timing_passes", "ladder_timing_dressing", "ladder_flops", "ladder_status_string",
            "ladder_destroy")
 
@@ -70,6 +71,8 @@ def load_library(path: str = LIB_PATH):
         "ladder_plan_mode": [_P, ip],
         "ladder_get_tuning": [_P, ctypes.POINTER(Tuning)],
         "ladder_set_tuning": [_P, ctypes.POINTER(Tuning)],
+        "ladder_tile_count": [_P, ip],
+        "ladder_set_tile_range": [_P, i, i],
         "ladder_workspace_size": [_P, ctypes.POINTER(sz)],
         "ladder_set_workspace": [_P, _P, sz],
         "ladder_tau": [_P, _P, _P, _P, _P],
@@ -85,6 +88,7 @@ def load_library(path: str = LIB_PATH):
         "ladder_plan_batched": [i, ip, ip, ip, i, pp],
         "ladder_set_member_tuning": [_P, i, ctypes.POINTER(Tuning)],
         "ladder_apply_batched": [_P, pp, pp, pp, _P],
+        "ladder_step_batched": [_P, pp, pp, pp, pp, pp, _P, _P],
         "ladder_last_device_error": [_P, _P, ip],
         "ladder_selftest_wait": [_P, ctypes.c_ulonglong, _P],
         "ladder_set_timing": [_P, i],
@@ -145,6 +149,16 @@ def ladder_get_tuning(plan) -> Tuning:
 
 def ladder_set_tuning(plan, t: Tuning) -> None:
     _check("ladder_set_tuning", load_library().ladder_set_tuning(plan, ctypes.byref(t)))
+
+
+def ladder_tile_count(plan) -> int:
+    n = ctypes.c_int()
+    _check("ladder_tile_count", load_library().ladder_tile_count(plan, ctypes.byref(n)))
+    return n.value
+
+
+def ladder_set_tile_range(plan, tile_lo: int, tile_hi: int) -> None:
+    _check("ladder_set_tile_range", load_library().ladder_set_tile_range(plan, int(tile_lo), int(tile_hi)))
 
 
 def ladder_workspace_size(plan) -> int:
@@ -251,6 +265,13 @@ def ladder_apply_batched(plan, Bs, taus, Rs, stream=None) -> None:
         plan, arr(Bs), arr(taus), arr(Rs), _stream(stream)))
 
 
+def ladder_step_batched(plan, Bs, t1s, t2s, taus, Rs, E, stream=None) -> None:
+    n = len(Bs)
+    arr = lambda ts: (ctypes.c_void_p * n)(*[t.data_ptr() for t in ts])
+    _check("ladder_step_batched", load_library().ladder_step_batched(
+        plan, arr(Bs), arr(t1s), arr(t2s), arr(taus), arr(Rs), _ptr(E), _stream(stream)))
+
+
 def ladder_last_device_error(plan, stream=None):
     where = ctypes.c_int()
     st = load_library().ladder_last_device_error(plan, _stream(stream), ctypes.byref(where))
@@ -307,12 +328,14 @@ class Ladder:
     """A plan plus its workspace (a torch uint8 tensor on the current device)."""
 
     def __init__(self, o: int, v: int, naux: int, mode="bf16x6", device=None, backward=False,
-                 tuning=None, dressed=False):
+                 tuning=None, dressed=False, tiles=None):
         """mode: "fp64", "bf16x3", "bf16x6", "ozaki" (the error-free split, FP64-class
         accuracy from the BF16 tensor cores), or "tuned" (the autotuner's cached
         choice of mode and launch parameters for this shape, see tune.py);
         tuning: a dict of ladder_tuning fields to override; dressed: size the
-        workspace for apply_dressed (the t1-dressed term) as well."""
+        workspace for apply_dressed (the t1-dressed term) as well; tiles:
+        (lo, hi) restricts the plan to pair tiles [lo, hi) (see partition.py),
+        applied before the tuning."""
         import torch
         self.o, self.v, self.naux = o, v, naux
         if mode == "tuned":
@@ -327,6 +350,8 @@ class Ladder:
         with torch.cuda.device(self.device):
             self.plan = ladder_plan(o, v, naux, m)
             self.mode = ladder_plan_mode(self.plan)
+            if tiles is not None:
+                ladder_set_tile_range(self.plan, tiles[0], tiles[1])
             if tuning and self.mode != LADDER_FP64:
                 t = ladder_get_tuning(self.plan)
                 for k, val in tuning.items():
@@ -453,6 +478,16 @@ class LadderBatch:
         outs = [torch.empty_like(t) for t in taus] if outs is None else outs
         ladder_apply_batched(self.plan, Bs, taus, outs)
         return outs
+
+    def step(self, Bs, t1s, t2s, taus=None, outs=None, E=None):
+        """One graph for every molecule: tau = t2 + t1 (x) t1, R, and E_L per
+        molecule (a device tensor of n doubles); returns (taus, outs, E)."""
+        import torch
+        taus = [torch.empty_like(t) for t in t2s] if taus is None else taus
+        outs = [torch.empty_like(t) for t in t2s] if outs is None else outs
+        E = torch.empty(len(Bs), dtype=torch.float64, device=t2s[0].device) if E is None else E
+        ladder_step_batched(self.plan, Bs, t1s, t2s, taus, outs, E)
+        return taus, outs, E
 
     def check_device(self):
         st, where = ladder_last_device_error(self.plan)

@@ -162,6 +162,8 @@ struct TcArgs {
   int nks;           // Np / 32
   int nA, nB8;       // 16-blocks of a, 8-blocks of b
   int ntiles, nchunks, ksplit;
+  int tile0;         // first (a 16-block, b 8-block) tile of the plan's range; the
+                     // work units and stored planes index tiles from it
   int racc_cols;
   int kc;            // GEMM1 K-steps (of 32 aux functions) per FP32 accumulation chain
   int xy_split;      // GEMM1: separate accumulators for hi*hi and the smaller products
@@ -235,6 +237,7 @@ struct OzArgs {
   int *status;
   int o, v, vp, Np, nbp, nks;
   int nB8, ntiles, nchunks, ksplit, racc_cols;
+  int tile0;             // the plan's tiles are tile0 .. tile0 + ntiles - 1 (local index t - tile0)
   int nitems;
   unsigned long long timeout_ns;
   TcChunk chunks[kMaxChunks];

@@ -103,6 +103,9 @@ struct ladder_plan_s {
   int two_pass = 0, vsplit = 1, racc_cols_v = 0, nplus = 0, wplus = 0, wminus = 0;
   int lam_only = 0;  // the paper's lambda-only contraction (two-pass form only)
   int oz_slices = kOzDefaultSlices;  // error-free mode: fixed-point slices per operand
+  // pair-tile range of the plan (multi-GPU partition): tiles tile0 ..
+  // tile0 + ntiles_tc - 1 of the shape's ntiles_all
+  int tile0 = 0, ntiles_all = 0;
   bool last_two_pass = false;
   std::vector<TcChunk> chunks_v;
   CUtensorMap tmA, tmB, tmTp, tmTm, tmVl;
@@ -758,6 +761,7 @@ static ladder_status init_plan(ladder_plan_s *pl, int o, int v, int naux, int mo
     const int nA = pl->vp / 16, nB8 = pl->vp / CB;
     pl->ntiles_tc = 0;
     for (int i = 0; i < nA; ++i) pl->ntiles_tc += nB8 - 2 * i;
+    pl->ntiles_all = pl->ntiles_tc;
     pl->two_pass = 1;
     pl->ksplit = auto_ksplit(pl);
     pl->vsplit = auto_vsplit(pl, false);
@@ -778,6 +782,7 @@ static ladder_status init_plan(ladder_plan_s *pl, int o, int v, int naux, int mo
     const int nA = pl->vp / 16, nB8 = pl->vp / CB;
     pl->ntiles_tc = 0;
     for (int i = 0; i < nA; ++i) pl->ntiles_tc += nB8 - 2 * i;
+    pl->ntiles_all = pl->ntiles_tc;
     // two-pass form whenever the stored tiles fit the default cap: it avoids
     // the fused kernel's per-chunk GEMM1 recompute, and its storing pass
     // issues wider MMAs, so it measured faster even where one chunk suffices
@@ -888,6 +893,25 @@ ladder_status ladder_set_tuning(ladder_plan_t pl, const ladder_tuning *t) {
   pl->xy_split = t->xy_split;
   pl->two_pass = t->two_pass;
   pl->ksplit = t->ksplit ? t->ksplit : auto_ksplit(pl);
+  compute_layout(pl);
+  return LADDER_OK;
+}
+
+ladder_status ladder_tile_count(ladder_plan_t pl, int *ntiles) {
+  if (!pl || !ntiles || pl->batched) return LADDER_EINVAL;
+  if (pl->mode == LADDER_FP64) return LADDER_ENOTSUP;
+  *ntiles = pl->ntiles_all;
+  return LADDER_OK;
+}
+
+ladder_status ladder_set_tile_range(ladder_plan_t pl, int tile_lo, int tile_hi) {
+  if (!pl || pl->batched || pl->ws) return LADDER_EINVAL;
+  if (pl->mode == LADDER_FP64) return LADDER_ENOTSUP;
+  if (tile_lo < 0 || tile_hi > pl->ntiles_all || tile_lo >= tile_hi) return LADDER_EINVAL;
+  pl->tile0 = tile_lo;
+  pl->ntiles_tc = tile_hi - tile_lo;
+  pl->ksplit = auto_ksplit(pl);
+  pl->vsplit = auto_vsplit(pl, false);
   compute_layout(pl);
   return LADDER_OK;
 }
@@ -1056,6 +1080,7 @@ static TcArgs tc_args(const ladder_plan_s *pl, double *R, int *status) {
   a.nA = pl->vp / 16;
   a.nB8 = pl->vp / CB;
   a.ntiles = pl->ntiles_tc;
+  a.tile0 = pl->tile0;
   a.nchunks = (int)pl->chunks_tc.size();
   a.ksplit = pl->ksplit;
   a.racc = ws_at<float2>(pl, pl->lay.slab);
@@ -1226,6 +1251,7 @@ static ladder_status apply_oz(ladder_plan_t pl, const double *B, const double *t
   a.nks = pl->Np / 32;
   a.nB8 = pl->vp / CB;
   a.ntiles = pl->ntiles_tc;
+  a.tile0 = pl->tile0;
   a.nchunks = (int)pl->chunks_v.size();
   for (int c = 0; c < a.nchunks; ++c) a.chunks[c] = pl->chunks_v[c];
   a.racc_cols = pl->racc_cols_v;
@@ -1272,6 +1298,7 @@ ladder_status ladder_apply_dressed(ladder_plan_t pl, const double *B, const doub
                                    const double *t1, const double *tau, double *R, void *stream) {
   if (!pl || pl->batched || !pl->dressed) return LADDER_EINVAL;
   if (!pl->ws) return LADDER_EWORKSPACE;
+  if (pl->ntiles_tc != pl->ntiles_all) return LADDER_ENOTSUP;  // the correction spans all of R
   if (!dev_ptr_ok(B) || !dev_ptr_ok(Bov) || !dev_ptr_ok(t1) || !dev_ptr_ok(tau) || !dev_ptr_ok(R) ||
       R == B || R == tau || R == Bov || R == t1)
     return LADDER_EINVAL;
@@ -1358,7 +1385,7 @@ ladder_status ladder_backward(ladder_plan_t pl, const double *B, const double *t
   if (dtau && (!dev_ptr_ok(dtau) || dtau == W || dtau == tau || dtau == B)) return LADDER_EINVAL;
   if (dB && (!dev_ptr_ok(dB) || dB == B)) return LADDER_EINVAL;
   if (dB && !pl->backward) return LADDER_EWORKSPACE;
-  if (pl->mode == LADDER_OZAKI) return LADDER_ENOTSUP;
+  if (pl->mode == LADDER_OZAKI || pl->ntiles_tc != pl->ntiles_all) return LADDER_ENOTSUP;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (dtau) {
     // transposed ladder: dtau = sum_ab W_ij^ab (ac|bd), i.e. the ladder of W
@@ -1665,26 +1692,40 @@ ladder_status ladder_set_member_tuning(ladder_plan_t pl, int m, const ladder_tun
   return LADDER_OK;
 }
 
-ladder_status ladder_apply_batched(ladder_plan_t pl, const double *const *B,
-                                   const double *const *tau, double *const *R, void *stream) {
+// Records (or replays) one batch step as a CUDA graph.  With t1, t2 and E
+// given, every molecule's step starts with tau = t2 + t1 (x) t1 into tau[m]
+// and ends with its ladder energy into E[m]; without them tau[m] is an input.
+static ladder_status batch_run(ladder_plan_t pl, const double *const *B, const double *const *t1,
+                               const double *const *t2, double *const *tau, double *const *R, double *E,
+                               void *stream) {
   if (!pl || !pl->batched) return LADDER_EINVAL;
   if (!pl->ws) return LADDER_EWORKSPACE;
   if (!B || !tau || !R) return LADDER_EINVAL;
+  const bool step = t1 != nullptr;
+  if (step && (!t2 || !dev_ptr_ok(E, 8))) return LADDER_EINVAL;
   const size_t n = pl->subs.size();
   std::vector<const void *> key;
   for (size_t m = 0; m < n; ++m) {
     if (!dev_ptr_ok(B[m]) || !dev_ptr_ok(tau[m]) || !dev_ptr_ok(R[m]) || R[m] == B[m] ||
         R[m] == tau[m])
       return LADDER_EINVAL;
+    if (step && (!dev_ptr_ok(t1[m]) || !dev_ptr_ok(t2[m]) || tau[m] == t2[m] || R[m] == t2[m]))
+      return LADDER_EINVAL;
     key.push_back(B[m]);
     key.push_back(tau[m]);
     key.push_back(R[m]);
+    if (step) {
+      key.push_back(t1[m]);
+      key.push_back(t2[m]);
+    }
   }
+  key.push_back(step ? E : nullptr);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (!pl->gexec || key != pl->gkey) {
     // (re)build: per-molecule arguments into the workspace table, then capture
-    // the whole batch (operand preparation of every molecule, one fused launch
-    // over the cost-sorted work units of all molecules, one unpack launch)
+    // the whole batch (tau assembly and operand preparation of every
+    // molecule, the fused, storing and GEMM2 launches over all molecules, the
+    // unpacks, and every molecule's energy)
     char *w = static_cast<char *>(pl->ws);
     int *status = ws_at<int>(pl, pl->lay.status);
     std::vector<TcArgs> args(n), args1(n), args2(n);
@@ -1731,18 +1772,22 @@ ladder_status ladder_apply_batched(ladder_plan_t pl, const double *const *B,
     cudaStream_t c = pl->cap_stream;
     if (cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return cuda_status(cudaErrorUnknown);
-    // operand preparation of every molecule; fused members in one persistent
-    // launch over their cost-sorted work units; two-pass members in one
-    // storing launch and one GEMM2 launch over all of them; the unpacks
     for (size_t m = 0; m < n; ++m) {
+      const ladder_plan_s *sp = pl->subs[m];
+      if (step) launch_tau(sp->o, sp->v, t1[m], t2[m], tau[m], c);
       tc_prep(pl->subs[m], B[m], tau[m], c, false, status);
-      if (pl->subs[m]->two_pass) pack_t2(pl->subs[m], c);
+      if (sp->two_pass) pack_t2(sp, c);
     }
     if (L.nitems) launch_ladder_tc(L, pl->S, std::min(L.nitems, pl->sm_count), c);
     if (L1.nitems) launch_ladder_vstore(L1, pl->S, std::min(L1.nitems, pl->sm_count), c);
     if (L2.nitems) launch_ladder_gemm2(L2, pl->S, std::min(L2.nitems, pl->sm_count), c);
     if (!pl->tcs.empty()) launch_unpack(L, (int)pl->tcs.size(), c);
     if (!pl->tcs2.empty()) launch_unpack2(L2, (int)pl->tcs2.size(), c);
+    if (step)
+      for (size_t m = 0; m < n; ++m) {
+        const ladder_plan_s *sp = pl->subs[m];
+        launch_energy(sp->o, sp->v, R[m], t2[m], ws_at<double>(sp, sp->lay.energy), E + m, c);
+      }
     cudaGraph_t graph = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(c, &graph);
     if (ce != cudaSuccess || !graph) return cuda_status(ce == cudaSuccess ? cudaErrorUnknown : ce);
@@ -1761,6 +1806,18 @@ ladder_status ladder_apply_batched(ladder_plan_t pl, const double *const *B,
   mark(pl, 2, s);
   mark(pl, 3, s);
   return st;
+}
+
+ladder_status ladder_apply_batched(ladder_plan_t pl, const double *const *B,
+                                   const double *const *tau, double *const *R, void *stream) {
+  return batch_run(pl, B, nullptr, nullptr, const_cast<double *const *>(tau), R, nullptr, stream);
+}
+
+ladder_status ladder_step_batched(ladder_plan_t pl, const double *const *B, const double *const *t1,
+                                  const double *const *t2, double *const *tau, double *const *R, double *E,
+                                  void *stream) {
+  if (!t1 || !t2) return LADDER_EINVAL;
+  return batch_run(pl, B, t1, t2, tau, R, E, stream);
 }
 
 ladder_status ladder_last_device_error(ladder_plan_t pl, void *stream, int *where) {

@@ -143,7 +143,7 @@ __device__ __forceinline__ Item decode(const OzArgs &A, int slot, int nchunks) {
   const int tc = slot / A.ksplit;
   const int tile = tc / nchunks;
   I.ch = tc % nchunks;
-  int iA = 0, t = tile;
+  int iA = 0, t = tile + A.tile0;  // tile0: first tile of the plan's range
   while (t >= A.nB8 - 2 * iA) {
     t -= A.nB8 - 2 * iA;
     ++iA;

@@ -155,7 +155,7 @@ __device__ __forceinline__ Item decode_item(const TcArgs &A, int item) {
   const int ksl = item % A.ksplit;
   const int tc = item / A.ksplit;
   const int tile = tc / A.nchunks, ch = tc % A.nchunks;
-  int iA = 0, t = tile;
+  int iA = 0, t = tile + A.tile0;  // tile0: first tile of the plan's range
   if (A.square) {
     iA = tile / A.nB8;
     t = tile % A.nB8 - 2 * iA;
@@ -668,7 +668,7 @@ __global__ void __launch_bounds__(128) unpack_kernel(const __grid_constant__ TcL
   const TcArgs &A = Lp.mols ? Lp.mols[Lp.tcs[blockIdx.x].x] : Lp.one;
   tc = Lp.mols ? Lp.tcs[blockIdx.x].y : (int)blockIdx.x;
   const int tile = tc / A.nchunks, ch = tc % A.nchunks;
-  int iA = 0, t = tile;
+  int iA = 0, t = tile + A.tile0;
   while (t >= A.nB8 - 2 * iA) {
     t -= A.nB8 - 2 * iA;
     ++iA;
@@ -969,7 +969,7 @@ __global__ void __launch_bounds__(128) unpack2_kernel(const __grid_constant__ Tc
   const TcArgs &A = Lp.mols ? Lp.mols[Lp.tcs[blockIdx.x].x] : Lp.one;
   const int blk = Lp.mols ? Lp.tcs[blockIdx.x].y : (int)blockIdx.x;
   const int tile = blk / A.nplus, cp = blk % A.nplus;
-  int iA = 0, t = tile;
+  int iA = 0, t = tile + A.tile0;
   while (t >= A.nB8 - 2 * iA) {
     t -= A.nB8 - 2 * iA;
     ++iA;
@@ -1017,7 +1017,7 @@ __global__ void __launch_bounds__(128) unpack2_kernel(const __grid_constant__ Tc
 __global__ void __launch_bounds__(128) unpack_lam_kernel(const __grid_constant__ TcLaunch Lp) {
   const TcArgs &A = Lp.one;
   const int tc = blockIdx.x, tile = tc / A.nchunks, ch = tc % A.nchunks;
-  int iA = 0, t = tile;
+  int iA = 0, t = tile + A.tile0;
   while (t >= A.nB8 - 2 * iA) {
     t -= A.nB8 - 2 * iA;
     ++iA;

@@ -164,3 +164,66 @@ def test_batch_tuned_mode(lad):
     batch.check_device()
     for k, x in enumerate(mols):
         assert rel_err(R[k].cpu().numpy(), oracle.ladder(x.B, taus[k])) < TOL["bf16x6"]
+
+
+def _e_scale(R, t2):
+    """sum |R_ij^ab (2 t_ij^ab - t_ij^ba)|: the scale of E_L's rounding."""
+    return float(np.sum(np.abs(R * (2.0 * t2 - t2.transpose(0, 1, 3, 2)))))
+
+
+@pytest.mark.parametrize("mode", ["bf16x6", "bf16x3"])
+def test_step_batched_tau_ladder_energy(lad, mode):
+    """ladder_step_batched: tau assembly, the ladder and E_L of every molecule
+    in one graph, from t1 and t2 on the device.  tau against the oracle to
+    rounding, R within the mode's bar, E_L within it relative to the sum of
+    its terms' magnitudes, and a replay with the same pointers bitwise equal."""
+    import torch
+    mols = [synthetic.make_inputs(o, v, n, s) for o, v, n, s in SHAPES + TWO_PASS_SHAPES[:2]]
+    batch = lad.LadderBatch([(x.o, x.v, x.naux) for x in mols], mode=mode)
+    Bs, t1s, t2s = ([to_dev(getattr(x, a)) for x in mols] for a in ("B", "t1", "t2"))
+    taus, Rs, E = batch.step(Bs, t1s, t2s)
+    torch.cuda.synchronize()
+    batch.check_device()
+    first = ([t.cpu().numpy() for t in taus], [r.cpu().numpy() for r in Rs], E.cpu().numpy())
+    batch.step(Bs, t1s, t2s, taus, Rs, E)   # replay
+    torch.cuda.synchronize()
+    for k, x in enumerate(mols):
+        tau_o = oracle.tau(x.t1, x.t2)
+        R_o = oracle.ladder(x.B, tau_o)
+        E_o = oracle.energy(R_o, x.t2)
+        e_tau = rel_err(first[0][k], tau_o)
+        e_R = rel_err(first[1][k], R_o)
+        e_E = abs(first[2][k] - E_o) / _e_scale(R_o, x.t2)
+        print("%s molecule %d (o=%d v=%d n=%d): tau %.1e  R %.3e  E_L %.3e" % (mode, k, x.o, x.v, x.naux,
+                                                                            e_tau, e_R, e_E))
+        assert e_tau < 1e-15
+        assert e_R < TOL[mode]
+        assert e_E < TOL[mode]
+        assert np.array_equal(Rs[k].cpu().numpy(), first[1][k])
+    assert np.array_equal(E.cpu().numpy(), first[2])
+    batch.close()
+
+
+def test_ragged48_step_energies(lad):
+    """The 48-molecule ragged batch through ladder_step_batched: every
+    member's E_L against the oracle for the members with v <= 64 (the oracle
+    needs the whole R), and tau of every member to rounding."""
+    import torch
+    mols = synthetic.ragged_batch()
+    batch = lad.LadderBatch([(x.o, x.v, x.naux) for x in mols], mode="tuned")
+    Bs, t1s, t2s = ([to_dev(getattr(x, a)) for x in mols] for a in ("B", "t1", "t2"))
+    taus, Rs, E = batch.step(Bs, t1s, t2s)
+    torch.cuda.synchronize()
+    batch.check_device()
+    E = E.cpu().numpy()
+    worst, nE = 0.0, 0
+    for k, x in enumerate(mols):
+        tau_o = oracle.tau(x.t1, x.t2)
+        assert rel_err(taus[k].cpu().numpy(), tau_o) < 1e-15
+        if x.v <= 64:
+            R_o = oracle.ladder(x.B, tau_o)
+            worst = max(worst, abs(E[k] - oracle.energy(R_o, x.t2)) / _e_scale(R_o, x.t2))
+            nE += 1
+    print("ragged48 step: %d energies checked, worst %.3e" % (nE, worst))
+    assert nE >= 1 and worst < TOL["bf16x6"]
+    batch.close()
