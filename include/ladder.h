@@ -79,9 +79,10 @@ typedef enum {
  * with 5 slices, 2^-48 with 6) and the double-single sums.  The mode always
  * runs the two-pass form and stores its sliced V+- tiles (S x 32 KiB per ab
  * tile and block pair: 136 GB at o=34, v=400, N_aux=1600 with 5 slices);
- * shapes whose tiles exceed 200 GiB return LADDER_ENOTSUP, as do
- * ladder_backward and batch plans.  ladder_apply_dressed runs its correction
- * in FP64 in this mode. */
+ * where all tiles would exceed 200 GiB it runs them in sequential ranges (see
+ * tile_chunk in ladder_tuning).  ladder_backward and batch plans return
+ * LADDER_ENOTSUP.  ladder_apply_dressed runs its correction in FP64 in this
+ * mode. */
 
 /* OR this into `mode` to size the workspace for ladder_backward as well
  * (the FP64 gradient with respect to B spills tiles of Gamma^{xb}_{yd}). */
@@ -109,8 +110,8 @@ ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out);
  *               pairs); 1: GEMM1 once per (ab tile, block pair) with the
  *               sliced V+- tiles stored in the workspace (2S x 16 KiB per
  *               tile and block pair), then GEMM2 from the stored tiles in
- *               chunks of up to 192 occupied pairs.  The plan picks 1 when the
- *               stored tiles take at most 128 GiB (LADDER_OZAKI: always 1).
+ *               chunks of up to 192 occupied pairs.  Single-molecule plans
+ *               pick 1 (LADDER_OZAKI: always 1);
  *   lambda_only 1: the paper's own contraction, which uses only the pair
  *               symmetry R_ij^ab = R_ji^ba (Sec. II.C), as an ablation of the
  *               +- split: the storing pass keeps (ac|bd) and (ad|bc) instead
@@ -119,13 +120,22 @@ ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out);
  *               two_pass = 1; 0 (default) is the +- form.
  *   oz_slices   LADDER_OZAKI only: fixed-point slices per operand, 5 (default)
  *               or 6; 0 keeps the plan's value.  The other fields of
- *               LADDER_OZAKI plans are fixed, except ksplit.
+ *               LADDER_OZAKI plans are fixed, except ksplit and tile_chunk;
+ *   tile_chunk  two-pass form and LADDER_OZAKI: tiles of 128 virtual pairs per
+ *               sequential range (both passes and the unpack run range by
+ *               range, reusing the stored-tile space; GEMM1 still runs once
+ *               per tile and block pair, B and tau are re-read per range).
+ *               0 (default): as many as keep one range's stored V+- tiles
+ *               within 128 GiB (200 GiB for LADDER_OZAKI), which is all of
+ *               them for o=34, v=400; >= 0.  With several ranges
+ *               ladder_timing_passes reports the ladder kernels as pass 1
+ *               and 0 for pass 2.
  * Longer chains are faster and less accurate (the tensor core's FP32
  * accumulation error grows with the MMAs per accumulator).  ladder_set_tuning
  * must come before ladder_set_workspace (the workspace size depends on
  * ksplit and two_pass); it returns LADDER_EINVAL for out-of-range values. */
 typedef struct {
-    int kc, s_pieces, flush_every, ksplit, xy_split, two_pass, lambda_only, oz_slices;
+    int kc, s_pieces, flush_every, ksplit, xy_split, two_pass, lambda_only, oz_slices, tile_chunk;
 } ladder_tuning;
 ladder_status ladder_get_tuning(ladder_plan_t plan, ladder_tuning *t);
 ladder_status ladder_set_tuning(ladder_plan_t plan, const ladder_tuning *t);

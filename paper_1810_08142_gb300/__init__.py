@@ -40,7 +40,7 @@ class Tuning(ctypes.Structure):
     """Mirror of ladder_tuning (include/ladder.h)."""
     _fields_ = [("kc", ctypes.c_int), ("s_pieces", ctypes.c_int), ("flush_every", ctypes.c_int),
                 ("ksplit", ctypes.c_int), ("xy_split", ctypes.c_int), ("two_pass", ctypes.c_int),
-                ("lambda_only", ctypes.c_int), ("oz_slices", ctypes.c_int)]
+                ("lambda_only", ctypes.c_int), ("oz_slices", ctypes.c_int), ("tile_chunk", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

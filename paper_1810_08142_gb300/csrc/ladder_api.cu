@@ -106,6 +106,9 @@ struct ladder_plan_s {
   // pair-tile range of the plan (multi-GPU partition): tiles tile0 ..
   // tile0 + ntiles_tc - 1 of the shape's ntiles_all
   int tile0 = 0, ntiles_all = 0;
+  // two-pass and error-free forms: tiles per sequential range (0: as many as
+  // keep one range's stored V+- tiles within the cap)
+  int tile_chunk = 0;
   bool last_two_pass = false;
   std::vector<TcChunk> chunks_v;
   CUtensorMap tmA, tmB, tmTp, tmTm, tmVl;
@@ -138,6 +141,8 @@ struct ladder_plan_s {
 };
 
 namespace {
+
+static int range_tiles(const ladder_plan_s *pl);
 
 // Occupied-pair chunks: consecutive j ranges whose lambda+ and lambda- row
 // counts both stay within `rows`.
@@ -277,14 +282,13 @@ void compute_layout(ladder_plan_s *pl) {
     off = align_up(off + S * pl->vp * pl->vp * pl->Np * 2, 1024);
     L.ozRs = off;
     off = align_up(off + (size_t)pl->vp * pl->vp * sizeof(float));
+    const size_t rt = range_tiles(pl);  // tiles of one sequential range
     L.slab = off;
-    off = align_up(off + (size_t)pl->ntiles_tc * pl->chunks_v.size() * pl->ksplit * 128 * pl->racc_cols_v *
-                             sizeof(float2),
-                   1024);
+    off = align_up(off + rt * pl->chunks_v.size() * pl->ksplit * 128 * pl->racc_cols_v * sizeof(float2), 1024);
     L.Vg = off;
-    off = align_up(off + (size_t)pl->ntiles_tc * pl->nbp * 2 * S * 128 * SLOTS * 2, 1024);
+    off = align_up(off + rt * pl->nbp * 2 * S * 128 * SLOTS * 2, 1024);
     L.ozSV = off;
-    off = align_up(off + (size_t)pl->ntiles_tc * pl->nbp * 2 * 128 * sizeof(float));
+    off = align_up(off + rt * pl->nbp * 2 * 128 * sizeof(float));
     L.T2 = off;
     size_t t2 = 0;
     for (auto &c : pl->chunks_v) {
@@ -312,10 +316,11 @@ void compute_layout(ladder_plan_s *pl) {
     L.slab = off;  // double-single accumulators of the tensor-core kernels
     const size_t nch = pl->two_pass ? pl->chunks_v.size() : pl->chunks_tc.size();
     const size_t cols = pl->two_pass ? pl->racc_cols_v : pl->racc_cols;
-    off = align_up(off + (size_t)pl->ntiles_tc * nch * pl->ksplit * 128 * cols * sizeof(double), 1024);
+    const size_t rt = pl->two_pass ? range_tiles(pl) : pl->ntiles_tc;  // tiles of one range
+    off = align_up(off + rt * nch * pl->ksplit * 128 * cols * sizeof(double), 1024);
     if (pl->two_pass) {
       L.Vg = off;
-      off = align_up(off + (size_t)pl->ntiles_tc * pl->nbp * 2 * S * 128 * SLOTS * 2, 1024);
+      off = align_up(off + rt * pl->nbp * 2 * S * 128 * SLOTS * 2, 1024);
       L.T2 = off;
       size_t t2 = 0;
       for (auto &c : pl->chunks_v) {
@@ -406,6 +411,19 @@ void compute_layout(ladder_plan_s *pl) {
 // them): at least about eight work units per SM, and ranges of at most about
 // 128 block pairs, which the kernel walks range-major.  A batch member takes
 // only the range limit (the batch itself fills the SMs).
+// Tiles per sequential range of the two-pass and error-free forms: the
+// requested count (tile_chunk), else as many as keep one range's stored V+-
+// tiles within the cap (128 GiB, 200 GiB for the error-free mode); at least
+// one.  Ranges run one after the other through both passes and the unpack,
+// so a shape of any size keeps GEMM1 at one evaluation per (tile, block
+// pair) and re-reads only B and tau per range.
+static int range_tiles(const ladder_plan_s *pl) {
+  if (pl->tile_chunk > 0) return std::min(pl->tile_chunk, pl->ntiles_tc);
+  const double per_tile = (double)pl->nbp * 2 * pl->S * 128 * SLOTS * 2;
+  const double cap = pl->mode == LADDER_OZAKI ? kVStoreOzCap : kVStoreDefaultCap;
+  return std::max(1, (int)std::min<double>(pl->ntiles_tc, cap / per_tile));
+}
+
 static int auto_vsplit(const ladder_plan_s *pl, bool batch_member) {
   int vs = batch_member ? 1 : (8 * pl->sm_count + pl->ntiles_tc - 1) / pl->ntiles_tc;
   vs = std::max(vs, (pl->nbp + 127) / 128);
@@ -765,12 +783,10 @@ static ladder_status init_plan(ladder_plan_s *pl, int o, int v, int naux, int mo
     pl->two_pass = 1;
     pl->ksplit = auto_ksplit(pl);
     pl->vsplit = auto_vsplit(pl, false);
-    const double vbytes = (double)pl->ntiles_tc * pl->nbp * 2 * 6 * 128 * SLOTS * 2;
     int major = 0, minor = 0;
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, pl->device);
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, pl->device);
-    if ((int)pl->chunks_v.size() > kMaxChunks || vbytes * pl->S / 6 > kVStoreOzCap || major != 10 || minor != 3)
-      return LADDER_ENOTSUP;
+    if ((int)pl->chunks_v.size() > kMaxChunks || major != 10 || minor != 3) return LADDER_ENOTSUP;
   } else if (mode != LADDER_FP64) {
     pl->S = tc_slices(mode);
     pl->Np = (naux + 31) / 32 * 32;
@@ -783,12 +799,12 @@ static ladder_status init_plan(ladder_plan_s *pl, int o, int v, int naux, int mo
     pl->ntiles_tc = 0;
     for (int i = 0; i < nA; ++i) pl->ntiles_tc += nB8 - 2 * i;
     pl->ntiles_all = pl->ntiles_tc;
-    // two-pass form whenever the stored tiles fit the default cap: it avoids
-    // the fused kernel's per-chunk GEMM1 recompute, and its storing pass
-    // issues wider MMAs, so it measured faster even where one chunk suffices
-    // (o=10, v=120: 1.60 vs 2.44 ms)
-    const double vbytes = (double)pl->ntiles_tc * pl->nbp * 2 * pl->S * 128 * SLOTS * 2;
-    pl->two_pass = (!batch_member && vbytes <= kVStoreDefaultCap) ? 1 : 0;
+    // the two-pass form for every single-molecule plan: it avoids the fused
+    // kernel's per-chunk GEMM1 recompute, its storing pass issues wider MMAs
+    // (it measured faster even where one chunk suffices: o=10, v=120, 1.60
+    // vs 2.44 ms), and shapes whose stored tiles exceed the cap run in
+    // sequential tile ranges (range_tiles)
+    pl->two_pass = batch_member ? 0 : 1;
     pl->ksplit = batch_member ? 1 : auto_ksplit(pl);
     pl->vsplit = auto_vsplit(pl, batch_member);
     // FP32 accumulation chains (see ladder_tc.cu).  GEMM1: with separate
@@ -854,6 +870,7 @@ ladder_status ladder_get_tuning(ladder_plan_t pl, ladder_tuning *t) {
   t->two_pass = pl->two_pass;
   t->lambda_only = pl->lam_only;
   t->oz_slices = pl->mode == LADDER_OZAKI ? pl->oz_slices : 0;
+  t->tile_chunk = pl->tile_chunk;
   return LADDER_OK;
 }
 
@@ -863,9 +880,10 @@ ladder_status ladder_set_tuning(ladder_plan_t pl, const ladder_tuning *t) {
   if (pl->mode == LADDER_OZAKI) {
     // only the slice count and the block-pair split apply
     if ((t->oz_slices != 0 && t->oz_slices != 5 && t->oz_slices != 6) || t->ksplit < 0 || t->ksplit > pl->nbp ||
-        t->two_pass != 1 || t->lambda_only != 0)
+        t->two_pass != 1 || t->lambda_only != 0 || t->tile_chunk < 0)
       return LADDER_EINVAL;
     if (t->oz_slices) pl->oz_slices = pl->S = t->oz_slices;
+    pl->tile_chunk = t->tile_chunk;
     pl->ksplit = t->ksplit ? t->ksplit : auto_ksplit(pl);
     compute_layout(pl);
     return LADDER_OK;
@@ -873,8 +891,9 @@ ladder_status ladder_set_tuning(ladder_plan_t pl, const ladder_tuning *t) {
   if (t->kc < 1 || t->kc > 64 || !(t->s_pieces == 1 || t->s_pieces == 2 || t->s_pieces == 4) ||
       t->flush_every < 1 || t->flush_every > 4096 || t->ksplit < 0 || t->ksplit > pl->nbp ||
       (t->xy_split != 0 && t->xy_split != 1) || (t->two_pass != 0 && t->two_pass != 1) ||
-      (t->lambda_only != 0 && t->lambda_only != 1) || (t->lambda_only && !t->two_pass))
+      (t->lambda_only != 0 && t->lambda_only != 1) || (t->lambda_only && !t->two_pass) || t->tile_chunk < 0)
     return LADDER_EINVAL;
+  pl->tile_chunk = t->tile_chunk;
   if (t->lambda_only != pl->lam_only) {
     pl->lam_only = t->lambda_only;
     if (pl->lam_only) {
@@ -926,7 +945,7 @@ static ladder_status encode_maps(ladder_plan_s *pl, char *w) {
   if (pl->mode == LADDER_FP64) return LADDER_OK;
   if (pl->mode == LADDER_OZAKI) {
     const uint64_t S = pl->S;
-    const uint64_t planes = (uint64_t)pl->ntiles_tc * pl->nbp * 2 * S;
+    const uint64_t planes = (uint64_t)range_tiles(pl) * pl->nbp * 2 * S;
     const bool ok =
         encode4d(&pl->tmA, w + pl->lay.Bt, pl->Np, pl->vp, pl->vp, S, 32, 8, 16, (uint32_t)S,
                  CU_TENSOR_MAP_SWIZZLE_64B) &&
@@ -947,7 +966,7 @@ static ladder_status encode_maps(ladder_plan_s *pl, char *w) {
                CU_TENSOR_MAP_SWIZZLE_32B);
   if (!ok) return LADDER_ECUDA;
   if (pl->two_pass) {
-    const uint64_t planes = (uint64_t)pl->ntiles_tc * pl->nbp * 2 * S;
+    const uint64_t planes = (uint64_t)range_tiles(pl) * pl->nbp * 2 * S;
     const bool okv = encode3d(&pl->tmVl, w + pl->lay.Vg, SLOTS, 128, planes, 16, 128, (uint32_t)S,
                               CU_TENSOR_MAP_SWIZZLE_32B);
     if (!okv) return LADDER_ECUDA;
@@ -1171,29 +1190,43 @@ static ladder_status apply_tc(ladder_plan_t pl, const double *B, const double *t
   if (st != LADDER_OK) return st;
   TcLaunch L;
   std::memset(&L, 0, sizeof(L));
-  pl->last_two_pass = pl->two_pass != 0;
   if (pl->two_pass) {
-    // pass 1: GEMM1 and the V+- slices of every (tile, block pair) to the workspace
-    TcLaunch L1 = L;
-    L1.one = pass1_args(pl, status);
-    L1.timeout_ns = L1.one.timeout_ns;
-    L1.nitems = L1.one.ntiles * L1.one.ksplit;
-    // pass 2: GEMM2 in chunks of up to kTcMaxColsV occupied pairs of one sign
-    L.one = pass2_args(pl, R, status);
-    L.timeout_ns = L.one.timeout_ns;
-    L.nitems = L.one.ntiles * L.one.nchunks * L.one.ksplit;
     if (!pl->lam_only) pack_t2(pl, s);
     st = cuda_status(cudaGetLastError());
     if (st != LADDER_OK) return st;
+    // tile ranges one after the other (one range unless the stored tiles of
+    // all tiles exceed the cap): pass 1 stores GEMM1's V+- slices of every
+    // (tile, block pair) of the range, pass 2 contracts them in chunks of up
+    // to kTcMaxColsV occupied pairs of one sign, the unpack writes R
+    const int nt = pl->ntiles_tc, rt = range_tiles(pl);
+    const bool one = rt >= nt;
+    pl->last_two_pass = one;
     mark(pl, 1, s);
-    st = cuda_status(launch_ladder_vstore(L1, pl->S, L1.nitems, s));
-    mark(pl, 4, s);
-    if (st == LADDER_OK) st = cuda_status(launch_ladder_gemm2(L, pl->S, L.nitems, s));
-    mark(pl, 2, s);
-    if (st == LADDER_OK)
-      st = cuda_status(pl->lam_only ? launch_unpack_lam(L, L.one.ntiles * L.one.nchunks, s)
-                                    : launch_unpack2(L, L.one.ntiles * L.one.nplus, s));
+    for (int r0 = 0; r0 < nt && st == LADDER_OK; r0 += rt) {
+      const int cnt = std::min(rt, nt - r0);
+      TcLaunch L1 = L;
+      L1.one = pass1_args(pl, status);
+      L1.one.tile0 += r0;
+      L1.one.ntiles = cnt;
+      L1.timeout_ns = L1.one.timeout_ns;
+      L1.nitems = cnt * L1.one.ksplit;
+      TcLaunch L2 = L;
+      L2.one = pass2_args(pl, R, status);
+      L2.one.tile0 += r0;
+      L2.one.ntiles = cnt;
+      L2.timeout_ns = L2.one.timeout_ns;
+      L2.nitems = cnt * L2.one.nchunks * L2.one.ksplit;
+      st = cuda_status(launch_ladder_vstore(L1, pl->S, L1.nitems, s));
+      if (one) mark(pl, 4, s);
+      if (st == LADDER_OK) st = cuda_status(launch_ladder_gemm2(L2, pl->S, L2.nitems, s));
+      if (one) mark(pl, 2, s);
+      if (st == LADDER_OK)
+        st = cuda_status(pl->lam_only ? launch_unpack_lam(L2, cnt * L2.one.nchunks, s)
+                                      : launch_unpack2(L2, cnt * L2.one.nplus, s));
+    }
+    if (!one) mark(pl, 2, s);
   } else {
+    pl->last_two_pass = false;
     L.one = tc_args(pl, R, status);
     L.timeout_ns = L.one.timeout_ns;
     L.nitems = L.one.ntiles * L.one.nchunks * L.one.ksplit;
@@ -1211,7 +1244,6 @@ static ladder_status apply_tc(ladder_plan_t pl, const double *B, const double *t
 // the unpack of the two-pass form.
 static ladder_status apply_oz(ladder_plan_t pl, const double *B, const double *tau, double *R,
                               cudaStream_t s) {
-  pl->last_two_pass = true;
   mark(pl, 0, s);
   int *status = ws_at<int>(pl, pl->lay.status);
   float *rsB = ws_at<float>(pl, pl->lay.ozRs);
@@ -1258,26 +1290,37 @@ static ladder_status apply_oz(ladder_plan_t pl, const double *B, const double *t
   // every single wait is far shorter than a pass; 2 s plus 20x a work unit's estimate
   const double unit_flops = 2.0 * 128.0 * 64.0 * 2.0 * pl->Np * 21.0 * ((double)pl->nbp / pl->vsplit);
   a.timeout_ns = (unsigned long long)(2e9 + 20.0 * unit_flops / 4e12 * 1e9);
-  // pass 1: GEMM1 of every (tile, block pair), V+- slices and scales stored
-  a.ksplit = pl->vsplit;
-  a.nitems = a.ntiles * pl->vsplit;
-  a.racc = nullptr;
+  // tile ranges one after the other (one unless the stored tiles exceed the
+  // cap): pass 1 (GEMM1 of every (tile, block pair), V+- slices and scales
+  // stored), pass 2 (GEMM2 per (tile, chunk, block-pair range)), unpack
+  const int nt = pl->ntiles_tc, rt = range_tiles(pl);
+  const bool one = rt >= nt;
+  pl->last_two_pass = one;
   mark(pl, 1, s);
-  st = cuda_status(launch_oz_vstore(a, pl->S, s));
-  mark(pl, 4, s);
-  // pass 2: GEMM2 per (tile, chunk, block-pair range)
-  a.ksplit = pl->ksplit;
-  a.nitems = a.ntiles * a.nchunks * pl->ksplit;
-  a.racc = ws_at<float2>(pl, pl->lay.slab);
-  if (st == LADDER_OK) st = cuda_status(launch_oz_gemm2(a, pl->S, s));
-  mark(pl, 2, s);
-  if (st == LADDER_OK) {
-    TcLaunch L;
-    std::memset(&L, 0, sizeof(L));
-    L.one = pass2_args(pl, R, status);
-    L.one.ntiles = pl->ntiles_tc;
-    st = cuda_status(launch_unpack2(L, pl->ntiles_tc * pl->nplus, s));
+  for (int r0 = 0; r0 < nt && st == LADDER_OK; r0 += rt) {
+    const int cnt = std::min(rt, nt - r0);
+    a.tile0 = pl->tile0 + r0;
+    a.ntiles = cnt;
+    a.ksplit = pl->vsplit;
+    a.nitems = cnt * pl->vsplit;
+    a.racc = nullptr;
+    st = cuda_status(launch_oz_vstore(a, pl->S, s));
+    if (one) mark(pl, 4, s);
+    a.ksplit = pl->ksplit;
+    a.nitems = cnt * a.nchunks * pl->ksplit;
+    a.racc = ws_at<float2>(pl, pl->lay.slab);
+    if (st == LADDER_OK) st = cuda_status(launch_oz_gemm2(a, pl->S, s));
+    if (one) mark(pl, 2, s);
+    if (st == LADDER_OK) {
+      TcLaunch L;
+      std::memset(&L, 0, sizeof(L));
+      L.one = pass2_args(pl, R, status);
+      L.one.tile0 = pl->tile0 + r0;
+      L.one.ntiles = cnt;
+      st = cuda_status(launch_unpack2(L, cnt * pl->nplus, s));
+    }
   }
+  if (!one) mark(pl, 2, s);
   mark(pl, 3, s);
   return st;
 }
@@ -1625,6 +1668,7 @@ static double member_vbytes(const ladder_plan_s *sp) {
 // for its GEMM2 units; a fused member runs whole tiles.
 static void set_member_form(ladder_plan_s *sp, bool two_pass) {
   sp->two_pass = two_pass ? 1 : 0;
+  sp->tile_chunk = sp->ntiles_tc;  // the batch cap keeps every member's tiles in one range
   sp->ksplit = two_pass ? std::max(1, std::min(sp->nbp, sp->nbp / 160)) : 1;
   compute_layout(sp);
 }

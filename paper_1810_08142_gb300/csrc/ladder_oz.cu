@@ -624,11 +624,16 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm2_kernel(const __grid_cons
 #pragma unroll
       for (int e = 0; e < 32; ++e) acc[e] = make_float2(0.f, 0.f);
       for (int p = I.p0; ok && p < I.p1; ++p) {
+        const float *svp = A.sV + ((size_t)(I.tile * A.nbp + p) * 2 + sg) * 128 + L;
+        const float *st = A.sT + ((size_t)I.ch * A.nbp + p) * kOzMaxCols + 32 * qw;
+        // this pair's scales into L1 while its MMAs run (the loads in the
+        // drain below then hit L1 instead of waiting on L2 group by group)
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(st));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(svp));
         if (!(ok = mbar_wait(bars.cfull(0), g & 1u, wd, kSiteRFull))) break;
         ++g;
         tc_fence_after();
-        const float sv = A.sV[((size_t)(I.tile * A.nbp + p) * 2 + sg) * 128 + L];
-        const float *st = A.sT + ((size_t)I.ch * A.nbp + p) * kOzMaxCols + 32 * qw;
+        const float sv = *svp;
 #pragma unroll
         for (int h = 0; h < 8; ++h) {
           if (h < ng) {
@@ -698,15 +703,23 @@ __global__ void oz_rowscale_kernel(int N, int v, int vp, const double *__restric
   rs[idx] = r;
 }
 
-// x = scale (x_0 + x_1 2^-8 + ...) with x_s = nearest integer of what is left:
-// slice s stored as the BF16 number x_s 2^(-8 s) (exact).
+// y (|y| <= 256, the element over its row's scale) = x_0 + x_1 2^-8 + ... with
+// x_s = nearest integer of what is left: slice s stored as the BF16 number
+// x_s 2^(-8 s) (exact).  y is carried as a double-single (hi, lo), about 48
+// bits, and every step runs on the FP32 pipe: x = rint(hi) and hi - x are
+// exact, TwoSum renormalises the remainder, and the scaling by 256 is exact.
 template <int S>
 __device__ __forceinline__ void fixed_slices(double y, __nv_bfloat16 (&out)[S]) {
+  float hi = __double2float_rn(y);
+  float lo = __double2float_rn(y - (double)hi);
 #pragma unroll
   for (int s = 0; s < S; ++s) {
-    const double x = rint(y);
-    out[s] = __float2bfloat16_rn((float)ldexp(x, -8 * s));
-    y = (y - x) * 256.0;
+    const float x = rint_small(hi);
+    float r, er;
+    two_sum(__fsub_rn(hi, x), lo, r, er);
+    hi = r * 256.f;
+    lo = er * 256.f;
+    out[s] = __float2bfloat16_rn(x * pow2f(-8 * s));
   }
 }
 

@@ -95,7 +95,7 @@ def test_ozaki_mode_and_nonfinite_status_are_exposed(lib):
     assert lad.MODES["ozaki"] == 4
     assert lad.STATUS[7] == "LADDER_ENONFINITE"
     assert b"NaN" in lib.ladder_status_string(7)
-    assert [f for f, _ in lad.Tuning._fields_][-1] == "oz_slices"
+    assert [f for f, _ in lad.Tuning._fields_][-2:] == ["oz_slices", "tile_chunk"]
     # mode 5 is out of range
     out = ctypes.c_void_p()
     assert lib.ladder_plan(4, 24, 96, 5, ctypes.byref(out)) == 1

@@ -80,3 +80,24 @@ def test_tile_range_arguments(lad):
     with pytest.raises(lad.LadderError):
         lad.ladder_set_tile_range(L.plan, 0, 1)         # after ladder_set_workspace
     L.close()
+
+
+@pytest.mark.parametrize("mode,extra", [("bf16x6", {"two_pass": 1}), ("bf16x6", {"two_pass": 1, "lambda_only": 1}),
+                                        ("ozaki", {})])
+def test_sequential_tile_ranges_match_one_range(lad, mode, extra):
+    """tile_chunk: both passes and the unpack run over ranges of tiles one
+    after the other (as a shape too large for one range does); R is bitwise
+    the one-range result with the same block-pair split."""
+    import torch
+    o, v, n, seed = 7, 41, 70, 14
+    x = synthetic.make_inputs(o, v, n, seed)
+    B, tau = to_dev(x.B), to_dev(oracle.tau(x.t1, x.t2))
+    outs = []
+    for chunk in (0, 5, 1):
+        L = lad.Ladder(o, v, n, mode=mode, tuning=dict(extra, ksplit=2, tile_chunk=chunk))
+        assert lad.ladder_get_tuning(L.plan).tile_chunk == chunk
+        outs.append(L.apply(B, tau).cpu().numpy())
+        torch.cuda.synchronize()
+        L.check_device()
+        L.close()
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
