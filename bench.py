@@ -182,8 +182,7 @@ def tuned_for(w, mode):
     if mode == "fp64":
         return None
     from paper_1810_08142_gb300 import tune
-    e = tune._load().get(tune._key(w.o, w.v, w.naux))
-    return e["tuning"] if e and e.get("mode") == mode else None
+    return tune.lookup_mode(w.o, w.v, w.naux, mode)
 
 
 def cpu_cores() -> int:
@@ -667,8 +666,10 @@ def main():
         e_vir = torch.from_numpy(x.e_vir).to(dev)
         ft = 12.0 * w.o ** 3 * w.v ** 3 * (w.v + w.o)
         tr = {"flops": ft, "note": "flops = 12 o^3 v^3 (v + o), the W contractions"}
-        for prec in ("fp32", "fp64"):
+        for prec in ("bf16x6", "fp32", "fp64"):
             if prec == "fp64" and ft > 5e12:
+                continue
+            if prec == "bf16x6" and w.v > 256:
                 continue
             n_ws = lad.ladder_triples_workspace_size(w.o, w.v, w.naux, lad.TRIPLES_PRECISION[prec])
             ws = torch.empty(n_ws, dtype=torch.uint8, device=dev)
@@ -686,10 +687,20 @@ def main():
                 tr[prec]["roofline"] = {"bound": "alu", "achieved": ft / (tms * 1e-3) / 1e12,
                                         "peak": FP32_ALU_TFLOPS, "unit": "TFLOP/s",
                                         "frac": ft / (tms * 1e-3) / 1e12 / FP32_ALU_TFLOPS}
+            if prec == "bf16x6":
+                # six slice products per multiply-add on the bf16 tensor pipe;
+                # the whole call's time (integrals, slicing and the energy
+                # kernel included) bounds the W kernels' share from below
+                ach = 6.0 * ft / (tms * 1e-3) / 1e12
+                tr[prec]["roofline"] = {"bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops_sustained"],
+                                        "unit": "TFLOP/s", "frac": ach / pk["bf16_tflops_sustained"],
+                                        "note": "6 x W flops / whole-call time; peak = bf16 sustained (%s)" % pk_kind}
             del ws
             torch.cuda.empty_cache()
         if "fp64" in tr:
-            tr["fp32_rel_diff"] = abs(tr["fp32"]["E_T"] - tr["fp64"]["E_T"]) / abs(tr["fp64"]["E_T"])
+            for prec in ("fp32", "bf16x6"):
+                if prec in tr:
+                    tr[prec + "_rel_diff"] = abs(tr[prec]["E_T"] - tr["fp64"]["E_T"]) / abs(tr["fp64"]["E_T"])
         extra["triples"] = tr
     if args.backward and args.mode in ("bf16x3", "bf16x6"):
         # the adjoint of E_L in the same mode and tuning: dE/dtau (the

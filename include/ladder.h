@@ -219,14 +219,19 @@ ladder_status ladder_apply_dressed(ladder_plan_t plan, const double *B, const do
  *   e_occ [o], e_vir [v]                                orbital energies
  * E_dev: one double (device memory).  precision LADDER_TRIPLES_FP64 forms W
  * in FP64; LADDER_TRIPLES_FP32 forms the integrals and W in FP32 (the energy
- * sums stay FP64).  The contractions run on the CUDA cores; the work is
- * 12 o^3 v^3 (v + o) flops.  The caller supplies a workspace of at least
+ * sums stay FP64), both on the CUDA cores; LADDER_TRIPLES_BF16X6 forms the
+ * integrals in FP32 and runs the W contractions on the tensor cores (tcgen05)
+ * as split-BF16 GEMMs: three BF16 slices of each FP32 operand, the six slice
+ * products p + q < 3, FP32 accumulation with the hi*hi product in its own
+ * accumulator (v <= 256, else LADDER_ENOTSUP; if one of its bounded device
+ * waits runs out, E_dev is NaN).  The work is 12 o^3 v^3 (v + o) flops.  The caller supplies a workspace of at least
  * ladder_triples_workspace_size bytes (256-byte aligned): the integrals
  * (o v^3 + o^3 v + o^2 v^2 elements), W for one (i, j) (o v^3) and the
  * reduction partials.  Asynchronous on `stream`; the result is reduced in a
  * fixed order (bitwise reproducible). */
 #define LADDER_TRIPLES_FP64 0
 #define LADDER_TRIPLES_FP32 1
+#define LADDER_TRIPLES_BF16X6 2
 ladder_status ladder_triples_workspace_size(int o, int v, int naux, int precision, size_t *bytes);
 ladder_status ladder_triples(int o, int v, int naux, int precision, const double *B, const double *Bov,
                              const double *Boo, const double *t1, const double *t2, const double *e_occ,

@@ -186,7 +186,7 @@ def ladder_apply_dressed(plan, B, B_ov, t1, tau, R, stream=None) -> None:
                                                _stream(stream)))
 
 
-TRIPLES_PRECISION = {"fp64": 0, "fp32": 1}
+TRIPLES_PRECISION = {"fp64": 0, "fp32": 1, "bf16x6": 2}
 
 
 def ladder_triples_workspace_size(o: int, v: int, naux: int, precision: int) -> int:
@@ -204,8 +204,9 @@ def ladder_triples(o, v, naux, precision, B, B_ov, B_oo, t1, t2, e_occ, e_vir, E
 
 def triples(B, B_ov, B_oo, t1, t2, e_occ, e_vir, precision="fp64", workspace=None):
     """The perturbative triples energy E(T) of Sec. II.A on the device (FP64
-    device tensors in, one FP64 device scalar out); precision "fp64" or
-    "fp32" (integrals and W in FP32, energy sums in FP64)."""
+    device tensors in, one FP64 device scalar out); precision "fp64", "fp32"
+    (integrals and W in FP32, energy sums in FP64) or "bf16x6" (FP32
+    integrals, W contractions on the tensor cores in split BF16)."""
     import torch
     naux, v, _ = B.shape
     o = t1.shape[0]
@@ -437,12 +438,11 @@ class LadderBatch:
         import torch
         self.shapes = [(int(o), int(v), int(n)) for o, v, n in shapes]
         if mode == "tuned":
-            from .tune import lookup
             mode = "bf16x6"
             tunings = []
+            from .tune import lookup_mode
             for o, v, n in self.shapes:
-                mm, tun = lookup(o, v, n)
-                tunings.append(tun if mm == mode else None)
+                tunings.append(lookup_mode(o, v, n, mode))
         m = MODES[mode] if isinstance(mode, str) else int(mode)
         self.device = torch.device(device if device is not None else "cuda")
         self.tunings = []

@@ -79,7 +79,30 @@ template <typename T>
 cudaError_t launch_triples_t2(int o, int v, const double *t2, T *t2c, T *t2T, cudaStream_t s);
 template <typename T>
 cudaError_t launch_triples_negate(T *x, long long n, cudaStream_t s);
-cudaError_t launch_triples_final(const double *part, long long n, double *E, cudaStream_t s);
+cudaError_t launch_triples_final(const double *part, long long n, double *E, cudaStream_t s,
+                                 const int *status = nullptr);
+
+// ---- perturbative triples on the tensor cores (triples_tc.cu): the W
+// contractions as batched split-BF16 GEMMs (three slices of the FP32
+// operands, six slice products), two K segments, kEpiAcc3-style epilogue.
+// Operand slices [S][g][rows][K] (rows and K zero-padded): A1 rows m over
+// K = d (K1p), B1 rows n over d, A2 rows m over K = l (K2p), B2 rows n over
+// l; the outer index g of each is fix + mul * batch.
+struct TwArgs {
+  CUtensorMap tmA1, tmB1, tmA2, tmB2;
+  float *W;
+  int *status;
+  int M, N, Nt, K1p, K2p, batch;
+  int a1_fix, a1_mul, b1_fix, b1_mul, a2_fix, a2_mul, b2_fix, b2_mul;
+  int pv, acc;
+  long long s1, s2, s3, so_batch;
+  unsigned long long timeout_ns;
+};
+uint32_t tw_smem_bytes(int Nt);
+cudaError_t tw_init_attributes();
+cudaError_t launch_tw_gemm(const TwArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_tw_slice(const float *src, long long sg, long long sr, long long sk, int G, int rows,
+                            int rows_pad, int K, int K_pad, __nv_bfloat16 *dst, cudaStream_t s);
 
 // ---- FP64 fused ladder (DMMA)
 struct Fp64Args {

@@ -519,14 +519,20 @@ ladder_status dress_correct(const ladder_plan_s *pl, const double *Bov, const do
 
 // ---- perturbative triples (Sec. II.A): workspace and launch sequence
 struct TriplesLayout {
+  size_t status = 0;  // word of the tensor-core kernel's bounded waits
   size_t ovvv = 0, ovvvT = 0, Q = 0, oovv = 0, t2c = 0, t2T = 0, W = 0, part = 0, total = 0;
+  // tensor-core W contractions: BF16 slices of the GEMM operands
+  size_t tA1 = 0, tA1T = 0, tB1 = 0, tA2 = 0, tA2T = 0, tB2 = 0;
+  int Nt = 0, K1p = 0, K2p = 0;
 };
 
-TriplesLayout triples_layout(int o, int v, bool fp32) {
+constexpr int kTwSlices = 3;
+
+TriplesLayout triples_layout(int o, int v, bool fp32, bool tc = false) {
   const size_t t = fp32 ? sizeof(float) : sizeof(double);
   const size_t ov = (size_t)o * v, v3 = (size_t)v * v * v;
   TriplesLayout L;
-  size_t off = 0;
+  size_t off = kAlign;  // the status word
   L.ovvv = off;
   off = align_up(off + o * v3 * t);
   L.ovvvT = off;
@@ -543,6 +549,24 @@ TriplesLayout triples_layout(int o, int v, bool fp32) {
   off = align_up(off + o * v3 * t);
   L.part = off;
   off = align_up(off + (size_t)o * o * o * triples_energy_blocks(v) * sizeof(double));
+  if (tc) {
+    // operand slices of the tensor-core W GEMMs, [S][g][rows][K] bf16
+    L.Nt = (v + 15) / 16 * 16;
+    L.K1p = (v + 31) / 32 * 32;
+    L.K2p = (o + 15) / 16 * 16;
+    const size_t S = kTwSlices, vv = (size_t)v * v;
+    auto region = [&](size_t &at, size_t elems) {
+      at = align_up(off, 1024);
+      off = at + S * elems * 2;
+    };
+    region(L.tA1, (size_t)o * vv * L.K1p);
+    region(L.tA1T, (size_t)o * vv * L.K1p);
+    region(L.tB1, (size_t)o * o * L.Nt * L.K1p);
+    region(L.tA2, (size_t)o * vv * L.K2p);
+    region(L.tA2T, (size_t)o * vv * L.K2p);
+    region(L.tB2, (size_t)o * o * L.Nt * L.K2p);
+    off = align_up(off);
+  }
   L.total = off;
   return L;
 }
@@ -554,7 +578,7 @@ TriplesLayout triples_layout(int o, int v, bool fp32) {
 template <typename T>
 cudaError_t triples_run(int o, int v, int n, const double *B, const double *Bov, const double *Boo,
                         const double *t1, const double *t2, const double *e_occ, const double *e_vir,
-                        double *E, char *ws, const TriplesLayout &L, cudaStream_t s) {
+                        double *E, char *ws, const TriplesLayout &L, cudaStream_t s, bool tc = false) {
   T *ovvv = reinterpret_cast<T *>(ws + L.ovvv);
   T *ovvvT = reinterpret_cast<T *>(ws + L.ovvvT);
   T *Q = reinterpret_cast<T *>(ws + L.Q);
@@ -647,6 +671,60 @@ cudaError_t triples_run(int o, int v, int n, const double *B, const double *Bov,
   // adds both of its K segments unscaled
   if (e == cudaSuccess) e = launch_triples_negate<T>(Q, (long long)o * o * ov, s);
   const T *t2x = t2c ? t2c : reinterpret_cast<const T *>(t2);
+  // tensor-core W GEMMs: BF16 slices of the FP32 operands in their GEMM
+  // layouts, and one tensor map per operand (see triples_tc.cu)
+  TwArgs tw;
+  std::memset(&tw, 0, sizeof(tw));
+  int tw_grid = 0;
+  int *tstatus = reinterpret_cast<int *>(ws + L.status);
+  if (tc && e == cudaSuccess) e = cudaMemsetAsync(tstatus, 0, sizeof(int), s);
+  if (tc && e == cudaSuccess) {
+    const float *f_ovvv = reinterpret_cast<const float *>(ovvv), *f_ovvvT = reinterpret_cast<const float *>(ovvvT);
+    const float *f_t2 = reinterpret_cast<const float *>(t2x), *f_t2T = reinterpret_cast<const float *>(t2T);
+    const float *f_Q = reinterpret_cast<const float *>(Q);
+    auto bf = [&](size_t off) { return reinterpret_cast<__nv_bfloat16 *>(ws + off); };
+    const int M = (int)vv;
+    // A1[x][m][d] = ovvv[x][m][d] (rows (b, a)) or ovvvT[x][m][d] (rows (a, b))
+    e = launch_tw_slice(f_ovvv, v3, v, 1, o, M, M, v, L.K1p, bf(L.tA1), s);
+    if (e == cudaSuccess) e = launch_tw_slice(f_ovvvT, v3, v, 1, o, M, M, v, L.K1p, bf(L.tA1T), s);
+    // B1[(z, y)][gamma][d] = t2[z][y][gamma][d]
+    if (e == cudaSuccess) e = launch_tw_slice(f_t2, vv, v, 1, o * o, v, L.Nt, v, L.K1p, bf(L.tB1), s);
+    // A2[x][m][l] = t2[x][l][m] (rows (a, b)) or t2T[x][l][m] (rows (b, a))
+    if (e == cudaSuccess) e = launch_tw_slice(f_t2, (long long)o * vv, 1, vv, o, M, M, o, L.K2p, bf(L.tA2), s);
+    if (e == cudaSuccess) e = launch_tw_slice(f_t2T, (long long)o * vv, 1, vv, o, M, M, o, L.K2p, bf(L.tA2T), s);
+    // B2[(z, y)][gamma][l] = -(gamma z | y l) = Q[z][y][gamma][l]
+    if (e == cudaSuccess) e = launch_tw_slice(f_Q, ov, o, 1, o * o, v, L.Nt, o, L.K2p, bf(L.tB2), s);
+    tw.W = reinterpret_cast<float *>(W);
+    tw.status = tstatus;
+    tw.M = M;
+    tw.N = v;
+    tw.Nt = L.Nt;
+    tw.K1p = L.K1p;
+    tw.K2p = L.K2p;
+    tw.batch = o;
+    tw.pv = v;
+    tw.so_batch = v3;
+    tw.timeout_ns = 2000000000ull;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    tw_grid = std::min(o * ((M + 127) / 128), sms);
+    if (e == cudaSuccess) e = tw_init_attributes();
+  }
+  CUtensorMap mA1, mA1T, mA2, mA2T;
+  if (tc && e == cudaSuccess) {
+    const uint64_t S = kTwSlices, M = (uint64_t)vv, uo = (uint64_t)o;
+    const bool ok =
+        encode4d(&mA1, ws + L.tA1, L.K1p, M, uo, S, 32, 128, 1, (uint32_t)S, CU_TENSOR_MAP_SWIZZLE_64B) &&
+        encode4d(&mA1T, ws + L.tA1T, L.K1p, M, uo, S, 32, 128, 1, (uint32_t)S, CU_TENSOR_MAP_SWIZZLE_64B) &&
+        encode4d(&tw.tmB1, ws + L.tB1, L.K1p, L.Nt, uo * uo, S, 32, (uint32_t)L.Nt, 1, (uint32_t)S,
+                 CU_TENSOR_MAP_SWIZZLE_64B) &&
+        encode4d(&mA2, ws + L.tA2, L.K2p, M, uo, S, 16, 128, 1, (uint32_t)S, CU_TENSOR_MAP_SWIZZLE_32B) &&
+        encode4d(&mA2T, ws + L.tA2T, L.K2p, M, uo, S, 16, 128, 1, (uint32_t)S, CU_TENSOR_MAP_SWIZZLE_32B) &&
+        encode4d(&tw.tmB2, ws + L.tB2, L.K2p, L.Nt, uo * uo, S, 16, (uint32_t)L.Nt, 1, (uint32_t)S,
+                 CU_TENSOR_MAP_SWIZZLE_32B);
+    if (!ok) e = cudaErrorInvalidValue;
+  }
   // the six orderings of P: (x, y, z) = (I[p0], I[p1], I[p2]) with I = (i, j, k),
   // and (alpha, beta, gamma) = (A[p0], A[p1], A[p2]) with A = (a, b, c)
   static const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {2, 0, 1}, {2, 1, 0}, {1, 2, 0}, {1, 0, 2}};
@@ -703,12 +781,33 @@ cudaError_t triples_run(int o, int v, int n, const double *B, const double *Bov,
         g.s2 = wstride[rowsBA ? p[0] : p[1]];
         g.s3 = wstride[p[2]];
         g.acc = q > 0;
-        e = launch_gemm<T, T, T>(g, o, s);
+        if (tc) {
+          // the same contraction on the tensor cores: operand g-indices
+          // fixed or the batch (k) itself, the same output strides
+          tw.tmA1 = rowsBA ? mA1 : mA1T;
+          tw.a1_fix = xk ? 0 : (int)x;
+          tw.a1_mul = xk ? 1 : 0;
+          tw.b1_fix = (zk ? 0 : (int)z * o) + (yk ? 0 : (int)y);
+          tw.b1_mul = zk ? o : (yk ? 1 : 0);
+          tw.tmA2 = rowsBA ? mA2T : mA2;
+          tw.a2_fix = tw.a1_fix;
+          tw.a2_mul = tw.a1_mul;
+          tw.b2_fix = tw.b1_fix;
+          tw.b2_mul = tw.b1_mul;
+          tw.s1 = g.s1;
+          tw.s2 = g.s2;
+          tw.s3 = g.s3;
+          tw.acc = g.acc;
+          e = launch_tw_gemm(tw, tw_grid, s);
+        } else {
+          e = launch_gemm<T, T, T>(g, o, s);
+        }
       }
       if (e == cudaSuccess) e = launch_triples_energy<T>(ta, W, i, j, part, s);
     }
+  // E = NaN if a bounded wait of the tensor-core kernel ran out
   if (e == cudaSuccess)
-    e = launch_triples_final(part, (long long)o * o * o * triples_energy_blocks(v), E, s);
+    e = launch_triples_final(part, (long long)o * o * o * triples_energy_blocks(v), E, s, tc ? tstatus : nullptr);
   return e;
 }
 
@@ -1384,9 +1483,10 @@ ladder_status ladder_apply_dressed(ladder_plan_t pl, const double *B, const doub
 
 ladder_status ladder_triples_workspace_size(int o, int v, int naux, int precision, size_t *bytes) {
   if (!bytes || o < 1 || o > 256 || v < 1 || v > 4096 || naux < 1 || naux > 65536 ||
-      (precision != LADDER_TRIPLES_FP64 && precision != LADDER_TRIPLES_FP32))
+      (precision != LADDER_TRIPLES_FP64 && precision != LADDER_TRIPLES_FP32 && precision != LADDER_TRIPLES_BF16X6))
     return LADDER_EINVAL;
-  *bytes = triples_layout(o, v, precision == LADDER_TRIPLES_FP32).total;
+  if (precision == LADDER_TRIPLES_BF16X6 && v > 256) return LADDER_ENOTSUP;
+  *bytes = triples_layout(o, v, precision != LADDER_TRIPLES_FP64, precision == LADDER_TRIPLES_BF16X6).total;
   return LADDER_OK;
 }
 
@@ -1402,12 +1502,14 @@ ladder_status ladder_triples(int o, int v, int naux, int precision, const double
   const void *ptrs[] = {B, Bov, Boo, t1, t2, e_occ, e_vir, E_dev, workspace};
   for (const void *q : ptrs)
     if (!dev_ptr_ok(q)) return LADDER_EINVAL;
-  const TriplesLayout L = triples_layout(o, v, precision == LADDER_TRIPLES_FP32);
+  const bool tc = precision == LADDER_TRIPLES_BF16X6;
+  const TriplesLayout L = triples_layout(o, v, precision != LADDER_TRIPLES_FP64, tc);
   char *ws = static_cast<char *>(workspace);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  return cuda_status(precision == LADDER_TRIPLES_FP32
-                         ? triples_run<float>(o, v, naux, B, Bov, Boo, t1, t2, e_occ, e_vir, E_dev, ws, L, s)
-                         : triples_run<double>(o, v, naux, B, Bov, Boo, t1, t2, e_occ, e_vir, E_dev, ws, L, s));
+  return cuda_status(precision == LADDER_TRIPLES_FP64
+                         ? triples_run<double>(o, v, naux, B, Bov, Boo, t1, t2, e_occ, e_vir, E_dev, ws, L, s)
+                         : triples_run<float>(o, v, naux, B, Bov, Boo, t1, t2, e_occ, e_vir, E_dev, ws, L, s,
+                                              tc));
 }
 
 ladder_status ladder_energy(ladder_plan_t pl, const double *R, const double *t2, double *E_dev,

@@ -88,8 +88,10 @@ __global__ void triples_negate_kernel(T *__restrict__ x, long long n) {
 }
 
 // One block: thread t sums partials t, t + 1024, ... in order, then a tree.
+// A nonzero *status (a bounded wait of the tensor-core W kernel ran out)
+// makes the result NaN.
 __global__ void __launch_bounds__(1024) triples_final_kernel(const double *__restrict__ part, long long n,
-                                                             double *__restrict__ E) {
+                                                             double *__restrict__ E, const int *status) {
   __shared__ double red[1024];
   double s = 0.0;
   for (long long q = threadIdx.x; q < n; q += 1024) s += part[q];
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(1024) triples_final_kernel(const double *__res
     if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *E = red[0];
+  if (threadIdx.x == 0) *E = (status && *status) ? __longlong_as_double(0x7ff8000000000000LL) : red[0];
 }
 
 }  // namespace
@@ -140,8 +142,8 @@ cudaError_t launch_triples_negate(T *x, long long n, cudaStream_t s) {
 template cudaError_t launch_triples_negate<double>(double *, long long, cudaStream_t);
 template cudaError_t launch_triples_negate<float>(float *, long long, cudaStream_t);
 
-cudaError_t launch_triples_final(const double *part, long long n, double *E, cudaStream_t s) {
-  triples_final_kernel<<<1, 1024, 0, s>>>(part, n, E);
+cudaError_t launch_triples_final(const double *part, long long n, double *E, cudaStream_t s, const int *status) {
+  triples_final_kernel<<<1, 1024, 0, s>>>(part, n, E, status);
   return cudaGetLastError();
 }
 

@@ -16,7 +16,10 @@ N_aux, not on v, so accuracy is measured on a proxy with the same o and N_aux
 and v capped at 64 (where the FP64 path is quick); speed on the full shape.
 
 Results go to a JSON cache ($LADDER_TUNE_CACHE, else tune_cache.json next to
-this file) keyed by "o,v,naux"; Ladder(..., mode="tuned") reads it.
+this file) keyed by "o,v,naux": the selected mode and launch parameters
+(Ladder(..., mode="tuned") reads them) and, under "by_mode", the fastest
+parameters of each mode that meet the R bound (what a caller who fixes the
+mode, e.g. a BF16X6 batch, wants).
 
     python -m paper_1810_08142_gb300.tune 34 400 1600 [--tol 1e-6]
 """
@@ -43,6 +46,16 @@ def _load() -> dict:
 
 def _key(o, v, naux) -> str:
     return "%d,%d,%d" % (o, v, naux)
+
+
+def lookup_mode(o: int, v: int, naux: int, mode: str):
+    """The cached parameters of `mode` for this exact shape, or None."""
+    e = _load().get(_key(o, v, naux))
+    if not e:
+        return None
+    if mode in e.get("by_mode", {}):
+        return e["by_mode"][mode]
+    return e["tuning"] if e.get("mode") == mode else None
 
 
 def lookup(o: int, v: int, naux: int):
@@ -159,6 +172,12 @@ def tune(o: int, v: int, naux: int, tol: float = 1e-6, etol_rel: float = 1e-13, 
     # the proxy's inputs are not the caller's: keep a factor of two in hand
     best = select(results, tol, etol_rel)
     entry = dict(best, tol=tol, etol_rel=etol_rel, candidates=len(results))
+    by_mode = {}
+    for m in sorted({r["mode"] for r in results}):
+        ok = [r for r in results if r["mode"] == m and r["err"] <= 0.5 * tol]
+        if ok:
+            by_mode[m] = min(ok, key=lambda r: r["ms"])["tuning"]
+    entry["by_mode"] = by_mode
     if write:
         c = _load()
         c[_key(o, v, naux)] = entry

@@ -1,7 +1,11 @@
 """The perturbative triples energy E(T) (Sec. II.A) through ladder_triples,
 against the CPU oracle.  FP64 forms W in FP64 (bar 1e-12 relative); FP32
 forms the integrals and W in FP32 with FP64 energy sums (bar 1e-5 relative:
-W carries FP32 rounding of sums over v + o terms)."""
+W carries FP32 rounding of sums over v + o terms); BF16X6 runs the W
+contractions on the tensor cores from three BF16 slices of each FP32 operand
+(bar 1e-5 relative: the slices hold the FP32 operands exactly, the six
+products drop terms 2^-24 below, and the tensor core's FP32 accumulation
+adds a bias of about 2e-8 per accumulation step)."""
 import numpy as np
 import pytest
 
@@ -11,7 +15,7 @@ from gpu_util import to_dev
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "bf16x6": 1e-5}
 SHAPES = [(2, 4, 3, 11), (3, 5, 4, 7), (4, 24, 96, 0), (5, 17, 33, 12), (8, 60, 240, 21)]
 
 
@@ -32,8 +36,8 @@ def run(lad, x, precision):
     return float(E.item())
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("o,v,n,seed", SHAPES)
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16x6"])
+@pytest.mark.parametrize("o,v,n,seed", SHAPES + [(3, 140, 60, 23), (17, 33, 40, 24)])
 def test_triples_matches_oracle(lad, precision, o, v, n, seed):
     x = synthetic.make_inputs(o, v, n, seed)
     E_g = run(lad, x, precision)
@@ -43,14 +47,14 @@ def test_triples_matches_oracle(lad, precision, o, v, n, seed):
     assert err < TOL[precision]
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16x6"])
 def test_triples_vanish_with_one_occupied_orbital(lad, precision):
     """o = 1: W_iii^abc is symmetric in (a, b, c) (P sums all six orderings),
     so sum_abc (4 W_abc + W_bca + W_cab)(V_abc - V_cba) = 0 up to rounding."""
     x = synthetic.make_inputs(1, 9, 12, 11)
     x2 = synthetic.make_inputs(2, 9, 12, 11)
     scale = abs(oracle.triples(x2.B, x2.B_ov, x2.B_oo, x2.t1, x2.t2, x2.e_occ, x2.e_vir))
-    assert abs(run(lad, x, precision)) <= (1e-9 if precision == "fp64" else TOL["fp32"]) * scale
+    assert abs(run(lad, x, precision)) <= (1e-9 if precision == "fp64" else TOL[precision]) * scale
     assert abs(oracle.triples(x.B, x.B_ov, x.B_oo, x.t1, x.t2, x.e_occ, x.e_vir)) <= 1e-12 * scale
 
 
@@ -69,7 +73,7 @@ def test_triples_rejects_a_small_workspace(lad):
                            to_dev(x.t2), to_dev(x.e_occ), to_dev(x.e_vir), E, ws)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16x6"])
 def test_triples_dimer_against_stored_oracle(lad, precision):
     """The water-dimer-sized workload (o=10, v=120, N_aux=480) against E(T)
     stored by tests/golden/make_golden.py --triples."""
@@ -87,3 +91,10 @@ def test_triples_dimer_against_stored_oracle(lad, precision):
     err = abs(E_g - g["E_T"]) / abs(g["E_T"])
     print("triples dimer %s: E(T) %.12e  rel err %.3e" % (precision, g["E_T"], err))
     assert err < TOL[precision]
+
+
+def test_triples_tensor_core_size_limit(lad):
+    """The tensor-core W kernel holds one column tile of at most 256 virtual
+    orbitals: larger v is refused before any launch."""
+    with pytest.raises(lad.LadderError):
+        lad.ladder_triples_workspace_size(4, 257, 40, lad.TRIPLES_PRECISION["bf16x6"])

@@ -29,3 +29,18 @@ def test_select_needs_both_bounds():
     # nothing meets an energy bound below every candidate: the most accurate in E
     assert tune.select(res, 1e-6, 1e-17)["ms"] == 1110.0
     assert ("ozaki", {"oz_slices": 5}) in tune.candidates((0, 1))
+
+
+def test_lookup_mode_reads_per_mode_entries(tmp_path, monkeypatch):
+    from paper_1810_08142_gb300 import tune
+    path = tmp_path / "cache.json"
+    monkeypatch.setenv("LADDER_TUNE_CACHE", str(path))
+    path.write_text(json.dumps({
+        "34,400,1600": {"mode": "ozaki", "tuning": {"oz_slices": 5},
+                        "by_mode": {"bf16x6": {"kc": 4, "flush_every": 128}, "ozaki": {"oz_slices": 5}}},
+        "10,120,480": {"mode": "bf16x6", "tuning": {"kc": 8}}}))
+    assert tune.lookup(34, 400, 1600) == ("ozaki", {"oz_slices": 5})
+    assert tune.lookup_mode(34, 400, 1600, "bf16x6") == {"kc": 4, "flush_every": 128}
+    assert tune.lookup_mode(10, 120, 480, "bf16x6") == {"kc": 8}      # older entries without by_mode
+    assert tune.lookup_mode(10, 120, 480, "ozaki") is None
+    assert tune.lookup_mode(4, 24, 96, "bf16x6") is None
