@@ -217,6 +217,7 @@ ladder_status ladder_apply_dressed(ladder_plan_t plan, const double *B, const do
  *   B [naux][v][v], Bov [naux][o][v], Boo [naux][o][o]   factors m^P
  *   t1 [o][v], t2 [o][o][v][v]                          amplitudes
  *   e_occ [o], e_vir [v]                                orbital energies
+ * 1 <= o <= 256, 1 <= v <= 1024, 1 <= naux <= 65536.
  * E_dev: one double (device memory).  precision LADDER_TRIPLES_FP64 forms W
  * in FP64; LADDER_TRIPLES_FP32 forms the integrals and W in FP32 (the energy
  * sums stay FP64), both on the CUDA cores; LADDER_TRIPLES_BF16X6 forms the

@@ -66,6 +66,7 @@ template <typename T>
 cudaError_t launch_reduce(T *X, long long n, int parts, cudaStream_t s);
 
 // ---- perturbative triples (triples.cu); W from launch_gemm with kEpiAcc3
+constexpr int kTriplesMaxV = 1024;  // ladder_triples: v at most this (shared-memory vectors of the energy kernel)
 struct TriplesArgs {
   const void *oovv;  // [j][k][b][c] = v_jk^bc = (bj|ck), element type T of the energy kernel
   const double *t1, *e_occ, *e_vir;

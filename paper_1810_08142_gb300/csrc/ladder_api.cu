@@ -1482,7 +1482,7 @@ ladder_status ladder_apply_dressed(ladder_plan_t pl, const double *B, const doub
 }
 
 ladder_status ladder_triples_workspace_size(int o, int v, int naux, int precision, size_t *bytes) {
-  if (!bytes || o < 1 || o > 256 || v < 1 || v > 4096 || naux < 1 || naux > 65536 ||
+  if (!bytes || o < 1 || o > 256 || v < 1 || v > kTriplesMaxV || naux < 1 || naux > 65536 ||
       (precision != LADDER_TRIPLES_FP64 && precision != LADDER_TRIPLES_FP32 && precision != LADDER_TRIPLES_BF16X6))
     return LADDER_EINVAL;
   if (precision == LADDER_TRIPLES_BF16X6 && v > 256) return LADDER_ENOTSUP;

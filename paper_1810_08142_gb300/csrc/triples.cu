@@ -14,55 +14,96 @@
 //   triples_energy_kernel   one partial sum per (i, j, k, block of abc)
 //   triples_final_kernel    the partials of all (i, j, k), one block, fixed order
 #include <algorithm>
+#include <type_traits>
 
 #include "kernels.h"
 
 namespace ladder {
 namespace {
 
-constexpr int kTE = 256;       // threads per energy block
-constexpr int kTPer = 16;      // abc elements per thread
+constexpr int kTE = 256;  // threads per energy block
+constexpr int kTC = 8;    // edge of the (a, b, c) cube of one block
 
+// One block per (8x8 (a, b) tile, k), walking the 8-wide blocks of c: for
+// each 8x8x8 cube the three permuted sub-cubes of W the terms need (W^bca,
+// W^cab, W^cba of the cube live in the cubes (b, c, a), (c, a, b) and
+// (c, b, a) of W) are first copied into shared memory with coalesced reads
+// (the last index is contiguous in both), so that no thread gathers W at a
+// stride of v or v^2.  One partial sum per block, reduced in a fixed order.
 template <typename T>
 __global__ void __launch_bounds__(kTE) triples_energy_kernel(const TriplesArgs a, const T *__restrict__ W,
                                                              int i, int j, double *__restrict__ part) {
-  __shared__ double red[kTE];
+  __shared__ T cube[3][kTC][kTC][kTC + 1];
+  __shared__ double red[kTE / 32];
+  __shared__ T sti[kTriplesMaxV], stj[kTriplesMaxV], stk[kTriplesMaxV], sev[kTriplesMaxV];
   const int k = blockIdx.y;
   const int v = a.v, o = a.o;
-  const long long v3 = (long long)v * v * v;
+  const int nc = (v + kTC - 1) / kTC;
+  const int A0 = (int)(blockIdx.x / nc) * kTC, B0 = (int)(blockIdx.x % nc) * kTC;
+  const long long vv = (long long)v * v, v3 = vv * v;
   const T *Wk = W + (long long)k * v3;
   const T *oovv = static_cast<const T *>(a.oovv);
-  const T *Ijk = oovv + ((long long)j * o + k) * v * v;  // v_jk^bc at [b][c]
-  const T *Iik = oovv + ((long long)i * o + k) * v * v;  // v_ik^ac at [a][c]
-  const T *Iij = oovv + ((long long)i * o + j) * v * v;  // v_ij^ab at [a][b]
-  const double *ti = a.t1 + (long long)i * v, *tj = a.t1 + (long long)j * v, *tk = a.t1 + (long long)k * v;
-  // terms in T (FP32 mode: the FP64 pipe is scarce on this part), sums in FP64
-  const T eijk = (T)(a.e_occ[i] + a.e_occ[j] + a.e_occ[k]);
-  double s = 0.0;
-  const long long e0 = ((long long)blockIdx.x * kTE * kTPer);
-  for (int r = 0; r < kTPer; ++r) {
-    const long long e = e0 + (long long)r * kTE + threadIdx.x;
-    if (e >= v3) break;
-    const int aa = (int)(e / ((long long)v * v)), bb = (int)((e / v) % v), cc = (int)(e % v);
-    const T wabc = Wk[e];
-    const T wbca = Wk[((long long)bb * v + cc) * v + aa];
-    const T wcab = Wk[((long long)cc * v + aa) * v + bb];
-    const T wcba = Wk[((long long)cc * v + bb) * v + aa];
-    const T vabc = wabc + Ijk[(long long)bb * v + cc] * (T)ti[aa] + Iik[(long long)aa * v + cc] * (T)tj[bb] +
-                   Iij[(long long)aa * v + bb] * (T)tk[cc];
-    const T vcba = wcba + Ijk[(long long)bb * v + aa] * (T)ti[cc] + Iik[(long long)cc * v + aa] * (T)tj[bb] +
-                   Iij[(long long)cc * v + bb] * (T)tk[aa];
-    const T D = eijk - (T)a.e_vir[aa] - (T)a.e_vir[bb] - (T)a.e_vir[cc];
-    s += (double)((T(4) * wabc + wbca + wcab) * (vabc - vcba) / (T(3) * D));
+  const T *Ijk = oovv + ((long long)j * o + k) * vv;  // v_jk^bc at [b][c]
+  const T *Iik = oovv + ((long long)i * o + k) * vv;  // v_ik^ac at [a][c]
+  const T *Iij = oovv + ((long long)i * o + j) * vv;  // v_ij^ab at [a][b]
+  // terms in T (FP32 mode: the FP64 pipe is scarce on this part, so the
+  // singles and orbital energies are converted once per block), sums in FP64
+  for (int x = threadIdx.x; x < v; x += kTE) {
+    sti[x] = (T)a.t1[(long long)i * v + x];
+    stj[x] = (T)a.t1[(long long)j * v + x];
+    stk[x] = (T)a.t1[(long long)k * v + x];
+    sev[x] = (T)a.e_vir[x];
   }
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = kTE / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+  const T eijk = (T)(a.e_occ[i] + a.e_occ[j] + a.e_occ[k]);
+  // the thread's sum: FP64 for T = double; for T = float a double-single
+  // (hi, lo) kept with TwoSum on the FP32 pipe (about 48 bits), widened once
+  double s = 0.0;
+  float sh = 0.f, sl = 0.f;
+  for (int C0 = 0; C0 < v; C0 += kTC) {
+    // cube q holds W[X0 + x][Y0 + y][Z0 + z] at [x][y][z]:
+    //   q = 0: (X, Y, Z) = (B, C, A);  q = 1: (C, A, B);  q = 2: (C, B, A)
+    for (int t = threadIdx.x; t < 3 * kTC * kTC * kTC; t += kTE) {
+      const int q = t / (kTC * kTC * kTC), r = t % (kTC * kTC * kTC);
+      const int x = r / (kTC * kTC), y = (r / kTC) % kTC, z = r % kTC;
+      const int X0 = q == 0 ? B0 : C0, Y0 = q == 0 ? C0 : (q == 1 ? A0 : B0), Z0 = q == 1 ? B0 : A0;
+      const int X = X0 + x, Y = Y0 + y, Z = Z0 + z;
+      cube[q][x][y][z] = (X < v && Y < v && Z < v) ? Wk[(long long)X * vv + (long long)Y * v + Z] : T(0);
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < kTC * kTC * kTC; r += kTE) {
+      const int al = r / (kTC * kTC), bl = (r / kTC) % kTC, cl = r % kTC;
+      const int aa = A0 + al, bb = B0 + bl, cc = C0 + cl;
+      if (aa >= v || bb >= v || cc >= v) continue;
+      const T wabc = Wk[(long long)aa * vv + (long long)bb * v + cc];
+      const T wbca = cube[0][bl][cl][al];
+      const T wcab = cube[1][cl][al][bl];
+      const T wcba = cube[2][cl][bl][al];
+      const T vabc = wabc + Ijk[(long long)bb * v + cc] * sti[aa] + Iik[(long long)aa * v + cc] * stj[bb] +
+                     Iij[(long long)aa * v + bb] * stk[cc];
+      const T vcba = wcba + Ijk[(long long)bb * v + aa] * sti[cc] + Iik[(long long)cc * v + aa] * stj[bb] +
+                     Iij[(long long)cc * v + bb] * stk[aa];
+      const T D = eijk - sev[aa] - sev[bb] - sev[cc];
+      const T term = (T(4) * wabc + wbca + wcab) * (vabc - vcba) / (T(3) * D);
+      if constexpr (std::is_same<T, float>::value) {
+        const float t = __fadd_rn(sh, term), bb = __fsub_rn(t, sh);
+        sl = __fadd_rn(sl, __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(term, bb)));
+        sh = t;
+      } else {
+        s += (double)term;
+      }
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0)
-    part[(((long long)i * o + j) * o + k) * gridDim.x + blockIdx.x] = red[0];
+  if constexpr (std::is_same<T, float>::value) s = (double)sh + (double)sl;
+  // fixed-order reduction: warp shuffles, then the warps' sums in order
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kTE / 32; ++w) t += red[w];
+    part[(((long long)i * o + j) * o + k) * gridDim.x + blockIdx.x] = t;
+  }
 }
 
 // t2 in the GEMMs' element type (t2c, skipped when null) and with the two
@@ -107,8 +148,8 @@ __global__ void __launch_bounds__(1024) triples_final_kernel(const double *__res
 }  // namespace
 
 int triples_energy_blocks(int v) {
-  const long long v3 = (long long)v * v * v;
-  return (int)((v3 + (long long)kTE * kTPer - 1) / ((long long)kTE * kTPer));
+  const int nc = (v + kTC - 1) / kTC;
+  return nc * nc;
 }
 
 template <typename T>

@@ -208,16 +208,29 @@ __global__ void __launch_bounds__(kThreads, 1) tw_gemm_kernel(const __grid_const
         tmem_ld16(tl + buf * 256u + c0, x);
         tmem_ld16(tl + buf * 256u + A.Nt + c0, y);
         tmem_ld_wait();
-        if (m < A.M) {
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int n = c0 + e;
-            if (n < A.N) {
-              float *w = O + (long long)n * A.s3;
-              const float val = x[e] + y[e];
-              *w = A.acc ? *w + val : val;
-            }
-          }
+        for (int e = 0; e < 16; ++e) x[e] += y[e];
+        if (m >= A.M) continue;
+        float *w0 = O + (long long)c0 * A.s3;
+        if (A.s3 == 1 && c0 + 16 <= A.N && (reinterpret_cast<uintptr_t>(w0) & 15u) == 0) {
+          // the 16 columns are contiguous: four 16-byte accesses, loads first
+          float4 *w4 = reinterpret_cast<float4 *>(w0);
+          float4 old[4];
+#pragma unroll
+          for (int h = 0; h < 4; ++h) old[h] = A.acc ? w4[h] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int h = 0; h < 4; ++h)
+            w4[h] = make_float4(old[h].x + x[4 * h], old[h].y + x[4 * h + 1], old[h].z + x[4 * h + 2],
+                                old[h].w + x[4 * h + 3]);
+        } else {
+          // every load of the group is issued before the first add, so the
+          // read-modify-write costs one memory latency per 16 columns
+          float old[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) old[e] = (A.acc && c0 + e < A.N) ? w0[(long long)e * A.s3] : 0.f;
+#pragma unroll
+          for (int e = 0; e < 16; ++e)
+            if (c0 + e < A.N) w0[(long long)e * A.s3] = old[e] + x[e];
         }
       }
       tc_fence_before();
