@@ -193,11 +193,32 @@ def cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
+def ragged_parity(Rs, E):
+    """Every member's E_L and four R columns against the stored oracle values
+    (tests/golden/ragged48.json), or None where that file is absent."""
+    path = os.path.join(ROOT, "tests", "golden", "ragged48.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        gold = json.load(f)["molecules"]
+    Eh = E.cpu().numpy()
+    dE, rel = [], []
+    for k, g in enumerate(gold):
+        cols = np.array(g["R_cols"])
+        got = np.stack([Rs[k][:, :, a, b].cpu().numpy() for a, b in zip(g["pairs_a"], g["pairs_b"])])
+        rel.append(float(np.linalg.norm(got - cols) / np.linalg.norm(cols)))
+        dE.append(abs(float(Eh[k]) - g["E_L"]))
+    return {"max_dE_L": max(dE), "molecules_dE_L_tol_met": sum(d <= TOL_E for d in dE),
+            "max_rel_fro_sampled_cols": max(rel), "dE_L_tol": TOL_E, "dE_L_tol_met": max(dE) <= TOL_E}
+
+
 def ragged_measure(steps, warmup, mode="bf16x6", fp64=True):
     """The 48-molecule ragged batch: one graph-replayed batched step
-    (ladder_step_batched: tau, the ladder and E_L of every molecule) in split
-    BF16 with each member's autotuned launch parameters, against the plan's
-    own rules and (fp64=True) 48 separate FP64 steps, all on inputs in HBM."""
+    (ladder_step_batched: tau, the ladder and E_L of every molecule), in
+    BF16X6 with each member's autotuned launch parameters (against the plan's
+    own rules) or in the error-free mode, and (fp64=True) 48 separate FP64
+    steps, all on inputs in HBM; parity of the last step against the stored
+    oracle values."""
     import torch
     import paper_1810_08142_gb300 as lad
     mols = synthetic.ragged_batch()
@@ -225,6 +246,7 @@ def ragged_measure(steps, warmup, mode="bf16x6", fp64=True):
     tuned = mode == "bf16x6"
     batch = lad.LadderBatch(shapes, mode="tuned" if tuned else mode)
     ms = timed(batch)
+    parity = ragged_parity(Rs, E)
     ntuned = sum(t is not None for t in batch.tunings)
     ntwo = sum(bool(t and t["two_pass"]) for t in batch.tunings)
     batch.close()
@@ -237,7 +259,8 @@ def ragged_measure(steps, warmup, mode="bf16x6", fp64=True):
         b2.close()
         del b2
         torch.cuda.empty_cache()
-    out = {"ms_per_step": ms, "tflops": F / (ms * 1e-3) / 1e12, "molecules": len(mols), "falg_total": F,
+    out = {"mode": mode, "ms_per_step": ms, "tflops": F / (ms * 1e-3) / 1e12, "molecules": len(mols),
+           "falg_total": F, "parity": parity,
            "call": "ladder_step_batched (tau, ladder, E_L per molecule, one CUDA graph)",
            "tuning": "per-member autotuned (cache)" if tuned else "plan defaults",
            "members_tuned": ntuned if tuned else 0, "members_two_pass": ntwo if tuned else None,
@@ -270,15 +293,18 @@ def ragged_measure(steps, warmup, mode="bf16x6", fp64=True):
 
 def run_ragged(args):
     """--workload ragged48: the batch as the line's headline."""
-    r = ragged_measure(args.steps, args.warmup, args.mode if args.mode != "ozaki" else "bf16x6",
-                       fp64=not args.no_fp64)
+    mode = args.mode if args.mode in ("ozaki", "bf16x6", "bf16x3") else "ozaki"
+    r = ragged_measure(args.steps, args.warmup, mode, fp64=not args.no_fp64)
     line = {"metric": METRIC, "value": r["tflops"], "unit": "TFLOP/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x6-split",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": ("bf16 fixed-point x5 slices, exact FP32 windows" if mode == "ozaki"
+                      else mode + "-split"),
             "data": "synthetic",
-            "config": {"workload": "ragged48", "molecules": r["molecules"], "falg_total": r["falg_total"],
-                       "tuning": r["tuning"], "members_tuned": r["members_tuned"],
+            "config": {"workload": "ragged48", "mode": mode, "molecules": r["molecules"],
+                       "falg_total": r["falg_total"], "tuning": r["tuning"], "members_tuned": r["members_tuned"],
                        "members_two_pass": r["members_two_pass"], "call": r["call"]},
+            "parity": r["parity"],
             "others": {"fp64_48_launches": r.get("fp64_48_launches"), "plan_defaults": r["plan_defaults"]}}
     print(json.dumps(line), flush=True)
     return 0
@@ -662,6 +688,9 @@ def main():
         # the 48-molecule ragged batch (one graph per step), timed in every
         # default run; its 48 FP64 steps (~40 s) only with --workload ragged48
         extra["ragged48"] = ragged_measure(max(1, args.steps), max(1, args.warmup), fp64=False)
+        torch.cuda.empty_cache()
+        extra["ragged48_ozaki"] = ragged_measure(max(1, args.steps), max(1, args.warmup), mode="ozaki",
+                                                 fp64=False)
         torch.cuda.empty_cache()
     if args.triples:
         # the perturbative triples energy E(T) on the same molecule (CUDA-core

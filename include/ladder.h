@@ -285,12 +285,16 @@ ladder_status ladder_apply_host(ladder_plan_t plan, const double *B_host, const 
                                 void *stream);
 
 /* Ragged batch: n molecules with their own (o_k, v_k, naux_k), one plan and one
- * workspace; mode LADDER_BF16X3 or LADDER_BF16X6 (else LADDER_ENOTSUP).
- * Molecules whose occupied pairs fit one chunk of the fused kernel run in one
- * persistent fused launch over all their work units, ordered by cost (largest
- * first); molecules that need several chunks take the two-pass form (see
- * ladder_tuning) while their stored V+- tiles fit 128 GiB in all, with one
- * storing launch and one GEMM2 launch over all of them.  A batched plan
+ * workspace; mode LADDER_BF16X3, LADDER_BF16X6 or LADDER_OZAKI (else
+ * LADDER_ENOTSUP).  BF16X3 / BF16X6: molecules whose occupied pairs fit one
+ * chunk of the fused kernel run in one persistent fused launch over all their
+ * work units, ordered by cost (largest first); molecules that need several
+ * chunks take the two-pass form (see ladder_tuning) while their stored V+-
+ * tiles fit 128 GiB in all, with one storing launch and one GEMM2 launch over
+ * all of them.  LADDER_OZAKI: every molecule takes the error-free two-pass
+ * form (five slices), one launch of each pass over all molecules' work units;
+ * the stored slices of all molecules must fit 200 GiB (else LADDER_ENOTSUP).
+ * A batched plan
  * serves only ladder_apply_batched and ladder_step_batched (the other calls
  * return LADDER_EINVAL);
  * ladder_energy_noalloc gives the energy of each molecule. */
@@ -301,7 +305,8 @@ ladder_status ladder_plan_batched(int n, const int *o, const int *v, const int *
  * ladder_tuning (ksplit is the plan's own; lambda_only must be 0).  A member
  * moved to the two-pass form must keep the batch's stored tiles within the
  * batch cap (else LADDER_ENOTSUP).  The autotuner's per-shape choices are
- * applied to a batch through this call. */
+ * applied to a batch through this call.  A LADDER_OZAKI batch has no member
+ * tuning (LADDER_ENOTSUP). */
 ladder_status ladder_set_member_tuning(ladder_plan_t plan, int m, const ladder_tuning *t);
 
 /* B[k], tau[k], R[k] are device pointers for molecule k (host arrays of n

@@ -431,8 +431,9 @@ class LadderBatch:
     CUDA graph) plus its workspace."""
 
     def __init__(self, shapes, mode="bf16x6", device=None, tunings=None):
-        """mode: "bf16x3", "bf16x6", or "tuned" (BF16X6 with each member's
-        launch parameters and form from the autotuner's cache, see tune.py);
+        """mode: "bf16x3", "bf16x6", "ozaki" (every member in the error-free
+        two-pass form), or "tuned" (BF16X6 with each member's launch
+        parameters and form from the autotuner's cache, see tune.py);
         tunings: optional list of per-member dicts of ladder_tuning fields
         (None entries keep the plan's choice)."""
         import torch

@@ -281,10 +281,22 @@ void launch_oz_rowscale(int N, int v, int vp, const double *B, float *rs, int *s
 void launch_oz_split_B(int N, int v, int vp, int Np, int nslices, const double *B, const float *rs,
                        __nv_bfloat16 *Bt, cudaStream_t s);
 void launch_oz_pack_t2(const OzPackArgs &a, cudaStream_t s);
+// One launch of an error-free pass: a single molecule (mols == nullptr, work
+// units 0..nitems-1 of `one`) or a batch (work unit k is local unit items[k].y
+// of molecule items[k].x, the molecules' args in device memory).  One CTA per
+// work unit.  status and timeout_ns serve every molecule of the launch.
+struct OzLaunch {
+  OzArgs one;
+  const OzArgs *mols;
+  const int2 *items;
+  int nitems;
+  int *status;
+  unsigned long long timeout_ns;
+};
 uint32_t oz_smem_bytes(int pass, int nslices);
 cudaError_t oz_init_attributes(int nslices);
-cudaError_t launch_oz_vstore(const OzArgs &a, int nslices, cudaStream_t s);
-cudaError_t launch_oz_gemm2(const OzArgs &a, int nslices, cudaStream_t s);
+cudaError_t launch_oz_vstore(const OzLaunch &L, int nslices, cudaStream_t s);
+cudaError_t launch_oz_gemm2(const OzLaunch &L, int nslices, cudaStream_t s);
 
 // One launch of the fused kernel: a single molecule (mols == nullptr, the
 // work units are 0..nitems-1 of `one`) or a batch (work unit k is local item

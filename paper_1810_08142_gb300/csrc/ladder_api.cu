@@ -129,6 +129,7 @@ struct ladder_plan_s {
   // two-pass members: storing-pass and GEMM2-pass work units, unpack blocks
   std::vector<int2> items1, items2, tcs2;
   size_t off_mols1 = 0, off_mols2 = 0, off_items1 = 0, off_items2 = 0, off_tcs2 = 0;
+  size_t off_oz1 = 0, off_oz2 = 0;  // error-free batch: OzArgs tables of the two passes
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
   std::vector<const void *> gkey;  // pointers the graph was captured with
@@ -848,7 +849,7 @@ static ladder_status init_plan(ladder_plan_s *pl, int o, int v, int naux, int mo
   if (o < 1 || o > 256 || v < 1 || v > 4096 || naux < 1 || naux > 65536) return LADDER_EINVAL;
   if (mode < LADDER_FP64 || mode > LADDER_OZAKI) return LADDER_EINVAL;
   if (mode == LADDER_AUTO) mode = LADDER_BF16X6;
-  if (mode == LADDER_OZAKI && (batch_member || with_backward)) return LADDER_ENOTSUP;
+  if (mode == LADDER_OZAKI && with_backward) return LADDER_ENOTSUP;
   pl->o = o;
   pl->v = v;
   pl->N = naux;
@@ -881,7 +882,7 @@ static ladder_status init_plan(ladder_plan_s *pl, int o, int v, int naux, int mo
     pl->ntiles_all = pl->ntiles_tc;
     pl->two_pass = 1;
     pl->ksplit = auto_ksplit(pl);
-    pl->vsplit = auto_vsplit(pl, false);
+    pl->vsplit = auto_vsplit(pl, batch_member);
     int major = 0, minor = 0;
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, pl->device);
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, pl->device);
@@ -1341,10 +1342,10 @@ static ladder_status apply_tc(ladder_plan_t pl, const double *B, const double *t
 // The error-free mode: operand preparation (B row scales and fixed-point
 // slices, tau+- slices per GEMM2 chunk), the storing pass, the GEMM2 pass and
 // the unpack of the two-pass form.
-static ladder_status apply_oz(ladder_plan_t pl, const double *B, const double *tau, double *R,
-                              cudaStream_t s) {
-  mark(pl, 0, s);
-  int *status = ws_at<int>(pl, pl->lay.status);
+// Error-free preparation of one molecule: row scales and fixed-point slices
+// of B, and the tau+- slices of every GEMM2 chunk.
+static void oz_prep(const ladder_plan_s *pl, const double *B, const double *tau, int *status,
+                    cudaStream_t s) {
   float *rsB = ws_at<float>(pl, pl->lay.ozRs);
   launch_oz_rowscale(pl->N, pl->v, pl->vp, B, rsB, status, s);
   launch_oz_split_B(pl->N, pl->v, pl->vp, pl->Np, pl->S, B, rsB, ws_at<__nv_bfloat16>(pl, pl->lay.Bt), s);
@@ -1361,8 +1362,12 @@ static ladder_status apply_oz(ladder_plan_t pl, const double *B, const double *t
   pk.nchunks = (int)pl->chunks_v.size();
   for (int c = 0; c < pk.nchunks; ++c) pk.chunks[c] = pl->chunks_v[c];
   launch_oz_pack_t2(pk, s);
-  ladder_status st = cuda_status(cudaGetLastError());
-  if (st != LADDER_OK) return st;
+}
+
+// Arguments of the error-free passes over all of a plan's tiles: pass 1
+// (pass = 1: block-pair ranges vsplit, no accumulators) or pass 2 (ranges
+// ksplit, accumulators in the slab).
+static OzArgs oz_args(const ladder_plan_s *pl, int pass, int *status) {
   OzArgs a;
   std::memset(&a, 0, sizeof(a));
   a.tmA = pl->tmA;
@@ -1370,7 +1375,7 @@ static ladder_status apply_oz(ladder_plan_t pl, const double *B, const double *t
   a.tmVl = pl->tmVl;
   a.Vst = ws_at<__nv_bfloat16>(pl, pl->lay.Vg);
   a.sV = ws_at<float>(pl, pl->lay.ozSV);
-  a.rsB = rsB;
+  a.rsB = ws_at<float>(pl, pl->lay.ozRs);
   a.T2 = ws_at<uint8_t>(pl, pl->lay.T2);
   a.sT = ws_at<float>(pl, pl->lay.ozST);
   a.status = status;
@@ -1389,6 +1394,30 @@ static ladder_status apply_oz(ladder_plan_t pl, const double *B, const double *t
   // every single wait is far shorter than a pass; 2 s plus 20x a work unit's estimate
   const double unit_flops = 2.0 * 128.0 * 64.0 * 2.0 * pl->Np * 21.0 * ((double)pl->nbp / pl->vsplit);
   a.timeout_ns = (unsigned long long)(2e9 + 20.0 * unit_flops / 4e12 * 1e9);
+  a.ksplit = pass == 1 ? pl->vsplit : pl->ksplit;
+  a.nitems = pl->ntiles_tc * (pass == 1 ? 1 : a.nchunks) * a.ksplit;
+  a.racc = pass == 1 ? nullptr : ws_at<float2>(pl, pl->lay.slab);
+  return a;
+}
+
+static OzLaunch oz_launch(const OzArgs &a) {
+  OzLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  L.one = a;
+  L.nitems = a.nitems;
+  L.status = a.status;
+  L.timeout_ns = a.timeout_ns;
+  return L;
+}
+
+static ladder_status apply_oz(ladder_plan_t pl, const double *B, const double *tau, double *R,
+                              cudaStream_t s) {
+  mark(pl, 0, s);
+  int *status = ws_at<int>(pl, pl->lay.status);
+  oz_prep(pl, B, tau, status, s);
+  ladder_status st = cuda_status(cudaGetLastError());
+  if (st != LADDER_OK) return st;
+  OzArgs a1 = oz_args(pl, 1, status), a2 = oz_args(pl, 2, status);
   // tile ranges one after the other (one unless the stored tiles exceed the
   // cap): pass 1 (GEMM1 of every (tile, block pair), V+- slices and scales
   // stored), pass 2 (GEMM2 per (tile, chunk, block-pair range)), unpack
@@ -1398,17 +1427,13 @@ static ladder_status apply_oz(ladder_plan_t pl, const double *B, const double *t
   mark(pl, 1, s);
   for (int r0 = 0; r0 < nt && st == LADDER_OK; r0 += rt) {
     const int cnt = std::min(rt, nt - r0);
-    a.tile0 = pl->tile0 + r0;
-    a.ntiles = cnt;
-    a.ksplit = pl->vsplit;
-    a.nitems = cnt * pl->vsplit;
-    a.racc = nullptr;
-    st = cuda_status(launch_oz_vstore(a, pl->S, s));
+    a1.tile0 = a2.tile0 = pl->tile0 + r0;
+    a1.ntiles = a2.ntiles = cnt;
+    a1.nitems = cnt * pl->vsplit;
+    a2.nitems = cnt * a2.nchunks * pl->ksplit;
+    st = cuda_status(launch_oz_vstore(oz_launch(a1), pl->S, s));
     if (one) mark(pl, 4, s);
-    a.ksplit = pl->ksplit;
-    a.nitems = cnt * a.nchunks * pl->ksplit;
-    a.racc = ws_at<float2>(pl, pl->lay.slab);
-    if (st == LADDER_OK) st = cuda_status(launch_oz_gemm2(a, pl->S, s));
+    if (st == LADDER_OK) st = cuda_status(launch_oz_gemm2(oz_launch(a2), pl->S, s));
     if (one) mark(pl, 2, s);
     if (st == LADDER_OK) {
       TcLaunch L;
@@ -1748,6 +1773,9 @@ static void batch_finalize(ladder_plan_s *pl) {
   region(pl->off_mols, (size_t)n * sizeof(TcArgs));
   region(pl->off_mols1, (size_t)n * sizeof(TcArgs));
   region(pl->off_mols2, (size_t)n * sizeof(TcArgs));
+  const size_t noz = pl->mode == LADDER_OZAKI ? (size_t)n : 0;
+  region(pl->off_oz1, noz * sizeof(OzArgs));
+  region(pl->off_oz2, noz * sizeof(OzArgs));
   region(pl->off_items, pl->items.size() * sizeof(int2));
   region(pl->off_tcs, pl->tcs.size() * sizeof(int2));
   region(pl->off_items1, pl->items1.size() * sizeof(int2));
@@ -1781,12 +1809,13 @@ ladder_status ladder_plan_batched(int n, const int *o, const int *v, const int *
   *out = nullptr;
   if (mode & LADDER_WITH_BACKWARD) return LADDER_ENOTSUP;
   if (mode == LADDER_AUTO) mode = LADDER_BF16X6;
-  if (mode != LADDER_BF16X3 && mode != LADDER_BF16X6) return LADDER_ENOTSUP;  // incl. LADDER_OZAKI
+  if (mode != LADDER_BF16X3 && mode != LADDER_BF16X6 && mode != LADDER_OZAKI) return LADDER_ENOTSUP;
+  const bool oz = mode == LADDER_OZAKI;
   ladder_plan_s *pl = new (std::nothrow) ladder_plan_s();
   if (!pl) return LADDER_ENOMEM;
   pl->batched = true;
   pl->mode = mode;
-  pl->S = tc_slices(mode);
+  pl->S = oz ? kOzDefaultSlices : tc_slices(mode);
   double vsum = 0.0;
   for (int m = 0; m < n; ++m) {
     ladder_plan_s *sp = new (std::nothrow) ladder_plan_s();
@@ -1802,6 +1831,17 @@ ladder_status ladder_plan_batched(int n, const int *o, const int *v, const int *
     }
     pl->device = sp->device;
     pl->sm_count = sp->sm_count;
+    if (oz) {
+      // the error-free mode has only the two-pass form: every member's
+      // stored slices must fit the cap together
+      vsum += member_vbytes(sp);
+      if (vsum > kVStoreOzCap) {
+        ladder_destroy(pl);
+        return LADDER_ENOTSUP;
+      }
+      set_member_form(sp, true);
+      continue;
+    }
     // members whose fused form would recompute GEMM1 per chunk take the
     // two-pass form while the batch's stored tiles fit the cap
     const double vb = member_vbytes(sp);
@@ -1818,6 +1858,7 @@ ladder_status ladder_plan_batched(int n, const int *o, const int *v, const int *
 
 ladder_status ladder_set_member_tuning(ladder_plan_t pl, int m, const ladder_tuning *t) {
   if (!pl || !t || !pl->batched || pl->ws || m < 0 || m >= (int)pl->subs.size()) return LADDER_EINVAL;
+  if (pl->mode == LADDER_OZAKI) return LADDER_ENOTSUP;
   if (t->kc < 1 || t->kc > 64 || !(t->s_pieces == 1 || t->s_pieces == 2 || t->s_pieces == 4) ||
       t->flush_every < 1 || t->flush_every > 4096 || (t->xy_split != 0 && t->xy_split != 1) ||
       (t->two_pass != 0 && t->two_pass != 1) || t->lambda_only != 0)
@@ -1874,10 +1915,21 @@ static ladder_status batch_run(ladder_plan_t pl, const double *const *B, const d
     // unpacks, and every molecule's energy)
     char *w = static_cast<char *>(pl->ws);
     int *status = ws_at<int>(pl, pl->lay.status);
+    const bool oz = pl->mode == LADDER_OZAKI;
     std::vector<TcArgs> args(n), args1(n), args2(n);
+    std::vector<OzArgs> oz1(oz ? n : 0), oz2(oz ? n : 0);
     unsigned long long tmax = 0;
     for (size_t m = 0; m < n; ++m) {
       const ladder_plan_s *sp = pl->subs[m];
+      if (oz) {
+        // error-free members: the passes read OzArgs; the unpack reads the
+        // two-pass TcArgs of the same accumulators
+        oz1[m] = oz_args(sp, 1, status);
+        oz2[m] = oz_args(sp, 2, status);
+        args[m] = args1[m] = args2[m] = pass2_args(sp, R[m], status);
+        tmax = std::max(tmax, oz1[m].timeout_ns);
+        continue;
+      }
       args[m] = tc_args(sp, R[m], status);
       if (sp->two_pass) {
         args1[m] = pass1_args(sp, status);
@@ -1887,6 +1939,12 @@ static ladder_status batch_run(ladder_plan_t pl, const double *const *B, const d
       }
       tmax = std::max(tmax, args[m].timeout_ns);
     }
+    if (oz && (cudaStreamSynchronize(s) != cudaSuccess ||
+               cudaMemcpy(w + pl->off_oz1, oz1.data(), n * sizeof(OzArgs), cudaMemcpyHostToDevice) !=
+                   cudaSuccess ||
+               cudaMemcpy(w + pl->off_oz2, oz2.data(), n * sizeof(OzArgs), cudaMemcpyHostToDevice) !=
+                   cudaSuccess))
+      return cuda_status(cudaErrorUnknown);
     if (cudaStreamSynchronize(s) != cudaSuccess ||
         cudaMemcpy(w + pl->off_mols, args.data(), n * sizeof(TcArgs), cudaMemcpyHostToDevice) !=
             cudaSuccess ||
@@ -1921,12 +1979,31 @@ static ladder_status batch_run(ladder_plan_t pl, const double *const *B, const d
     for (size_t m = 0; m < n; ++m) {
       const ladder_plan_s *sp = pl->subs[m];
       if (step) launch_tau(sp->o, sp->v, t1[m], t2[m], tau[m], c);
+      if (oz) {
+        oz_prep(sp, B[m], tau[m], status, c);
+        continue;
+      }
       tc_prep(pl->subs[m], B[m], tau[m], c, false, status);
       if (sp->two_pass) pack_t2(sp, c);
     }
+    if (oz) {
+      // both error-free passes over every member's work units, one CTA each
+      auto oz_batch = [&](size_t mols, size_t items, int nitems) {
+        OzLaunch Lz;
+        std::memset(&Lz, 0, sizeof(Lz));
+        Lz.mols = reinterpret_cast<const OzArgs *>(w + mols);
+        Lz.items = reinterpret_cast<const int2 *>(w + items);
+        Lz.nitems = nitems;
+        Lz.status = status;
+        Lz.timeout_ns = tmax;
+        return Lz;
+      };
+      launch_oz_vstore(oz_batch(pl->off_oz1, pl->off_items1, (int)pl->items1.size()), pl->S, c);
+      launch_oz_gemm2(oz_batch(pl->off_oz2, pl->off_items2, (int)pl->items2.size()), pl->S, c);
+    }
     if (L.nitems) launch_ladder_tc(L, pl->S, std::min(L.nitems, pl->sm_count), c);
-    if (L1.nitems) launch_ladder_vstore(L1, pl->S, std::min(L1.nitems, pl->sm_count), c);
-    if (L2.nitems) launch_ladder_gemm2(L2, pl->S, std::min(L2.nitems, pl->sm_count), c);
+    if (!oz && L1.nitems) launch_ladder_vstore(L1, pl->S, std::min(L1.nitems, pl->sm_count), c);
+    if (!oz && L2.nitems) launch_ladder_gemm2(L2, pl->S, std::min(L2.nitems, pl->sm_count), c);
     if (!pl->tcs.empty()) launch_unpack(L, (int)pl->tcs.size(), c);
     if (!pl->tcs2.empty()) launch_unpack2(L2, (int)pl->tcs2.size(), c);
     if (step)

@@ -36,8 +36,8 @@
 // fixed-point slices with one scale per (ab row, block pair), stored to the
 // workspace with their scales.  Pass 2 (oz_gemm2_kernel): per (tile, chunk of
 // <= 128 occupied pairs of one sign, block-pair range): the S x S slice
-// products of every 16-slot piece with p + q < S, drained once per block
-// pair.  The unpack kernel of the two-pass form then writes R.
+// products of every 16-slot piece with p + q < S, issued and drained by order
+// group so that draining one group overlaps the MMAs of the others.  The unpack kernel of the two-pass form then writes R.
 //
 // Warp roles (576 threads): warp 0 TMA producer, warp 1 MMA issuer (one
 // thread), warps 2-17 conversion (four per TMEM lane quadrant, each owning a
@@ -90,6 +90,60 @@ __device__ __forceinline__ void ds_acc(float2 &acc, float h, float l) {
   two_sum(acc.x, h, s, e);
   acc.x = s;
   acc.y = __fadd_rn(acc.y, __fadd_rn(l, e));
+}
+
+// Two FP32 lanes per instruction (add / sub / mul .f32x2, sm_100 and later),
+// each lane rounded to nearest exactly like the scalar instruction.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  float2 d;
+  asm("{.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  float2 d;
+  asm("{.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  float2 d;
+  asm("{.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+// two_sum on two lanes at once
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &e) {
+  s = add2(a, b);
+  const float2 bb = sub2(s, a);
+  e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+// (H, L) += (h, l) and (H, L) += x, two accumulators at once (as ds_acc)
+__device__ __forceinline__ void ds_acc2(float2 &H, float2 &L, float2 h, float2 l) {
+  float2 s, e;
+  two_sum2(H, h, s, e);
+  H = s;
+  L = add2(L, add2(l, e));
+}
+__device__ __forceinline__ void ds_add2(float2 &H, float2 &L, float2 x) {
+  float2 s, e;
+  two_sum2(H, x, s, e);
+  H = s;
+  L = add2(L, e);
 }
 
 // 2^e as a float for -126 <= e <= 127
@@ -158,15 +212,38 @@ __device__ __forceinline__ Item decode(const OzArgs &A, int slot, int nchunks) {
   return I;
 }
 
+// The molecule's arguments and the local unit index of work unit u: a single
+// molecule reads them from the launch parameters, a batch from its device table.
+template <bool kBatch>
+__device__ __forceinline__ const OzArgs &oz_args(const OzLaunch &Lp, int u, int &local) {
+  if constexpr (!kBatch) {
+    local = u;
+    return Lp.one;
+  } else {
+    const int2 w = Lp.items[u];
+    local = w.y;
+    return Lp.mols[w.x];
+  }
+}
+// Pass 1 units walk range-major (unit u: range u / tiles of tile u % tiles) so
+// the resident CTAs share B panels in L2; pass 2 likewise over (tile, chunk).
+__device__ __forceinline__ int vstore_slot(const OzArgs &A, int u) {
+  return (u % A.ntiles) * A.ksplit + u / A.ntiles;
+}
+__device__ __forceinline__ int gemm2_slot(const OzArgs &A, int u) {
+  const int tcs = A.ntiles * A.nchunks;
+  return (u % tcs) * A.ksplit + u / tcs;
+}
+
 struct Bars {
   uint32_t base;
   int stages;
   __device__ uint32_t full(int s) const { return base + 8u * s; }
   __device__ uint32_t empty(int s) const { return base + 8u * (stages + s); }
   __device__ uint32_t cfull(int b) const { return base + 8u * (2 * stages + b); }
-  __device__ uint32_t cfree(int b) const { return base + 8u * (2 * stages + 2 + b); }
-  __device__ uint32_t done() const { return base + 8u * (2 * stages + 4); }
-  static constexpr int kCount = 5;  // + 2 * stages
+  __device__ uint32_t cfree(int b) const { return base + 8u * (2 * stages + 3 + b); }
+  __device__ uint32_t done() const { return base + 8u * (2 * stages + 6); }
+  static constexpr int kCount = 7;  // + 2 * stages
 };
 
 template <int S>
@@ -188,8 +265,8 @@ struct Cfg2 {
 // GEMM1 of every (tile, block pair) in exact windows, V+- = X +- Y', fixed-point
 // slices of V+- to the workspace.  Work units walk range-major (unit u: range
 // u / tiles of tile u % tiles) so the resident CTAs share B panels in L2.
-template <int S>
-__global__ void __launch_bounds__(kThreads, 1) oz_vstore_kernel(const __grid_constant__ OzArgs A) {
+template <int S, bool kBatch>
+__global__ void __launch_bounds__(kThreads, 1) oz_vstore_kernel(const __grid_constant__ OzLaunch Lp) {
   using C = Cfg1<S>;
   static_assert(C::kStages >= 3 && 8 * (2 * C::kStages + Bars::kCount) + 8 <= 256, "ring");
   static_assert(S >= 4 && S <= 6, "slices");
@@ -224,9 +301,7 @@ __global__ void __launch_bounds__(kThreads, 1) oz_vstore_kernel(const __grid_con
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
-  const Watchdog wd{A.status, abort_flag, A.timeout_ns};
-  const int nwin = (A.nks + kOzKc - 1) / kOzKc;
-  auto unit_slot = [&](int u) { return (u % A.ntiles) * A.ksplit + u / A.ntiles; };
+  const Watchdog wd{Lp.status, abort_flag, Lp.timeout_ns};
 
   if (warp == 0) {
     // ================================================================ TMA producer
@@ -234,10 +309,13 @@ __global__ void __launch_bounds__(kThreads, 1) oz_vstore_kernel(const __grid_con
       int stage = 0;
       uint32_t phase = 0, armed = 0, armed_par = 0;
       bool ok = true;
-      tma_prefetch_desc(&A.tmA);
-      tma_prefetch_desc(&A.tmB);
-      for (int u = blockIdx.x; ok && u < A.nitems; u += gridDim.x) {
-        const Item I = decode(A, unit_slot(u), 1);
+      for (int u = blockIdx.x; ok && u < Lp.nitems; u += gridDim.x) {
+        int local;
+        const OzArgs &A = oz_args<kBatch>(Lp, u, local);
+        const Item I = decode(A, vstore_slot(A, local), 1);
+        const int nwin = (A.nks + kOzKc - 1) / kOzKc;
+        tma_prefetch_desc(&A.tmA);
+        tma_prefetch_desc(&A.tmB);
         for (int p = I.p0; ok && p < I.p1; ++p) {
           int k, l;
           pair_of(p, k, l);
@@ -262,7 +340,7 @@ __global__ void __launch_bounds__(kThreads, 1) oz_vstore_kernel(const __grid_con
         }
       }
       if (!ok) {
-        DrainWatch dw(A.status, A.timeout_ns);
+        DrainWatch dw(Lp.status, Lp.timeout_ns);
         for (int s = 0; s < C::kStages; ++s)
           if (armed & (1u << s)) mbar_wait(bars.full(s), (armed_par >> s) & 1u, dw.wd, kSiteTmaFull);
       }
@@ -276,8 +354,11 @@ __global__ void __launch_bounds__(kThreads, 1) oz_vstore_kernel(const __grid_con
       const uint32_t hi64 = desc_hi(512, kSwizzle64);
       const uint32_t id64 = idesc_bf16(128, 64);
       bool ok = true;
-      for (int u = blockIdx.x; ok && u < A.nitems; u += gridDim.x) {
-        const Item I = decode(A, unit_slot(u), 1);
+      for (int u = blockIdx.x; ok && u < Lp.nitems; u += gridDim.x) {
+        int local;
+        const OzArgs &A = oz_args<kBatch>(Lp, u, local);
+        const Item I = decode(A, vstore_slot(A, local), 1);
+        const int nwin = (A.nks + kOzKc - 1) / kOzKc;
         for (int p = I.p0; ok && p < I.p1; ++p) {
           int k, l;
           pair_of(p, k, l);
@@ -323,7 +404,7 @@ __global__ void __launch_bounds__(kThreads, 1) oz_vstore_kernel(const __grid_con
         }
       }
       mma_commit(bars.done());
-      DrainWatch dw(A.status, A.timeout_ns);
+      DrainWatch dw(Lp.status, Lp.timeout_ns);
       mbar_wait(bars.done(), 0, dw.wd, kSiteRFull);
     }
   } else {
@@ -335,8 +416,11 @@ __global__ void __launch_bounds__(kThreads, 1) oz_vstore_kernel(const __grid_con
     const int a_l = L >> 3, x_l = L & 7;
     uint32_t use[2] = {0, 0};
     bool ok = true;
-    for (int u = blockIdx.x; ok && u < A.nitems; u += gridDim.x) {
-      const Item I = decode(A, unit_slot(u), 1);
+    for (int u = blockIdx.x; ok && u < Lp.nitems; u += gridDim.x) {
+      int local;
+      const OzArgs &A = oz_args<kBatch>(Lp, u, local);
+      const Item I = decode(A, vstore_slot(A, local), 1);
+      const int nwin = (A.nks + kOzKc - 1) / kOzKc;
       const int a = I.A0 + a_l;
       for (int p = I.p0; ok && p < I.p1; ++p) {
         int k, l;
@@ -486,14 +570,15 @@ __global__ void __launch_bounds__(kThreads, 1) oz_vstore_kernel(const __grid_con
 
 // ============================================================================ pass 2
 // GEMM2 of one (tile, chunk of <= 128 occupied pairs of one sign, block-pair
-// range): per 16-slot piece the slice products V_p T_q^T (p + q < S) into the
-// four order accumulators (columns 0, 128, 256, 384), drained once per block
-// pair with the pair's row scales into double-single sums in registers.
-// Work units walk range-major (unit u: range u / (tiles * chunks)).
-template <int S>
-__global__ void __launch_bounds__(kThreads, 1) oz_gemm2_kernel(const __grid_constant__ OzArgs A) {
+// range): per block pair the slice products V_p T_q^T (p + q < S) of its four
+// 16-slot pieces into the four order accumulators (columns 0, 128, 256, 384),
+// issued and drained group by group (orders 0-1, 2, >= 3) with the pair's row
+// scales into double-single sums in registers.  Work units walk range-major
+// (unit u: range u / (tiles * chunks)).
+template <int S, bool kBatch>
+__global__ void __launch_bounds__(kThreads, 1) oz_gemm2_kernel(const __grid_constant__ OzLaunch Lp) {
   using C = Cfg2<S>;
-  static_assert(C::kStages >= 3 && 8 * (2 * C::kStages + Bars::kCount) + 8 <= 256, "ring");
+  static_assert(C::kStages >= SLOTS / TPIECE && 8 * (2 * C::kStages + Bars::kCount) + 8 <= 256, "ring");
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
@@ -509,8 +594,10 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm2_kernel(const __grid_cons
       mbar_init(bars.full(s), 1);
       mbar_init(bars.empty(s), 1);
     }
-    mbar_init(bars.cfull(0), 1);
-    mbar_init(bars.cfree(0), kEpi);
+    for (int b = 0; b < 3; ++b) {
+      mbar_init(bars.cfull(b), 1);
+      mbar_init(bars.cfree(b), kEpi);
+    }
     mbar_init(bars.done(), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -523,10 +610,8 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm2_kernel(const __grid_cons
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
-  const Watchdog wd{A.status, abort_flag, A.timeout_ns};
+  const Watchdog wd{Lp.status, abort_flag, Lp.timeout_ns};
   constexpr int kPieces = SLOTS / TPIECE;
-  const int tcs = A.ntiles * A.nchunks;
-  auto unit_slot = [&](int u) { return (u % tcs) * A.ksplit + u / tcs; };
 
   if (warp == 0) {
     // ================================================================ TMA producer
@@ -534,9 +619,11 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm2_kernel(const __grid_cons
       int stage = 0;
       uint32_t phase = 0, armed = 0, armed_par = 0;
       bool ok = true;
-      tma_prefetch_desc(&A.tmVl);
-      for (int u = blockIdx.x; ok && u < A.nitems; u += gridDim.x) {
-        const Item I = decode(A, unit_slot(u), A.nchunks);
+      for (int u = blockIdx.x; ok && u < Lp.nitems; u += gridDim.x) {
+        int local;
+        const OzArgs &A = oz_args<kBatch>(Lp, u, local);
+        const Item I = decode(A, gemm2_slot(A, local), A.nchunks);
+        tma_prefetch_desc(&A.tmVl);
         const uint32_t sc = (uint32_t)(I.CH.nps + I.CH.nms);
         const int sg = I.CH.nps > 0 ? 0 : 1;
         const uint32_t tbytes = (uint32_t)S * sc * 32u;
@@ -559,104 +646,161 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm2_kernel(const __grid_cons
         }
       }
       if (!ok) {
-        DrainWatch dw(A.status, A.timeout_ns);
+        DrainWatch dw(Lp.status, Lp.timeout_ns);
         for (int s = 0; s < C::kStages; ++s)
           if (armed & (1u << s)) mbar_wait(bars.full(s), (armed_par >> s) & 1u, dw.wd, kSiteTmaFull);
       }
     }
   } else if (warp == 1) {
     // ================================================================ MMA issuer
+    // Per block pair the products go out by order group: orders 0 and 1
+    // (accumulators 0 and 1, 3 MMAs per piece), order 2 (accumulator 2, 3
+    // per piece), orders >= 3 (accumulator 3).  Each group is committed on its
+    // own barrier, so the drain of a group overlaps the MMAs of the later
+    // groups, and the next pair's group starts as soon as its accumulator has
+    // been drained.  The four pieces of a pair stay in the ring until their
+    // last (order >= 3) MMAs.
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0, g = 0;
       const uint32_t hi32 = desc_hi(256, kSwizzle32);
       bool ok = true;
-      for (int u = blockIdx.x; ok && u < A.nitems; u += gridDim.x) {
-        const Item I = decode(A, unit_slot(u), A.nchunks);
+      for (int u = blockIdx.x; ok && u < Lp.nitems; u += gridDim.x) {
+        int local;
+        const OzArgs &A = oz_args<kBatch>(Lp, u, local);
+        const Item I = decode(A, gemm2_slot(A, local), A.nchunks);
         const uint32_t sc = (uint32_t)(I.CH.nps + I.CH.nms);
         const uint32_t id = idesc_bf16(128, (int)sc);
         for (int p = I.p0; ok && p < I.p1; ++p) {
-          // the four accumulators are free once the last pair has been drained
+          int sidx[kPieces];
+          // orders 0 and 1, waiting for each piece's operands
           if (!(ok = mbar_wait(bars.cfree(0), (g & 1u) ^ 1u, wd, kSiteRFree))) break;
           tc_fence_after();
           for (int piece = 0; ok && piece < kPieces; ++piece) {
             if (!(ok = mbar_wait(bars.full(stage), phase, wd, kSiteTmaFull))) break;
-            const uint32_t st = ring + (uint32_t)stage * C::kStage;
-            const uint32_t stt = st + S * VP_PLANE;
-#pragma unroll
-            for (int pa = 0; pa < S; ++pa)
-#pragma unroll
-              for (int q = 0; q < S - pa; ++q) {
-                const int grp = pa + q < 3 ? pa + q : 3;
-                const bool first = piece == 0 && pa == 0 && q <= 3;
-                mma_bf16(tmem + 128u * grp, desc64(st + pa * VP_PLANE, hi32), desc64(stt + q * sc * 32u, hi32), id,
-                         first ? 0u : 1u);
-              }
-            mma_commit(bars.empty(stage));
+            sidx[piece] = stage;
             if (++stage == C::kStages) {
               stage = 0;
               phase ^= 1u;
             }
+            const uint32_t st = ring + (uint32_t)sidx[piece] * C::kStage, stt = st + S * VP_PLANE;
+            const uint32_t acc = piece ? 1u : 0u;
+            mma_bf16(tmem, desc64(st, hi32), desc64(stt, hi32), id, acc);
+            mma_bf16(tmem + 128u, desc64(st, hi32), desc64(stt + sc * 32u, hi32), id, acc);
+            mma_bf16(tmem + 128u, desc64(st + VP_PLANE, hi32), desc64(stt, hi32), id, 1u);
           }
           if (!ok) break;
           mma_commit(bars.cfull(0));
+          // order 2
+          if (!(ok = mbar_wait(bars.cfree(1), (g & 1u) ^ 1u, wd, kSiteRFree))) break;
+          tc_fence_after();
+          for (int piece = 0; piece < kPieces; ++piece) {
+            const uint32_t st = ring + (uint32_t)sidx[piece] * C::kStage, stt = st + S * VP_PLANE;
+#pragma unroll
+            for (int pa = 0; pa <= 2; ++pa)
+              mma_bf16(tmem + 256u, desc64(st + pa * VP_PLANE, hi32), desc64(stt + (2 - pa) * sc * 32u, hi32), id,
+                       (piece == 0 && pa == 0) ? 0u : 1u);
+          }
+          mma_commit(bars.cfull(1));
+          // orders >= 3; a piece's stage goes back to the producer after them
+          if (!(ok = mbar_wait(bars.cfree(2), (g & 1u) ^ 1u, wd, kSiteRFree))) break;
+          tc_fence_after();
+          for (int piece = 0; piece < kPieces; ++piece) {
+            const uint32_t st = ring + (uint32_t)sidx[piece] * C::kStage, stt = st + S * VP_PLANE;
+#pragma unroll
+            for (int pa = 0; pa < S; ++pa)
+#pragma unroll
+              for (int q = (pa < 3 ? 3 - pa : 0); q < S - pa; ++q)
+                mma_bf16(tmem + 384u, desc64(st + pa * VP_PLANE, hi32), desc64(stt + q * sc * 32u, hi32), id,
+                         (piece == 0 && pa == 0 && q == 3) ? 0u : 1u);
+            mma_commit(bars.empty(sidx[piece]));
+          }
+          mma_commit(bars.cfull(2));
           ++g;
         }
       }
       mma_commit(bars.done());
-      DrainWatch dw(A.status, A.timeout_ns);
+      DrainWatch dw(Lp.status, Lp.timeout_ns);
       mbar_wait(bars.done(), 0, dw.wd, kSiteRFull);
     }
   } else {
     // ================================================================ drains -> sums
+    // Group by group, as the MMA issuer commits them, each scaled by the
+    // pair's row scales (exact powers of two): orders 0 + 1 as one TwoSum
+    // pair into the double-single sums, order 2 (2^-16 below the window) with
+    // a TwoSum, orders >= 3 (2^-24 below) fused into the low words, where the
+    // rounding is 2^-48 of the window; two columns per f32x2 instruction.
     const int quad = warp & 3;
     const int qw = (warp - 2) >> 2;  // columns 32 qw .. 32 qw + 31
     const int L = quad * 32 + lane;  // TMEM lane = ab row of the tile
     const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + 32u * qw;
     uint32_t g = 0;
     bool ok = true;
-    for (int u = blockIdx.x; ok && u < A.nitems; u += gridDim.x) {
-      const Item I = decode(A, unit_slot(u), A.nchunks);
+    for (int u = blockIdx.x; ok && u < Lp.nitems; u += gridDim.x) {
+      int local;
+      const OzArgs &A = oz_args<kBatch>(Lp, u, local);
+      const Item I = decode(A, gemm2_slot(A, local), A.nchunks);
       const int sc = I.CH.nps + I.CH.nms;
       const int sg = I.CH.nps > 0 ? 0 : 1;
       const int ng = min(8, max(0, (sc - 32 * qw) / 4));  // this thread's 4-column groups
-      float2 acc[32];
+      float2 H[16], Lo[16];  // (hi, lo) sums of columns 32 qw + 2k and 2k + 1 (as .x and .y)
 #pragma unroll
-      for (int e = 0; e < 32; ++e) acc[e] = make_float2(0.f, 0.f);
+      for (int e = 0; e < 16; ++e) H[e] = Lo[e] = make_float2(0.f, 0.f);
       for (int p = I.p0; ok && p < I.p1; ++p) {
         const float *svp = A.sV + ((size_t)(I.tile * A.nbp + p) * 2 + sg) * 128 + L;
         const float *st = A.sT + ((size_t)I.ch * A.nbp + p) * kOzMaxCols + 32 * qw;
-        // this pair's scales into L1 while its MMAs run (the loads in the
-        // drain below then hit L1 instead of waiting on L2 group by group)
+        // this pair's scales into L1 while its MMAs run
         asm volatile("prefetch.global.L1 [%0];" ::"l"(st));
         asm volatile("prefetch.global.L1 [%0];" ::"l"(svp));
         if (!(ok = mbar_wait(bars.cfull(0), g & 1u, wd, kSiteRFull))) break;
-        ++g;
         tc_fence_after();
         const float sv = *svp;
+        const float2 sv2 = make_float2(sv, sv);
 #pragma unroll
         for (int h = 0; h < 8; ++h) {
           if (h < ng) {
-            float g0[4], g1[4], g2[4], g3[4];
+            float g0[4], g1[4];
             const uint32_t c0 = tl + 4u * h;
             tmem_ld4(c0, g0);
             tmem_ld4(c0 + 128u, g1);
-            tmem_ld4(c0 + 256u, g2);
-            tmem_ld4(c0 + 384u, g3);
             const float4 t0 = *reinterpret_cast<const float4 *>(st + 4 * h);
-            const float ts[4] = {t0.x, t0.y, t0.z, t0.w};
             tmem_ld_wait();
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              float hh, ll;
-              window_value(g0[e], g1[e], g2[e], g3[e], hh, ll);
-              const float s = sv * ts[e];
-              ds_acc(acc[4 * h + e], hh * s, ll * s);
-            }
+            const float2 s01 = mul2(sv2, make_float2(t0.x, t0.y)), s23 = mul2(sv2, make_float2(t0.z, t0.w));
+            float2 hh, ll;
+            two_sum2(make_float2(g0[0], g0[1]), make_float2(g1[0], g1[1]), hh, ll);
+            ds_acc2(H[2 * h], Lo[2 * h], mul2(hh, s01), mul2(ll, s01));
+            two_sum2(make_float2(g0[2], g0[3]), make_float2(g1[2], g1[3]), hh, ll);
+            ds_acc2(H[2 * h + 1], Lo[2 * h + 1], mul2(hh, s23), mul2(ll, s23));
           }
         }
         tc_fence_before();
         mbar_arrive(bars.cfree(0));
+#pragma unroll
+        for (int grp = 2; grp < 4; ++grp) {
+          if (!(ok = mbar_wait(bars.cfull(grp - 1), g & 1u, wd, kSiteRFull))) break;
+          tc_fence_after();
+#pragma unroll
+          for (int h = 0; h < 8; ++h) {
+            if (h < ng) {
+              float gg[4];
+              tmem_ld4(tl + 4u * h + 128u * grp, gg);
+              const float4 t0 = *reinterpret_cast<const float4 *>(st + 4 * h);
+              tmem_ld_wait();
+              const float2 s01 = mul2(sv2, make_float2(t0.x, t0.y)), s23 = mul2(sv2, make_float2(t0.z, t0.w));
+              if (grp == 2) {
+                ds_add2(H[2 * h], Lo[2 * h], mul2(make_float2(gg[0], gg[1]), s01));
+                ds_add2(H[2 * h + 1], Lo[2 * h + 1], mul2(make_float2(gg[2], gg[3]), s23));
+              } else {
+                Lo[2 * h] = fma2(make_float2(gg[0], gg[1]), s01, Lo[2 * h]);
+                Lo[2 * h + 1] = fma2(make_float2(gg[2], gg[3]), s23, Lo[2 * h + 1]);
+              }
+            }
+          }
+          tc_fence_before();
+          mbar_arrive(bars.cfree(grp - 1));
+        }
+        if (!ok) break;
+        ++g;
       }
       if (!ok) break;
       // this unit's sums, [col][lane]
@@ -664,7 +808,11 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm2_kernel(const __grid_cons
       for (int h = 0; h < 8; ++h)
         if (h < ng)
 #pragma unroll
-          for (int e = 0; e < 4; ++e) I.racc[(size_t)(32 * qw + 4 * h + e) * 128 + L] = acc[4 * h + e];
+          for (int k = 0; k < 2; ++k) {
+            const size_t c = (size_t)(32 * qw + 4 * h + 2 * k);
+            I.racc[c * 128 + L] = make_float2(H[2 * h + k].x, Lo[2 * h + k].x);
+            I.racc[(c + 1) * 128 + L] = make_float2(H[2 * h + k].y, Lo[2 * h + k].y);
+          }
     }
   }
 
@@ -865,33 +1013,50 @@ uint32_t oz_smem_bytes(int pass, int nslices) {
   return nslices == 5 ? Cfg2<5>::kSmem : Cfg2<6>::kSmem;
 }
 
-cudaError_t oz_init_attributes(int nslices) {
+template <int S>
+cudaError_t oz_attrs() {
   const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  if (nslices == 5) {
-    cudaError_t e = cudaFuncSetAttribute(oz_vstore_kernel<5>, at, (int)Cfg1<5>::kSmem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(oz_gemm2_kernel<5>, at, (int)Cfg2<5>::kSmem);
-    return e;
-  }
-  cudaError_t e = cudaFuncSetAttribute(oz_vstore_kernel<6>, at, (int)Cfg1<6>::kSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(oz_gemm2_kernel<6>, at, (int)Cfg2<6>::kSmem);
+  cudaError_t e = cudaFuncSetAttribute(oz_vstore_kernel<S, false>, at, (int)Cfg1<S>::kSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(oz_vstore_kernel<S, true>, at, (int)Cfg1<S>::kSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(oz_gemm2_kernel<S, false>, at, (int)Cfg2<S>::kSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(oz_gemm2_kernel<S, true>, at, (int)Cfg2<S>::kSmem);
   return e;
 }
 
-cudaError_t launch_oz_vstore(const OzArgs &a, int nslices, cudaStream_t s) {
-  if (a.nitems <= 0) return cudaSuccess;
-  if (nslices == 5)
-    oz_vstore_kernel<5><<<a.nitems, kThreads, Cfg1<5>::kSmem, s>>>(a);
-  else
-    oz_vstore_kernel<6><<<a.nitems, kThreads, Cfg1<6>::kSmem, s>>>(a);
+cudaError_t oz_init_attributes(int nslices) { return nslices == 5 ? oz_attrs<5>() : oz_attrs<6>(); }
+
+// one CTA per work unit
+cudaError_t launch_oz_vstore(const OzLaunch &L, int nslices, cudaStream_t s) {
+  if (L.nitems <= 0) return cudaSuccess;
+  const bool b = L.mols != nullptr;
+  if (nslices == 5) {
+    if (b)
+      oz_vstore_kernel<5, true><<<L.nitems, kThreads, Cfg1<5>::kSmem, s>>>(L);
+    else
+      oz_vstore_kernel<5, false><<<L.nitems, kThreads, Cfg1<5>::kSmem, s>>>(L);
+  } else {
+    if (b)
+      oz_vstore_kernel<6, true><<<L.nitems, kThreads, Cfg1<6>::kSmem, s>>>(L);
+    else
+      oz_vstore_kernel<6, false><<<L.nitems, kThreads, Cfg1<6>::kSmem, s>>>(L);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_oz_gemm2(const OzArgs &a, int nslices, cudaStream_t s) {
-  if (a.nitems <= 0) return cudaSuccess;
-  if (nslices == 5)
-    oz_gemm2_kernel<5><<<a.nitems, kThreads, Cfg2<5>::kSmem, s>>>(a);
-  else
-    oz_gemm2_kernel<6><<<a.nitems, kThreads, Cfg2<6>::kSmem, s>>>(a);
+cudaError_t launch_oz_gemm2(const OzLaunch &L, int nslices, cudaStream_t s) {
+  if (L.nitems <= 0) return cudaSuccess;
+  const bool b = L.mols != nullptr;
+  if (nslices == 5) {
+    if (b)
+      oz_gemm2_kernel<5, true><<<L.nitems, kThreads, Cfg2<5>::kSmem, s>>>(L);
+    else
+      oz_gemm2_kernel<5, false><<<L.nitems, kThreads, Cfg2<5>::kSmem, s>>>(L);
+  } else {
+    if (b)
+      oz_gemm2_kernel<6, true><<<L.nitems, kThreads, Cfg2<6>::kSmem, s>>>(L);
+    else
+      oz_gemm2_kernel<6, false><<<L.nitems, kThreads, Cfg2<6>::kSmem, s>>>(L);
+  }
   return cudaGetLastError();
 }
 

@@ -50,6 +50,9 @@ WORKLOADS = {
     "mid_o34_v400_n1600": Workload("mid_o34_v400_n1600", 34, 400, 1600, 2),
     "grad_o16_v200_n800": Workload("grad_o16_v200_n800", 16, 200, 800, 3),
     "fd_o3_v10_n30": Workload("fd_o3_v10_n30", 3, 10, 30, 3),
+    # the mid-size workload's occupied count (its GEMM2 chunk structure) with
+    # a small virtual space: a profiling case that holds ~2 GB on the device
+    "probe_o34_v120_n480": Workload("probe_o34_v120_n480", 34, 120, 480, 5),
 }
 
 
