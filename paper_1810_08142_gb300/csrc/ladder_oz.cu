@@ -70,28 +70,6 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// Value of one exactness window from its four order accumulators, as a
-// double-single (h, l) renormalised so that |l| <= ulp(h) / 2.  In units of
-// the order-0 products: h + e = g0 + g1 exactly (TwoSum); e is a multiple of
-// 2^-8 below 1/2 and g2 a multiple of 2^-16 below 2^7, so e + g2 is exact in
-// FP32; the TwoSum with h then leaves a remainder of at most ulp(h) / 2, to
-// which the tail orders (2^-24 below h) are added with a rounding 2^-48 below
-// h.  (Adding g2 straight into the low word would round it 2^-40 below h.)
-__device__ __forceinline__ void window_value(float g0, float g1, float g2, float g3, float &h, float &l) {
-  float h0, e;
-  two_sum(g0, g1, h0, e);
-  two_sum(h0, __fadd_rn(e, g2), h, l);
-  l = __fadd_rn(l, g3);
-}
-
-// acc (H, L) += (h, l)
-__device__ __forceinline__ void ds_acc(float2 &acc, float h, float l) {
-  float s, e;
-  two_sum(acc.x, h, s, e);
-  acc.x = s;
-  acc.y = __fadd_rn(acc.y, __fadd_rn(l, e));
-}
-
 // Two FP32 lanes per instruction (add / sub / mul .f32x2, sm_100 and later),
 // each lane rounded to nearest exactly like the scalar instruction.
 __device__ __forceinline__ float2 add2(float2 a, float2 b) {
@@ -144,6 +122,41 @@ __device__ __forceinline__ void ds_add2(float2 &H, float2 &L, float2 x) {
   two_sum2(H, x, s, e);
   H = s;
   L = add2(L, e);
+}
+
+// One exactness window of pass 1 into the double-single sums of 16 columns,
+// two columns per f32x2 instruction.  The window's value comes from its four
+// order accumulators g0..g3 (TMEM columns cbase + 64 g) as a double-single
+// (h, l) with |l| <= ulp(h) / 2.  In units of the order-0 products:
+// h0 + e = g0 + g1 exactly (TwoSum); e is a multiple of 2^-8 below 1/2 and g2
+// a multiple of 2^-16 below 2^7, so e + g2 is exact in FP32; the TwoSum with
+// h0 then leaves a remainder of at most ulp(h) / 2, to which the tail orders
+// (2^-24 below h) are added with a rounding 2^-48 below h.  (Adding g2
+// straight into the low word would round it 2^-40 below h.)  (h, l) then goes
+// into the running sum as ds_acc2 does.
+__device__ __forceinline__ void drain_window(uint32_t cbase, float2 (&acc)[16]) {
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    float g0[4], g1[4], g2[4], g3[4];
+    const uint32_t c0 = cbase + 4u * h;
+    tmem_ld4(c0, g0);
+    tmem_ld4(c0 + 64u, g1);
+    tmem_ld4(c0 + 128u, g2);
+    tmem_ld4(c0 + 192u, g3);
+    tmem_ld_wait();
+#pragma unroll
+    for (int e = 0; e < 4; e += 2) {
+      float2 h0, er, hh, ll;
+      two_sum2(make_float2(g0[e], g0[e + 1]), make_float2(g1[e], g1[e + 1]), h0, er);
+      two_sum2(h0, add2(er, make_float2(g2[e], g2[e + 1])), hh, ll);
+      ll = add2(ll, make_float2(g3[e], g3[e + 1]));
+      float2 H = make_float2(acc[4 * h + e].x, acc[4 * h + e + 1].x);
+      float2 L = make_float2(acc[4 * h + e].y, acc[4 * h + e + 1].y);
+      ds_acc2(H, L, hh, ll);
+      acc[4 * h + e] = make_float2(H.x, L.x);
+      acc[4 * h + e + 1] = make_float2(H.y, L.y);
+    }
+  }
 }
 
 // 2^e as a float for -126 <= e <= 127
@@ -434,23 +447,10 @@ __global__ void __launch_bounds__(kThreads, 1) oz_vstore_kernel(const __grid_con
             if (!(ok = mbar_wait(bars.cfull(tt), use[tt] & 1u, wd, kSiteXYFull))) break;
             ++use[tt];
             tc_fence_after();
-            float2 *acc = tt ? Y : X;
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-              float g0[4], g1[4], g2[4], g3[4];
-              const uint32_t c0 = tl + 256u * tt + 4u * h;
-              tmem_ld4(c0, g0);
-              tmem_ld4(c0 + 64u, g1);
-              tmem_ld4(c0 + 128u, g2);
-              tmem_ld4(c0 + 192u, g3);
-              tmem_ld_wait();
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                float hh, ll;
-                window_value(g0[e], g1[e], g2[e], g3[e], hh, ll);
-                ds_acc(acc[4 * h + e], hh, ll);
-              }
-            }
+            if (tt == 0)
+              drain_window(tl, X);
+            else
+              drain_window(tl + 256u, Y);
             tc_fence_before();
             mbar_arrive(bars.cfree(tt));
           }
@@ -488,17 +488,21 @@ __global__ void __launch_bounds__(kThreads, 1) oz_vstore_kernel(const __grid_con
 #pragma unroll
           for (int e = 0; e < 8; ++e) Y[8 * j + e] = make_float2(rh[e], rl[e]);
         }
-        // V+ = X + Y' into X, V- = X - Y' into Y (double-single, renormalised)
+        // V+ = X + Y' into X, V- = X - Y' into Y (double-single, renormalised),
+        // two columns per f32x2 instruction
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const float2 x = X[e], y = Y[e];
-          float s, er, lo;
-          two_sum(x.x, y.x, s, er);
-          lo = __fadd_rn(__fadd_rn(x.y, y.y), er);
-          two_sum(s, lo, X[e].x, X[e].y);
-          two_sum(x.x, -y.x, s, er);
-          lo = __fadd_rn(__fsub_rn(x.y, y.y), er);
-          two_sum(s, lo, Y[e].x, Y[e].y);
+        for (int e = 0; e < 16; e += 2) {
+          const float2 xh = make_float2(X[e].x, X[e + 1].x), xl = make_float2(X[e].y, X[e + 1].y);
+          const float2 yh = make_float2(Y[e].x, Y[e + 1].x), yl = make_float2(Y[e].y, Y[e + 1].y);
+          float2 sm, er, hi, lo;
+          two_sum2(xh, yh, sm, er);
+          two_sum2(sm, add2(add2(xl, yl), er), hi, lo);
+          X[e] = make_float2(hi.x, lo.x);
+          X[e + 1] = make_float2(hi.y, lo.y);
+          two_sum2(xh, mul2(yh, make_float2(-1.f, -1.f)), sm, er);
+          two_sum2(sm, add2(sub2(xl, yl), er), hi, lo);
+          Y[e] = make_float2(hi.x, lo.x);
+          Y[e + 1] = make_float2(hi.y, lo.y);
         }
         // one scale per (ab row, sign): the row's 64 slots are the 8 values of
         // this thread for its b and the 8 lanes x_l
@@ -524,28 +528,25 @@ __global__ void __launch_bounds__(kThreads, 1) oz_vstore_kernel(const __grid_con
               inv = pow2f(8 - E);
               scale = pow2f(E - 8);
             }
+            // slices two columns at a time (f32x2): x_s = rint(h), (h, l) =
+            // 256 (h - x_s + l) as a TwoSum pair, x_s stored as x_s 2^(-8 s)
             uint4 out[S];
+            const float2 inv2 = make_float2(inv, inv), magic = make_float2(12582912.0f, 12582912.0f);
+            const float2 c256 = make_float2(256.f, 256.f);
 #pragma unroll
             for (int e2 = 0; e2 < 4; ++e2) {
-              float hs[2], ls[2];
-#pragma unroll
-              for (int z = 0; z < 2; ++z) {
-                hs[z] = V[2 * e2 + z].x * inv;
-                ls[z] = V[2 * e2 + z].y * inv;
-              }
+              float2 hs = mul2(make_float2(V[2 * e2].x, V[2 * e2 + 1].x), inv2);
+              float2 ls = mul2(make_float2(V[2 * e2].y, V[2 * e2 + 1].y), inv2);
 #pragma unroll
               for (int s = 0; s < S; ++s) {
-                float xs[2];
-#pragma unroll
-                for (int z = 0; z < 2; ++z) {
-                  xs[z] = rint_small(hs[z]);
-                  float r, er;
-                  two_sum(__fsub_rn(hs[z], xs[z]), ls[z], r, er);
-                  hs[z] = r * 256.f;
-                  ls[z] = er * 256.f;
-                  xs[z] *= pow2f(-8 * s);
-                }
-                const __nv_bfloat162 b2 = __floats2bfloat162_rn(xs[0], xs[1]);
+                const float2 xs = sub2(add2(hs, magic), magic);
+                float2 r, er;
+                two_sum2(sub2(hs, xs), ls, r, er);
+                hs = mul2(r, c256);
+                ls = mul2(er, c256);
+                const float ps = pow2f(-8 * s);
+                const float2 xo = mul2(xs, make_float2(ps, ps));
+                const __nv_bfloat162 b2 = __floats2bfloat162_rn(xo.x, xo.y);
                 (&out[s].x)[e2] = *reinterpret_cast<const uint32_t *>(&b2);
               }
             }
