@@ -16,6 +16,10 @@ With --grad it stores 1024 seeded entries each of dE_L/dtau and dE_L/dB (the
 oracle's entry-wise analytic gradient, weights W = 2 t2 - t2^T) in
 <workload>_grad.json:
     python tests/golden/make_golden.py --grad grad_o16_v200_n800
+With --ragged it stores, for each of the 48 molecules of the ragged batch
+(synthetic.ragged_batch), E_L, the Frobenius norm of R and four R columns, in
+ragged48.json:
+    python tests/golden/make_golden.py --ragged
 """
 import json
 import os
@@ -125,8 +129,33 @@ def main_grad(name, m=1024):
     print(name, "gradient entries, seconds", time.time() - t0)
 
 
+def main_ragged():
+    t0 = time.time()
+    mols = []
+    for k, x in enumerate(synthetic.ragged_batch()):
+        t1 = time.time()
+        tau = oracle.tau(x.t1, x.t2)
+        R = oracle.ladder(x.B, tau)
+        pa, pb = sample_pairs(x.v, n=4, seed=1000 + k)
+        mols.append({"o": x.o, "v": x.v, "naux": x.naux, "E_L": oracle.energy(R, x.t2),
+                     "R_fro": float(np.linalg.norm(R)), "pairs_a": pa, "pairs_b": pb,
+                     "R_cols": [R[:, :, a, b].tolist() for a, b in zip(pa, pb)]})
+        print(k, x.o, x.v, x.naux, "E_L", mols[-1]["E_L"], "seconds", time.time() - t1, flush=True)
+    out = {"workload": "ragged48", "first_seed": 100, "molecules": mols,
+           "oracle_threads": oracle.threads(), "oracle_seconds": time.time() - t0,
+           "note": "48-molecule ragged batch; written by tests/golden/make_golden.py --ragged "
+                   "from the plain FP64 CPU oracle"}
+    path = os.path.join(ROOT, "tests", "golden", "ragged48.json")
+    with open(path, "w") as f:
+        json.dump(out, f)
+    print("ragged48 seconds", time.time() - t0)
+
+
 if __name__ == "__main__":
     args = sys.argv[1:]
+    if "--ragged" in args:
+        main_ragged()
+        sys.exit(0)
     run = (main_dressed if "--dressed" in args else main_triples if "--triples" in args
            else main_grad if "--grad" in args else main)
     for n in args:

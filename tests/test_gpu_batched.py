@@ -227,3 +227,66 @@ def test_ragged48_step_energies(lad):
     print("ragged48 step: %d energies checked, worst %.3e" % (nE, worst))
     assert nE >= 1 and worst < TOL["bf16x6"]
     batch.close()
+
+
+def test_step_batched_ozaki(lad):
+    """The error-free mode as a batch: every member in the two-pass form, both
+    passes over all members' work units in one launch each, inside one graph
+    with tau and E_L.  R within 1e-10 relative (worst element within 2e-10 of
+    max |R|), |dE_L| <= 1 uEh and within 1e-12 of the sum of the energy
+    terms' magnitudes, and a replay bitwise equal."""
+    import torch
+    shapes = SHAPES + TWO_PASS_SHAPES[:2] + [(12, 140, 150, 21)]
+    mols = [synthetic.make_inputs(o, v, n, s) for o, v, n, s in shapes]
+    batch = lad.LadderBatch([(x.o, x.v, x.naux) for x in mols], mode="ozaki")
+    Bs, t1s, t2s = ([to_dev(getattr(x, a)) for x in mols] for a in ("B", "t1", "t2"))
+    taus, Rs, E = batch.step(Bs, t1s, t2s)
+    torch.cuda.synchronize()
+    batch.check_device()
+    first = ([r.cpu().numpy() for r in Rs], E.cpu().numpy())
+    batch.step(Bs, t1s, t2s, taus, Rs, E)   # replay
+    torch.cuda.synchronize()
+    for k, x in enumerate(mols):
+        tau_o = oracle.tau(x.t1, x.t2)
+        R_o = oracle.ladder(x.B, tau_o)
+        E_o = oracle.energy(R_o, x.t2)
+        e_R = rel_err(first[0][k], R_o)
+        dE = abs(first[1][k] - E_o)
+        print("ozaki molecule %d (o=%d v=%d n=%d): R %.3e  |dE_L| %.3e  E_L %.6e" % (k, x.o, x.v, x.naux,
+                                                                                  e_R, dE, E_o))
+        assert rel_err(taus[k].cpu().numpy(), tau_o) < 1e-15
+        assert e_R < 1e-10
+        assert dE <= 1e-6 and dE <= 1e-12 * _e_scale(R_o, x.t2)
+        assert np.array_equal(Rs[k].cpu().numpy(), first[0][k])
+    assert np.array_equal(E.cpu().numpy(), first[1])
+    batch.close()
+
+
+def test_ragged48_ozaki_against_stored_oracle(lad):
+    """The 48-molecule ragged batch in the error-free mode through
+    ladder_step_batched: every member's E_L within 1 uEh of the stored oracle
+    value (tests/golden/ragged48.json, written by make_golden.py --ragged)
+    and four stored R columns per member within 1e-10."""
+    import json
+    import torch
+    with open(os.path.join(os.path.dirname(__file__), "golden", "ragged48.json")) as f:
+        gold = json.load(f)["molecules"]
+    mols = synthetic.ragged_batch()
+    assert len(gold) == len(mols)
+    batch = lad.LadderBatch([(x.o, x.v, x.naux) for x in mols], mode="ozaki")
+    Bs, t1s, t2s = ([to_dev(getattr(x, a)) for x in mols] for a in ("B", "t1", "t2"))
+    taus, Rs, E = batch.step(Bs, t1s, t2s)
+    torch.cuda.synchronize()
+    batch.check_device()
+    E = E.cpu().numpy()
+    worst_E, worst_R = 0.0, 0.0
+    for k, (x, g) in enumerate(zip(mols, gold)):
+        assert (g["o"], g["v"], g["naux"]) == (x.o, x.v, x.naux)
+        worst_E = max(worst_E, abs(E[k] - g["E_L"]))
+        R = Rs[k]
+        got = np.stack([R[:, :, a, b].cpu().numpy() for a, b in zip(g["pairs_a"], g["pairs_b"])])
+        worst_R = max(worst_R, rel_err(got, np.array(g["R_cols"])))
+    print("ragged48 ozaki: worst |dE_L| %.3e Eh, worst column rel err %.3e" % (worst_E, worst_R))
+    assert worst_E <= 1e-6
+    assert worst_R < 1e-10
+    batch.close()
