@@ -737,10 +737,13 @@ def main():
                 if prec in tr:
                     tr[prec + "_rel_diff"] = abs(tr[prec]["E_T"] - tr["fp64"]["E_T"]) / abs(tr["fp64"]["E_T"])
         extra["triples"] = tr
-    if args.backward and args.mode in ("bf16x3", "bf16x6"):
-        # the adjoint of E_L in the same mode and tuning: dE/dtau (the
-        # transposed ladder) and dE/dB (Gamma stored once, then contracted)
-        Lb = lad.Ladder(w.o, w.v, w.naux, mode=args.mode, device=dev, tuning=tun, backward=True)
+    if args.backward and args.mode in ("bf16x3", "bf16x6", "ozaki"):
+        # the adjoint of E_L: dE/dtau (the transposed ladder) and dE/dB (Gamma
+        # stored once, then contracted), in the same split mode and tuning, or
+        # in BF16X6 behind the error-free forward (which has no adjoint)
+        bmode = "bf16x6" if args.mode == "ozaki" else args.mode
+        Lb = lad.Ladder(w.o, w.v, w.naux, mode=bmode, device=dev,
+                        tuning=tuned_for(w, bmode) if args.mode == "ozaki" else tun, backward=True)
         lad.ladder_tau(Lb.plan, t1, t2, tau)
         Wt = Lb.weights(t2)
         dt, db = torch.empty_like(tau), torch.empty_like(B)
@@ -756,6 +759,7 @@ def main():
             bw[name + "_ms"] = b0.elapsed_time(b1)
         Lb.check_device()
         bw["dtau_tflops"] = F / (bw["dtau_ms"] * 1e-3) / 1e12
+        bw["mode"] = bmode
         bw["note"] = "dtau_tflops counts F_alg (the transposed ladder has the forward's flops)"
         extra["backward"] = bw
         Lb.close()

@@ -6,8 +6,11 @@ W = 2 t2 - t2^T (ladder_pair_combine):
     dE/dtau = transposed ladder of W           (ladder_backward)
     dE/dB   = 2 sum Gamma B, Gamma = W^T tau    (ladder_backward)
     dE/dt2  = 2 R - R^T                         (ladder_pair_combine)
-Both ladder_backward terms run in the plan's mode (FP64, BF16X3 or BF16X6;
-the error-free mode has no adjoint).
+Both ladder_backward terms run in the mode of the plan that serves the
+backward: the forward plan itself (FP64, BF16X3 or BF16X6), or a separate
+`grad_ladder`.  The error-free mode has no adjoint of its own, so an
+error-free forward plan (E_L and R to FP64 class) takes a BF16X6 or FP64
+grad_ladder created with backward=True; dE/dt2 comes from the forward's R.
 All arithmetic runs in the library's kernels; the incoming gradient (a
 scalar) is applied with an in-place multiply.
 """
@@ -20,11 +23,11 @@ from . import Ladder, ladder_pair_combine
 
 class LadderEnergy(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, B, tau, t2, ladder: Ladder):
+    def forward(ctx, B, tau, t2, ladder: Ladder, grad_ladder=None):
         R = ladder.apply(B, tau)
         E = ladder.energy(R, t2)
         ctx.save_for_backward(B, tau, t2, R)
-        ctx.ladder = ladder
+        ctx.ladder = ladder if grad_ladder is None else grad_ladder
         return E
 
     @staticmethod
@@ -43,10 +46,15 @@ class LadderEnergy(torch.autograd.Function):
         for t in (dB, dtau, dt2):
             if t is not None:
                 t.mul_(g)
-        return dB, dtau, dt2, None
+        return dB, dtau, dt2, None, None
 
 
-def ladder_energy(B, tau, t2, ladder: Ladder):
+def ladder_energy(B, tau, t2, ladder: Ladder, grad_ladder: Ladder = None):
     """Differentiable E_L(B, tau, t2) computed by `ladder` (a Ladder plan;
-    create it with backward=True when dE/dB is wanted)."""
-    return LadderEnergy.apply(B, tau, t2, ladder)
+    create it with backward=True when it serves the backward too).
+    grad_ladder: a plan of the same shape with backward=True that serves the
+    backward instead, e.g. BF16X6 behind an error-free forward."""
+    if grad_ladder is not None and (grad_ladder.o, grad_ladder.v, grad_ladder.naux) != (
+            ladder.o, ladder.v, ladder.naux):
+        raise ValueError("grad_ladder has another shape than ladder")
+    return LadderEnergy.apply(B, tau, t2, ladder, grad_ladder)

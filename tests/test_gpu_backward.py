@@ -128,3 +128,42 @@ def test_backward_full_size_sampled(lad, mode):
     assert e_B < DTAU_TOL[mode]
     # the dtau output keeps the pair symmetry of the ladder
     assert np.array_equal(dtau, dtau.transpose(1, 0, 3, 2))
+
+
+def test_autograd_error_free_forward_split_adjoint(lad):
+    """Gradient workload o=16, v=200, N_aux=800 through the autograd Function
+    with an error-free forward plan and a BF16X6 plan for the adjoint: E_L
+    within 1 uEh of the stored oracle value, and 1024 stored entries each of
+    dE/dtau and dE/dB within the BF16X6 bar."""
+    import json
+    import os
+    import torch
+    from paper_1810_08142_gb300.autograd import ladder_energy
+    w = synthetic.WORKLOADS["grad_o16_v200_n800"]
+    gdir = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    with open(os.path.join(gdir, w.name + ".json")) as f:
+        gold = json.load(f)
+    with open(os.path.join(gdir, w.name + "_grad.json")) as f:
+        g = json.load(f)
+    x = synthetic.make_inputs(w.o, w.v, w.naux, w.seed)
+    B = to_dev(x.B).requires_grad_(True)
+    tau = to_dev(oracle.tau(x.t1, x.t2)).requires_grad_(True)
+    t2 = to_dev(x.t2)
+    L = lad.Ladder(w.o, w.v, w.naux, mode="ozaki")
+    Lg = lad.Ladder(w.o, w.v, w.naux, mode="bf16x6", backward=True)
+    E = ladder_energy(B, tau, t2, L, Lg)
+    E.backward()
+    torch.cuda.synchronize()
+    L.check_device()
+    Lg.check_device()
+    dE = abs(float(E) - gold["E_L"])
+    dtau, dB = tau.grad.cpu().numpy(), B.grad.cpu().numpy()
+    i, j, c, d = (np.asarray(t) for t in g["dtau_index"])
+    P, xx, yy = (np.asarray(t) for t in g["dB_index"])
+    e_tau = rel_err(dtau[i, j, c, d], np.asarray(g["dtau"]))
+    e_B = rel_err(dB[P, xx, yy], np.asarray(g["dB"]))
+    print("ozaki forward + bf16x6 adjoint: |dE_L| %.3e  dtau rel %.3e  dB rel %.3e" % (dE, e_tau, e_B))
+    assert dE <= 1e-6
+    assert e_tau < DTAU_TOL["bf16x6"] and e_B < DTAU_TOL["bf16x6"]
+    with pytest.raises(ValueError):
+        ladder_energy(B, tau, t2, L, lad.Ladder(4, 24, 96, mode="bf16x6", backward=True))
