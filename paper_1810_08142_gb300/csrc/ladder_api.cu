@@ -572,7 +572,8 @@ TriplesLayout triples_layout(int o, int v, bool fp32, bool tc = false) {
   return L;
 }
 
-// E(T) = sum over (i, j) of one batched pass over k:
+// E(T) = sum over (i, j), i >= j, of one batched pass over k <= j (the sorted
+// triples; the energy kernel weighs each by the orderings it stands for):
 //   W[k] = P applied to  sum_d v_di^ba t_kj^cd - sum_l v_kl^cj t_il^ab
 // as twelve GEMMs (two per ordering of P), each written into W[k][a][b][c]
 // through the kEpiAcc3 epilogue, then the energy kernel on W[k].
@@ -587,6 +588,7 @@ cudaError_t triples_run(int o, int v, int n, const double *B, const double *Bov,
   T *W = reinterpret_cast<T *>(ws + L.W);
   double *part = reinterpret_cast<double *>(ws + L.part);
   const long long ov = (long long)o * v, vv = (long long)v * v, v3 = vv * v;
+  const int M_rows = (int)vv;  // rows (alpha, beta) of every W GEMM
   auto base = [](GemmArgs &g) {
     std::memset(&g, 0, sizeof(g));
     g.ksplit = 1;
@@ -702,7 +704,6 @@ cudaError_t triples_run(int o, int v, int n, const double *B, const double *Bov,
     tw.Nt = L.Nt;
     tw.K1p = L.K1p;
     tw.K2p = L.K2p;
-    tw.batch = o;
     tw.pv = v;
     tw.so_batch = v3;
     tw.timeout_ns = 2000000000ull;
@@ -737,9 +738,13 @@ cudaError_t triples_run(int o, int v, int n, const double *B, const double *Bov,
   ta.e_vir = e_vir;
   ta.o = o;
   ta.v = v;
+  // partials of the triples that are not sorted stay zero
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(part, 0, (size_t)o * o * o * triples_energy_blocks(v) * sizeof(double), s);
   for (int i = 0; e == cudaSuccess && i < o; ++i)
-    for (int j = 0; e == cudaSuccess && j < o; ++j) {
+    for (int j = 0; e == cudaSuccess && j <= i; ++j) {
       const int I[3] = {i, j, 0};
+      const int nk = j + 1;  // k = 0 .. j
       for (int q = 0; e == cudaSuccess && q < 6; ++q) {
         const int *p = perm[q];
         // x, y, z of the ordering; the one that is k varies with the batch
@@ -799,9 +804,10 @@ cudaError_t triples_run(int o, int v, int n, const double *B, const double *Bov,
           tw.s2 = g.s2;
           tw.s3 = g.s3;
           tw.acc = g.acc;
-          e = launch_tw_gemm(tw, tw_grid, s);
+          tw.batch = nk;
+          e = launch_tw_gemm(tw, std::min(tw_grid, nk * ((M_rows + 127) / 128)), s);
         } else {
-          e = launch_gemm<T, T, T>(g, o, s);
+          e = launch_gemm<T, T, T>(g, nk, s);
         }
       }
       if (e == cudaSuccess) e = launch_triples_energy<T>(ta, W, i, j, part, s);

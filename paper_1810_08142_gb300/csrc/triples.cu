@@ -7,11 +7,12 @@
 //
 // W_ijk^abc itself (the permutation operator P over the six orderings of the
 // two contractions of Sec. II.A, one two-segment GEMM per ordering) is
-// accumulated by the CUDA-core GEMM of dress.cu, for one (i, j) and every k
-// at a time, into W[k][a][b][c].  These
-// kernels read that W, form V from it and the integrals v_jk^bc = (bj|ck)
-// (stored [j][k][b][c]), and reduce the energy in a fixed order:
-//   triples_energy_kernel   one partial sum per (i, j, k, block of abc)
+// accumulated by the CUDA-core GEMM of dress.cu or the tensor-core GEMM of
+// triples_tc.cu, for one (i, j) with i >= j and every k <= j at a time, into
+// W[k][a][b][c].  These kernels read that W, form V from it and the
+// integrals v_jk^bc = (bj|ck) (stored [j][k][b][c]), and reduce the energy of
+// the sorted triples in a fixed order:
+//   triples_energy_kernel   one partial sum per (sorted i >= j >= k, block of abc)
 //   triples_final_kernel    the partials of all (i, j, k), one block, fixed order
 #include <algorithm>
 #include <type_traits>
@@ -24,20 +25,38 @@ namespace {
 constexpr int kTE = 256;  // threads per energy block
 constexpr int kTC = 8;    // edge of the (a, b, c) cube of one block
 
-// One block per (8x8 (a, b) tile, k), walking the 8-wide blocks of c: for
-// each 8x8x8 cube the three permuted sub-cubes of W the terms need (W^bca,
-// W^cab, W^cba of the cube live in the cubes (b, c, a), (c, a, b) and
-// (c, b, a) of W) are first copied into shared memory with coalesced reads
-// (the last index is contiguous in both), so that no thread gathers W at a
-// stride of v or v^2.  One partial sum per block, reduced in a fixed order.
+// Sorted triples.  W and V are symmetric under a simultaneous permutation of
+// (i, j, k) and (a, b, c), and D is symmetric in each, so the energy of a
+// permuted triple is the sum over abc of the same tensors with permuted
+// virtual indices.  Relabelling the sum, the factor
+//   Z^abc = 4 W^abc + W^bca + W^cab
+// is unchanged (the two 3-cycles are conjugate to each other), and V^cba
+// becomes V with one of the three transpositions of (a, b, c) applied.  Over
+// the six orderings of a triple each transposition comes twice, so
+//   sum over the distinct orderings of (i, j, k) of E_ijk
+//     = m_ijk sum_abc Z^abc (3 V^abc - V^acb - V^bac - V^cba) / (3 D^abc)
+// with m = 2 for i > j > k, 1 for two equal indices, 1/3 for i = j = k.  The
+// W contractions then run only for i >= j >= k (a sixth of the triples).
+//
+// One block per (8x8 (a, b) tile, k <= j), walking the 8-wide blocks of c:
+// for each 8x8x8 cube the five permuted sub-cubes of W the terms need
+// (W^bca, W^cab, W^cba, W^acb, W^bac of the cube live in the cubes (b, c, a),
+// (c, a, b), (c, b, a), (a, c, b) and (b, a, c) of W) are first copied into
+// shared memory with coalesced reads (the last index is contiguous in both),
+// so that no thread gathers W at a stride of v or v^2.  One partial sum per
+// block, reduced in a fixed order.
 template <typename T>
 __global__ void __launch_bounds__(kTE) triples_energy_kernel(const TriplesArgs a, const T *__restrict__ W,
                                                              int i, int j, double *__restrict__ part) {
-  __shared__ T cube[3][kTC][kTC][kTC + 1];
+  constexpr int kCube = kTC * kTC * kTC;
   __shared__ double red[kTE / 32];
-  __shared__ T sti[kTriplesMaxV], stj[kTriplesMaxV], stk[kTriplesMaxV], sev[kTriplesMaxV];
+  // dynamic shared memory: the five cubes, then t1 of i, j, k and e_vir (v each)
+  extern __shared__ __align__(16) unsigned char tri_smem[];
+  T(*cube)[kTC][kTC][kTC + 1] = reinterpret_cast<T(*)[kTC][kTC][kTC + 1]>(tri_smem);
   const int k = blockIdx.y;
   const int v = a.v, o = a.o;
+  T *sti = reinterpret_cast<T *>(tri_smem) + 5 * kTC * kTC * (kTC + 1);
+  T *stj = sti + v, *stk = stj + v, *sev = stk + v;
   const int nc = (v + kTC - 1) / kTC;
   const int A0 = (int)(blockIdx.x / nc) * kTC, B0 = (int)(blockIdx.x % nc) * kTC;
   const long long vv = (long long)v * v, v3 = vv * v;
@@ -55,22 +74,29 @@ __global__ void __launch_bounds__(kTE) triples_energy_kernel(const TriplesArgs a
     sev[x] = (T)a.e_vir[x];
   }
   const T eijk = (T)(a.e_occ[i] + a.e_occ[j] + a.e_occ[k]);
+  // V^xyz = W^xyz + v_jk^yz t_i^x + v_ik^xz t_j^y + v_ij^xy t_k^z
+  auto singles = [&](int x, int y, int z) -> T {
+    return Ijk[(long long)y * v + z] * sti[x] + Iik[(long long)x * v + z] * stj[y] +
+           Iij[(long long)x * v + y] * stk[z];
+  };
   // the thread's sum: FP64 for T = double; for T = float a double-single
   // (hi, lo) kept with TwoSum on the FP32 pipe (about 48 bits), widened once
   double s = 0.0;
   float sh = 0.f, sl = 0.f;
   for (int C0 = 0; C0 < v; C0 += kTC) {
     // cube q holds W[X0 + x][Y0 + y][Z0 + z] at [x][y][z]:
-    //   q = 0: (X, Y, Z) = (B, C, A);  q = 1: (C, A, B);  q = 2: (C, B, A)
-    for (int t = threadIdx.x; t < 3 * kTC * kTC * kTC; t += kTE) {
-      const int q = t / (kTC * kTC * kTC), r = t % (kTC * kTC * kTC);
+    //   q = 0: (X, Y, Z) = (B, C, A);  1: (C, A, B);  2: (C, B, A);  3: (A, C, B);  4: (B, A, C)
+    for (int t = threadIdx.x; t < 5 * kCube; t += kTE) {
+      const int q = t / kCube, r = t % kCube;
       const int x = r / (kTC * kTC), y = (r / kTC) % kTC, z = r % kTC;
-      const int X0 = q == 0 ? B0 : C0, Y0 = q == 0 ? C0 : (q == 1 ? A0 : B0), Z0 = q == 1 ? B0 : A0;
+      const int X0 = (q == 0 || q == 4) ? B0 : (q == 3 ? A0 : C0);
+      const int Y0 = q == 0 ? C0 : (q == 1 || q == 4) ? A0 : (q == 2 ? B0 : C0);
+      const int Z0 = (q == 1 || q == 3) ? B0 : (q == 4 ? C0 : A0);
       const int X = X0 + x, Y = Y0 + y, Z = Z0 + z;
       cube[q][x][y][z] = (X < v && Y < v && Z < v) ? Wk[(long long)X * vv + (long long)Y * v + Z] : T(0);
     }
     __syncthreads();
-    for (int r = threadIdx.x; r < kTC * kTC * kTC; r += kTE) {
+    for (int r = threadIdx.x; r < kCube; r += kTE) {
       const int al = r / (kTC * kTC), bl = (r / kTC) % kTC, cl = r % kTC;
       const int aa = A0 + al, bb = B0 + bl, cc = C0 + cl;
       if (aa >= v || bb >= v || cc >= v) continue;
@@ -78,15 +104,17 @@ __global__ void __launch_bounds__(kTE) triples_energy_kernel(const TriplesArgs a
       const T wbca = cube[0][bl][cl][al];
       const T wcab = cube[1][cl][al][bl];
       const T wcba = cube[2][cl][bl][al];
-      const T vabc = wabc + Ijk[(long long)bb * v + cc] * sti[aa] + Iik[(long long)aa * v + cc] * stj[bb] +
-                     Iij[(long long)aa * v + bb] * stk[cc];
-      const T vcba = wcba + Ijk[(long long)bb * v + aa] * sti[cc] + Iik[(long long)cc * v + aa] * stj[bb] +
-                     Iij[(long long)cc * v + bb] * stk[aa];
+      const T wacb = cube[3][al][cl][bl];
+      const T wbac = cube[4][bl][al][cl];
+      const T vabc = wabc + singles(aa, bb, cc);
+      const T vacb = wacb + singles(aa, cc, bb);
+      const T vbac = wbac + singles(bb, aa, cc);
+      const T vcba = wcba + singles(cc, bb, aa);
       const T D = eijk - sev[aa] - sev[bb] - sev[cc];
-      const T term = (T(4) * wabc + wbca + wcab) * (vabc - vcba) / (T(3) * D);
+      const T term = (T(4) * wabc + wbca + wcab) * (T(3) * vabc - vacb - vbac - vcba) / (T(3) * D);
       if constexpr (std::is_same<T, float>::value) {
-        const float t = __fadd_rn(sh, term), bb = __fsub_rn(t, sh);
-        sl = __fadd_rn(sl, __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(term, bb)));
+        const float t = __fadd_rn(sh, term), bp = __fsub_rn(t, sh);
+        sl = __fadd_rn(sl, __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(term, bp)));
         sh = t;
       } else {
         s += (double)term;
@@ -102,7 +130,9 @@ __global__ void __launch_bounds__(kTE) triples_energy_kernel(const TriplesArgs a
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < kTE / 32; ++w) t += red[w];
-    part[(((long long)i * o + j) * o + k) * gridDim.x + blockIdx.x] = t;
+    // multiplicity of the sorted triple (i >= j >= k)
+    const double m = (i == k) ? 1.0 / 3.0 : (i == j || j == k) ? 1.0 : 2.0;
+    part[(((long long)i * o + j) * o + k) * gridDim.x + blockIdx.x] = m * t;
   }
 }
 
@@ -145,6 +175,12 @@ __global__ void __launch_bounds__(1024) triples_final_kernel(const double *__res
   if (threadIdx.x == 0) *E = (status && *status) ? __longlong_as_double(0x7ff8000000000000LL) : red[0];
 }
 
+// dynamic shared memory of the energy kernel for v virtual orbitals
+template <typename T>
+size_t triples_energy_smem(int v) {
+  return (5 * kTC * kTC * (kTC + 1) + 4 * (size_t)v) * sizeof(T);
+}
+
 }  // namespace
 
 int triples_energy_blocks(int v) {
@@ -155,8 +191,15 @@ int triples_energy_blocks(int v) {
 template <typename T>
 cudaError_t launch_triples_energy(const TriplesArgs &a, const T *W, int i, int j, double *part,
                                   cudaStream_t s) {
-  const dim3 grid((unsigned)triples_energy_blocks(a.v), (unsigned)a.o);
-  triples_energy_kernel<T><<<grid, kTE, 0, s>>>(a, W, i, j, part);
+  // k = 0 .. j of the sorted triples i >= j >= k
+  const dim3 grid((unsigned)triples_energy_blocks(a.v), (unsigned)(j + 1));
+  const size_t smem = triples_energy_smem<T>(a.v);
+  if (smem > 48 * 1024) {  // FP64 at large v only; set on the current device
+    const cudaError_t e =
+        cudaFuncSetAttribute(triples_energy_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  triples_energy_kernel<T><<<grid, kTE, smem, s>>>(a, W, i, j, part);
   return cudaGetLastError();
 }
 template cudaError_t launch_triples_energy<double>(const TriplesArgs &, const double *, int, int, double *,

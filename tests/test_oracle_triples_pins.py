@@ -142,3 +142,54 @@ def test_energy_scaling_and_vanishing_doubles():
     assert abs(E3 - 9.0 * E1) <= 1e-12 * abs(E3)
     t1 = rng.standard_normal((o, v))
     assert oracle.triples(B, B_ov, B_oo, t1, np.zeros_like(t2), e_occ, e_vir) == 0.0
+
+
+def test_sorted_triple_identity():
+    """The identity the GPU evaluation rests on: for a sorted triple
+    i >= j >= k, the printed per-(i,j,k) sums over its distinct orderings
+    equal m * sum_abc Z^abc (3 V^abc - V^acb - V^bac - V^cba) / (3 D^abc)
+    with Z^abc = 4 W^abc + W^bca + W^cab, formed from W and V of the sorted
+    triple alone; m = 2, 1 or 1/3 for three, two or one distinct indices.
+    Also: the per-ordering sums are not all equal (so the weight alone would
+    not do), and summing the right-hand side over the sorted triples gives
+    the oracle's E(T).  Brute force over the oracle's own W and V."""
+    import synthetic
+    o, v, n = 4, 6, 14
+    x = synthetic.make_inputs(o, v, n, 7)
+    args = (x.B, x.B_ov, x.B_oo, x.t1, x.t2)
+
+    def D(i, j, k):
+        return (x.e_occ[i] + x.e_occ[j] + x.e_occ[k])[()] - (
+            x.e_vir[:, None, None] + x.e_vir[None, :, None] + x.e_vir[None, None, :])
+
+    def printed(i, j, k):
+        W, V = oracle.triples_wv(*args, i, j, k)
+        Z = 4.0 * W + W.transpose(1, 2, 0) + W.transpose(2, 0, 1)
+        return float(np.sum(Z * (V - V.transpose(2, 1, 0)) / (3.0 * D(i, j, k))))
+
+    def sorted_form(i, j, k):
+        W, V = oracle.triples_wv(*args, i, j, k)
+        Z = 4.0 * W + W.transpose(1, 2, 0) + W.transpose(2, 0, 1)
+        Y = 3.0 * V - V.transpose(0, 2, 1) - V.transpose(1, 0, 2) - V.transpose(2, 1, 0)
+        m = 1.0 / 3.0 if i == k else (1.0 if (i == j or j == k) else 2.0)
+        Dijk = D(i, j, k)
+        # scale of the rounding: the terms' magnitudes before V's cancellation
+        Ya = 3.0 * np.abs(V) + np.abs(V.transpose(0, 2, 1)) + np.abs(V.transpose(1, 0, 2)) + \
+            np.abs(V.transpose(2, 1, 0))
+        return (m * float(np.sum(Z * Y / (3.0 * Dijk))),
+                m * float(np.sum(np.abs(Z) * Ya / (3.0 * np.abs(Dijk)))))
+
+    total = 0.0
+    for i in range(o):
+        for j in range(i + 1):
+            for k in range(j + 1):
+                perms = set(itertools.permutations((i, j, k)))
+                lhs = sum(printed(*p) for p in perms)
+                rhs, scale = sorted_form(i, j, k)
+                # (i = i = k: both sides vanish; rounding is measured on the terms' scale)
+                assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), scale), (i, j, k, lhs, rhs)
+                total += rhs
+    vals = sorted(printed(*p) for p in itertools.permutations((3, 1, 0)))
+    assert max(vals) - min(vals) > 1e-3 * abs(vals[0])
+    E = oracle.triples(*args, x.e_occ, x.e_vir)
+    assert abs(total - E) <= 1e-12 * abs(E)
