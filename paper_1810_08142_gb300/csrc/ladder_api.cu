@@ -521,7 +521,7 @@ ladder_status dress_correct(const ladder_plan_s *pl, const double *Bov, const do
 // ---- perturbative triples (Sec. II.A): workspace and launch sequence
 struct TriplesLayout {
   size_t status = 0;  // word of the tensor-core kernel's bounded waits
-  size_t ovvv = 0, ovvvT = 0, Q = 0, oovv = 0, t2c = 0, t2T = 0, W = 0, part = 0, total = 0;
+  size_t ovvv = 0, ovvvT = 0, Q = 0, oovv = 0, t2c = 0, t2T = 0, W = 0, W2 = 0, part = 0, total = 0;
   // tensor-core W contractions: BF16 slices of the GEMM operands
   size_t tA1 = 0, tA1T = 0, tB1 = 0, tA2 = 0, tA2T = 0, tB2 = 0;
   int Nt = 0, K1p = 0, K2p = 0;
@@ -547,6 +547,8 @@ TriplesLayout triples_layout(int o, int v, bool fp32, bool tc = false) {
   L.t2T = off;
   off = align_up(off + ov * ov * t);
   L.W = off;
+  off = align_up(off + o * v3 * t);
+  L.W2 = off;  // the second stream's W
   off = align_up(off + o * v3 * t);
   L.part = off;
   off = align_up(off + (size_t)o * o * o * triples_energy_blocks(v) * sizeof(double));
@@ -585,7 +587,7 @@ cudaError_t triples_run(int o, int v, int n, const double *B, const double *Bov,
   T *ovvvT = reinterpret_cast<T *>(ws + L.ovvvT);
   T *Q = reinterpret_cast<T *>(ws + L.Q);
   T *oovv = reinterpret_cast<T *>(ws + L.oovv);
-  T *W = reinterpret_cast<T *>(ws + L.W);
+  T *Wbuf[2] = {reinterpret_cast<T *>(ws + L.W), reinterpret_cast<T *>(ws + L.W2)};
   double *part = reinterpret_cast<double *>(ws + L.part);
   const long long ov = (long long)o * v, vv = (long long)v * v, v3 = vv * v;
   const int M_rows = (int)vv;  // rows (alpha, beta) of every W GEMM
@@ -697,7 +699,6 @@ cudaError_t triples_run(int o, int v, int n, const double *B, const double *Bov,
     if (e == cudaSuccess) e = launch_tw_slice(f_t2T, (long long)o * vv, 1, vv, o, M, M, o, L.K2p, bf(L.tA2T), s);
     // B2[(z, y)][gamma][l] = -(gamma z | y l) = Q[z][y][gamma][l]
     if (e == cudaSuccess) e = launch_tw_slice(f_Q, ov, o, 1, o * o, v, L.Nt, o, L.K2p, bf(L.tB2), s);
-    tw.W = reinterpret_cast<float *>(W);
     tw.status = tstatus;
     tw.M = M;
     tw.N = v;
@@ -741,10 +742,23 @@ cudaError_t triples_run(int o, int v, int n, const double *B, const double *Bov,
   // partials of the triples that are not sorted stay zero
   if (e == cudaSuccess)
     e = cudaMemsetAsync(part, 0, (size_t)o * o * o * triples_energy_blocks(v) * sizeof(double), s);
+  // the (i, j) pairs alternate between the caller's stream and a second one,
+  // each with its own W: the small k-batches of one pair leave SMs free for
+  // the other's launches
+  cudaStream_t st[2] = {s, nullptr};
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st[1], cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st[1], ev[0], 0);
+  int npair = 0;
   for (int i = 0; e == cudaSuccess && i < o; ++i)
-    for (int j = 0; e == cudaSuccess && j <= i; ++j) {
+    for (int j = 0; e == cudaSuccess && j <= i; ++j, ++npair) {
       const int I[3] = {i, j, 0};
       const int nk = j + 1;  // k = 0 .. j
+      cudaStream_t sq = st[npair & 1];
+      T *W = Wbuf[npair & 1];
       for (int q = 0; e == cudaSuccess && q < 6; ++q) {
         const int *p = perm[q];
         // x, y, z of the ordering; the one that is k varies with the batch
@@ -805,13 +819,22 @@ cudaError_t triples_run(int o, int v, int n, const double *B, const double *Bov,
           tw.s3 = g.s3;
           tw.acc = g.acc;
           tw.batch = nk;
-          e = launch_tw_gemm(tw, std::min(tw_grid, nk * ((M_rows + 127) / 128)), s);
+          tw.W = reinterpret_cast<float *>(W);
+          e = launch_tw_gemm(tw, std::min(tw_grid, nk * ((M_rows + 127) / 128)), sq);
         } else {
-          e = launch_gemm<T, T, T>(g, nk, s);
+          e = launch_gemm<T, T, T>(g, nk, sq);
         }
       }
-      if (e == cudaSuccess) e = launch_triples_energy<T>(ta, W, i, j, part, s);
+      if (e == cudaSuccess) e = launch_triples_energy<T>(ta, W, i, j, part, sq);
     }
+  // join the second stream back into the caller's
+  if (st[1]) {
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], st[1]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1], 0);
+    cudaStreamDestroy(st[1]);
+  }
+  for (cudaEvent_t x : ev)
+    if (x) cudaEventDestroy(x);
   // E = NaN if a bounded wait of the tensor-core kernel ran out
   if (e == cudaSuccess)
     e = launch_triples_final(part, (long long)o * o * o * triples_energy_blocks(v), E, s, tc ? tstatus : nullptr);
