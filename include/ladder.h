@@ -277,9 +277,13 @@ ladder_status ladder_pair_combine(int o, int v, double alpha, double beta, const
                                   double *Y, void *stream);
 
 /* Host-buffer convenience path: copies B and tau from host memory (pinned
- * memory recommended), runs ladder_apply and ladder_energy-free apply, and
+ * memory recommended), runs the ladder as ladder_apply does (no energy), and
  * copies R back to R_host.  Needs device buffers d_B, d_tau, d_R of the
- * sizes above, supplied by the caller.  Synchronises `stream` before return. */
+ * sizes above, supplied by the caller (d_R distinct from d_B and d_tau).  In
+ * the error-free mode tau's upload and preparation run on a side stream of
+ * the plan, overlapping B's upload and the first pass; the side stream is
+ * joined into `stream` before R is copied back.  Synchronises `stream`
+ * before return; LADDER_EWORKSPACE without a workspace. */
 ladder_status ladder_apply_host(ladder_plan_t plan, const double *B_host, const double *tau_host,
                                 double *R_host, double *d_B, double *d_tau, double *d_R,
                                 void *stream);

@@ -131,6 +131,10 @@ struct ladder_plan_s {
   size_t off_mols1 = 0, off_mols2 = 0, off_items1 = 0, off_items2 = 0, off_tcs2 = 0;
   size_t off_oz1 = 0, off_oz2 = 0;  // error-free batch: OzArgs tables of the two passes
   cudaStream_t cap_stream = nullptr;
+  // ladder_apply_host: a side stream for the tau upload and its preparation,
+  // and the events that fork it from and join it into the caller's stream
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t side_ev[2] = {nullptr, nullptr};
   cudaGraphExec_t gexec = nullptr;
   std::vector<const void *> gkey;  // pointers the graph was captured with
   bool timing = false;
@@ -759,6 +763,7 @@ cudaError_t triples_run(int o, int v, int n, const double *B, const double *Bov,
       const int nk = j + 1;  // k = 0 .. j
       cudaStream_t sq = st[npair & 1];
       T *W = Wbuf[npair & 1];
+      TwArgs twq[6];
       for (int q = 0; e == cudaSuccess && q < 6; ++q) {
         const int *p = perm[q];
         // x, y, z of the ordering; the one that is k varies with the batch
@@ -820,9 +825,34 @@ cudaError_t triples_run(int o, int v, int n, const double *B, const double *Bov,
           tw.acc = g.acc;
           tw.batch = nk;
           tw.W = reinterpret_cast<float *>(W);
-          e = launch_tw_gemm(tw, std::min(tw_grid, nk * ((M_rows + 127) / 128)), sq);
+          tw.nord = 1;
+          twq[q] = tw;
         } else {
           e = launch_gemm<T, T, T>(g, nk, sq);
+        }
+      }
+      if (tc) {
+        // orderings 1 and 2 write W through the same strides (rows (a, c),
+        // columns b), and so do 3 and 4 (rows (b, c), columns a): each pair
+        // runs as one launch whose second ordering adds its K segments into
+        // the same accumulators, so W is read and written four times, not six
+        auto same_out = [&](int x, int y) {
+          return twq[x].s1 == twq[y].s1 && twq[x].s2 == twq[y].s2 && twq[x].s3 == twq[y].s3;
+        };
+        for (int q = 0; e == cudaSuccess && q < 6; ++q) {
+          TwArgs a = twq[q];
+          if ((q == 1 || q == 3) && same_out(q, q + 1)) {
+            const TwArgs &b2 = twq[q + 1];
+            a.nord = 2;
+            a.tmA1b = b2.tmA1;
+            a.tmA2b = b2.tmA2;
+            a.a1b_fix = b2.a1_fix;
+            a.a1b_mul = b2.a1_mul;
+            a.b1b_fix = b2.b1_fix;
+            a.b1b_mul = b2.b1_mul;
+            ++q;
+          }
+          e = launch_tw_gemm(a, std::min(tw_grid, nk * ((M_rows + 127) / 128)), sq);
         }
       }
       if (e == cudaSuccess) e = launch_triples_energy<T>(ta, W, i, j, part, sq);
@@ -1372,12 +1402,14 @@ static ladder_status apply_tc(ladder_plan_t pl, const double *B, const double *t
 // slices, tau+- slices per GEMM2 chunk), the storing pass, the GEMM2 pass and
 // the unpack of the two-pass form.
 // Error-free preparation of one molecule: row scales and fixed-point slices
-// of B, and the tau+- slices of every GEMM2 chunk.
-static void oz_prep(const ladder_plan_s *pl, const double *B, const double *tau, int *status,
-                    cudaStream_t s) {
+// of B (oz_prep_B, which pass 1 needs), and the tau+- slices of every GEMM2
+// chunk (oz_prep_tau, which only pass 2 needs).
+static void oz_prep_B(const ladder_plan_s *pl, const double *B, int *status, cudaStream_t s) {
   float *rsB = ws_at<float>(pl, pl->lay.ozRs);
   launch_oz_rowscale(pl->N, pl->v, pl->vp, B, rsB, status, s);
   launch_oz_split_B(pl->N, pl->v, pl->vp, pl->Np, pl->S, B, rsB, ws_at<__nv_bfloat16>(pl, pl->lay.Bt), s);
+}
+static void oz_prep_tau(const ladder_plan_s *pl, const double *tau, int *status, cudaStream_t s) {
   OzPackArgs pk;
   std::memset(&pk, 0, sizeof(pk));
   pk.tau = tau;
@@ -1391,6 +1423,10 @@ static void oz_prep(const ladder_plan_s *pl, const double *B, const double *tau,
   pk.nchunks = (int)pl->chunks_v.size();
   for (int c = 0; c < pk.nchunks; ++c) pk.chunks[c] = pl->chunks_v[c];
   launch_oz_pack_t2(pk, s);
+}
+static void oz_prep(const ladder_plan_s *pl, const double *B, const double *tau, int *status, cudaStream_t s) {
+  oz_prep_B(pl, B, status, s);
+  oz_prep_tau(pl, tau, status, s);
 }
 
 // Arguments of the error-free passes over all of a plan's tiles: pass 1
@@ -1439,11 +1475,16 @@ static OzLaunch oz_launch(const OzArgs &a) {
   return L;
 }
 
+// side: when given, tau's preparation was enqueued on another stream and
+// side_done marks its end; pass 2 waits for it (pass 1 does not need tau).
 static ladder_status apply_oz(ladder_plan_t pl, const double *B, const double *tau, double *R,
-                              cudaStream_t s) {
+                              cudaStream_t s, cudaEvent_t side_done = nullptr) {
   mark(pl, 0, s);
   int *status = ws_at<int>(pl, pl->lay.status);
-  oz_prep(pl, B, tau, status, s);
+  if (side_done)
+    oz_prep_B(pl, B, status, s);
+  else
+    oz_prep(pl, B, tau, status, s);
   ladder_status st = cuda_status(cudaGetLastError());
   if (st != LADDER_OK) return st;
   OzArgs a1 = oz_args(pl, 1, status), a2 = oz_args(pl, 2, status);
@@ -1462,6 +1503,7 @@ static ladder_status apply_oz(ladder_plan_t pl, const double *B, const double *t
     a2.nitems = cnt * a2.nchunks * pl->ksplit;
     st = cuda_status(launch_oz_vstore(oz_launch(a1), pl->S, s));
     if (one) mark(pl, 4, s);
+    if (st == LADDER_OK && side_done && r0 == 0) st = cuda_status(cudaStreamWaitEvent(s, side_done, 0));
     if (st == LADDER_OK) st = cuda_status(launch_oz_gemm2(oz_launch(a2), pl->S, s));
     if (one) mark(pl, 2, s);
     if (st == LADDER_OK) {
@@ -1731,11 +1773,35 @@ ladder_status ladder_apply_host(ladder_plan_t pl, const double *B_host, const do
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t nB = (size_t)pl->N * pl->v * pl->v * sizeof(double);
   const size_t nT = (size_t)pl->o * pl->o * pl->v * pl->v * sizeof(double);
-  if (!dev_ptr_ok(d_B) || !dev_ptr_ok(d_tau) || !dev_ptr_ok(d_R)) return LADDER_EINVAL;
-  if (cudaMemcpyAsync(d_B, B_host, nB, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(d_tau, tau_host, nT, cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return cuda_status(cudaErrorUnknown);
-  ladder_status st = ladder_apply(pl, d_B, d_tau, d_R, stream);
+  if (!dev_ptr_ok(d_B) || !dev_ptr_ok(d_tau) || !dev_ptr_ok(d_R) || d_R == d_B || d_R == d_tau)
+    return LADDER_EINVAL;
+  if (!pl->ws) return LADDER_EWORKSPACE;
+  ladder_status st = LADDER_OK;
+  if (pl->mode == LADDER_OZAKI) {
+    // tau's upload and preparation run on a side stream, overlapping B's
+    // upload, B's preparation and pass 1; pass 2 waits for them
+    if (!pl->side_stream &&
+        (cudaStreamCreateWithFlags(&pl->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&pl->side_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&pl->side_ev[1], cudaEventDisableTiming) != cudaSuccess))
+      return cuda_status(cudaErrorUnknown);
+    cudaStream_t t = pl->side_stream;
+    if (cudaEventRecord(pl->side_ev[0], s) != cudaSuccess || cudaStreamWaitEvent(t, pl->side_ev[0], 0) != cudaSuccess ||
+        cudaMemcpyAsync(d_tau, tau_host, nT, cudaMemcpyHostToDevice, t) != cudaSuccess)
+      return cuda_status(cudaErrorUnknown);
+    oz_prep_tau(pl, d_tau, ws_at<int>(pl, pl->lay.status), t);
+    if (cudaEventRecord(pl->side_ev[1], t) != cudaSuccess ||
+        cudaMemcpyAsync(d_B, B_host, nB, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return cuda_status(cudaErrorUnknown);
+    st = apply_oz(pl, d_B, d_tau, d_R, s, pl->side_ev[1]);
+    // the side stream's work is joined before R leaves the device
+    if (st == LADDER_OK) st = cuda_status(cudaStreamWaitEvent(s, pl->side_ev[1], 0));
+  } else {
+    if (cudaMemcpyAsync(d_B, B_host, nB, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d_tau, tau_host, nT, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return cuda_status(cudaErrorUnknown);
+    st = ladder_apply(pl, d_B, d_tau, d_R, stream);
+  }
   if (st != LADDER_OK) return st;
   if (cudaMemcpyAsync(R_host, d_R, nT, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return cuda_status(cudaErrorUnknown);
@@ -2166,6 +2232,9 @@ void ladder_destroy(ladder_plan_t pl) {
   for (auto *sp : pl->subs) ladder_destroy(sp);
   if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
   if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+  if (pl->side_stream) cudaStreamDestroy(pl->side_stream);
+  for (auto &e : pl->side_ev)
+    if (e) cudaEventDestroy(e);
   delete pl;
 }
 
