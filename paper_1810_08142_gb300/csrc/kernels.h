@@ -91,10 +91,15 @@ cudaError_t launch_triples_final(const double *part, long long n, double *E, cud
 // l; the outer index g of each is fix + mul * batch.
 struct TwArgs {
   CUtensorMap tmA1, tmB1, tmA2, tmB2;
+  // nord = 2: a second ordering of P with the same output strides adds its
+  // two K segments into the same accumulators (A maps tmA1b / tmA2b, outer
+  // indices a1b / b1b for both of its segments)
+  CUtensorMap tmA1b, tmA2b;
   float *W;
   int *status;
   int M, N, Nt, K1p, K2p, batch;
   int a1_fix, a1_mul, b1_fix, b1_mul, a2_fix, a2_mul, b2_fix, b2_mul;
+  int nord, a1b_fix, a1b_mul, b1b_fix, b1b_mul;
   int pv, acc;
   long long s1, s2, s3, so_batch;
   unsigned long long timeout_ns;

@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(kThreads, 1) tw_gemm_kernel(const __grid_const
   const int mtiles = (A.M + 127) / 128;
   const int nunits = A.batch * mtiles;
   const int nk1 = A.K1p / kK1, nk2 = A.K2p / kK2;
+  const int nks = A.nord * (nk1 + nk2);  // K steps of one unit over its orderings
 
   if (warp == 0) {
     // ================================================================ TMA producer
@@ -114,11 +115,14 @@ __global__ void __launch_bounds__(kThreads, 1) tw_gemm_kernel(const __grid_const
       bool ok = true;
       for (int u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
         const int b = u / mtiles, m0 = (u % mtiles) * 128;
-        const int a1 = outer(A.a1_fix, A.a1_mul, b), b1 = outer(A.b1_fix, A.b1_mul, b);
-        const int a2 = outer(A.a2_fix, A.a2_mul, b), b2 = outer(A.b2_fix, A.b2_mul, b);
-        for (int ks = 0; ok && ks < nk1 + nk2; ++ks) {
+        for (int kq = 0; ok && kq < nks; ++kq) {
           if (!(ok = mbar_wait(bars.empty(stage), phase ^ 1u, wd, kSiteTmaEmpty))) break;
           const uint32_t dst = ring + (uint32_t)stage * kStage;
+          const bool o2 = kq >= nk1 + nk2;  // the second ordering's segments
+          const int ks = o2 ? kq - (nk1 + nk2) : kq;
+          const int a1 = o2 ? outer(A.a1b_fix, A.a1b_mul, b) : outer(A.a1_fix, A.a1_mul, b);
+          const int b1 = o2 ? outer(A.b1b_fix, A.b1b_mul, b) : outer(A.b1_fix, A.b1_mul, b);
+          const int a2 = o2 ? a1 : outer(A.a2_fix, A.a2_mul, b), b2 = o2 ? b1 : outer(A.b2_fix, A.b2_mul, b);
           const bool seg1 = ks < nk1;
           const uint32_t bytes = seg1 ? (uint32_t)kS * (128u + A.Nt) * kK1 * 2u
                                       : (uint32_t)kS * (128u + A.Nt) * kK2 * 2u;
@@ -126,11 +130,11 @@ __global__ void __launch_bounds__(kThreads, 1) tw_gemm_kernel(const __grid_const
           armed |= 1u << stage;
           armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
           if (seg1) {
-            tma_load_4d(dst, &A.tmA1, bars.full(stage), ks * kK1, m0, a1, 0);
+            tma_load_4d(dst, o2 ? &A.tmA1b : &A.tmA1, bars.full(stage), ks * kK1, m0, a1, 0);
             tma_load_4d(dst + kStageA, &A.tmB1, bars.full(stage), ks * kK1, 0, b1, 0);
           } else {
             const int k2 = ks - nk1;
-            tma_load_4d(dst, &A.tmA2, bars.full(stage), k2 * kK2, m0, a2, 0);
+            tma_load_4d(dst, o2 ? &A.tmA2b : &A.tmA2, bars.full(stage), k2 * kK2, m0, a2, 0);
             tma_load_4d(dst + kStageA, &A.tmB2, bars.full(stage), k2 * kK2, 0, b2, 0);
           }
           if (++stage == stages) {
@@ -158,11 +162,11 @@ __global__ void __launch_bounds__(kThreads, 1) tw_gemm_kernel(const __grid_const
         if (!(ok = mbar_wait(bars.cfree(buf), ((g / nbuf) & 1u) ^ 1u, wd, kSiteXYFree))) break;
         tc_fence_after();
         const uint32_t d0 = tmem + buf * 256u;  // acc0 [0, Nt), acc1 [Nt, 2 Nt) of the buffer
-        for (int ks = 0; ok && ks < nk1 + nk2; ++ks) {
+        for (int kq = 0; ok && kq < nks; ++kq) {
           if (!(ok = mbar_wait(bars.full(stage), phase, wd, kSiteTmaFull))) break;
           tc_fence_after();
           const uint32_t st = ring + (uint32_t)stage * kStage;
-          const bool seg1 = ks < nk1;
+          const bool seg1 = (kq % (nk1 + nk2)) < nk1;
           const int kk_n = seg1 ? kK1 / 16 : 1;
           const uint32_t rowb = seg1 ? kK1 * 2u : kK2 * 2u;  // bytes per operand row
           const uint32_t hi = seg1 ? hi64 : hi32;
@@ -171,7 +175,7 @@ __global__ void __launch_bounds__(kThreads, 1) tw_gemm_kernel(const __grid_const
             for (int q = 0; q < 6; ++q) {
               const uint64_t ad = desc64(st + kPa(q) * 128u * rowb + kk * 32, hi);
               const uint64_t bd = desc64(st + kStageA + kPb(q) * A.Nt * rowb + kk * 32, hi);
-              const bool first = ks == 0 && kk == 0 && q <= 1;
+              const bool first = kq == 0 && kk == 0 && q <= 1;
               mma_bf16(d0 + (q > 0 ? (uint32_t)A.Nt : 0u), ad, bd, id, first ? 0u : 1u);
             }
           mma_commit(bars.empty(stage));
