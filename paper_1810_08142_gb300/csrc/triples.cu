@@ -23,6 +23,7 @@ namespace ladder {
 namespace {
 
 constexpr int kTE = 256;  // threads per energy block
+constexpr int kTriplesMaxBlocks = 1024;  // energy blocks per k (each walks several orbits)
 constexpr int kTC = 8;    // edge of the (a, b, c) cube of one block
 
 // Sorted triples.  W and V are symmetric under a simultaneous permutation of
@@ -38,27 +39,32 @@ constexpr int kTC = 8;    // edge of the (a, b, c) cube of one block
 // with m = 2 for i > j > k, 1 for two equal indices, 1/3 for i = j = k.  The
 // W contractions then run only for i >= j >= k (a sixth of the triples).
 //
-// One block per (8x8 (a, b) tile, k <= j), walking the 8-wide blocks of c:
-// for each 8x8x8 cube the five permuted sub-cubes of W the terms need
-// (W^bca, W^cab, W^cba, W^acb, W^bac of the cube live in the cubes (b, c, a),
-// (c, a, b), (c, b, a), (a, c, b) and (b, a, c) of W) are first copied into
-// shared memory with coalesced reads (the last index is contiguous in both),
-// so that no thread gathers W at a stride of v or v^2.  One partial sum per
-// block, reduced in a fixed order.
+// Blocks over (orbits of 8-wide index blocks, k <= j), each block walking
+// orbits blockIdx.x, blockIdx.x + gridDim.x, ... (at most kTriplesMaxBlocks
+// blocks per k, so the partials stay bounded).  An orbit is a
+// sorted block triple A0 <= B0 <= C0 with its distinct orderings (6, 3 or
+// 1): the elements (a, b, c) of every ordering's 8x8x8 cube need W only at
+// the six index permutations of (a, b, c), and those lie in the cubes of the
+// same orbit.  The block therefore copies each of the orbit's cubes of W[k]
+// into shared memory once (coalesced rows of 8) and reads every permuted W
+// from there, so W is read from memory once per k instead of six times.
+// One partial sum per block, reduced in a fixed order.
 template <typename T>
 __global__ void __launch_bounds__(kTE) triples_energy_kernel(const TriplesArgs a, const T *__restrict__ W,
                                                              int i, int j, double *__restrict__ part) {
   constexpr int kCube = kTC * kTC * kTC;
   __shared__ double red[kTE / 32];
-  // dynamic shared memory: the five cubes, then t1 of i, j, k and e_vir (v each)
+  __shared__ int pos[6][3];     // the orbit's distinct block orderings (X0, Y0, Z0)
+  __shared__ int cid[6][6];     // cube index of permutation q of position p
+  __shared__ int npos;
+  // dynamic shared memory: six cubes, then t1 of i, j, k and e_vir (v each)
   extern __shared__ __align__(16) unsigned char tri_smem[];
   T(*cube)[kTC][kTC][kTC + 1] = reinterpret_cast<T(*)[kTC][kTC][kTC + 1]>(tri_smem);
   const int k = blockIdx.y;
   const int v = a.v, o = a.o;
-  T *sti = reinterpret_cast<T *>(tri_smem) + 5 * kTC * kTC * (kTC + 1);
-  T *stj = sti + v, *stk = stj + v, *sev = stk + v;
   const int nc = (v + kTC - 1) / kTC;
-  const int A0 = (int)(blockIdx.x / nc) * kTC, B0 = (int)(blockIdx.x % nc) * kTC;
+  T *sti = reinterpret_cast<T *>(tri_smem) + 6 * kTC * kTC * (kTC + 1);
+  T *stj = sti + v, *stk = stj + v, *sev = stk + v;
   const long long vv = (long long)v * v, v3 = vv * v;
   const T *Wk = W + (long long)k * v3;
   const T *oovv = static_cast<const T *>(a.oovv);
@@ -76,52 +82,98 @@ __global__ void __launch_bounds__(kTE) triples_energy_kernel(const TriplesArgs a
   const T eijk = (T)(a.e_occ[i] + a.e_occ[j] + a.e_occ[k]);
   // V^xyz = W^xyz + v_jk^yz t_i^x + v_ik^xz t_j^y + v_ij^xy t_k^z
   auto singles = [&](int x, int y, int z) -> T {
-    return Ijk[(long long)y * v + z] * sti[x] + Iik[(long long)x * v + z] * stj[y] +
-           Iij[(long long)x * v + y] * stk[z];
+    return Ijk[y * v + z] * sti[x] + Iik[x * v + z] * stj[y] + Iij[x * v + y] * stk[z];
   };
   // the thread's sum: FP64 for T = double; for T = float a double-single
   // (hi, lo) kept with TwoSum on the FP32 pipe (about 48 bits), widened once
   double s = 0.0;
   float sh = 0.f, sl = 0.f;
-  for (int C0 = 0; C0 < v; C0 += kTC) {
-    // cube q holds W[X0 + x][Y0 + y][Z0 + z] at [x][y][z]:
-    //   q = 0: (X, Y, Z) = (B, C, A);  1: (C, A, B);  2: (C, B, A);  3: (A, C, B);  4: (B, A, C)
-    for (int t = threadIdx.x; t < 5 * kCube; t += kTE) {
-      const int q = t / kCube, r = t % kCube;
-      const int x = r / (kTC * kTC), y = (r / kTC) % kTC, z = r % kTC;
-      const int X0 = (q == 0 || q == 4) ? B0 : (q == 3 ? A0 : C0);
-      const int Y0 = q == 0 ? C0 : (q == 1 || q == 4) ? A0 : (q == 2 ? B0 : C0);
-      const int Z0 = (q == 1 || q == 3) ? B0 : (q == 4 ? C0 : A0);
-      const int X = X0 + x, Y = Y0 + y, Z = Z0 + z;
-      cube[q][x][y][z] = (X < v && Y < v && Z < v) ? Wk[(long long)X * vv + (long long)Y * v + Z] : T(0);
-    }
-    __syncthreads();
-    for (int r = threadIdx.x; r < kCube; r += kTE) {
-      const int al = r / (kTC * kTC), bl = (r / kTC) % kTC, cl = r % kTC;
-      const int aa = A0 + al, bb = B0 + bl, cc = C0 + cl;
-      if (aa >= v || bb >= v || cc >= v) continue;
-      const T wabc = Wk[(long long)aa * vv + (long long)bb * v + cc];
-      const T wbca = cube[0][bl][cl][al];
-      const T wcab = cube[1][cl][al][bl];
-      const T wcba = cube[2][cl][bl][al];
-      const T wacb = cube[3][al][cl][bl];
-      const T wbac = cube[4][bl][al][cl];
-      const T vabc = wabc + singles(aa, bb, cc);
-      const T vacb = wacb + singles(aa, cc, bb);
-      const T vbac = wbac + singles(bb, aa, cc);
-      const T vcba = wcba + singles(cc, bb, aa);
-      const T D = eijk - sev[aa] - sev[bb] - sev[cc];
-      const T term = (T(4) * wabc + wbca + wcab) * (T(3) * vabc - vacb - vbac - vcba) / (T(3) * D);
-      if constexpr (std::is_same<T, float>::value) {
-        const float t = __fadd_rn(sh, term), bp = __fsub_rn(t, sh);
-        sl = __fadd_rn(sl, __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(term, bp)));
-        sh = t;
-      } else {
-        s += (double)term;
+  const int norb = nc * (nc + 1) * (nc + 2) / 6;
+  for (int orb = blockIdx.x; orb < norb; orb += gridDim.x) {
+    __syncthreads();  // the previous orbit's cubes and tables are no longer read
+    if (threadIdx.x == 0) {
+      // orbit -> sorted block triple (A, B, C), A <= B <= C
+      int rem = orb, A = 0, B = 0, C = 0;
+      for (A = 0; A < nc; ++A) {
+        const int m = nc - A, cnt = m * (m + 1) / 2;  // pairs B <= C in [A, nc)
+        if (rem < cnt) break;
+        rem -= cnt;
+      }
+      for (B = A; B < nc; ++B) {
+        const int cnt = nc - B;
+        if (rem < cnt) break;
+        rem -= cnt;
+      }
+      C = B + rem;
+      const int t3[3] = {A, B, C};
+      static constexpr int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+      int n = 0;
+      for (int q = 0; q < 6; ++q) {
+        const int x = t3[P[q][0]], y = t3[P[q][1]], z = t3[P[q][2]];
+        bool seen = false;
+        for (int r = 0; r < n; ++r) seen |= pos[r][0] == x && pos[r][1] == y && pos[r][2] == z;
+        if (!seen) {
+          pos[n][0] = x;
+          pos[n][1] = y;
+          pos[n][2] = z;
+          ++n;
+        }
+      }
+      npos = n;
+      // for position (X, Y, Z): the cubes (X,Y,Z), (Y,Z,X), (Z,X,Y), (X,Z,Y), (Y,X,Z), (Z,Y,X)
+      for (int p = 0; p < n; ++p) {
+        const int X = pos[p][0], Y = pos[p][1], Z = pos[p][2];
+        const int want[6][3] = {{X, Y, Z}, {Y, Z, X}, {Z, X, Y}, {X, Z, Y}, {Y, X, Z}, {Z, Y, X}};
+        for (int q = 0; q < 6; ++q)
+          for (int r = 0; r < n; ++r)
+            if (pos[r][0] == want[q][0] && pos[r][1] == want[q][1] && pos[r][2] == want[q][2]) cid[p][q] = r;
       }
     }
     __syncthreads();
-  }
+    const int n = npos;
+    // the orbit's cubes: thread t copies elements t and t + 256 of each
+    for (int p = 0; p < n; ++p) {
+      const int X0 = pos[p][0] * kTC, Y0 = pos[p][1] * kTC, Z0 = pos[p][2] * kTC;
+  #pragma unroll
+      for (int h = 0; h < kCube / kTE; ++h) {
+        const int e = threadIdx.x + h * kTE;
+        const int x = e / (kTC * kTC), y = (e / kTC) % kTC, z = e % kTC;
+        const int X = X0 + x, Y = Y0 + y, Z = Z0 + z;
+        cube[p][x][y][z] = (X < v && Y < v && Z < v) ? Wk[(long long)X * vv + (long long)Y * v + Z] : T(0);
+      }
+    }
+    __syncthreads();
+    for (int p = 0; p < n; ++p) {
+      const int X0 = pos[p][0] * kTC, Y0 = pos[p][1] * kTC, Z0 = pos[p][2] * kTC;
+      const int c0 = cid[p][0], c1 = cid[p][1], c2 = cid[p][2], c3 = cid[p][3], c4 = cid[p][4], c5 = cid[p][5];
+  #pragma unroll
+      for (int h = 0; h < kCube / kTE; ++h) {
+        const int e = threadIdx.x + h * kTE;
+        const int al = e / (kTC * kTC), bl = (e / kTC) % kTC, cl = e % kTC;
+        const int aa = X0 + al, bb = Y0 + bl, cc = Z0 + cl;
+        if (aa >= v || bb >= v || cc >= v) continue;
+        const T wabc = cube[c0][al][bl][cl];
+        const T wbca = cube[c1][bl][cl][al];
+        const T wcab = cube[c2][cl][al][bl];
+        const T wacb = cube[c3][al][cl][bl];
+        const T wbac = cube[c4][bl][al][cl];
+        const T wcba = cube[c5][cl][bl][al];
+        const T vabc = wabc + singles(aa, bb, cc);
+        const T vacb = wacb + singles(aa, cc, bb);
+        const T vbac = wbac + singles(bb, aa, cc);
+        const T vcba = wcba + singles(cc, bb, aa);
+        const T D = eijk - sev[aa] - sev[bb] - sev[cc];
+        const T term = (T(4) * wabc + wbca + wcab) * (T(3) * vabc - vacb - vbac - vcba) / (T(3) * D);
+        if constexpr (std::is_same<T, float>::value) {
+          const float t = __fadd_rn(sh, term), bp = __fsub_rn(t, sh);
+          sl = __fadd_rn(sl, __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(term, bp)));
+          sh = t;
+        } else {
+          s += (double)term;
+        }
+      }
+    }
+  }  // orbits
   if constexpr (std::is_same<T, float>::value) s = (double)sh + (double)sl;
   // fixed-order reduction: warp shuffles, then the warps' sums in order
   for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
@@ -178,14 +230,15 @@ __global__ void __launch_bounds__(1024) triples_final_kernel(const double *__res
 // dynamic shared memory of the energy kernel for v virtual orbitals
 template <typename T>
 size_t triples_energy_smem(int v) {
-  return (5 * kTC * kTC * (kTC + 1) + 4 * (size_t)v) * sizeof(T);
+  return (6 * kTC * kTC * (kTC + 1) + 4 * (size_t)v) * sizeof(T);
 }
 
 }  // namespace
 
+// orbits of sorted 8-wide block triples
 int triples_energy_blocks(int v) {
   const int nc = (v + kTC - 1) / kTC;
-  return nc * nc;
+  return std::min(nc * (nc + 1) * (nc + 2) / 6, kTriplesMaxBlocks);
 }
 
 template <typename T>
