@@ -80,6 +80,10 @@ template <typename T>
 cudaError_t launch_triples_t2(int o, int v, const double *t2, T *t2c, T *t2T, cudaStream_t s);
 template <typename T>
 cudaError_t launch_triples_negate(T *x, long long n, cudaStream_t s);
+// dst[g][x][y][d] = src[g][y][x][d] for g < G, x, y, d < v (the middle two
+// indices exchanged)
+template <typename T>
+cudaError_t launch_triples_swap12(const T *src, T *dst, int G, int v, cudaStream_t s);
 cudaError_t launch_triples_final(const double *part, long long n, double *E, cudaStream_t s,
                                  const int *status = nullptr);
 

@@ -620,22 +620,9 @@ cudaError_t triples_run(int o, int v, int n, const double *B, const double *Bov,
   g.pn = v;
   cudaError_t e = launch_gemm<double, double, T>(g, 1, s);
   // the same integrals as ovvvT[i][a][b][d] (rows (a, b)), for the orderings
-  // whose b-index lands on W's contiguous index
-  base(g);
-  g.A = Bov;
-  g.B = B;
-  g.Out = ovvvT;
-  g.sam = 1;
-  g.sak = ov;
-  g.sbn = 1;
-  g.sbk = vv;
-  g.M = (int)ov;
-  g.N = (int)vv;
-  g.K = n;
-  g.kchunk = n;
-  g.ldo = (int)vv;
-  g.epi = kEpiStore;
-  if (e == cudaSuccess) e = launch_gemm<double, double, T>(g, 1, s);
+  // whose b-index lands on W's contiguous index: ovvv with its middle two
+  // indices exchanged
+  if (e == cudaSuccess) e = launch_triples_swap12<T>(ovvv, ovvvT, o, v, s);
   // Q[k][j][c][l] = (ck|jl) = v_kl^cj = sum_P Bov[P][k][c] Boo[P][j][l] (negated below)
   base(g);
   g.A = Bov;

@@ -203,6 +203,18 @@ __global__ void triples_t2_kernel(long long n, int v, const double *__restrict__
   }
 }
 
+// dst[g][x][y][d] = src[g][y][x][d]; consecutive threads take consecutive d
+template <typename T>
+__global__ void triples_swap12_kernel(const T *__restrict__ src, T *__restrict__ dst, long long n, int v) {
+  const long long vv = (long long)v * v;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long g = e / (vv * v), r = e % (vv * v);
+    const long long x = r / vv, y = (r / v) % v, d = r % v;
+    dst[e] = src[g * vv * v + (y * v + x) * v + d];
+  }
+}
+
 template <typename T>
 __global__ void triples_negate_kernel(T *__restrict__ x, long long n) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
@@ -269,6 +281,16 @@ cudaError_t launch_triples_t2(int o, int v, const double *t2, T *t2c, T *t2T, cu
 }
 template cudaError_t launch_triples_t2<double>(int, int, const double *, double *, double *, cudaStream_t);
 template cudaError_t launch_triples_t2<float>(int, int, const double *, float *, float *, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_triples_swap12(const T *src, T *dst, int G, int v, cudaStream_t s) {
+  const long long n = (long long)G * v * v * v;
+  const long long blocks = std::min<long long>((n + 255) / 256, 152 * 64);
+  if (blocks > 0) triples_swap12_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(src, dst, n, v);
+  return cudaGetLastError();
+}
+template cudaError_t launch_triples_swap12<double>(const double *, double *, int, int, cudaStream_t);
+template cudaError_t launch_triples_swap12<float>(const float *, float *, int, int, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_triples_negate(T *x, long long n, cudaStream_t s) {
