@@ -142,6 +142,9 @@ ladder_status ladder_set_tuning(ladder_plan_t plan, const ladder_tuning *t);
 
 /* Mode the plan resolved to (LADDER_AUTO resolves at plan time). */
 ladder_status ladder_plan_mode(ladder_plan_t plan, int *mode);
+/* The (o, v, naux) a single-molecule plan was made for (LADDER_EINVAL for a
+ * batched plan). */
+ladder_status ladder_plan_shape(ladder_plan_t plan, int *o, int *v, int *naux);
 
 /* Multi-GPU partition of one molecule's term (the GPU analogue of the
  * paper's split of the virtual pairs over domains, Sec. II.D, Eq. pp-Ladder-3).
@@ -269,6 +272,30 @@ ladder_status ladder_energy_noalloc(int o, int v, const double *R, const double 
  * to skip it.  Outputs are overwritten.  dtau may not alias W or tau. */
 ladder_status ladder_backward(ladder_plan_t plan, const double *B, const double *tau,
                               const double *W, double *dtau, double *dB, void *stream);
+
+/* Closed-shell RI-CCSD (Sec. II.A): the CCSD amplitude equations for a
+ * canonical Hartree-Fock reference (orbital energies e_occ, e_vir) with the
+ * integrals of the RI factors B [naux][v][v], Bov [naux][o][v] and Boo
+ * [naux][o][o] (device, FP64), solved from zero amplitudes by Jacobi steps
+ * with DIIS over the last ndiis iterates (0 <= ndiis <= 8; 0: plain
+ * Jacobi).  Stops when the energy changes by less than tol and the step's
+ * 2-norm is below 1000 tol, or after max_iter steps.  The particle-particle
+ * ladder of every step is ladder_apply on `plan` (a single-molecule plan of
+ * the same (o, v, naux) with its workspace set; its mode decides the ladder's
+ * precision, LADDER_FP64 or LADDER_OZAKI for an FP64-class solution); every
+ * other term runs in FP64.  The residual is evaluated in spin orbitals (the
+ * projections of exp(-T) H exp(T) with the one- and two-body intermediates
+ * of Stanton, Gauss, Watts and Bartlett 1991), so the workspace grows as
+ * 16 (o+v)^4 + 2 (2o)(2v)^3 doubles: small molecules only (o <= 64,
+ * v <= 512; ladder_ccsd_workspace_size gives the bytes).  Outputs: t1
+ * [o][v], t2 [o][o][v][v] (device), the correlation energy
+ * sum_ijab (2 v_ab^ij - v_ba^ij)(t_ij^ab + t_i^a t_j^b) in *E (host) and the
+ * steps taken in *iters (host).  Synchronises `stream`. */
+ladder_status ladder_ccsd_workspace_size(int o, int v, int naux, int ndiis, size_t *bytes);
+ladder_status ladder_ccsd(ladder_plan_t plan, int o, int v, int naux, const double *B, const double *Bov,
+                          const double *Boo, const double *e_occ, const double *e_vir, int max_iter,
+                          double tol, int ndiis, double *t1, double *t2, double *E, int *iters,
+                          void *workspace, size_t workspace_bytes, void *stream);
 
 /* Y_ij^ab = alpha X_ij^ab + beta X_ij^ba over [o][o][v][v] (device arrays,
  * Y may not alias X).  (2, -1) applied to t2 gives the energy weights

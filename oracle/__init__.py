@@ -19,7 +19,9 @@ Functions and the passages they follow (arxiv 1810.08142):
   triples_wv       W_ijk^abc and V_ijk^abc of one (i,j,k)
   grad_tau, grad_B and their *_entries variants: derivatives of
                    sum W_ij^ab R_ij^ab, written out term by term.
-Every function is pinned by tests/test_oracle_pins.py.
+Every function is pinned by tests/test_oracle_pins.py.  The module
+oracle/ccsd.py (numpy) holds the closed-shell CCSD iteration of Sec. II.A,
+pinned by tests/test_oracle_ccsd_pins.py.
 """
 from __future__ import annotations
 

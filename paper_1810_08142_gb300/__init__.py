@@ -27,7 +27,8 @@ STATUS = {0: "LADDER_OK", 1: "LADDER_EINVAL", 2: "LADDER_ENOMEM", 3: "LADDER_ECU
           4: "LADDER_ETIMEOUT", 5: "LADDER_ENOTSUP", 6: "LADDER_EWORKSPACE", 7: "LADDER_ENONFINITE"}
 
 # every entry point that include/ladder.h declares
-EXPORTS = ("ladder_plan", "ladder_plan_mode", "ladder_get_tuning", "ladder_set_tuning", "ladder_tile_count",
+EXPORTS = ("ladder_plan", "ladder_plan_mode", "ladder_plan_shape", "ladder_ccsd_workspace_size", "ladder_ccsd",
+           "ladder_get_tuning", "ladder_set_tuning", "ladder_tile_count",
            "ladder_set_tile_range", "ladder_workspace_size", "ladder_set_workspace",
            "ladder_tau", "ladder_apply", "ladder_apply_dressed", "ladder_triples_workspace_size",
            "ladder_triples", "ladder_energy", "ladder_energy_noalloc", "ladder_backward", "ladder_pair_combine", "ladder_apply_host",
@@ -69,6 +70,10 @@ def load_library(path: str = LIB_PATH):
     sig = {
         "ladder_plan": [i, i, i, i, pp],
         "ladder_plan_mode": [_P, ip],
+        "ladder_plan_shape": [_P, ip, ip, ip],
+        "ladder_ccsd_workspace_size": [i, i, i, i, ctypes.POINTER(sz)],
+        "ladder_ccsd": [_P, i, i, i] + [_P] * 5 + [i, ctypes.c_double, i, _P, _P,
+                                                  ctypes.POINTER(ctypes.c_double), ip, _P, sz, _P],
         "ladder_get_tuning": [_P, ctypes.POINTER(Tuning)],
         "ladder_set_tuning": [_P, ctypes.POINTER(Tuning)],
         "ladder_tile_count": [_P, ip],
@@ -184,6 +189,48 @@ def ladder_apply_dressed(plan, B, B_ov, t1, tau, R, stream=None) -> None:
     _check("ladder_apply_dressed",
            load_library().ladder_apply_dressed(plan, _ptr(B), _ptr(B_ov), _ptr(t1), _ptr(tau), _ptr(R),
                                                _stream(stream)))
+
+
+def ladder_plan_shape(plan):
+    o, v, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check("ladder_plan_shape", load_library().ladder_plan_shape(plan, ctypes.byref(o), ctypes.byref(v),
+                                                                 ctypes.byref(n)))
+    return o.value, v.value, n.value
+
+
+def ladder_ccsd_workspace_size(o: int, v: int, naux: int, ndiis: int) -> int:
+    n = ctypes.c_size_t()
+    _check("ladder_ccsd_workspace_size",
+           load_library().ladder_ccsd_workspace_size(o, v, naux, ndiis, ctypes.byref(n)))
+    return n.value
+
+
+def ladder_ccsd(plan, o, v, naux, B, B_ov, B_oo, e_occ, e_vir, max_iter, tol, ndiis, t1, t2, ws, stream=None):
+    """The C call itself; returns (E, iterations)."""
+    E, it = ctypes.c_double(), ctypes.c_int()
+    _check("ladder_ccsd", load_library().ladder_ccsd(
+        plan, int(o), int(v), int(naux), _ptr(B), _ptr(B_ov), _ptr(B_oo), _ptr(e_occ), _ptr(e_vir),
+        int(max_iter), float(tol), int(ndiis), _ptr(t1), _ptr(t2), ctypes.byref(E), ctypes.byref(it), _ptr(ws),
+        ws.numel() * ws.element_size(), _stream(stream)))
+    return E.value, it.value
+
+
+def ccsd(ladder, B, B_ov, B_oo, e_occ, e_vir, max_iter=100, tol=1e-10, ndiis=3, workspace=None, stream=None):
+    """Closed-shell RI-CCSD (Sec. II.A): Jacobi steps with DIIS from zero
+    amplitudes, the ladder of every step on `ladder` (a Ladder of the same
+    shape; its mode sets the ladder's precision).  FP64 device tensors in;
+    returns (t1, t2, E, iterations) with t1, t2 on the device."""
+    import torch
+    naux, v, _ = B.shape
+    o = B_oo.shape[1]
+    if workspace is None:
+        nb = ladder_ccsd_workspace_size(o, v, naux, ndiis)
+        workspace = torch.empty(max(nb, 256), dtype=torch.uint8, device=B.device)
+    t1 = torch.empty((o, v), dtype=torch.float64, device=B.device)
+    t2 = torch.empty((o, o, v, v), dtype=torch.float64, device=B.device)
+    E, it = ladder_ccsd(ladder.plan, o, v, naux, B, B_ov, B_oo, e_occ, e_vir, max_iter, tol, ndiis, t1, t2,
+                        workspace, stream)
+    return t1, t2, E, it
 
 
 TRIPLES_PRECISION = {"fp64": 0, "fp32": 1, "bf16x6": 2}

@@ -1000,6 +1000,14 @@ ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out) 
   return LADDER_OK;
 }
 
+ladder_status ladder_plan_shape(ladder_plan_t pl, int *o, int *v, int *naux) {
+  if (!pl || pl->batched || !o || !v || !naux) return LADDER_EINVAL;
+  *o = pl->o;
+  *v = pl->v;
+  *naux = pl->N;
+  return LADDER_OK;
+}
+
 ladder_status ladder_plan_mode(ladder_plan_t pl, int *mode) {
   if (!pl || !mode) return LADDER_EINVAL;
   *mode = pl->mode;
