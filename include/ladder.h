@@ -290,7 +290,8 @@ ladder_status ladder_backward(ladder_plan_t plan, const double *B, const double 
  * v <= 512; ladder_ccsd_workspace_size gives the bytes).  Outputs: t1
  * [o][v], t2 [o][o][v][v] (device), the correlation energy
  * sum_ijab (2 v_ab^ij - v_ba^ij)(t_ij^ab + t_i^a t_j^b) in *E (host) and the
- * steps taken in *iters (host).  Synchronises `stream`. */
+ * steps taken in *iters (host); LADDER_ENONFINITE if the energy stops being
+ * finite (a diverging iteration).  Synchronises `stream`. */
 ladder_status ladder_ccsd_workspace_size(int o, int v, int naux, int ndiis, size_t *bytes);
 ladder_status ladder_ccsd(ladder_plan_t plan, int o, int v, int naux, const double *B, const double *Bov,
                           const double *Boo, const double *e_occ, const double *e_vir, int max_iter,

@@ -40,15 +40,22 @@ struct PermArgs {
   double alpha, beta;
 };
 
-// out[e] = alpha in[perm(e)] (+ beta out[e]) over the output's row-major order
+// out[e] = alpha in[perm(e)] (+ beta out[e]) over the output's row-major
+// order; index arithmetic in 32 bits when the arrays allow it
+template <typename I>
 __global__ void permute_kernel(const PermArgs a) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < a.n;
-       e += (long long)gridDim.x * blockDim.x) {
-    long long r = e, off = 0;
+  const I n = (I)a.n;
+  I od[4], is[4];
+  for (int d = 0; d < 4; ++d) {
+    od[d] = (I)a.od[d];
+    is[d] = (I)a.istr[d];
+  }
+  for (I e = blockIdx.x * (I)blockDim.x + threadIdx.x; e < n; e += (I)gridDim.x * blockDim.x) {
+    I r = e, off = 0;
     for (int d = a.nd - 1; d >= 0; --d) {
-      const long long x = r % a.od[d];
-      r /= a.od[d];
-      off += x * a.istr[d];
+      const I x = r % od[d];
+      r /= od[d];
+      off += x * is[d];
     }
     const double v = a.alpha * a.in[off];
     a.out[e] = a.beta != 0.0 ? v + a.beta * a.out[e] : v;
@@ -258,7 +265,10 @@ struct Engine {
       const char *f = std::strchr(li, lo[k]);
       a.istr[k] = istr[f - li];
     }
-    permute_kernel<<<grid_for(a.n), 256, 0, s>>>(a);
+    if (a.n < (1ll << 31) && in.size() < (1ll << 31))
+      permute_kernel<unsigned><<<grid_for(a.n), 256, 0, s>>>(a);
+    else
+      permute_kernel<unsigned long long><<<grid_for(a.n), 256, 0, s>>>(a);
     err = cudaGetLastError();
   }
 
@@ -280,6 +290,12 @@ struct Engine {
     for (char c : M) m *= extent(c);
     for (char c : N) n *= extent(c);
     for (char c : K) k *= extent(c);
+    // split K over CTAs when the product has few 128 x 128 tiles (the FP64
+    // pipe of one SM is slow): partial products side by side in tc, summed
+    const long long tiles = ((m + 127) / 128) * ((n + 127) / 128);
+    long long ks = 1;
+    if (tiles < 2 * 152 && k >= 1024) ks = std::min<long long>((2 * 152 + tiles - 1) / tiles, k / 512);
+    ks = std::max<long long>(1, std::min<long long>(ks, scratch / std::max<long long>(m * n, 1)));
     if (m * k > scratch || n * k > scratch || m * n > scratch) {
       err = cudaErrorInvalidValue;
       return;
@@ -307,16 +323,13 @@ struct Engine {
     g.M = (int)m;
     g.N = (int)n;
     g.K = (int)k;
-    g.kchunk = (int)k;
-    g.ksplit = 1;
-    g.epi = kEpiAcc3;  // tc[m][n] = product, m / pv = 0
-    g.pv = (int)m;
-    g.s1 = 0;
-    g.s2 = n;
-    g.s3 = 1;
-    g.alpha = 1.0;
-    g.acc = 0;
+    g.ksplit = (int)ks;
+    g.kchunk = (int)((k + ks - 1) / ks);
+    g.epi = kEpiStore;  // split q of K at tc + q m n, [m][n]
+    g.ldo = (int)n;
+    g.so_batch = m * n;
     err = launch_gemm<double, double, double>(g, 1, s);
+    if (err == cudaSuccess && ks > 1) err = launch_reduce<double>(tc, m * n, (int)ks, s);
     if (err != cudaSuccess) return;
     Ten t;
     t.p = tc;
@@ -691,6 +704,7 @@ ladder_status ladder_ccsd(ladder_plan_t plan, int o, int v, int naux, const doub
     // tau - t2 = t1 t1 - (t1 t1)^ab: 1/2 <ij||ab> t_i^a t_j^b = 1/4 <ij||ab> (tau - t2)_ijab
     if (!dot(g_oovv, tau, z.t2, eb)) return LADDER_ECUDA;
     const double En = 0.25 * ea + 0.25 * (eb - ea);
+    if (!std::isfinite(En)) return LADDER_ENONFINITE;  // the iteration diverged
     const bool done = std::fabs(En - E) < tol && emax < 1e3 * tol;
     E = En;
     if (done) {
