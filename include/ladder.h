@@ -283,11 +283,13 @@ ladder_status ladder_backward(ladder_plan_t plan, const double *B, const double 
  * ladder of every step is ladder_apply on `plan` (a single-molecule plan of
  * the same (o, v, naux) with its workspace set; its mode decides the ladder's
  * precision, LADDER_FP64 or LADDER_OZAKI for an FP64-class solution); every
- * other term runs in FP64.  The residual is evaluated in spin orbitals (the
+ * other term runs in FP64.  The residual is the spin-orbital one (the
  * projections of exp(-T) H exp(T) with the one- and two-body intermediates
- * of Stanton, Gauss, Watts and Bartlett 1991), so the workspace grows as
- * 16 (o+v)^4 + 2 (2o)(2v)^3 doubles: small molecules only (o <= 64,
- * v <= 512; ladder_ccsd_workspace_size gives the bytes).  Outputs: t1
+ * of Stanton, Gauss, Watts and Bartlett 1991) held by closed-shell spin
+ * blocks (three spatial arrays per four-index tensor); the workspace holds
+ * the spatial (pq|rs) over all o + v orbitals, (o+v)^4 doubles, and about
+ * 9 o v^3 more: small and medium molecules (o <= 128, v <= 1024;
+ * ladder_ccsd_workspace_size gives the bytes).  Outputs: t1
  * [o][v], t2 [o][o][v][v] (device), the correlation energy
  * sum_ijab (2 v_ab^ij - v_ba^ij)(t_ij^ab + t_i^a t_j^b) in *E (host) and the
  * steps taken in *iters (host); LADDER_ENONFINITE if the energy stops being

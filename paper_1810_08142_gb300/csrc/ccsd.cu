@@ -7,12 +7,19 @@
 // orbitals, organised with the one- and two-body intermediates of Stanton,
 // Gauss, Watts and Bartlett (J. Chem. Phys. 94, 4334, 1991); the reference is
 // canonical Hartree-Fock (diagonal Fock matrix of the orbital energies) and
-// the integrals come from the RI factors, (pq|rs) = sum_P B^P_pq B^P_rs.  The
-// amplitudes of a closed-shell reference are spin adapted by construction, so
-// the closed-shell t_i^a and t_ij^ab are read off the spin-orbital ones.  The
-// spin-orbital arrays are 16 times the closed-shell ones, which limits this
-// path to small molecules (a few GB of integrals at o = 10, v = 120); the
-// ladder itself, the O(o^2 v^4) term, runs on the spatial RI factors.
+// the integrals come from the RI factors, (pq|rs) = sum_P B^P_pq B^P_rs.
+//
+// Spin blocks.  For a closed-shell reference every spin-orbital tensor is
+// unchanged when all its spins flip, and it vanishes unless spin is conserved
+// along its two index pairs.  Every four-index tensor here pairs positions
+// (0, 2) and (1, 3) (<pq||rs>: p-r and q-s; t_ij^ab: i-a and j-b), so it is
+// held as three spatial arrays, the spin blocks aaaa, abab and abba (the
+// others are their flips or zero), and a two-index tensor as one (aa).  A
+// spin-orbital contraction is then the sum, over the spins of its summed
+// indices, of spatial contractions of the matching blocks, for each block of
+// the result: the same equations as in spin orbitals, on arrays of spatial
+// size.  The closed-shell amplitudes are t_i^a (the aa block) and t_ij^ab
+// (the abab block).
 //
 // Every contraction is a GEMM of the CUDA-core kernel of dress.cu on operands
 // brought into [rows][K] order by a permutation kernel (transpose - GEMM -
@@ -62,110 +69,93 @@ __global__ void permute_kernel(const PermArgs a) {
   }
 }
 
-// Spin-orbital index maps: occupied spin orbital 2i + s, virtual 2a + s.
-// <PQ||RS> = (pr|qs) [sP = sR][sQ = sS] - (ps|qr) [sP = sS][sQ = sR] for one
-// block of the four index ranges (occupied or virtual each), from the
-// spatial integrals eri[p][q][r][s] = (pq|rs) over all n orbitals.
-struct SoArgs {
+// The three spin blocks of <pq||rs> = <pq|rs> - <pq|sr> over one range of
+// each index (occupied or virtual), from the spatial (pq|rs) = eri[p][q][r][s]:
+//   aaaa = (pr|qs) - (ps|qr),  abab = (pr|qs),  abba = -(ps|qr).
+struct IntArgs {
   const double *eri;
-  double *out;
+  double *aaaa, *abab, *abba;
   int n, o;
-  int vir[4];  // 1: that index runs over virtual spin orbitals
+  int vir[4];  // 1: that index runs over the virtual orbitals
   long long ext[4];
 };
 
-__global__ void so_block_kernel(const SoArgs a) {
+__global__ void int_blocks_kernel(const IntArgs a) {
   const long long tot = a.ext[0] * a.ext[1] * a.ext[2] * a.ext[3];
   const long long n = a.n, nn = n * n, nnn = nn * n;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
        e += (long long)gridDim.x * blockDim.x) {
     long long r = e;
-    int sp[4], orb[4];
+    long long orb[4];
     for (int d = 3; d >= 0; --d) {
-      const int x = (int)(r % a.ext[d]);
+      const long long x = r % a.ext[d];
       r /= a.ext[d];
-      sp[d] = x & 1;
-      orb[d] = (x >> 1) + (a.vir[d] ? a.o : 0);
+      orb[d] = x + (a.vir[d] ? a.o : 0);
     }
-    double g = 0.0;
-    if (sp[0] == sp[2] && sp[1] == sp[3]) g += a.eri[orb[0] * nnn + orb[2] * nn + orb[1] * n + orb[3]];
-    if (sp[0] == sp[3] && sp[1] == sp[2]) g -= a.eri[orb[0] * nnn + orb[3] * nn + orb[1] * n + orb[2]];
-    a.out[e] = g;
+    const double J = a.eri[orb[0] * nnn + orb[2] * nn + orb[1] * n + orb[3]];  // (pr|qs)
+    const double K = a.eri[orb[0] * nnn + orb[3] * nn + orb[1] * n + orb[2]];  // (ps|qr)
+    a.aaaa[e] = J - K;
+    a.abab[e] = J;
+    a.abba[e] = -K;
   }
 }
 
-// tau = t2 + t1 t1 - (t1 t1 with a <-> b), tau_t the same with halves, and
-// X = t2 / 2 + t_j^f t_n^b laid out [j][n][f][b]
-__global__ void tau_so_kernel(const double *__restrict__ t1, const double *__restrict__ t2, double *tau,
-                              double *tau_t, double *X, int O, int V) {
-  const long long n = (long long)O * O * V * V;
+// tau = t2 + t1 t1 - (t1 t1, a <-> b), tau_t the same with halves, and
+// X = t2 / 2 + t_j^f t_n^b (laid out [j][n][f][b]), block by block: the
+// product t_i^a t_j^b lives in the aaaa and abab blocks, t_i^b t_j^a in aaaa
+// and abba.
+__global__ void tau_blocks_kernel(const double *__restrict__ t1, const double *const *t2, double *const *tau,
+                                  double *const *tau_t, double *const *X, int o, int v) {
+  const long long n = (long long)o * o * v * v;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(e % V), a = (int)((e / V) % V), j = (int)((e / V / V) % O), i = (int)(e / V / V / O);
-    const double p = t1[(long long)i * V + a] * t1[(long long)j * V + b];
-    const double q = t1[(long long)i * V + b] * t1[(long long)j * V + a];
-    tau[e] = t2[e] + p - q;
-    tau_t[e] = t2[e] + 0.5 * (p - q);
-    // X[j][n][f][b] with (j, n, f, b) = (i, j, a, b) of this element
-    X[e] = 0.5 * t2[e] + p;
+    const int b = (int)(e % v), a = (int)((e / v) % v), j = (int)((e / v / v) % o), i = (int)(e / v / v / o);
+    const double p = t1[(long long)i * v + a] * t1[(long long)j * v + b];
+    const double q = t1[(long long)i * v + b] * t1[(long long)j * v + a];
+    // aaaa, abab, abba
+    const double pp[3] = {p, p, 0.0}, qq[3] = {q, 0.0, q};
+    for (int k = 0; k < 3; ++k) {
+      const double t = t2[k][e];
+      tau[k][e] = t + pp[k] - qq[k];
+      tau_t[k][e] = t + 0.5 * (pp[k] - qq[k]);
+      X[k][e] = 0.5 * t + pp[k];
+    }
   }
 }
 
-// x_new = rhs / D (D = eps_occ sums - eps_vir sums), err = x_new - x
+// x_new = rhs / D (D = eps_occ sums - eps_vir sums, spatial), err = x_new - x
 __global__ void jacobi_kernel(const double *__restrict__ rhs, const double *__restrict__ x, const double *eps,
-                              int O, int V, int rank, double *__restrict__ xn, double *__restrict__ err) {
-  const long long n = rank == 1 ? (long long)O * V : (long long)O * O * V * V;
+                              int o, int v, int rank, double *__restrict__ xn, double *__restrict__ err) {
+  const long long n = rank == 1 ? (long long)o * v : (long long)o * o * v * v;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
     double D;
     if (rank == 1) {
-      D = eps[e / V] - eps[O + e % V];
+      D = eps[e / v] - eps[o + e % v];
     } else {
-      const int b = (int)(e % V), a = (int)((e / V) % V), j = (int)((e / V / V) % O), i = (int)(e / V / V / O);
-      D = eps[i] + eps[j] - eps[O + a] - eps[O + b];
+      const int b = (int)(e % v), a = (int)((e / v) % v), j = (int)((e / v / v) % o), i = (int)(e / v / v / o);
+      D = eps[i] + eps[j] - eps[o + a] - eps[o + b];
     }
-    const double v = rhs[e] / D;
-    xn[e] = v;
-    err[e] = v - x[e];
+    const double y = rhs[e] / D;
+    xn[e] = y;
+    err[e] = y - x[e];
   }
 }
 
-// Add the ladder R_ij^ab = sum_cd (ac|bd) tau_ij^cd (spatial) as the term
-// 1/2 sum_ef tau_ij^ef <ab||ef> of the spin-orbital doubles: R for the
-// (alpha beta | alpha beta) spin blocks, -R^ba for (alpha beta | beta alpha),
-// R - R^ba for equal spins.
-__global__ void ladder_so_kernel(const double *__restrict__ R, double *__restrict__ rhs2, int o, int v) {
-  const int O = 2 * o, V = 2 * v;
-  const long long n = (long long)O * O * V * V, vv = (long long)v * v;
+// The ladder R_ij^ab = sum_cd (ac|bd) tau_ij^cd (spatial) as the term
+// 1/2 sum_ef tau_ij^ef <ab||ef> of the doubles: abab += R, abba -= R^ba,
+// aaaa += R - R^ba.
+__global__ void ladder_blocks_kernel(const double *__restrict__ R, double *__restrict__ aaaa,
+                                     double *__restrict__ abab, double *__restrict__ abba, int o, int v) {
+  const long long n = (long long)o * o * v * v, vv = (long long)v * v;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
-    const int B = (int)(e % V), A = (int)((e / V) % V), J = (int)((e / V / V) % O), I = (int)(e / V / V / O);
-    const int si = I & 1, sj = J & 1, sa = A & 1, sb = B & 1;
-    const long long ij = ((long long)(I >> 1) * o + (J >> 1)) * vv;
-    const double rab = R[ij + (long long)(A >> 1) * v + (B >> 1)], rba = R[ij + (long long)(B >> 1) * v + (A >> 1)];
-    double add = 0.0;
-    if (si == sj) {
-      if (sa == si && sb == si) add = rab - rba;
-    } else if (sa == si && sb == sj) {
-      add = rab;
-    } else if (sa == sj && sb == si) {
-      add = -rba;
-    }
-    rhs2[e] += add;
-  }
-}
-
-// spatial tau_ij^ab = tau_so[2i][2j+1][2a][2b+1] and the closed-shell
-// amplitudes t_i^a = t1_so[2i][2a], t_ij^ab = t2_so[2i][2j+1][2a][2b+1]
-__global__ void extract_kernel(const double *__restrict__ so1, const double *__restrict__ so2, double *out1,
-                               double *out2, int o, int v) {
-  const int O = 2 * o, V = 2 * v;
-  const long long n2 = (long long)o * o * v * v;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n2;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(e % v), a = (int)((e / v) % v), j = (int)((e / v / v) % o), i = (int)(e / v / v / o);
-    out2[e] = so2[(((long long)(2 * i) * O + 2 * j + 1) * V + 2 * a) * V + 2 * b + 1];
-    if (out1 && j == 0 && b == 0) out1[(long long)i * v + a] = so1[(long long)(2 * i) * V + 2 * a];
+    const long long ij = e / vv;
+    const int b = (int)(e % v), a = (int)((e / v) % v);
+    const double rab = R[e], rba = R[ij * vv + (long long)b * v + a];
+    aaaa[e] += rab - rba;
+    abab[e] += rab;
+    abba[e] -= rba;
   }
 }
 
@@ -339,47 +329,111 @@ struct Engine {
   }
 };
 
+// A closed-shell spin-orbital tensor by spin blocks: nd = 2 holds the aa
+// block, nd = 4 the aaaa, abab and abba blocks (positions (0, 2) and (1, 3)
+// paired); the flipped blocks are equal to these, the rest vanish.
+struct ST {
+  int nd = 0;
+  Ten b[3];
+};
+
+// block index of the spins s[] (0 alpha, 1 beta) of a tensor's indices, -1 if zero
+int st_block(int nd, const int *s) {
+  if (nd == 2) return s[0] == s[1] ? 0 : -1;
+  if (s[0] == s[1] && s[1] == s[2] && s[2] == s[3]) return 0;
+  if (s[0] == s[2] && s[1] == s[3]) return 1;
+  if (s[0] == s[3] && s[1] == s[2]) return 2;
+  return -1;
+}
+
+// spins of the stored blocks, in label order
+const int kBlockSpins[3][4] = {{0, 0, 0, 0}, {0, 1, 0, 1}, {0, 1, 1, 0}};
+
+struct SpinEngine {
+  Engine *e;
+
+  void scale(const Ten &t, double beta) {
+    if (beta == 1.0 || e->err != cudaSuccess) return;
+    if (beta == 0.0) {
+      e->err = cudaMemsetAsync(t.p, 0, (size_t)t.size() * sizeof(double), e->s);
+      return;
+    }
+    std::string l = std::string("pqrs").substr(0, t.nd);
+    e->permute(t, l.c_str(), t, l.c_str(), beta, 0.0);
+  }
+
+  // Z (labels lc) = alpha sum over the shared labels of X Y + beta Z, summed
+  // over the spins of the shared labels for every stored block of Z
+  void contract(const char *la, const ST &X, const char *lb, const ST &Y, const char *lc, const ST &Z,
+                double alpha, double beta) {
+    std::string K;
+    for (const char *c = la; *c; ++c)
+      if (!std::strchr(lc, *c)) K += *c;
+    const int nb = Z.nd == 2 ? 1 : 3;
+    for (int ob = 0; ob < nb; ++ob) {
+      int spin[128];
+      for (int k = 0; lc[k]; ++k) spin[(int)lc[k]] = kBlockSpins[ob][k];
+      bool first = true;
+      for (int mask = 0; mask < (1 << K.size()); ++mask) {
+        for (size_t t = 0; t < K.size(); ++t) spin[(int)K[t]] = (mask >> t) & 1;
+        int sx[4], sy[4];
+        for (int k = 0; la[k]; ++k) sx[k] = spin[(int)la[k]];
+        for (int k = 0; lb[k]; ++k) sy[k] = spin[(int)lb[k]];
+        const int bx = st_block(X.nd, sx), by = st_block(Y.nd, sy);
+        if (bx < 0 || by < 0) continue;
+        e->contract(la, X.b[bx], lb, Y.b[by], lc, Z.b[ob], alpha, first ? beta : 1.0);
+        first = false;
+      }
+      if (first) scale(Z.b[ob], beta);
+    }
+  }
+
+  // Z (labels lo) = alpha X (labels li) + beta Z, block by block
+  void permute(const ST &X, const char *li, const ST &Z, const char *lo, double alpha, double beta) {
+    const int nb = Z.nd == 2 ? 1 : 3;
+    for (int ob = 0; ob < nb; ++ob) {
+      int spin[128], sx[4];
+      for (int k = 0; lo[k]; ++k) spin[(int)lo[k]] = kBlockSpins[ob][k];
+      for (int k = 0; li[k]; ++k) sx[k] = spin[(int)li[k]];
+      const int bx = st_block(X.nd, sx);
+      if (bx < 0)
+        scale(Z.b[ob], beta);
+      else
+        e->permute(X.b[bx], li, Z.b[ob], lo, alpha, beta);
+    }
+  }
+};
+
 }  // namespace
 
+
 // ---------------------------------------------------------------- solver
+// Workspace of the solver, in doubles: the spatial (pq|rs), three spin blocks
+// of each integral class, the amplitudes and intermediates by spin block, the
+// contraction scratch and the DIIS history.
 struct CcsdSizes {
-  long long eri, oooo, ooov, oovv, ovov, ovvv, oovo, ovvo, vvvo, ovoo, t1, t2, scratch;
+  long long eri, ints, t1, t2, scratch;
   size_t bytes;
 };
 
 static CcsdSizes ccsd_sizes(int o, int v, int naux, int ndiis) {
-  const long long n = o + v, O = 2 * o, V = 2 * v;
+  const long long n = o + v, oo = (long long)o * o, vv = (long long)v * v, ov = (long long)o * v;
   CcsdSizes z;
   z.eri = n * n * n * n;
-  z.oooo = O * O * O * O;
-  z.ooov = O * O * O * V;
-  z.oovv = O * O * V * V;
-  z.ovov = z.oovv;
-  z.ovvv = O * V * V * V;
-  z.oovo = z.ooov;
-  z.ovvo = z.oovv;
-  z.vvvo = z.ovvv;
-  z.ovoo = z.ooov;
-  z.t1 = O * V;
-  z.t2 = z.oovv;
-  // the largest operand of any contraction: a [V][V][V][O]-sized array
-  z.scratch = std::max<long long>(z.ovvv, std::max<long long>(z.oovv, (long long)n * n * 8));
-  const long long per = [&] {
-    long long s = 0;
-    s += z.eri + z.oooo + z.ooov + z.oovv + z.ovov + 2 * z.ovvv + z.oovo + z.ovvo + z.vvvo + z.ovoo;
-    s += 3 * z.scratch;                       // engine scratch
-    s += 2 * (z.t1 + z.t2);                   // amplitudes and new amplitudes
-    s += 2 * (z.t1 + z.t2);                   // right-hand sides and errors
-    s += 3 * z.t2;                            // tau, tau_t, X
-    s += 4 * z.t2;                            // ring, Q and two work arrays
-    s += 2 * (long long)o * o * v * v;        // spatial tau and R
-    s += 2 * (z.t1 + z.t2) * ndiis;           // DIIS history
-    s += O * O * O * O + O * O * V * O + V * V * V * O + V * V + O * O + O * V + O * V * V * O;  // intermediates
-    s += 4096 + O + V;                        // reductions, orbital energies
-    s += (long long)naux * n * n;             // B^P_pq over all orbitals
-    return s;
-  }();
-  z.bytes = (size_t)per * sizeof(double) + 128 * 256;  // + the alignment of every array
+  // oooo, ooov, oovv, ovov, ovvv, vovv, oovo, ovvo, vvvo, ovoo
+  z.ints = 3 * (oo * oo + 2 * oo * ov + 3 * oo * vv + 3 * ov * vv + oo * ov);
+  z.t1 = ov;
+  z.t2 = oo * vv;
+  z.scratch = std::max<long long>(std::max<long long>(ov * vv, oo * vv), std::max<long long>(n * n * 8, naux * ov));
+  long long s = z.eri + z.ints + 3 * z.scratch + (long long)naux * n * n;
+  s += 4 * z.t1 + 4 * 3 * z.t2;                                  // t, t new, rhs, step
+  s += 3 * 3 * z.t2;                                              // tau, tau_t, X
+  s += 3 * 3 * z.t2 + 3 * std::max<long long>(oo * oo, z.t2);    // ring, Q, W1 and W2
+  s += z.t2;                                                      // the spatial ladder R
+  s += vv + oo + ov + 3 * oo * oo + 3 * ov * ov + 3 * oo * ov + 3 * vv * ov;  // intermediates
+  s += 2 * (long long)ndiis * (z.t1 + 3 * z.t2);                  // DIIS history
+  s += 4096 + n;
+  z.bytes = (size_t)s * sizeof(double) + 256 * 256;  // + the alignment of every array
   return z;
 }
 
@@ -390,7 +444,7 @@ using namespace ladder;
 extern "C" {
 
 ladder_status ladder_ccsd_workspace_size(int o, int v, int naux, int ndiis, size_t *bytes) {
-  if (!bytes || o < 1 || v < 1 || naux < 1 || ndiis < 0 || ndiis > 8 || o > 64 || v > 512) return LADDER_EINVAL;
+  if (!bytes || o < 1 || v < 1 || naux < 1 || ndiis < 0 || ndiis > 8 || o > 128 || v > 1024) return LADDER_EINVAL;
   *bytes = ccsd_sizes(o, v, naux, ndiis).bytes;
   return LADDER_OK;
 }
@@ -401,17 +455,16 @@ ladder_status ladder_ccsd(ladder_plan_t plan, int o, int v, int naux, const doub
                           size_t ws_bytes, void *stream) {
   int po = 0, pv = 0, pn = 0;
   if (!plan || ladder_plan_shape(plan, &po, &pv, &pn) != LADDER_OK || po != o || pv != v || pn != naux ||
-      !B || !Bov || !Boo || !e_occ || !e_vir || !t1 || !t2 || !E_host || !iters || !workspace ||
-      max_iter < 1 || !(tol > 0.0) || ndiis < 0 || ndiis > 8 || o < 1 || v < 1 || naux < 1 || o > 64 || v > 512)
+      !B || !Bov || !Boo || !e_occ || !e_vir || !t1 || !t2 || !E_host || !iters || !workspace || max_iter < 1 ||
+      !(tol > 0.0) || ndiis < 0 || ndiis > 8 || o < 1 || v < 1 || naux < 1 || o > 128 || v > 1024)
     return LADDER_EINVAL;
   const CcsdSizes z = ccsd_sizes(o, v, naux, ndiis);
   if (ws_bytes < z.bytes) return LADDER_EWORKSPACE;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int n = o + v, O = 2 * o, V = 2 * v;
+  const int n = o + v;
   Arena ar;
   ar.base = static_cast<char *>(workspace);
   ar.cap = ws_bytes;
-  // ---- integrals: B^P_pq over all orbitals, (pq|rs), spin-orbital blocks
   double *Bf = ar.take((long long)naux * n * n);
   double *eri = ar.take(z.eri);
   Engine eng;
@@ -420,41 +473,52 @@ ladder_status ladder_ccsd(ladder_plan_t plan, int o, int v, int naux, const doub
   eng.ta = ar.take(z.scratch);
   eng.tb = ar.take(z.scratch);
   eng.tc = ar.take(z.scratch);
-  double *g_oooo = ar.take(z.oooo), *g_ooov = ar.take(z.ooov), *g_oovv = ar.take(z.oovv);
-  double *g_ovov = ar.take(z.ovov), *g_ovvv = ar.take(z.ovvv), *g_vovv = ar.take(z.ovvv);
-  double *g_oovo = ar.take(z.oovo), *g_ovvo = ar.take(z.ovvo), *g_vvvo = ar.take(z.vvvo);
-  double *g_ovoo = ar.take(z.ovoo);
-  double *T1 = ar.take(z.t1), *T2 = ar.take(z.t2), *T1n = ar.take(z.t1), *T2n = ar.take(z.t2);
-  double *R1 = ar.take(z.t1), *R2 = ar.take(z.t2), *E1 = ar.take(z.t1), *E2 = ar.take(z.t2);
-  double *tau = ar.take(z.t2), *tau_t = ar.take(z.t2), *X = ar.take(z.t2);
-  double *ring = ar.take(z.t2), *Q = ar.take(z.t2), *W1 = ar.take(z.t2), *W2 = ar.take(z.t2);
-  double *tau_sp = ar.take((long long)o * o * v * v), *Rsp = ar.take((long long)o * o * v * v);
-  double *Fae = ar.take((long long)V * V), *Fmi = ar.take((long long)O * O), *Fme = ar.take((long long)O * V);
-  double *Wmnij = ar.take((long long)O * O * O * O), *Wmbej = ar.take((long long)O * V * V * O);
-  double *Zijam = ar.take((long long)O * O * V * O), *U = ar.take((long long)V * V * V * O);
-  double *eps = ar.take(O + V), *red = ar.take(4096);
+  SpinEngine se{&eng};
+  auto st2 = [&](long long d0, long long d1) {
+    ST t;
+    t.nd = 2;
+    t.b[0] = ten(ar.take(d0 * d1), {d0, d1});
+    return t;
+  };
+  auto st4 = [&](long long d0, long long d1, long long d2, long long d3) {
+    ST t;
+    t.nd = 4;
+    for (int k = 0; k < 3; ++k) t.b[k] = ten(ar.take(d0 * d1 * d2 * d3), {d0, d1, d2, d3});
+    return t;
+  };
+  const long long O = o, V = v;
+  const ST g_oooo = st4(O, O, O, O), g_ooov = st4(O, O, O, V), g_oovv = st4(O, O, V, V);
+  const ST g_ovov = st4(O, V, O, V), g_ovvv = st4(O, V, V, V), g_vovv = st4(V, O, V, V);
+  const ST g_oovo = st4(O, O, V, O), g_ovvo = st4(O, V, V, O), g_vvvo = st4(V, V, V, O);
+  const ST g_ovoo = st4(O, V, O, O);
+  const ST T1 = st2(O, V), T1n = st2(O, V), R1 = st2(O, V), E1 = st2(O, V);
+  const ST T2 = st4(O, O, V, V), T2n = st4(O, O, V, V), R2 = st4(O, O, V, V), E2 = st4(O, O, V, V);
+  const ST Tau = st4(O, O, V, V), Taut = st4(O, O, V, V), X = st4(O, O, V, V);
+  const ST Ring = st4(O, O, V, V), Q = st4(O, O, V, V), W1 = st4(O, O, V, V);
+  ST W2;  // Y_ijmn and the P(ij) term of Wmnij
+  W2.nd = 4;
+  for (int k = 0; k < 3; ++k) W2.b[k] = ten(ar.take(std::max<long long>(O * O * O * O, z.t2)), {O, O, O, O});
+  double *Rsp = ar.take(z.t2);
+  const ST Fae = st2(V, V), Fmi = st2(O, O), Fme = st2(O, V);
+  const ST Wmnij = st4(O, O, O, O), Wmbej = st4(O, V, V, O), Zijam = st4(O, O, V, O), U = st4(V, V, V, O);
+  double *eps = ar.take(n), *red = ar.take(4096);
   std::vector<double *> hv, he;
+  const long long nvec = z.t1 + 3 * z.t2;
   for (int k = 0; k < ndiis; ++k) {
-    hv.push_back(ar.take(z.t1 + z.t2));
-    he.push_back(ar.take(z.t1 + z.t2));
+    hv.push_back(ar.take(nvec));
+    he.push_back(ar.take(nvec));
   }
   if (!red || (ndiis && !he.back())) return LADDER_EWORKSPACE;
-  // Bf: [P][p][q] from the oo, ov and vv blocks
+  // ---- integrals: B^P_pq over all orbitals, (pq|rs), spin blocks of <pq||rs>
   {
-    std::vector<double> h_eps(O + V);
-    std::vector<double> eo(o), ev(v);
-    if (cudaMemcpyAsync(eo.data(), e_occ, o * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemcpyAsync(ev.data(), e_vir, v * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
+    std::vector<double> h_eps(n);
+    if (cudaMemcpyAsync(h_eps.data(), e_occ, o * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(h_eps.data() + o, e_vir, v * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess ||
+        cudaMemcpyAsync(eps, h_eps.data(), n * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(Bf, 0, (size_t)naux * n * n * sizeof(double), s) != cudaSuccess)
       return LADDER_ECUDA;
-    for (int i = 0; i < O; ++i) h_eps[i] = eo[i / 2];
-    for (int a = 0; a < V; ++a) h_eps[O + a] = ev[a / 2];
-    if (cudaMemcpyAsync(eps, h_eps.data(), (O + V) * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
-      return LADDER_ECUDA;
-    const Ten tBov = ten(const_cast<double *>(Bov), {naux, o, v});
-    // the four blocks of Bf through strided copies, one P at a time
-    if (cudaMemsetAsync(Bf, 0, (size_t)naux * n * n * sizeof(double), s) != cudaSuccess) return LADDER_ECUDA;
-    for (int P = 0; P < naux; ++P) {
+    for (int P = 0; P < naux; ++P)
       if (cudaMemcpy2DAsync(Bf + (size_t)P * n * n, n * sizeof(double), Boo + (size_t)P * o * o, o * sizeof(double),
                             o * sizeof(double), o, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
           cudaMemcpy2DAsync(Bf + (size_t)P * n * n + o, n * sizeof(double), Bov + (size_t)P * o * v,
@@ -462,74 +526,60 @@ ladder_status ladder_ccsd(ladder_plan_t plan, int o, int v, int naux, const doub
           cudaMemcpy2DAsync(Bf + (size_t)P * n * n + (size_t)o * n + o, n * sizeof(double), B + (size_t)P * v * v,
                             v * sizeof(double), v * sizeof(double), v, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return LADDER_ECUDA;
-    }
     // the vo block: Bf[P][o + a][i] = Bov[P][i][a]
-    Ten tBovT = ten(eng.ta, {naux, v, o});
-    eng.permute(tBov, "Pia", tBovT, "Pai", 1.0, 0.0);
+    eng.permute(ten(const_cast<double *>(Bov), {naux, o, v}), "Pia", ten(eng.ta, {naux, v, o}), "Pai", 1.0, 0.0);
     for (int P = 0; P < naux && eng.err == cudaSuccess; ++P)
       if (cudaMemcpy2DAsync(Bf + (size_t)P * n * n + (size_t)o * n, n * sizeof(double), eng.ta + (size_t)P * v * o,
                             o * sizeof(double), o * sizeof(double), v, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return LADDER_ECUDA;
     // eri[(pq)][(rs)] = sum_P Bf[P][pq] Bf[P][rs]
-    {
-      GemmArgs g;
-      std::memset(&g, 0, sizeof(g));
-      g.A = Bf;
-      g.B = Bf;
-      g.Out = eri;
-      g.sam = 1;
-      g.sak = (long long)n * n;
-      g.sbn = 1;
-      g.sbk = (long long)n * n;
-      g.M = g.N = n * n;
-      g.K = naux;
-      g.kchunk = naux;
-      g.ksplit = 1;
-      g.ldo = n * n;
-      g.epi = kEpiStore;
-      if (launch_gemm<double, double, double>(g, 1, s) != cudaSuccess) return LADDER_ECUDA;
-    }
-    auto block = [&](double *out, int v0, int v1, int v2, int v3) {
-      SoArgs a;
+    GemmArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.A = Bf;
+    g.B = Bf;
+    g.Out = eri;
+    g.sam = 1;
+    g.sak = (long long)n * n;
+    g.sbn = 1;
+    g.sbk = (long long)n * n;
+    g.M = g.N = n * n;
+    g.K = naux;
+    g.kchunk = naux;
+    g.ksplit = 1;
+    g.ldo = n * n;
+    g.epi = kEpiStore;
+    if (launch_gemm<double, double, double>(g, 1, s) != cudaSuccess) return LADDER_ECUDA;
+    auto blocks = [&](const ST &t, int v0, int v1, int v2, int v3) {
+      IntArgs a;
       a.eri = eri;
-      a.out = out;
+      a.aaaa = t.b[0].p;
+      a.abab = t.b[1].p;
+      a.abba = t.b[2].p;
       a.n = n;
       a.o = o;
       const int vv_[4] = {v0, v1, v2, v3};
       for (int d = 0; d < 4; ++d) {
         a.vir[d] = vv_[d];
-        a.ext[d] = vv_[d] ? V : O;
+        a.ext[d] = vv_[d] ? v : o;
       }
-      const long long tot = a.ext[0] * a.ext[1] * a.ext[2] * a.ext[3];
-      so_block_kernel<<<grid_for(tot), 256, 0, s>>>(a);
+      int_blocks_kernel<<<grid_for(a.ext[0] * a.ext[1] * a.ext[2] * a.ext[3]), 256, 0, s>>>(a);
     };
-    block(g_oooo, 0, 0, 0, 0);
-    block(g_ooov, 0, 0, 0, 1);
-    block(g_oovv, 0, 0, 1, 1);
-    block(g_ovov, 0, 1, 0, 1);
-    block(g_ovvv, 0, 1, 1, 1);
-    block(g_vovv, 1, 0, 1, 1);
-    block(g_oovo, 0, 0, 1, 0);
-    block(g_ovvo, 0, 1, 1, 0);
-    block(g_vvvo, 1, 1, 1, 0);
-    block(g_ovoo, 0, 1, 0, 0);
+    blocks(g_oooo, 0, 0, 0, 0);
+    blocks(g_ooov, 0, 0, 0, 1);
+    blocks(g_oovv, 0, 0, 1, 1);
+    blocks(g_ovov, 0, 1, 0, 1);
+    blocks(g_ovvv, 0, 1, 1, 1);
+    blocks(g_vovv, 1, 0, 1, 1);
+    blocks(g_oovo, 0, 0, 1, 0);
+    blocks(g_ovvo, 0, 1, 1, 0);
+    blocks(g_vvvo, 1, 1, 1, 0);
+    blocks(g_ovoo, 0, 1, 0, 0);
     if (cudaGetLastError() != cudaSuccess || eng.err != cudaSuccess) return LADDER_ECUDA;
   }
-  const Ten tT1 = ten(T1, {O, V}), tT2 = ten(T2, {O, O, V, V});
-  const Ten tR1 = ten(R1, {O, V}), tR2 = ten(R2, {O, O, V, V});
-  const Ten tTau = ten(tau, {O, O, V, V}), tTaut = ten(tau_t, {O, O, V, V}), tX = ten(X, {O, O, V, V});
-  const Ten tFae = ten(Fae, {V, V}), tFmi = ten(Fmi, {O, O}), tFme = ten(Fme, {O, V});
-  const Ten tWmnij = ten(Wmnij, {O, O, O, O}), tWmbej = ten(Wmbej, {O, V, V, O});
-  const Ten goooo = ten(g_oooo, {O, O, O, O}), gooov = ten(g_ooov, {O, O, O, V}), goovv = ten(g_oovv, {O, O, V, V});
-  const Ten govov = ten(g_ovov, {O, V, O, V}), govvv = ten(g_ovvv, {O, V, V, V}), gvovv = ten(g_vovv, {V, O, V, V});
-  const Ten goovo = ten(g_oovo, {O, O, V, O}), govvo = ten(g_ovvo, {O, V, V, O}), gvvvo = ten(g_vvvo, {V, V, V, O});
-  const Ten govoo = ten(g_ovoo, {O, V, O, O});
-  const Ten tRing = ten(ring, {O, O, V, V}), tQ = ten(Q, {O, O, V, V}), tW1 = ten(W1, {O, O, V, V});
-  const Ten tZ = ten(Zijam, {O, O, V, O}), tU = ten(U, {V, V, V, O});
-  const Ten tW2 = ten(W2, {O, O, O, O});  // Y_ijmn (fits: O^4 <= O^2 V^2)
-  if (cudaMemsetAsync(T1, 0, z.t1 * sizeof(double), s) != cudaSuccess ||
-      cudaMemsetAsync(T2, 0, z.t2 * sizeof(double), s) != cudaSuccess)
-    return LADDER_ECUDA;
+  // ---- zero amplitudes
+  if (cudaMemsetAsync(T1.b[0].p, 0, z.t1 * sizeof(double), s) != cudaSuccess) return LADDER_ECUDA;
+  for (int k = 0; k < 3; ++k)
+    if (cudaMemsetAsync(T2.b[k].p, 0, z.t2 * sizeof(double), s) != cudaSuccess) return LADDER_ECUDA;
   auto dot = [&](const double *x, const double *y, long long len, double &out) -> bool {
     dot_kernel<<<1024, 256, 0, s>>>(x, y, len, red);
     std::vector<double> h(1024);
@@ -541,180 +591,191 @@ ladder_status ladder_ccsd(ladder_plan_t plan, int o, int v, int naux, const doub
     for (double x_ : h) out += x_;
     return true;
   };
+  // the device pointer tables of the block kernels
+  double *ptrs = ar.take(64);
+  if (!ptrs) return LADDER_EWORKSPACE;
+  {
+    const double *tab[12] = {T2.b[0].p, T2.b[1].p, T2.b[2].p, Tau.b[0].p, Tau.b[1].p, Tau.b[2].p,
+                             Taut.b[0].p, Taut.b[1].p, Taut.b[2].p, X.b[0].p, X.b[1].p, X.b[2].p};
+    if (cudaMemcpyAsync(ptrs, tab, sizeof(tab), cudaMemcpyHostToDevice, s) != cudaSuccess) return LADDER_ECUDA;
+  }
+  double *const *dT2 = reinterpret_cast<double *const *>(ptrs);
+  auto tau_blocks = [&]() {
+    tau_blocks_kernel<<<grid_for(z.t2), 256, 0, s>>>(T1.b[0].p, reinterpret_cast<const double *const *>(dT2), dT2 + 3,
+                                                    dT2 + 6, dT2 + 9, o, v);
+  };
   double E = 0.0;
   int it = 0, stored = 0;
   for (; it < max_iter; ++it) {
-    // ---- tau, tau_t, X
-    tau_so_kernel<<<grid_for(z.t2), 256, 0, s>>>(T1, T2, tau, tau_t, X, O, V);
-    // ---- one-body intermediates
-    eng.contract("mf", tT1, "mafe", govvv, "ae", tFae, 1.0, 0.0);
-    eng.contract("mnaf", tTaut, "mnef", goovv, "ae", tFae, -0.5, 1.0);
-    eng.contract("ne", tT1, "mnie", gooov, "mi", tFmi, 1.0, 0.0);
-    eng.contract("inef", tTaut, "mnef", goovv, "mi", tFmi, 0.5, 1.0);
-    eng.contract("nf", tT1, "mnef", goovv, "me", tFme, 1.0, 0.0);
+    tau_blocks();
+    // ---- one-body intermediates (diagonal Fock parts and f_ia vanish)
+    se.contract("mf", T1, "mafe", g_ovvv, "ae", Fae, 1.0, 0.0);
+    se.contract("mnaf", Taut, "mnef", g_oovv, "ae", Fae, -0.5, 1.0);
+    se.contract("ne", T1, "mnie", g_ooov, "mi", Fmi, 1.0, 0.0);
+    se.contract("inef", Taut, "mnef", g_oovv, "mi", Fmi, 0.5, 1.0);
+    se.contract("nf", T1, "mnef", g_oovv, "me", Fme, 1.0, 0.0);
     // ---- Wmnij = <mn||ij> + P(ij) t_j^e <mn||ie> + 1/4 tau_ij^ef <mn||ef>
-    eng.permute(goooo, "mnij", tWmnij, "mnij", 1.0, 0.0);
-    eng.contract("je", tT1, "mnie", gooov, "mnij", tW2, 1.0, 0.0);
-    eng.permute(tW2, "mnij", tWmnij, "mnij", 1.0, 1.0);
-    eng.permute(tW2, "mnji", tWmnij, "mnij", -1.0, 1.0);
-    eng.contract("ijef", tTau, "mnef", goovv, "mnij", tWmnij, 0.25, 1.0);
+    se.permute(g_oooo, "mnij", Wmnij, "mnij", 1.0, 0.0);
+    se.contract("je", T1, "mnie", g_ooov, "mnij", W2, 1.0, 0.0);
+    se.permute(W2, "mnij", Wmnij, "mnij", 1.0, 1.0);
+    se.permute(W2, "mnji", Wmnij, "mnij", -1.0, 1.0);
+    se.contract("ijef", Tau, "mnef", g_oovv, "mnij", Wmnij, 0.25, 1.0);
     // ---- Wmbej = <mb||ej> + t_j^f <mb||ef> - t_n^b <mn||ej> - (t_jn^fb / 2 + t_j^f t_n^b) <mn||ef>
-    eng.permute(govvo, "mbej", tWmbej, "mbej", 1.0, 0.0);
-    eng.contract("jf", tT1, "mbef", govvv, "mbej", tWmbej, 1.0, 1.0);
-    eng.contract("nb", tT1, "mnej", goovo, "mbej", tWmbej, -1.0, 1.0);
-    eng.contract("jnfb", tX, "mnef", goovv, "mbej", tWmbej, -1.0, 1.0);
-    // ---- singles right-hand side (f_ia = 0)
-    eng.contract("ie", tT1, "ae", tFae, "ia", tR1, 1.0, 0.0);
-    eng.contract("ma", tT1, "mi", tFmi, "ia", tR1, -1.0, 1.0);
-    eng.contract("imae", tT2, "me", tFme, "ia", tR1, 1.0, 1.0);
-    eng.contract("nf", tT1, "naif", govov, "ia", tR1, -1.0, 1.0);
-    eng.contract("imef", tT2, "maef", govvv, "ia", tR1, -0.5, 1.0);
-    eng.contract("mnae", tT2, "nmei", goovo, "ia", tR1, -0.5, 1.0);
+    se.permute(g_ovvo, "mbej", Wmbej, "mbej", 1.0, 0.0);
+    se.contract("jf", T1, "mbef", g_ovvv, "mbej", Wmbej, 1.0, 1.0);
+    se.contract("nb", T1, "mnej", g_oovo, "mbej", Wmbej, -1.0, 1.0);
+    se.contract("jnfb", X, "mnef", g_oovv, "mbej", Wmbej, -1.0, 1.0);
+    // ---- singles right-hand side
+    se.contract("ie", T1, "ae", Fae, "ia", R1, 1.0, 0.0);
+    se.contract("ma", T1, "mi", Fmi, "ia", R1, -1.0, 1.0);
+    se.contract("imae", T2, "me", Fme, "ia", R1, 1.0, 1.0);
+    se.contract("nf", T1, "naif", g_ovov, "ia", R1, -1.0, 1.0);
+    se.contract("imef", T2, "maef", g_ovvv, "ia", R1, -0.5, 1.0);
+    se.contract("mnae", T2, "nmei", g_oovo, "ia", R1, -0.5, 1.0);
     // ---- doubles right-hand side
-    eng.permute(goovv, "ijab", tR2, "ijab", 1.0, 0.0);
+    se.permute(g_oovv, "ijab", R2, "ijab", 1.0, 0.0);
     // P(ab) t_ij^ae F'_be with F'_be = F_be - t_m^b F_me / 2 (formed in Fae's storage)
-    eng.contract("mb", tT1, "me", tFme, "be", tFae, -0.5, 1.0);
-    eng.contract("ijae", tT2, "be", tFae, "ijab", tW1, 1.0, 0.0);
-    eng.permute(tW1, "ijab", tR2, "ijab", 1.0, 1.0);
-    eng.permute(tW1, "ijba", tR2, "ijab", -1.0, 1.0);
-    // - P(ij) t_im^ab (F_mj + t_j^e F_me / 2)
-    eng.contract("je", tT1, "me", tFme, "mj", tFmi, 0.5, 1.0);
-    eng.contract("imab", tT2, "mj", tFmi, "ijab", tW1, 1.0, 0.0);
-    eng.permute(tW1, "ijab", tR2, "ijab", -1.0, 1.0);
-    eng.permute(tW1, "jiab", tR2, "ijab", 1.0, 1.0);
+    se.contract("mb", T1, "me", Fme, "be", Fae, -0.5, 1.0);
+    se.contract("ijae", T2, "be", Fae, "ijab", W1, 1.0, 0.0);
+    se.permute(W1, "ijab", R2, "ijab", 1.0, 1.0);
+    se.permute(W1, "ijba", R2, "ijab", -1.0, 1.0);
+    // - P(ij) t_im^ab F'_mj with F'_mj = F_mj + t_j^e F_me / 2
+    se.contract("je", T1, "me", Fme, "mj", Fmi, 0.5, 1.0);
+    se.contract("imab", T2, "mj", Fmi, "ijab", W1, 1.0, 0.0);
+    se.permute(W1, "ijab", R2, "ijab", -1.0, 1.0);
+    se.permute(W1, "jiab", R2, "ijab", 1.0, 1.0);
     // 1/2 tau_mn^ab Wmnij
-    eng.contract("mnab", tTau, "mnij", tWmnij, "ijab", tR2, 0.5, 1.0);
+    se.contract("mnab", Tau, "mnij", Wmnij, "ijab", R2, 0.5, 1.0);
     // 1/2 tau_ij^ef Wabef without <ab||ef>: -1/2 P(ab) t_m^b Z_ijam + 1/8 tau_mn^ab Y_ijmn
-    eng.contract("ijef", tTau, "amef", gvovv, "ijam", tZ, 1.0, 0.0);
-    eng.contract("ijam", tZ, "mb", tT1, "ijab", tQ, 1.0, 0.0);
-    eng.permute(tQ, "ijab", tR2, "ijab", -0.5, 1.0);
-    eng.permute(tQ, "ijba", tR2, "ijab", 0.5, 1.0);
-    eng.contract("ijef", tTau, "mnef", goovv, "ijmn", tW2, 1.0, 0.0);
-    eng.contract("mnab", tTau, "ijmn", tW2, "ijab", tR2, 0.125, 1.0);
+    se.contract("ijef", Tau, "amef", g_vovv, "ijam", Zijam, 1.0, 0.0);
+    se.contract("ijam", Zijam, "mb", T1, "ijab", Q, 1.0, 0.0);
+    se.permute(Q, "ijab", R2, "ijab", -0.5, 1.0);
+    se.permute(Q, "ijba", R2, "ijab", 0.5, 1.0);
+    se.contract("ijef", Tau, "mnef", g_oovv, "ijmn", W2, 1.0, 0.0);
+    se.contract("mnab", Tau, "ijmn", W2, "ijab", R2, 0.125, 1.0);
     // P(ij) P(ab) (t_im^ae Wmbej - t_i^e t_m^a <mb||ej>)
-    eng.contract("imae", tT2, "mbej", tWmbej, "ijab", tRing, 1.0, 0.0);
-    eng.contract("ma", tT1, "mbej", govvo, "abej", tU, 1.0, 0.0);
-    eng.contract("ie", tT1, "abej", tU, "ijab", tRing, -1.0, 1.0);
-    eng.permute(tRing, "ijab", tR2, "ijab", 1.0, 1.0);
-    eng.permute(tRing, "jiab", tR2, "ijab", -1.0, 1.0);
-    eng.permute(tRing, "ijba", tR2, "ijab", -1.0, 1.0);
-    eng.permute(tRing, "jiba", tR2, "ijab", 1.0, 1.0);
+    se.contract("imae", T2, "mbej", Wmbej, "ijab", Ring, 1.0, 0.0);
+    se.contract("ma", T1, "mbej", g_ovvo, "abej", U, 1.0, 0.0);
+    se.contract("ie", T1, "abej", U, "ijab", Ring, -1.0, 1.0);
+    se.permute(Ring, "ijab", R2, "ijab", 1.0, 1.0);
+    se.permute(Ring, "jiab", R2, "ijab", -1.0, 1.0);
+    se.permute(Ring, "ijba", R2, "ijab", -1.0, 1.0);
+    se.permute(Ring, "jiba", R2, "ijab", 1.0, 1.0);
     // P(ij) t_i^e <ab||ej> - P(ab) t_m^a <mb||ij>
-    eng.contract("ie", tT1, "abej", gvvvo, "ijab", tW1, 1.0, 0.0);
-    eng.permute(tW1, "ijab", tR2, "ijab", 1.0, 1.0);
-    eng.permute(tW1, "jiab", tR2, "ijab", -1.0, 1.0);
-    eng.contract("ma", tT1, "mbij", govoo, "ijab", tW1, 1.0, 0.0);
-    eng.permute(tW1, "ijab", tR2, "ijab", -1.0, 1.0);
-    eng.permute(tW1, "ijba", tR2, "ijab", 1.0, 1.0);
+    se.contract("ie", T1, "abej", g_vvvo, "ijab", W1, 1.0, 0.0);
+    se.permute(W1, "ijab", R2, "ijab", 1.0, 1.0);
+    se.permute(W1, "jiab", R2, "ijab", -1.0, 1.0);
+    se.contract("ma", T1, "mbij", g_ovoo, "ijab", W1, 1.0, 0.0);
+    se.permute(W1, "ijab", R2, "ijab", -1.0, 1.0);
+    se.permute(W1, "ijba", R2, "ijab", 1.0, 1.0);
     if (eng.err != cudaSuccess) return LADDER_ECUDA;
-    // the ladder: 1/2 tau_ij^ef <ab||ef> from the spatial RI ladder of tau
-    extract_kernel<<<grid_for((long long)o * o * v * v), 256, 0, s>>>(nullptr, tau, nullptr, tau_sp, o, v);
+    // the ladder: 1/2 tau_ij^ef <ab||ef> from the spatial RI ladder of tau's
+    // abab block (t_ij^ab + t_i^a t_j^b)
     {
-      const ladder_status st = ladder_apply(plan, B, tau_sp, Rsp, s);
+      const ladder_status st = ladder_apply(plan, B, Tau.b[1].p, Rsp, s);
       if (st != LADDER_OK) return st;
     }
-    ladder_so_kernel<<<grid_for(z.t2), 256, 0, s>>>(Rsp, R2, o, v);
+    ladder_blocks_kernel<<<grid_for(z.t2), 256, 0, s>>>(Rsp, R2.b[0].p, R2.b[1].p, R2.b[2].p, o, v);
     // ---- Jacobi step, DIIS
-    jacobi_kernel<<<grid_for(z.t1), 256, 0, s>>>(R1, T1, eps, O, V, 1, T1n, E1);
-    jacobi_kernel<<<grid_for(z.t2), 256, 0, s>>>(R2, T2, eps, O, V, 2, T2n, E2);
+    jacobi_kernel<<<grid_for(z.t1), 256, 0, s>>>(R1.b[0].p, T1.b[0].p, eps, o, v, 1, T1n.b[0].p, E1.b[0].p);
+    for (int k = 0; k < 3; ++k)
+      jacobi_kernel<<<grid_for(z.t2), 256, 0, s>>>(R2.b[k].p, T2.b[k].p, eps, o, v, 2, T2n.b[k].p, E2.b[k].p);
     if (cudaGetLastError() != cudaSuccess) return LADDER_ECUDA;
-    double emax = 0.0;
+    // the pieces of one DIIS vector: t1, then the three t2 blocks
+    const double *pn_[4] = {T1n.b[0].p, T2n.b[0].p, T2n.b[1].p, T2n.b[2].p};
+    const double *pe_[4] = {E1.b[0].p, E2.b[0].p, E2.b[1].p, E2.b[2].p};
+    double *pt_[4] = {T1.b[0].p, T2.b[0].p, T2.b[1].p, T2.b[2].p};
+    const long long len_[4] = {z.t1, z.t2, z.t2, z.t2}, off_[4] = {0, z.t1, z.t1 + z.t2, z.t1 + 2 * z.t2};
+    bool copied = false;
     if (ndiis > 0) {
-      // history slot it % ndiis: vector (t1n, t2n) and error (e1, e2)
       const int slot = it % ndiis;
-      if (cudaMemcpyAsync(hv[slot], T1n, z.t1 * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-          cudaMemcpyAsync(hv[slot] + z.t1, T2n, z.t2 * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-          cudaMemcpyAsync(he[slot], E1, z.t1 * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-          cudaMemcpyAsync(he[slot] + z.t1, E2, z.t2 * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        return LADDER_ECUDA;
+      for (int q = 0; q < 4; ++q)
+        if (cudaMemcpyAsync(hv[slot] + off_[q], pn_[q], len_[q] * sizeof(double), cudaMemcpyDeviceToDevice, s) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(he[slot] + off_[q], pe_[q], len_[q] * sizeof(double), cudaMemcpyDeviceToDevice, s) !=
+                cudaSuccess)
+          return LADDER_ECUDA;
       stored = std::min(stored + 1, ndiis);
       if (stored > 1) {
-        // Pulay: minimise |sum c_k e_k| with sum c_k = 1
-        const int m = stored;
-        std::vector<double> Bm((m + 1) * (m + 1), 0.0), rhs(m + 1, 0.0);
+        // Pulay: minimise |sum c_k e_k| with sum c_k = 1 (the spin-orbital
+        // norm counts each block twice, which scales the system uniformly)
+        const int m = stored, q1 = m + 1;
+        std::vector<double> A((size_t)q1 * q1, 0.0), rhs(q1, 0.0), c(q1, 0.0);
         for (int x = 0; x < m; ++x)
           for (int y = 0; y <= x; ++y) {
             double d;
-            if (!dot(he[x], he[y], z.t1 + z.t2, d)) return LADDER_ECUDA;
-            Bm[x * (m + 1) + y] = Bm[y * (m + 1) + x] = d;
+            if (!dot(he[x], he[y], nvec, d)) return LADDER_ECUDA;
+            A[x * q1 + y] = A[y * q1 + x] = d;
           }
-        for (int x = 0; x < m; ++x) Bm[x * (m + 1) + m] = Bm[m * (m + 1) + x] = -1.0;
+        for (int x = 0; x < m; ++x) A[x * q1 + m] = A[m * q1 + x] = -1.0;
         rhs[m] = -1.0;
-        // Gaussian elimination with partial pivoting on the (m+1) system
-        const int q = m + 1;
-        std::vector<double> Aug(Bm);
-        std::vector<int> piv(q);
-        for (int c = 0; c < q; ++c) {
-          int pr = c;
-          for (int r = c + 1; r < q; ++r)
-            if (std::fabs(Aug[r * q + c]) > std::fabs(Aug[pr * q + c])) pr = r;
-          if (Aug[pr * q + c] == 0.0) break;
-          if (pr != c) {
-            for (int k = 0; k < q; ++k) std::swap(Aug[c * q + k], Aug[pr * q + k]);
-            std::swap(rhs[c], rhs[pr]);
+        // Gaussian elimination with partial pivoting
+        for (int col = 0; col < q1; ++col) {
+          int pr = col;
+          for (int r = col + 1; r < q1; ++r)
+            if (std::fabs(A[r * q1 + col]) > std::fabs(A[pr * q1 + col])) pr = r;
+          if (A[pr * q1 + col] == 0.0) break;
+          if (pr != col) {
+            for (int k = 0; k < q1; ++k) std::swap(A[col * q1 + k], A[pr * q1 + k]);
+            std::swap(rhs[col], rhs[pr]);
           }
-          for (int r = c + 1; r < q; ++r) {
-            const double f = Aug[r * q + c] / Aug[c * q + c];
-            for (int k = c; k < q; ++k) Aug[r * q + k] -= f * Aug[c * q + k];
-            rhs[r] -= f * rhs[c];
+          for (int r = col + 1; r < q1; ++r) {
+            const double f = A[r * q1 + col] / A[col * q1 + col];
+            for (int k = col; k < q1; ++k) A[r * q1 + k] -= f * A[col * q1 + k];
+            rhs[r] -= f * rhs[col];
           }
         }
-        std::vector<double> c(q, 0.0);
-        for (int r = q - 1; r >= 0; --r) {
+        for (int r = q1 - 1; r >= 0; --r) {
           double acc = rhs[r];
-          for (int k = r + 1; k < q; ++k) acc -= Aug[r * q + k] * c[k];
-          c[r] = Aug[r * q + r] != 0.0 ? acc / Aug[r * q + r] : 0.0;
+          for (int k = r + 1; k < q1; ++k) acc -= A[r * q1 + k] * c[k];
+          c[r] = A[r * q1 + r] != 0.0 ? acc / A[r * q1 + r] : 0.0;
         }
-        CombArgs ca;
-        std::memset(&ca, 0, sizeof(ca));
-        ca.m = m;
-        for (int k = 0; k < m; ++k) {
-          ca.x[k] = hv[k];
-          ca.c[k] = c[k];
+        for (int q = 0; q < 4; ++q) {
+          CombArgs ca;
+          std::memset(&ca, 0, sizeof(ca));
+          ca.m = m;
+          for (int k = 0; k < m; ++k) {
+            ca.x[k] = hv[k] + off_[q];
+            ca.c[k] = c[k];
+          }
+          ca.y = pt_[q];
+          ca.n = len_[q];
+          combine_kernel<<<grid_for(ca.n), 256, 0, s>>>(ca);
         }
-        // (T1n, T2n) are contiguous in the history slot layout only, so combine
-        // into T1 / T2 through the two parts
-        for (int part = 0; part < 2; ++part) {
-          CombArgs cp = ca;
-          for (int k = 0; k < m; ++k) cp.x[k] = hv[k] + (part ? z.t1 : 0);
-          cp.y = part ? T2 : T1;
-          cp.n = part ? z.t2 : z.t1;
-          combine_kernel<<<grid_for(cp.n), 256, 0, s>>>(cp);
-        }
-      } else {
-        if (cudaMemcpyAsync(T1, T1n, z.t1 * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-            cudaMemcpyAsync(T2, T2n, z.t2 * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-          return LADDER_ECUDA;
+        copied = true;
       }
-    } else {
-      if (cudaMemcpyAsync(T1, T1n, z.t1 * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-          cudaMemcpyAsync(T2, T2n, z.t2 * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        return LADDER_ECUDA;
     }
-    // largest step of this iteration (|e|^2 as a cheap norm for the test)
-    double e2 = 0.0;
-    if (!dot(E2, E2, z.t2, e2)) return LADDER_ECUDA;
-    double e1 = 0.0;
-    if (!dot(E1, E1, z.t1, e1)) return LADDER_ECUDA;
-    emax = std::sqrt(e1 + e2);
-    // energy: 1/4 <ij||ab> t_ij^ab + 1/2 <ij||ab> t_i^a t_j^b
-    double ea = 0.0, eb = 0.0;
-    tau_so_kernel<<<grid_for(z.t2), 256, 0, s>>>(T1, T2, tau, tau_t, X, O, V);
-    if (!dot(g_oovv, T2, z.t2, ea)) return LADDER_ECUDA;
-    // tau - t2 = t1 t1 - (t1 t1)^ab: 1/2 <ij||ab> t_i^a t_j^b = 1/4 <ij||ab> (tau - t2)_ijab
-    if (!dot(g_oovv, tau, z.t2, eb)) return LADDER_ECUDA;
-    const double En = 0.25 * ea + 0.25 * (eb - ea);
+    if (!copied)
+      for (int q = 0; q < 4; ++q)
+        if (cudaMemcpyAsync(pt_[q], pn_[q], len_[q] * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+          return LADDER_ECUDA;
+    // step size (2-norm over the stored blocks) and the energy
+    // E = 1/4 sum <ij||ab> tau_ij^ab over spin orbitals = 1/2 sum over the three blocks
+    double step = 0.0, En = 0.0;
+    for (int q = 0; q < 4; ++q) {
+      double d;
+      if (!dot(pe_[q], pe_[q], len_[q], d)) return LADDER_ECUDA;
+      step += d;
+    }
+    tau_blocks();
+    for (int k = 0; k < 3; ++k) {
+      double d;
+      if (!dot(g_oovv.b[k].p, Tau.b[k].p, z.t2, d)) return LADDER_ECUDA;
+      En += 0.5 * d;
+    }
     if (!std::isfinite(En)) return LADDER_ENONFINITE;  // the iteration diverged
-    const bool done = std::fabs(En - E) < tol && emax < 1e3 * tol;
+    const bool done = std::fabs(En - E) < tol && std::sqrt(step) < 1e3 * tol;
     E = En;
     if (done) {
       ++it;
       break;
     }
   }
-  // closed-shell amplitudes
-  extract_kernel<<<grid_for((long long)o * o * v * v), 256, 0, s>>>(T1, T2, t1, t2, o, v);
-  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return LADDER_ECUDA;
+  // closed-shell amplitudes: the aa block of t1 and the abab block of t2
+  if (cudaMemcpyAsync(t1, T1.b[0].p, z.t1 * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(t2, T2.b[1].p, z.t2 * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return LADDER_ECUDA;
   *E_host = E;
   *iters = it;
   return LADDER_OK;
