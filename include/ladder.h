@@ -80,9 +80,11 @@ typedef enum {
  * runs the two-pass form and stores its sliced V+- tiles (S x 32 KiB per ab
  * tile and block pair: 136 GB at o=34, v=400, N_aux=1600 with 5 slices);
  * where all tiles would exceed 200 GiB it runs them in sequential ranges (see
- * tile_chunk in ladder_tuning).  ladder_backward and batch plans return
- * LADDER_ENOTSUP.  ladder_apply_dressed runs its correction in FP64 in this
- * mode. */
+ * tile_chunk in ladder_tuning).  With sym_b set in ladder_tuning (B^P_ac =
+ * B^P_ca, the RI factors of real orbitals) it forms each distinct integral
+ * tile once instead of GEMM1 per (ab tile, block pair).  ladder_backward
+ * returns LADDER_ENOTSUP.  ladder_apply_dressed runs its correction in FP64
+ * in this mode. */
 
 /* OR this into `mode` to size the workspace for ladder_backward as well
  * (the FP64 gradient with respect to B spills tiles of Gamma^{xb}_{yd}). */
@@ -130,12 +132,28 @@ ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out);
  *               them for o=34, v=400; >= 0.  With several ranges
  *               ladder_timing_passes reports the ladder kernels as pass 1
  *               and 0 for pass 2.
+ *   sym_b       LADDER_OZAKI only (0 for the other modes, else LADDER_EINVAL):
+ *               1 promises B^P_ac = B^P_ca for every P, a, c, as for the RI
+ *               factors of real orbitals.  Then (ac|bd) depends only on the
+ *               unordered pairs {a,c}, {b,d} and on them in either order, and
+ *               the plan computes each distinct 64 x 64 integral tile (row
+ *               block pair <= column block pair; about a quarter of the
+ *               GEMM1 of the general form) once, in the same exact windows,
+ *               keeps them in the workspace as double-single sums (32 KiB
+ *               per tile: 26.7 GB at v=400), and forms and slices V+- of
+ *               every ab tile from them; R agrees with the general form to
+ *               the rounding of the tail slice orders (about 2^-48 of each
+ *               integral).  Every ladder_apply checks
+ *               the symmetry bitwise on the device; a B that breaks it makes
+ *               ladder_last_device_error return LADDER_EINVAL.  Not with a
+ *               tile range, a plan made LADDER_WITH_DRESSING, or distinct
+ *               tiles above 96 GiB (v above about 550): LADDER_ENOTSUP.
  * Longer chains are faster and less accurate (the tensor core's FP32
  * accumulation error grows with the MMAs per accumulator).  ladder_set_tuning
  * must come before ladder_set_workspace (the workspace size depends on
  * ksplit and two_pass); it returns LADDER_EINVAL for out-of-range values. */
 typedef struct {
-    int kc, s_pieces, flush_every, ksplit, xy_split, two_pass, lambda_only, oz_slices, tile_chunk;
+    int kc, s_pieces, flush_every, ksplit, xy_split, two_pass, lambda_only, oz_slices, tile_chunk, sym_b;
 } ladder_tuning;
 ladder_status ladder_get_tuning(ladder_plan_t plan, ladder_tuning *t);
 ladder_status ladder_set_tuning(ladder_plan_t plan, const ladder_tuning *t);
@@ -371,8 +389,10 @@ ladder_status ladder_step_batched(ladder_plan_t plan, const double *const *B, co
  * Returns LADDER_OK, LADDER_ETIMEOUT (a bounded wait ran out; *where receives
  * the site code of the first one) or LADDER_ENONFINITE (the slicing or packing
  * of B or tau met a NaN or an infinity, site code 50; the tensor-core modes and
- * LADDER_OZAKI check, the FP64 path lets them propagate into R).  *where is 0
- * when nothing was recorded. */
+ * LADDER_OZAKI check, the FP64 path lets them propagate into R) or
+ * LADDER_EINVAL (a LADDER_OZAKI plan with sym_b met a B that is not
+ * symmetric, site code 51; its R is then meaningless).  *where is 0 when
+ * nothing was recorded. */
 ladder_status ladder_last_device_error(ladder_plan_t plan, void *stream, int *where);
 
 /* Self-test of the device-side failure detection: one kernel waits, with the
@@ -399,6 +419,12 @@ ladder_status ladder_timing_passes(ladder_plan_t plan, float *pass1_ms, float *p
  * rank-o correction after the ladder.  LADDER_EINVAL if the plan has no
  * dressing or timing is off. */
 ladder_status ladder_timing_dressing(ladder_plan_t plan, float *bd_ms, float *correction_ms);
+/* The last ladder_apply of a LADDER_OZAKI plan with sym_b (timing on; waits
+ * for it): the distinct integral tiles and the formation of V+- from them,
+ * which together make up what ladder_timing_passes reports as pass 1.
+ * LADDER_EINVAL if that call did not take the symmetric-B form in one range
+ * or timing is off. */
+ladder_status ladder_timing_sym(ladder_plan_t plan, float *xsym_ms, float *form_ms);
 
 /* Algorithmic flop count of one ladder_apply (two flops per multiply-add of
  * the symmetric/antisymmetric scheme; identical for every mode). */

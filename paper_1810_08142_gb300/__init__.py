@@ -33,7 +33,7 @@ EXPORTS = ("ladder_plan", "ladder_plan_mode", "ladder_plan_shape", "ladder_ccsd_
            "ladder_tau", "ladder_apply", "ladder_apply_dressed", "ladder_triples_workspace_size",
            "ladder_triples", "ladder_energy", "ladder_energy_noalloc", "ladder_backward", "ladder_pair_combine", "ladder_apply_host",
            "ladder_plan_batched", "ladder_set_member_tuning", "ladder_apply_batched", "ladder_step_batched", "ladder_last_device_error", "ladder_selftest_wait",
-           "ladder_set_timing", "ladder_timing", "ladder_timing_passes", "ladder_timing_dressing", "ladder_flops", "ladder_status_string",
+           "ladder_set_timing", "ladder_timing", "ladder_timing_passes", "ladder_timing_dressing", "ladder_timing_sym", "ladder_flops", "ladder_status_string",
            "ladder_destroy")
 
 
@@ -41,7 +41,8 @@ class Tuning(ctypes.Structure):
     """Mirror of ladder_tuning (include/ladder.h)."""
     _fields_ = [("kc", ctypes.c_int), ("s_pieces", ctypes.c_int), ("flush_every", ctypes.c_int),
                 ("ksplit", ctypes.c_int), ("xy_split", ctypes.c_int), ("two_pass", ctypes.c_int),
-                ("lambda_only", ctypes.c_int), ("oz_slices", ctypes.c_int), ("tile_chunk", ctypes.c_int)]
+                ("lambda_only", ctypes.c_int), ("oz_slices", ctypes.c_int), ("tile_chunk", ctypes.c_int),
+                ("sym_b", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -101,6 +102,7 @@ def load_library(path: str = LIB_PATH):
                           ctypes.POINTER(ctypes.c_float)],
         "ladder_timing_passes": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)],
         "ladder_timing_dressing": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)],
+        "ladder_timing_sym": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)],
         "ladder_flops": [_P],
         "ladder_status_string": [i],
         "ladder_destroy": [_P],
@@ -351,6 +353,14 @@ def ladder_timing_dressing(plan):
     product and the rank-o correction after the ladder."""
     t = [ctypes.c_float() for _ in range(2)]
     _check("ladder_timing_dressing", load_library().ladder_timing_dressing(plan, *[ctypes.byref(x) for x in t]))
+    return tuple(x.value for x in t)
+
+
+def ladder_timing_sym(plan):
+    """(xsym_ms, form_ms) of the last ladder_apply of an error-free plan with
+    sym_b: the distinct integral tiles and the formation of V+- from them."""
+    t = [ctypes.c_float() for _ in range(2)]
+    _check("ladder_timing_sym", load_library().ladder_timing_sym(plan, *[ctypes.byref(x) for x in t]))
     return tuple(x.value for x in t)
 
 

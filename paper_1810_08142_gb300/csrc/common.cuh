@@ -24,6 +24,7 @@ enum : int {
   kSiteRFull = 7,
   kSiteRFree = 8,
   kSiteNonFinite = 50,  // an input element was NaN or infinite (not a wait)
+  kSiteAsymmetric = 51, // B declared symmetric is not (not a wait)
 };
 
 __host__ __device__ inline int ppos(int n) { return n * (n + 1) / 2; }

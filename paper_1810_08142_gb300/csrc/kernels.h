@@ -267,6 +267,8 @@ struct OzArgs {
   const uint8_t *T2;     // per-chunk tau+- slices (oz_pack_t2), byte offset chunks[c].t2off
   const float *sT;       // [chunk][pair][kOzMaxCols] scale of each tau+- row
   float2 *racc;          // double-single sums, [item][col][128 lanes]
+  float2 *Xs;            // symmetric B: distinct integral tiles [(r <= q)][64][64], double-single
+  const int4 *xunits;    // symmetric B: (iA, kk, q0, q1) work units of the distinct tiles
   int *status;
   int o, v, vp, Np, nbp, nks;
   int nB8, ntiles, nchunks, ksplit, racc_cols;
@@ -306,6 +308,12 @@ uint32_t oz_smem_bytes(int pass, int nslices);
 cudaError_t oz_init_attributes(int nslices);
 cudaError_t launch_oz_vstore(const OzLaunch &L, int nslices, cudaStream_t s);
 cudaError_t launch_oz_gemm2(const OzLaunch &L, int nslices, cudaStream_t s);
+// Symmetric B: the distinct integral tiles (one CTA per unit of one.xunits),
+// V+- of a tile range formed and sliced from them (nunits = tiles x block
+// pairs), and the bitwise check B^P_ac = B^P_ca.
+cudaError_t launch_oz_xsym(const OzLaunch &L, int nslices, cudaStream_t s);
+cudaError_t launch_oz_vform(const OzArgs &a, int nunits, int nslices, int sm_count, cudaStream_t s);
+void launch_oz_symcheck(int N, int v, const double *B, int *status, cudaStream_t s);
 
 // One launch of the fused kernel: a single molecule (mols == nullptr, the
 // work units are 0..nitems-1 of `one`) or a batch (work unit k is local item

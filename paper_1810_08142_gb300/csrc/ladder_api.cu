@@ -28,6 +28,7 @@ struct Layout {
   size_t gG = 0, gT2 = 0, gacc2 = 0;           // two-pass dB: Gamma planes, B per chunk, sums
   size_t dBd = 0, dG = 0, dX = 0, dY = 0;      // t1 dressing: B - mbar, (kc|ld), X, Y
   size_t ozRs = 0, ozSV = 0, ozST = 0;         // error-free mode: B row scales, V+- and tau+- row scales
+  size_t ozXs = 0, ozXu = 0;                   // symmetric B: distinct integral tiles, their work units
 };
 
 // Two-pass form: at most this many bytes of stored V+- tiles by default.
@@ -36,6 +37,10 @@ constexpr double kVStoreDefaultCap = 128.0 * (1ull << 30);
 // exceed this are not supported.
 constexpr double kVStoreOzCap = 200.0 * (1ull << 30);
 constexpr int kOzDefaultSlices = 5;
+// Symmetric B: at most this many bytes of distinct integral tiles (v up to
+// about 550), and column block pairs per work unit of their pass.
+constexpr double kXsymCap = 96.0 * (1ull << 30);
+constexpr int kXsymRange = 32;
 
 int tc_slices(int mode) { return mode == LADDER_BF16X3 ? 2 : 3; }
 
@@ -103,6 +108,10 @@ struct ladder_plan_s {
   int two_pass = 0, vsplit = 1, racc_cols_v = 0, nplus = 0, wplus = 0, wminus = 0;
   int lam_only = 0;  // the paper's lambda-only contraction (two-pass form only)
   int oz_slices = kOzDefaultSlices;  // error-free mode: fixed-point slices per operand
+  // error-free mode with symmetric B: the distinct integral tiles once, then
+  // V+- formed from them (xunits: the (iA, kk, q0, q1) units of their pass)
+  int sym_b = 0;
+  std::vector<int4> xunits;
   // pair-tile range of the plan (multi-GPU partition): tiles tile0 ..
   // tile0 + ntiles_tc - 1 of the shape's ntiles_all
   int tile0 = 0, ntiles_all = 0;
@@ -110,6 +119,7 @@ struct ladder_plan_s {
   // keep one range's stored V+- tiles within the cap)
   int tile_chunk = 0;
   bool last_two_pass = false;
+  bool last_sym = false;  // the last error-free call took the symmetric-B form in one range
   std::vector<TcChunk> chunks_v;
   CUtensorMap tmA, tmB, tmTp, tmTm, tmVl;
   CUtensorMap tmGW, tmGT, tmGBs;  // split-BF16 dB operands
@@ -139,8 +149,9 @@ struct ladder_plan_s {
   std::vector<const void *> gkey;  // pointers the graph was captured with
   bool timing = false;
   // 0..3: prep / ladder / unpack boundaries, 4: between the two passes,
-  // 5..7: dressed call (start, Bd done, correction done)
-  cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  // 5..7: dressed call (start, Bd done, correction done), 8: symmetric B,
+  // distinct integral tiles done (their V+- formation runs from 8 to 4)
+  cudaEvent_t ev[10] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   void *ws = nullptr;
   size_t ws_bytes = 0;
 };
@@ -148,6 +159,30 @@ struct ladder_plan_s {
 namespace {
 
 static int range_tiles(const ladder_plan_s *pl);
+
+// Symmetric B: bytes of the distinct integral tiles (r <= q over the block
+// pairs, 64 x 64 double-single each).
+size_t xsym_bytes(const ladder_plan_s *pl) {
+  return (size_t)pl->nbp * (pl->nbp + 1) / 2 * 4096 * sizeof(float2);
+}
+
+// Work units of the distinct-tile pass: row tiles (iA, kk >= 2 iA) in order,
+// each against its column block pairs q >= ppos(kk) + 2 iA (the first row
+// block pair it holds) in ranges that end at multiples of kXsymRange, so that
+// the units of neighbouring row tiles, which run at the same time, read the
+// same column block pairs.
+std::vector<int4> make_xunits(int nb) {
+  std::vector<int4> u;
+  const int nbp = ppos(nb);
+  for (int iA = 0; 2 * iA < nb; ++iA)
+    for (int kk = 2 * iA; kk < nb; ++kk)
+      for (int q0 = ppos(kk) + 2 * iA; q0 < nbp;) {
+        const int q1 = std::min(nbp, (q0 / kXsymRange + 1) * kXsymRange);
+        u.push_back(make_int4(iA, kk, q0, q1));
+        q0 = q1;
+      }
+  return u;
+}
 
 // Occupied-pair chunks: consecutive j ranges whose lambda+ and lambda- row
 // counts both stay within `rows`.
@@ -303,6 +338,12 @@ void compute_layout(ladder_plan_s *pl) {
     off = align_up(off + t2, 1024);
     L.ozST = off;
     off = align_up(off + pl->chunks_v.size() * pl->nbp * kOzMaxCols * sizeof(float));
+    if (pl->sym_b) {
+      L.ozXs = off;
+      off = align_up(off + xsym_bytes(pl), 1024);
+      L.ozXu = off;
+      off = align_up(off + pl->xunits.size() * sizeof(int4));
+    }
   } else if (pl->mode == LADDER_FP64) {
     L.Tp = off;
     off = align_up(off + (size_t)pl->nlp * pl->K * sizeof(double));
@@ -425,7 +466,8 @@ void compute_layout(ladder_plan_s *pl) {
 static int range_tiles(const ladder_plan_s *pl) {
   if (pl->tile_chunk > 0) return std::min(pl->tile_chunk, pl->ntiles_tc);
   const double per_tile = (double)pl->nbp * 2 * pl->S * 128 * SLOTS * 2;
-  const double cap = pl->mode == LADDER_OZAKI ? kVStoreOzCap : kVStoreDefaultCap;
+  double cap = pl->mode == LADDER_OZAKI ? kVStoreOzCap : kVStoreDefaultCap;
+  if (pl->sym_b) cap -= (double)xsym_bytes(pl);
   return std::max(1, (int)std::min<double>(pl->ntiles_tc, cap / per_tile));
 }
 
@@ -1025,6 +1067,7 @@ ladder_status ladder_get_tuning(ladder_plan_t pl, ladder_tuning *t) {
   t->lambda_only = pl->lam_only;
   t->oz_slices = pl->mode == LADDER_OZAKI ? pl->oz_slices : 0;
   t->tile_chunk = pl->tile_chunk;
+  t->sym_b = pl->sym_b;
   return LADDER_OK;
 }
 
@@ -1034,14 +1077,21 @@ ladder_status ladder_set_tuning(ladder_plan_t pl, const ladder_tuning *t) {
   if (pl->mode == LADDER_OZAKI) {
     // only the slice count and the block-pair split apply
     if ((t->oz_slices != 0 && t->oz_slices != 5 && t->oz_slices != 6) || t->ksplit < 0 || t->ksplit > pl->nbp ||
-        t->two_pass != 1 || t->lambda_only != 0 || t->tile_chunk < 0)
+        t->two_pass != 1 || t->lambda_only != 0 || t->tile_chunk < 0 || (t->sym_b != 0 && t->sym_b != 1))
       return LADDER_EINVAL;
+    // the distinct integral tiles serve every tile of the shape: not with a
+    // tile range, and only while they fit their cap
+    if (t->sym_b && (pl->ntiles_tc != pl->ntiles_all || pl->dressed || (double)xsym_bytes(pl) > kXsymCap))
+      return LADDER_ENOTSUP;
     if (t->oz_slices) pl->oz_slices = pl->S = t->oz_slices;
     pl->tile_chunk = t->tile_chunk;
+    pl->sym_b = t->sym_b;
+    pl->xunits = pl->sym_b ? make_xunits(pl->nb) : std::vector<int4>();
     pl->ksplit = t->ksplit ? t->ksplit : auto_ksplit(pl);
     compute_layout(pl);
     return LADDER_OK;
   }
+  if (t->sym_b != 0) return LADDER_EINVAL;
   if (t->kc < 1 || t->kc > 64 || !(t->s_pieces == 1 || t->s_pieces == 2 || t->s_pieces == 4) ||
       t->flush_every < 1 || t->flush_every > 4096 || t->ksplit < 0 || t->ksplit > pl->nbp ||
       (t->xy_split != 0 && t->xy_split != 1) || (t->two_pass != 0 && t->two_pass != 1) ||
@@ -1081,6 +1131,7 @@ ladder_status ladder_set_tile_range(ladder_plan_t pl, int tile_lo, int tile_hi) 
   if (!pl || pl->batched || pl->ws) return LADDER_EINVAL;
   if (pl->mode == LADDER_FP64) return LADDER_ENOTSUP;
   if (tile_lo < 0 || tile_hi > pl->ntiles_all || tile_lo >= tile_hi) return LADDER_EINVAL;
+  if (pl->sym_b) return LADDER_ENOTSUP;
   pl->tile0 = tile_lo;
   pl->ntiles_tc = tile_hi - tile_lo;
   pl->ksplit = auto_ksplit(pl);
@@ -1175,6 +1226,9 @@ ladder_status ladder_set_workspace(ladder_plan_t pl, void *dptr, size_t bytes) {
   } else {
     const ladder_status st = encode_maps(pl, w);
     if (st != LADDER_OK) return st;
+    if (pl->sym_b && cudaMemcpy(w + pl->lay.ozXu, pl->xunits.data(), pl->xunits.size() * sizeof(int4),
+                                cudaMemcpyHostToDevice) != cudaSuccess)
+      return cuda_status(cudaErrorUnknown);
   }
   pl->ws = dptr;
   pl->ws_bytes = bytes;
@@ -1438,6 +1492,10 @@ static OzArgs oz_args(const ladder_plan_s *pl, int pass, int *status) {
   a.rsB = ws_at<float>(pl, pl->lay.ozRs);
   a.T2 = ws_at<uint8_t>(pl, pl->lay.T2);
   a.sT = ws_at<float>(pl, pl->lay.ozST);
+  if (pl->sym_b) {
+    a.Xs = ws_at<float2>(pl, pl->lay.ozXs);
+    a.xunits = ws_at<int4>(pl, pl->lay.ozXu);
+  }
   a.status = status;
   a.o = pl->o;
   a.v = pl->v;
@@ -1472,10 +1530,13 @@ static OzLaunch oz_launch(const OzArgs &a) {
 
 // side: when given, tau's preparation was enqueued on another stream and
 // side_done marks its end; pass 2 waits for it (pass 1 does not need tau).
+// sym: the plan's symmetric-B form applies to this B (not to a dressed B).
 static ladder_status apply_oz(ladder_plan_t pl, const double *B, const double *tau, double *R,
-                              cudaStream_t s, cudaEvent_t side_done = nullptr) {
+                              cudaStream_t s, cudaEvent_t side_done = nullptr, bool sym = true) {
   mark(pl, 0, s);
   int *status = ws_at<int>(pl, pl->lay.status);
+  sym = sym && pl->sym_b;
+  if (sym) launch_oz_symcheck(pl->N, pl->v, B, status, s);
   if (side_done)
     oz_prep_B(pl, B, status, s);
   else
@@ -1485,18 +1546,30 @@ static ladder_status apply_oz(ladder_plan_t pl, const double *B, const double *t
   OzArgs a1 = oz_args(pl, 1, status), a2 = oz_args(pl, 2, status);
   // tile ranges one after the other (one unless the stored tiles exceed the
   // cap): pass 1 (GEMM1 of every (tile, block pair), V+- slices and scales
-  // stored), pass 2 (GEMM2 per (tile, chunk, block-pair range)), unpack
+  // stored; with symmetric B the distinct integral tiles once, before the
+  // first range, then V+- of each range formed from them), pass 2 (GEMM2 per
+  // (tile, chunk, block-pair range)), unpack
   const int nt = pl->ntiles_tc, rt = range_tiles(pl);
   const bool one = rt >= nt;
   pl->last_two_pass = one;
+  pl->last_sym = sym && one;
   mark(pl, 1, s);
+  if (sym) {
+    OzArgs ax = a1;
+    ax.nitems = (int)pl->xunits.size();
+    st = cuda_status(launch_oz_xsym(oz_launch(ax), pl->S, s));
+    if (one) mark(pl, 8, s);
+  }
   for (int r0 = 0; r0 < nt && st == LADDER_OK; r0 += rt) {
     const int cnt = std::min(rt, nt - r0);
     a1.tile0 = a2.tile0 = pl->tile0 + r0;
     a1.ntiles = a2.ntiles = cnt;
     a1.nitems = cnt * pl->vsplit;
     a2.nitems = cnt * a2.nchunks * pl->ksplit;
-    st = cuda_status(launch_oz_vstore(oz_launch(a1), pl->S, s));
+    if (sym)
+      st = cuda_status(launch_oz_vform(a1, cnt * pl->nbp, pl->S, pl->sm_count, s));
+    else
+      st = cuda_status(launch_oz_vstore(oz_launch(a1), pl->S, s));
     if (one) mark(pl, 4, s);
     if (st == LADDER_OK && side_done && r0 == 0) st = cuda_status(cudaStreamWaitEvent(s, side_done, 0));
     if (st == LADDER_OK) st = cuda_status(launch_oz_gemm2(oz_launch(a2), pl->S, s));
@@ -1564,7 +1637,7 @@ ladder_status ladder_apply_dressed(ladder_plan_t pl, const double *B, const doub
   if (st != LADDER_OK) return st;
   mark(pl, 6, s);
   st = pl->mode == LADDER_FP64 ? apply_fp64(pl, Bd, tau, R, s)
-       : pl->mode == LADDER_OZAKI ? apply_oz(pl, Bd, tau, R, s)
+       : pl->mode == LADDER_OZAKI ? apply_oz(pl, Bd, tau, R, s, nullptr, false)
                                   : apply_tc(pl, Bd, tau, R, s);
   if (st != LADDER_OK) return st;
   st = f64 ? dress_correct<double>(pl, Bov, t1, tau, R, s) : dress_correct<float>(pl, Bov, t1, tau, R, s);
@@ -2144,6 +2217,7 @@ ladder_status ladder_last_device_error(ladder_plan_t pl, void *stream, int *wher
     return cuda_status(cudaErrorUnknown);
   if (where) *where = h;
   if (h == kSiteNonFinite) return LADDER_ENONFINITE;
+  if (h == kSiteAsymmetric) return LADDER_EINVAL;
   return h == 0 ? LADDER_OK : LADDER_ETIMEOUT;
 }
 
@@ -2192,6 +2266,18 @@ ladder_status ladder_timing_passes(ladder_plan_t pl, float *pass1_ms, float *pas
   }
   if (pass1_ms) *pass1_ms = t1;
   if (pass2_ms) *pass2_ms = t2;
+  return LADDER_OK;
+}
+
+ladder_status ladder_timing_sym(ladder_plan_t pl, float *xsym_ms, float *form_ms) {
+  if (!pl || !pl->timing || !pl->ev[0] || !pl->last_sym) return LADDER_EINVAL;
+  if (cudaEventSynchronize(pl->ev[3]) != cudaSuccess) return cuda_status(cudaErrorUnknown);
+  float t1 = 0.f, t2 = 0.f;
+  if (cudaEventElapsedTime(&t1, pl->ev[1], pl->ev[8]) != cudaSuccess ||
+      cudaEventElapsedTime(&t2, pl->ev[8], pl->ev[4]) != cudaSuccess)
+    return cuda_status(cudaErrorUnknown);
+  if (xsym_ms) *xsym_ms = t1;
+  if (form_ms) *form_ms = t2;
   return LADDER_OK;
 }
 

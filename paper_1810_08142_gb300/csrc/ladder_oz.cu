@@ -42,6 +42,8 @@
 // Warp roles (576 threads): warp 0 TMA producer, warp 1 MMA issuer (one
 // thread), warps 2-17 conversion (four per TMEM lane quadrant, each owning a
 // quarter of the columns).
+#include <algorithm>
+
 #include "kernels.h"
 #include "tc_ptx.cuh"
 
@@ -274,6 +276,76 @@ struct Cfg2 {
   static constexpr uint32_t kSmem = kRing + 256 + 1024;
 };
 
+// V+- = X +- Y' of one ab row (double-single, renormalised; this lane holds
+// the 8 slots (c = x_l, d = 0..7) of it in Xj and Yj, two columns per f32x2
+// instruction), then per sign the row's scale (a power of two above the
+// largest of its 64 slots, taken over the 8 lanes x_l) and the S fixed-point
+// slices, stored to the row of the stored planes.
+template <int S>
+__device__ __forceinline__ void vpm_store(const float2 *Xj, const float2 *Yj, __nv_bfloat16 *vbase, float *sbase,
+                                          int row, int x_l) {
+  float2 Vp[8], Vm[8];
+#pragma unroll
+  for (int e = 0; e < 8; e += 2) {
+    const float2 xh = make_float2(Xj[e].x, Xj[e + 1].x), xl = make_float2(Xj[e].y, Xj[e + 1].y);
+    const float2 yh = make_float2(Yj[e].x, Yj[e + 1].x), yl = make_float2(Yj[e].y, Yj[e + 1].y);
+    float2 sm, er, hi, lo;
+    two_sum2(xh, yh, sm, er);
+    two_sum2(sm, add2(add2(xl, yl), er), hi, lo);
+    Vp[e] = make_float2(hi.x, lo.x);
+    Vp[e + 1] = make_float2(hi.y, lo.y);
+    two_sum2(xh, mul2(yh, make_float2(-1.f, -1.f)), sm, er);
+    two_sum2(sm, add2(sub2(xl, yl), er), hi, lo);
+    Vm[e] = make_float2(hi.x, lo.x);
+    Vm[e + 1] = make_float2(hi.y, lo.y);
+  }
+#pragma unroll
+  for (int sg = 0; sg < 2; ++sg) {
+    const float2 *V = sg ? Vm : Vp;
+    float m = 0.f;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) m = fmaxf(m, fabsf(V[e].x));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
+    // rows below 2^-119 (far under any integral of interest) count as zero,
+    // which keeps both powers of two normal floats
+    float inv = 0.f, scale = 0.f;
+    const int E = exp_above(m);
+    if (m > 0.f && E >= -118) {
+      inv = pow2f(8 - E);
+      scale = pow2f(E - 8);
+    }
+    // slices two columns at a time (f32x2): x_s = rint(h), (h, l) =
+    // 256 (h - x_s + l) as a TwoSum pair, x_s stored as x_s 2^(-8 s)
+    uint4 out[S];
+    const float2 inv2 = make_float2(inv, inv), magic = make_float2(12582912.0f, 12582912.0f);
+    const float2 c256 = make_float2(256.f, 256.f);
+#pragma unroll
+    for (int e2 = 0; e2 < 4; ++e2) {
+      float2 hs = mul2(make_float2(V[2 * e2].x, V[2 * e2 + 1].x), inv2);
+      float2 ls = mul2(make_float2(V[2 * e2].y, V[2 * e2 + 1].y), inv2);
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const float2 xs = sub2(add2(hs, magic), magic);
+        float2 r, er;
+        two_sum2(sub2(hs, xs), ls, r, er);
+        hs = mul2(r, c256);
+        ls = mul2(er, c256);
+        const float ps = pow2f(-8 * s);
+        const float2 xo = mul2(xs, make_float2(ps, ps));
+        const __nv_bfloat162 b2 = __floats2bfloat162_rn(xo.x, xo.y);
+        (&out[s].x)[e2] = *reinterpret_cast<const uint32_t *>(&b2);
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+      __stcs(reinterpret_cast<uint4 *>(vbase + (size_t)(sg * S + s) * (128 * SLOTS) + row * SLOTS + x_l * CB),
+             out[s]);
+    if (x_l == 0) sbase[sg * 128 + row] = scale;
+  }
+}
+
 // ============================================================================ pass 1
 // GEMM1 of every (tile, block pair) in exact windows, V+- = X +- Y', fixed-point
 // slices of V+- to the workspace.  Work units walk range-major (unit u: range
@@ -488,73 +560,252 @@ __global__ void __launch_bounds__(kThreads, 1) oz_vstore_kernel(const __grid_con
 #pragma unroll
           for (int e = 0; e < 8; ++e) Y[8 * j + e] = make_float2(rh[e], rl[e]);
         }
-        // V+ = X + Y' into X, V- = X - Y' into Y (double-single, renormalised),
-        // two columns per f32x2 instruction
-#pragma unroll
-        for (int e = 0; e < 16; e += 2) {
-          const float2 xh = make_float2(X[e].x, X[e + 1].x), xl = make_float2(X[e].y, X[e + 1].y);
-          const float2 yh = make_float2(Y[e].x, Y[e + 1].x), yl = make_float2(Y[e].y, Y[e + 1].y);
-          float2 sm, er, hi, lo;
-          two_sum2(xh, yh, sm, er);
-          two_sum2(sm, add2(add2(xl, yl), er), hi, lo);
-          X[e] = make_float2(hi.x, lo.x);
-          X[e + 1] = make_float2(hi.y, lo.y);
-          two_sum2(xh, mul2(yh, make_float2(-1.f, -1.f)), sm, er);
-          two_sum2(sm, add2(sub2(xl, yl), er), hi, lo);
-          Y[e] = make_float2(hi.x, lo.x);
-          Y[e + 1] = make_float2(hi.y, lo.y);
-        }
-        // one scale per (ab row, sign): the row's 64 slots are the 8 values of
-        // this thread for its b and the 8 lanes x_l
         __nv_bfloat16 *vbase = A.Vst + (size_t)(I.tile * A.nbp + p) * 2 * S * (128 * SLOTS);
         float *sbase = A.sV + (size_t)(I.tile * A.nbp + p) * 2 * 128;
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          const int row = a_l * 8 + 2 * qw + j;
-#pragma unroll
-          for (int sg = 0; sg < 2; ++sg) {
-            const float2 *V = sg ? Y + 8 * j : X + 8 * j;
-            float m = 0.f;
-#pragma unroll
-            for (int e = 0; e < 8; ++e) m = fmaxf(m, fabsf(V[e].x));
-            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
-            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
-            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
-            // rows below 2^-119 (far under any integral of interest) count as zero,
-            // which keeps both powers of two normal floats
-            float inv = 0.f, scale = 0.f;
-            const int E = exp_above(m);
-            if (m > 0.f && E >= -118) {
-              inv = pow2f(8 - E);
-              scale = pow2f(E - 8);
-            }
-            // slices two columns at a time (f32x2): x_s = rint(h), (h, l) =
-            // 256 (h - x_s + l) as a TwoSum pair, x_s stored as x_s 2^(-8 s)
-            uint4 out[S];
-            const float2 inv2 = make_float2(inv, inv), magic = make_float2(12582912.0f, 12582912.0f);
-            const float2 c256 = make_float2(256.f, 256.f);
-#pragma unroll
-            for (int e2 = 0; e2 < 4; ++e2) {
-              float2 hs = mul2(make_float2(V[2 * e2].x, V[2 * e2 + 1].x), inv2);
-              float2 ls = mul2(make_float2(V[2 * e2].y, V[2 * e2 + 1].y), inv2);
-#pragma unroll
-              for (int s = 0; s < S; ++s) {
-                const float2 xs = sub2(add2(hs, magic), magic);
-                float2 r, er;
-                two_sum2(sub2(hs, xs), ls, r, er);
-                hs = mul2(r, c256);
-                ls = mul2(er, c256);
-                const float ps = pow2f(-8 * s);
-                const float2 xo = mul2(xs, make_float2(ps, ps));
-                const __nv_bfloat162 b2 = __floats2bfloat162_rn(xo.x, xo.y);
-                (&out[s].x)[e2] = *reinterpret_cast<const uint32_t *>(&b2);
+        for (int j = 0; j < 2; ++j) vpm_store<S>(X + 8 * j, Y + 8 * j, vbase, sbase, a_l * 8 + 2 * qw + j, x_l);
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// ============================================================================ symmetric B
+// With B^P_ac = B^P_ca for every P (the RI factors of real orbitals) the
+// integral (ac|bd) = sum_P B^P_ac B^P_bd depends only on the unordered pairs
+// {a, c} and {b, d}, and on them in either order.  Rows (a, c) of B with a in
+// virtual block alpha and c in block gamma, alpha <= gamma, form the row block
+// pair r = (alpha, gamma) (numbered as the block pairs of the slot scheme);
+// the distinct integrals are the 64 x 64 tiles
+//   X'(r, q)[(i % 8) * 8 + j % 8][(i' % 8) * 8 + j' % 8] = sum_P B^P_ij B^P_i'j',
+// i in alpha, j in gamma, i' in beta, j' in lambda, q = (beta, lambda), r <= q,
+// both orders of a diagonal block pair present.  They are computed once each
+// (about a quarter of the general pass 1's GEMM1) in the same exact windows
+// and kept as double-single sums in B units; the formation kernel then builds
+// V+- of every (ab tile, block pair) from them and slices it as pass 1 does.
+
+// Tile (r, q), r <= q, of the distinct integrals in row-major triangular order.
+__device__ __forceinline__ size_t xtri(int r, int q, int nbp) {
+  return (size_t)r * nbp - (size_t)r * (r - 1) / 2 + (size_t)(q - r);
+}
+
+// Element (ac|bd) of the distinct integral tiles.
+__device__ __forceinline__ size_t xaddr(int a, int c, int b, int d, int nbp) {
+  const int ba = a >> 3, bc = c >> 3, bb = b >> 3, bd = d >> 3;
+  int r, row, q, col;
+  if (ba <= bc) {
+    r = ppos(bc) + ba;
+    row = (a & 7) * 8 + (c & 7);
+  } else {
+    r = ppos(ba) + bc;
+    row = (c & 7) * 8 + (a & 7);
+  }
+  if (bb <= bd) {
+    q = ppos(bd) + bb;
+    col = (b & 7) * 8 + (d & 7);
+  } else {
+    q = ppos(bb) + bd;
+    col = (d & 7) * 8 + (b & 7);
+  }
+  return r <= q ? xtri(r, q, nbp) * 4096 + (size_t)(row * 64 + col) : xtri(q, r, nbp) * 4096 + (size_t)(col * 64 + row);
+}
+
+// Pass 1 of the symmetric form.  A work unit (xunits[u] = (iA, kk, q0, q1)) is
+// the row tile of rows (a in the 16-block iA, c in block kk >= 2 iA), i.e. the
+// row block pairs r = (2 iA, kk) and (2 iA + 1, kk), against the column block
+// pairs q0 .. q1 - 1, taken two at a time: their windows alternate between the
+// two TMEM halves as X and Y do in pass 1.  Tiles with r > q are computed but
+// not stored (their transposes are the tiles (q, r)), and nor is the half
+// (2 iA + 1, 2 iA) of the row tile kk = 2 iA (the half (2 iA, 2 iA + 1) of the
+// row tile kk = 2 iA + 1 holds it).
+template <int S>
+__global__ void __launch_bounds__(kThreads, 1) oz_xsym_kernel(const __grid_constant__ OzLaunch Lp) {
+  using C = Cfg1<S>;
+  static_assert(C::kStages >= 3 && 8 * (2 * C::kStages + Bars::kCount) + 8 <= 256, "ring");
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
+  uint8_t *smem = smem_raw + pad;
+  const uint32_t ring = raw + pad;
+  Bars bars{ring + C::kRing, C::kStages};
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(smem + C::kRing + 8 * (2 * C::kStages + Bars::kCount));
+  int *abort_flag = reinterpret_cast<int *>(tmem_holder + 1);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const OzArgs &A = Lp.one;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::kStages; ++s) {
+      mbar_init(bars.full(s), 1);
+      mbar_init(bars.empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(bars.cfull(b), 1);
+      mbar_init(bars.cfree(b), kEpi);
+    }
+    mbar_init(bars.done(), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_holder), 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+  const Watchdog wd{Lp.status, abort_flag, Lp.timeout_ns};
+  const int nwin = (A.nks + kOzKc - 1) / kOzKc;
+
+  if (warp == 0) {
+    // ================================================================ TMA producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0, armed = 0, armed_par = 0;
+      bool ok = true;
+      tma_prefetch_desc(&A.tmA);
+      tma_prefetch_desc(&A.tmB);
+      for (int u = blockIdx.x; ok && u < Lp.nitems; u += gridDim.x) {
+        const int4 U = A.xunits[u];
+        for (int q = U.z; ok && q < U.w; q += 2) {
+          const int ntile = min(2, U.w - q);
+          for (int w = 0; ok && w < nwin; ++w)
+            for (int tt = 0; ok && tt < ntile; ++tt) {
+              int bq, lq;
+              pair_of(q + tt, bq, lq);
+              for (int ks = w * kOzKc; ok && ks < min(A.nks, (w + 1) * kOzKc); ++ks) {
+                if (!(ok = mbar_wait(bars.empty(stage), phase ^ 1u, wd, kSiteTmaEmpty))) break;
+                const uint32_t dst = ring + (uint32_t)stage * C::kStage;
+                mbar_arrive_expect_tx(bars.full(stage), C::kStage);
+                armed |= 1u << stage;
+                armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+                // rows (a in 16-block iA, c in block kk) x rows (b in block bq, d in block lq)
+                tma_load_4d(dst, &A.tmA, bars.full(stage), ks * KSTEP, U.y * CB, U.x * 16, 0);
+                tma_load_4d(dst + S * A_TILE, &A.tmB, bars.full(stage), ks * KSTEP, lq * CB, bq * CB, 0);
+                if (++stage == C::kStages) {
+                  stage = 0;
+                  phase ^= 1u;
+                }
               }
             }
+        }
+      }
+      if (!ok) {
+        DrainWatch dw(Lp.status, Lp.timeout_ns);
+        for (int s = 0; s < C::kStages; ++s)
+          if (armed & (1u << s)) mbar_wait(bars.full(s), (armed_par >> s) & 1u, dw.wd, kSiteTmaFull);
+      }
+    }
+  } else if (warp == 1) {
+    // ================================================================ MMA issuer (as in pass 1)
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t use[2] = {0, 0};
+      const uint32_t hi64 = desc_hi(512, kSwizzle64);
+      const uint32_t id64 = idesc_bf16(128, 64);
+      bool ok = true;
+      for (int u = blockIdx.x; ok && u < Lp.nitems; u += gridDim.x) {
+        const int4 U = A.xunits[u];
+        for (int q = U.z; ok && q < U.w; q += 2) {
+          const int ntile = min(2, U.w - q);
+          for (int w = 0; ok && w < nwin; ++w)
+            for (int tt = 0; ok && tt < ntile; ++tt) {
+              if (!(ok = mbar_wait(bars.cfree(tt), (use[tt] & 1u) ^ 1u, wd, kSiteXYFree))) break;
+              tc_fence_after();
+              const uint32_t dT = tmem + 256u * tt;
+              const int ks0 = w * kOzKc;
+              for (int ks = ks0; ok && ks < min(A.nks, ks0 + kOzKc); ++ks) {
+                if (!(ok = mbar_wait(bars.full(stage), phase, wd, kSiteTmaFull))) break;
+                const uint32_t st = ring + (uint32_t)stage * C::kStage;
+                const uint32_t sb = st + S * A_TILE;
 #pragma unroll
-            for (int s = 0; s < S; ++s)
-              __stcs(reinterpret_cast<uint4 *>(vbase + (size_t)(sg * S + s) * (128 * SLOTS) + row * SLOTS + x_l * CB),
-                     out[s]);
-            if (x_l == 0) sbase[sg * 128 + row] = scale;
+                for (int kk = 0; kk < KSTEP / 16; ++kk) {
+#pragma unroll
+                  for (int pa = 0; pa < S; ++pa) {
+                    const uint64_t ad = desc64(st + pa * A_TILE + kk * 32, hi64);
+                    if (pa <= 3) {
+                      const bool first = ks == ks0 && kk == 0 && pa == 0;
+                      mma_bf16(dT + 64u * pa, ad, desc64(sb + kk * 32, hi64), idesc_bf16(128, 64 * (4 - pa)),
+                               first ? 0u : 1u);
+                    }
+#pragma unroll
+                    for (int qq = (pa <= 4 ? 4 - pa : 0); qq <= S - 1 - pa; ++qq)
+                      mma_bf16(dT + 192u, ad, desc64(sb + qq * B_TILE + kk * 32, hi64), id64, 1u);
+                  }
+                }
+                mma_commit(bars.empty(stage));
+                if (++stage == C::kStages) {
+                  stage = 0;
+                  phase ^= 1u;
+                }
+              }
+              if (!ok) break;
+              mma_commit(bars.cfull(tt));
+              ++use[tt];
+            }
+        }
+      }
+      mma_commit(bars.done());
+      DrainWatch dw(Lp.status, Lp.timeout_ns);
+      mbar_wait(bars.done(), 0, dw.wd, kSiteRFull);
+    }
+  } else {
+    // ================================================================ conversion warps
+    const int quad = warp & 3;
+    const int qw = (warp - 2) >> 2;  // columns 16 qw .. 16 qw + 15: b % 8 = 2 qw + j, d % 8 = e
+    const int L = quad * 32 + lane;  // TMEM lane = row (a, c): a = 16 iA + L / 8, c = 8 kk + L % 8
+    const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + 16u * qw;
+    const int a_l = L >> 3, x_l = L & 7, h = a_l >> 3;
+    uint32_t use[2] = {0, 0};
+    bool ok = true;
+    for (int u = blockIdx.x; ok && u < Lp.nitems; u += gridDim.x) {
+      const int4 U = A.xunits[u];
+      const int a = U.x * 16 + a_l, c = U.y * CB + x_l;
+      const int r = ppos(U.y) + 2 * U.x + h;  // row block pair (2 iA + h, kk)
+      const bool dup = h == 1 && U.y == 2 * U.x;
+      const float ra = A.rsB[(size_t)a * A.vp + c];
+      for (int q = U.z; ok && q < U.w; q += 2) {
+        const int ntile = min(2, U.w - q);
+        float2 X[2][16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) X[0][e] = X[1][e] = make_float2(0.f, 0.f);
+        for (int w = 0; ok && w < nwin; ++w)
+          for (int tt = 0; tt < ntile; ++tt) {
+            if (!(ok = mbar_wait(bars.cfull(tt), use[tt] & 1u, wd, kSiteXYFull))) break;
+            ++use[tt];
+            tc_fence_after();
+            if (tt == 0)
+              drain_window(tl, X[0]);
+            else
+              drain_window(tl + 256u, X[1]);
+            tc_fence_before();
+            mbar_arrive(bars.cfree(tt));
+          }
+        if (!ok) break;
+#pragma unroll
+        for (int tt = 0; tt < 2; ++tt) {
+          const int qt = q + tt;
+          if (tt >= ntile || dup || r > qt) continue;
+          int bq, lq;
+          pair_of(qt, bq, lq);
+          float4 *dst = reinterpret_cast<float4 *>(A.Xs + xtri(r, qt, A.nbp) * 4096 + (size_t)((L & 63) * 64 + 16 * qw));
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const int b = bq * CB + 2 * qw + j;
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+              const float s0 = ra * A.rsB[(size_t)b * A.vp + lq * CB + e];
+              const float s1 = ra * A.rsB[(size_t)b * A.vp + lq * CB + e + 1];
+              const float2 v0 = X[tt][8 * j + e], v1 = X[tt][8 * j + e + 1];
+              dst[(8 * j + e) / 2] = make_float4(v0.x * s0, v0.y * s0, v1.x * s1, v1.y * s1);
+            }
           }
         }
       }
@@ -567,6 +818,70 @@ __global__ void __launch_bounds__(kThreads, 1) oz_vstore_kernel(const __grid_con
     tc_fence_after();
     tmem_dealloc(tmem, 512);
   }
+}
+
+// V+- of every (ab tile, block pair) of the plan's tile range from the
+// distinct integral tiles: X[(a, c), (b, d)] = (ac|bd) and Y'[(a, c), (b, d)]
+// = (ad|bc) read straight from them, then vpm_store as in pass 1.  Work unit u
+// = (local tile u / nbp, block pair u % nbp); 512 threads, each the ab rows
+// (a = A0 + L / 8, b = B0 + 2 qw + j) and the slot row c = 8 k + L % 8, as
+// pass 1's conversion warps.
+template <int S>
+__global__ void __launch_bounds__(512) oz_vform_kernel(const OzArgs A, int nunits) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int L = (warp & 3) * 32 + lane, qw = warp >> 2;
+  const int a_l = L >> 3, x_l = L & 7;
+  const float2 *__restrict__ Xs = A.Xs;
+  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+    const int t = u / A.nbp, p = u - t * A.nbp;
+    int iA = 0, tr = t + A.tile0;
+    while (tr >= A.nB8 - 2 * iA) {
+      tr -= A.nB8 - 2 * iA;
+      ++iA;
+    }
+    const int a = iA * 16 + a_l, B0 = (2 * iA + tr) * CB;
+    int k, l;
+    pair_of(p, k, l);
+    const int c = k * CB + x_l;
+    __nv_bfloat16 *vbase = A.Vst + (size_t)(t * A.nbp + p) * 2 * S * (128 * SLOTS);
+    float *sbase = A.sV + (size_t)(t * A.nbp + p) * 2 * 128;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int b = B0 + 2 * qw + j;
+      float2 X[8], Y[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int d = l * CB + e;
+        X[e] = __ldg(Xs + xaddr(a, c, b, d, A.nbp));
+        Y[e] = __ldg(Xs + xaddr(a, d, b, c, A.nbp));
+      }
+      vpm_store<S>(X, Y, vbase, sbase, a_l * 8 + 2 * qw + j, x_l);
+    }
+  }
+}
+
+// B^P_ac = B^P_ca for every P and a, c < v (bitwise), checked on 32 x 32
+// tiles of the upper triangle; a mismatch records kSiteAsymmetric.
+__global__ void oz_symcheck_kernel(int N, int v, const double *__restrict__ B, int *status) {
+  __shared__ double t[32][33];
+  const int ta = blockIdx.x, tc = blockIdx.y;
+  if (tc < ta) return;
+  bool bad = false;
+  for (int P = blockIdx.z; P < N; P += gridDim.z) {
+    const double *Bp = B + (size_t)P * v * v;
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+      const int a = tc * 32 + y, c = ta * 32 + threadIdx.x;
+      if (a < v && c < v) t[y][threadIdx.x] = Bp[(size_t)a * v + c];
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+      const int a = ta * 32 + y, c = tc * 32 + threadIdx.x;
+      if (a < v && c < v)
+        bad |= __double_as_longlong(Bp[(size_t)a * v + c]) != __double_as_longlong(t[threadIdx.x][y]);
+    }
+  }
+  if (bad) record_status(status, kSiteAsymmetric);
 }
 
 // ============================================================================ pass 2
@@ -1021,6 +1336,7 @@ cudaError_t oz_attrs() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(oz_vstore_kernel<S, true>, at, (int)Cfg1<S>::kSmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(oz_gemm2_kernel<S, false>, at, (int)Cfg2<S>::kSmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(oz_gemm2_kernel<S, true>, at, (int)Cfg2<S>::kSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(oz_xsym_kernel<S>, at, (int)Cfg1<S>::kSmem);
   return e;
 }
 
@@ -1059,6 +1375,31 @@ cudaError_t launch_oz_gemm2(const OzLaunch &L, int nslices, cudaStream_t s) {
       oz_gemm2_kernel<6, false><<<L.nitems, kThreads, Cfg2<6>::kSmem, s>>>(L);
   }
   return cudaGetLastError();
+}
+
+// one CTA per work unit of the distinct integral tiles
+cudaError_t launch_oz_xsym(const OzLaunch &L, int nslices, cudaStream_t s) {
+  if (L.nitems <= 0) return cudaSuccess;
+  if (nslices == 5)
+    oz_xsym_kernel<5><<<L.nitems, kThreads, Cfg1<5>::kSmem, s>>>(L);
+  else
+    oz_xsym_kernel<6><<<L.nitems, kThreads, Cfg1<6>::kSmem, s>>>(L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oz_vform(const OzArgs &a, int nunits, int nslices, int sm_count, cudaStream_t s) {
+  if (nunits <= 0) return cudaSuccess;
+  const int grid = std::min(nunits, 2 * sm_count);
+  if (nslices == 5)
+    oz_vform_kernel<5><<<grid, 512, 0, s>>>(a, nunits);
+  else
+    oz_vform_kernel<6><<<grid, 512, 0, s>>>(a, nunits);
+  return cudaGetLastError();
+}
+
+void launch_oz_symcheck(int N, int v, const double *B, int *status, cudaStream_t s) {
+  const int nt = (v + 31) / 32;
+  oz_symcheck_kernel<<<dim3(nt, nt, std::min(N, 4096)), dim3(32, 8), 0, s>>>(N, v, B, status);
 }
 
 }  // namespace ladder

@@ -95,7 +95,12 @@ def test_ozaki_mode_and_nonfinite_status_are_exposed(lib):
     assert lad.MODES["ozaki"] == 4
     assert lad.STATUS[7] == "LADDER_ENONFINITE"
     assert b"NaN" in lib.ladder_status_string(7)
-    assert [f for f, _ in lad.Tuning._fields_][-2:] == ["oz_slices", "tile_chunk"]
+    # the ctypes mirror of ladder_tuning lists the header's fields in order
+    hdr = open(os.path.join(ROOT, "include", "ladder.h")).read()
+    body = hdr[hdr.index("typedef struct {", hdr.index("Launch parameters")):hdr.index("} ladder_tuning;")]
+    fields = [f.strip() for f in body.split("int", 1)[1].replace(";", "").split(",")]
+    assert [f for f, _ in lad.Tuning._fields_] == fields
+    assert fields[-3:] == ["oz_slices", "tile_chunk", "sym_b"]
     # mode 5 is out of range
     out = ctypes.c_void_p()
     assert lib.ladder_plan(4, 24, 96, 5, ctypes.byref(out)) == 1

@@ -44,9 +44,9 @@ def lad():
     return lad
 
 
-CASES = [("dimer_o10_v120_n480", m) for m in ("fp64", "ozaki", "bf16x6", "bf16x3")] + \
-        [("grad_o16_v200_n800", m) for m in ("fp64", "ozaki", "bf16x6")] + \
-        [("mid_o34_v400_n1600", m) for m in ("ozaki", "bf16x6", "fp64")]
+CASES = [("dimer_o10_v120_n480", m) for m in ("fp64", "ozaki", "ozaki_sym", "bf16x6", "bf16x3")] + \
+        [("grad_o16_v200_n800", m) for m in ("fp64", "ozaki", "ozaki_sym", "bf16x6")] + \
+        [("mid_o34_v400_n1600", m) for m in ("ozaki", "ozaki_sym", "bf16x6", "fp64")]
 
 
 @pytest.mark.parametrize("name,mode", CASES)
@@ -55,7 +55,10 @@ def test_full_size_against_stored_oracle(lad, name, mode):
     w = synthetic.WORKLOADS[name]
     assert (g["o"], g["v"], g["naux"], g["seed"]) == (w.o, w.v, w.naux, w.seed)
     x = synthetic.make_inputs(w.o, w.v, w.naux, w.seed)
-    L = lad.Ladder(w.o, w.v, w.naux, mode=mode)
+    # ozaki_sym: the error-free mode's symmetric-B form (the generator's B is symmetric)
+    tuning = {"sym_b": 1} if mode == "ozaki_sym" else None
+    mode = "ozaki" if mode == "ozaki_sym" else mode
+    L = lad.Ladder(w.o, w.v, w.naux, mode=mode, tuning=tuning)
     _, R, E = run_forward(L, x)
     L.close()
     got = np.stack([R[:, :, a, b] for a, b in zip(g["pairs_a"], g["pairs_b"])])

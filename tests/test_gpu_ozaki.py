@@ -169,3 +169,94 @@ def test_ozaki_dimer_full(lad):
     L.close()
     R_o = oracle.ladder(x.B, oracle.tau(x.t1, x.t2))
     _check(R_g, E_g, R_o, oracle.energy(R_o, x.t2), 5, "dimer", x.t2)
+
+
+# ---------------------------------------------------------------- symmetric B
+# The generator's B is symmetric in a <-> c, so (ac|bd) depends only on the
+# unordered pairs {a,c} and {b,d} and their order; with sym_b the plan computes
+# each distinct 64 x 64 integral tile once and forms V+- from them.
+
+@pytest.mark.parametrize("S", [5, 6])
+@pytest.mark.parametrize("o,v,n,seed", SHAPES)
+def test_ozaki_symmetric_B_matches_oracle(lad, S, o, v, n, seed):
+    x = synthetic.make_inputs(o, v, n, seed)
+    assert np.array_equal(x.B, x.B.transpose(0, 2, 1))
+    L = lad.Ladder(o, v, n, mode="ozaki", tuning={"oz_slices": S, "sym_b": 1})
+    assert lad.ladder_get_tuning(L.plan).sym_b == 1
+    _, R_g, E_g = run_forward(L, x)
+    L.close()
+    R_o = oracle.ladder(x.B, oracle.tau(x.t1, x.t2))
+    _check(R_g, E_g, R_o, oracle.energy(R_o, x.t2), S, "sym o=%d v=%d n=%d" % (o, v, n), x.t2)
+    # the general form on the same input: the two differ only in the rounding
+    # of the tail slice orders' FP32 sums (about 2^-48 of an integral)
+    G = lad.Ladder(o, v, n, mode="ozaki", tuning={"oz_slices": S})
+    _, R_gen, _ = run_forward(G, x)
+    G.close()
+    scale = max(float(np.max(np.abs(R_o))), 1e-300)
+    assert float(np.max(np.abs(R_g - R_gen))) <= 1e-13 * scale
+
+
+def test_ozaki_symmetric_B_timing_and_dimer(lad):
+    """The dimer-size workload in the symmetric-B form, with the two stages
+    of its first pass timed."""
+    w = synthetic.WORKLOADS["dimer_o10_v120_n480"]
+    x = synthetic.make_inputs(w.o, w.v, w.naux, w.seed)
+    L = lad.Ladder(w.o, w.v, w.naux, mode="ozaki", tuning={"sym_b": 1})
+    lad.ladder_set_timing(L.plan, True)
+    _, R_g, E_g = run_forward(L, x)
+    xs, fm = lad.ladder_timing_sym(L.plan)
+    p1, p2 = lad.ladder_timing_passes(L.plan)
+    L.close()
+    print("dimer sym: distinct tiles %.3f ms, formation %.3f ms, pass 1 %.3f ms, pass 2 %.3f ms" % (xs, fm, p1, p2))
+    assert xs > 0 and fm > 0 and abs(xs + fm - p1) <= 0.05 * p1 + 0.01
+    R_o = oracle.ladder(x.B, oracle.tau(x.t1, x.t2))
+    _check(R_g, E_g, R_o, oracle.energy(R_o, x.t2), 5, "sym dimer", x.t2)
+
+
+def test_ozaki_symmetric_B_asymmetric_input_reported(lad):
+    """A B that breaks the promised symmetry is reported as LADDER_EINVAL
+    (site 51) by the device status word; a symmetric B then reports nothing."""
+    import torch
+    o, v, n, seed = 4, 24, 96, 0
+    x = synthetic.make_inputs(o, v, n, seed)
+    B = x.B.copy()
+    B[7, 3, 17] += 1e-9
+    tau = to_dev(oracle.tau(x.t1, x.t2))
+    L = lad.Ladder(o, v, n, mode="ozaki", tuning={"sym_b": 1})
+    L.apply(to_dev(B), tau)
+    torch.cuda.synchronize()
+    st, where = lad.ladder_last_device_error(L.plan)
+    assert lad.STATUS[st] == "LADDER_EINVAL" and where == 51
+    L.apply(to_dev(x.B), tau)
+    torch.cuda.synchronize()
+    assert lad.ladder_last_device_error(L.plan) == (0, 0)
+    L.close()
+
+
+def test_ozaki_symmetric_B_unsupported_combinations(lad):
+    """sym_b is refused with a tile range, on a plan sized for the dressed
+    term, and outside the error-free mode."""
+    o, v, n = 4, 40, 60
+
+    def refused(plan, status):
+        t = lad.ladder_get_tuning(plan)
+        t.sym_b = 1
+        with pytest.raises(lad.LadderError) as ei:
+            lad.ladder_set_tuning(plan, t)
+        assert lad.STATUS[ei.value.status] == status
+        lad.ladder_destroy(plan)
+
+    P = lad.ladder_plan(o, v, n, lad.MODES["ozaki"])
+    lad.ladder_set_tile_range(P, 0, 2)
+    refused(P, "LADDER_ENOTSUP")
+    refused(lad.ladder_plan(o, v, n, lad.MODES["ozaki"] | lad.LADDER_WITH_DRESSING), "LADDER_ENOTSUP")
+    refused(lad.ladder_plan(o, v, n, lad.MODES["bf16x6"]), "LADDER_EINVAL")
+    # the other order: a symmetric-B plan takes no tile range
+    P = lad.ladder_plan(o, v, n, lad.MODES["ozaki"])
+    t = lad.ladder_get_tuning(P)
+    t.sym_b = 1
+    lad.ladder_set_tuning(P, t)
+    with pytest.raises(lad.LadderError) as ei:
+        lad.ladder_set_tile_range(P, 0, 2)
+    assert lad.STATUS[ei.value.status] == "LADDER_ENOTSUP"
+    lad.ladder_destroy(P)
