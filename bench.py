@@ -51,6 +51,35 @@ TOL_R = 1e-6      # relative Frobenius error of R, split modes
 TOL_E = 1e-6      # |dE_L| in Hartree
 
 
+def _ppos(n):
+    return n * (n + 1) // 2
+
+
+def xsym_pairs(v):
+    """(row tile, column block pair) tile products of the symmetric-B form's
+    distinct-tile pass: row tiles (iA, kk >= 2 iA) of 8-blocks, each against
+    the column block pairs from its first row block pair on."""
+    nb = (v + 15) // 16 * 2
+    nbp = _ppos(nb)
+    return sum(nbp - (_ppos(kk) + 2 * iA) for iA in range(nb // 2) for kk in range(2 * iA, nb))
+
+
+def xsym_flops(v, naux):
+    """Multiply-add flops of the distinct-tile pass per slice product: 128 x 64
+    tiles over N_aux (the halves it computes but does not store included)."""
+    return 2.0 * xsym_pairs(v) * 128 * 64 * naux
+
+
+def vform_bytes(v, S):
+    """Algorithmic bytes of the V+- formation: the distinct tiles read once
+    (64 x 64 double-single each) and the S-slice V+- planes and their row
+    scales written for every (ab tile, block pair)."""
+    nb = (v + 15) // 16 * 2
+    nbp = _ppos(nb)
+    ntiles = sum(nb - 2 * i for i in range(nb // 2))
+    return nbp * (nbp + 1) / 2 * 4096 * 8 + ntiles * nbp * 2 * (S * 128 * 64 * 2 + 128 * 4)
+
+
 def products(mode, tun):
     """Slice products per multiply-add of a mode (issued tensor flops / F_alg)."""
     if mode == "ozaki":
@@ -403,6 +432,9 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--mode", default="ozaki", choices=["ozaki", "bf16x3", "bf16x6", "fp64"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
+    ap.add_argument("--general-b", action="store_true",
+                    help="error-free mode: do not use the a<->c symmetry of B (the generator's B has it); "
+                         "the general form then runs as the headline")
     ap.add_argument("--no-others", action="store_true", help="skip every comparison mode")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
@@ -526,8 +558,40 @@ def main():
                 "kernel": "ladder_tc_kernel<%d,false,false>" % (2 if mode == "bf16x3" else 3),
                 "note": "achieved = %d x F_alg / fused-kernel time; peak = bf16 sustained (%s)" % (prod, pk_kind)}
 
+    def roofline_sym(tun, xs_ms, fm_ms, p2_ms):
+        """The symmetric-B form's three kernels (distinct tiles, V+- formation,
+        GEMM2) against their peaks; the slowest one is the dominant kernel."""
+        prod = products("ozaki", tun)
+        nS = tun["oz_slices"]
+        peak, hbm = pk["bf16_tflops_sustained"], pk["hbm_gbs"]
+        ax = prod * xsym_flops(w.v, w.naux) / (xs_ms * 1e-3) / 1e12
+        a2 = prod * (F - F1) / (p2_ms * 1e-3) / 1e12
+        bf = vform_bytes(w.v, nS)
+        af = bf / (fm_ms * 1e-3) / 1e9
+        ks = [{"bound": "tensor", "achieved": ax, "peak": peak, "unit": "TFLOP/s", "frac": ax / peak,
+               "traffic": None, "kernel": "oz_xsym_kernel<%d> (distinct integral tiles)" % nS, "kernel_ms": xs_ms,
+               "note": "achieved = %d slice products x 2 x 128 x 64 x N_aux per (row tile, column block "
+                       "pair) computed (%d of them) / CUDA-event time; peak = bf16 sustained (%s)"
+                       % (prod, xsym_pairs(w.v), pk_kind)},
+              {"bound": "hbm", "achieved": af, "peak": hbm, "unit": "GB/s", "frac": af / hbm,
+               "traffic": None, "kernel": "oz_vform_kernel<%d> (V+- formed from the distinct tiles)" % nS,
+               "kernel_ms": fm_ms,
+               "note": "achieved = distinct tiles read once + V+- slices and scales written (%.1f GB) / "
+                       "CUDA-event time; peak = HBM copy (%s)" % (bf / 1e9, pk_kind)},
+              {"bound": "tensor", "achieved": a2, "peak": peak, "unit": "TFLOP/s", "frac": a2 / peak,
+               "traffic": None, "kernel": "oz_gemm2_kernel<%d> (GEMM2 from stored V+-)" % nS, "kernel_ms": p2_ms,
+               "note": "achieved = %d slice products x 2 [P+(o) P+(v)^2 + P-(o) P-(v)^2] / CUDA-event time; "
+                       "peak = bf16 sustained (%s)" % (prod, pk_kind)}]
+        dom = max(ks, key=lambda k: k["kernel_ms"])
+        return dict(dom, kernels=ks)
+
     # ---------------------------------------------------------------- headline
     tuning = plan_tuning(args.mode, args.form)
+    sym = args.mode == "ozaki" and not args.general_b
+    if sym:
+        # the generator symmetrises B^P_ac in a <-> c, as RI factors of real
+        # orbitals are: the plan uses it (and checks it on the device)
+        tuning = dict(tuning or {}, sym_b=1)
     if args.tuning and args.mode != "fp64":
         # explicit overrides, e.g. --tuning flush_every=32,kc=8 or oz_slices=6
         tuning = dict(tuning or {}, **{k: int(v) for k, v in
@@ -543,12 +607,14 @@ def main():
     clocks.start()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    stages, passes = [], []
+    stages, passes, symt = [], [], []
     e0.record(stream)
     for _ in range(args.steps):
         step(L)
         stages.append(lad.ladder_timing(L.plan))  # waits for this step's events
         passes.append(lad.ladder_timing_passes(L.plan))
+        if sym:
+            symt.append(lad.ladder_timing_sym(L.plan))
     e1.record(stream)
     barrier()
     clk = clocks.stop()
@@ -565,7 +631,12 @@ def main():
     two_pass = bool(tun and tun["two_pass"])
     E_val = float(E.item())
     parity = parity_of(E_val)
-    roof = roofline(args.mode, tun, pass1_ms, pass2_ms, ladder_ms, two_pass)
+    if sym:
+        xsym_ms = statistics.mean(f[0] for f in symt)
+        form_ms = statistics.mean(f[1] for f in symt)
+        roof = roofline_sym(tun, xsym_ms, form_ms, pass2_ms)
+    else:
+        roof = roofline(args.mode, tun, pass1_ms, pass2_ms, ladder_ms, two_pass)
     prod = products(args.mode, tun) if tun else 1
 
     # ---------------------------------------------------------------- end to end
@@ -608,6 +679,8 @@ def main():
     extra = {}
     others = []
     if not args.no_others:
+        if sym:
+            others.append("ozaki_general")  # the error-free mode without B's symmetry
         if args.mode != "bf16x6":
             others.append("bf16x6")
         if args.mode in ("ozaki", "bf16x6"):
@@ -629,6 +702,8 @@ def main():
         elif m.endswith("_lambda"):
             Lm = lad.Ladder(w.o, w.v, w.naux, mode=base, device=dev,
                             tuning={**(mt or {}), "two_pass": 1, "lambda_only": 1, "ksplit": 0})
+        elif m == "ozaki_general":
+            Lm = lad.Ladder(w.o, w.v, w.naux, mode=base, device=dev, tuning=mt)
         elif m.endswith("_fused"):
             Lm = lad.Ladder(w.o, w.v, w.naux, mode=base, device=dev,
                             tuning={**(mt or {}), "two_pass": 0, "ksplit": 0})
@@ -759,7 +834,7 @@ def main():
             B_oo = torch.from_numpy(lam * x.B_oo).to(dev)
             e_occ = torch.from_numpy(x.e_occ).to(dev)
             e_vir = torch.from_numpy(x.e_vir).to(dev)
-            Lc = lad.Ladder(w.o, w.v, w.naux, mode="ozaki", device=dev)
+            Lc = lad.Ladder(w.o, w.v, w.naux, mode="ozaki", device=dev, tuning={"sym_b": 1})
             wsc = torch.empty(nb, dtype=torch.uint8, device=dev)
             c0 = time.perf_counter()
             _, _, Ec, itc = lad.ccsd(Lc, Bs, B_ov, B_oo, e_occ, e_vir, tol=1e-10, max_iter=60, workspace=wsc)
@@ -807,7 +882,10 @@ def main():
                "sample": desc, "sample_s": dt, "full_term_s_at_this_rate": full}
 
     if rank == 0:
-        launches = {"ozaki": 9, "fp64": 4}.get(args.mode, 9 if two_pass else 7)
+        # per step: tau; symmetry check (symmetric form), B row scales, B slices,
+        # tau+- slices, the ladder passes (distinct tiles + V+- formation, or
+        # GEMM1), GEMM2, unpack; the two energy kernels
+        launches = 11 if sym else {"ozaki": 9, "fp64": 4}.get(args.mode, 9 if two_pass else 7)
         line = {
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -818,13 +896,16 @@ def main():
             "config": {"workload": args.workload, "o": w.o, "v": w.v, "naux": w.naux,
                        "seed": w.seed, "mode": args.mode, "parallelism": "replicas",
                        "tuning": tun, "slice_products": prod,
-                       "form": None if tun is None else ("two-pass (V+- stored in HBM)" if two_pass
-                                                         else "fused (integral tiles on chip)"),
+                       "form": None if tun is None else (
+                           "symmetric B: distinct integral tiles once, V+- formed from them and stored in HBM"
+                           if sym else "two-pass (V+- stored in HBM)" if two_pass
+                           else "fused (integral tiles on chip)"),
                        "l2": "inputs larger than L2 (B %.2f GB, tau %.2f GB)"
                              % (B.numel() * 8 / 1e9, tau.numel() * 8 / 1e9)},
             "stages_ms": {"prep": prep_ms, "ladder": ladder_ms, "unpack": unpack_ms,
                           "pass1": pass1_ms if two_pass else None,
-                          "pass2": pass2_ms if two_pass else None},
+                          "pass2": pass2_ms if two_pass else None,
+                          "xsym": xsym_ms if sym else None, "vform": form_ms if sym else None},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": launches * args.steps, "parity": parity, "E_L": E_val, "others": extra,
         }
