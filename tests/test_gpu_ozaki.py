@@ -260,3 +260,18 @@ def test_ozaki_symmetric_B_unsupported_combinations(lad):
         lad.ladder_set_tile_range(P, 0, 2)
     assert lad.STATUS[ei.value.status] == "LADDER_ENOTSUP"
     lad.ladder_destroy(P)
+
+
+@pytest.mark.parametrize("chunk", [5, 1])
+def test_ozaki_symmetric_B_tile_ranges(lad, chunk):
+    """Sequential tile ranges: the distinct tiles are formed once, V+- range
+    by range from them; R is bit for bit that of one range."""
+    o, v, n, seed = 7, 41, 70, 14
+    x = synthetic.make_inputs(o, v, n, seed)
+    L = lad.Ladder(o, v, n, mode="ozaki", tuning={"sym_b": 1})
+    _, R1, _ = run_forward(L, x)
+    L.close()
+    L = lad.Ladder(o, v, n, mode="ozaki", tuning={"sym_b": 1, "tile_chunk": chunk})
+    _, R2, _ = run_forward(L, x)
+    L.close()
+    assert np.array_equal(R1, R2)
