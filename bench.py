@@ -273,7 +273,10 @@ def ragged_measure(steps, warmup, mode="bf16x6", fp64=True):
         return e0.elapsed_time(e1) / steps
 
     tuned = mode == "bf16x6"
-    batch = lad.LadderBatch(shapes, mode="tuned" if tuned else mode)
+    # the error-free batch uses each member's a <-> c symmetry of B (the
+    # generator's B has it), and its general form is timed beside it
+    sym = mode == "ozaki"
+    batch = lad.LadderBatch(shapes, mode="tuned" if tuned else mode, sym_b=sym)
     ms = timed(batch)
     parity = ragged_parity(Rs, E)
     ntuned = sum(t is not None for t in batch.tunings)
@@ -281,10 +284,13 @@ def ragged_measure(steps, warmup, mode="bf16x6", fp64=True):
     batch.close()
     del batch
     torch.cuda.empty_cache()
-    default_ms = None
-    if tuned:
+    default_ms = general_ms = None
+    if tuned or sym:
         b2 = lad.LadderBatch(shapes, mode=mode)
-        default_ms = timed(b2)
+        if tuned:
+            default_ms = timed(b2)
+        else:
+            general_ms = timed(b2)
         b2.close()
         del b2
         torch.cuda.empty_cache()
@@ -294,7 +300,9 @@ def ragged_measure(steps, warmup, mode="bf16x6", fp64=True):
            "tuning": "per-member autotuned (cache)" if tuned else "plan defaults",
            "members_tuned": ntuned if tuned else 0, "members_two_pass": ntwo if tuned else None,
            "plan_defaults": None if default_ms is None else
-           {"ms_per_step": default_ms, "tflops": F / (default_ms * 1e-3) / 1e12}}
+           {"ms_per_step": default_ms, "tflops": F / (default_ms * 1e-3) / 1e12},
+           "sym_b": sym, "general_form": None if general_ms is None else
+           {"ms_per_step": general_ms, "tflops": F / (general_ms * 1e-3) / 1e12}}
     if fp64:
         plans = [lad.Ladder(x.o, x.v, x.naux, mode="fp64") for x in mols]
         Es = [torch.empty((), dtype=torch.float64, device=dev) for _ in mols]
@@ -332,9 +340,10 @@ def run_ragged(args):
             "data": "synthetic",
             "config": {"workload": "ragged48", "mode": mode, "molecules": r["molecules"],
                        "falg_total": r["falg_total"], "tuning": r["tuning"], "members_tuned": r["members_tuned"],
-                       "members_two_pass": r["members_two_pass"], "call": r["call"]},
+                       "members_two_pass": r["members_two_pass"], "call": r["call"], "sym_b": r["sym_b"]},
             "parity": r["parity"],
-            "others": {"fp64_48_launches": r.get("fp64_48_launches"), "plan_defaults": r["plan_defaults"]}}
+            "others": {"fp64_48_launches": r.get("fp64_48_launches"), "plan_defaults": r["plan_defaults"],
+                       "general_form": r["general_form"]}}
     print(json.dumps(line), flush=True)
     return 0
 

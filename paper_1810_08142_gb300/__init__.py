@@ -487,12 +487,15 @@ class LadderBatch:
     all molecules' work units, fused or two-pass per molecule, replayed as a
     CUDA graph) plus its workspace."""
 
-    def __init__(self, shapes, mode="bf16x6", device=None, tunings=None):
+    def __init__(self, shapes, mode="bf16x6", device=None, tunings=None, sym_b=False):
         """mode: "bf16x3", "bf16x6", "ozaki" (every member in the error-free
         two-pass form), or "tuned" (BF16X6 with each member's launch
         parameters and form from the autotuner's cache, see tune.py);
         tunings: optional list of per-member dicts of ladder_tuning fields
-        (None entries keep the plan's choice)."""
+        (None entries keep the plan's choice); sym_b (mode "ozaki"; a bool
+        for every member or a list of one per member): the member's B is
+        symmetric in a <-> c, so it forms its distinct integral tiles once
+        (checked on the device, see ladder_tuning)."""
         import torch
         self.shapes = [(int(o), int(v), int(n)) for o, v, n in shapes]
         if mode == "tuned":
@@ -523,6 +526,13 @@ class LadderBatch:
                     t.two_pass = 0
                     ladder_set_member_tuning(self.plan, k, t)
                     self.tunings.append(t.as_dict())
+            sym = [bool(x) for x in sym_b] if isinstance(sym_b, (list, tuple)) else [bool(sym_b)] * len(self.shapes)
+            if any(sym):
+                if m != LADDER_OZAKI:
+                    raise ValueError("sym_b applies to the error-free mode")
+                for k, on in enumerate(sym):
+                    if on:
+                        ladder_set_member_tuning(self.plan, k, Tuning(sym_b=1))
             n = ladder_workspace_size(self.plan)
             self.workspace = torch.empty(max(n, 256), dtype=torch.uint8, device=self.device)
             ladder_set_workspace(self.plan, self.workspace)

@@ -308,11 +308,12 @@ uint32_t oz_smem_bytes(int pass, int nslices);
 cudaError_t oz_init_attributes(int nslices);
 cudaError_t launch_oz_vstore(const OzLaunch &L, int nslices, cudaStream_t s);
 cudaError_t launch_oz_gemm2(const OzLaunch &L, int nslices, cudaStream_t s);
-// Symmetric B: the distinct integral tiles (one CTA per unit of one.xunits),
-// V+- of a tile range formed and sliced from them (nunits = tiles x block
-// pairs), and the bitwise check B^P_ac = B^P_ca.
+// Symmetric B: the distinct integral tiles (one CTA per unit of xunits), V+-
+// of a tile range formed and sliced from them (units = tiles x block pairs),
+// a single molecule (`one`) or a batch (mols / items) each, and the bitwise
+// check B^P_ac = B^P_ca.
 cudaError_t launch_oz_xsym(const OzLaunch &L, int nslices, cudaStream_t s);
-cudaError_t launch_oz_vform(const OzArgs &a, int nunits, int nslices, int sm_count, cudaStream_t s);
+cudaError_t launch_oz_vform(const OzLaunch &L, int nslices, int sm_count, cudaStream_t s);
 void launch_oz_symcheck(int N, int v, const double *B, int *status, cudaStream_t s);
 
 // One launch of the fused kernel: a single molecule (mols == nullptr, the

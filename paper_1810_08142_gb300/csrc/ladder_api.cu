@@ -139,6 +139,9 @@ struct ladder_plan_s {
   // two-pass members: storing-pass and GEMM2-pass work units, unpack blocks
   std::vector<int2> items1, items2, tcs2;
   size_t off_mols1 = 0, off_mols2 = 0, off_items1 = 0, off_items2 = 0, off_tcs2 = 0;
+  // symmetric-B error-free members: distinct-tile and V+- formation work units
+  std::vector<int2> itemsX, itemsF;
+  size_t off_itemsX = 0, off_itemsF = 0;
   size_t off_oz1 = 0, off_oz2 = 0;  // error-free batch: OzArgs tables of the two passes
   cudaStream_t cap_stream = nullptr;
   // ladder_apply_host: a side stream for the tau upload and its preparation,
@@ -1208,11 +1211,15 @@ ladder_status ladder_set_workspace(ladder_plan_t pl, void *dptr, size_t bytes) {
       sp->ws_bytes = sp->lay.total;
       const ladder_status st = encode_maps(sp, static_cast<char *>(sp->ws));
       if (st != LADDER_OK) return st;
+      if (sp->sym_b && cudaMemcpy(static_cast<char *>(sp->ws) + sp->lay.ozXu, sp->xunits.data(),
+                                  sp->xunits.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess)
+        return cuda_status(cudaErrorUnknown);
     }
     // work lists of the batched launches
     const std::pair<size_t, const std::vector<int2> *> lists[] = {
         {pl->off_items, &pl->items},   {pl->off_tcs, &pl->tcs},     {pl->off_items1, &pl->items1},
-        {pl->off_items2, &pl->items2}, {pl->off_tcs2, &pl->tcs2}};
+        {pl->off_items2, &pl->items2}, {pl->off_tcs2, &pl->tcs2},   {pl->off_itemsX, &pl->itemsX},
+        {pl->off_itemsF, &pl->itemsF}};
     for (const auto &li : lists)
       if (!li.second->empty() &&
           cudaMemcpy(w + li.first, li.second->data(), li.second->size() * sizeof(int2),
@@ -1566,10 +1573,13 @@ static ladder_status apply_oz(ladder_plan_t pl, const double *B, const double *t
     a1.ntiles = a2.ntiles = cnt;
     a1.nitems = cnt * pl->vsplit;
     a2.nitems = cnt * a2.nchunks * pl->ksplit;
-    if (sym)
-      st = cuda_status(launch_oz_vform(a1, cnt * pl->nbp, pl->S, pl->sm_count, s));
-    else
+    if (sym) {
+      OzArgs af = a1;
+      af.nitems = cnt * pl->nbp;
+      st = cuda_status(launch_oz_vform(oz_launch(af), pl->S, pl->sm_count, s));
+    } else {
       st = cuda_status(launch_oz_vstore(oz_launch(a1), pl->S, s));
+    }
     if (one) mark(pl, 4, s);
     if (st == LADDER_OK && side_done && r0 == 0) st = cuda_status(cudaStreamWaitEvent(s, side_done, 0));
     if (st == LADDER_OK) st = cuda_status(launch_oz_gemm2(oz_launch(a2), pl->S, s));
@@ -1919,10 +1929,19 @@ static void batch_finalize(ladder_plan_s *pl) {
                    [](const std::pair<double, int> &x, const std::pair<double, int> &y) {
                      return x.first > y.first;
                    });
+  pl->itemsX.clear();
+  pl->itemsF.clear();
   for (auto &t : twopass) {
     const ladder_plan_s *sp = pl->subs[t.second];
     const int m = t.second;
-    for (int k = 0; k < sp->ntiles_tc * sp->vsplit; ++k) pl->items1.push_back(make_int2(m, k));
+    if (sp->sym_b) {
+      // symmetric-B error-free member: its distinct tiles and V+- formation
+      // take the place of the storing pass
+      for (int k = 0; k < (int)sp->xunits.size(); ++k) pl->itemsX.push_back(make_int2(m, k));
+      for (int k = 0; k < sp->ntiles_tc * sp->nbp; ++k) pl->itemsF.push_back(make_int2(m, k));
+    } else {
+      for (int k = 0; k < sp->ntiles_tc * sp->vsplit; ++k) pl->items1.push_back(make_int2(m, k));
+    }
     for (int k = 0; k < sp->ntiles_tc * (int)sp->chunks_v.size() * sp->ksplit; ++k)
       pl->items2.push_back(make_int2(m, k));
     for (int k = 0; k < sp->ntiles_tc * sp->nplus; ++k) pl->tcs2.push_back(make_int2(m, k));
@@ -1944,6 +1963,8 @@ static void batch_finalize(ladder_plan_s *pl) {
   region(pl->off_items1, pl->items1.size() * sizeof(int2));
   region(pl->off_items2, pl->items2.size() * sizeof(int2));
   region(pl->off_tcs2, pl->tcs2.size() * sizeof(int2));
+  region(pl->off_itemsX, pl->itemsX.size() * sizeof(int2));
+  region(pl->off_itemsF, pl->itemsF.size() * sizeof(int2));
   for (auto *sp : pl->subs) {
     off = align_up(off, 1024);
     pl->sub_off.push_back(off);
@@ -2021,7 +2042,23 @@ ladder_status ladder_plan_batched(int n, const int *o, const int *v, const int *
 
 ladder_status ladder_set_member_tuning(ladder_plan_t pl, int m, const ladder_tuning *t) {
   if (!pl || !t || !pl->batched || pl->ws || m < 0 || m >= (int)pl->subs.size()) return LADDER_EINVAL;
-  if (pl->mode == LADDER_OZAKI) return LADDER_ENOTSUP;
+  if (pl->mode == LADDER_OZAKI) {
+    // an error-free member takes only sym_b; its slices, form and splits
+    // are the batch's
+    if (t->sym_b != 0 && t->sym_b != 1) return LADDER_EINVAL;
+    ladder_plan_s *sp = pl->subs[m];
+    if (t->sym_b && (double)xsym_bytes(sp) > kXsymCap) return LADDER_ENOTSUP;
+    double tot = 0.0;
+    for (auto *q : pl->subs)
+      tot += member_vbytes(q) + ((q == sp ? t->sym_b : q->sym_b) ? (double)xsym_bytes(q) : 0.0);
+    if (tot > kVStoreOzCap) return LADDER_ENOTSUP;
+    sp->sym_b = t->sym_b;
+    sp->xunits = sp->sym_b ? make_xunits(sp->nb) : std::vector<int4>();
+    compute_layout(sp);
+    batch_finalize(pl);
+    return LADDER_OK;
+  }
+  if (t->sym_b != 0) return LADDER_EINVAL;
   if (t->kc < 1 || t->kc > 64 || !(t->s_pieces == 1 || t->s_pieces == 2 || t->s_pieces == 4) ||
       t->flush_every < 1 || t->flush_every > 4096 || (t->xy_split != 0 && t->xy_split != 1) ||
       (t->two_pass != 0 && t->two_pass != 1) || t->lambda_only != 0)
@@ -2143,6 +2180,7 @@ static ladder_status batch_run(ladder_plan_t pl, const double *const *B, const d
       const ladder_plan_s *sp = pl->subs[m];
       if (step) launch_tau(sp->o, sp->v, t1[m], t2[m], tau[m], c);
       if (oz) {
+        if (sp->sym_b) launch_oz_symcheck(sp->N, sp->v, B[m], status, c);
         oz_prep(sp, B[m], tau[m], status, c);
         continue;
       }
@@ -2161,6 +2199,8 @@ static ladder_status batch_run(ladder_plan_t pl, const double *const *B, const d
         Lz.timeout_ns = tmax;
         return Lz;
       };
+      launch_oz_xsym(oz_batch(pl->off_oz1, pl->off_itemsX, (int)pl->itemsX.size()), pl->S, c);
+      launch_oz_vform(oz_batch(pl->off_oz1, pl->off_itemsF, (int)pl->itemsF.size()), pl->S, pl->sm_count, c);
       launch_oz_vstore(oz_batch(pl->off_oz1, pl->off_items1, (int)pl->items1.size()), pl->S, c);
       launch_oz_gemm2(oz_batch(pl->off_oz2, pl->off_items2, (int)pl->items2.size()), pl->S, c);
     }

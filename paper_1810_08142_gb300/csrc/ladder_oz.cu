@@ -624,7 +624,7 @@ __device__ __forceinline__ size_t xaddr(int a, int c, int b, int d, int nbp) {
 // not stored (their transposes are the tiles (q, r)), and nor is the half
 // (2 iA + 1, 2 iA) of the row tile kk = 2 iA (the half (2 iA, 2 iA + 1) of the
 // row tile kk = 2 iA + 1 holds it).
-template <int S>
+template <int S, bool kBatch>
 __global__ void __launch_bounds__(kThreads, 1) oz_xsym_kernel(const __grid_constant__ OzLaunch Lp) {
   using C = Cfg1<S>;
   static_assert(C::kStages >= 3 && 8 * (2 * C::kStages + Bars::kCount) + 8 <= 256, "ring");
@@ -637,7 +637,6 @@ __global__ void __launch_bounds__(kThreads, 1) oz_xsym_kernel(const __grid_const
   uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(smem + C::kRing + 8 * (2 * C::kStages + Bars::kCount));
   int *abort_flag = reinterpret_cast<int *>(tmem_holder + 1);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const OzArgs &A = Lp.one;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::kStages; ++s) {
@@ -661,7 +660,6 @@ __global__ void __launch_bounds__(kThreads, 1) oz_xsym_kernel(const __grid_const
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
   const Watchdog wd{Lp.status, abort_flag, Lp.timeout_ns};
-  const int nwin = (A.nks + kOzKc - 1) / kOzKc;
 
   if (warp == 0) {
     // ================================================================ TMA producer
@@ -669,10 +667,13 @@ __global__ void __launch_bounds__(kThreads, 1) oz_xsym_kernel(const __grid_const
       int stage = 0;
       uint32_t phase = 0, armed = 0, armed_par = 0;
       bool ok = true;
-      tma_prefetch_desc(&A.tmA);
-      tma_prefetch_desc(&A.tmB);
       for (int u = blockIdx.x; ok && u < Lp.nitems; u += gridDim.x) {
-        const int4 U = A.xunits[u];
+        int local;
+        const OzArgs &A = oz_args<kBatch>(Lp, u, local);
+        const int4 U = A.xunits[local];
+        const int nwin = (A.nks + kOzKc - 1) / kOzKc;
+        tma_prefetch_desc(&A.tmA);
+        tma_prefetch_desc(&A.tmB);
         for (int q = U.z; ok && q < U.w; q += 2) {
           const int ntile = min(2, U.w - q);
           for (int w = 0; ok && w < nwin; ++w)
@@ -712,7 +713,10 @@ __global__ void __launch_bounds__(kThreads, 1) oz_xsym_kernel(const __grid_const
       const uint32_t id64 = idesc_bf16(128, 64);
       bool ok = true;
       for (int u = blockIdx.x; ok && u < Lp.nitems; u += gridDim.x) {
-        const int4 U = A.xunits[u];
+        int local;
+        const OzArgs &A = oz_args<kBatch>(Lp, u, local);
+        const int4 U = A.xunits[local];
+        const int nwin = (A.nks + kOzKc - 1) / kOzKc;
         for (int q = U.z; ok && q < U.w; q += 2) {
           const int ntile = min(2, U.w - q);
           for (int w = 0; ok && w < nwin; ++w)
@@ -766,7 +770,10 @@ __global__ void __launch_bounds__(kThreads, 1) oz_xsym_kernel(const __grid_const
     uint32_t use[2] = {0, 0};
     bool ok = true;
     for (int u = blockIdx.x; ok && u < Lp.nitems; u += gridDim.x) {
-      const int4 U = A.xunits[u];
+      int local;
+      const OzArgs &A = oz_args<kBatch>(Lp, u, local);
+      const int4 U = A.xunits[local];
+      const int nwin = (A.nks + kOzKc - 1) / kOzKc;
       const int a = U.x * 16 + a_l, c = U.y * CB + x_l;
       const int r = ppos(U.y) + 2 * U.x + h;  // row block pair (2 iA + h, kk)
       const bool dup = h == 1 && U.y == 2 * U.x;
@@ -822,18 +829,21 @@ __global__ void __launch_bounds__(kThreads, 1) oz_xsym_kernel(const __grid_const
 
 // V+- of every (ab tile, block pair) of the plan's tile range from the
 // distinct integral tiles: X[(a, c), (b, d)] = (ac|bd) and Y'[(a, c), (b, d)]
-// = (ad|bc) read straight from them, then vpm_store as in pass 1.  Work unit u
-// = (local tile u / nbp, block pair u % nbp); 512 threads, each the ab rows
+// = (ad|bc) read straight from them, then vpm_store as in pass 1.  Local work
+// unit (of a molecule of a batch, or of `one`) = (local tile / nbp, block
+// pair % nbp); 512 threads, each the ab rows
 // (a = A0 + L / 8, b = B0 + 2 qw + j) and the slot row c = 8 k + L % 8, as
 // pass 1's conversion warps.
-template <int S>
-__global__ void __launch_bounds__(512) oz_vform_kernel(const OzArgs A, int nunits) {
+template <int S, bool kBatch>
+__global__ void __launch_bounds__(512) oz_vform_kernel(const __grid_constant__ OzLaunch Lp) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int L = (warp & 3) * 32 + lane, qw = warp >> 2;
   const int a_l = L >> 3, x_l = L & 7;
-  const float2 *__restrict__ Xs = A.Xs;
-  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
-    const int t = u / A.nbp, p = u - t * A.nbp;
+  for (int u = blockIdx.x; u < Lp.nitems; u += gridDim.x) {
+    int local;
+    const OzArgs &A = oz_args<kBatch>(Lp, u, local);
+    const float2 *__restrict__ Xs = A.Xs;
+    const int t = local / A.nbp, p = local - t * A.nbp;
     int iA = 0, tr = t + A.tile0;
     while (tr >= A.nB8 - 2 * iA) {
       tr -= A.nB8 - 2 * iA;
@@ -1336,7 +1346,8 @@ cudaError_t oz_attrs() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(oz_vstore_kernel<S, true>, at, (int)Cfg1<S>::kSmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(oz_gemm2_kernel<S, false>, at, (int)Cfg2<S>::kSmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(oz_gemm2_kernel<S, true>, at, (int)Cfg2<S>::kSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(oz_xsym_kernel<S>, at, (int)Cfg1<S>::kSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(oz_xsym_kernel<S, false>, at, (int)Cfg1<S>::kSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(oz_xsym_kernel<S, true>, at, (int)Cfg1<S>::kSmem);
   return e;
 }
 
@@ -1380,20 +1391,37 @@ cudaError_t launch_oz_gemm2(const OzLaunch &L, int nslices, cudaStream_t s) {
 // one CTA per work unit of the distinct integral tiles
 cudaError_t launch_oz_xsym(const OzLaunch &L, int nslices, cudaStream_t s) {
   if (L.nitems <= 0) return cudaSuccess;
-  if (nslices == 5)
-    oz_xsym_kernel<5><<<L.nitems, kThreads, Cfg1<5>::kSmem, s>>>(L);
-  else
-    oz_xsym_kernel<6><<<L.nitems, kThreads, Cfg1<6>::kSmem, s>>>(L);
+  const bool b = L.mols != nullptr;
+  if (nslices == 5) {
+    if (b)
+      oz_xsym_kernel<5, true><<<L.nitems, kThreads, Cfg1<5>::kSmem, s>>>(L);
+    else
+      oz_xsym_kernel<5, false><<<L.nitems, kThreads, Cfg1<5>::kSmem, s>>>(L);
+  } else {
+    if (b)
+      oz_xsym_kernel<6, true><<<L.nitems, kThreads, Cfg1<6>::kSmem, s>>>(L);
+    else
+      oz_xsym_kernel<6, false><<<L.nitems, kThreads, Cfg1<6>::kSmem, s>>>(L);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_oz_vform(const OzArgs &a, int nunits, int nslices, int sm_count, cudaStream_t s) {
-  if (nunits <= 0) return cudaSuccess;
-  const int grid = std::min(nunits, 2 * sm_count);
-  if (nslices == 5)
-    oz_vform_kernel<5><<<grid, 512, 0, s>>>(a, nunits);
-  else
-    oz_vform_kernel<6><<<grid, 512, 0, s>>>(a, nunits);
+// two blocks per SM, each walking the units
+cudaError_t launch_oz_vform(const OzLaunch &L, int nslices, int sm_count, cudaStream_t s) {
+  if (L.nitems <= 0) return cudaSuccess;
+  const int grid = std::min(L.nitems, 2 * sm_count);
+  const bool b = L.mols != nullptr;
+  if (nslices == 5) {
+    if (b)
+      oz_vform_kernel<5, true><<<grid, 512, 0, s>>>(L);
+    else
+      oz_vform_kernel<5, false><<<grid, 512, 0, s>>>(L);
+  } else {
+    if (b)
+      oz_vform_kernel<6, true><<<grid, 512, 0, s>>>(L);
+    else
+      oz_vform_kernel<6, false><<<grid, 512, 0, s>>>(L);
+  }
   return cudaGetLastError();
 }
 

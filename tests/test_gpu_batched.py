@@ -229,16 +229,19 @@ def test_ragged48_step_energies(lad):
     batch.close()
 
 
-def test_step_batched_ozaki(lad):
+@pytest.mark.parametrize("sym", ["general", "symmetric", "mixed"])
+def test_step_batched_ozaki(lad, sym):
     """The error-free mode as a batch: every member in the two-pass form, both
     passes over all members' work units in one launch each, inside one graph
     with tau and E_L.  R within 1e-10 relative (worst element within 2e-10 of
     max |R|), |dE_L| <= 1 uEh and within 1e-12 of the sum of the energy
-    terms' magnitudes, and a replay bitwise equal."""
+    terms' magnitudes, and a replay bitwise equal.  symmetric: every member
+    forms its distinct integral tiles once (sym_b); mixed: every other one."""
     import torch
     shapes = SHAPES + TWO_PASS_SHAPES[:2] + [(12, 140, 150, 21)]
     mols = [synthetic.make_inputs(o, v, n, s) for o, v, n, s in shapes]
-    batch = lad.LadderBatch([(x.o, x.v, x.naux) for x in mols], mode="ozaki")
+    flags = {"general": False, "symmetric": True, "mixed": [k % 2 == 1 for k in range(len(mols))]}[sym]
+    batch = lad.LadderBatch([(x.o, x.v, x.naux) for x in mols], mode="ozaki", sym_b=flags)
     Bs, t1s, t2s = ([to_dev(getattr(x, a)) for x in mols] for a in ("B", "t1", "t2"))
     taus, Rs, E = batch.step(Bs, t1s, t2s)
     torch.cuda.synchronize()
@@ -262,18 +265,20 @@ def test_step_batched_ozaki(lad):
     batch.close()
 
 
-def test_ragged48_ozaki_against_stored_oracle(lad):
+@pytest.mark.parametrize("sym_b", [False, True])
+def test_ragged48_ozaki_against_stored_oracle(lad, sym_b):
     """The 48-molecule ragged batch in the error-free mode through
     ladder_step_batched: every member's E_L within 1 uEh of the stored oracle
     value (tests/golden/ragged48.json, written by make_golden.py --ragged)
-    and four stored R columns per member within 1e-10."""
+    and four stored R columns per member within 1e-10; with sym_b every
+    member forms its distinct integral tiles once."""
     import json
     import torch
     with open(os.path.join(os.path.dirname(__file__), "golden", "ragged48.json")) as f:
         gold = json.load(f)["molecules"]
     mols = synthetic.ragged_batch()
     assert len(gold) == len(mols)
-    batch = lad.LadderBatch([(x.o, x.v, x.naux) for x in mols], mode="ozaki")
+    batch = lad.LadderBatch([(x.o, x.v, x.naux) for x in mols], mode="ozaki", sym_b=sym_b)
     Bs, t1s, t2s = ([to_dev(getattr(x, a)) for x in mols] for a in ("B", "t1", "t2"))
     taus, Rs, E = batch.step(Bs, t1s, t2s)
     torch.cuda.synchronize()
@@ -286,7 +291,7 @@ def test_ragged48_ozaki_against_stored_oracle(lad):
         R = Rs[k]
         got = np.stack([R[:, :, a, b].cpu().numpy() for a, b in zip(g["pairs_a"], g["pairs_b"])])
         worst_R = max(worst_R, rel_err(got, np.array(g["R_cols"])))
-    print("ragged48 ozaki: worst |dE_L| %.3e Eh, worst column rel err %.3e" % (worst_E, worst_R))
+    print("ragged48 ozaki (sym_b %s): worst |dE_L| %.3e Eh, worst column rel err %.3e" % (sym_b, worst_E, worst_R))
     assert worst_E <= 1e-6
     assert worst_R < 1e-10
     batch.close()
