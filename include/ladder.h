@@ -357,8 +357,14 @@ ladder_status ladder_plan_batched(int n, const int *o, const int *v, const int *
  * ladder_tuning (ksplit is the plan's own; lambda_only must be 0).  A member
  * moved to the two-pass form must keep the batch's stored tiles within the
  * batch cap (else LADDER_ENOTSUP).  The autotuner's per-shape choices are
- * applied to a batch through this call.  A LADDER_OZAKI batch has no member
- * tuning (LADDER_ENOTSUP). */
+ * applied to a batch through this call.  A member of a LADDER_OZAKI batch
+ * takes only sym_b (the other fields are ignored; 0 or 1, else
+ * LADDER_EINVAL): 1 promises that member's B symmetric in a <-> c, and the
+ * batch then forms its distinct integral tiles once and its V+- from them
+ * (checked on the device as for a single plan).  Its distinct tiles count
+ * toward the 200 GiB cap with the stored slices, and above 96 GiB for one
+ * member the call returns LADDER_ENOTSUP.  The other modes return
+ * LADDER_EINVAL for sym_b != 0. */
 ladder_status ladder_set_member_tuning(ladder_plan_t plan, int m, const ladder_tuning *t);
 
 /* B[k], tau[k], R[k] are device pointers for molecule k (host arrays of n
