@@ -1159,14 +1159,17 @@ __global__ void oz_rowscale_kernel(int N, int v, int vp, const double *__restric
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= vp * vp) return;
   const int a = idx / vp, c = idx % vp;
-  double m = 0.0;
-  bool bad = false;
+  // the largest |B^P_ac| as the largest magnitude bit pattern (the order of
+  // non-negative doubles), and NaN or infinity as an all-ones exponent: both
+  // on the integer pipe
+  unsigned long long mb = 0;
   if (a < v && c < v)
     for (int P = 0; P < N; ++P) {
-      const double x = B[((size_t)P * v + a) * v + c];
-      bad |= !isfinite(x);
-      m = fmax(m, fabs(x));
+      const unsigned long long x = (unsigned long long)__double_as_longlong(B[((size_t)P * v + a) * v + c]);
+      mb = max(mb, x & 0x7fffffffffffffffull);
     }
+  const bool bad = mb >= 0x7ff0000000000000ull;
+  const double m = __longlong_as_double((long long)mb);
   if (bad) record_status(status, kSiteNonFinite);
   float r = 0.f;
   if (m > 0.0 && !bad) {
@@ -1216,8 +1219,13 @@ __global__ void oz_split_B_kernel(int N, int v, int vp, int Np, const double *__
     const int c = c0 + r, P = P0 + tx;
     if (c < vp && P < Np) {
       const float sc = rs[(size_t)a * vp + c];
+      // 1 / sc exactly (sc is a power of two): built from its exponent for a
+      // normal sc, which spares the FP64 division; a subnormal sc divides
+      const int eb = (__float_as_int(sc) >> 23) & 0xff;
+      const double inv = eb ? __longlong_as_double((long long)(1023 + 127 - eb) << 52)
+                            : (sc > 0.f ? 1.0 / (double)sc : 0.0);
       __nv_bfloat16 sl[S];
-      fixed_slices<S>(sc > 0.f ? tile[tx][r] / (double)sc : 0.0, sl);
+      fixed_slices<S>(tile[tx][r] * inv, sl);
       const size_t off = ((size_t)a * vp + c) * Np + P;
 #pragma unroll
       for (int q = 0; q < S; ++q) Bt[q * slice + off] = sl[q];
