@@ -834,6 +834,28 @@ __global__ void __launch_bounds__(kThreads, 1) oz_xsym_kernel(const __grid_const
 // pair % nbp); 512 threads, each the ab rows
 // (a = A0 + L / 8, b = B0 + 2 qw + j) and the slot row c = 8 k + L % 8, as
 // pass 1's conversion warps.
+// The 8 values of one thread: (a c | b d) (y = false) or (a d | b c) (y =
+// true) for d = d0 .. d0 + 7.  Where the tile holds them at 8 consecutive
+// places (the thread's own 64 bytes) they come in four 16-byte loads; else
+// (the lanes of the warp hold consecutive places) one 8-byte load each.
+__device__ __forceinline__ void vf_gather(const float2 *__restrict__ Xs, int nbp, int a, int c, int b, int d0, bool y,
+                                          float2 (&v)[8]) {
+  const size_t p0 = y ? xaddr(a, d0, b, c, nbp) : xaddr(a, c, b, d0, nbp);
+  const size_t p7 = y ? xaddr(a, d0 + 7, b, c, nbp) : xaddr(a, c, b, d0 + 7, nbp);
+  if (p7 == p0 + 7) {
+    const float4 *q = reinterpret_cast<const float4 *>(Xs + p0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float4 t = __ldg(q + i);
+      v[2 * i] = make_float2(t.x, t.y);
+      v[2 * i + 1] = make_float2(t.z, t.w);
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = __ldg(Xs + (y ? xaddr(a, d0 + e, b, c, nbp) : xaddr(a, c, b, d0 + e, nbp)));
+  }
+}
+
 template <int S, bool kBatch>
 __global__ void __launch_bounds__(512) oz_vform_kernel(const __grid_constant__ OzLaunch Lp) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -859,12 +881,8 @@ __global__ void __launch_bounds__(512) oz_vform_kernel(const __grid_constant__ O
     for (int j = 0; j < 2; ++j) {
       const int b = B0 + 2 * qw + j;
       float2 X[8], Y[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int d = l * CB + e;
-        X[e] = __ldg(Xs + xaddr(a, c, b, d, A.nbp));
-        Y[e] = __ldg(Xs + xaddr(a, d, b, c, A.nbp));
-      }
+      vf_gather(Xs, A.nbp, a, c, b, l * CB, false, X);  // (a c | b d), d = 8 l + e
+      vf_gather(Xs, A.nbp, a, c, b, l * CB, true, Y);   // (a d | b c)
       vpm_store<S>(X, Y, vbase, sbase, a_l * 8 + 2 * qw + j, x_l);
     }
   }
