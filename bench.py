@@ -668,6 +668,17 @@ def main():
             return float(E.item())
 
         e2e_step()
+        # the pinned copy rates this box gives (outside the timed region):
+        # the e2e number moves with them from box to box
+        c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        c0.record(stream)
+        d_B.copy_(h_B, non_blocking=True)
+        c1.record(stream)
+        h_R.copy_(d_R, non_blocking=True)
+        c2.record(stream)
+        torch.cuda.synchronize()
+        copy_gbs = {"h2d_GBps": h_B.numel() * 8 / (c0.elapsed_time(c1) * 1e-3) / 1e9,
+                    "d2h_GBps": h_R.numel() * 8 / (c1.elapsed_time(c2) * 1e-3) / 1e9}
         barrier()
         q0 = time.perf_counter()
         for _ in range(args.steps):
@@ -678,7 +689,8 @@ def main():
                "h2d_bytes_per_step": (h_B.numel() + h_tau.numel()) * 8,
                "d2h_bytes_per_step": h_R.numel() * 8 + 8, "ms_per_step": ems,
                "call": "ladder_apply_host (B, tau in; R out; synchronises) + ladder_energy",
-               "R_host_matches_device": bool(torch.equal(h_R, R.cpu())), "E_L": E_e2e}
+               "R_host_matches_device": bool(torch.equal(h_R, R.cpu())), "E_L": E_e2e,
+               "pinned_copy_rates": copy_gbs}
         del d_B, d_tau, d_R, h_B, h_tau, h_R
     L.close()
     del L
