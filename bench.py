@@ -718,7 +718,9 @@ def main():
         base = m.split("_")[0]
         mt = plan_tuning(base) if base != "fp64" else None
         if m.endswith("_dressed"):
-            Lm = lad.Ladder(w.o, w.v, w.naux, mode=base, device=dev, tuning=tun, dressed=True)
+            # the dressed term's B - mbar is not symmetric: the general form
+            Lm = lad.Ladder(w.o, w.v, w.naux, mode=base, device=dev, tuning=dict(tun or {}, sym_b=0) if tun else None,
+                            dressed=True)
             B_ov = torch.from_numpy(x.B_ov).to(dev)
         elif m.endswith("_lambda"):
             Lm = lad.Ladder(w.o, w.v, w.naux, mode=base, device=dev,
