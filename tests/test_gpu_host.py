@@ -11,7 +11,7 @@ from gpu_util import rel_err
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "ozaki": 1e-10, "bf16x6": 1e-6}
+TOL = {"fp64": 1e-12, "ozaki": 1e-10, "ozaki_sym": 1e-10, "bf16x6": 1e-6}
 
 
 @pytest.fixture(scope="module")
@@ -24,14 +24,16 @@ def lad():
 
 
 @pytest.mark.parametrize("pinned", [True, False])
-@pytest.mark.parametrize("mode", ["fp64", "ozaki", "bf16x6"])
+@pytest.mark.parametrize("mode", ["fp64", "ozaki", "ozaki_sym", "bf16x6"])
 def test_apply_host_matches_oracle(lad, mode, pinned):
+    """ozaki_sym: the error-free mode's symmetric-B form (the bench's e2e call)."""
     import torch
     o, v, n, seed = 7, 41, 70, 14
     x = synthetic.make_inputs(o, v, n, seed)
     tau = oracle.tau(x.t1, x.t2)
     R_o = oracle.ladder(x.B, tau)
-    L = lad.Ladder(o, v, n, mode=mode)
+    L = lad.Ladder(o, v, n, mode="ozaki" if mode == "ozaki_sym" else mode,
+                   tuning={"sym_b": 1} if mode == "ozaki_sym" else None)
     h_B, h_tau = torch.from_numpy(x.B), torch.from_numpy(tau)
     h_R = torch.full_like(h_tau, float("nan"))
     if pinned:
