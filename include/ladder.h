@@ -83,8 +83,8 @@ typedef enum {
  * tile_chunk in ladder_tuning).  With sym_b set in ladder_tuning (B^P_ac =
  * B^P_ca, the RI factors of real orbitals) it forms each distinct integral
  * tile once instead of GEMM1 per (ab tile, block pair).  ladder_backward
- * returns LADDER_ENOTSUP.  ladder_apply_dressed runs its correction in FP64
- * in this mode. */
+ * gives dtau only, with sym_b (see there).  ladder_apply_dressed runs its
+ * correction in FP64 in this mode. */
 
 /* OR this into `mode` to size the workspace for ladder_backward as well
  * (the FP64 gradient with respect to B spills tiles of Gamma^{xb}_{yd}). */
@@ -287,7 +287,11 @@ ladder_status ladder_energy_noalloc(int o, int v, const double *R, const double 
  * under the pair symmetry of W and tau) as Gamma^{xb}_{yd} = sum_ij W_ij^{xb}
  * tau_ij^{yd} tiles contracted with B^P_bd; it needs a plan created with
  * LADDER_WITH_BACKWARD (else LADDER_EWORKSPACE).  Either output may be NULL
- * to skip it.  Outputs are overwritten.  dtau may not alias W or tau. */
+ * to skip it.  Outputs are overwritten.  dtau may not alias W or tau.
+ * LADDER_OZAKI plans give dtau only, and only with sym_b: B^P symmetric makes
+ * the transposed ladder the ladder itself, so dtau is the error-free forward
+ * of W (FP64-class, no LADDER_WITH_BACKWARD needed); dB or a plan without
+ * sym_b returns LADDER_ENOTSUP. */
 ladder_status ladder_backward(ladder_plan_t plan, const double *B, const double *tau,
                               const double *W, double *dtau, double *dB, void *stream);
 

@@ -8,9 +8,12 @@ W = 2 t2 - t2^T (ladder_pair_combine):
     dE/dt2  = 2 R - R^T                         (ladder_pair_combine)
 Both ladder_backward terms run in the mode of the plan that serves the
 backward: the forward plan itself (FP64, BF16X3 or BF16X6), or a separate
-`grad_ladder`.  The error-free mode has no adjoint of its own, so an
+`grad_ladder`.  The error-free mode has no dE/dB of its own, so an
 error-free forward plan (E_L and R to FP64 class) takes a BF16X6 or FP64
-grad_ladder created with backward=True; dE/dt2 comes from the forward's R.
+grad_ladder created with backward=True for dE/dB; when that forward plan
+has sym_b (B symmetric in a <-> c), the transposed ladder is the ladder
+itself and dE/dtau comes from the forward plan, error-free, instead.
+dE/dt2 comes from the forward's R.
 All arithmetic runs in the library's kernels; the incoming gradient (a
 scalar) is applied with an in-place multiply.
 """
@@ -18,7 +21,11 @@ from __future__ import annotations
 
 import torch
 
-from . import Ladder, ladder_pair_combine
+from . import LADDER_OZAKI, Ladder, ladder_get_tuning, ladder_pair_combine
+
+
+def _error_free_symmetric(L: Ladder) -> bool:
+    return L.mode == LADDER_OZAKI and ladder_get_tuning(L.plan).sym_b == 1
 
 
 class LadderEnergy(torch.autograd.Function):
@@ -28,17 +35,25 @@ class LadderEnergy(torch.autograd.Function):
         E = ladder.energy(R, t2)
         ctx.save_for_backward(B, tau, t2, R)
         ctx.ladder = ladder if grad_ladder is None else grad_ladder
+        # an error-free forward with symmetric B serves dE/dtau itself
+        ctx.tau_ladder = ladder if _error_free_symmetric(ladder) else ctx.ladder
         return E
 
     @staticmethod
     def backward(ctx, gE):
         B, tau, t2, R = ctx.saved_tensors
-        L = ctx.ladder
+        L, Lt = ctx.ladder, ctx.tau_ladder
         need_B, need_tau, need_t2 = ctx.needs_input_grad[:3]
         dB = dtau = dt2 = None
         if need_B or need_tau:
             W = L.weights(t2)
-            dtau, dB = L.backward(B, tau, W, dtau=bool(need_tau), dB=bool(need_B))
+            if Lt is L:
+                dtau, dB = L.backward(B, tau, W, dtau=bool(need_tau), dB=bool(need_B))
+            else:
+                if need_tau:
+                    dtau, _ = Lt.backward(B, tau, W, dtau=True, dB=False)
+                if need_B:
+                    _, dB = L.backward(B, tau, W, dtau=False, dB=True)
         if need_t2:
             dt2 = torch.empty_like(t2)
             ladder_pair_combine(L.o, L.v, 2.0, -1.0, R, dt2)

@@ -1703,8 +1703,14 @@ ladder_status ladder_backward(ladder_plan_t pl, const double *B, const double *t
   if (!dev_ptr_ok(B) || !dev_ptr_ok(tau) || !dev_ptr_ok(W)) return LADDER_EINVAL;
   if (dtau && (!dev_ptr_ok(dtau) || dtau == W || dtau == tau || dtau == B)) return LADDER_EINVAL;
   if (dB && (!dev_ptr_ok(dB) || dB == B)) return LADDER_EINVAL;
+  if (pl->mode == LADDER_OZAKI) {
+    // with B symmetric the transposed ladder is the ladder itself, so dtau
+    // comes from the error-free forward passes; this mode has no dB
+    if (dB || !pl->sym_b) return LADDER_ENOTSUP;
+    return dtau ? apply_oz(pl, B, W, dtau, static_cast<cudaStream_t>(stream)) : LADDER_OK;
+  }
   if (dB && !pl->backward) return LADDER_EWORKSPACE;
-  if (pl->mode == LADDER_OZAKI || pl->ntiles_tc != pl->ntiles_all) return LADDER_ENOTSUP;
+  if (pl->ntiles_tc != pl->ntiles_all) return LADDER_ENOTSUP;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (dtau) {
     // transposed ladder: dtau = sum_ab W_ij^ab (ac|bd), i.e. the ladder of W

@@ -130,11 +130,13 @@ def test_backward_full_size_sampled(lad, mode):
     assert np.array_equal(dtau, dtau.transpose(1, 0, 3, 2))
 
 
-def test_autograd_error_free_forward_split_adjoint(lad):
+@pytest.mark.parametrize("sym_b", [0, 1])
+def test_autograd_error_free_forward_split_adjoint(lad, sym_b):
     """Gradient workload o=16, v=200, N_aux=800 through the autograd Function
     with an error-free forward plan and a BF16X6 plan for the adjoint: E_L
     within 1 uEh of the stored oracle value, and 1024 stored entries each of
-    dE/dtau and dE/dB within the BF16X6 bar."""
+    dE/dtau and dE/dB within the BF16X6 bar; with sym_b the forward plan
+    gives dE/dtau itself, error-free (within 1e-10)."""
     import json
     import os
     import torch
@@ -149,7 +151,7 @@ def test_autograd_error_free_forward_split_adjoint(lad):
     B = to_dev(x.B).requires_grad_(True)
     tau = to_dev(oracle.tau(x.t1, x.t2)).requires_grad_(True)
     t2 = to_dev(x.t2)
-    L = lad.Ladder(w.o, w.v, w.naux, mode="ozaki")
+    L = lad.Ladder(w.o, w.v, w.naux, mode="ozaki", tuning={"sym_b": sym_b})
     Lg = lad.Ladder(w.o, w.v, w.naux, mode="bf16x6", backward=True)
     E = ladder_energy(B, tau, t2, L, Lg)
     E.backward()
@@ -162,8 +164,36 @@ def test_autograd_error_free_forward_split_adjoint(lad):
     P, xx, yy = (np.asarray(t) for t in g["dB_index"])
     e_tau = rel_err(dtau[i, j, c, d], np.asarray(g["dtau"]))
     e_B = rel_err(dB[P, xx, yy], np.asarray(g["dB"]))
-    print("ozaki forward + bf16x6 adjoint: |dE_L| %.3e  dtau rel %.3e  dB rel %.3e" % (dE, e_tau, e_B))
+    print("ozaki (sym_b %d) forward + bf16x6 adjoint: |dE_L| %.3e  dtau rel %.3e  dB rel %.3e" % (sym_b, dE, e_tau, e_B))
     assert dE <= 1e-6
-    assert e_tau < DTAU_TOL["bf16x6"] and e_B < DTAU_TOL["bf16x6"]
+    assert e_tau < (1e-10 if sym_b else DTAU_TOL["bf16x6"]) and e_B < DTAU_TOL["bf16x6"]
     with pytest.raises(ValueError):
         ladder_energy(B, tau, t2, L, lad.Ladder(4, 24, 96, mode="bf16x6", backward=True))
+
+
+@pytest.mark.parametrize("o,v,n,seed", [(3, 10, 30, 4), (7, 41, 70, 14)])
+def test_error_free_dtau_with_symmetric_B(lad, o, v, n, seed):
+    """ladder_backward on an error-free plan with sym_b: dE/dtau (the forward
+    of W, since B is symmetric) against the oracle's gradient within 1e-10
+    (worst entry included); dE/dB and plans without sym_b are refused."""
+    import torch
+    x = synthetic.make_inputs(o, v, n, seed)
+    tau = oracle.tau(x.t1, x.t2)
+    W = oracle.energy_weights(x.t2)
+    g_o = oracle.grad_tau(x.B, W)
+    L = lad.Ladder(o, v, n, mode="ozaki", tuning={"sym_b": 1})
+    dtau, _ = L.backward(to_dev(x.B), to_dev(tau), to_dev(W), dtau=True, dB=False)
+    torch.cuda.synchronize()
+    L.check_device()
+    got = dtau.cpu().numpy()
+    err = rel_err(got, g_o)
+    emax = float(np.abs(got - g_o).max() / np.abs(g_o).max())
+    print("error-free dtau o=%d v=%d n=%d: rel-F %.3e  max %.3e" % (o, v, n, err, emax))
+    assert err < 1e-10 and emax < 1e-10
+    with pytest.raises(lad.LadderError):
+        L.backward(to_dev(x.B), to_dev(tau), to_dev(W), dtau=True, dB=True)
+    L.close()
+    G = lad.Ladder(o, v, n, mode="ozaki")
+    with pytest.raises(lad.LadderError):
+        G.backward(to_dev(x.B), to_dev(tau), to_dev(W), dtau=True, dB=False)
+    G.close()
