@@ -872,7 +872,8 @@ def main():
     if args.backward and args.mode in ("bf16x3", "bf16x6", "ozaki"):
         # the adjoint of E_L: dE/dtau (the transposed ladder) and dE/dB (Gamma
         # stored once, then contracted), in the same split mode and tuning, or
-        # in BF16X6 behind the error-free forward (which has no adjoint)
+        # in BF16X6 behind the error-free forward (which has no dE/dB), and
+        # the error-free dE/dtau of the symmetric-B form
         bmode = "bf16x6" if args.mode == "ozaki" else args.mode
         Lb = lad.Ladder(w.o, w.v, w.naux, mode=bmode, device=dev,
                         tuning=tuned_for(w, bmode) if args.mode == "ozaki" else tun, backward=True)
@@ -893,10 +894,27 @@ def main():
         bw["dtau_tflops"] = F / (bw["dtau_ms"] * 1e-3) / 1e12
         bw["mode"] = bmode
         bw["note"] = "dtau_tflops counts F_alg (the transposed ladder has the forward's flops)"
-        extra["backward"] = bw
         Lb.close()
         del Lb
         torch.cuda.empty_cache()
+        if sym:
+            # error-free dE/dtau: with B symmetric the transposed ladder is the
+            # forward of W, which the headline's error-free plan computes
+            Le = lad.Ladder(w.o, w.v, w.naux, mode="ozaki", device=dev, tuning=tuning)
+            lad.ladder_backward(Le.plan, B, tau, Wt, dt, None)  # warm-up
+            torch.cuda.synchronize()
+            b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            b0.record(stream)
+            lad.ladder_backward(Le.plan, B, tau, Wt, dt, None)
+            b1.record(stream)
+            torch.cuda.synchronize()
+            Le.check_device()
+            bw["dtau_error_free_ms"] = b0.elapsed_time(b1)
+            bw["dtau_error_free_tflops"] = F / (bw["dtau_error_free_ms"] * 1e-3) / 1e12
+            Le.close()
+            del Le
+            torch.cuda.empty_cache()
+        extra["backward"] = bw
 
     cpu = None
     if rank == 0 and not args.no_cpu:
