@@ -84,7 +84,8 @@ typedef enum {
  * B^P_ca, the RI factors of real orbitals) it forms each distinct integral
  * tile once instead of GEMM1 per (ab tile, block pair).  ladder_backward
  * gives dtau only, with sym_b (see there).  ladder_apply_dressed runs its
- * correction in FP64 in this mode. */
+ * correction in double-single FP32 arithmetic in this mode (compensated dot
+ * products, about 48 bits). */
 
 /* OR this into `mode` to size the workspace for ladder_backward as well
  * (the FP64 gradient with respect to B spills tiles of Gamma^{xb}_{yd}). */

@@ -24,7 +24,8 @@
 //                   forms Bd = B - mbar (one v x v product per P, K = o),
 //                   (kc|ld), X and the two t1 contractions of the correction
 //   reduce_kernel   sums split-K partials
-// T is double for the FP64 path and float for the split-BF16 paths (the
+// T is double for the FP64 path, DS (double-single on the FP32 pipe, about
+// 48 bits) for the error-free mode, and float for the split-BF16 paths (the
 // correction is about 1e-4 of R there, so FP32 keeps it far inside their
 // tolerance).
 #include <algorithm>
@@ -34,6 +35,57 @@
 
 namespace ladder {
 namespace {
+
+// ---------------------------------------------------------------- double-single
+// h + l, an unevaluated sum of two floats.  A product keeps the rounding error
+// of h h' (an FMA gives it exactly) and the cross terms in its low word; a sum
+// adds the high words with Knuth's TwoSum and collects that error and the low
+// words in the low word, without renormalising: the accumulation of a dot
+// product is then the compensated Dot2 of Ogita, Rump and Oishi (SIAM J. Sci.
+// Comput. 26, 2005), as accurate as a dot product in about 48 bits.  Values
+// are renormalised (Dekker's Fast2Sum) only where they are stored.
+__device__ __forceinline__ DS ds_make(double x) {
+  DS r;
+  r.h = __double2float_rn(x);
+  r.l = __double2float_rn(x - (double)r.h);
+  return r;
+}
+__device__ __forceinline__ DS ds_norm(float s, float e) {
+  DS r;
+  r.h = __fadd_rn(s, e);
+  r.l = __fsub_rn(e, __fsub_rn(r.h, s));
+  return r;
+}
+__device__ __forceinline__ DS operator*(DS a, DS b) {
+  DS r;
+  r.h = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -r.h);
+  e = __fmaf_rn(a.h, b.l, e);
+  r.l = __fmaf_rn(a.l, b.h, e);
+  return r;
+}
+__device__ __forceinline__ DS operator+(DS a, DS b) {
+  DS r;
+  r.h = __fadd_rn(a.h, b.h);
+  const float bb = __fsub_rn(r.h, a.h);
+  const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(r.h, bb)), __fsub_rn(b.h, bb));
+  r.l = __fadd_rn(__fadd_rn(a.l, b.l), e);
+  return r;
+}
+__device__ __forceinline__ DS &operator+=(DS &a, DS b) { return a = a + b; }
+__device__ __forceinline__ DS &operator*=(DS &a, DS b) { return a = a * b; }
+// conversions between the GEMM's types
+template <typename T> __device__ __forceinline__ T to_t(double x) { return (T)x; }
+template <> __device__ __forceinline__ DS to_t<DS>(double x) { return ds_make(x); }
+template <typename T> __device__ __forceinline__ T to_t(float x) { return (T)x; }
+template <typename T> __device__ __forceinline__ T to_t(DS x) { return (T)((double)x.h + (double)x.l); }
+template <> __device__ __forceinline__ DS to_t<DS>(DS x) { return x; }
+// the value as stored: a double-single renormalised (|l| <= ulp(h) / 2)
+template <typename T> __device__ __forceinline__ T ds_store(T x) { return x; }
+template <> __device__ __forceinline__ DS ds_store<DS>(DS x) { return ds_norm(x.h, x.l); }
+__device__ __forceinline__ double to_double(double x) { return x; }
+__device__ __forceinline__ double to_double(float x) { return x; }
+__device__ __forceinline__ double to_double(DS x) { return (double)x.h + (double)x.l; }
 
 // ---------------------------------------------------------------- CUDA-core GEMM
 constexpr int kBM = 128, kBN = 128, kBK = 8;
@@ -47,6 +99,12 @@ __device__ __forceinline__ void load4(const double *p, double *r) {
   const double2 x = *reinterpret_cast<const double2 *>(p);
   const double2 y = *reinterpret_cast<const double2 *>(p + 2);
   r[0] = x.x; r[1] = x.y; r[2] = y.x; r[3] = y.y;
+}
+__device__ __forceinline__ void load4(const DS *p, DS *r) {
+  const float4 x = *reinterpret_cast<const float4 *>(p);
+  const float4 y = *reinterpret_cast<const float4 *>(p + 2);
+  r[0].h = x.x; r[0].l = x.y; r[1].h = x.z; r[1].l = x.w;
+  r[2].h = y.x; r[2].l = y.y; r[3].h = y.z; r[3].l = y.w;
 }
 
 // Operand loader: element (row, k) of a [rows x K] operand at
@@ -63,7 +121,7 @@ __device__ __forceinline__ void gemm_fetch(const TM *__restrict__ base, long lon
     const int rr = kfast ? e / kBK : e % kBM;
     const int kk = kfast ? e % kBK : e / kBM;
     const int row = row0 + rr, k = k0 + kk;
-    reg[r] = (row < rows && k < kend) ? (T)base[(long long)row * srow + (long long)k * sk] : T(0);
+    reg[r] = (row < rows && k < kend) ? to_t<T>(base[(long long)row * srow + (long long)k * sk]) : to_t<T>(0.0);
   }
 }
 template <typename T>
@@ -121,7 +179,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) gemm_kernel(const
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
+    for (int j = 0; j < 8; ++j) acc[i][j] = to_t<T>(0.0);
 
   // an optional second K segment (A2, B2, K2; B2 scaled by beta2) follows
   // the first in the same accumulators
@@ -142,7 +200,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) gemm_kernel(const
     gemm_fetch(A2, g.sam2, g.sak2, g.M, m0, kk, g.K2, akf2, ra);
     gemm_fetch(B2, g.sbn2, g.sbk2, g.N, n0, kk, g.K2, bkf2, rb);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) rb[r] *= (T)g.beta2;
+    for (int r = 0; r < 4; ++r) rb[r] *= to_t<T>(g.beta2);
     return true;
   };
   auto stage = [&](int buf, bool seg2) {
@@ -226,7 +284,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) gemm_kernel(const
     static_assert(32 * (kBN + 1) <= 2 * 2 * kBK * (kBM + kPadF), "stage fits the operand rings");
     T *stage = sAB;
     T *O = static_cast<T *>(g.Out) + (long long)batch * g.so_batch;
-    const T alpha = (T)g.alpha;
+    const T alpha = to_t<T>(g.alpha);
     for (int sl = 0; sl < 4; ++sl) {
       // rows 32 sl .. 32 sl + 31 belong to ty in [8 (sl & 1), 8 (sl & 1) + 8), half sl >> 1
       if ((ty >> 3) == (sl & 1)) {
@@ -236,7 +294,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) gemm_kernel(const
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const int c = j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4);
-            stage[r * (kBN + 1) + c] = acc[(sl >> 1) ? 4 + i : i][j];
+            stage[r * (kBN + 1) + c] = ds_store(acc[(sl >> 1) ? 4 + i : i][j]);
           }
         }
       }
@@ -263,7 +321,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) gemm_kernel(const
     for (int j = 0; j < 8; ++j) {
       const int n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
       if (n >= g.N) continue;
-      const T val = acc[i][j];
+      const T val = ds_store(acc[i][j]);
       if (g.epi == kEpiStore) {
         static_cast<T *>(g.Out)[(long long)z * g.so_batch + (long long)m * g.ldo + n] = val;
       } else if (g.epi == kEpiPerm) {
@@ -277,14 +335,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) gemm_kernel(const
       } else if (g.epi == kEpiAcc3) {
         T *O = static_cast<T *>(g.Out) + (long long)batch * g.so_batch + (long long)(m / g.pv) * g.s1 +
                (long long)(m % g.pv) * g.s2 + (long long)n * g.s3;
-        const T x = (T)g.alpha * val;
+        const T x = to_t<T>(g.alpha) * val;
         *O = g.acc ? *O + x : x;
       } else if (g.epi == kEpiSubR) {  // R -= val (FP64 result)
         double *R = static_cast<double *>(g.Out);
-        R[(long long)batch * g.so_batch + (long long)m * g.ldo + n] -= (double)val;
+        R[(long long)batch * g.so_batch + (long long)m * g.ldo + n] -= to_double(val);
       } else {  // kEpiFromSrc: Out = Src - val (FP64)
         const long long at = (long long)batch * g.so_batch + (long long)m * g.ldo + n;
-        static_cast<double *>(g.Out)[at] = g.Src[at] - (double)val;
+        static_cast<double *>(g.Out)[at] = g.Src[at] - to_double(val);
       }
     }
   }
@@ -296,7 +354,7 @@ __global__ void reduce_kernel(T *__restrict__ X, long long n, int parts) {
        e += (long long)gridDim.x * blockDim.x) {
     T s = X[e];
     for (int p = 1; p < parts; ++p) s += X[(long long)p * n + e];
-    X[e] = s;
+    X[e] = ds_store(s);
   }
 }
 
@@ -327,6 +385,9 @@ template cudaError_t launch_gemm<double, double, float>(const GemmArgs &, int, c
 template cudaError_t launch_gemm<double, float, float>(const GemmArgs &, int, cudaStream_t);
 template cudaError_t launch_gemm<float, double, float>(const GemmArgs &, int, cudaStream_t);
 template cudaError_t launch_gemm<float, float, float>(const GemmArgs &, int, cudaStream_t);
+template cudaError_t launch_gemm<double, double, DS>(const GemmArgs &, int, cudaStream_t);
+template cudaError_t launch_gemm<double, DS, DS>(const GemmArgs &, int, cudaStream_t);
+template cudaError_t launch_gemm<DS, double, DS>(const GemmArgs &, int, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_reduce(T *X, long long n, int parts, cudaStream_t s) {
@@ -337,5 +398,6 @@ cudaError_t launch_reduce(T *X, long long n, int parts, cudaStream_t s) {
 }
 template cudaError_t launch_reduce<double>(double *, long long, int, cudaStream_t);
 template cudaError_t launch_reduce<float>(float *, long long, int, cudaStream_t);
+template cudaError_t launch_reduce<DS>(DS *, long long, int, cudaStream_t);
 
 }  // namespace ladder

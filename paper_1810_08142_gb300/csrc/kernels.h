@@ -60,6 +60,13 @@ struct GemmArgs {
   double alpha;
   int ntm, ntn, zoff;  // set by the launcher
 };
+// Double-single number (an unevaluated sum h + l of two floats, about 48
+// bits): the accumulation type of the error-free mode's dressing correction,
+// which runs on the FP32 pipe (far faster than FP64 on this GPU).  Its
+// arithmetic is defined where the GEMM kernel is (dress.cu).
+struct DS {
+  float h, l;
+};
 template <typename TA, typename TB, typename T>
 cudaError_t launch_gemm(const GemmArgs &g, int batch, cudaStream_t s);
 template <typename T>

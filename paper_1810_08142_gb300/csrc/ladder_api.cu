@@ -1650,7 +1650,11 @@ ladder_status ladder_apply_dressed(ladder_plan_t pl, const double *B, const doub
        : pl->mode == LADDER_OZAKI ? apply_oz(pl, Bd, tau, R, s, nullptr, false)
                                   : apply_tc(pl, Bd, tau, R, s);
   if (st != LADDER_OK) return st;
-  st = f64 ? dress_correct<double>(pl, Bov, t1, tau, R, s) : dress_correct<float>(pl, Bov, t1, tau, R, s);
+  // the correction's GEMMs: FP64 for the plain method, double-single on the
+  // FP32 pipe for the error-free mode, FP32 for the split-BF16 modes
+  st = pl->mode == LADDER_FP64    ? dress_correct<double>(pl, Bov, t1, tau, R, s)
+       : pl->mode == LADDER_OZAKI ? dress_correct<DS>(pl, Bov, t1, tau, R, s)
+                                  : dress_correct<float>(pl, Bov, t1, tau, R, s);
   mark(pl, 7, s);
   return st;
 }

@@ -3,7 +3,8 @@ with the CPU oracle, through ladder_apply_dressed.
 
 The library evaluates the undressed ladder of B - mbar in the plan's mode and
 subtracts the rank-o correction sum_kl t_k^a t_l^b sum_cd (kc|ld) tau_ij^cd
-(FP64 for LADDER_FP64 and the error-free mode, FP32 otherwise); the oracle
+(FP64 for LADDER_FP64, double-single FP32 for the error-free mode, FP32
+otherwise); the oracle
 follows Eq. pp-Ladder-2 term by term.  Tolerances on the relative Frobenius
 error of R are those of the undressed term: FP64 1e-12, the error-free split
 1e-10, BF16X6 1e-6, BF16X3 2e-5.
