@@ -96,7 +96,8 @@ typedef enum {
 
 /* Create a plan for one shape.  1 <= o <= 256, 1 <= v <= 4096, 1 <= naux <= 65536.
  * The plan owns no device memory; see ladder_workspace_size.  LADDER_OZAKI
- * with LADDER_WITH_BACKWARD returns LADDER_ENOTSUP. */
+ * with LADDER_WITH_BACKWARD returns LADDER_ENOTSUP (its dtau needs no
+ * backward workspace and it has no dB; see ladder_backward). */
 ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out);
 
 /* Launch parameters of the split-BF16 kernel (ignored by LADDER_FP64):
