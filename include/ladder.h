@@ -147,9 +147,11 @@ ladder_status ladder_plan(int o, int v, int naux, int mode, ladder_plan_t *out);
  *               the rounding of the tail slice orders (about 2^-48 of each
  *               integral).  Every ladder_apply checks
  *               the symmetry bitwise on the device; a B that breaks it makes
- *               ladder_last_device_error return LADDER_EINVAL.  Not with a
- *               tile range, a plan made LADDER_WITH_DRESSING, or distinct
- *               tiles above 96 GiB (v above about 550): LADDER_ENOTSUP.
+ *               ladder_last_device_error return LADDER_EINVAL.  A plan with
+ *               a tile range (ladder_set_tile_range) forms all the distinct
+ *               tiles and V+- of its own tiles.  Not with a plan made
+ *               LADDER_WITH_DRESSING, or distinct tiles above 96 GiB (v
+ *               above about 550): LADDER_ENOTSUP.
  * Longer chains are faster and less accurate (the tensor core's FP32
  * accumulation error grows with the MMAs per accumulator).  ladder_set_tuning
  * must come before ladder_set_workspace (the workspace size depends on
@@ -182,9 +184,11 @@ ladder_status ladder_plan_shape(ladder_plan_t plan, int *o, int *v, int *naux);
  * b in [8 jB, 8 jB + 8) for iA = 0, 1, ... and jB = 2 iA .. vp/8 - 1 (vp = v
  * rounded up to 16).  LADDER_FP64 plans return LADDER_ENOTSUP; a plan with a
  * partial range refuses ladder_backward and ladder_apply_dressed
- * (LADDER_ENOTSUP).  The range also sets the plan's block-pair splits
- * (ksplit) anew; set ksplit afterwards with ladder_set_tuning to match
- * another plan's. */
+ * (LADDER_ENOTSUP).  A LADDER_OZAKI plan with sym_b forms all the distinct
+ * integral tiles in every range (they serve every tile) and V+- of its own
+ * tiles only.  The range also sets the plan's block-pair splits (ksplit)
+ * anew; set ksplit afterwards with ladder_set_tuning to match another
+ * plan's. */
 ladder_status ladder_tile_count(ladder_plan_t plan, int *ntiles);
 ladder_status ladder_set_tile_range(ladder_plan_t plan, int tile_lo, int tile_hi);
 

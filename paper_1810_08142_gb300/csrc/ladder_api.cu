@@ -1082,10 +1082,10 @@ ladder_status ladder_set_tuning(ladder_plan_t pl, const ladder_tuning *t) {
     if ((t->oz_slices != 0 && t->oz_slices != 5 && t->oz_slices != 6) || t->ksplit < 0 || t->ksplit > pl->nbp ||
         t->two_pass != 1 || t->lambda_only != 0 || t->tile_chunk < 0 || (t->sym_b != 0 && t->sym_b != 1))
       return LADDER_EINVAL;
-    // the distinct integral tiles serve every tile of the shape: not with a
-    // tile range, and only while they fit their cap
-    if (t->sym_b && (pl->ntiles_tc != pl->ntiles_all || pl->dressed || (double)xsym_bytes(pl) > kXsymCap))
-      return LADDER_ENOTSUP;
+    // the distinct integral tiles serve every tile of the shape (a plan with
+    // a tile range forms all of them and V+- of its own tiles), while they
+    // fit their cap; B - mbar of the dressed term is not symmetric
+    if (t->sym_b && (pl->dressed || (double)xsym_bytes(pl) > kXsymCap)) return LADDER_ENOTSUP;
     if (t->oz_slices) pl->oz_slices = pl->S = t->oz_slices;
     pl->tile_chunk = t->tile_chunk;
     pl->sym_b = t->sym_b;
@@ -1134,7 +1134,6 @@ ladder_status ladder_set_tile_range(ladder_plan_t pl, int tile_lo, int tile_hi) 
   if (!pl || pl->batched || pl->ws) return LADDER_EINVAL;
   if (pl->mode == LADDER_FP64) return LADDER_ENOTSUP;
   if (tile_lo < 0 || tile_hi > pl->ntiles_all || tile_lo >= tile_hi) return LADDER_EINVAL;
-  if (pl->sym_b) return LADDER_ENOTSUP;
   pl->tile0 = tile_lo;
   pl->ntiles_tc = tile_hi - tile_lo;
   pl->ksplit = auto_ksplit(pl);
@@ -1710,7 +1709,7 @@ ladder_status ladder_backward(ladder_plan_t pl, const double *B, const double *t
   if (pl->mode == LADDER_OZAKI) {
     // with B symmetric the transposed ladder is the ladder itself, so dtau
     // comes from the error-free forward passes; this mode has no dB
-    if (dB || !pl->sym_b) return LADDER_ENOTSUP;
+    if (dB || !pl->sym_b || pl->ntiles_tc != pl->ntiles_all) return LADDER_ENOTSUP;
     return dtau ? apply_oz(pl, B, W, dtau, static_cast<cudaStream_t>(stream)) : LADDER_OK;
   }
   if (dB && !pl->backward) return LADDER_EWORKSPACE;

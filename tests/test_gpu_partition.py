@@ -23,15 +23,19 @@ def lad():
     return lad
 
 
-@pytest.mark.parametrize("mode,two_pass", [("bf16x6", 1), ("bf16x6", 0), ("ozaki", 1)])
+@pytest.mark.parametrize("mode,two_pass", [("bf16x6", 1), ("bf16x6", 0), ("ozaki", 1), ("ozaki_sym", 1)])
 def test_two_ranges_assemble_the_full_term(lad, mode, two_pass):
+    """ozaki_sym: the error-free mode's symmetric-B form, where each range's
+    plan forms all the distinct integral tiles and V+- of its own tiles."""
     import torch
     from paper_1810_08142_gb300 import partition as pt
     o, v, n, seed = 7, 41, 70, 14
     x = synthetic.make_inputs(o, v, n, seed)
     tau_h = oracle.tau(x.t1, x.t2)
     B, tau = to_dev(x.B), to_dev(tau_h)
-    tun = {"ksplit": 2} if mode == "ozaki" else {"two_pass": two_pass, "ksplit": 2}
+    tun = ({"ksplit": 2, "sym_b": 1} if mode == "ozaki_sym" else {"ksplit": 2} if mode == "ozaki"
+           else {"two_pass": two_pass, "ksplit": 2})
+    mode = "ozaki" if mode == "ozaki_sym" else mode
     L = lad.Ladder(o, v, n, mode=mode, tuning=tun)
     ntiles = lad.ladder_tile_count(L.plan)
     assert ntiles == pt.tile_count(v)
